@@ -1,0 +1,217 @@
+"""FP64 CPU oracle of the slope-decoupled DG2 scheme (Sec. 2.1, Eqs. 1-7, 11).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow statement of the method that the
+CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference legs may import this package; the
+product library never does, and this package imports nothing from it.
+
+The arithmetic lives in ``dg2_oracle.c`` (plain C, built with
+``-ffp-contract=off``); this module only builds it with gcc and marshals numpy
+arrays through ctypes.
+
+Parity status per function (pins live in ``tests/test_oracle_*.py``):
+  - spatial operator, HLL flux, RK2 step, mass: pinned (lake at rest, wall
+    balance, closed-wall mass, Ritter/Stoker closed forms, order of accuracy,
+    transposition / mirror symmetry).
+  - friction: pinned by the exact solution of the friction ODE at the centre
+    and at every Gauss point.
+  - limiter: pinned by brute-force detector / minmod cases.
+  - inflow ghost and point/rain sources: parity unpinned beyond the mass
+    ledger (the paper does not define them).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dg2_oracle.c")
+_LIB = os.path.join(_HERE, "libdg2_oracle.so")
+
+WALL, OPEN = 0, 1
+WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) into oracle/libdg2_oracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "orc_create": (P, [I, I, D, D, D, D, D, D, D, I, ip]),
+        "orc_destroy": (None, [P]),
+        "orc_set_dem": (None, [P, dp, dp, D, dp]),
+        "orc_add_inflow": (I, [P, I, D, D, dp, dp, I]),
+        "orc_set_sources": (None, [P, D, D, D, D, D, D]),
+        "orc_cfl_dt": (D, [P]),
+        "orc_step": (None, [P, D]),
+        "orc_get_state": (None, [P, dp, dp]),
+        "orc_set_state": (None, [P, dp, D]),
+        "orc_get_topo": (None, [P, dp]),
+        "orc_time": (D, [P]),
+        "orc_ledger": (D, [P]),
+        "orc_mass": (D, [P]),
+        "orc_operator": (D, [P, dp, D, dp]),
+        "orc_friction": (None, [P, dp, D]),
+        "orc_limit": (None, [P, dp, dp]),
+        "orc_hll": (None, [P, I, dp, dp, dp]),
+        "orc_minmod": (D, [D, D, D]),
+        "orc_gauge_h": (D, [P, D, D]),
+        "orc_run_to": (ctypes.c_long, [P, D, D, I, dp, dp, dp, I, ip]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def minmod(a: float, b: float, c: float) -> float:
+    return _load().orc_minmod(a, b, c)
+
+
+class Oracle:
+    """One DG2 problem on an nx x ny grid (x index fastest), FP64 on the CPU.
+
+    State arrays are (9, ny, nx): planes h0, h1x, h1y, qx0, qx1x, qx1y, qy0,
+    qy1x, qy1y (Eq. 2).  Corner arrays are (ny+1, nx+1).
+    """
+
+    def __init__(self, nx, ny, dx, dy, *, g=9.80665, cfl=0.33, tol_dry=1e-5, ds_thresh=10.0,
+                 dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL)):
+        self.lib = _load()
+        self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
+        self.g, self.cfl, self.tol_dry = g, cfl, tol_dry
+        bca = (ctypes.c_int * 4)(*[int(b) for b in bc])
+        self.h = self.lib.orc_create(self.nx, self.ny, self.dx, self.dy, g, cfl, tol_dry, ds_thresh,
+                                     dt_max, int(bool(limiter)), bca)
+        if not self.h:
+            raise ValueError("bad grid size")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.orc_destroy(h)
+            self.h = None
+
+    # -- set-up ---------------------------------------------------------
+    def set_dem(self, z_corner, manning=None, n_uniform=0.0, eta_corner=None):
+        z = _f64(z_corner)
+        assert z.shape == (self.ny + 1, self.nx + 1)
+        m = None if manning is None else _f64(manning)
+        e = None if eta_corner is None else _f64(eta_corner)
+        self.lib.orc_set_dem(self.h, _dp(z), _dp(m), float(n_uniform), _dp(e))
+
+    def add_inflow(self, edge, s0, length, t_knots, q_knots):
+        tk, qk = _f64(t_knots), _f64(q_knots)
+        if self.lib.orc_add_inflow(self.h, int(edge), float(s0), float(length), _dp(tk), _dp(qk),
+                                   len(tk)) != 0:
+            raise ValueError("inflow rejected")
+
+    def set_sources(self, rain=0.0, rain_t0=0.0, rain_t1=0.0, px=0.0, py=0.0, qp=0.0):
+        self.lib.orc_set_sources(self.h, rain, rain_t0, rain_t1, px, py, qp)
+
+    # -- stepping -------------------------------------------------------
+    def cfl_dt(self) -> float:
+        return self.lib.orc_cfl_dt(self.h)
+
+    def step(self, dt=None) -> float:
+        if dt is None or dt <= 0:
+            dt = self.cfl_dt()
+        self.lib.orc_step(self.h, float(dt))
+        return dt
+
+    def run_to(self, t_end, sample_every=0.0, gauges_xy=None, cap=100000):
+        g = np.zeros((0, 2)) if gauges_xy is None else _f64(gauges_xy).reshape(-1, 2)
+        ng = g.shape[0]
+        t_out = np.zeros(cap)
+        h_out = np.zeros((cap, max(ng, 1)))
+        ns = ctypes.c_int(0)
+        steps = self.lib.orc_run_to(self.h, float(t_end), float(sample_every), ng, _dp(_f64(g)),
+                                    _dp(t_out), _dp(h_out), cap, ctypes.byref(ns))
+        n = min(ns.value, cap)
+        return steps, t_out[:n].copy(), h_out[:n, :ng].copy()
+
+    # -- state ----------------------------------------------------------
+    @property
+    def t(self) -> float:
+        return self.lib.orc_time(self.h)
+
+    def state(self):
+        out = np.zeros((9, self.ny, self.nx))
+        self.lib.orc_get_state(self.h, _dp(out), None)
+        return out
+
+    def set_state(self, planes, t=0.0):
+        p = _f64(planes)
+        assert p.shape == (9, self.ny, self.nx)
+        self.lib.orc_set_state(self.h, _dp(p), float(t))
+
+    def topo(self):
+        out = np.zeros((3, self.ny, self.nx))
+        self.lib.orc_get_topo(self.h, _dp(out))
+        return out
+
+    def mass(self) -> float:
+        return self.lib.orc_mass(self.h)
+
+    def ledger(self) -> float:
+        return self.lib.orc_ledger(self.h)
+
+    def gauge_h(self, x, y) -> float:
+        return self.lib.orc_gauge_h(self.h, float(x), float(y))
+
+    # -- pieces for pin tests -------------------------------------------
+    def operator(self, planes, t=0.0):
+        p = _f64(planes)
+        out = np.zeros_like(p)
+        b = self.lib.orc_operator(self.h, _dp(p), float(t), _dp(out))
+        return out, b
+
+    def friction(self, planes, dt):
+        p = _f64(planes).copy()
+        self.lib.orc_friction(self.h, _dp(p), float(dt))
+        return p
+
+    def limit(self, planes):
+        p = _f64(planes)
+        out = np.zeros_like(p)
+        self.lib.orc_limit(self.h, _dp(p), _dp(out))
+        return out
+
+    def hll(self, direction, left, right):
+        l, r = _f64(left), _f64(right)
+        f = np.zeros(3)
+        self.lib.orc_hll(self.h, int(direction), _dp(l), _dp(r), _dp(f))
+        return f
