@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 DG2 flood solver (cell-updates per second).
+
+Workload: the synthetic floodplain, 2000 x 1000 cells at dx = 2 m (fBm terrain,
+Hurst 0.8, 3 m relief, incised sinuous channel holding 1 m of water, triangular
+20 m^3/s inflow hydrograph on a 40 m west-edge segment, Manning 0.035 / 0.05,
+transmissive east/south/north edges), FP64.  A step is one full RK2 time step
+(friction, [local limiting], both stages with fluxes, operators, wet-dry
+treatment, Courant reduction, time/ledger update) through the C ABI.
+
+One line of JSON on rank 0.  With --impl reference the CPU oracle is timed
+instead (a bounded 500 x 250 sample of the same workload recipe).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG2 cell-updates/s (FP64, FP32) & % HBM roofline; adjoint/forward time ratio"
+NX, NY, DX = 2000, 1000, 2.0
+# Unique bytes each kernel must move per cell (FP64): see the design doc (roofline section).
+BYTES_PER_CELL = {
+    "friction": 16 * 8,
+    "stage1": {"nl": 21 * 8, "ll": 27 * 8},
+    "stage2": {"nl": 30 * 8, "ll": 30 * 8},
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(nx=NX, ny=NY, dx=DX):
+    from paper_2010_02003_gb300 import inputs
+    return inputs.floodplain(nx=nx, ny=ny, dx=dx, initial="channel")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def time_variant(B, torch, case, variant, steps, warmup, timing=True):
+    """Device-timed steps of one variant; returns dict of timings."""
+    s = B.solver_from_case(case, variant=variant)
+    st = s.stream
+    for _ in range(warmup):
+        s.step(-1.0)
+    torch.cuda.synchronize()
+    wet = float((s.state()[0] > 1e-5).mean())
+    if timing:
+        B.dg2_enable_kernel_timing(s.ctx, True)
+    l0 = s.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    for _ in range(steps):
+        s.step(-1.0)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launches() - l0
+    kt, n = B.dg2_kernel_times(s.ctx) if timing else (np.zeros(3), 0)
+    t_sim, _ = s.time()
+    return {"solver": s, "ms": ms, "launches": launches, "kernel_ms": kt, "timed": n,
+            "wet_fraction": wet, "t_sim": t_sim}
+
+
+def e2e_run(B, torch, case, variant, steps):
+    """Same steps through the public API with host buffers: the initial state goes up
+    from pinned host memory, the final state and the mass come back, all timed."""
+    s = B.solver_from_case(case, variant=variant)
+    nx, ny = case.nx, case.ny
+    init = s.state()
+    pin_in = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    pin_out = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    pin_in[...] = init
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.dg2_set_state(s.ctx, pin_in, 0.0)
+    for _ in range(steps):
+        s.step(-1.0)
+    B.dg2_get_state(s.ctx, nx, ny, out=pin_out)
+    mass, ledger = s.mass()
+    dt_s = time.perf_counter() - t0
+    return dt_s, pin_in.nbytes, pin_out.nbytes + 16
+
+
+def cpu_baseline(case_small, steps_budget_s=15.0, variant_ll=True):
+    import oracle
+    o = oracle.Oracle(case_small.nx, case_small.ny, case_small.dx, case_small.dy, cfl=case_small.cfl,
+                      limiter=variant_ll, bc=case_small.bc)
+    o.set_dem(case_small.z_corner, case_small.manning, case_small.n_uniform, case_small.eta_corner)
+    for f in case_small.inflows:
+        o.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)
+    o.step()
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < steps_budget_s:
+        o.step()
+        n += 1
+    el = time.perf_counter() - t0
+    return case_small.nx * case_small.ny * n / el, n, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    small = workload(500, 250)
+    import oracle
+    o = oracle.Oracle(small.nx, small.ny, small.dx, small.dy, cfl=small.cfl, limiter=True, bc=small.bc)
+    o.set_dem(small.z_corner, small.manning, small.n_uniform, small.eta_corner)
+    for f in small.inflows:
+        o.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    el = time.perf_counter() - t0
+    v = small.nx * small.ny * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "floodplain 500x250 dx=2 m (bounded sample of the 2000x1000 "
+                                   "floodplain recipe), DG2-LL, FP64 CPU oracle"},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} DG2-LL steps on a 500x250 floodplain"},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_2010_02003_gb300 import binding as B, build as build_mod
+    if not os.path.exists(B.LIB_PATH):
+        build_mod.build()
+    torch.cuda.set_device(local)
+    case = workload()
+    cells = case.nx * case.ny
+    warmup = max(3, args.warmup)
+
+    # headline: DG2-LL (every row of the step, limiter included); DG2-NL beside it
+    barrier(world)
+    clk = ClockSampler(local)
+    clk.start()
+    ll = time_variant(B, torch, case, B.DG2_LL, args.steps, warmup)
+    clocks = clk.stop()
+    ms_ll = max_over_ranks(ll["ms"], world)
+    barrier(world)
+    nl = time_variant(B, torch, case, B.DG2_NL, args.steps, warmup)
+    ms_nl = max_over_ranks(nl["ms"], world)
+    value = world * cells * args.steps / (ms_ll * 1e-3)
+    value_nl = world * cells * args.steps / (ms_nl * 1e-3)
+
+    # roofline of the dominant kernel (stage 2 or stage 1 of DG2-LL), live event timing
+    kms = ll["kernel_ms"] / max(ll["timed"], 1)
+    names = ["friction", "stage1", "stage2"]
+    dom = int(np.argmax(kms))
+    per_cell = BYTES_PER_CELL[names[dom]] if dom == 0 else BYTES_PER_CELL[names[dom]]["ll"]
+    pk, pk_src = peaks()
+    achieved = per_cell * cells / (kms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"stage_kernel<LL,{dom}>" if dom else "friction_kernel",
+                "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_src,
+                "kernel_ms": {n: float(k) for n, k in zip(names, kms)}}
+
+    # end to end through the C ABI with host buffers
+    e2e_s, h2d, d2h = e2e_run(B, torch, case, B.DG2_LL, args.steps)
+    e2e = {"value": world * cells * args.steps / max_over_ranks(e2e_s, world),
+           "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / args.steps,
+           "d2h_bytes_per_step": d2h / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, el = cpu_baseline(workload(500, 250))
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} DG2-LL steps of a 500x250 floodplain (same recipe), {el:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": warmup, "ms_per_step": ms_ll / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "floodplain 2000x1000 dx=2 m, DG2-LL, FP64",
+                           "variant": "DG2-LL", "cells": cells,
+                           "wet_fraction": ll["wet_fraction"],
+                           "l2": "inputs larger than L2 (state 2 x 144 MB)",
+                           "parallelism": f"replicas x{world}"},
+                "variants": {"fp64_nl": {"value": value_nl, "ms_per_step": ms_nl / args.steps,
+                                         "wet_fraction": nl["wet_fraction"]}},
+                "gpu_launches": int(ll["launches"]), "roofline": roofline, "e2e": e2e,
+                "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * dg2.h -- C ABI of the GB300 DG2 flood solver.
+ *
+ * The solver advances the slope-decoupled second-order discontinuous Galerkin
+ * (DG2) solution of the 2D shallow water equations of Ayog et al.,
+ * "Second-order discontinuous Galerkin flood model" (Sec. 2.1): per cell an
+ * average and an x- and y-slope coefficient of h, hu, hv (Eq. 2), topography
+ * coefficients from DEM corner nodes (Eq. 3), explicit two-stage RK2 steps of
+ * the operators of Eqs. 4-5 with HLL fluxes, implicit Manning friction
+ * (Sec. 2.1.3), optional local slope limiting (Eqs. 6-7) and a global
+ * Courant-number time step.
+ *
+ * Conventions
+ *  - Grid: nx cells along x (west -> east), ny along y (south -> north); cell
+ *    (i, j) spans [i dx, (i+1) dx] x [j dy, (j+1) dy].  Host arrays are
+ *    row-major with the x index fastest.
+ *  - State planes (host side, dense, ny*nx each), in this order:
+ *    h0, h1x, h1y, qx0, qx1x, qx1y, qy0, qy1x, qy1y  (Eq. 2 coefficients).
+ *  - Corner arrays (DEM, initial free surface) are (ny+1) x (nx+1).
+ *  - Every function returns DG2_OK (0) or a negative DG2_E_* code; the text
+ *    of the last error of the calling thread is in dg2_last_error().
+ *  - Host input arrays are copied before the call returns; the caller keeps
+ *    ownership.  Host output arrays are caller-allocated.
+ *  - Device memory: the caller provides one device workspace of at least
+ *    dg2_workspace_bytes() bytes (e.g. a torch uint8 tensor) and keeps it alive
+ *    until dg2_destroy().  The library allocates no device memory itself.
+ *  - Stream: every kernel and copy is issued on the caller's stream (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream).  Calls that
+ *    return host data synchronise that stream.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef DG2_H
+#define DG2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    DG2_OK = 0,
+    DG2_E_ARG = -1,        /* invalid argument (size, pointer, range)          */
+    DG2_E_STATE = -2,      /* call order (e.g. stepping before dg2_set_dem)     */
+    DG2_E_CUDA = -3,       /* a CUDA runtime call or kernel launch failed       */
+    DG2_E_NONFINITE = -4,  /* a NaN/Inf or a time step <= 0 appeared on device  */
+    DG2_E_NOMEM = -5,      /* workspace smaller than dg2_workspace_bytes()      */
+    DG2_E_OVERFLOW = -7    /* gauge sample buffer full; extra samples dropped   */
+};
+
+enum { DG2_NL = 0, DG2_LL = 1 };            /* DG2-NL: no limiting; DG2-LL: Eqs. 6-7 */
+enum { DG2_FP64 = 0 };                      /* arithmetic of the state and operators */
+enum { DG2_WALL = 0, DG2_OPEN = 1 };        /* edge types                            */
+enum { DG2_WEST = 0, DG2_EAST = 1, DG2_SOUTH = 2, DG2_NORTH = 3 };
+
+typedef struct dg2_params {
+    double g;           /* gravity, m/s^2 (default 9.80665)                         */
+    double cfl;         /* Courant number Cr (Sec. 2.1.2; default 0.3)               */
+    double tol_dry;     /* drying tolerance on h (Sec. 2.1.3; default 1e-5 m)        */
+    double ds_thresh;   /* shock-detector threshold of Eq. 6 (default 10)            */
+    double dt_max;      /* time step when no cell is wet, and upper cap (default 1 s)*/
+    int variant;        /* DG2_NL or DG2_LL                                          */
+    int precision;      /* DG2_FP64                                                  */
+    int bc[4];          /* DG2_WALL or DG2_OPEN per edge, indexed by DG2_WEST..NORTH */
+    int max_gauges;     /* capacity of the gauge table (default 64)                  */
+    int max_samples;    /* capacity of the gauge sample buffer in rows (default 4096)*/
+} dg2_params;
+
+typedef struct dg2_ctx dg2_ctx;
+
+/* Fills *p with the defaults listed above (variant NL, FP64, all walls). */
+void dg2_default_params(dg2_params *p);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *dg2_last_error(void);
+
+/* Device workspace needed for an nx x ny grid under *p (bytes; 0 on bad args).
+ * Holds the state, one stage state, limited-slope scratch (DG2_LL), topography,
+ * Manning n, per-block partials, the gauge buffers and device scalars. */
+size_t dg2_workspace_bytes(int nx, int ny, const dg2_params *p);
+
+/* Creates a context on the current CUDA device.
+ * nx, ny >= 1; dx, dy > 0; p may be NULL for defaults.  dev_workspace must be
+ * 256-byte aligned device memory of ws_bytes >= dg2_workspace_bytes().  The
+ * grid starts dry and flat until dg2_set_dem().  *out receives the context. */
+int dg2_init_grid(dg2_ctx **out, int nx, int ny, double dx, double dy, const dg2_params *p,
+                  void *dev_workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Topography, roughness and initial water (Sec. 2.1.1).
+ * z_corner: (ny+1)*(nx+1) DEM at corner nodes (m), required.
+ * manning: ny*nx per-cell Manning n (s m^-1/3), or NULL to use n_uniform.
+ * eta_corner: (ny+1)*(nx+1) initial free-surface elevation at corners, or NULL
+ *   for a dry start.  Corner depths eta - z are averaged to face nodes and
+ *   turned into modes by Eq. 3 without clipping; a cell whose average depth
+ *   is not positive starts dry.  Discharges start at zero.
+ * Resets t = 0, the mass ledger and the gauge buffer, and computes the first
+ * time step. */
+int dg2_set_dem(dg2_ctx *ctx, const double *z_corner, const double *manning, double n_uniform,
+                const double *eta_corner);
+
+/* Adds an inflow hydrograph Q(t) (m^3/s, piecewise linear in t_knots, held
+ * constant outside them) on the faces of `edge` whose centres lie in
+ * [s0_m, s0_m + len_m] along the edge.  The discharge per unit width is Q
+ * divided by the total length of those faces; it enters through a
+ * critical-depth ghost state.  At most 8 inflows, 4096 knots each, t_knots
+ * strictly increasing.  DG2_E_ARG if no face lies in the segment. */
+int dg2_set_bc_inflow(dg2_ctx *ctx, int edge, double s0_m, double len_m, const double *t_knots,
+                      const double *q_knots, int nknots);
+
+/* Uniform rainfall (m/s) during [rain_t0, rain_t1) and a point inflow
+ * q_point_m3s at (px, py), both added to the average depth equation.  These
+ * sources are not in the paper; they drive the urban-style workloads. */
+int dg2_set_sources(dg2_ctx *ctx, double rain_mps, double rain_t0, double rain_t1, double px,
+                    double py, double q_point_m3s);
+
+/* One RK2 time step (Sec. 2.1.2).  dt > 0 forces that step size; dt <= 0
+ * takes the Courant-number step computed from the current state.  The step
+ * taken is written to *dt_taken (may be NULL; writing it synchronises). */
+int dg2_step(dg2_ctx *ctx, double dt, double *dt_taken);
+
+/* Advances until t_end with Courant-number steps, landing exactly on t_end
+ * and on every gauge sample time.  Runs on the device with no host round
+ * trip per step (chunks of steps; a device flag stops work past t_end).
+ * *steps_taken (may be NULL) receives the number of steps. */
+int dg2_run_to(dg2_ctx *ctx, double t_end, int64_t *steps_taken);
+
+/* Gauges: xy = ngauge (x, y) pairs in metres; depth max(0, planar h) in the
+ * containing cell is recorded at every multiple of sample_every_s reached by
+ * dg2_run_to.  Replaces earlier gauges and clears the sample buffer. */
+int dg2_set_gauges(dg2_ctx *ctx, const double *xy, int ngauge, double sample_every_s);
+
+/* Copies the recorded samples out and clears the buffer: t_out[cap],
+ * h_out[cap][ngauge]; *nsamp = rows written.  DG2_E_OVERFLOW if samples were
+ * dropped since the last read (the rows kept are still returned). */
+int dg2_read_gauges(dg2_ctx *ctx, double *t_out, double *h_out, int cap, int *nsamp);
+
+/* Domain mass sum(h0) dx dy (Eq. 11) and the ledger: initial mass plus the
+ * volume that boundaries and sources added since dg2_set_dem/dg2_set_state.
+ * Either pointer may be NULL. */
+int dg2_mass(dg2_ctx *ctx, double *mass_m3, double *ledger_m3);
+
+/* State in and out: planes = 9 dense ny*nx host planes in the order above. */
+int dg2_get_state(dg2_ctx *ctx, double *planes, double *t);
+int dg2_set_state(dg2_ctx *ctx, const double *planes, double t);
+
+/* Topography modes z0, z1x, z1y (3 dense planes) as computed from the DEM. */
+int dg2_get_topo(dg2_ctx *ctx, double *planes3);
+
+/* Current time and the step size the next Courant step would take. */
+int dg2_get_time(dg2_ctx *ctx, double *t, double *dt_next);
+
+/* Per-kernel timing with CUDA events on the context's stream.  While enabled,
+ * each dg2_step records an event before and after each of its three kernels
+ * (friction, stage 1, stage 2) -- at most 8192 steps between reads.
+ * dg2_kernel_times() synchronises the stream, writes the summed milliseconds
+ * of each kernel to ms[0..2] and the number of steps timed to *nsteps, and
+ * starts a new count.  dg2_run_to is never timed this way. */
+int dg2_enable_kernel_timing(dg2_ctx *ctx, int enable);
+int dg2_kernel_times(dg2_ctx *ctx, double *ms3, int64_t *nsteps);
+
+/* Number of kernels this context has launched (for launch accounting). */
+int64_t dg2_launch_count(const dg2_ctx *ctx);
+
+/* Releases the host-side context (the workspace stays the caller's). */
+int dg2_destroy(dg2_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG2_H */

@@ -20,7 +20,9 @@
  *     before stage 1 (Sec. 2.1.3).
  *   - Local limiter: Jacobi (all cells read the pre-limit state), directional
  *     wet-dry guard over {W,c,E} / {S,c,N}, no limiting normal to a domain
- *     edge, Eq. 6 tested in the division-free form J > thresh * den.
+ *     edge, Eq. 6 tested in the division-free form J > thresh * den, with the
+ *     magnitude in den floored at tol_dry (so round-off in still water, where
+ *     the discharge magnitude vanishes, never counts as a shock).
  *   - RK2: two-stage SSP form; after each stage a wet-dry treatment (dry cells
  *     keep only h0; a wet cell drops to first order in a direction where a face
  *     depth reaches tol_dry at a non-wall face); averages are never clipped.
@@ -424,7 +426,9 @@ static real limit_component(const orc_t *o, real half, real k0w, real k1w, real 
     real jE = fabs((k0e - k1e) - (k0 + k1));           /* |U_E^+ - U_E^-| */
     real jW = fabs((k0 - k1) - (k0w + k1w));           /* |U_W^+ - U_W^-| */
     real a = fabs(k0 - k1 / s3), b = fabs(k0 + k1 / s3);
-    real den = half * (a > b ? a : b);
+    real m = a > b ? a : b;
+    if (m < o->tol_dry) m = o->tol_dry;       /* still water: round-off cannot trigger */
+    real den = half * m;
     real jm = jE > jW ? jE : jW;
     if (!(jm > o->ds_thresh * den)) return k1;          /* Eq. 6 detector: no shock */
     return minmod3(k1, k0e - k0, k0 - k0w);             /* Eq. 7 */

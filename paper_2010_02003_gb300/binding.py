@@ -1,0 +1,328 @@
+"""Python binding of the C ABI in include/dg2.h (argument marshalling only).
+
+Every function named ``dg2_*`` here calls the library function of the same
+name; every step of the solver runs in the library's CUDA kernels.  PyTorch is
+used only to own the device workspace and to supply the CUDA stream.  There is
+no CPU fallback: if ``libdg2.so`` has not been built, or no CUDA device is
+visible, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdg2.so")
+
+DG2_OK, DG2_E_ARG, DG2_E_STATE, DG2_E_CUDA, DG2_E_NONFINITE, DG2_E_NOMEM = 0, -1, -2, -3, -4, -5
+DG2_E_OVERFLOW = -7
+DG2_NL, DG2_LL = 0, 1
+DG2_FP64 = 0
+DG2_WALL, DG2_OPEN = 0, 1
+DG2_WEST, DG2_EAST, DG2_SOUTH, DG2_NORTH = 0, 1, 2, 3
+
+# Every symbol declared in include/dg2.h.
+EXPORTS = (
+    "dg2_default_params", "dg2_last_error", "dg2_workspace_bytes", "dg2_init_grid", "dg2_set_dem",
+    "dg2_set_bc_inflow", "dg2_set_sources", "dg2_step", "dg2_run_to", "dg2_set_gauges",
+    "dg2_read_gauges", "dg2_mass", "dg2_get_state", "dg2_set_state", "dg2_get_topo",
+    "dg2_get_time", "dg2_enable_kernel_timing", "dg2_kernel_times", "dg2_launch_count",
+    "dg2_destroy",
+)
+
+
+class Dg2Params(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("cfl", ctypes.c_double), ("tol_dry", ctypes.c_double),
+                ("ds_thresh", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("variant", ctypes.c_int), ("precision", ctypes.c_int), ("bc", ctypes.c_int * 4),
+                ("max_gauges", ctypes.c_int), ("max_samples", ctypes.c_int)]
+
+
+class Dg2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dg2 error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libdg2.so and declares its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2010_02003_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    pp = ctypes.POINTER(Dg2Params)
+    sig = {
+        "dg2_default_params": (None, [pp]),
+        "dg2_last_error": (ctypes.c_char_p, []),
+        "dg2_workspace_bytes": (ctypes.c_size_t, [I, I, pp]),
+        "dg2_init_grid": (I, [ctypes.POINTER(P), I, I, D, D, pp, P, ctypes.c_size_t, P]),
+        "dg2_set_dem": (I, [P, dp, dp, D, dp]),
+        "dg2_set_bc_inflow": (I, [P, I, D, D, dp, dp, I]),
+        "dg2_set_sources": (I, [P, D, D, D, D, D, D]),
+        "dg2_step": (I, [P, D, dp]),
+        "dg2_run_to": (I, [P, D, i64p]),
+        "dg2_set_gauges": (I, [P, dp, I, D]),
+        "dg2_read_gauges": (I, [P, dp, dp, I, ip]),
+        "dg2_mass": (I, [P, dp, dp]),
+        "dg2_get_state": (I, [P, dp, dp]),
+        "dg2_set_state": (I, [P, dp, D]),
+        "dg2_get_topo": (I, [P, dp]),
+        "dg2_get_time": (I, [P, dp, dp]),
+        "dg2_enable_kernel_timing": (I, [P, I]),
+        "dg2_kernel_times": (I, [P, dp, i64p]),
+        "dg2_launch_count": (ctypes.c_int64, [P]),
+        "dg2_destroy": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != DG2_OK:
+        raise Dg2Error(code, load().dg2_last_error().decode())
+    return code
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---- same-named wrappers of the C entry points -------------------------------
+
+def dg2_default_params() -> Dg2Params:
+    p = Dg2Params()
+    load().dg2_default_params(ctypes.byref(p))
+    return p
+
+
+def dg2_workspace_bytes(nx: int, ny: int, params: Dg2Params) -> int:
+    return int(load().dg2_workspace_bytes(nx, ny, ctypes.byref(params)))
+
+
+def dg2_init_grid(nx, ny, dx, dy, params, dev_ptr: int, ws_bytes: int, stream_ptr: int):
+    h = ctypes.c_void_p()
+    _check(load().dg2_init_grid(ctypes.byref(h), nx, ny, dx, dy, ctypes.byref(params),
+                                ctypes.c_void_p(dev_ptr), ws_bytes, ctypes.c_void_p(stream_ptr)))
+    return h
+
+
+def dg2_set_dem(ctx, z_corner, manning=None, n_uniform=0.0, eta_corner=None):
+    z, m, e = _f64(z_corner), _f64(manning), _f64(eta_corner)
+    _check(load().dg2_set_dem(ctx, _dp(z), _dp(m), float(n_uniform), _dp(e)))
+
+
+def dg2_set_bc_inflow(ctx, edge, s0, length, t_knots, q_knots):
+    tk, qk = _f64(t_knots), _f64(q_knots)
+    _check(load().dg2_set_bc_inflow(ctx, int(edge), float(s0), float(length), _dp(tk), _dp(qk),
+                                    len(tk)))
+
+
+def dg2_set_sources(ctx, rain=0.0, t0=0.0, t1=0.0, px=0.0, py=0.0, qp=0.0):
+    _check(load().dg2_set_sources(ctx, rain, t0, t1, px, py, qp))
+
+
+def dg2_step(ctx, dt: float = -1.0, want_dt: bool = False):
+    out = ctypes.c_double(0.0)
+    _check(load().dg2_step(ctx, float(dt), ctypes.byref(out) if want_dt else None))
+    return out.value if want_dt else None
+
+
+def dg2_run_to(ctx, t_end: float) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().dg2_run_to(ctx, float(t_end), ctypes.byref(n)))
+    return n.value
+
+
+def dg2_set_gauges(ctx, xy, every):
+    a = _f64(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
+    _check(load().dg2_set_gauges(ctx, _dp(a), a.shape[0], float(every)))
+
+
+def dg2_read_gauges(ctx, ngauge: int, cap: int = 100000):
+    t = np.zeros(cap)
+    h = np.zeros((cap, max(ngauge, 1)))
+    n = ctypes.c_int(0)
+    code = load().dg2_read_gauges(ctx, _dp(t), _dp(h), cap, ctypes.byref(n))
+    if code not in (DG2_OK, DG2_E_OVERFLOW):
+        _check(code)
+    return t[:n.value].copy(), h[:n.value, :ngauge].copy(), code == DG2_E_OVERFLOW
+
+
+def dg2_mass(ctx):
+    m, l = ctypes.c_double(), ctypes.c_double()
+    _check(load().dg2_mass(ctx, ctypes.byref(m), ctypes.byref(l)))
+    return m.value, l.value
+
+
+def dg2_get_state(ctx, nx, ny, out=None):
+    out = np.zeros((9, ny, nx)) if out is None else out
+    t = ctypes.c_double()
+    _check(load().dg2_get_state(ctx, _dp(out), ctypes.byref(t)))
+    return out, t.value
+
+
+def dg2_set_state(ctx, planes, t=0.0):
+    p = _f64(planes)
+    _check(load().dg2_set_state(ctx, _dp(p), float(t)))
+
+
+def dg2_get_topo(ctx, nx, ny):
+    out = np.zeros((3, ny, nx))
+    _check(load().dg2_get_topo(ctx, _dp(out)))
+    return out
+
+
+def dg2_get_time(ctx):
+    t, dt = ctypes.c_double(), ctypes.c_double()
+    _check(load().dg2_get_time(ctx, ctypes.byref(t), ctypes.byref(dt)))
+    return t.value, dt.value
+
+
+def dg2_enable_kernel_timing(ctx, enable: bool):
+    _check(load().dg2_enable_kernel_timing(ctx, int(bool(enable))))
+
+
+def dg2_kernel_times(ctx):
+    ms = np.zeros(3)
+    n = ctypes.c_int64(0)
+    _check(load().dg2_kernel_times(ctx, _dp(ms), ctypes.byref(n)))
+    return ms, n.value
+
+
+def dg2_launch_count(ctx) -> int:
+    return int(load().dg2_launch_count(ctx))
+
+
+def dg2_destroy(ctx):
+    _check(load().dg2_destroy(ctx))
+
+
+# ---- convenience object owning a torch workspace ----------------------------
+
+class Solver:
+    """One DG2 problem on the current CUDA device.  The device workspace is a torch
+    uint8 tensor; kernels run on ``stream`` (default: a new torch stream)."""
+
+    def __init__(self, nx, ny, dx, dy=None, *, variant=DG2_NL, cfl=0.3, tol_dry=1e-5,
+                 ds_thresh=10.0, dt_max=1.0, g=9.80665, bc: Sequence[int] = (DG2_WALL,) * 4,
+                 max_gauges=64, max_samples=4096, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DG2 solver needs a CUDA device")
+        load()
+        self.nx, self.ny, self.dx = int(nx), int(ny), float(dx)
+        self.dy = float(dx if dy is None else dy)
+        p = dg2_default_params()
+        p.g, p.cfl, p.tol_dry, p.ds_thresh, p.dt_max = g, cfl, tol_dry, ds_thresh, dt_max
+        p.variant, p.precision = int(variant), DG2_FP64
+        for k in range(4):
+            p.bc[k] = int(bc[k])
+        p.max_gauges, p.max_samples = int(max_gauges), int(max_samples)
+        self.params = p
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = dg2_workspace_bytes(self.nx, self.ny, p)
+        if nbytes == 0:
+            raise Dg2Error(DG2_E_ARG, "invalid grid size")
+        with torch.cuda.device(self.device):
+            # a stream of its own by default: dg2_run_to captures CUDA graphs on it, which
+            # the legacy default stream does not allow
+            self.stream = torch.cuda.Stream(self.device) if stream is None else stream
+            # the workspace comes from torch's allocator on the current stream
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+            # over-allocate by the alignment so the base can be rounded up to 256 bytes
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            self._base = (base + 255) // 256 * 256
+            self.ctx = dg2_init_grid(self.nx, self.ny, self.dx, self.dy, p, self._base, nbytes,
+                                     self.stream.cuda_stream)
+        self.ngauge = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            dg2_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # set-up
+    def set_dem(self, z_corner, manning=None, n_uniform=0.0, eta_corner=None):
+        dg2_set_dem(self.ctx, z_corner, manning, n_uniform, eta_corner)
+
+    def add_inflow(self, edge, s0, length, t_knots, q_knots):
+        dg2_set_bc_inflow(self.ctx, edge, s0, length, t_knots, q_knots)
+
+    def set_sources(self, rain=0.0, t0=0.0, t1=0.0, px=0.0, py=0.0, qp=0.0):
+        dg2_set_sources(self.ctx, rain, t0, t1, px, py, qp)
+
+    def set_gauges(self, xy, every):
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        dg2_set_gauges(self.ctx, xy, every)
+        self.ngauge = xy.shape[0]
+
+    # stepping
+    def step(self, dt: float = -1.0, want_dt: bool = False):
+        return dg2_step(self.ctx, dt, want_dt)
+
+    def run_to(self, t_end: float) -> int:
+        return dg2_run_to(self.ctx, t_end)
+
+    # outputs
+    def state(self):
+        return dg2_get_state(self.ctx, self.nx, self.ny)[0]
+
+    def set_state(self, planes, t=0.0):
+        dg2_set_state(self.ctx, planes, t)
+
+    def topo(self):
+        return dg2_get_topo(self.ctx, self.nx, self.ny)
+
+    def time(self):
+        return dg2_get_time(self.ctx)
+
+    def mass(self):
+        return dg2_mass(self.ctx)
+
+    def read_gauges(self, cap=100000):
+        return dg2_read_gauges(self.ctx, self.ngauge, cap)
+
+    def launches(self) -> int:
+        return dg2_launch_count(self.ctx)
+
+
+def solver_from_case(case, variant=DG2_NL, **kw) -> Solver:
+    """Builds a Solver from an inputs.Case (DEM, water, roughness, inflows, sources, gauges)."""
+    s = Solver(case.nx, case.ny, case.dx, case.dy, variant=variant, cfl=case.cfl, bc=case.bc, **kw)
+    s.set_dem(case.z_corner, case.manning, case.n_uniform, case.eta_corner)
+    for f in case.inflows:
+        s.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)
+    r, r0, r1 = case.rain
+    px, py, qp = case.point
+    if r != 0.0 or qp != 0.0:
+        s.set_sources(r, r0, r1, px, py, qp)
+    if case.gauges is not None and case.sample_every > 0:
+        s.set_gauges(case.gauges, case.sample_every)
+    return s

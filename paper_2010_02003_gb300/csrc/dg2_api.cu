@@ -1,0 +1,653 @@
+// dg2_api.cu -- host runtime and C ABI of the GB300 DG2 solver (include/dg2.h).
+//
+// The context lives on the host; every array lives in the caller's device
+// workspace; every kernel and copy goes to the caller's stream.  dg2_run_to
+// advances in chunks of steps captured once into a CUDA graph: the stage-2
+// kernel's last block advances t on the device and raises a stop flag at
+// t_end, so the host only reads the scalars once per chunk.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg2.h"
+#include "dg2_device.cuh"
+
+using dg2::Dev;
+using dg2::Scalars;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(DG2_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxKnots = 4096;
+constexpr int kChunkMin = 16, kChunkMax = 1024;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  int pitch;
+  long long plane;
+  size_t off_S, off_T, off_Q, off_Z, off_N, off_bpart, off_mpart, off_kt, off_kq;
+  size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, total;
+  int nblocks, mblocks;
+};
+
+bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
+  if (nx < 1 || ny < 1 || p.max_gauges < 0 || p.max_gauges > dg2::kMaxGauges ||
+      p.max_samples < 1)
+    return false;
+  L.pitch = (nx + 31) / 32 * 32;
+  L.plane = (long long)L.pitch * ny;
+  const size_t pb = (size_t)L.plane * sizeof(double);
+  L.nblocks = ((nx + dg2::TX - 1) / dg2::TX) * ((ny + dg2::TY - 1) / dg2::TY);
+  L.mblocks = ((nx + 31) / 32) * ((ny + 7) / 8);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.off_S = take(9 * pb);
+  L.off_T = take(9 * pb);
+  L.off_Q = take(p.variant == DG2_LL ? 6 * pb : 0);
+  L.off_Z = take(3 * pb);
+  L.off_N = take(pb);
+  L.off_bpart = take(2 * (size_t)L.nblocks * sizeof(double));
+  L.off_mpart = take((size_t)L.mblocks * sizeof(double));
+  L.off_kt = take((size_t)dg2::kMaxInflow * kMaxKnots * sizeof(double));
+  L.off_kq = take((size_t)dg2::kMaxInflow * kMaxKnots * sizeof(double));
+  const size_t ng = p.max_gauges > 0 ? p.max_gauges : 1;
+  L.off_gidx = take(ng * sizeof(long long));
+  L.off_gxi = take(ng * sizeof(double));
+  L.off_geta = take(ng * sizeof(double));
+  L.off_st = take((size_t)p.max_samples * sizeof(double));
+  L.off_sh = take((size_t)p.max_samples * ng * sizeof(double));
+  L.off_sc = take(sizeof(Scalars));
+  L.total = o;
+  return true;
+}
+
+}  // namespace
+
+struct dg2_ctx {
+  Dev d;
+  dg2_params p;
+  Layout lay;
+  cudaStream_t st;
+  char* ws;
+  int dem_set;
+  int64_t launches;
+  dim3 sgrid, sblock, pgrid, pblock;
+  std::vector<double> kt, kq;   // host copies of the knot tables
+  // run_to graphs of 16 << k steps, k = 0..6 (dropped when the launch setup changes)
+  cudaGraphExec_t graph[7];
+  // optional per-kernel event timing of dg2_step
+  int timing;
+  int timed_steps;
+  std::vector<cudaEvent_t> ev;   // 4 per timed step
+};
+
+namespace {
+
+int launch_check(dg2_ctx* c, int nkernels) {
+  c->launches += nkernels;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DG2_E_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  return DG2_OK;
+}
+
+void drop_graph(dg2_ctx* c) {
+  for (auto& g : c->graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+constexpr int kMaxTimedSteps = 8192;
+
+// Enqueues one RK2 step: friction, stage 1, stage 2 (3 kernels).  With
+// `timed`, records an event before and after each kernel.
+void enqueue_step(dg2_ctx* c, bool timed = false) {
+  const Dev& d = c->d;
+  cudaEvent_t* e = nullptr;
+  if (timed && c->timing && c->timed_steps < kMaxTimedSteps) {
+    const size_t need = 4 * (size_t)(c->timed_steps + 1);
+    while (c->ev.size() < need) {
+      cudaEvent_t x;
+      if (cudaEventCreate(&x) != cudaSuccess) break;
+      c->ev.push_back(x);
+    }
+    if (c->ev.size() >= need) e = &c->ev[4 * (size_t)c->timed_steps++];
+  }
+  if (e) cudaEventRecord(e[0], c->st);
+  dg2::friction_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(d);
+  if (e) cudaEventRecord(e[1], c->st);
+  if (c->p.variant == DG2_LL)
+    dg2::stage_kernel<true, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  else
+    dg2::stage_kernel<false, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  if (e) cudaEventRecord(e[2], c->st);
+  if (c->p.variant == DG2_LL)
+    dg2::stage_kernel<true, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  else
+    dg2::stage_kernel<false, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  if (e) cudaEventRecord(e[3], c->st);
+}
+
+int read_scalars(dg2_ctx* c, Scalars* out) {
+  CU(cudaMemcpyAsync(out, c->d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  return DG2_OK;
+}
+
+int check_arg_ctx(dg2_ctx* c, bool need_dem) {
+  if (!c) return fail(DG2_E_ARG, "null context");
+  if (need_dem && !c->dem_set) return fail(DG2_E_STATE, "dg2_set_dem or dg2_set_state first");
+  return DG2_OK;
+}
+
+int recompute_dt(dg2_ctx* c) {
+  dg2::rate_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
+  return launch_check(c, 1);
+}
+
+int reset_ledger(dg2_ctx* c) {
+  // mass kernel with the ledger-reset flag set by a one-field copy
+  const int one = 1;
+  CU(cudaMemcpyAsync(&c->d.sc->ledger_init, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  dg2::mass_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
+  return launch_check(c, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+void dg2_default_params(dg2_params* p) {
+  if (!p) return;
+  p->g = 9.80665;
+  p->cfl = 0.3;
+  p->tol_dry = 1e-5;
+  p->ds_thresh = 10.0;
+  p->dt_max = 1.0;
+  p->variant = DG2_NL;
+  p->precision = DG2_FP64;
+  for (int k = 0; k < 4; ++k) p->bc[k] = DG2_WALL;
+  p->max_gauges = 64;
+  p->max_samples = 4096;
+}
+
+const char* dg2_last_error(void) { return g_err.c_str(); }
+
+size_t dg2_workspace_bytes(int nx, int ny, const dg2_params* pp) {
+  dg2_params p;
+  if (pp) p = *pp; else dg2_default_params(&p);
+  Layout L;
+  if (!make_layout(nx, ny, p, L)) return 0;
+  return L.total;
+}
+
+int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2_params* pp,
+                  void* dev_workspace, size_t ws_bytes, void* cuda_stream) {
+  g_err.clear();
+  if (!out) return fail(DG2_E_ARG, "out is null");
+  *out = nullptr;
+  dg2_params p;
+  if (pp) p = *pp; else dg2_default_params(&p);
+  if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return fail(DG2_E_ARG, "dx, dy must be positive");
+  if (!(p.g > 0.0) || !(p.cfl > 0.0) || !(p.tol_dry >= 0.0) || !(p.dt_max > 0.0) ||
+      (p.variant != DG2_NL && p.variant != DG2_LL) || p.precision != DG2_FP64)
+    return fail(DG2_E_ARG, "invalid parameters (g, cfl, tol_dry, dt_max, variant, precision)");
+  for (int k = 0; k < 4; ++k)
+    if (p.bc[k] != DG2_WALL && p.bc[k] != DG2_OPEN) return fail(DG2_E_ARG, "bad edge type");
+  if ((long long)nx * ny > (1ll << 31)) return fail(DG2_E_ARG, "grid too large");
+  Layout L;
+  if (!make_layout(nx, ny, p, L))
+    return fail(DG2_E_ARG, "invalid grid size or gauge capacities");
+  if (!dev_workspace) return fail(DG2_E_ARG, "workspace is null");
+  if ((uintptr_t)dev_workspace % kAlign) return fail(DG2_E_ARG, "workspace not 256-byte aligned");
+  if (ws_bytes < L.total)
+    return fail(DG2_E_NOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, dev_workspace) != cudaSuccess ||
+      attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(DG2_E_ARG, "workspace is not device memory");
+  }
+
+  dg2_ctx* c = new dg2_ctx();
+  c->p = p;
+  c->lay = L;
+  c->st = (cudaStream_t)cuda_stream;
+  c->ws = (char*)dev_workspace;
+  for (auto& g : c->graph) g = nullptr;
+  Dev& d = c->d;
+  memset(&d, 0, sizeof d);
+  d.nx = nx; d.ny = ny; d.pitch = L.pitch; d.plane = L.plane;
+  d.dx = dx; d.dy = dy; d.inv_dx = 1.0 / dx; d.inv_dy = 1.0 / dy;
+  d.g = p.g; d.cfl = p.cfl; d.tol = p.tol_dry; d.ds = p.ds_thresh; d.dt_max = p.dt_max;
+  for (int k = 0; k < 4; ++k) d.bc[k] = p.bc[k];
+  d.S = (double*)(c->ws + L.off_S);
+  d.T = (double*)(c->ws + L.off_T);
+  d.Q = p.variant == DG2_LL ? (double*)(c->ws + L.off_Q) : nullptr;
+  d.Z = (const double*)(c->ws + L.off_Z);
+  d.N = (const double*)(c->ws + L.off_N);
+  d.bpart = (double*)(c->ws + L.off_bpart);
+  d.mpart = (double*)(c->ws + L.off_mpart);
+  d.knot_t = (const double*)(c->ws + L.off_kt);
+  d.knot_q = (const double*)(c->ws + L.off_kq);
+  d.g_idx = (const long long*)(c->ws + L.off_gidx);
+  d.g_xi = (const double*)(c->ws + L.off_gxi);
+  d.g_eta = (const double*)(c->ws + L.off_geta);
+  d.samp_t = (double*)(c->ws + L.off_st);
+  d.samp_h = (double*)(c->ws + L.off_sh);
+  d.sc = (Scalars*)(c->ws + L.off_sc);
+  d.max_samples = p.max_samples;
+  d.src_idx = -1;
+  d.nblocks = L.nblocks;
+  c->sblock = dim3(dg2::TX, dg2::TY);
+  c->sgrid = dim3((nx + dg2::TX - 1) / dg2::TX, (ny + dg2::TY - 1) / dg2::TY);
+  c->pblock = dim3(32, 8);
+  c->pgrid = dim3((nx + 31) / 32, (ny + 7) / 8);
+
+  // zero the state, topography and scalars; t_end / samples at +inf
+  cudaError_t e = cudaMemsetAsync(c->ws, 0, L.total, c->st);
+  Scalars s0;
+  memset(&s0, 0, sizeof s0);
+  s0.t_end = INFINITY;
+  s0.next_sample = INFINITY;
+  s0.dt = p.dt_max;
+  s0.dt_cfl = p.dt_max;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.sc, &s0, sizeof s0, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(DG2_E_CUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return DG2_OK;
+}
+
+int dg2_set_dem(dg2_ctx* c, const double* z_corner, const double* manning, double n_uniform,
+                const double* eta_corner) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!z_corner) return fail(DG2_E_ARG, "z_corner is null");
+  if (!manning && !(n_uniform >= 0.0)) return fail(DG2_E_ARG, "n_uniform must be >= 0");
+  const int nx = c->d.nx, ny = c->d.ny;
+  const size_t nc = (size_t)(nx + 1) * (ny + 1), ncell = (size_t)nx * ny;
+  for (size_t k = 0; k < nc; ++k)
+    if (!std::isfinite(z_corner[k]) || (eta_corner && !std::isfinite(eta_corner[k])))
+      return fail(DG2_E_ARG, "non-finite DEM or free surface at corner %zu", k);
+  if (manning)
+    for (size_t k = 0; k < ncell; ++k)
+      if (!(manning[k] >= 0.0) || !std::isfinite(manning[k]))
+        return fail(DG2_E_ARG, "invalid Manning n at cell %zu", k);
+  drop_graph(c);
+  // stage the corner arrays (and the Manning field) in the stage buffer T
+  double* zc = c->d.T;
+  double* ec = zc + nc;
+  double* mn = ec + nc;
+  CU(cudaMemcpyAsync(zc, z_corner, nc * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  if (eta_corner)
+    CU(cudaMemcpyAsync(ec, eta_corner, nc * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  if (manning)
+    CU(cudaMemcpyAsync(mn, manning, ncell * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  dg2::init_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d, zc, eta_corner ? ec : nullptr,
+                                                      manning ? mn : nullptr, n_uniform,
+                                                      (double*)c->d.Z, (double*)c->d.N);
+  if ((r = launch_check(c, 1))) return r;
+  CU(cudaMemsetAsync(c->d.T, 0, 9 * (size_t)c->d.plane * sizeof(double), c->st));
+  // scalars: t = 0, clear run state and samples
+  Scalars s0;
+  CU(cudaMemcpyAsync(&s0, c->d.sc, sizeof s0, cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  s0.t = 0.0;
+  s0.t_end = INFINITY;
+  s0.nsamp = 0;
+  s0.done = 0;
+  s0.nonfinite = 0;
+  s0.steps = 0;
+  s0.count = 0;
+  s0.lam_bits = 0;
+  s0.next_sample = s0.sample_every > 0.0 ? s0.sample_every : INFINITY;
+  CU(cudaMemcpyAsync(c->d.sc, &s0, sizeof s0, cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  c->dem_set = 1;
+  if ((r = reset_ledger(c))) return r;
+  if ((r = recompute_dt(c))) return r;
+  CU(cudaStreamSynchronize(c->st));
+  return DG2_OK;
+}
+
+int dg2_set_bc_inflow(dg2_ctx* c, int edge, double s0_m, double len_m, const double* t_knots,
+                      const double* q_knots, int nknots) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (edge < 0 || edge > 3) return fail(DG2_E_ARG, "edge must be 0..3");
+  if (c->d.n_in >= dg2::kMaxInflow) return fail(DG2_E_ARG, "at most %d inflows", dg2::kMaxInflow);
+  if (!t_knots || !q_knots || nknots < 1 || nknots > kMaxKnots)
+    return fail(DG2_E_ARG, "need 1..%d knots", kMaxKnots);
+  if (!(len_m >= 0.0) || !std::isfinite(s0_m)) return fail(DG2_E_ARG, "bad segment");
+  for (int k = 0; k < nknots; ++k) {
+    if (!std::isfinite(t_knots[k]) || !std::isfinite(q_knots[k]))
+      return fail(DG2_E_ARG, "non-finite knot %d", k);
+    if (k && !(t_knots[k] > t_knots[k - 1])) return fail(DG2_E_ARG, "t_knots must increase");
+  }
+  const bool ew = edge <= 1;
+  const int n = ew ? c->d.ny : c->d.nx;
+  const double h = ew ? c->d.dy : c->d.dx;
+  int nf = 0;
+  for (int k = 0; k < n; ++k) {
+    const double s = (k + 0.5) * h;
+    if (s >= s0_m && s <= s0_m + len_m) ++nf;
+  }
+  if (nf == 0) return fail(DG2_E_ARG, "no face centre lies in the inflow segment");
+  drop_graph(c);
+  dg2::InflowDesc& f = c->d.in[c->d.n_in];
+  f.edge = edge;
+  f.nk = nknots;
+  f.koff = c->d.n_in * kMaxKnots;
+  f.nfaces = nf;
+  f.s0 = s0_m;
+  f.s1 = s0_m + len_m;
+  f.width = nf * h;
+  CU(cudaMemcpyAsync((double*)c->d.knot_t + f.koff, t_knots, nknots * sizeof(double),
+                     cudaMemcpyHostToDevice, c->st));
+  CU(cudaMemcpyAsync((double*)c->d.knot_q + f.koff, q_knots, nknots * sizeof(double),
+                     cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  c->d.n_in += 1;
+  return DG2_OK;
+}
+
+int dg2_set_sources(dg2_ctx* c, double rain, double t0, double t1, double px, double py,
+                    double qp) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!std::isfinite(rain) || !std::isfinite(t0) || !std::isfinite(t1) || !std::isfinite(px) ||
+      !std::isfinite(py) || !std::isfinite(qp))
+    return fail(DG2_E_ARG, "non-finite source parameter");
+  drop_graph(c);
+  c->d.rain = rain;
+  c->d.rain_t0 = t0;
+  c->d.rain_t1 = t1;
+  c->d.qp = qp;
+  c->d.src_idx = -1;
+  if (qp != 0.0) {
+    int i = (int)std::floor(px / c->d.dx), j = (int)std::floor(py / c->d.dy);
+    i = i < 0 ? 0 : (i >= c->d.nx ? c->d.nx - 1 : i);
+    j = j < 0 ? 0 : (j >= c->d.ny ? c->d.ny - 1 : j);
+    c->d.src_idx = (long long)j * c->d.pitch + i;
+  }
+  return DG2_OK;
+}
+
+int dg2_step(dg2_ctx* c, double dt, double* dt_taken) {
+  int r = check_arg_ctx(c, true);
+  if (r) return r;
+  if (!std::isfinite(dt)) return fail(DG2_E_ARG, "dt must be finite");
+  dg2::begin_step_kernel<<<1, 1, 0, c->st>>>(c->d, dt);
+  enqueue_step(c, true);
+  if ((r = launch_check(c, 4))) return r;
+  if (dt_taken) {
+    Scalars s;
+    if ((r = read_scalars(c, &s))) return r;
+    if (s.nonfinite) return fail(DG2_E_NONFINITE, "non-finite state or step at t=%g", s.t);
+    *dt_taken = s.last_dt;
+  }
+  return DG2_OK;
+}
+
+int dg2_run_to(dg2_ctx* c, double t_end, int64_t* steps_taken) {
+  int r = check_arg_ctx(c, true);
+  if (r) return r;
+  if (!std::isfinite(t_end)) return fail(DG2_E_ARG, "t_end must be finite");
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  const long long steps0 = s.steps;
+  if (s.t >= t_end) {
+    if (steps_taken) *steps_taken = 0;
+    return DG2_OK;
+  }
+  dg2::begin_run_kernel<<<1, 1, 0, c->st>>>(c->d, t_end);
+  if ((r = launch_check(c, 1))) return r;
+  int level = 0;  // chunk = kChunkMin << level steps
+  double t_prev = s.t;
+  // The legacy NULL stream cannot be captured: launch the chunk directly there.
+  const bool use_graph = c->st != nullptr;
+  for (;;) {
+    const int chunk = kChunkMin << level;
+    if (use_graph) {
+      if (!c->graph[level]) {
+        cudaGraph_t gr;
+        CU(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < chunk; ++k) enqueue_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->st, &gr);
+        if (e != cudaSuccess)
+          return fail(DG2_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph[level], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess)
+          return fail(DG2_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+      }
+      CU(cudaGraphLaunch(c->graph[level], c->st));
+    } else {
+      for (int k = 0; k < chunk; ++k) enqueue_step(c);
+      if ((r = launch_check(c, 0))) return r;
+    }
+    c->launches += 3 * (int64_t)chunk;
+    if ((r = read_scalars(c, &s))) return r;
+    if (s.nonfinite) return fail(DG2_E_NONFINITE, "non-finite state or step near t=%g", s.t);
+    if (s.done) break;
+    if (!(s.t > t_prev)) return fail(DG2_E_NONFINITE, "time stopped advancing at t=%g", s.t);
+    t_prev = s.t;
+    if ((kChunkMin << level) < kChunkMax) ++level;
+  }
+  if (steps_taken) *steps_taken = s.steps - steps0;
+  return DG2_OK;
+}
+
+int dg2_set_gauges(dg2_ctx* c, const double* xy, int ngauge, double every) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (ngauge < 0 || ngauge > c->p.max_gauges)
+    return fail(DG2_E_ARG, "ngauge must be 0..%d", c->p.max_gauges);
+  if (ngauge > 0 && !xy) return fail(DG2_E_ARG, "xy is null");
+  if (!(every >= 0.0) || !std::isfinite(every)) return fail(DG2_E_ARG, "bad sample interval");
+  std::vector<long long> idx(ngauge > 0 ? ngauge : 1);
+  std::vector<double> xi(ngauge > 0 ? ngauge : 1), et(ngauge > 0 ? ngauge : 1);
+  for (int k = 0; k < ngauge; ++k) {
+    const double x = xy[2 * k], y = xy[2 * k + 1];
+    if (!std::isfinite(x) || !std::isfinite(y)) return fail(DG2_E_ARG, "non-finite gauge %d", k);
+    int i = (int)std::floor(x / c->d.dx), j = (int)std::floor(y / c->d.dy);
+    i = i < 0 ? 0 : (i >= c->d.nx ? c->d.nx - 1 : i);
+    j = j < 0 ? 0 : (j >= c->d.ny ? c->d.ny - 1 : j);
+    idx[k] = (long long)j * c->d.pitch + i;
+    xi[k] = (x - (i + 0.5) * c->d.dx) / (0.5 * c->d.dx);
+    et[k] = (y - (j + 0.5) * c->d.dy) / (0.5 * c->d.dy);
+  }
+  drop_graph(c);
+  if (ngauge > 0) {
+    CU(cudaMemcpyAsync((void*)c->d.g_idx, idx.data(), ngauge * sizeof(long long),
+                       cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync((void*)c->d.g_xi, xi.data(), ngauge * sizeof(double),
+                       cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync((void*)c->d.g_eta, et.data(), ngauge * sizeof(double),
+                       cudaMemcpyHostToDevice, c->st));
+  }
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  s.sample_every = ngauge > 0 ? every : 0.0;
+  s.next_sample = (ngauge > 0 && every > 0.0)
+                      ? (std::floor(s.t / every + 1e-9) + 1.0) * every
+                      : INFINITY;
+  s.nsamp = 0;
+  CU(cudaMemcpyAsync(c->d.sc, &s, sizeof s, cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  c->d.ngauge = ngauge;
+  return DG2_OK;
+}
+
+int dg2_read_gauges(dg2_ctx* c, double* t_out, double* h_out, int cap, int* nsamp) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (cap < 0 || (cap > 0 && (!t_out || (c->d.ngauge > 0 && !h_out))))
+    return fail(DG2_E_ARG, "bad output buffers");
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  const int kept = s.nsamp < c->d.max_samples ? s.nsamp : c->d.max_samples;
+  const int n = kept < cap ? kept : cap;
+  if (n > 0) {
+    CU(cudaMemcpyAsync(t_out, c->d.samp_t, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (c->d.ngauge > 0)
+      CU(cudaMemcpyAsync(h_out, c->d.samp_h, (size_t)n * c->d.ngauge * sizeof(double),
+                         cudaMemcpyDeviceToHost, c->st));
+  }
+  const int zero = 0;
+  CU(cudaMemcpyAsync(&c->d.sc->nsamp, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  if (nsamp) *nsamp = n;
+  if (s.nsamp > c->d.max_samples || kept > cap)
+    return fail(DG2_E_OVERFLOW, "%d samples recorded, %d returned", s.nsamp, n);
+  return DG2_OK;
+}
+
+int dg2_mass(dg2_ctx* c, double* mass, double* ledger) {
+  int r = check_arg_ctx(c, true);
+  if (r) return r;
+  dg2::mass_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
+  if ((r = launch_check(c, 1))) return r;
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  if (mass) *mass = s.mass;
+  if (ledger) *ledger = s.ledger;
+  return DG2_OK;
+}
+
+int dg2_get_state(dg2_ctx* c, double* planes, double* t) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!planes) return fail(DG2_E_ARG, "planes is null");
+  const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
+  for (int k = 0; k < 9; ++k)
+    CU(cudaMemcpy2DAsync(planes + (size_t)k * c->d.nx * c->d.ny, w, c->d.S + k * c->d.plane, pb,
+                         w, c->d.ny, cudaMemcpyDeviceToHost, c->st));
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  if (t) *t = s.t;
+  return DG2_OK;
+}
+
+int dg2_set_state(dg2_ctx* c, const double* planes, double t) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!planes || !std::isfinite(t)) return fail(DG2_E_ARG, "bad planes or t");
+  const size_t n = (size_t)9 * c->d.nx * c->d.ny;
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(planes[k])) return fail(DG2_E_ARG, "non-finite state value %zu", k);
+  const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
+  for (int k = 0; k < 9; ++k)
+    CU(cudaMemcpy2DAsync(c->d.S + k * c->d.plane, pb, planes + (size_t)k * c->d.nx * c->d.ny, w,
+                         w, c->d.ny, cudaMemcpyHostToDevice, c->st));
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  s.t = t;
+  s.done = 0;
+  s.nonfinite = 0;
+  s.t_end = INFINITY;
+  s.next_sample = s.sample_every > 0.0 ? (std::floor(t / s.sample_every + 1e-9) + 1.0) * s.sample_every
+                                       : INFINITY;
+  CU(cudaMemcpyAsync(c->d.sc, &s, sizeof s, cudaMemcpyHostToDevice, c->st));
+  c->dem_set = 1;
+  if ((r = reset_ledger(c))) return r;
+  if ((r = recompute_dt(c))) return r;
+  CU(cudaStreamSynchronize(c->st));
+  return DG2_OK;
+}
+
+int dg2_get_topo(dg2_ctx* c, double* planes3) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!planes3) return fail(DG2_E_ARG, "planes3 is null");
+  const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
+  for (int k = 0; k < 3; ++k)
+    CU(cudaMemcpy2DAsync(planes3 + (size_t)k * c->d.nx * c->d.ny, w, c->d.Z + k * c->d.plane, pb,
+                         w, c->d.ny, cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  return DG2_OK;
+}
+
+int dg2_get_time(dg2_ctx* c, double* t, double* dt_next) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  if (t) *t = s.t;
+  if (dt_next) *dt_next = s.dt_cfl;
+  return DG2_OK;
+}
+
+int dg2_enable_kernel_timing(dg2_ctx* c, int enable) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  c->timing = enable ? 1 : 0;
+  c->timed_steps = 0;
+  return DG2_OK;
+}
+
+int dg2_kernel_times(dg2_ctx* c, double* ms3, int64_t* nsteps) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!ms3) return fail(DG2_E_ARG, "ms3 is null");
+  CU(cudaStreamSynchronize(c->st));
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < c->timed_steps; ++k)
+    for (int q = 0; q < 3; ++q) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, c->ev[4 * k + q], c->ev[4 * k + q + 1]));
+      acc[q] += ms;
+    }
+  for (int q = 0; q < 3; ++q) ms3[q] = acc[q];
+  if (nsteps) *nsteps = c->timed_steps;
+  c->timed_steps = 0;
+  return DG2_OK;
+}
+
+int64_t dg2_launch_count(const dg2_ctx* c) { return c ? c->launches : -1; }
+
+int dg2_destroy(dg2_ctx* c) {
+  if (!c) return fail(DG2_E_ARG, "null context");
+  drop_graph(c);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+  return DG2_OK;
+}
+
+}  // extern "C"

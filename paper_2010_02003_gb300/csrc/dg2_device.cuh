@@ -1,0 +1,868 @@
+// dg2_device.cuh -- device code of the GB300 DG2 solver (sm_103a).
+//
+// One RK2 step of the slope-decoupled DG2 scheme (Sec. 2.1 of Ayog et al.)
+// is three launches on the caller's stream:
+//   friction_kernel   implicit Manning friction at the centre and the four
+//                     Gauss points of every cell (Sec. 2.1.3), in place;
+//   stage_kernel<1>   [local limiting, Eqs. 6-7] + spatial operator
+//                     (Eqs. 4-5) + U1 = Un + dt L(Un) + wet-dry treatment;
+//   stage_kernel<2>   [limiting] + operator + Un+1 = (Un + U1 + dt L(U1)) / 2
+//                     + wet-dry treatment, then the Courant-number reduction
+//                     for the next step; its last block to finish advances t,
+//                     the mass ledger and the gauges (no host round trip).
+//
+// Layout: structure of arrays, one FP64 plane per coefficient, row pitch a
+// multiple of 32 elements.  A block owns a TX x TY tile of cells; it computes
+// every revised face limit once (Sec. 2.1.2), keeps the east/north limits in
+// shared memory so each interior face flux is evaluated once per tile, and
+// evaluates the halo limits (and ghost states on domain edges) itself.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dg2 {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int kMaxInflow = 8;
+constexpr int kMaxGauges = 256;
+
+// Plane indices of the 9 flow coefficients (Eq. 2): variable * 3 + mode.
+enum { H0 = 0, H1X, H1Y, QX0, QX1X, QX1Y, QY0, QY1X, QY1Y };
+
+struct InflowDesc {
+  int edge;        // 0 W, 1 E, 2 S, 3 N
+  int nk;          // knots
+  int koff;        // offset into the knot arrays
+  int nfaces;      // faces whose centre lies in the segment
+  double s0, s1;   // segment [s0, s1] along the edge
+  double width;    // nfaces * face length
+};
+
+// Device-resident scalars of a context (one per context, in the workspace).
+struct Scalars {
+  double t;            // simulated time
+  double dt;           // step size of the next step (capped)
+  double dt_cfl;       // Courant-number step of the current state (uncapped)
+  double t_end;        // run_to target (+inf outside run_to)
+  double next_sample;  // next gauge sample time (+inf if none)
+  double sample_every;
+  double ledger;       // initial mass + boundary / source volumes
+  double mass;         // last dg2_mass result
+  unsigned long long lam_bits;  // max wave speed / cell size, as FP64 bits
+  unsigned int count;  // blocks finished (last-block-done pattern)
+  int done;            // t reached t_end during run_to
+  int land;            // the capped dt lands exactly on the target
+  int fixed_dt;        // dg2_step with a caller-forced dt: no landing logic
+  int nonfinite;       // a non-finite value or h0 < -1 appeared
+  int nsamp;           // samples recorded (may exceed capacity)
+  int ledger_init;     // mass kernel: also reset the ledger
+  int pad;
+  long long steps;     // completed steps (count of stage-2 finalisations)
+  double last_dt;      // size of the last completed step
+};
+
+struct Dev {
+  // grid
+  int nx, ny, pitch;
+  long long plane;           // elements per plane
+  double dx, dy, inv_dx, inv_dy;
+  // parameters
+  double g, cfl, tol, ds, dt_max;
+  int bc[4];
+  // inflows
+  int n_in;
+  InflowDesc in[kMaxInflow];
+  const double* knot_t;
+  const double* knot_q;
+  // sources
+  double rain, rain_t0, rain_t1;
+  double qp;                 // point inflow, m^3/s
+  long long src_idx;         // plane index of the point-source cell, -1 if none
+  // buffers
+  double* S;                 // 9 planes: state Un
+  double* T;                 // 9 planes: stage state U1
+  double* Q;                 // 6 planes: limited slopes of Un (DG2-LL)
+  const double* Z;           // 3 planes: z0, z1x, z1y
+  const double* N;           // 1 plane: Manning n
+  double* bpart;             // [2][nblocks] boundary mass-rate partials
+  double* mpart;             // [nblocks] mass partials
+  Scalars* sc;
+  // gauges
+  int ngauge, max_samples;
+  const long long* g_idx;    // plane index of each gauge cell
+  const double* g_xi;        // local coordinates in [-1, 1]
+  const double* g_eta;
+  double* samp_t;            // [max_samples]
+  double* samp_h;            // [max_samples][ngauge]
+  int nblocks;               // blocks of the stage grid
+};
+
+// ---------------------------------------------------------------------------
+// Point-state helpers
+// ---------------------------------------------------------------------------
+
+// A revised face limit (Sec. 2.1.2): h* = max(0, h), velocities q/h above
+// tol_dry and zero otherwise, q* = h* u.  The velocities are kept for the flux.
+struct Lim {
+  double h, qx, qy, u, v;
+};
+
+struct F3 {
+  double h, x, y;
+};
+
+__device__ __forceinline__ Lim revise(double h, double qx, double qy, double tol) {
+  Lim r;
+  if (h > tol) {
+    r.u = qx / h;
+    r.v = qy / h;
+  } else {
+    r.u = 0.0;
+    r.v = 0.0;
+  }
+  r.h = h > 0.0 ? h : 0.0;
+  r.qx = r.h * r.u;
+  r.qy = r.h * r.v;
+  return r;
+}
+
+// HLL flux normal to a face (Toro's wave-speed estimates with the dry-bed
+// forms).  n = normal, t = tangential component; (un, ut) are the limit's
+// velocities.  Returns (mass, normal momentum, tangential momentum).
+__device__ __forceinline__ F3 hll(double hL, double qnL, double qtL, double unL, double utL,
+                                  double hR, double qnR, double qtR, double unR, double utR,
+                                  double g, double tol) {
+  F3 f;
+  if (hL <= tol && hR <= tol) {
+    f.h = 0.0; f.x = 0.0; f.y = 0.0;
+    return f;
+  }
+  const double cL = sqrt(g * hL), cR = sqrt(g * hR);
+  double sL, sR;
+  if (hL <= tol) {
+    sL = unR - 2.0 * cR;
+    sR = unR + cR;
+  } else if (hR <= tol) {
+    sL = unL - cL;
+    sR = unL + 2.0 * cL;
+  } else {
+    const double us = 0.5 * (unL + unR) + cL - cR;
+    const double cs = 0.5 * (cL + cR) + 0.25 * (unL - unR);
+    sL = fmin(unL - cL, us - cs);
+    sR = fmax(unR + cR, us + cs);
+  }
+  // physical normal flux [h un, h un^2 + g h^2 / 2, h un ut] of each side
+  const double fLh = hL * unL, fLn = hL * unL * unL + 0.5 * g * hL * hL, fLt = hL * unL * utL;
+  const double fRh = hR * unR, fRn = hR * unR * unR + 0.5 * g * hR * hR, fRt = hR * unR * utR;
+  if (sL >= 0.0) {
+    f.h = fLh; f.x = fLn; f.y = fLt;
+    return f;
+  }
+  if (sR <= 0.0) {
+    f.h = fRh; f.x = fRn; f.y = fRt;
+    return f;
+  }
+  const double inv = 1.0 / (sR - sL), sLR = sL * sR;
+  f.h = (sR * fLh - sL * fRh + sLR * (hR - hL)) * inv;
+  f.x = (sR * fLn - sL * fRn + sLR * (qnR - qnL)) * inv;
+  f.y = (sR * fLt - sL * fRt + sLR * (qtR - qtL)) * inv;
+  return f;
+}
+
+// x-face flux: returns [F^h, F^qx, F^qy].
+__device__ __forceinline__ F3 flux_x(const Lim& L, const Lim& R, double g, double tol) {
+  return hll(L.h, L.qx, L.qy, L.u, L.v, R.h, R.qx, R.qy, R.u, R.v, g, tol);
+}
+
+// y-face flux in the rotated frame, mapped back: returns [G^h, G^qx, G^qy].
+__device__ __forceinline__ F3 flux_y(const Lim& S, const Lim& N, double g, double tol) {
+  F3 r = hll(S.h, S.qy, S.qx, S.v, S.u, N.h, N.qy, N.qx, N.v, N.u, g, tol);
+  F3 o;
+  o.h = r.h; o.x = r.y; o.y = r.x;
+  return o;
+}
+
+// Physical flux F (x) or G (y) of a point state, velocities by the tol rule.
+__device__ __forceinline__ F3 phys_flux(double h, double qx, double qy, double g, double tol,
+                                        bool ydir) {
+  double u = 0.0, v = 0.0;
+  if (h > tol) {
+    u = qx / h;
+    v = qy / h;
+  }
+  F3 f;
+  const double p = 0.5 * g * h * h;
+  if (!ydir) {
+    f.h = h * u; f.x = h * u * u + p; f.y = h * u * v;
+  } else {
+    f.h = h * v; f.x = h * u * v; f.y = h * v * v + p;
+  }
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Boundary ghosts
+// ---------------------------------------------------------------------------
+
+__device__ double hydrograph(const Dev& d, const InflowDesc& f, double t) {
+  const double* tk = d.knot_t + f.koff;
+  const double* qk = d.knot_q + f.koff;
+  if (t <= tk[0]) return qk[0];
+  for (int k = 0; k + 1 < f.nk; ++k) {
+    if (t <= tk[k + 1]) {
+      const double w = (t - tk[k]) / (tk[k + 1] - tk[k]);
+      return qk[k] + w * (qk[k + 1] - qk[k]);
+    }
+  }
+  return qk[f.nk - 1];
+}
+
+// Outside state at a face of `edge` whose centre has edge coordinate s,
+// built from the cell's own unrevised limit (h, qx, qy).
+__device__ void ghost(const Dev& d, int edge, double s, double t, double& h, double& qx,
+                      double& qy) {
+  for (int k = 0; k < d.n_in; ++k) {
+    const InflowDesc& f = d.in[k];
+    if (f.edge != edge || s < f.s0 || s > f.s1) continue;
+    const double qin = hydrograph(d, f, t) / f.width;
+    const double hin = h > 0.0 ? h : 0.0;
+    const double hc = cbrt(qin * qin / d.g);
+    const double hg = hin > hc ? hin : hc;
+    const double qn = (edge == 0 || edge == 2) ? qin : -qin;
+    h = hg;
+    if (edge <= 1) { qx = qn; qy = 0.0; } else { qx = 0.0; qy = qn; }
+    return;
+  }
+  if (d.bc[edge] == 1) {
+    // free outflow: copy, without an inward normal discharge
+    if (edge == 0 && qx > 0.0) qx = 0.0;
+    if (edge == 1 && qx < 0.0) qx = 0.0;
+    if (edge == 2 && qy > 0.0) qy = 0.0;
+    if (edge == 3 && qy < 0.0) qy = 0.0;
+    return;
+  }
+  if (edge <= 1) qx = -qx; else qy = -qy;  // wall
+}
+
+// ---------------------------------------------------------------------------
+// Local limiting (Eqs. 6-7)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(fmin(a, b), c);
+  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(fmax(a, b), c);
+  return 0.0;
+}
+
+// Detector (Eq. 6, tested as J > thresh * den, the magnitude in den floored at
+// tol_dry) and generalised minmod (Eq. 7) for one component along one direction.
+__device__ __forceinline__ double limit_component(double thresh, double tol, double half,
+                                                  double k0w, double k1w, double k0, double k1,
+                                                  double k0e, double k1e) {
+  const double s3 = 1.7320508075688772;  // sqrt(3) rounded to nearest
+  const double jE = fabs((k0e - k1e) - (k0 + k1));
+  const double jW = fabs((k0 - k1) - (k0w + k1w));
+  const double a = fabs(k0 - k1 / s3), b = fabs(k0 + k1 / s3);
+  double mag = a > b ? a : b;
+  if (mag < tol) mag = tol;  // still water: round-off never counts as a shock
+  const double den = half * mag;
+  const double jm = jE > jW ? jE : jW;
+  if (!(jm > thresh * den)) return k1;
+  return minmod3(k1, k0e - k0, k0 - k0w);
+}
+
+// Slopes (h, qx, qy) of cell (i, j) along `dir` (1 = x, 2 = y) from buffer U,
+// limited by Eqs. 6-7 when the cell and both neighbours are wet and the cell
+// is not on the edge normal to `dir`; eta = h + z is limited instead of h.
+__device__ void limited_slopes(const Dev& d, const double* __restrict__ U, int i, int j, int dir,
+                               double& sh, double& sqx, double& sqy) {
+  const long long P = d.plane;
+  const long long c = (long long)j * d.pitch + i;
+  sh = U[(dir)*P + c];
+  sqx = U[(3 + dir) * P + c];
+  sqy = U[(6 + dir) * P + c];
+  const bool lo = dir == 1 ? i > 0 : j > 0;
+  const bool hi = dir == 1 ? i + 1 < d.nx : j + 1 < d.ny;
+  if (!lo || !hi) return;
+  const long long cl = dir == 1 ? c - 1 : c - d.pitch;
+  const long long ch = dir == 1 ? c + 1 : c + d.pitch;
+  const double hl = U[cl], hc = U[c], hh = U[ch];
+  if (hl <= d.tol || hc <= d.tol || hh <= d.tol) return;
+  const double half = 0.5 * (dir == 1 ? d.dx : d.dy);
+  const double* z0 = d.Z;
+  const double* z1 = d.Z + dir * P;
+  const double e1c = sh + z1[c];
+  const double e1 = limit_component(d.ds, d.tol, half, hl + z0[cl], U[dir * P + cl] + z1[cl],
+                                    hc + z0[c], e1c, hh + z0[ch], U[dir * P + ch] + z1[ch]);
+  if (e1 != e1c) sh = e1 - z1[c];
+  {
+    const double* k0 = U + 3 * P;
+    const double* k1 = U + (3 + dir) * P;
+    sqx = limit_component(d.ds, d.tol, half, k0[cl], k1[cl], k0[c], k1[c], k0[ch], k1[ch]);
+  }
+  {
+    const double* k0 = U + 6 * P;
+    const double* k1 = U + (6 + dir) * P;
+    sqy = limit_component(d.ds, d.tol, half, k0[cl], k1[cl], k0[c], k1[c], k0[ch], k1[ch]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wet-dry treatment after each stage (mass-neutral; averages untouched)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void wetdry(double* m, double z0, double z1x, double z1y, double tol) {
+  const double h0 = m[H0];
+  if (h0 <= tol) {
+#pragma unroll
+    for (int k = 1; k < 9; ++k) m[k] = 0.0;
+    return;
+  }
+  const double eta0 = h0 + z0;
+  // x direction
+  {
+    const bool fe = (h0 + m[H1X] <= tol) && !(z0 + z1x > eta0);
+    const bool fw = (h0 - m[H1X] <= tol) && !(z0 - z1x > eta0);
+    if (fe || fw) { m[H1X] = 0.0; m[QX1X] = 0.0; m[QY1X] = 0.0; }
+  }
+  {
+    const bool fn = (h0 + m[H1Y] <= tol) && !(z0 + z1y > eta0);
+    const bool fs = (h0 - m[H1Y] <= tol) && !(z0 - z1y > eta0);
+    if (fn || fs) { m[H1Y] = 0.0; m[QX1Y] = 0.0; m[QY1Y] = 0.0; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions
+// ---------------------------------------------------------------------------
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < NT / 32 ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < NT / 32 ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  return r;
+}
+
+// Courant wave-speed rate of a cell: max((|u|+c)/dx, (|v|+c)/dy) if wet.
+__device__ __forceinline__ double cell_rate(const Dev& d, double h0, double qx0, double qy0) {
+  if (!(h0 > d.tol)) return 0.0;
+  const double u = qx0 / h0, v = qy0 / h0, c = sqrt(d.g * h0);
+  return fmax((fabs(u) + c) * d.inv_dx, (fabs(v) + c) * d.inv_dy);
+}
+
+// Turns the reduced rate into the next step: Courant step (capped by dt_max,
+// dt_max if nothing is wet) then capped to land on the next target time.
+__device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
+  double dt = d.dt_max;
+  if (lam > 0.0) {
+    dt = d.cfl / lam;
+    if (dt > d.dt_max) dt = d.dt_max;
+  }
+  sc->dt_cfl = dt;
+  sc->land = 0;
+  if (!sc->fixed_dt) {
+    double target = sc->t_end;
+    if (sc->next_sample <= target) target = sc->next_sample;
+    if (sc->t + dt >= target) {
+      dt = target - sc->t;
+      sc->land = 1;
+    }
+  }
+  sc->dt = dt;
+  sc->lam_bits = 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+// Initial modes from corner data (Eq. 3): corners staged in `zc` / `ec`
+// ((ny+1) x (nx+1) dense); ec == nullptr for a dry start; man == nullptr for
+// the uniform n.
+__global__ void init_kernel(Dev d, const double* __restrict__ zc, const double* __restrict__ ec,
+                            const double* __restrict__ man, double n_uniform, double* Zw,
+                            double* Nw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= d.nx || j >= d.ny) return;
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  const int W = d.nx + 1;
+  const double* r0 = zc + (long long)j * W;
+  const double* r1 = zc + (long long)(j + 1) * W;
+  {
+    const double fE = 0.5 * (r0[i + 1] + r1[i + 1]), fW = 0.5 * (r0[i] + r1[i]);
+    const double fN = 0.5 * (r1[i] + r1[i + 1]), fS = 0.5 * (r0[i] + r0[i + 1]);
+    Zw[c] = 0.5 * (fE + fW);
+    Zw[P + c] = 0.5 * (fE - fW);
+    Zw[2 * P + c] = 0.5 * (fN - fS);
+  }
+  double h0 = 0.0, h1x = 0.0, h1y = 0.0;
+  if (ec) {
+    const double* e0 = ec + (long long)j * W;
+    const double* e1 = ec + (long long)(j + 1) * W;
+    const double a = e0[i] - r0[i], b = e0[i + 1] - r0[i + 1];
+    const double cc = e1[i] - r1[i], dd = e1[i + 1] - r1[i + 1];
+    const double fE = 0.5 * (b + dd), fW = 0.5 * (a + cc);
+    const double fN = 0.5 * (cc + dd), fS = 0.5 * (a + b);
+    h0 = 0.5 * (fE + fW);
+    h1x = 0.5 * (fE - fW);
+    h1y = 0.5 * (fN - fS);
+    if (h0 <= 0.0) { h0 = 0.0; h1x = 0.0; h1y = 0.0; }
+  }
+  double* S = d.S;
+  S[H0 * P + c] = h0;
+  S[H1X * P + c] = h1x;
+  S[H1Y * P + c] = h1y;
+#pragma unroll
+  for (int k = 3; k < 9; ++k) S[k * P + c] = 0.0;
+  Nw[c] = man ? man[(long long)j * d.nx + i] : n_uniform;
+}
+
+// Point-implicit friction (Sec. 2.1.3) at one point: q /= 1 + dt g n^2 |q| / h^(7/3).
+__device__ __forceinline__ void friction_point(double gn2dt, double tol, double h, double& qx,
+                                               double& qy) {
+  if (!(h > tol)) return;
+  const double qm = sqrt(qx * qx + qy * qy);
+  const double den = 1.0 + gn2dt * qm / (h * h * cbrt(h));
+  qx = qx / den;
+  qy = qy / den;
+}
+
+__global__ void __launch_bounds__(256) friction_kernel(Dev d) {
+  const Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= d.nx || j >= d.ny) return;
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  const double n = d.N[c];
+  if (n == 0.0) return;
+  const double dt = sc->dt;
+  const double gn2dt = dt * d.g * n * n;
+  double* S = d.S;
+  const double h0 = S[H0 * P + c], x0 = S[QX0 * P + c], y0 = S[QY0 * P + c];
+  double cx = x0, cy = y0;
+  friction_point(gn2dt, d.tol, h0, cx, cy);
+  const double r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
+  double nq[2][2];
+#pragma unroll
+  for (int dd = 1; dd <= 2; ++dd) {
+    const double h1 = S[dd * P + c], x1 = S[(3 + dd) * P + c], y1 = S[(6 + dd) * P + c];
+    double xp = x0 + x1 * r3, yp = y0 + y1 * r3, xm = x0 - x1 * r3, ym = y0 - y1 * r3;
+    friction_point(gn2dt, d.tol, h0 + h1 * r3, xp, yp);
+    friction_point(gn2dt, d.tol, h0 - h1 * r3, xm, ym);
+    nq[dd - 1][0] = hs3 * (xp - xm);
+    nq[dd - 1][1] = hs3 * (yp - ym);
+  }
+  S[QX0 * P + c] = cx;
+  S[QY0 * P + c] = cy;
+  S[QX1X * P + c] = nq[0][0];
+  S[QY1X * P + c] = nq[0][1];
+  S[QX1Y * P + c] = nq[1][0];
+  S[QY1Y * P + c] = nq[1][1];
+}
+
+// Loads the 9 coefficients of cell c from buffer U.
+__device__ __forceinline__ void load9(const double* __restrict__ U, long long P, long long c,
+                                      double* m) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = U[k * P + c];
+}
+
+struct StageSmem {
+  Lim e[TY][TX];     // east limit of each cell (left state of the face to its east)
+  Lim n[TY][TX];     // north limit of each cell
+  Lim hw[TY];        // limit west of the tile's first column (neighbour or ghost)
+  Lim he[TY];        // limit east of the tile's last column
+  Lim hs[TX];        // limit south of the tile's first row
+  Lim hn[TX];        // limit north of the tile's last row
+  F3 fx[TY][TX + 1]; // x-face fluxes; fx[ty][tx] is the west face of column tx
+  F3 fy[TY + 1][TX]; // y-face fluxes; fy[ty][tx] is the south face of row ty
+  double red[32];
+};
+
+template <bool LL, int STAGE>
+__global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
+  __shared__ StageSmem sm;
+  Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * TX + tx, j = blockIdx.y * TY + ty;
+  const bool act = i < d.nx && j < d.ny;
+  const long long P = d.plane;
+  const long long c = (long long)j * d.pitch + i;
+  const double dt = sc->dt;
+  const double ts = STAGE == 1 ? sc->t : sc->t + dt;  // boundary-condition time
+  const double* __restrict__ In = STAGE == 1 ? d.S : d.T;
+  const double g = d.g, tol = d.tol;
+  const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
+  const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
+
+  double m[9];
+  double z0 = 0.0, z1x = 0.0, z1y = 0.0;
+  Lim Es, Ws, Ns, Ss;
+  double eh = 0, eqx = 0, eqy = 0, nh = 0, nqx = 0, nqy = 0;  // own unrevised E / N limits
+  double zb1x = 0.0, zb1y = 0.0;
+  if (act) {
+    load9(In, P, c, m);
+    if (LL) {
+      limited_slopes(d, In, i, j, 1, m[H1X], m[QX1X], m[QY1X]);
+      limited_slopes(d, In, i, j, 2, m[H1Y], m[QX1Y], m[QY1Y]);
+    }
+    z0 = d.Z[c];
+    z1x = d.Z[P + c];
+    z1y = d.Z[2 * P + c];
+    eh = m[H0] + m[H1X]; eqx = m[QX0] + m[QX1X]; eqy = m[QY0] + m[QY1X];
+    const double wh = m[H0] - m[H1X], wqx = m[QX0] - m[QX1X], wqy = m[QY0] - m[QY1X];
+    nh = m[H0] + m[H1Y]; nqx = m[QX0] + m[QX1Y]; nqy = m[QY0] + m[QY1Y];
+    const double shh = m[H0] - m[H1Y], sqx = m[QX0] - m[QX1Y], sqy = m[QY0] - m[QY1Y];
+    Es = revise(eh, eqx, eqy, tol);
+    Ws = revise(wh, wqx, wqy, tol);
+    Ns = revise(nh, nqx, nqy, tol);
+    Ss = revise(shh, sqx, sqy, tol);
+    // topography limits revised with the own depth limit at each face
+    const double zE = (z0 + z1x) - (eh < 0.0 ? -eh : 0.0);
+    const double zW = (z0 - z1x) - (wh < 0.0 ? -wh : 0.0);
+    const double zN = (z0 + z1y) - (nh < 0.0 ? -nh : 0.0);
+    const double zS = (z0 - z1y) - (shh < 0.0 ? -shh : 0.0);
+    zb1x = 0.5 * (zE - zW);
+    zb1y = 0.5 * (zN - zS);
+    sm.e[ty][tx] = Es;
+    sm.n[ty][tx] = Ns;
+
+    // west neighbour's east limit, or the west-edge ghost
+    if (tx == 0) {
+      double h, qx, qy;
+      if (i == 0) {
+        h = wh; qx = wqx; qy = wqy;
+        ghost(d, 0, (j + 0.5) * d.dy, ts, h, qx, qy);
+      } else {
+        const long long cw = c - 1;
+        double s1h = In[H1X * P + cw], s1x = In[QX1X * P + cw], s1y = In[QY1X * P + cw];
+        if (LL) limited_slopes(d, In, i - 1, j, 1, s1h, s1x, s1y);
+        h = In[H0 * P + cw] + s1h; qx = In[QX0 * P + cw] + s1x; qy = In[QY0 * P + cw] + s1y;
+      }
+      sm.hw[ty] = revise(h, qx, qy, tol);
+    }
+    if (east_edge) {
+      double h, qx, qy;
+      if (i == d.nx - 1) {
+        h = eh; qx = eqx; qy = eqy;
+        ghost(d, 1, (j + 0.5) * d.dy, ts, h, qx, qy);
+      } else {
+        const long long ce = c + 1;
+        double s1h = In[H1X * P + ce], s1x = In[QX1X * P + ce], s1y = In[QY1X * P + ce];
+        if (LL) limited_slopes(d, In, i + 1, j, 1, s1h, s1x, s1y);
+        h = In[H0 * P + ce] - s1h; qx = In[QX0 * P + ce] - s1x; qy = In[QY0 * P + ce] - s1y;
+      }
+      sm.he[ty] = revise(h, qx, qy, tol);
+    }
+    if (ty == 0) {
+      double h, qx, qy;
+      if (j == 0) {
+        h = shh; qx = sqx; qy = sqy;
+        ghost(d, 2, (i + 0.5) * d.dx, ts, h, qx, qy);
+      } else {
+        const long long cs = c - d.pitch;
+        double s1h = In[H1Y * P + cs], s1x = In[QX1Y * P + cs], s1y = In[QY1Y * P + cs];
+        if (LL) limited_slopes(d, In, i, j - 1, 2, s1h, s1x, s1y);
+        h = In[H0 * P + cs] + s1h; qx = In[QX0 * P + cs] + s1x; qy = In[QY0 * P + cs] + s1y;
+      }
+      sm.hs[tx] = revise(h, qx, qy, tol);
+    }
+    if (north_edge) {
+      double h, qx, qy;
+      if (j == d.ny - 1) {
+        h = nh; qx = nqx; qy = nqy;
+        ghost(d, 3, (i + 0.5) * d.dx, ts, h, qx, qy);
+      } else {
+        const long long cn = c + d.pitch;
+        double s1h = In[H1Y * P + cn], s1x = In[QX1Y * P + cn], s1y = In[QY1Y * P + cn];
+        if (LL) limited_slopes(d, In, i, j + 1, 2, s1h, s1x, s1y);
+        h = In[H0 * P + cn] - s1h; qx = In[QX0 * P + cn] - s1x; qy = In[QY0 * P + cn] - s1y;
+      }
+      sm.hn[tx] = revise(h, qx, qy, tol);
+    }
+  }
+  __syncthreads();
+
+  // one HLL flux per face of the tile
+  double brate = 0.0;  // water entering through domain-edge faces (m^3/s)
+  if (act) {
+    const Lim& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
+    const F3 fw = flux_x(Lw, Ws, g, tol);
+    sm.fx[ty][tx] = fw;
+    if (i == 0) brate += fw.h * d.dy;
+    if (east_edge) {
+      const F3 fe = flux_x(Es, sm.he[ty], g, tol);
+      sm.fx[ty][tx + 1] = fe;
+      if (i == d.nx - 1) brate -= fe.h * d.dy;
+    }
+    const Lim& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
+    const F3 fs = flux_y(Ls, Ss, g, tol);
+    sm.fy[ty][tx] = fs;
+    if (j == 0) brate += fs.h * d.dx;
+    if (north_edge) {
+      const F3 fn = flux_y(Ns, sm.hn[tx], g, tol);
+      sm.fy[ty + 1][tx] = fn;
+      if (j == d.ny - 1) brate -= fn.h * d.dx;
+    }
+  }
+  __syncthreads();
+
+  double lam = 0.0;
+  bool bad = false;
+  if (act) {
+    const F3 FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
+    const F3 GS = sm.fy[ty][tx], GN = sm.fy[ty + 1][tx];
+    // dummy modes (Eq. 5; the second line read as the 0y mode)
+    const double h0x = 0.5 * (Es.h + Ws.h), x0x = 0.5 * (Es.qx + Ws.qx), y0x = 0.5 * (Es.qy + Ws.qy);
+    const double h1x_ = 0.5 * (Es.h - Ws.h), x1x = 0.5 * (Es.qx - Ws.qx), y1x = 0.5 * (Es.qy - Ws.qy);
+    const double h0y = 0.5 * (Ns.h + Ss.h), x0y = 0.5 * (Ns.qx + Ss.qx), y0y = 0.5 * (Ns.qy + Ss.qy);
+    const double h1y_ = 0.5 * (Ns.h - Ss.h), x1y = 0.5 * (Ns.qx - Ss.qx), y1y = 0.5 * (Ns.qy - Ss.qy);
+    const double r3 = 1.0 / 1.7320508075688772;
+    const F3 Fp = phys_flux(h0x + h1x_ * r3, x0x + x1x * r3, y0x + y1x * r3, g, tol, false);
+    const F3 Fm = phys_flux(h0x - h1x_ * r3, x0x - x1x * r3, y0x - y1x * r3, g, tol, false);
+    const F3 Gp = phys_flux(h0y + h1y_ * r3, x0y + x1y * r3, y0y + y1y * r3, g, tol, true);
+    const F3 Gm = phys_flux(h0y - h1y_ * r3, x0y - x1y * r3, y0y - y1y * r3, g, tol, true);
+    const double idx = d.inv_dx, idy = d.inv_dy;
+    // Eq. 4a
+    double L[9];
+    L[H0] = -(FE.h - FW.h) * idx - (GN.h - GS.h) * idy;
+    L[QX0] = -(FE.x - FW.x) * idx - (GN.x - GS.x) * idy - 2.0 * g * h0x * zb1x * idx;
+    L[QY0] = -(FE.y - FW.y) * idx - (GN.y - GS.y) * idy - 2.0 * g * h0y * zb1y * idy;
+    if (d.rain != 0.0 && ts >= d.rain_t0 && ts < d.rain_t1) L[H0] += d.rain;
+    if (c == d.src_idx) L[H0] += d.qp * idx * idy;
+    // Eq. 4b
+    const double k3x = -3.0 * idx, k3y = -3.0 * idy, g23 = 2.0 * g / 3.0;
+    L[H1X] = k3x * ((FE.h + FW.h) - (Fp.h + Fm.h));
+    L[QX1X] = k3x * ((FE.x + FW.x) - (Fp.x + Fm.x) + g23 * h1x_ * zb1x);
+    L[QY1X] = k3x * ((FE.y + FW.y) - (Fp.y + Fm.y));
+    // Eq. 4c
+    L[H1Y] = k3y * ((GN.h + GS.h) - (Gp.h + Gm.h));
+    L[QX1Y] = k3y * ((GN.x + GS.x) - (Gp.x + Gm.x));
+    L[QY1Y] = k3y * ((GN.y + GS.y) - (Gp.y + Gm.y) + g23 * h1y_ * zb1y);
+
+    double out[9];
+    if (STAGE == 1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[k] = m[k] + dt * L[k];
+      wetdry(out, z0, z1x, z1y, tol);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) d.T[k * P + c] = out[k];
+      if (LL) {
+        d.Q[0 * P + c] = m[H1X]; d.Q[1 * P + c] = m[H1Y];
+        d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
+        d.Q[4 * P + c] = m[QY1X]; d.Q[5 * P + c] = m[QY1Y];
+      }
+    } else {
+      double un[9];
+      un[H0] = d.S[H0 * P + c]; un[QX0] = d.S[QX0 * P + c]; un[QY0] = d.S[QY0 * P + c];
+      if (LL) {
+        un[H1X] = d.Q[0 * P + c]; un[H1Y] = d.Q[1 * P + c];
+        un[QX1X] = d.Q[2 * P + c]; un[QX1Y] = d.Q[3 * P + c];
+        un[QY1X] = d.Q[4 * P + c]; un[QY1Y] = d.Q[5 * P + c];
+      } else {
+        un[H1X] = d.S[H1X * P + c]; un[H1Y] = d.S[H1Y * P + c];
+        un[QX1X] = d.S[QX1X * P + c]; un[QX1Y] = d.S[QX1Y * P + c];
+        un[QY1X] = d.S[QY1X * P + c]; un[QY1Y] = d.S[QY1Y * P + c];
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[k] = 0.5 * (un[k] + m[k] + dt * L[k]);
+      wetdry(out, z0, z1x, z1y, tol);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
+      lam = cell_rate(d, out[H0], out[QX0], out[QY0]);
+      bad = !(isfinite(out[H0]) && isfinite(out[QX0]) && isfinite(out[QY0])) || out[H0] < -1.0;
+    }
+  }
+
+  // per-block boundary mass rate (fixed slot per block: deterministic sums)
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const double bsum = block_sum<TX * TY>(brate, sm.red);
+  if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
+  if (STAGE == 1) return;
+
+  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+  const double bl = block_max<TX * TY>(lam, sm.red);
+  __shared__ bool last;
+  if (tx == 0 && ty == 0) {
+    if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
+    __threadfence();
+    const unsigned int k = atomicAdd(&sc->count, 1u);
+    last = (k == (unsigned int)d.nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+
+  // ---- last block: time, ledger, gauges, next step ----
+  const int tid = ty * TX + tx;
+  double part = 0.0;
+  for (int k = tid; k < d.nblocks; k += TX * TY)
+    part += __ldcg(&d.bpart[k]) + __ldcg(&d.bpart[d.nblocks + k]);
+  const double btot = block_sum<TX * TY>(part, sm.red);
+  if (tid == 0) {
+    const double t = sc->t;
+    double src1 = 0.0, src2 = 0.0;
+    const double area = d.dx * d.dy * (double)d.nx * (double)d.ny;
+    if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
+    if (d.rain != 0.0 && t + dt >= d.rain_t0 && t + dt < d.rain_t1) src2 += d.rain * area;
+    if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
+    sc->ledger += dt * 0.5 * (btot + src1 + src2);
+    double tn;
+    bool at_sample = false;
+    if (sc->land && !sc->fixed_dt) {
+      double target = sc->t_end;
+      if (sc->next_sample <= target) { target = sc->next_sample; at_sample = true; }
+      tn = target;
+    } else {
+      tn = t + dt;
+    }
+    sc->t = tn;
+    if (at_sample) {
+      const int r = sc->nsamp;
+      if (r < d.max_samples) {
+        d.samp_t[r] = tn;
+        for (int k = 0; k < d.ngauge; ++k) {
+          const long long gc = d.g_idx[k];
+          const double h = __ldcg(&d.S[gc]) + d.g_xi[k] * __ldcg(&d.S[P + gc]) +
+                           d.g_eta[k] * __ldcg(&d.S[2 * P + gc]);
+          d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
+        }
+      }
+      sc->nsamp = r + 1;
+      sc->next_sample += sc->sample_every;
+    }
+    if (!(dt > 0.0) || !isfinite(tn)) sc->nonfinite = 1;
+    sc->steps += 1;
+    sc->last_dt = dt;
+    schedule_next_dt(d, sc, __longlong_as_double((long long)atomicAdd(&sc->lam_bits, 0ull)));
+    if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
+    sc->count = 0u;
+  }
+}
+
+// Courant reduction of the current state alone (after set-up or set_state).
+__global__ void __launch_bounds__(256) rate_kernel(Dev d) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double lam = 0.0;
+  if (i < d.nx && j < d.ny) {
+    const long long P = d.plane, c = (long long)j * d.pitch + i;
+    lam = cell_rate(d, d.S[c], d.S[QX0 * P + c], d.S[QY0 * P + c]);
+  }
+  const double bl = block_max<256>(lam, red);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  Scalars* sc = d.sc;
+  if (tid == 0) {
+    if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
+    __threadfence();
+    const unsigned int k = atomicAdd(&sc->count, 1u);
+    last = (k == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (last && tid == 0) {
+    __threadfence();
+    schedule_next_dt(d, sc, __longlong_as_double((long long)atomicAdd(&sc->lam_bits, 0ull)));
+    sc->count = 0u;
+  }
+}
+
+// Starts a run_to: sets the target, recomputes the next sample time from the
+// current time and re-caps the pending Courant step to land on the targets.
+__global__ void begin_run_kernel(Dev d, double t_end) {
+  Scalars* sc = d.sc;
+  sc->t_end = t_end;
+  sc->fixed_dt = 0;
+  if (sc->sample_every > 0.0)
+    sc->next_sample = (floor(sc->t / sc->sample_every + 1e-9) + 1.0) * sc->sample_every;
+  double dt = sc->dt_cfl;
+  sc->land = 0;
+  double target = sc->t_end;
+  if (sc->next_sample <= target) target = sc->next_sample;
+  if (sc->t + dt >= target) {
+    dt = target - sc->t;
+    sc->land = 1;
+  }
+  sc->dt = dt;
+  sc->done = sc->t >= sc->t_end ? 1 : 0;
+}
+
+// Starts a dg2_step: forced dt (> 0) or the pending Courant step, no landing.
+__global__ void begin_step_kernel(Dev d, double dt) {
+  Scalars* sc = d.sc;
+  sc->fixed_dt = 1;
+  sc->done = 0;
+  sc->land = 0;
+  sc->dt = dt > 0.0 ? dt : sc->dt_cfl;
+}
+
+// Domain mass sum(h0) dx dy (Eq. 11): fixed-order block partials, then the
+// last block sums them in block order (deterministic).
+__global__ void __launch_bounds__(256) mass_kernel(Dev d) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double v = 0.0;
+  if (i < d.nx && j < d.ny) v = d.S[(long long)j * d.pitch + i];
+  const double s = block_sum<256>(v, red);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nb = gridDim.x * gridDim.y;
+  Scalars* sc = d.sc;
+  if (tid == 0) {
+    d.mpart[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+    const unsigned int k = atomicAdd(&sc->count, 1u);
+    last = (k == (unsigned int)nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double part = 0.0;
+  for (int k = tid; k < nb; k += 256) part += __ldcg(&d.mpart[k]);
+  const double tot = block_sum<256>(part, red);
+  if (tid == 0) {
+    sc->mass = tot * d.dx * d.dy;
+    if (sc->ledger_init) {
+      sc->ledger = sc->mass;
+      sc->ledger_init = 0;
+    }
+    sc->count = 0u;
+  }
+}
+
+}  // namespace dg2

@@ -200,3 +200,15 @@ def test_limiter_is_inactive_on_smooth_flow():
             o.step(0.02)
         runs.append(o.state())
     assert np.array_equal(runs[0], runs[1])
+
+
+def test_limiter_is_inactive_at_rest():
+    """Still water against walls: the discharges are round-off, below the detector's floor,
+    so DG2-LL takes exactly the DG2-NL steps."""
+    from conftest import make_oracle
+    case = inputs.wall_blocks()
+    a, b = make_oracle(case, limiter=False), make_oracle(case, limiter=True)
+    for _ in range(30):
+        a.step()
+        b.step()
+    assert np.array_equal(a.state(), b.state())
