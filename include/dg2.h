@@ -162,6 +162,30 @@ int dg2_kernel_times(dg2_ctx *ctx, double *ms3, int64_t *nsteps);
 /* Number of kernels this context has launched (for launch accounting). */
 int64_t dg2_launch_count(const dg2_ctx *ctx);
 
+/* Largest grid height (rows) that dg2_mass_noalloc accepts. */
+#define DG2_NOALLOC_MAX_ROWS 65536
+
+/* Domain mass sum(h0) * dx * dy of a depth-average plane, computed without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory themselves
+ * (a fixed memory pool they do not own, a plugin given only raw pointers).
+ *   h0_dev   device pointer to ny rows of pitch doubles (row j at h0_dev + j*pitch;
+ *            the first nx of each row are summed), e.g. plane 0 of a state.
+ *   mass_dev device pointer to one double that receives the mass (m^3).
+ *   cuda_stream  the stream the reduction runs on (void* cudaStream_t, NULL =
+ *            legacy default stream); the call returns before it finishes.
+ * Scratch: one partial per grid row and a block counter in a fixed
+ * file-scope __device__ array (DG2_NOALLOC_MAX_ROWS doubles, 512 KiB), held by
+ * every GPU that loads the library until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Every call
+ * shares the array, so calls that overlap on the GPU race; the counter is
+ * cleared at the start of each call.  DG2_E_ARG if ny > DG2_NOALLOC_MAX_ROWS,
+ * nx or ny < 1, pitch < nx, dx or dy <= 0, or a pointer is NULL.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine. */
+int dg2_mass_noalloc(const double *h0_dev, int nx, int ny, int pitch, double dx, double dy,
+                     double *mass_dev, void *cuda_stream);
+
 /* Releases the host-side context (the workspace stays the caller's). */
 int dg2_destroy(dg2_ctx *ctx);
 

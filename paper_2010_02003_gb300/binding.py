@@ -30,8 +30,9 @@ EXPORTS = (
     "dg2_set_bc_inflow", "dg2_set_sources", "dg2_step", "dg2_run_to", "dg2_set_gauges",
     "dg2_read_gauges", "dg2_mass", "dg2_get_state", "dg2_set_state", "dg2_get_topo",
     "dg2_get_time", "dg2_enable_kernel_timing", "dg2_kernel_times", "dg2_launch_count",
-    "dg2_destroy",
+    "dg2_mass_noalloc", "dg2_destroy",
 )
+DG2_NOALLOC_MAX_ROWS = 65536
 
 
 class Dg2Params(ctypes.Structure):
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
         "dg2_enable_kernel_timing": (I, [P, I]),
         "dg2_kernel_times": (I, [P, dp, i64p]),
         "dg2_launch_count": (ctypes.c_int64, [P]),
+        "dg2_mass_noalloc": (I, [P, I, I, I, D, D, P, P]),
         "dg2_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -211,6 +213,14 @@ def dg2_kernel_times(ctx):
 
 def dg2_launch_count(ctx) -> int:
     return int(load().dg2_launch_count(ctx))
+
+
+def dg2_mass_noalloc(h0_ptr: int, nx: int, ny: int, pitch: int, dx: float, dy: float,
+                     mass_ptr: int, stream_ptr: int = 0):
+    """Mass of a device depth plane into a device double, with no device allocation
+    (the library's fixed scratch); see include/dg2.h."""
+    _check(load().dg2_mass_noalloc(ctypes.c_void_p(h0_ptr), nx, ny, pitch, float(dx), float(dy),
+                                   ctypes.c_void_p(mass_ptr), ctypes.c_void_p(stream_ptr)))
 
 
 def dg2_destroy(ctx):

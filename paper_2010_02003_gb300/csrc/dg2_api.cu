@@ -92,6 +92,11 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
 
 }  // namespace
 
+namespace dg2 {
+// Lets the other translation units of the library report through dg2_last_error().
+void set_error_text(const std::string& s) { g_err = s; }
+}  // namespace dg2
+
 struct dg2_ctx {
   Dev d;
   dg2_params p;
