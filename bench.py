@@ -28,10 +28,13 @@ METRIC = "DG2 cell-updates/s (FP64, FP32) & % HBM roofline; adjoint/forward time
 NX, NY, DX = 2000, 1000, 2.0
 # Unique bytes each kernel must move per cell (FP64): see the design doc (roofline section).
 BYTES_PER_CELL = {
-    "friction": 16 * 8,
-    "stage1": {"nl": 21 * 8, "ll": 27 * 8},
-    "stage2": {"nl": 30 * 8, "ll": 30 * 8},
+    "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
+             "stage2": {"nl": 30 * 8, "ll": 30 * 8}},
+    # FP32 free-surface form: 9 state planes, 2 face-topography planes, Manning n
+    "fp32": {"friction": (10 + 2 + 6) * 4, "stage1": {"nl": (9 + 2 + 9) * 4, "ll": (9 + 2 + 15) * 4},
+             "stage2": {"nl": (9 + 9 + 2 + 9) * 4, "ll": (9 + 9 + 2 + 9) * 4}},
 }
+KERNELS = ["friction", "stage1", "stage2"]
 
 
 def parse():
@@ -131,9 +134,23 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def time_variant(B, torch, case, variant, steps, warmup, timing=True):
+def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
+    """HBM roofline of the dominant kernel of one timed run (live event timing)."""
+    kms = run["kernel_ms"] / max(run["timed"], 1)
+    dom = int(np.argmax(kms))
+    tab = BYTES_PER_CELL[prec][KERNELS[dom]]
+    per_cell = tab if dom == 0 else tab[var]
+    achieved = per_cell * cells / (kms[dom] * 1e-3) / 1e9
+    names = {"friction": "friction", "stage1": "stage 1", "stage2": "stage 2"}
+    return {"bound": "hbm", "kernel": f"{prec} {var.upper()} {names[KERNELS[dom]]}",
+            "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
+            "traffic": None, "peak_source": peak_src, "bytes_per_cell": per_cell,
+            "kernel_ms": {n: float(k) for n, k in zip(KERNELS, kms)}}
+
+
+def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=0):
     """Device-timed steps of one variant; returns dict of timings."""
-    s = B.solver_from_case(case, variant=variant)
+    s = B.solver_from_case(case, variant=variant, precision=precision)
     st = s.stream
     for _ in range(warmup):
         s.step(-1.0)
@@ -250,17 +267,16 @@ def main():
     value = world * cells * args.steps / (ms_ll * 1e-3)
     value_nl = world * cells * args.steps / (ms_nl * 1e-3)
 
-    # roofline of the dominant kernel (stage 2 or stage 1 of DG2-LL), live event timing
-    kms = ll["kernel_ms"] / max(ll["timed"], 1)
-    names = ["friction", "stage1", "stage2"]
-    dom = int(np.argmax(kms))
-    per_cell = BYTES_PER_CELL[names[dom]] if dom == 0 else BYTES_PER_CELL[names[dom]]["ll"]
+    # FP32 free-surface path, both variants
+    barrier(world)
+    f_ll = time_variant(B, torch, case, B.DG2_LL, args.steps, warmup, precision=B.DG2_FP32)
+    f_nl = time_variant(B, torch, case, B.DG2_NL, args.steps, warmup, precision=B.DG2_FP32)
+    ms_fll = max_over_ranks(f_ll["ms"], world)
+    ms_fnl = max_over_ranks(f_nl["ms"], world)
+
+    # roofline of the dominant kernel of each run, live event timing
     pk, pk_src = peaks()
-    achieved = per_cell * cells / (kms[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"stage_kernel<LL,{dom}>" if dom else "friction_kernel",
-                "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_src,
-                "kernel_ms": {n: float(k) for n, k in zip(names, kms)}}
+    roofline = kernel_roofline(ll, "fp64", "ll", cells, pk["hbm_gbs"], pk_src)
 
     # end to end through the C ABI with host buffers
     e2e_s, h2d, d2h = e2e_run(B, torch, case, B.DG2_LL, args.steps)
@@ -283,8 +299,16 @@ def main():
                            "wet_fraction": ll["wet_fraction"],
                            "l2": "inputs larger than L2 (state 2 x 144 MB)",
                            "parallelism": f"replicas x{world}"},
-                "variants": {"fp64_nl": {"value": value_nl, "ms_per_step": ms_nl / args.steps,
-                                         "wet_fraction": nl["wet_fraction"]}},
+                "variants": {
+                    "fp64_nl": {"value": value_nl, "ms_per_step": ms_nl / args.steps,
+                                "roofline": kernel_roofline(nl, "fp64", "nl", cells, pk["hbm_gbs"], pk_src)},
+                    "fp32_ll": {"value": world * cells * args.steps / (ms_fll * 1e-3),
+                                "ms_per_step": ms_fll / args.steps,
+                                "roofline": kernel_roofline(f_ll, "fp32", "ll", cells, pk["hbm_gbs"], pk_src)},
+                    "fp32_nl": {"value": world * cells * args.steps / (ms_fnl * 1e-3),
+                                "ms_per_step": ms_fnl / args.steps,
+                                "roofline": kernel_roofline(f_nl, "fp32", "nl", cells, pk["hbm_gbs"], pk_src)},
+                },
                 "gpu_launches": int(ll["launches"]), "roofline": roofline, "e2e": e2e,
                 "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line))

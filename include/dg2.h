@@ -50,7 +50,12 @@ enum {
 };
 
 enum { DG2_NL = 0, DG2_LL = 1 };            /* DG2-NL: no limiting; DG2-LL: Eqs. 6-7 */
-enum { DG2_FP64 = 0 };                      /* arithmetic of the state and operators */
+/* Arithmetic of the bulk update.  DG2_FP64: FP64 depth modes, the form of
+ * Eqs. 4-5.  DG2_FP32: FP32 free-surface modes eta = h + z with the momentum
+ * terms regrouped around each limit's own hydrostatic pressure (algebraically
+ * Eqs. 4-5, exactly still at rest in FP32); time, step size, reductions and
+ * the mass ledger stay FP64 in both.  State I/O is FP64 depth modes in both. */
+enum { DG2_FP64 = 0, DG2_FP32 = 1 };
 enum { DG2_WALL = 0, DG2_OPEN = 1 };        /* edge types                            */
 enum { DG2_WEST = 0, DG2_EAST = 1, DG2_SOUTH = 2, DG2_NORTH = 3 };
 
@@ -61,7 +66,7 @@ typedef struct dg2_params {
     double ds_thresh;   /* shock-detector threshold of Eq. 6 (default 10)            */
     double dt_max;      /* time step when no cell is wet, and upper cap (default 1 s)*/
     int variant;        /* DG2_NL or DG2_LL                                          */
-    int precision;      /* DG2_FP64                                                  */
+    int precision;      /* DG2_FP64 or DG2_FP32                                      */
     int bc[4];          /* DG2_WALL or DG2_OPEN per edge, indexed by DG2_WEST..NORTH */
     int max_gauges;     /* capacity of the gauge table (default 64)                  */
     int max_samples;    /* capacity of the gauge sample buffer in rows (default 4096)*/

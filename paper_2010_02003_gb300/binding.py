@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libdg2.so")
 DG2_OK, DG2_E_ARG, DG2_E_STATE, DG2_E_CUDA, DG2_E_NONFINITE, DG2_E_NOMEM = 0, -1, -2, -3, -4, -5
 DG2_E_OVERFLOW = -7
 DG2_NL, DG2_LL = 0, 1
-DG2_FP64 = 0
+DG2_FP64, DG2_FP32 = 0, 1
 DG2_WALL, DG2_OPEN = 0, 1
 DG2_WEST, DG2_EAST, DG2_SOUTH, DG2_NORTH = 0, 1, 2, 3
 
@@ -233,9 +233,10 @@ class Solver:
     """One DG2 problem on the current CUDA device.  The device workspace is a torch
     uint8 tensor; kernels run on ``stream`` (default: a new torch stream)."""
 
-    def __init__(self, nx, ny, dx, dy=None, *, variant=DG2_NL, cfl=0.3, tol_dry=1e-5,
-                 ds_thresh=10.0, dt_max=1.0, g=9.80665, bc: Sequence[int] = (DG2_WALL,) * 4,
-                 max_gauges=64, max_samples=4096, stream=None, device=None):
+    def __init__(self, nx, ny, dx, dy=None, *, variant=DG2_NL, precision=DG2_FP64, cfl=0.3,
+                 tol_dry=1e-5, ds_thresh=10.0, dt_max=1.0, g=9.80665,
+                 bc: Sequence[int] = (DG2_WALL,) * 4, max_gauges=64, max_samples=4096,
+                 stream=None, device=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the DG2 solver needs a CUDA device")
@@ -244,7 +245,7 @@ class Solver:
         self.dy = float(dx if dy is None else dy)
         p = dg2_default_params()
         p.g, p.cfl, p.tol_dry, p.ds_thresh, p.dt_max = g, cfl, tol_dry, ds_thresh, dt_max
-        p.variant, p.precision = int(variant), DG2_FP64
+        p.variant, p.precision = int(variant), int(precision)
         for k in range(4):
             p.bc[k] = int(bc[k])
         p.max_gauges, p.max_samples = int(max_gauges), int(max_samples)
@@ -323,9 +324,10 @@ class Solver:
         return dg2_launch_count(self.ctx)
 
 
-def solver_from_case(case, variant=DG2_NL, **kw) -> Solver:
+def solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, **kw) -> Solver:
     """Builds a Solver from an inputs.Case (DEM, water, roughness, inflows, sources, gauges)."""
-    s = Solver(case.nx, case.ny, case.dx, case.dy, variant=variant, cfl=case.cfl, bc=case.bc, **kw)
+    s = Solver(case.nx, case.ny, case.dx, case.dy, variant=variant, precision=precision,
+               cfl=case.cfl, bc=case.bc, **kw)
     s.set_dem(case.z_corner, case.manning, case.n_uniform, case.eta_corner)
     for f in case.inflows:
         s.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)

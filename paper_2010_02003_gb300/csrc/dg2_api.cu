@@ -16,8 +16,10 @@
 
 #include "../../include/dg2.h"
 #include "dg2_device.cuh"
+#include "dg2_fs32.cuh"
 
 using dg2::Dev;
+using dg2::f32::D32;
 using dg2::Scalars;
 
 namespace {
@@ -48,9 +50,9 @@ constexpr int kChunkMin = 16, kChunkMax = 1024;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  int pitch;
+  int pitch, zpx;
   long long plane;
-  size_t off_S, off_T, off_Q, off_Z, off_N, off_bpart, off_mpart, off_kt, off_kq;
+  size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
   size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, total;
   int nblocks, mblocks;
 };
@@ -60,8 +62,13 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
       p.max_samples < 1)
     return false;
   L.pitch = (nx + 31) / 32 * 32;
+  L.zpx = (nx + 1 + 31) / 32 * 32;
   L.plane = (long long)L.pitch * ny;
-  const size_t pb = (size_t)L.plane * sizeof(double);
+  const bool f32 = p.precision == DG2_FP32;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  const size_t pb = (size_t)L.plane * esz;
+  // set_dem stages the FP64 corner arrays and Manning field in the stage buffer
+  const size_t staging = sizeof(double) * (2 * (size_t)(nx + 1) * (ny + 1) + (size_t)nx * ny);
   L.nblocks = ((nx + dg2::TX - 1) / dg2::TX) * ((ny + dg2::TY - 1) / dg2::TY);
   L.mblocks = ((nx + 31) / 32) * ((ny + 7) / 8);
   size_t o = 0;
@@ -71,9 +78,11 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
     return at;
   };
   L.off_S = take(9 * pb);
-  L.off_T = take(9 * pb);
+  L.off_T = take(9 * pb > staging ? 9 * pb : staging);
   L.off_Q = take(p.variant == DG2_LL ? 6 * pb : 0);
-  L.off_Z = take(3 * pb);
+  L.off_Z = take(f32 ? 0 : 3 * pb);
+  L.off_ZX = take(f32 ? (size_t)ny * L.zpx * sizeof(float) : 0);
+  L.off_ZY = take(f32 ? (size_t)(ny + 1) * L.pitch * sizeof(float) : 0);
   L.off_N = take(pb);
   L.off_bpart = take(2 * (size_t)L.nblocks * sizeof(double));
   L.off_mpart = take((size_t)L.mblocks * sizeof(double));
@@ -98,7 +107,9 @@ void set_error_text(const std::string& s) { g_err = s; }
 }  // namespace dg2
 
 struct dg2_ctx {
-  Dev d;
+  Dev d;          // FP64 launch parameters (also carries the shared scalars/tables)
+  D32 f;          // FP32 free-surface launch parameters
+  int fp32;
   dg2_params p;
   Layout lay;
   cudaStream_t st;
@@ -133,6 +144,18 @@ void drop_graph(dg2_ctx* c) {
 
 constexpr int kMaxTimedSteps = 8192;
 
+// Copies the tables shared by both precisions (inflows, sources, gauges) from
+// the FP64 parameter block into the FP32 one.
+void mirror(dg2_ctx* c) {
+  D32& f = c->f;
+  const Dev& d = c->d;
+  f.n_in = d.n_in;
+  for (int k = 0; k < dg2::kMaxInflow; ++k) f.in[k] = d.in[k];
+  f.rain = d.rain; f.rain_t0 = d.rain_t0; f.rain_t1 = d.rain_t1;
+  f.qp = d.qp; f.src_idx = d.src_idx;
+  f.ngauge = d.ngauge;
+}
+
 // Enqueues one RK2 step: friction, stage 1, stage 2 (3 kernels).  With
 // `timed`, records an event before and after each kernel.
 void enqueue_step(dg2_ctx* c, bool timed = false) {
@@ -147,18 +170,28 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
     }
     if (c->ev.size() >= need) e = &c->ev[4 * (size_t)c->timed_steps++];
   }
+  const bool ll = c->p.variant == DG2_LL;
   if (e) cudaEventRecord(e[0], c->st);
-  dg2::friction_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(d);
+  if (c->fp32)
+    dg2::f32::friction32_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->f);
+  else
+    dg2::friction_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
-  if (c->p.variant == DG2_LL)
-    dg2::stage_kernel<true, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
-  else
-    dg2::stage_kernel<false, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  if (c->fp32) {
+    if (ll) dg2::f32::stage32_kernel<true, 1><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
+    else dg2::f32::stage32_kernel<false, 1><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
+  } else {
+    if (ll) dg2::stage_kernel<true, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+    else dg2::stage_kernel<false, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  }
   if (e) cudaEventRecord(e[2], c->st);
-  if (c->p.variant == DG2_LL)
-    dg2::stage_kernel<true, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
-  else
-    dg2::stage_kernel<false, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  if (c->fp32) {
+    if (ll) dg2::f32::stage32_kernel<true, 2><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
+    else dg2::f32::stage32_kernel<false, 2><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
+  } else {
+    if (ll) dg2::stage_kernel<true, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+    else dg2::stage_kernel<false, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+  }
   if (e) cudaEventRecord(e[3], c->st);
 }
 
@@ -175,8 +208,14 @@ int check_arg_ctx(dg2_ctx* c, bool need_dem) {
 }
 
 int recompute_dt(dg2_ctx* c) {
-  dg2::rate_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
+  if (c->fp32) dg2::f32::rate32_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->f);
+  else dg2::rate_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
   return launch_check(c, 1);
+}
+
+void launch_mass(dg2_ctx* c) {
+  if (c->fp32) dg2::f32::mass32_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->f);
+  else dg2::mass_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
 }
 
 int reset_ledger(dg2_ctx* c) {
@@ -184,8 +223,37 @@ int reset_ledger(dg2_ctx* c) {
   const int one = 1;
   CU(cudaMemcpyAsync(&c->d.sc->ledger_init, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
   CU(cudaStreamSynchronize(c->st));
-  dg2::mass_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
+  launch_mass(c);
   return launch_check(c, 1);
+}
+
+}  // namespace
+
+namespace {
+
+// FP32 contexts: host copies of the face topography and the cell modes of z
+// formed exactly as the kernels form them (FP32 sums of face values).
+int f32_topo_modes(dg2_ctx* c, std::vector<float>& z0, std::vector<float>& z1x,
+                   std::vector<float>& z1y) {
+  const int nx = c->f.nx, ny = c->f.ny;
+  std::vector<float> zx((size_t)ny * (nx + 1)), zy((size_t)(ny + 1) * nx);
+  CU(cudaMemcpy2DAsync(zx.data(), (nx + 1) * sizeof(float), c->f.ZX, c->f.zpx * sizeof(float),
+                       (nx + 1) * sizeof(float), ny, cudaMemcpyDeviceToHost, c->st));
+  CU(cudaMemcpy2DAsync(zy.data(), nx * sizeof(float), c->f.ZY, c->f.pitch * sizeof(float),
+                       nx * sizeof(float), ny + 1, cudaMemcpyDeviceToHost, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  const size_t n = (size_t)nx * ny;
+  z0.resize(n); z1x.resize(n); z1y.resize(n);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const float zW = zx[(size_t)j * (nx + 1) + i], zE = zx[(size_t)j * (nx + 1) + i + 1];
+      const float zS = zy[(size_t)j * nx + i], zN = zy[(size_t)(j + 1) * nx + i];
+      const size_t k = (size_t)j * nx + i;
+      z0[k] = 0.5f * (zE + zW);
+      z1x[k] = 0.5f * (zE - zW);
+      z1y[k] = 0.5f * (zN - zS);
+    }
+  return DG2_OK;
 }
 
 }  // namespace
@@ -226,7 +294,8 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
     return fail(DG2_E_ARG, "dx, dy must be positive");
   if (!(p.g > 0.0) || !(p.cfl > 0.0) || !(p.tol_dry >= 0.0) || !(p.dt_max > 0.0) ||
-      (p.variant != DG2_NL && p.variant != DG2_LL) || p.precision != DG2_FP64)
+      (p.variant != DG2_NL && p.variant != DG2_LL) ||
+      (p.precision != DG2_FP64 && p.precision != DG2_FP32))
     return fail(DG2_E_ARG, "invalid parameters (g, cfl, tol_dry, dt_max, variant, precision)");
   for (int k = 0; k < 4; ++k)
     if (p.bc[k] != DG2_WALL && p.bc[k] != DG2_OPEN) return fail(DG2_E_ARG, "bad edge type");
@@ -257,6 +326,9 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.dx = dx; d.dy = dy; d.inv_dx = 1.0 / dx; d.inv_dy = 1.0 / dy;
   d.g = p.g; d.cfl = p.cfl; d.tol = p.tol_dry; d.ds = p.ds_thresh; d.dt_max = p.dt_max;
   for (int k = 0; k < 4; ++k) d.bc[k] = p.bc[k];
+  c->fp32 = p.precision == DG2_FP32;
+  // plane buffers: FP64 depth modes, or FP32 free-surface modes (the FP64
+  // pointers then alias the same bytes and are used only for staging)
   d.S = (double*)(c->ws + L.off_S);
   d.T = (double*)(c->ws + L.off_T);
   d.Q = p.variant == DG2_LL ? (double*)(c->ws + L.off_Q) : nullptr;
@@ -275,6 +347,29 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.max_samples = p.max_samples;
   d.src_idx = -1;
   d.nblocks = L.nblocks;
+  {
+    D32& f = c->f;
+    memset(&f, 0, sizeof f);
+    f.nx = nx; f.ny = ny; f.pitch = L.pitch; f.zpx = L.zpx; f.plane = L.plane;
+    f.dx = (float)dx; f.dy = (float)dy;
+    f.inv_dx = (float)(1.0 / dx); f.inv_dy = (float)(1.0 / dy);
+    f.g = (float)p.g; f.tol = (float)p.tol_dry; f.ds = (float)p.ds_thresh;
+    f.dxd = dx; f.dyd = dy; f.cfl = p.cfl; f.dt_max = p.dt_max;
+    for (int k = 0; k < 4; ++k) f.bc[k] = p.bc[k];
+    f.knot_t = d.knot_t; f.knot_q = d.knot_q;
+    f.S = (float*)(c->ws + L.off_S);
+    f.T = (float*)(c->ws + L.off_T);
+    f.Q = p.variant == DG2_LL ? (float*)(c->ws + L.off_Q) : nullptr;
+    f.ZX = (const float*)(c->ws + L.off_ZX);
+    f.ZY = (const float*)(c->ws + L.off_ZY);
+    f.N = (const float*)(c->ws + L.off_N);
+    f.bpart = d.bpart; f.mpart = d.mpart; f.sc = d.sc;
+    f.max_samples = d.max_samples;
+    f.g_idx = d.g_idx; f.g_xi = d.g_xi; f.g_eta = d.g_eta;
+    f.samp_t = d.samp_t; f.samp_h = d.samp_h;
+    f.nblocks = L.nblocks;
+    f.src_idx = -1;
+  }
   c->sblock = dim3(dg2::TX, dg2::TY);
   c->sgrid = dim3((nx + dg2::TX - 1) / dg2::TX, (ny + dg2::TY - 1) / dg2::TY);
   c->pblock = dim3(32, 8);
@@ -324,11 +419,18 @@ int dg2_set_dem(dg2_ctx* c, const double* z_corner, const double* manning, doubl
     CU(cudaMemcpyAsync(ec, eta_corner, nc * sizeof(double), cudaMemcpyHostToDevice, c->st));
   if (manning)
     CU(cudaMemcpyAsync(mn, manning, ncell * sizeof(double), cudaMemcpyHostToDevice, c->st));
-  dg2::init_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d, zc, eta_corner ? ec : nullptr,
-                                                      manning ? mn : nullptr, n_uniform,
-                                                      (double*)c->d.Z, (double*)c->d.N);
+  if (c->fp32) {
+    const dim3 g1((nx + 1 + 31) / 32, (ny + 1 + 7) / 8);
+    dg2::f32::init32_kernel<<<g1, c->pblock, 0, c->st>>>(
+        c->f, zc, eta_corner ? ec : nullptr, manning ? mn : nullptr, n_uniform, (float*)c->f.ZX,
+        (float*)c->f.ZY, (float*)c->f.N);
+  } else {
+    dg2::init_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d, zc, eta_corner ? ec : nullptr,
+                                                        manning ? mn : nullptr, n_uniform,
+                                                        (double*)c->d.Z, (double*)c->d.N);
+  }
   if ((r = launch_check(c, 1))) return r;
-  CU(cudaMemsetAsync(c->d.T, 0, 9 * (size_t)c->d.plane * sizeof(double), c->st));
+  CU(cudaMemsetAsync(c->d.T, 0, c->lay.off_Q - c->lay.off_T, c->st));
   // scalars: t = 0, clear run state and samples
   Scalars s0;
   CU(cudaMemcpyAsync(&s0, c->d.sc, sizeof s0, cudaMemcpyDeviceToHost, c->st));
@@ -389,6 +491,7 @@ int dg2_set_bc_inflow(dg2_ctx* c, int edge, double s0_m, double len_m, const dou
                      cudaMemcpyHostToDevice, c->st));
   CU(cudaStreamSynchronize(c->st));
   c->d.n_in += 1;
+  mirror(c);
   return DG2_OK;
 }
 
@@ -411,6 +514,7 @@ int dg2_set_sources(dg2_ctx* c, double rain, double t0, double t1, double px, do
     j = j < 0 ? 0 : (j >= c->d.ny ? c->d.ny - 1 : j);
     c->d.src_idx = (long long)j * c->d.pitch + i;
   }
+  mirror(c);
   return DG2_OK;
 }
 
@@ -517,6 +621,7 @@ int dg2_set_gauges(dg2_ctx* c, const double* xy, int ngauge, double every) {
   CU(cudaMemcpyAsync(c->d.sc, &s, sizeof s, cudaMemcpyHostToDevice, c->st));
   CU(cudaStreamSynchronize(c->st));
   c->d.ngauge = ngauge;
+  mirror(c);
   return DG2_OK;
 }
 
@@ -547,7 +652,7 @@ int dg2_read_gauges(dg2_ctx* c, double* t_out, double* h_out, int cap, int* nsam
 int dg2_mass(dg2_ctx* c, double* mass, double* ledger) {
   int r = check_arg_ctx(c, true);
   if (r) return r;
-  dg2::mass_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
+  launch_mass(c);
   if ((r = launch_check(c, 1))) return r;
   Scalars s;
   if ((r = read_scalars(c, &s))) return r;
@@ -560,6 +665,28 @@ int dg2_get_state(dg2_ctx* c, double* planes, double* t) {
   int r = check_arg_ctx(c, false);
   if (r) return r;
   if (!planes) return fail(DG2_E_ARG, "planes is null");
+  if (c->fp32) {
+    // FP32 free-surface modes -> FP64 depth modes h = eta - z
+    const int nx = c->f.nx, ny = c->f.ny;
+    const size_t n = (size_t)nx * ny;
+    std::vector<float> buf(9 * n);
+    for (int k = 0; k < 9; ++k)
+      CU(cudaMemcpy2DAsync(buf.data() + k * n, nx * sizeof(float), c->f.S + k * c->f.plane,
+                           c->f.pitch * sizeof(float), nx * sizeof(float), ny,
+                           cudaMemcpyDeviceToHost, c->st));
+    std::vector<float> z0, z1x, z1y;
+    if ((r = f32_topo_modes(c, z0, z1x, z1y))) return r;
+    for (size_t k = 0; k < n; ++k) {
+      planes[k] = (double)buf[k] - (double)z0[k];
+      planes[n + k] = (double)buf[n + k] - (double)z1x[k];
+      planes[2 * n + k] = (double)buf[2 * n + k] - (double)z1y[k];
+    }
+    for (size_t k = 3 * n; k < 9 * n; ++k) planes[k] = buf[k];
+    Scalars s;
+    if ((r = read_scalars(c, &s))) return r;
+    if (t) *t = s.t;
+    return DG2_OK;
+  }
   const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
   for (int k = 0; k < 9; ++k)
     CU(cudaMemcpy2DAsync(planes + (size_t)k * c->d.nx * c->d.ny, w, c->d.S + k * c->d.plane, pb,
@@ -577,10 +704,30 @@ int dg2_set_state(dg2_ctx* c, const double* planes, double t) {
   const size_t n = (size_t)9 * c->d.nx * c->d.ny;
   for (size_t k = 0; k < n; ++k)
     if (!std::isfinite(planes[k])) return fail(DG2_E_ARG, "non-finite state value %zu", k);
-  const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
-  for (int k = 0; k < 9; ++k)
-    CU(cudaMemcpy2DAsync(c->d.S + k * c->d.plane, pb, planes + (size_t)k * c->d.nx * c->d.ny, w,
-                         w, c->d.ny, cudaMemcpyHostToDevice, c->st));
+  if (c->fp32) {
+    // FP64 depth modes -> FP32 free-surface modes eta = h + z
+    const int nx = c->f.nx, ny = c->f.ny;
+    std::vector<float> z0, z1x, z1y;
+    if ((r = f32_topo_modes(c, z0, z1x, z1y))) return r;
+    std::vector<float> buf(9 * (size_t)nx * ny);
+    const size_t m = (size_t)nx * ny;
+    for (size_t k = 0; k < m; ++k) {
+      buf[k] = (float)(planes[k] + (double)z0[k]);
+      buf[m + k] = (float)(planes[m + k] + (double)z1x[k]);
+      buf[2 * m + k] = (float)(planes[2 * m + k] + (double)z1y[k]);
+    }
+    for (size_t k = 3 * m; k < 9 * m; ++k) buf[k] = (float)planes[k];
+    for (int k = 0; k < 9; ++k)
+      CU(cudaMemcpy2DAsync(c->f.S + k * c->f.plane, c->f.pitch * sizeof(float), buf.data() + k * m,
+                           nx * sizeof(float), nx * sizeof(float), ny, cudaMemcpyHostToDevice,
+                           c->st));
+    CU(cudaStreamSynchronize(c->st));
+  } else {
+    const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
+    for (int k = 0; k < 9; ++k)
+      CU(cudaMemcpy2DAsync(c->d.S + k * c->d.plane, pb, planes + (size_t)k * c->d.nx * c->d.ny,
+                           w, w, c->d.ny, cudaMemcpyHostToDevice, c->st));
+  }
   Scalars s;
   if ((r = read_scalars(c, &s))) return r;
   s.t = t;
@@ -601,6 +748,17 @@ int dg2_get_topo(dg2_ctx* c, double* planes3) {
   int r = check_arg_ctx(c, false);
   if (r) return r;
   if (!planes3) return fail(DG2_E_ARG, "planes3 is null");
+  if (c->fp32) {
+    std::vector<float> z0, z1x, z1y;
+    if ((r = f32_topo_modes(c, z0, z1x, z1y))) return r;
+    const size_t n = z0.size();
+    for (size_t k = 0; k < n; ++k) {
+      planes3[k] = z0[k];
+      planes3[n + k] = z1x[k];
+      planes3[2 * n + k] = z1y[k];
+    }
+    return DG2_OK;
+  }
   const size_t w = (size_t)c->d.nx * sizeof(double), pb = (size_t)c->d.pitch * sizeof(double);
   for (int k = 0; k < 3; ++k)
     CU(cudaMemcpy2DAsync(planes3 + (size_t)k * c->d.nx * c->d.ny, w, c->d.Z + k * c->d.plane, pb,

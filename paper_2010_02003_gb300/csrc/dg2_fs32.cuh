@@ -1,0 +1,741 @@
+// dg2_fs32.cuh -- FP32 free-surface form of the DG2 step (sm_103a).
+//
+// The bulk update runs in FP32 on free-surface modes eta0, eta1x, eta1y
+// (eta = h + z) and the discharge modes; simulated time, the step size, the
+// Courant reduction, the mass ledger and every reduction stay in FP64.
+//
+// Momentum is written in deviation form.  With h* + z* = eta at every face
+// (the revision of Sec. 2.1.2 gives z* = z when h >= 0 and z* = z + h = eta
+// when h < 0), the pressure and bed terms of Eq. 4 regroup exactly:
+//   Eq. 4a:  dF/dx + 2g h0x z1x / dx  ==  dF_dev/dx + g h0x (eta_E - eta_W) / dx
+//   Eq. 4b:  (F_E + F_W) - (F(G+) + F(G-)) + (2g/3) h1x z1x
+//        ==  (F_E,dev + F_W,dev) - (F_dev(G+) + F_dev(G-)) + (2g/3) h1x eta1x_bar
+// where every *_dev flux is the flux minus the hydrostatic pressure g h^2 / 2
+// of the cell's own limit (of the Gauss point for F_dev(G)), and the HLL flux
+// is evaluated directly in that deviation form.  Topography is stored as face
+// values, so both sides of a face see the same z.  Still water (flat eta,
+// q = 0) then gives every term exactly zero in FP32: the lake at rest survives
+// rounding, including water held by high ground (clipped limits).
+#pragma once
+#include "dg2_device.cuh"
+
+namespace dg2 {
+namespace f32 {
+
+enum { E0 = 0, E1X, E1Y };  // free-surface modes occupy the h slots
+
+struct D32 {
+  int nx, ny, pitch;   // cell planes: ny rows of `pitch` floats
+  int zpx;             // x-face topography plane: ny rows of `zpx` floats (nx+1 used)
+  long long plane;     // ny * pitch
+  float dx, dy, inv_dx, inv_dy, g, tol, ds;
+  double dxd, dyd, cfl, dt_max;
+  int bc[4];
+  int n_in;
+  InflowDesc in[kMaxInflow];
+  const double* knot_t;
+  const double* knot_q;
+  double rain, rain_t0, rain_t1, qp;
+  long long src_idx;
+  float* S;            // 9 planes: eta0 eta1x eta1y qx0 qx1x qx1y qy0 qy1x qy1y
+  float* T;            // 9 planes: stage state
+  float* Q;            // 6 planes: limited slopes of Un (DG2-LL)
+  const float* ZX;     // z at x-faces: face i of row j at ZX[j * zpx + i], i = 0..nx
+  const float* ZY;     // z at y-faces: face j of column i at ZY[j * pitch + i], j = 0..ny
+  const float* N;      // Manning n
+  double* bpart;
+  double* mpart;
+  Scalars* sc;
+  int ngauge, max_samples;
+  const long long* g_idx;
+  const double* g_xi;
+  const double* g_eta;
+  double* samp_t;
+  double* samp_h;
+  int nblocks;
+};
+
+struct LimF {
+  float h, qx, qy, u, v;
+};
+
+// Face flux in deviation form: mass, normal momentum minus the LEFT side's
+// pressure, tangential momentum, and dP = g (hL^2 - hR^2) / 2 so that the
+// right-referenced normal momentum is fn + dP.
+struct FaceF {
+  float h, n, t, dp;
+};
+
+__device__ __forceinline__ LimF revise32(float h, float qx, float qy, float tol) {
+  LimF r;
+  if (h > tol) {
+    r.u = qx / h;
+    r.v = qy / h;
+  } else {
+    r.u = 0.f;
+    r.v = 0.f;
+  }
+  r.h = h > 0.f ? h : 0.f;
+  r.qx = r.h * r.u;
+  r.qy = r.h * r.v;
+  return r;
+}
+
+// HLL (same wave speeds as the FP64 path) returned relative to the left pressure.
+__device__ __forceinline__ FaceF hll_dev(float hL, float qnL, float qtL, float unL, float utL,
+                                         float hR, float qnR, float qtR, float unR, float utR,
+                                         float g, float tol) {
+  FaceF f;
+  const float hg = 0.5f * g;
+  f.dp = hg * (hL - hR) * (hL + hR);
+  if (hL <= tol && hR <= tol) {
+    f.h = 0.f; f.n = -hg * hL * hL; f.t = 0.f;
+    return f;
+  }
+  const float cL = sqrtf(g * hL), cR = sqrtf(g * hR);
+  float sL, sR;
+  if (hL <= tol) {
+    sL = unR - 2.f * cR;
+    sR = unR + cR;
+  } else if (hR <= tol) {
+    sL = unL - cL;
+    sR = unL + 2.f * cL;
+  } else {
+    const float us = 0.5f * (unL + unR) + cL - cR;
+    const float cs = 0.5f * (cL + cR) + 0.25f * (unL - unR);
+    sL = fminf(unL - cL, us - cs);
+    sR = fmaxf(unR + cR, us + cs);
+  }
+  const float fLh = hL * unL, fLn = hL * unL * unL, fLt = hL * unL * utL;
+  const float fRh = hR * unR, fRn = hR * unR * unR - f.dp, fRt = hR * unR * utR;
+  if (sL >= 0.f) {
+    f.h = fLh; f.n = fLn; f.t = fLt;
+    return f;
+  }
+  if (sR <= 0.f) {
+    f.h = fRh; f.n = fRn; f.t = fRt;
+    return f;
+  }
+  const float inv = 1.f / (sR - sL), sLR = sL * sR;
+  f.h = (sR * fLh - sL * fRh + sLR * (hR - hL)) * inv;
+  f.n = (sR * fLn - sL * fRn + sLR * (qnR - qnL)) * inv;
+  f.t = (sR * fLt - sL * fRt + sLR * (qtR - qtL)) * inv;
+  return f;
+}
+
+__device__ __forceinline__ FaceF flux_x32(const LimF& L, const LimF& R, float g, float tol) {
+  return hll_dev(L.h, L.qx, L.qy, L.u, L.v, R.h, R.qx, R.qy, R.u, R.v, g, tol);
+}
+__device__ __forceinline__ FaceF flux_y32(const LimF& S, const LimF& N, float g, float tol) {
+  return hll_dev(S.h, S.qy, S.qx, S.v, S.u, N.h, N.qy, N.qx, N.v, N.u, g, tol);
+}
+
+// Pressure-free physical flux of a Gauss point along x (h u, h u^2, h u v) or y.
+__device__ __forceinline__ void gauss_dev(float h, float qx, float qy, float tol, bool ydir,
+                                          float& fh, float& fx, float& fy) {
+  float u = 0.f, v = 0.f;
+  if (h > tol) {
+    u = qx / h;
+    v = qy / h;
+  }
+  if (!ydir) {
+    fh = h * u; fx = h * u * u; fy = h * u * v;
+  } else {
+    fh = h * v; fx = h * u * v; fy = h * v * v;
+  }
+}
+
+__device__ void ghost32(const D32& d, int edge, float s, double t, float& h, float& qx,
+                        float& qy) {
+  for (int k = 0; k < d.n_in; ++k) {
+    const InflowDesc& f = d.in[k];
+    if (f.edge != edge || s < f.s0 || s > f.s1) continue;
+    const double* tk = d.knot_t + f.koff;
+    const double* qk = d.knot_q + f.koff;
+    double Q = qk[f.nk - 1];
+    if (t <= tk[0]) {
+      Q = qk[0];
+    } else {
+      for (int k2 = 0; k2 + 1 < f.nk; ++k2)
+        if (t <= tk[k2 + 1]) {
+          Q = qk[k2] + (t - tk[k2]) / (tk[k2 + 1] - tk[k2]) * (qk[k2 + 1] - qk[k2]);
+          break;
+        }
+    }
+    const float qin = (float)(Q / f.width);
+    const float hin = h > 0.f ? h : 0.f;
+    const float hc = cbrtf(qin * qin / d.g);
+    const float hg = hin > hc ? hin : hc;
+    const float qn = (edge == 0 || edge == 2) ? qin : -qin;
+    h = hg;
+    if (edge <= 1) { qx = qn; qy = 0.f; } else { qx = 0.f; qy = qn; }
+    return;
+  }
+  if (d.bc[edge] == 1) {
+    if (edge == 0 && qx > 0.f) qx = 0.f;
+    if (edge == 1 && qx < 0.f) qx = 0.f;
+    if (edge == 2 && qy > 0.f) qy = 0.f;
+    if (edge == 3 && qy < 0.f) qy = 0.f;
+    return;
+  }
+  if (edge <= 1) qx = -qx; else qy = -qy;
+}
+
+__device__ __forceinline__ float minmod3f(float a, float b, float c) {
+  if (a > 0.f && b > 0.f && c > 0.f) return fminf(fminf(a, b), c);
+  if (a < 0.f && b < 0.f && c < 0.f) return fmaxf(fmaxf(a, b), c);
+  return 0.f;
+}
+
+__device__ __forceinline__ float limit_comp32(float thresh, float tol, float half, float k0w,
+                                              float k1w, float k0, float k1, float k0e,
+                                              float k1e) {
+  const float r3 = 0.57735026918962576f;  // 1 / sqrt(3)
+  const float jE = fabsf((k0e - k1e) - (k0 + k1));
+  const float jW = fabsf((k0 - k1) - (k0w + k1w));
+  float mag = fmaxf(fabsf(k0 - k1 * r3), fabsf(k0 + k1 * r3));
+  if (mag < tol) mag = tol;
+  if (!(fmaxf(jE, jW) > thresh * half * mag)) return k1;
+  return minmod3f(k1, k0e - k0, k0 - k0w);
+}
+
+__device__ __forceinline__ void cell_z(const D32& d, int i, int j, float& z0, float& z1x,
+                                       float& z1y, float& zE, float& zW, float& zN, float& zS) {
+  zW = d.ZX[(long long)j * d.zpx + i];
+  zE = d.ZX[(long long)j * d.zpx + i + 1];
+  zS = d.ZY[(long long)j * d.pitch + i];
+  zN = d.ZY[(long long)(j + 1) * d.pitch + i];
+  z0 = 0.5f * (zE + zW);
+  z1x = 0.5f * (zE - zW);
+  z1y = 0.5f * (zN - zS);
+}
+
+// Limited slopes (eta, qx, qy) along dir of cell (i, j): Eqs. 6-7 on the
+// free surface and the discharges (the free-surface form makes Sec. 2.1.3's
+// eta limiting direct).
+__device__ void limited_slopes32(const D32& d, const float* __restrict__ U, int i, int j, int dir,
+                                 float& se, float& sqx, float& sqy) {
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  se = U[dir * P + c];
+  sqx = U[(3 + dir) * P + c];
+  sqy = U[(6 + dir) * P + c];
+  const bool lo = dir == 1 ? i > 0 : j > 0;
+  const bool hi = dir == 1 ? i + 1 < d.nx : j + 1 < d.ny;
+  if (!lo || !hi) return;
+  const int il = dir == 1 ? i - 1 : i, jl = dir == 1 ? j : j - 1;
+  const int ih = dir == 1 ? i + 1 : i, jh = dir == 1 ? j : j + 1;
+  const long long cl = (long long)jl * d.pitch + il, ch = (long long)jh * d.pitch + ih;
+  float z0, z1x, z1y, zE, zW, zN, zS;
+  cell_z(d, il, jl, z0, z1x, z1y, zE, zW, zN, zS);
+  const float hl = U[cl] - z0;
+  cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
+  const float hc = U[c] - z0;
+  cell_z(d, ih, jh, z0, z1x, z1y, zE, zW, zN, zS);
+  const float hh = U[ch] - z0;
+  if (hl <= d.tol || hc <= d.tol || hh <= d.tol) return;
+  const float half = 0.5f * (dir == 1 ? d.dx : d.dy);
+  se = limit_comp32(d.ds, d.tol, half, U[cl], U[dir * P + cl], U[c], se, U[ch], U[dir * P + ch]);
+  {
+    const float* k0 = U + 3 * P;
+    const float* k1 = U + (3 + dir) * P;
+    sqx = limit_comp32(d.ds, d.tol, half, k0[cl], k1[cl], k0[c], k1[c], k0[ch], k1[ch]);
+  }
+  {
+    const float* k0 = U + 6 * P;
+    const float* k1 = U + (6 + dir) * P;
+    sqy = limit_comp32(d.ds, d.tol, half, k0[cl], k1[cl], k0[c], k1[c], k0[ch], k1[ch]);
+  }
+}
+
+// Wet-dry treatment in free-surface variables (same rule as the FP64 path):
+// a zeroed depth slope is eta1 = z1.
+__device__ __forceinline__ void wetdry32(float* m, float z0, float z1x, float z1y, float zE,
+                                         float zW, float zN, float zS, float tol) {
+  const float h0 = m[E0] - z0;
+  if (h0 <= tol) {
+    m[E1X] = z1x; m[E1Y] = z1y;
+#pragma unroll
+    for (int k = 3; k < 9; ++k) m[k] = 0.f;
+    return;
+  }
+  const float eta0 = m[E0];
+  {
+    const bool fe = ((m[E0] + m[E1X]) - zE <= tol) && !(zE > eta0);
+    const bool fw = ((m[E0] - m[E1X]) - zW <= tol) && !(zW > eta0);
+    if (fe || fw) { m[E1X] = z1x; m[QX1X] = 0.f; m[QY1X] = 0.f; }
+  }
+  {
+    const bool fn = ((m[E0] + m[E1Y]) - zN <= tol) && !(zN > eta0);
+    const bool fs = ((m[E0] - m[E1Y]) - zS <= tol) && !(zS > eta0);
+    if (fn || fs) { m[E1Y] = z1y; m[QX1Y] = 0.f; m[QY1Y] = 0.f; }
+  }
+}
+
+__device__ __forceinline__ double rate32(const D32& d, float h0, float qx0, float qy0) {
+  if (!(h0 > d.tol)) return 0.0;
+  const float u = qx0 / h0, v = qy0 / h0, c = sqrtf(d.g * h0);
+  return (double)fmaxf((fabsf(u) + c) * d.inv_dx, (fabsf(v) + c) * d.inv_dy);
+}
+
+__device__ void schedule32(const D32& d, Scalars* sc, double lam) {
+  double dt = d.dt_max;
+  if (lam > 0.0) {
+    dt = d.cfl / lam;
+    if (dt > d.dt_max) dt = d.dt_max;
+  }
+  sc->dt_cfl = dt;
+  sc->land = 0;
+  if (!sc->fixed_dt) {
+    double target = sc->t_end;
+    if (sc->next_sample <= target) target = sc->next_sample;
+    if (sc->t + dt >= target) {
+      dt = target - sc->t;
+      sc->land = 1;
+    }
+  }
+  sc->dt = dt;
+  sc->lam_bits = 0ull;
+}
+
+// Initial modes from FP64 corner data: face-average topography (rounded to
+// FP32 once), free-surface modes by Eq. 3, dry cells with eta modes equal to
+// the FP32 topography modes (zero depth exactly).
+__global__ void init32_kernel(D32 d, const double* __restrict__ zc, const double* __restrict__ ec,
+                              const double* __restrict__ man, double n_uniform, float* ZXw,
+                              float* ZYw, float* Nw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int W = d.nx + 1;
+  // face topography: x-face (i, j) for i <= nx, y-face (i, j) for j <= ny
+  if (i <= d.nx && j < d.ny)
+    ZXw[(long long)j * d.zpx + i] = (float)(0.5 * (zc[(long long)j * W + i] + zc[(long long)(j + 1) * W + i]));
+  if (i < d.nx && j <= d.ny)
+    ZYw[(long long)j * d.pitch + i] = (float)(0.5 * (zc[(long long)j * W + i] + zc[(long long)j * W + i + 1]));
+  if (i >= d.nx || j >= d.ny) return;
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  const double* r0 = zc + (long long)j * W;
+  const double* r1 = zc + (long long)(j + 1) * W;
+  // FP32 topography modes exactly as the stage kernels will form them
+  const float zW = (float)(0.5 * (r0[i] + r1[i])), zE = (float)(0.5 * (r0[i + 1] + r1[i + 1]));
+  const float zS = (float)(0.5 * (r0[i] + r0[i + 1])), zN = (float)(0.5 * (r1[i] + r1[i + 1]));
+  const float z0 = 0.5f * (zE + zW), z1x = 0.5f * (zE - zW), z1y = 0.5f * (zN - zS);
+  float e0 = z0, e1x = z1x, e1y = z1y;
+  if (ec) {
+    const double* e0r = ec + (long long)j * W;
+    const double* e1r = ec + (long long)(j + 1) * W;
+    // depth modes decide wetness exactly as in FP64 (Eq. 3 on eta - z)
+    const double a = e0r[i] - r0[i], b = e0r[i + 1] - r0[i + 1];
+    const double cc = e1r[i] - r1[i], dd = e1r[i + 1] - r1[i + 1];
+    const double h0 = 0.5 * (0.5 * (b + dd) + 0.5 * (a + cc));
+    if (h0 > 0.0) {
+      const double fE = 0.5 * (e0r[i + 1] + e1r[i + 1]), fW = 0.5 * (e0r[i] + e1r[i]);
+      const double fN = 0.5 * (e1r[i] + e1r[i + 1]), fS = 0.5 * (e0r[i] + e0r[i + 1]);
+      e0 = (float)(0.5 * (fE + fW));
+      e1x = (float)(0.5 * (fE - fW));
+      e1y = (float)(0.5 * (fN - fS));
+    }
+  }
+  float* S = d.S;
+  S[E0 * P + c] = e0;
+  S[E1X * P + c] = e1x;
+  S[E1Y * P + c] = e1y;
+#pragma unroll
+  for (int k = 3; k < 9; ++k) S[k * P + c] = 0.f;
+  Nw[c] = (float)(man ? man[(long long)j * d.nx + i] : n_uniform);
+}
+
+__device__ __forceinline__ void friction_point32(float gn2dt, float tol, float h, float& qx,
+                                                 float& qy) {
+  if (!(h > tol)) return;
+  const float qm = sqrtf(qx * qx + qy * qy);
+  const float den = 1.f + gn2dt * qm / (h * h * cbrtf(h));
+  qx = qx / den;
+  qy = qy / den;
+}
+
+__global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
+  const Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= d.nx || j >= d.ny) return;
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  const float n = d.N[c];
+  if (n == 0.f) return;
+  float* S = d.S;
+  float z0, z1x, z1y, zE, zW, zN, zS;
+  cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
+  const float h0 = S[E0 * P + c] - z0;
+  if (!(h0 > d.tol)) {
+    // a dry average can still have wet Gauss points only through slopes, which
+    // the wet-dry treatment has zeroed; nothing to do
+    bool any = false;
+    for (int dd = 1; dd <= 2 && !any; ++dd) {
+      const float h1 = S[dd * P + c] - (dd == 1 ? z1x : z1y);
+      any = fabsf(h1) * 0.57735026918962576f + h0 > d.tol;
+    }
+    if (!any) return;
+  }
+  const float gn2dt = (float)(sc->dt * (double)d.g) * n * n;
+  const float x0 = S[QX0 * P + c], y0 = S[QY0 * P + c];
+  float cx = x0, cy = y0;
+  friction_point32(gn2dt, d.tol, h0, cx, cy);
+  const float r3 = 0.57735026918962576f, hs3 = 0.86602540378443865f;
+  float nq[2][2];
+#pragma unroll
+  for (int dd = 1; dd <= 2; ++dd) {
+    const float h1 = S[dd * P + c] - (dd == 1 ? z1x : z1y);
+    const float x1 = S[(3 + dd) * P + c], y1 = S[(6 + dd) * P + c];
+    float xp = x0 + x1 * r3, yp = y0 + y1 * r3, xm = x0 - x1 * r3, ym = y0 - y1 * r3;
+    friction_point32(gn2dt, d.tol, h0 + h1 * r3, xp, yp);
+    friction_point32(gn2dt, d.tol, h0 - h1 * r3, xm, ym);
+    nq[dd - 1][0] = hs3 * (xp - xm);
+    nq[dd - 1][1] = hs3 * (yp - ym);
+  }
+  S[QX0 * P + c] = cx;
+  S[QY0 * P + c] = cy;
+  S[QX1X * P + c] = nq[0][0];
+  S[QY1X * P + c] = nq[0][1];
+  S[QX1Y * P + c] = nq[1][0];
+  S[QY1Y * P + c] = nq[1][1];
+}
+
+struct StageSmem32 {
+  LimF e[TY][TX];
+  LimF n[TY][TX];
+  LimF hw[TY], he[TY], hs[TX], hn[TX];
+  FaceF fx[TY][TX + 1];
+  FaceF fy[TY + 1][TX];
+  double red[32];
+};
+
+template <bool LL, int STAGE>
+__global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
+  __shared__ StageSmem32 sm;
+  Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * TX + tx, j = blockIdx.y * TY + ty;
+  const bool act = i < d.nx && j < d.ny;
+  const long long P = d.plane;
+  const long long c = (long long)j * d.pitch + i;
+  const double dtd = sc->dt;
+  const float dt = (float)dtd;
+  const double ts = STAGE == 1 ? sc->t : sc->t + dtd;
+  const float* __restrict__ In = STAGE == 1 ? d.S : d.T;
+  const float g = d.g, tol = d.tol;
+  const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
+  const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
+
+  float m[9];
+  float z0 = 0.f, z1x = 0.f, z1y = 0.f, zE = 0.f, zW = 0.f, zN = 0.f, zS = 0.f;
+  LimF Es, Ws, Ns, Ss;
+  float etaE = 0.f, etaW = 0.f, etaN = 0.f, etaS = 0.f;
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = In[k * P + c];
+    if (LL) {
+      limited_slopes32(d, In, i, j, 1, m[E1X], m[QX1X], m[QY1X]);
+      limited_slopes32(d, In, i, j, 2, m[E1Y], m[QX1Y], m[QY1Y]);
+    }
+    cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
+    etaE = m[E0] + m[E1X]; etaW = m[E0] - m[E1X];
+    etaN = m[E0] + m[E1Y]; etaS = m[E0] - m[E1Y];
+    const float eh = etaE - zE, wh = etaW - zW, nh = etaN - zN, shh = etaS - zS;
+    const float eqx = m[QX0] + m[QX1X], eqy = m[QY0] + m[QY1X];
+    const float wqx = m[QX0] - m[QX1X], wqy = m[QY0] - m[QY1X];
+    const float nqx = m[QX0] + m[QX1Y], nqy = m[QY0] + m[QY1Y];
+    const float sqx = m[QX0] - m[QX1Y], sqy = m[QY0] - m[QY1Y];
+    Es = revise32(eh, eqx, eqy, tol);
+    Ws = revise32(wh, wqx, wqy, tol);
+    Ns = revise32(nh, nqx, nqy, tol);
+    Ss = revise32(shh, sqx, sqy, tol);
+    sm.e[ty][tx] = Es;
+    sm.n[ty][tx] = Ns;
+    if (tx == 0) {
+      float h, qx, qy;
+      if (i == 0) {
+        h = wh; qx = wqx; qy = wqy;
+        ghost32(d, 0, (j + 0.5f) * d.dy, ts, h, qx, qy);
+      } else {
+        const long long cw = c - 1;
+        float se = In[E1X * P + cw], s1x = In[QX1X * P + cw], s1y = In[QY1X * P + cw];
+        if (LL) limited_slopes32(d, In, i - 1, j, 1, se, s1x, s1y);
+        h = (In[E0 * P + cw] + se) - zW;   // the west cell's east face is our west face
+        qx = In[QX0 * P + cw] + s1x; qy = In[QY0 * P + cw] + s1y;
+      }
+      sm.hw[ty] = revise32(h, qx, qy, tol);
+    }
+    if (east_edge) {
+      float h, qx, qy;
+      if (i == d.nx - 1) {
+        h = eh; qx = eqx; qy = eqy;
+        ghost32(d, 1, (j + 0.5f) * d.dy, ts, h, qx, qy);
+      } else {
+        const long long ce = c + 1;
+        float se = In[E1X * P + ce], s1x = In[QX1X * P + ce], s1y = In[QY1X * P + ce];
+        if (LL) limited_slopes32(d, In, i + 1, j, 1, se, s1x, s1y);
+        h = (In[E0 * P + ce] - se) - zE;
+        qx = In[QX0 * P + ce] - s1x; qy = In[QY0 * P + ce] - s1y;
+      }
+      sm.he[ty] = revise32(h, qx, qy, tol);
+    }
+    if (ty == 0) {
+      float h, qx, qy;
+      if (j == 0) {
+        h = shh; qx = sqx; qy = sqy;
+        ghost32(d, 2, (i + 0.5f) * d.dx, ts, h, qx, qy);
+      } else {
+        const long long cs = c - d.pitch;
+        float se = In[E1Y * P + cs], s1x = In[QX1Y * P + cs], s1y = In[QY1Y * P + cs];
+        if (LL) limited_slopes32(d, In, i, j - 1, 2, se, s1x, s1y);
+        h = (In[E0 * P + cs] + se) - zS;
+        qx = In[QX0 * P + cs] + s1x; qy = In[QY0 * P + cs] + s1y;
+      }
+      sm.hs[tx] = revise32(h, qx, qy, tol);
+    }
+    if (north_edge) {
+      float h, qx, qy;
+      if (j == d.ny - 1) {
+        h = nh; qx = nqx; qy = nqy;
+        ghost32(d, 3, (i + 0.5f) * d.dx, ts, h, qx, qy);
+      } else {
+        const long long cn = c + d.pitch;
+        float se = In[E1Y * P + cn], s1x = In[QX1Y * P + cn], s1y = In[QY1Y * P + cn];
+        if (LL) limited_slopes32(d, In, i, j + 1, 2, se, s1x, s1y);
+        h = (In[E0 * P + cn] - se) - zN;
+        qx = In[QX0 * P + cn] - s1x; qy = In[QY0 * P + cn] - s1y;
+      }
+      sm.hn[tx] = revise32(h, qx, qy, tol);
+    }
+  }
+  __syncthreads();
+
+  double brate = 0.0;
+  if (act) {
+    const LimF& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
+    const FaceF fw = flux_x32(Lw, Ws, g, tol);
+    sm.fx[ty][tx] = fw;
+    if (i == 0) brate += (double)fw.h * d.dyd;
+    if (east_edge) {
+      const FaceF fe = flux_x32(Es, sm.he[ty], g, tol);
+      sm.fx[ty][tx + 1] = fe;
+      if (i == d.nx - 1) brate -= (double)fe.h * d.dyd;
+    }
+    const LimF& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
+    const FaceF fs = flux_y32(Ls, Ss, g, tol);
+    sm.fy[ty][tx] = fs;
+    if (j == 0) brate += (double)fs.h * d.dxd;
+    if (north_edge) {
+      const FaceF fn = flux_y32(Ns, sm.hn[tx], g, tol);
+      sm.fy[ty + 1][tx] = fn;
+      if (j == d.ny - 1) brate -= (double)fn.h * d.dxd;
+    }
+  }
+  __syncthreads();
+
+  double lam = 0.0;
+  bool bad = false;
+  if (act) {
+    // own faces: east / north faces are referenced to our (left / south) pressure,
+    // west / south faces to the neighbour's, so add dP to get ours
+    const FaceF fE = sm.fx[ty][tx + 1], fW = sm.fx[ty][tx];
+    const FaceF gN = sm.fy[ty + 1][tx], gS = sm.fy[ty][tx];
+    const float FEh = fE.h, FEx = fE.n, FEy = fE.t;
+    const float FWh = fW.h, FWx = fW.n + fW.dp, FWy = fW.t;
+    const float GNh = gN.h, GNx = gN.t, GNy = gN.n;
+    const float GSh = gS.h, GSx = gS.t, GSy = gS.n + gS.dp;
+    const float h0x = 0.5f * (Es.h + Ws.h), x0x = 0.5f * (Es.qx + Ws.qx), y0x = 0.5f * (Es.qy + Ws.qy);
+    const float h1x_ = 0.5f * (Es.h - Ws.h), x1x = 0.5f * (Es.qx - Ws.qx), y1x = 0.5f * (Es.qy - Ws.qy);
+    const float h0y = 0.5f * (Ns.h + Ss.h), x0y = 0.5f * (Ns.qx + Ss.qx), y0y = 0.5f * (Ns.qy + Ss.qy);
+    const float h1y_ = 0.5f * (Ns.h - Ss.h), x1y = 0.5f * (Ns.qx - Ss.qx), y1y = 0.5f * (Ns.qy - Ss.qy);
+    const float r3 = 0.57735026918962576f;
+    float Fph, Fpx, Fpy, Fmh, Fmx, Fmy, Gph, Gpx, Gpy, Gmh, Gmx, Gmy;
+    gauss_dev(h0x + h1x_ * r3, x0x + x1x * r3, y0x + y1x * r3, tol, false, Fph, Fpx, Fpy);
+    gauss_dev(h0x - h1x_ * r3, x0x - x1x * r3, y0x - y1x * r3, tol, false, Fmh, Fmx, Fmy);
+    gauss_dev(h0y + h1y_ * r3, x0y + x1y * r3, y0y + y1y * r3, tol, true, Gph, Gpx, Gpy);
+    gauss_dev(h0y - h1y_ * r3, x0y - x1y * r3, y0y - y1y * r3, tol, true, Gmh, Gmx, Gmy);
+    const float idx = d.inv_dx, idy = d.inv_dy;
+    const float dEx = etaE - etaW, dEy = etaN - etaS;
+    float L[9];
+    L[E0] = -(FEh - FWh) * idx - (GNh - GSh) * idy;
+    L[QX0] = -(FEx - FWx) * idx - (GNx - GSx) * idy - g * h0x * dEx * idx;
+    L[QY0] = -(FEy - FWy) * idx - (GNy - GSy) * idy - g * h0y * dEy * idy;
+    if (d.rain != 0.0 && ts >= d.rain_t0 && ts < d.rain_t1) L[E0] += (float)d.rain;
+    if (c == d.src_idx) L[E0] += (float)(d.qp / (d.dxd * d.dyd));
+    const float k3x = -3.f * idx, k3y = -3.f * idy, g23 = 2.f * g / 3.f;
+    L[E1X] = k3x * ((FEh + FWh) - (Fph + Fmh));
+    L[QX1X] = k3x * ((FEx + FWx) - (Fpx + Fmx) + g23 * h1x_ * (0.5f * dEx));
+    L[QY1X] = k3x * ((FEy + FWy) - (Fpy + Fmy));
+    L[E1Y] = k3y * ((GNh + GSh) - (Gph + Gmh));
+    L[QX1Y] = k3y * ((GNx + GSx) - (Gpx + Gmx));
+    L[QY1Y] = k3y * ((GNy + GSy) - (Gpy + Gmy) + g23 * h1y_ * (0.5f * dEy));
+
+    float out[9];
+    if (STAGE == 1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[k] = m[k] + dt * L[k];
+      wetdry32(out, z0, z1x, z1y, zE, zW, zN, zS, tol);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) d.T[k * P + c] = out[k];
+      if (LL) {
+        d.Q[0 * P + c] = m[E1X]; d.Q[1 * P + c] = m[E1Y];
+        d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
+        d.Q[4 * P + c] = m[QY1X]; d.Q[5 * P + c] = m[QY1Y];
+      }
+    } else {
+      float un[9];
+      un[E0] = d.S[E0 * P + c]; un[QX0] = d.S[QX0 * P + c]; un[QY0] = d.S[QY0 * P + c];
+      if (LL) {
+        un[E1X] = d.Q[0 * P + c]; un[E1Y] = d.Q[1 * P + c];
+        un[QX1X] = d.Q[2 * P + c]; un[QX1Y] = d.Q[3 * P + c];
+        un[QY1X] = d.Q[4 * P + c]; un[QY1Y] = d.Q[5 * P + c];
+      } else {
+        un[E1X] = d.S[E1X * P + c]; un[E1Y] = d.S[E1Y * P + c];
+        un[QX1X] = d.S[QX1X * P + c]; un[QX1Y] = d.S[QX1Y * P + c];
+        un[QY1X] = d.S[QY1X * P + c]; un[QY1Y] = d.S[QY1Y * P + c];
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[k] = 0.5f * (un[k] + m[k] + dt * L[k]);
+      wetdry32(out, z0, z1x, z1y, zE, zW, zN, zS, tol);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
+      lam = rate32(d, out[E0] - z0, out[QX0], out[QY0]);
+      bad = !(isfinite(out[E0]) && isfinite(out[QX0]) && isfinite(out[QY0]));
+    }
+  }
+
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const double bsum = block_sum<TX * TY>(brate, sm.red);
+  if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
+  if (STAGE == 1) return;
+
+  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+  const double bl = block_max<TX * TY>(lam, sm.red);
+  __shared__ bool last;
+  if (tx == 0 && ty == 0) {
+    if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
+    __threadfence();
+    const unsigned int k = atomicAdd(&sc->count, 1u);
+    last = (k == (unsigned int)d.nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int tid = ty * TX + tx;
+  double part = 0.0;
+  for (int k = tid; k < d.nblocks; k += TX * TY)
+    part += __ldcg(&d.bpart[k]) + __ldcg(&d.bpart[d.nblocks + k]);
+  const double btot = block_sum<TX * TY>(part, sm.red);
+  if (tid == 0) {
+    const double t = sc->t;
+    double src1 = 0.0, src2 = 0.0;
+    const double area = d.dxd * d.dyd * (double)d.nx * (double)d.ny;
+    if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
+    if (d.rain != 0.0 && t + dtd >= d.rain_t0 && t + dtd < d.rain_t1) src2 += d.rain * area;
+    if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
+    sc->ledger += dtd * 0.5 * (btot + src1 + src2);
+    double tn;
+    bool at_sample = false;
+    if (sc->land && !sc->fixed_dt) {
+      double target = sc->t_end;
+      if (sc->next_sample <= target) { target = sc->next_sample; at_sample = true; }
+      tn = target;
+    } else {
+      tn = t + dtd;
+    }
+    sc->t = tn;
+    if (at_sample) {
+      const int r = sc->nsamp;
+      if (r < d.max_samples) {
+        d.samp_t[r] = tn;
+        for (int k = 0; k < d.ngauge; ++k) {
+          const long long gc = d.g_idx[k];
+          const int gi = (int)(gc % d.pitch), gj = (int)(gc / d.pitch);
+          float gz0, gz1x, gz1y, a, b, e, f;
+          cell_z(d, gi, gj, gz0, gz1x, gz1y, a, b, e, f);
+          const double h = (double)(__ldcg(&d.S[gc]) - gz0) +
+                           d.g_xi[k] * (double)(__ldcg(&d.S[P + gc]) - gz1x) +
+                           d.g_eta[k] * (double)(__ldcg(&d.S[2 * P + gc]) - gz1y);
+          d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
+        }
+      }
+      sc->nsamp = r + 1;
+      sc->next_sample += sc->sample_every;
+    }
+    if (!(dtd > 0.0) || !isfinite(tn)) sc->nonfinite = 1;
+    sc->steps += 1;
+    sc->last_dt = dtd;
+    schedule32(d, sc, __longlong_as_double((long long)atomicAdd(&sc->lam_bits, 0ull)));
+    if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
+    sc->count = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(256) rate32_kernel(D32 d) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double lam = 0.0;
+  if (i < d.nx && j < d.ny) {
+    const long long P = d.plane, c = (long long)j * d.pitch + i;
+    float z0, z1x, z1y, zE, zW, zN, zS;
+    cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
+    lam = rate32(d, d.S[c] - z0, d.S[QX0 * P + c], d.S[QY0 * P + c]);
+  }
+  const double bl = block_max<256>(lam, red);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  Scalars* sc = d.sc;
+  if (tid == 0) {
+    if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
+    __threadfence();
+    last = atomicAdd(&sc->count, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (last && tid == 0) {
+    __threadfence();
+    schedule32(d, sc, __longlong_as_double((long long)atomicAdd(&sc->lam_bits, 0ull)));
+    sc->count = 0u;
+  }
+}
+
+// Mass sum(eta0 - z0) dx dy, accumulated in FP64 in a fixed order.
+__global__ void __launch_bounds__(256) mass32_kernel(D32 d) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double v = 0.0;
+  if (i < d.nx && j < d.ny) {
+    float z0, z1x, z1y, zE, zW, zN, zS;
+    cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
+    v = (double)d.S[(long long)j * d.pitch + i] - (double)z0;
+  }
+  const double s = block_sum<256>(v, red);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nb = gridDim.x * gridDim.y;
+  Scalars* sc = d.sc;
+  if (tid == 0) {
+    d.mpart[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(&sc->count, 1u) == (unsigned int)nb - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double part = 0.0;
+  for (int k = tid; k < nb; k += 256) part += __ldcg(&d.mpart[k]);
+  const double tot = block_sum<256>(part, red);
+  if (tid == 0) {
+    sc->mass = tot * d.dxd * d.dyd;
+    if (sc->ledger_init) {
+      sc->ledger = sc->mass;
+      sc->ledger_init = 0;
+    }
+    sc->count = 0u;
+  }
+}
+
+}  // namespace f32
+}  // namespace dg2
