@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="", help="comma-separated variant keys (profiling)")
     return ap.parse_args()
 
 
@@ -239,6 +240,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+VARIANTS = [
+    # key, workload, variant, precision
+    ("fp64_ll", "floodplain", 1, 0),
+    ("fp64_nl", "floodplain", 0, 0),
+    ("fp32_ll", "floodplain", 1, 1),
+    ("fp32_nl", "floodplain", 0, 1),
+    ("fp64_nl_flooded", "flooded", 0, 0),
+    ("fp32_nl_flooded", "flooded", 0, 1),
+    ("fp32_ll_flooded", "flooded", 1, 1),
+]
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
@@ -246,43 +259,45 @@ def main():
         run_reference(args, rank, world)
         return
     import torch
-    from paper_2010_02003_gb300 import binding as B, build as build_mod
+    from paper_2010_02003_gb300 import binding as B, build as build_mod, inputs
     if not os.path.exists(B.LIB_PATH):
         build_mod.build()
     torch.cuda.set_device(local)
-    case = workload()
-    cells = case.nx * case.ny
+    cases = {"floodplain": workload(), "flooded": inputs.flooded_plain(NX, NY, DX)}
+    cells = NX * NY
     warmup = max(3, args.warmup)
-
-    # headline: DG2-LL (every row of the step, limiter included); DG2-NL beside it
-    barrier(world)
-    clk = ClockSampler(local)
-    clk.start()
-    ll = time_variant(B, torch, case, B.DG2_LL, args.steps, warmup)
-    clocks = clk.stop()
-    ms_ll = max_over_ranks(ll["ms"], world)
-    barrier(world)
-    nl = time_variant(B, torch, case, B.DG2_NL, args.steps, warmup)
-    ms_nl = max_over_ranks(nl["ms"], world)
-    value = world * cells * args.steps / (ms_ll * 1e-3)
-    value_nl = world * cells * args.steps / (ms_nl * 1e-3)
-
-    # FP32 free-surface path, both variants
-    barrier(world)
-    f_ll = time_variant(B, torch, case, B.DG2_LL, args.steps, warmup, precision=B.DG2_FP32)
-    f_nl = time_variant(B, torch, case, B.DG2_NL, args.steps, warmup, precision=B.DG2_FP32)
-    ms_fll = max_over_ranks(f_ll["ms"], world)
-    ms_fnl = max_over_ranks(f_nl["ms"], world)
-
-    # roofline of the dominant kernel of each run, live event timing
     pk, pk_src = peaks()
-    roofline = kernel_roofline(ll, "fp64", "ll", cells, pk["hbm_gbs"], pk_src)
+    only = set(args.only.split(",")) if args.only else None
 
-    # end to end through the C ABI with host buffers
-    e2e_s, h2d, d2h = e2e_run(B, torch, case, B.DG2_LL, args.steps)
-    e2e = {"value": world * cells * args.steps / max_over_ranks(e2e_s, world),
-           "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / args.steps,
-           "d2h_bytes_per_step": d2h / args.steps}
+    results = {}
+    clocks = None
+    for key, wl, var, prec in VARIANTS:
+        if only and key not in only:
+            continue
+        barrier(world)
+        clk = ClockSampler(local) if key == "fp64_ll" else None
+        if clk:
+            clk.start()
+        run = time_variant(B, torch, cases[wl], var, args.steps, warmup, precision=prec)
+        if clk:
+            clocks = clk.stop()
+        ms = max_over_ranks(run["ms"], world)
+        run["value"] = world * cells * args.steps / (ms * 1e-3)
+        run["ms_max"] = ms
+        run["roofline"] = kernel_roofline(run, "fp32" if prec else "fp64", "ll" if var else "nl",
+                                          cells, pk["hbm_gbs"], pk_src)
+        run.pop("solver").close()
+        results[key] = run
+        torch.cuda.empty_cache()
+
+    head = "fp64_ll" if "fp64_ll" in results else next(iter(results))
+    hd = results[head]
+    e2e = None
+    if not only or "fp64_ll" in only:
+        e2e_s, h2d, d2h = e2e_run(B, torch, cases["floodplain"], B.DG2_LL, args.steps)
+        e2e = {"value": world * cells * args.steps / max_over_ranks(e2e_s, world),
+               "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -290,26 +305,21 @@ def main():
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} DG2-LL steps of a 500x250 floodplain (same recipe), {el:.1f} s"}
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-                "steps": args.steps, "warmup": warmup, "ms_per_step": ms_ll / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": "floodplain 2000x1000 dx=2 m, DG2-LL, FP64",
-                           "variant": "DG2-LL", "cells": cells,
-                           "wet_fraction": ll["wet_fraction"],
-                           "l2": "inputs larger than L2 (state 2 x 144 MB)",
+        variants = {k: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
+                        "wet_fraction": r["wet_fraction"], "roofline": r["roofline"]}
+                    for k, r in results.items() if k != head}
+        line = {"metric": METRIC, "value": hd["value"], "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": warmup, "ms_per_step": hd["ms_max"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if head.startswith("fp64") else "f32", "data": "synthetic",
+                "config": {"workload": "floodplain 2000x1000 dx=2 m, DG2-LL, FP64"
+                           if head == "fp64_ll" else head,
+                           "variant": head, "cells": cells,
+                           "wet_fraction": hd["wet_fraction"],
+                           "l2": "inputs larger than L2 (state 2 x 145 MB)",
                            "parallelism": f"replicas x{world}"},
-                "variants": {
-                    "fp64_nl": {"value": value_nl, "ms_per_step": ms_nl / args.steps,
-                                "roofline": kernel_roofline(nl, "fp64", "nl", cells, pk["hbm_gbs"], pk_src)},
-                    "fp32_ll": {"value": world * cells * args.steps / (ms_fll * 1e-3),
-                                "ms_per_step": ms_fll / args.steps,
-                                "roofline": kernel_roofline(f_ll, "fp32", "ll", cells, pk["hbm_gbs"], pk_src)},
-                    "fp32_nl": {"value": world * cells * args.steps / (ms_fnl * 1e-3),
-                                "ms_per_step": ms_fnl / args.steps,
-                                "roofline": kernel_roofline(f_nl, "fp32", "nl", cells, pk["hbm_gbs"], pk_src)},
-                },
-                "gpu_launches": int(ll["launches"]), "roofline": roofline, "e2e": e2e,
+                "variants": variants,
+                "gpu_launches": int(hd["launches"]), "roofline": hd["roofline"], "e2e": e2e,
                 "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line))
     if world > 1:

@@ -70,6 +70,10 @@ typedef struct dg2_params {
     int bc[4];          /* DG2_WALL or DG2_OPEN per edge, indexed by DG2_WEST..NORTH */
     int max_gauges;     /* capacity of the gauge table (default 64)                  */
     int max_samples;    /* capacity of the gauge sample buffer in rows (default 4096)*/
+    int skip_dry_tiles; /* 1 (default): leave 32 x 8 tiles of still, dry cells with
+                           still, dry neighbours untouched -- they are exact fixed
+                           points of a step, so results are bit-identical; 0: compute
+                           every tile */
 } dg2_params;
 
 typedef struct dg2_ctx dg2_ctx;

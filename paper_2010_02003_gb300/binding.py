@@ -39,7 +39,8 @@ class Dg2Params(ctypes.Structure):
     _fields_ = [("g", ctypes.c_double), ("cfl", ctypes.c_double), ("tol_dry", ctypes.c_double),
                 ("ds_thresh", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("variant", ctypes.c_int), ("precision", ctypes.c_int), ("bc", ctypes.c_int * 4),
-                ("max_gauges", ctypes.c_int), ("max_samples", ctypes.c_int)]
+                ("max_gauges", ctypes.c_int), ("max_samples", ctypes.c_int),
+                ("skip_dry_tiles", ctypes.c_int)]
 
 
 class Dg2Error(RuntimeError):
@@ -236,7 +237,7 @@ class Solver:
     def __init__(self, nx, ny, dx, dy=None, *, variant=DG2_NL, precision=DG2_FP64, cfl=0.3,
                  tol_dry=1e-5, ds_thresh=10.0, dt_max=1.0, g=9.80665,
                  bc: Sequence[int] = (DG2_WALL,) * 4, max_gauges=64, max_samples=4096,
-                 stream=None, device=None):
+                 skip_dry_tiles=True, stream=None, device=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the DG2 solver needs a CUDA device")
@@ -249,6 +250,7 @@ class Solver:
         for k in range(4):
             p.bc[k] = int(bc[k])
         p.max_gauges, p.max_samples = int(max_gauges), int(max_samples)
+        p.skip_dry_tiles = int(bool(skip_dry_tiles))
         self.params = p
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         nbytes = dg2_workspace_bytes(self.nx, self.ny, p)

@@ -53,7 +53,7 @@ struct Layout {
   int pitch, zpx;
   long long plane;
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
-  size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, total;
+  size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, total;
   int nblocks, mblocks;
 };
 
@@ -95,6 +95,8 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   L.off_st = take((size_t)p.max_samples * sizeof(double));
   L.off_sh = take((size_t)p.max_samples * ng * sizeof(double));
   L.off_sc = take(sizeof(Scalars));
+  L.off_tflag = take((size_t)L.nblocks);
+  L.off_tact = take((size_t)L.nblocks);
   L.total = o;
   return true;
 }
@@ -218,6 +220,13 @@ void launch_mass(dg2_ctx* c) {
   else dg2::mass_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->d);
 }
 
+// Marks every tile non-quiescent so the next step computes the whole grid
+// (after a new DEM or state; the first stage 2 then sets the true flags).
+int reset_tiles(dg2_ctx* c) {
+  CU(cudaMemsetAsync(c->d.tiles.flag, 1, (size_t)c->lay.nblocks, c->st));
+  return DG2_OK;
+}
+
 int reset_ledger(dg2_ctx* c) {
   // mass kernel with the ledger-reset flag set by a one-field copy
   const int one = 1;
@@ -272,6 +281,7 @@ void dg2_default_params(dg2_params* p) {
   for (int k = 0; k < 4; ++k) p->bc[k] = DG2_WALL;
   p->max_gauges = 64;
   p->max_samples = 4096;
+  p->skip_dry_tiles = 1;
 }
 
 const char* dg2_last_error(void) { return g_err.c_str(); }
@@ -347,6 +357,9 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.max_samples = p.max_samples;
   d.src_idx = -1;
   d.nblocks = L.nblocks;
+  d.tiles.flag = (unsigned char*)(c->ws + L.off_tflag);
+  d.tiles.act = (unsigned char*)(c->ws + L.off_tact);
+  d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
   {
     D32& f = c->f;
     memset(&f, 0, sizeof f);
@@ -369,6 +382,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     f.samp_t = d.samp_t; f.samp_h = d.samp_h;
     f.nblocks = L.nblocks;
     f.src_idx = -1;
+    f.tiles = d.tiles;
   }
   c->sblock = dim3(dg2::TX, dg2::TY);
   c->sgrid = dim3((nx + dg2::TX - 1) / dg2::TX, (ny + dg2::TY - 1) / dg2::TY);
@@ -447,6 +461,7 @@ int dg2_set_dem(dg2_ctx* c, const double* z_corner, const double* manning, doubl
   CU(cudaMemcpyAsync(c->d.sc, &s0, sizeof s0, cudaMemcpyHostToDevice, c->st));
   CU(cudaStreamSynchronize(c->st));
   c->dem_set = 1;
+  if ((r = reset_tiles(c))) return r;
   if ((r = reset_ledger(c))) return r;
   if ((r = recompute_dt(c))) return r;
   CU(cudaStreamSynchronize(c->st));
@@ -738,6 +753,7 @@ int dg2_set_state(dg2_ctx* c, const double* planes, double t) {
                                        : INFINITY;
   CU(cudaMemcpyAsync(c->d.sc, &s, sizeof s, cudaMemcpyHostToDevice, c->st));
   c->dem_set = 1;
+  if ((r = reset_tiles(c))) return r;
   if ((r = reset_ledger(c))) return r;
   if ((r = recompute_dt(c))) return r;
   CU(cudaStreamSynchronize(c->st));

@@ -62,6 +62,23 @@ struct Scalars {
   double last_dt;      // size of the last completed step
 };
 
+// Exact skipping of quiescent dry tiles.  A cell is quiescent when its depth
+// average is at or below tol_dry and every other mode is zero (FP64 form) or
+// its free-surface slopes equal the topography slopes and its discharges are
+// zero (FP32 form) -- the state the wet-dry treatment leaves in dry cells.  A
+// quiescent cell whose neighbours are quiescent is a fixed point of a stage:
+// every face between dry limits carries zero flux, the depth modes do not
+// change and the treatment re-zeroes the discharges.  Water moves at most one
+// cell per stage (Courant number < 1), two per step, fewer than a 32 x 8 tile,
+// so a tile whose 3 x 3 tile neighbourhood holds no non-quiescent or forced
+// (inflow, point source, rain) tile is left untouched, bit for bit as if it
+// had been computed.
+struct Tiles {
+  unsigned char* flag;  // [ntiles] tile held a non-quiescent cell after the last stage 2
+  unsigned char* act;   // [ntiles] tile computed in the current step (stage-1 decision)
+  int skip;             // 0: compute every tile
+};
+
 struct Dev {
   // grid
   int nx, ny, pitch;
@@ -96,6 +113,7 @@ struct Dev {
   double* samp_t;            // [max_samples]
   double* samp_h;            // [max_samples][ngauge]
   int nblocks;               // blocks of the stage grid
+  Tiles tiles;
 };
 
 // ---------------------------------------------------------------------------
@@ -373,6 +391,24 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return r;
 }
 
+template <int NT>
+__device__ __forceinline__ float block_max_f(float v, float* sh) {
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (warp == 0) {
+    r = lane < NT / 32 ? sh[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  return r;
+}
+
 // Courant wave-speed rate of a cell: max((|u|+c)/dx, (|v|+c)/dy) if wet.
 __device__ __forceinline__ double cell_rate(const Dev& d, double h0, double qx0, double qy0) {
   if (!(h0 > d.tol)) return 0.0;
@@ -400,6 +436,56 @@ __device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
   }
   sc->dt = dt;
   sc->lam_bits = 0ull;
+}
+
+// Tiles that must be computed whatever their state: every tile while it rains,
+// the tile of the point source, and the edge tiles an inflow segment touches.
+template <class D>
+__device__ bool tile_forced(const D& d, int bx, int by, int ntx, int nty, double dx, double dy) {
+  if (d.rain != 0.0) return true;
+  if (d.src_idx >= 0) {
+    const int si = (int)(d.src_idx % d.pitch), sj = (int)(d.src_idx / d.pitch);
+    if (si / TX == bx && sj / TY == by) return true;
+  }
+  for (int k = 0; k < d.n_in; ++k) {
+    const InflowDesc& f = d.in[k];
+    double lo, hi;
+    if (f.edge <= 1) {
+      if ((f.edge == 0 && bx != 0) || (f.edge == 1 && bx != ntx - 1)) continue;
+      lo = (double)by * TY * dy;
+      hi = (double)(by + 1) * TY * dy;
+    } else {
+      if ((f.edge == 2 && by != 0) || (f.edge == 3 && by != nty - 1)) continue;
+      lo = (double)bx * TX * dx;
+      hi = (double)(bx + 1) * TX * dx;
+    }
+    if (f.s1 >= lo && f.s0 <= hi) return true;
+  }
+  return false;
+}
+
+// 1: compute the tile; 2 (stage 1 only): copy its state to the stage buffer
+// because a neighbouring tile is computed and reads it as halo; 0: nothing.
+template <int STAGE, class D>
+__device__ int tile_mode(const D& d, double dx, double dy) {
+  const int bx = blockIdx.x, by = blockIdx.y, ntx = gridDim.x, nty = gridDim.y;
+  const int t = by * ntx + bx;
+  if (STAGE == 2) return (!d.tiles.skip || d.tiles.act[t]) ? 1 : 0;
+  if (!d.tiles.skip) {
+    d.tiles.act[t] = 1;
+    return 1;
+  }
+  bool act = false, front = false;
+  for (int oy = -2; oy <= 2; ++oy)
+    for (int ox = -2; ox <= 2; ++ox) {
+      const int x = bx + ox, y = by + oy;
+      if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
+      if (!d.tiles.flag[y * ntx + x] && !tile_forced(d, x, y, ntx, nty, dx, dy)) continue;
+      front = true;
+      if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1) act = true;
+    }
+  d.tiles.act[t] = act ? 1 : 0;
+  return act ? 1 : (front ? 2 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -461,6 +547,8 @@ __device__ __forceinline__ void friction_point(double gn2dt, double tol, double 
 __global__ void __launch_bounds__(256) friction_kernel(Dev d) {
   const Scalars* sc = d.sc;
   if (sc->done) return;
+  // a tile of quiescent cells has no water to rub (same 32 x 8 tiling as the stages)
+  if (d.tiles.skip && !d.tiles.flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
@@ -528,6 +616,18 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
   const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
 
+  __shared__ int s_mode;
+  if (tx == 0 && ty == 0) s_mode = tile_mode<STAGE>(d, d.dx, d.dy);
+  __syncthreads();
+  const int mode = s_mode;
+  double brate = 0.0;  // water entering through domain-edge faces (m^3/s)
+  double lam = 0.0;
+  bool bad = false, nonq = false;
+  if (STAGE == 1 && mode == 2 && act) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d.T[k * P + c] = d.S[k * P + c];
+  }
+  if (mode == 1) {
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
   Lim Es, Ws, Ns, Ss;
@@ -617,7 +717,6 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   __syncthreads();
 
   // one HLL flux per face of the tile
-  double brate = 0.0;  // water entering through domain-edge faces (m^3/s)
   if (act) {
     const Lim& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
     const F3 fw = flux_x(Lw, Ws, g, tol);
@@ -640,8 +739,6 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   }
   __syncthreads();
 
-  double lam = 0.0;
-  bool bad = false;
   if (act) {
     const F3 FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
     const F3 GS = sm.fy[ty][tx], GN = sm.fy[ty + 1][tx];
@@ -704,8 +801,12 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
       for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
       lam = cell_rate(d, out[H0], out[QX0], out[QY0]);
       bad = !(isfinite(out[H0]) && isfinite(out[QX0]) && isfinite(out[QY0])) || out[H0] < -1.0;
+      nonq = !(out[H0] <= tol);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) nonq = nonq || out[k] != 0.0;
     }
   }
+  }  // mode == 1
 
   // per-block boundary mass rate (fixed slot per block: deterministic sums)
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -714,6 +815,8 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   if (STAGE == 1) return;
 
   if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+  const int any_nonq = __syncthreads_or(nonq);
+  if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
   const double bl = block_max<TX * TY>(lam, sm.red);
   __shared__ bool last;
   if (tx == 0 && ty == 0) {

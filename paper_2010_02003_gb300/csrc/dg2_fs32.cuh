@@ -53,6 +53,7 @@ struct D32 {
   double* samp_t;
   double* samp_h;
   int nblocks;
+  Tiles tiles;
 };
 
 struct LimF {
@@ -271,10 +272,10 @@ __device__ __forceinline__ void wetdry32(float* m, float z0, float z1x, float z1
   }
 }
 
-__device__ __forceinline__ double rate32(const D32& d, float h0, float qx0, float qy0) {
-  if (!(h0 > d.tol)) return 0.0;
+__device__ __forceinline__ float rate32(const D32& d, float h0, float qx0, float qy0) {
+  if (!(h0 > d.tol)) return 0.f;
   const float u = qx0 / h0, v = qy0 / h0, c = sqrtf(d.g * h0);
-  return (double)fmaxf((fabsf(u) + c) * d.inv_dx, (fabsf(v) + c) * d.inv_dy);
+  return fmaxf((fabsf(u) + c) * d.inv_dx, (fabsf(v) + c) * d.inv_dy);
 }
 
 __device__ void schedule32(const D32& d, Scalars* sc, double lam) {
@@ -356,6 +357,7 @@ __device__ __forceinline__ void friction_point32(float gn2dt, float tol, float h
 __global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
   const Scalars* sc = d.sc;
   if (sc->done) return;
+  if (d.tiles.skip && !d.tiles.flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
@@ -407,6 +409,7 @@ struct StageSmem32 {
   FaceF fx[TY][TX + 1];
   FaceF fy[TY + 1][TX];
   double red[32];
+  float redf[32];
 };
 
 template <bool LL, int STAGE>
@@ -419,14 +422,40 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
   const bool act = i < d.nx && j < d.ny;
   const long long P = d.plane;
   const long long c = (long long)j * d.pitch + i;
-  const double dtd = sc->dt;
-  const float dt = (float)dtd;
-  const double ts = STAGE == 1 ? sc->t : sc->t + dtd;
   const float* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const float g = d.g, tol = d.tol;
   const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
   const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
+  // FP64 work happens once per block here, never per cell: on this part one
+  // FP64 operation costs the issue slots of 64 FP32 operations
+  const bool edge_block = blockIdx.x == 0 || blockIdx.y == 0 || blockIdx.x == gridDim.x - 1 ||
+                          blockIdx.y == gridDim.y - 1;
 
+  __shared__ int s_mode, s_rain;
+  __shared__ float s_dt, s_rainf;
+  __shared__ double s_dtd, s_ts;
+  if (tx == 0 && ty == 0) {
+    s_mode = tile_mode<STAGE>(d, d.dxd, d.dyd);
+    const double dtd0 = sc->dt;
+    const double ts0 = STAGE == 1 ? sc->t : sc->t + dtd0;
+    s_dtd = dtd0;
+    s_ts = ts0;
+    s_dt = (float)dtd0;
+    s_rain = d.rain != 0.0 && ts0 >= d.rain_t0 && ts0 < d.rain_t1;
+    s_rainf = (float)d.rain;
+  }
+  __syncthreads();
+  const int mode = s_mode;
+  const float dt = s_dt;
+  const double dtd = s_dtd, ts = s_ts;
+  float brate = 0.f;  // water entering through domain-edge faces (m^3/s), FP32 per cell
+  float lam = 0.f;
+  bool bad = false, nonq = false;
+  if (STAGE == 1 && mode == 2 && act) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d.T[k * P + c] = d.S[k * P + c];
+  }
+  if (mode == 1) {
   float m[9];
   float z0 = 0.f, z1x = 0.f, z1y = 0.f, zE = 0.f, zW = 0.f, zN = 0.f, zS = 0.f;
   LimF Es, Ws, Ns, Ss;
@@ -511,31 +540,28 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
   }
   __syncthreads();
 
-  double brate = 0.0;
   if (act) {
     const LimF& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
     const FaceF fw = flux_x32(Lw, Ws, g, tol);
     sm.fx[ty][tx] = fw;
-    if (i == 0) brate += (double)fw.h * d.dyd;
+    if (i == 0) brate += fw.h * d.dy;
     if (east_edge) {
       const FaceF fe = flux_x32(Es, sm.he[ty], g, tol);
       sm.fx[ty][tx + 1] = fe;
-      if (i == d.nx - 1) brate -= (double)fe.h * d.dyd;
+      if (i == d.nx - 1) brate -= fe.h * d.dy;
     }
     const LimF& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
     const FaceF fs = flux_y32(Ls, Ss, g, tol);
     sm.fy[ty][tx] = fs;
-    if (j == 0) brate += (double)fs.h * d.dxd;
+    if (j == 0) brate += fs.h * d.dx;
     if (north_edge) {
       const FaceF fn = flux_y32(Ns, sm.hn[tx], g, tol);
       sm.fy[ty + 1][tx] = fn;
-      if (j == d.ny - 1) brate -= (double)fn.h * d.dxd;
+      if (j == d.ny - 1) brate -= fn.h * d.dx;
     }
   }
   __syncthreads();
 
-  double lam = 0.0;
-  bool bad = false;
   if (act) {
     // own faces: east / north faces are referenced to our (left / south) pressure,
     // west / south faces to the neighbour's, so add dP to get ours
@@ -561,7 +587,7 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
     L[E0] = -(FEh - FWh) * idx - (GNh - GSh) * idy;
     L[QX0] = -(FEx - FWx) * idx - (GNx - GSx) * idy - g * h0x * dEx * idx;
     L[QY0] = -(FEy - FWy) * idx - (GNy - GSy) * idy - g * h0y * dEy * idy;
-    if (d.rain != 0.0 && ts >= d.rain_t0 && ts < d.rain_t1) L[E0] += (float)d.rain;
+    if (s_rain) L[E0] += s_rainf;
     if (c == d.src_idx) L[E0] += (float)(d.qp / (d.dxd * d.dyd));
     const float k3x = -3.f * idx, k3y = -3.f * idy, g23 = 2.f * g / 3.f;
     L[E1X] = k3x * ((FEh + FWh) - (Fph + Fmh));
@@ -602,16 +628,23 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
       for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
       lam = rate32(d, out[E0] - z0, out[QX0], out[QY0]);
       bad = !(isfinite(out[E0]) && isfinite(out[QX0]) && isfinite(out[QY0]));
+      nonq = !(out[E0] - z0 <= tol) || out[E1X] != z1x || out[E1Y] != z1y;
+#pragma unroll
+      for (int k = 3; k < 9; ++k) nonq = nonq || out[k] != 0.f;
     }
   }
+  }  // mode == 1
 
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  const double bsum = block_sum<TX * TY>(brate, sm.red);
+  // only blocks on the domain edge have boundary faces (block-uniform branch)
+  const double bsum = (edge_block && mode == 1) ? block_sum<TX * TY>((double)brate, sm.red) : 0.0;
   if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
   if (STAGE == 1) return;
 
   if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
-  const double bl = block_max<TX * TY>(lam, sm.red);
+  const int any_nonq = __syncthreads_or(nonq);
+  if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
+  const double bl = mode == 1 ? (double)block_max_f<TX * TY>(lam, sm.redf) : 0.0;
   __shared__ bool last;
   if (tx == 0 && ty == 0) {
     if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
@@ -682,7 +715,7 @@ __global__ void __launch_bounds__(256) rate32_kernel(D32 d) {
     const long long P = d.plane, c = (long long)j * d.pitch + i;
     float z0, z1x, z1y, zE, zW, zN, zS;
     cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-    lam = rate32(d, d.S[c] - z0, d.S[QX0 * P + c], d.S[QY0 * P + c]);
+    lam = (double)rate32(d, d.S[c] - z0, d.S[QX0 * P + c], d.S[QY0 * P + c]);
   }
   const double bl = block_max<256>(lam, red);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;

@@ -193,3 +193,14 @@ def random_terrain(nx, ny, dx=1.0, seed=7, relief=1.0, eta=0.6, dam=True):
     man = rng.uniform(0.02, 0.06, size=(ny, nx))
     return Case(name=f"terrain{nx}x{ny}", nx=nx, ny=ny, dx=dx, dy=dx, z_corner=z, eta_corner=e,
                 manning=man, t_end=5.0)
+
+
+def flooded_plain(nx=2000, ny=1000, dx=2.0, seed=2010, freeboard=0.5, tilt=1e-4):
+    """The floodplain terrain fully under water: free surface `freeboard` m above the
+    highest ground at the west edge, falling eastwards with slope `tilt`, so every cell
+    is wet and the water starts to move; same inflow and edges as the floodplain."""
+    case = floodplain(nx=nx, ny=ny, dx=dx, seed=seed)
+    X, _ = corner_xy(nx, ny, dx, dx)
+    case.eta_corner = case.z_corner.max() + freeboard - tilt * X
+    case.name = f"flooded{nx}x{ny}"
+    return case
