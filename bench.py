@@ -30,11 +30,20 @@ NX, NY, DX = 2000, 1000, 2.0
 BYTES_PER_CELL = {
     "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
              "stage2": {"nl": 30 * 8, "ll": 30 * 8}},
-    # FP32 free-surface form: 9 state planes, 2 face-topography planes, Manning n
-    "fp32": {"friction": (10 + 2 + 6) * 4, "stage1": {"nl": (9 + 2 + 9) * 4, "ll": (9 + 2 + 15) * 4},
-             "stage2": {"nl": (9 + 9 + 2 + 9) * 4, "ll": (9 + 9 + 2 + 9) * 4}},
+    # FP32 free-surface form: 10 state planes (eta0 as hi + lo), 2 face-topography planes,
+    # Manning n
+    "fp32": {"friction": (13 + 6) * 4, "stage1": {"nl": (10 + 2 + 10) * 4, "ll": (10 + 2 + 16) * 4},
+             "stage2": {"nl": (10 + 10 + 2 + 10) * 4, "ll": (10 + 10 + 2 + 10) * 4}},
 }
 KERNELS = ["friction", "stage1", "stage2"]
+# Algorithmic FP64 operations per wet cell (add, mul, div, sqrt, cbrt each one), each
+# face flux counted once: measured with oracle/opcount.cpp (friction 111, spatial
+# operator 381, limiter 70 per cell; RK combination 18 / 27; Courant rate 8).
+FLOPS_PER_WET_CELL = {"friction": 111, "stage1": {"nl": 399, "ll": 469},
+                      "stage2": {"nl": 416, "ll": 486}}
+# FP64 issue rate of GB300: 2 DFMA per SM per cycle (ncu
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / cycle), 152 SMs
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
 def parse():
@@ -135,18 +144,51 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def active_cells(state, tol=1e-5, tx=32, ty=8, case=None):
+    """Cells of the tiles the kernels compute: tiles within one tile of a tile holding a
+    wet cell or a moving/sloped dry cell (the kernels' quiescence rule); every tile while
+    rain is configured."""
+    h0 = state[0]
+    if case is not None and case.rain[0] != 0.0:
+        return h0.size, float((h0 > tol).mean())
+    busy = (h0 > tol) | (np.abs(state[1:]).max(axis=0) != 0)
+    ny, nx = h0.shape
+    nty, ntx = -(-ny // ty), -(-nx // tx)
+    pad = np.zeros((nty * ty, ntx * tx), dtype=bool)
+    pad[:ny, :nx] = busy
+    t = pad.reshape(nty, ty, ntx, tx).any(axis=(1, 3))
+    d = t.copy()
+    d[1:] |= t[:-1]; d[:-1] |= t[1:]
+    d2 = d.copy()
+    d2[:, 1:] |= d[:, :-1]; d2[:, :-1] |= d[:, 1:]
+    return int(d2.sum()) * tx * ty, float(busy.mean())
+
+
 def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
-    """HBM roofline of the dominant kernel of one timed run (live event timing)."""
+    """Roofline of the dominant kernel of one timed run (live CUDA-event timing).
+    FP64: FP64-pipe bound, algorithmic FLOPs per wet cell; FP32: HBM bound, unique
+    bytes per cell of the tiles computed (dry tiles are exact fixed points, skipped)."""
     kms = run["kernel_ms"] / max(run["timed"], 1)
     dom = int(np.argmax(kms))
+    names = {"friction": "friction", "stage1": "stage 1", "stage2": "stage 2"}
+    kname = f"{prec} {var.upper()} {names[KERNELS[dom]]}"
+    kernel_ms = {n: float(k) for n, k in zip(KERNELS, kms)}
+    if prec == "fp64":
+        tab = FLOPS_PER_WET_CELL[KERNELS[dom]]
+        per_cell = tab if dom == 0 else tab[var]
+        wet = run["wet_fraction"] * cells
+        achieved = per_cell * wet / (kms[dom] * 1e-3) / 1e9
+        return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
+                "flops_per_wet_cell": per_cell, "wet_cells": wet, "kernel_ms": kernel_ms}
     tab = BYTES_PER_CELL[prec][KERNELS[dom]]
     per_cell = tab if dom == 0 else tab[var]
-    achieved = per_cell * cells / (kms[dom] * 1e-3) / 1e9
-    names = {"friction": "friction", "stage1": "stage 1", "stage2": "stage 2"}
-    return {"bound": "hbm", "kernel": f"{prec} {var.upper()} {names[KERNELS[dom]]}",
-            "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
-            "traffic": None, "peak_source": peak_src, "bytes_per_cell": per_cell,
-            "kernel_ms": {n: float(k) for n, k in zip(KERNELS, kms)}}
+    act = run.get("active_cells", cells)
+    achieved = per_cell * act / (kms[dom] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_gbs,
+            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None, "peak_source": peak_src,
+            "bytes_per_cell": per_cell, "active_cells": act, "kernel_ms": kernel_ms}
 
 
 def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=0):
@@ -156,7 +198,9 @@ def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=
     for _ in range(warmup):
         s.step(-1.0)
     torch.cuda.synchronize()
-    wet = float((s.state()[0] > 1e-5).mean())
+    st0 = s.state()
+    act, _ = active_cells(st0, case=case)
+    wet = float((st0[0] > 1e-5).mean())
     if timing:
         B.dg2_enable_kernel_timing(s.ctx, True)
     l0 = s.launches()
@@ -172,7 +216,7 @@ def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=
     kt, n = B.dg2_kernel_times(s.ctx) if timing else (np.zeros(3), 0)
     t_sim, _ = s.time()
     return {"solver": s, "ms": ms, "launches": launches, "kernel_ms": kt, "timed": n,
-            "wet_fraction": wet, "t_sim": t_sim}
+            "wet_fraction": wet, "active_cells": act, "t_sim": t_sim}
 
 
 def e2e_run(B, torch, case, variant, steps):
@@ -249,7 +293,9 @@ VARIANTS = [
     ("fp64_nl_flooded", "flooded", 0, 0),
     ("fp32_nl_flooded", "flooded", 0, 1),
     ("fp32_ll_flooded", "flooded", 1, 1),
+    ("fp32_nl_urban", "urban", 0, 1),      # 8192 x 8192, rain + point inflow, 500 steps
 ]
+URBAN_STEPS = 500
 
 
 def main():
@@ -263,11 +309,13 @@ def main():
     if not os.path.exists(B.LIB_PATH):
         build_mod.build()
     torch.cuda.set_device(local)
+    only = set(args.only.split(",")) if args.only else None
     cases = {"floodplain": workload(), "flooded": inputs.flooded_plain(NX, NY, DX)}
+    if not only or any(k.endswith("urban") for k in only):
+        cases["urban"] = inputs.urban()
     cells = NX * NY
     warmup = max(3, args.warmup)
     pk, pk_src = peaks()
-    only = set(args.only.split(",")) if args.only else None
 
     results = {}
     clocks = None
@@ -278,14 +326,19 @@ def main():
         clk = ClockSampler(local) if key == "fp64_ll" else None
         if clk:
             clk.start()
-        run = time_variant(B, torch, cases[wl], var, args.steps, warmup, precision=prec)
+        case = cases[wl]
+        ncell = case.nx * case.ny
+        nsteps = URBAN_STEPS if (wl == "urban" and args.steps >= 50) else args.steps
+        run = time_variant(B, torch, case, var, nsteps, warmup, precision=prec)
         if clk:
             clocks = clk.stop()
         ms = max_over_ranks(run["ms"], world)
-        run["value"] = world * cells * args.steps / (ms * 1e-3)
+        run["value"] = world * ncell * nsteps / (ms * 1e-3)
         run["ms_max"] = ms
+        run["steps"] = nsteps
+        run["cells"] = ncell
         run["roofline"] = kernel_roofline(run, "fp32" if prec else "fp64", "ll" if var else "nl",
-                                          cells, pk["hbm_gbs"], pk_src)
+                                          ncell, pk["hbm_gbs"], pk_src)
         run.pop("solver").close()
         results[key] = run
         torch.cuda.empty_cache()
@@ -305,11 +358,12 @@ def main():
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} DG2-LL steps of a 500x250 floodplain (same recipe), {el:.1f} s"}
     if rank == 0:
-        variants = {k: {"value": r["value"], "ms_per_step": r["ms_max"] / args.steps,
+        variants = {k: {"value": r["value"], "ms_per_step": r["ms_max"] / r["steps"],
+                        "steps": r["steps"], "cells": r["cells"],
                         "wet_fraction": r["wet_fraction"], "roofline": r["roofline"]}
                     for k, r in results.items() if k != head}
         line = {"metric": METRIC, "value": hd["value"], "unit": "cell-updates/s", "n_gpus": world,
-                "steps": args.steps, "warmup": warmup, "ms_per_step": hd["ms_max"] / args.steps,
+                "steps": hd["steps"], "warmup": warmup, "ms_per_step": hd["ms_max"] / hd["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if head.startswith("fp64") else "f32", "data": "synthetic",
                 "config": {"workload": "floodplain 2000x1000 dx=2 m, DG2-LL, FP64"

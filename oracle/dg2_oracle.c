@@ -117,7 +117,7 @@ static st3 revise(const orc_t *o, st3 s)
 {
     real u, v;
     velocities(o, s, &u, &v);
-    real hs = s.h > 0.0 ? s.h : 0.0;
+    real hs = s.h > 0.0 ? s.h : (real)0.0;
     return mk(hs, hs * u, hs * v);
 }
 
@@ -205,7 +205,7 @@ static st3 ghost(const orc_t *o, int edge, double s, st3 in, double t)
         int nf = inflow_nfaces(o, f);
         double d = (edge == EW || edge == EE) ? o->dy : o->dx;
         real qin = hydrograph(f, t) / (nf * d);          /* discharge per unit width */
-        real hin = in.h > 0.0 ? in.h : 0.0;
+        real hin = in.h > 0.0 ? in.h : (real)0.0;
         real hc = cbrt(qin * qin / o->g);                /* critical depth of qin */
         real hg = hin > hc ? hin : hc;
         real qn = (edge == EW || edge == ES) ? qin : -qin;   /* pointing into the domain */
@@ -298,10 +298,10 @@ static double spatial_operator(const orc_t *o, const double *U, double t, double
             st3 Nn = limit_at(o, U, i, j, EN), S = limit_at(o, U, i, j, ES);
             st3 Es = revise(o, E), Ws = revise(o, W), Ns = revise(o, Nn), Ss = revise(o, S);
             /* topography limits, revised with the own depth limit at each face */
-            real zE = zlimit_at(o, i, j, EE) - (E.h < 0.0 ? -E.h : 0.0);
-            real zW = zlimit_at(o, i, j, EW) - (W.h < 0.0 ? -W.h : 0.0);
-            real zN = zlimit_at(o, i, j, EN) - (Nn.h < 0.0 ? -Nn.h : 0.0);
-            real zS = zlimit_at(o, i, j, ES) - (S.h < 0.0 ? -S.h : 0.0);
+            real zE = zlimit_at(o, i, j, EE) - (E.h < 0.0 ? -E.h : (real)0.0);
+            real zW = zlimit_at(o, i, j, EW) - (W.h < 0.0 ? -W.h : (real)0.0);
+            real zN = zlimit_at(o, i, j, EN) - (Nn.h < 0.0 ? -Nn.h : (real)0.0);
+            real zS = zlimit_at(o, i, j, ES) - (S.h < 0.0 ? -S.h : (real)0.0);
             /* inter-elemental fluxes */
             st3 FE = hll_x(o, Es, revise(o, outer_limit(o, U, i, j, EE, t)));
             st3 FW = hll_x(o, revise(o, outer_limit(o, U, i, j, EW, t)), Ws);

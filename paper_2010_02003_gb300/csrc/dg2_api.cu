@@ -53,7 +53,8 @@ struct Layout {
   int pitch, zpx;
   long long plane;
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
-  size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, total;
+  size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, off_tforced,
+      total;
   int nblocks, mblocks;
 };
 
@@ -77,8 +78,9 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
     o = align_up(o + bytes);
     return at;
   };
-  L.off_S = take(9 * pb);
-  L.off_T = take(9 * pb > staging ? 9 * pb : staging);
+  const size_t nplanes = f32 ? dg2::f32::kPlanes32 : 9;
+  L.off_S = take(nplanes * pb);
+  L.off_T = take(nplanes * pb > staging ? nplanes * pb : staging);
   L.off_Q = take(p.variant == DG2_LL ? 6 * pb : 0);
   L.off_Z = take(f32 ? 0 : 3 * pb);
   L.off_ZX = take(f32 ? (size_t)ny * L.zpx * sizeof(float) : 0);
@@ -97,6 +99,7 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   L.off_sc = take(sizeof(Scalars));
   L.off_tflag = take((size_t)L.nblocks);
   L.off_tact = take((size_t)L.nblocks);
+  L.off_tforced = take((size_t)L.nblocks);
   L.total = o;
   return true;
 }
@@ -146,6 +149,37 @@ void drop_graph(dg2_ctx* c) {
 
 constexpr int kMaxTimedSteps = 8192;
 
+// Host-side mask of the tiles that must be computed whatever their state: the
+// tile holding the point source and the edge tiles whose faces an inflow
+// segment covers.  Rain marks every tile (all_forced).
+int update_forced_tiles(dg2_ctx* c) {
+  Dev& d = c->d;
+  const int ntx = (int)c->sgrid.x, nty = (int)c->sgrid.y;
+  std::vector<unsigned char> m((size_t)ntx * nty, 0);
+  if (d.src_idx >= 0) {
+    const int si = (int)(d.src_idx % d.pitch), sj = (int)(d.src_idx / d.pitch);
+    m[(size_t)(sj / dg2::TY) * ntx + si / dg2::TX] = 1;
+  }
+  for (int k = 0; k < d.n_in; ++k) {
+    const dg2::InflowDesc& f = d.in[k];
+    const bool ew = f.edge <= 1;
+    const int n = ew ? d.ny : d.nx;
+    const double h = ew ? d.dy : d.dx;
+    for (int q = 0; q < n; ++q) {
+      const double sc = (q + 0.5) * h;
+      if (sc < f.s0 || sc > f.s1) continue;
+      int bx, by;
+      if (ew) { by = q / dg2::TY; bx = f.edge == 0 ? 0 : ntx - 1; }
+      else { bx = q / dg2::TX; by = f.edge == 2 ? 0 : nty - 1; }
+      m[(size_t)by * ntx + bx] = 1;
+    }
+  }
+  d.tiles.all_forced = d.rain != 0.0 ? 1 : 0;
+  CU(cudaMemcpyAsync((void*)d.tiles.forced, m.data(), m.size(), cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  return DG2_OK;
+}
+
 // Copies the tables shared by both precisions (inflows, sources, gauges) from
 // the FP64 parameter block into the FP32 one.
 void mirror(dg2_ctx* c) {
@@ -156,6 +190,7 @@ void mirror(dg2_ctx* c) {
   f.rain = d.rain; f.rain_t0 = d.rain_t0; f.rain_t1 = d.rain_t1;
   f.qp = d.qp; f.src_idx = d.src_idx;
   f.ngauge = d.ngauge;
+  f.tiles = d.tiles;
 }
 
 // Enqueues one RK2 step: friction, stage 1, stage 2 (3 kernels).  With
@@ -359,6 +394,8 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.nblocks = L.nblocks;
   d.tiles.flag = (unsigned char*)(c->ws + L.off_tflag);
   d.tiles.act = (unsigned char*)(c->ws + L.off_tact);
+  d.tiles.forced = (const unsigned char*)(c->ws + L.off_tforced);
+  d.tiles.all_forced = 0;
   d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
   {
     D32& f = c->f;
@@ -506,6 +543,7 @@ int dg2_set_bc_inflow(dg2_ctx* c, int edge, double s0_m, double len_m, const dou
                      cudaMemcpyHostToDevice, c->st));
   CU(cudaStreamSynchronize(c->st));
   c->d.n_in += 1;
+  if ((r = update_forced_tiles(c))) return r;
   mirror(c);
   return DG2_OK;
 }
@@ -529,6 +567,8 @@ int dg2_set_sources(dg2_ctx* c, double rain, double t0, double t1, double px, do
     j = j < 0 ? 0 : (j >= c->d.ny ? c->d.ny - 1 : j);
     c->d.src_idx = (long long)j * c->d.pitch + i;
   }
+  int r2 = update_forced_tiles(c);
+  if (r2) return r2;
   mirror(c);
   return DG2_OK;
 }
@@ -684,15 +724,15 @@ int dg2_get_state(dg2_ctx* c, double* planes, double* t) {
     // FP32 free-surface modes -> FP64 depth modes h = eta - z
     const int nx = c->f.nx, ny = c->f.ny;
     const size_t n = (size_t)nx * ny;
-    std::vector<float> buf(9 * n);
-    for (int k = 0; k < 9; ++k)
+    std::vector<float> buf(10 * n);
+    for (int k = 0; k < 10; ++k)
       CU(cudaMemcpy2DAsync(buf.data() + k * n, nx * sizeof(float), c->f.S + k * c->f.plane,
                            c->f.pitch * sizeof(float), nx * sizeof(float), ny,
                            cudaMemcpyDeviceToHost, c->st));
     std::vector<float> z0, z1x, z1y;
     if ((r = f32_topo_modes(c, z0, z1x, z1y))) return r;
     for (size_t k = 0; k < n; ++k) {
-      planes[k] = (double)buf[k] - (double)z0[k];
+      planes[k] = ((double)buf[k] - (double)z0[k]) + (double)buf[9 * n + k];
       planes[n + k] = (double)buf[n + k] - (double)z1x[k];
       planes[2 * n + k] = (double)buf[2 * n + k] - (double)z1y[k];
     }
@@ -724,15 +764,17 @@ int dg2_set_state(dg2_ctx* c, const double* planes, double t) {
     const int nx = c->f.nx, ny = c->f.ny;
     std::vector<float> z0, z1x, z1y;
     if ((r = f32_topo_modes(c, z0, z1x, z1y))) return r;
-    std::vector<float> buf(9 * (size_t)nx * ny);
+    std::vector<float> buf(10 * (size_t)nx * ny);
     const size_t m = (size_t)nx * ny;
     for (size_t k = 0; k < m; ++k) {
-      buf[k] = (float)(planes[k] + (double)z0[k]);
+      const double e0 = planes[k] + (double)z0[k];
+      buf[k] = (float)e0;
+      buf[9 * m + k] = (float)(e0 - (double)buf[k]);
       buf[m + k] = (float)(planes[m + k] + (double)z1x[k]);
       buf[2 * m + k] = (float)(planes[2 * m + k] + (double)z1y[k]);
     }
     for (size_t k = 3 * m; k < 9 * m; ++k) buf[k] = (float)planes[k];
-    for (int k = 0; k < 9; ++k)
+    for (int k = 0; k < 10; ++k)
       CU(cudaMemcpy2DAsync(c->f.S + k * c->f.plane, c->f.pitch * sizeof(float), buf.data() + k * m,
                            nx * sizeof(float), nx * sizeof(float), ny, cudaMemcpyHostToDevice,
                            c->st));

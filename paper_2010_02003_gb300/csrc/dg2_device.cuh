@@ -74,9 +74,11 @@ struct Scalars {
 // (inflow, point source, rain) tile is left untouched, bit for bit as if it
 // had been computed.
 struct Tiles {
-  unsigned char* flag;  // [ntiles] tile held a non-quiescent cell after the last stage 2
-  unsigned char* act;   // [ntiles] tile computed in the current step (stage-1 decision)
-  int skip;             // 0: compute every tile
+  unsigned char* flag;          // [ntiles] tile held a non-quiescent cell after the last stage 2
+  unsigned char* act;           // [ntiles] tile computed in the current step (stage-1 decision)
+  const unsigned char* forced;  // [ntiles] tile must be computed (inflow, source); set on the host
+  int all_forced;               // every tile must be computed (rain)
+  int skip;                     // 0: compute every tile
 };
 
 struct Dev {
@@ -438,54 +440,34 @@ __device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
   sc->lam_bits = 0ull;
 }
 
-// Tiles that must be computed whatever their state: every tile while it rains,
-// the tile of the point source, and the edge tiles an inflow segment touches.
-template <class D>
-__device__ bool tile_forced(const D& d, int bx, int by, int ntx, int nty, double dx, double dy) {
-  if (d.rain != 0.0) return true;
-  if (d.src_idx >= 0) {
-    const int si = (int)(d.src_idx % d.pitch), sj = (int)(d.src_idx / d.pitch);
-    if (si / TX == bx && sj / TY == by) return true;
-  }
-  for (int k = 0; k < d.n_in; ++k) {
-    const InflowDesc& f = d.in[k];
-    double lo, hi;
-    if (f.edge <= 1) {
-      if ((f.edge == 0 && bx != 0) || (f.edge == 1 && bx != ntx - 1)) continue;
-      lo = (double)by * TY * dy;
-      hi = (double)(by + 1) * TY * dy;
-    } else {
-      if ((f.edge == 2 && by != 0) || (f.edge == 3 && by != nty - 1)) continue;
-      lo = (double)bx * TX * dx;
-      hi = (double)(bx + 1) * TX * dx;
-    }
-    if (f.s1 >= lo && f.s0 <= hi) return true;
-  }
-  return false;
-}
-
 // 1: compute the tile; 2 (stage 1 only): copy its state to the stage buffer
 // because a neighbouring tile is computed and reads it as halo; 0: nothing.
+// Called by every thread of warp 0 (lane t < 25 gathers the flags of one tile
+// of the 5 x 5 neighbourhood, in parallel); lane 0's result is the block's.
 template <int STAGE, class D>
-__device__ int tile_mode(const D& d, double dx, double dy) {
+__device__ int tile_mode_warp(const D& d) {
   const int bx = blockIdx.x, by = blockIdx.y, ntx = gridDim.x, nty = gridDim.y;
   const int t = by * ntx + bx;
   if (STAGE == 2) return (!d.tiles.skip || d.tiles.act[t]) ? 1 : 0;
-  if (!d.tiles.skip) {
-    d.tiles.act[t] = 1;
+  const int lane = threadIdx.x;
+  if (!d.tiles.skip || d.tiles.all_forced) {
+    if (lane == 0) d.tiles.act[t] = 1;
     return 1;
   }
-  bool act = false, front = false;
-  for (int oy = -2; oy <= 2; ++oy)
-    for (int ox = -2; ox <= 2; ++ox) {
-      const int x = bx + ox, y = by + oy;
-      if (x < 0 || y < 0 || x >= ntx || y >= nty) continue;
-      if (!d.tiles.flag[y * ntx + x] && !tile_forced(d, x, y, ntx, nty, dx, dy)) continue;
-      front = true;
-      if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1) act = true;
+  bool busy = false, inner = false;
+  if (lane < 25) {
+    const int ox = lane % 5 - 2, oy = lane / 5 - 2;
+    const int x = bx + ox, y = by + oy;
+    if (x >= 0 && y >= 0 && x < ntx && y < nty) {
+      const int q = y * ntx + x;
+      busy = (d.tiles.flag[q] | d.tiles.forced[q]) != 0;
     }
-  d.tiles.act[t] = act ? 1 : 0;
-  return act ? 1 : (front ? 2 : 0);
+    inner = ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1;
+  }
+  const unsigned any = __ballot_sync(0xffffffffu, busy);
+  const unsigned act = __ballot_sync(0xffffffffu, busy && inner);
+  if (lane == 0) d.tiles.act[t] = act ? 1 : 0;
+  return act ? 1 : (any ? 2 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -617,7 +599,10 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
 
   __shared__ int s_mode;
-  if (tx == 0 && ty == 0) s_mode = tile_mode<STAGE>(d, d.dx, d.dy);
+  if (ty == 0) {
+    const int md = tile_mode_warp<STAGE>(d);
+    if (tx == 0) s_mode = md;
+  }
   __syncthreads();
   const int mode = s_mode;
   double brate = 0.0;  // water entering through domain-edge faces (m^3/s)
@@ -808,16 +793,21 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   }
   }  // mode == 1
 
-  // per-block boundary mass rate (fixed slot per block: deterministic sums)
+  // per-block boundary mass rate (fixed slot per block: deterministic sums);
+  // only computed tiles on the domain edge have boundary faces
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  const double bsum = block_sum<TX * TY>(brate, sm.red);
+  const bool edge_block = blockIdx.x == 0 || blockIdx.y == 0 || blockIdx.x == gridDim.x - 1 ||
+                          blockIdx.y == gridDim.y - 1;
+  const double bsum = (edge_block && mode == 1) ? block_sum<TX * TY>(brate, sm.red) : 0.0;
   if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
   if (STAGE == 1) return;
 
-  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
-  const int any_nonq = __syncthreads_or(nonq);
-  if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
-  const double bl = block_max<TX * TY>(lam, sm.red);
+  if (mode == 1) {
+    if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+    const int any_nonq = __syncthreads_or(nonq);
+    if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
+  }
+  const double bl = mode == 1 ? block_max<TX * TY>(lam, sm.red) : 0.0;
   __shared__ bool last;
   if (tx == 0 && ty == 0) {
     if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));

@@ -23,6 +23,20 @@ namespace dg2 {
 namespace f32 {
 
 enum { E0 = 0, E1X, E1Y };  // free-surface modes occupy the h slots
+// eta0 is carried as an unevaluated pair hi + lo of FP32 values: plane E0 holds
+// hi, plane E0L the remainder lo (|lo| <= half an ulp of hi), updated with
+// error-free TwoSum.  One FP32 ulp of the free surface over terrain of a few
+// metres is ~1e-6 m, coarser than a rain increment per step or a thin film;
+// the pair resolves the depth and conserves mass, all on FP32 units.
+enum { E0L = 9 };
+constexpr int kPlanes32 = 10;
+
+// s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
 
 struct D32 {
   int nx, ny, pitch;   // cell planes: ny rows of `pitch` floats
@@ -37,8 +51,8 @@ struct D32 {
   const double* knot_q;
   double rain, rain_t0, rain_t1, qp;
   long long src_idx;
-  float* S;            // 9 planes: eta0 eta1x eta1y qx0 qx1x qx1y qy0 qy1x qy1y
-  float* T;            // 9 planes: stage state
+  float* S;            // 10 planes: eta0 eta1x eta1y qx0 qx1x qx1y qy0 qy1x qy1y, eta0 lo
+  float* T;            // 10 planes: stage state
   float* Q;            // 6 planes: limited slopes of Un (DG2-LL)
   const float* ZX;     // z at x-faces: face i of row j at ZX[j * zpx + i], i = 0..nx
   const float* ZY;     // z at y-faces: face j of column i at ZY[j * pitch + i], j = 0..ny
@@ -228,11 +242,11 @@ __device__ void limited_slopes32(const D32& d, const float* __restrict__ U, int 
   const long long cl = (long long)jl * d.pitch + il, ch = (long long)jh * d.pitch + ih;
   float z0, z1x, z1y, zE, zW, zN, zS;
   cell_z(d, il, jl, z0, z1x, z1y, zE, zW, zN, zS);
-  const float hl = U[cl] - z0;
+  const float hl = (U[cl] - z0) + U[E0L * P + cl];
   cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-  const float hc = U[c] - z0;
+  const float hc = (U[c] - z0) + U[E0L * P + c];
   cell_z(d, ih, jh, z0, z1x, z1y, zE, zW, zN, zS);
-  const float hh = U[ch] - z0;
+  const float hh = (U[ch] - z0) + U[E0L * P + ch];
   if (hl <= d.tol || hc <= d.tol || hh <= d.tol) return;
   const float half = 0.5f * (dir == 1 ? d.dx : d.dy);
   se = limit_comp32(d.ds, d.tol, half, U[cl], U[dir * P + cl], U[c], se, U[ch], U[dir * P + ch]);
@@ -250,9 +264,9 @@ __device__ void limited_slopes32(const D32& d, const float* __restrict__ U, int 
 
 // Wet-dry treatment in free-surface variables (same rule as the FP64 path):
 // a zeroed depth slope is eta1 = z1.
-__device__ __forceinline__ void wetdry32(float* m, float z0, float z1x, float z1y, float zE,
-                                         float zW, float zN, float zS, float tol) {
-  const float h0 = m[E0] - z0;
+__device__ __forceinline__ void wetdry32(float* m, float lo, float z0, float z1x, float z1y,
+                                         float zE, float zW, float zN, float zS, float tol) {
+  const float h0 = (m[E0] - z0) + lo;
   if (h0 <= tol) {
     m[E1X] = z1x; m[E1Y] = z1y;
 #pragma unroll
@@ -261,13 +275,13 @@ __device__ __forceinline__ void wetdry32(float* m, float z0, float z1x, float z1
   }
   const float eta0 = m[E0];
   {
-    const bool fe = ((m[E0] + m[E1X]) - zE <= tol) && !(zE > eta0);
-    const bool fw = ((m[E0] - m[E1X]) - zW <= tol) && !(zW > eta0);
+    const bool fe = (((m[E0] - zE) + m[E1X]) + lo <= tol) && !(zE > eta0);
+    const bool fw = (((m[E0] - zW) - m[E1X]) + lo <= tol) && !(zW > eta0);
     if (fe || fw) { m[E1X] = z1x; m[QX1X] = 0.f; m[QY1X] = 0.f; }
   }
   {
-    const bool fn = ((m[E0] + m[E1Y]) - zN <= tol) && !(zN > eta0);
-    const bool fs = ((m[E0] - m[E1Y]) - zS <= tol) && !(zS > eta0);
+    const bool fn = (((m[E0] - zN) + m[E1Y]) + lo <= tol) && !(zN > eta0);
+    const bool fs = (((m[E0] - zS) - m[E1Y]) + lo <= tol) && !(zS > eta0);
     if (fn || fs) { m[E1Y] = z1y; m[QX1Y] = 0.f; m[QY1Y] = 0.f; }
   }
 }
@@ -320,7 +334,7 @@ __global__ void init32_kernel(D32 d, const double* __restrict__ zc, const double
   const float zW = (float)(0.5 * (r0[i] + r1[i])), zE = (float)(0.5 * (r0[i + 1] + r1[i + 1]));
   const float zS = (float)(0.5 * (r0[i] + r0[i + 1])), zN = (float)(0.5 * (r1[i] + r1[i + 1]));
   const float z0 = 0.5f * (zE + zW), z1x = 0.5f * (zE - zW), z1y = 0.5f * (zN - zS);
-  float e0 = z0, e1x = z1x, e1y = z1y;
+  float e0 = z0, e0l = 0.f, e1x = z1x, e1y = z1y;
   if (ec) {
     const double* e0r = ec + (long long)j * W;
     const double* e1r = ec + (long long)(j + 1) * W;
@@ -331,13 +345,16 @@ __global__ void init32_kernel(D32 d, const double* __restrict__ zc, const double
     if (h0 > 0.0) {
       const double fE = 0.5 * (e0r[i + 1] + e1r[i + 1]), fW = 0.5 * (e0r[i] + e1r[i]);
       const double fN = 0.5 * (e1r[i] + e1r[i + 1]), fS = 0.5 * (e0r[i] + e0r[i + 1]);
-      e0 = (float)(0.5 * (fE + fW));
+      const double e0d = 0.5 * (fE + fW);
+      e0 = (float)e0d;
+      e0l = (float)(e0d - (double)e0);
       e1x = (float)(0.5 * (fE - fW));
       e1y = (float)(0.5 * (fN - fS));
     }
   }
   float* S = d.S;
   S[E0 * P + c] = e0;
+  S[E0L * P + c] = e0l;
   S[E1X * P + c] = e1x;
   S[E1Y * P + c] = e1y;
 #pragma unroll
@@ -367,7 +384,7 @@ __global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
   float* S = d.S;
   float z0, z1x, z1y, zE, zW, zN, zS;
   cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-  const float h0 = S[E0 * P + c] - z0;
+  const float h0 = (S[E0 * P + c] - z0) + S[E0L * P + c];
   if (!(h0 > d.tol)) {
     // a dry average can still have wet Gauss points only through slopes, which
     // the wet-dry treatment has zeroed; nothing to do
@@ -434,8 +451,11 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
   __shared__ int s_mode, s_rain;
   __shared__ float s_dt, s_rainf;
   __shared__ double s_dtd, s_ts;
+  if (ty == 0) {
+    const int md = tile_mode_warp<STAGE>(d);
+    if (tx == 0) s_mode = md;
+  }
   if (tx == 0 && ty == 0) {
-    s_mode = tile_mode<STAGE>(d, d.dxd, d.dyd);
     const double dtd0 = sc->dt;
     const double ts0 = STAGE == 1 ? sc->t : sc->t + dtd0;
     s_dtd = dtd0;
@@ -453,24 +473,26 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
   bool bad = false, nonq = false;
   if (STAGE == 1 && mode == 2 && act) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) d.T[k * P + c] = d.S[k * P + c];
+    for (int k = 0; k < kPlanes32; ++k) d.T[k * P + c] = d.S[k * P + c];
   }
   if (mode == 1) {
   float m[9];
   float z0 = 0.f, z1x = 0.f, z1y = 0.f, zE = 0.f, zW = 0.f, zN = 0.f, zS = 0.f;
   LimF Es, Ws, Ns, Ss;
-  float etaE = 0.f, etaW = 0.f, etaN = 0.f, etaS = 0.f;
+  float mlo = 0.f;
   if (act) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) m[k] = In[k * P + c];
+    mlo = In[E0L * P + c];
     if (LL) {
       limited_slopes32(d, In, i, j, 1, m[E1X], m[QX1X], m[QY1X]);
       limited_slopes32(d, In, i, j, 2, m[E1Y], m[QX1Y], m[QY1Y]);
     }
     cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-    etaE = m[E0] + m[E1X]; etaW = m[E0] - m[E1X];
-    etaN = m[E0] + m[E1Y]; etaS = m[E0] - m[E1Y];
-    const float eh = etaE - zE, wh = etaW - zW, nh = etaN - zN, shh = etaS - zS;
+    // face depths (hi - z_face) +- eta1 + lo: hi - z_face is exact for shallow water
+    // (Sterbenz), and both sides of a face form it from the same terms at rest
+    const float eh = ((m[E0] - zE) + m[E1X]) + mlo, wh = ((m[E0] - zW) - m[E1X]) + mlo;
+    const float nh = ((m[E0] - zN) + m[E1Y]) + mlo, shh = ((m[E0] - zS) - m[E1Y]) + mlo;
     const float eqx = m[QX0] + m[QX1X], eqy = m[QY0] + m[QY1X];
     const float wqx = m[QX0] - m[QX1X], wqy = m[QY0] - m[QY1X];
     const float nqx = m[QX0] + m[QX1Y], nqy = m[QY0] + m[QY1Y];
@@ -490,7 +512,7 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
         const long long cw = c - 1;
         float se = In[E1X * P + cw], s1x = In[QX1X * P + cw], s1y = In[QY1X * P + cw];
         if (LL) limited_slopes32(d, In, i - 1, j, 1, se, s1x, s1y);
-        h = (In[E0 * P + cw] + se) - zW;   // the west cell's east face is our west face
+        h = ((In[E0 * P + cw] - zW) + se) + In[E0L * P + cw];  // its east face is our west face
         qx = In[QX0 * P + cw] + s1x; qy = In[QY0 * P + cw] + s1y;
       }
       sm.hw[ty] = revise32(h, qx, qy, tol);
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
         const long long ce = c + 1;
         float se = In[E1X * P + ce], s1x = In[QX1X * P + ce], s1y = In[QY1X * P + ce];
         if (LL) limited_slopes32(d, In, i + 1, j, 1, se, s1x, s1y);
-        h = (In[E0 * P + ce] - se) - zE;
+        h = ((In[E0 * P + ce] - zE) - se) + In[E0L * P + ce];
         qx = In[QX0 * P + ce] - s1x; qy = In[QY0 * P + ce] - s1y;
       }
       sm.he[ty] = revise32(h, qx, qy, tol);
@@ -518,7 +540,7 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
         const long long cs = c - d.pitch;
         float se = In[E1Y * P + cs], s1x = In[QX1Y * P + cs], s1y = In[QY1Y * P + cs];
         if (LL) limited_slopes32(d, In, i, j - 1, 2, se, s1x, s1y);
-        h = (In[E0 * P + cs] + se) - zS;
+        h = ((In[E0 * P + cs] - zS) + se) + In[E0L * P + cs];
         qx = In[QX0 * P + cs] + s1x; qy = In[QY0 * P + cs] + s1y;
       }
       sm.hs[tx] = revise32(h, qx, qy, tol);
@@ -532,7 +554,7 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
         const long long cn = c + d.pitch;
         float se = In[E1Y * P + cn], s1x = In[QX1Y * P + cn], s1y = In[QY1Y * P + cn];
         if (LL) limited_slopes32(d, In, i, j + 1, 2, se, s1x, s1y);
-        h = (In[E0 * P + cn] - se) - zN;
+        h = ((In[E0 * P + cn] - zN) - se) + In[E0L * P + cn];
         qx = In[QX0 * P + cn] - s1x; qy = In[QY0 * P + cn] - s1y;
       }
       sm.hn[tx] = revise32(h, qx, qy, tol);
@@ -582,7 +604,7 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
     gauss_dev(h0y + h1y_ * r3, x0y + x1y * r3, y0y + y1y * r3, tol, true, Gph, Gpx, Gpy);
     gauss_dev(h0y - h1y_ * r3, x0y - x1y * r3, y0y - y1y * r3, tol, true, Gmh, Gmx, Gmy);
     const float idx = d.inv_dx, idy = d.inv_dy;
-    const float dEx = etaE - etaW, dEy = etaN - etaS;
+    const float dEx = 2.f * m[E1X], dEy = 2.f * m[E1Y];  // eta_E - eta_W, eta_N - eta_S
     float L[9];
     L[E0] = -(FEh - FWh) * idx - (GNh - GSh) * idy;
     L[QX0] = -(FEx - FWx) * idx - (GNx - GSx) * idy - g * h0x * dEx * idx;
@@ -600,10 +622,13 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
     float out[9];
     if (STAGE == 1) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) out[k] = m[k] + dt * L[k];
-      wetdry32(out, z0, z1x, z1y, zE, zW, zN, zS, tol);
+      for (int k = 1; k < 9; ++k) out[k] = m[k] + dt * L[k];
+      float olo;
+      two_sum(m[E0], mlo + dt * L[E0], out[E0], olo);
+      wetdry32(out, olo, z0, z1x, z1y, zE, zW, zN, zS, tol);
 #pragma unroll
       for (int k = 0; k < 9; ++k) d.T[k * P + c] = out[k];
+      d.T[E0L * P + c] = olo;
       if (LL) {
         d.Q[0 * P + c] = m[E1X]; d.Q[1 * P + c] = m[E1Y];
         d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
@@ -622,13 +647,26 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
         un[QY1X] = d.S[QY1X * P + c]; un[QY1Y] = d.S[QY1Y * P + c];
       }
 #pragma unroll
-      for (int k = 0; k < 9; ++k) out[k] = 0.5f * (un[k] + m[k] + dt * L[k]);
-      wetdry32(out, z0, z1x, z1y, zE, zW, zN, zS, tol);
+      for (int k = 1; k < 9; ++k) out[k] = 0.5f * (un[k] + m[k] + dt * L[k]);
+      // (Un + U1 + dt L) / 2 for the pair: TwoSum of the high parts, the rest added to
+      // the error term, renormalised, halved exactly
+      float olo;
+      {
+        float s1, e1, r1, e2;
+        two_sum(un[E0], m[E0], s1, e1);
+        e1 += (d.S[E0L * P + c] + mlo) + dt * L[E0];
+        two_sum(s1, e1, r1, e2);
+        out[E0] = 0.5f * r1;
+        olo = 0.5f * e2;
+      }
+      wetdry32(out, olo, z0, z1x, z1y, zE, zW, zN, zS, tol);
 #pragma unroll
       for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
-      lam = rate32(d, out[E0] - z0, out[QX0], out[QY0]);
-      bad = !(isfinite(out[E0]) && isfinite(out[QX0]) && isfinite(out[QY0]));
-      nonq = !(out[E0] - z0 <= tol) || out[E1X] != z1x || out[E1Y] != z1y;
+      d.S[E0L * P + c] = olo;
+      const float h0n = (out[E0] - z0) + olo;
+      lam = rate32(d, h0n, out[QX0], out[QY0]);
+      bad = !(isfinite(out[E0]) && isfinite(olo) && isfinite(out[QX0]) && isfinite(out[QY0]));
+      nonq = !(h0n <= tol) || out[E1X] != z1x || out[E1Y] != z1y;
 #pragma unroll
       for (int k = 3; k < 9; ++k) nonq = nonq || out[k] != 0.f;
     }
@@ -641,9 +679,11 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
   if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
   if (STAGE == 1) return;
 
-  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
-  const int any_nonq = __syncthreads_or(nonq);
-  if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
+  if (mode == 1) {
+    if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+    const int any_nonq = __syncthreads_or(nonq);
+    if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
+  }
   const double bl = mode == 1 ? (double)block_max_f<TX * TY>(lam, sm.redf) : 0.0;
   __shared__ bool last;
   if (tx == 0 && ty == 0) {
@@ -687,7 +727,8 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
           const int gi = (int)(gc % d.pitch), gj = (int)(gc / d.pitch);
           float gz0, gz1x, gz1y, a, b, e, f;
           cell_z(d, gi, gj, gz0, gz1x, gz1y, a, b, e, f);
-          const double h = (double)(__ldcg(&d.S[gc]) - gz0) +
+          const double h = ((double)__ldcg(&d.S[gc]) - (double)gz0) +
+                           (double)__ldcg(&d.S[E0L * P + gc]) +
                            d.g_xi[k] * (double)(__ldcg(&d.S[P + gc]) - gz1x) +
                            d.g_eta[k] * (double)(__ldcg(&d.S[2 * P + gc]) - gz1y);
           d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
@@ -715,7 +756,7 @@ __global__ void __launch_bounds__(256) rate32_kernel(D32 d) {
     const long long P = d.plane, c = (long long)j * d.pitch + i;
     float z0, z1x, z1y, zE, zW, zN, zS;
     cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-    lam = (double)rate32(d, d.S[c] - z0, d.S[QX0 * P + c], d.S[QY0 * P + c]);
+    lam = (double)rate32(d, (d.S[c] - z0) + d.S[E0L * P + c], d.S[QX0 * P + c], d.S[QY0 * P + c]);
   }
   const double bl = block_max<256>(lam, red);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -743,7 +784,8 @@ __global__ void __launch_bounds__(256) mass32_kernel(D32 d) {
   if (i < d.nx && j < d.ny) {
     float z0, z1x, z1y, zE, zW, zN, zS;
     cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-    v = (double)d.S[(long long)j * d.pitch + i] - (double)z0;
+    const long long c = (long long)j * d.pitch + i;
+    v = ((double)d.S[c] - (double)z0) + (double)d.S[E0L * d.plane + c];
   }
   const double s = block_sum<256>(v, red);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;

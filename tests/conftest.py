@@ -17,6 +17,7 @@ def pytest_configure(config):
 def make_oracle(case, limiter=False, **kw):
     """Oracle problem built from an inputs.Case (test helper)."""
     import oracle
+    kw.setdefault("dt_max", case.dt_max)
     o = oracle.Oracle(case.nx, case.ny, case.dx, case.dy, cfl=case.cfl, limiter=limiter, bc=case.bc,
                       **kw)
     o.set_dem(case.z_corner, case.manning, case.n_uniform, case.eta_corner)

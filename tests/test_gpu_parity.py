@@ -206,3 +206,13 @@ def test_bad_arguments_are_rejected_on_the_host():
         B.dg2_set_bc_inflow(ctx, 0, 100.0, 5.0, [0.0, 1.0], [1.0, 1.0])   # segment off the edge
     assert e.value.code == B.DG2_E_ARG
     B.dg2_destroy(ctx)
+
+
+@pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
+def test_urban_recipe_small(limiter):
+    """The urban recipe (buildings, roads, rain, point inflow) on a 192 x 160 grid."""
+    case = inputs.urban(nx=192, ny=160, dx=0.5, nblocks=30)
+    s, o, _, _ = run_pair(case, limiter, 100)
+    assert plane_err(s.state(), o.state()).max() <= TOL
+    m, led = s.mass()
+    assert abs(m - led) <= 1e-12 * m
