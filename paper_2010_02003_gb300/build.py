@@ -12,7 +12,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "dg2_api.cu"), os.path.join(HERE, "csrc", "dg2_noalloc.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "dg2_device.cuh"), os.path.join(ROOT, "include", "dg2.h")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("dg2_device.cuh", "dg2_fs32.cuh")] + [
+    os.path.join(ROOT, "include", "dg2.h")]
 LIB = os.path.join(HERE, "libdg2.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

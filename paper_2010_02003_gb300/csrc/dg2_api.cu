@@ -54,7 +54,7 @@ struct Layout {
   long long plane;
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
   size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, off_tforced,
-      total;
+      off_tlist, off_tfront, total;
   int nblocks, mblocks;
 };
 
@@ -100,6 +100,8 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   L.off_tflag = take((size_t)L.nblocks);
   L.off_tact = take((size_t)L.nblocks);
   L.off_tforced = take((size_t)L.nblocks);
+  L.off_tlist = take((size_t)L.nblocks * sizeof(int));
+  L.off_tfront = take((size_t)L.nblocks * sizeof(int));
   L.total = o;
   return true;
 }
@@ -122,6 +124,8 @@ struct dg2_ctx {
   int dem_set;
   int64_t launches;
   dim3 sgrid, sblock, pgrid, pblock;
+  int g_fric, g_st1, g_st2;   // persistent grid sizes (blocks) of friction / stage 1 / stage 2
+  dim3 lgrid, lblock;          // lists_kernel: one thread per tile
   std::vector<double> kt, kq;   // host copies of the knot tables
   // run_to graphs of 16 << k steps, k = 0..6 (dropped when the launch setup changes)
   cudaGraphExec_t graph[7];
@@ -149,6 +153,19 @@ void drop_graph(dg2_ctx* c) {
 
 constexpr int kMaxTimedSteps = 8192;
 
+// End of step (time, ledger, gauges, next dt) and the next step's tile lists
+// (2 kernels); with lists_only, just the lists (after a new DEM / state /
+// forced mask).
+void launch_finalize(dg2_ctx* c, int lists_only) {
+  if (c->fp32) {
+    dg2::f32::finalize32_kernel<<<1, dg2::kFinThreads, 0, c->st>>>(c->f, lists_only);
+    dg2::lists_kernel<<<c->lgrid, c->lblock, 0, c->st>>>(c->f);
+  } else {
+    dg2::finalize_kernel<<<1, dg2::kFinThreads, 0, c->st>>>(c->d, lists_only);
+    dg2::lists_kernel<<<c->lgrid, c->lblock, 0, c->st>>>(c->d);
+  }
+}
+
 // Host-side mask of the tiles that must be computed whatever their state: the
 // tile holding the point source and the edge tiles whose faces an inflow
 // segment covers.  Rain marks every tile (all_forced).
@@ -175,7 +192,13 @@ int update_forced_tiles(dg2_ctx* c) {
     }
   }
   d.tiles.all_forced = d.rain != 0.0 ? 1 : 0;
+  c->f.tiles = d.tiles;
   CU(cudaMemcpyAsync((void*)d.tiles.forced, m.data(), m.size(), cudaMemcpyHostToDevice, c->st));
+  if (c->dem_set) {
+    launch_finalize(c, 1);   // the computed set depends on the forced mask
+    int r = launch_check(c, 2);
+    if (r) return r;
+  }
   CU(cudaStreamSynchronize(c->st));
   return DG2_OK;
 }
@@ -193,7 +216,7 @@ void mirror(dg2_ctx* c) {
   f.tiles = d.tiles;
 }
 
-// Enqueues one RK2 step: friction, stage 1, stage 2 (3 kernels).  With
+// Enqueues one RK2 step: friction, stage 1, stage 2, finalize, lists (5 kernels).  With
 // `timed`, records an event before and after each kernel.
 void enqueue_step(dg2_ctx* c, bool timed = false) {
   const Dev& d = c->d;
@@ -210,26 +233,27 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   const bool ll = c->p.variant == DG2_LL;
   if (e) cudaEventRecord(e[0], c->st);
   if (c->fp32)
-    dg2::f32::friction32_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(c->f);
+    dg2::f32::friction32_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(c->f);
   else
-    dg2::friction_kernel<<<c->pgrid, c->pblock, 0, c->st>>>(d);
+    dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
   if (c->fp32) {
-    if (ll) dg2::f32::stage32_kernel<true, 1><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
-    else dg2::f32::stage32_kernel<false, 1><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
+    if (ll) dg2::f32::stage32_kernel<true, 1><<<c->g_st1, c->sblock, 0, c->st>>>(c->f);
+    else dg2::f32::stage32_kernel<false, 1><<<c->g_st1, c->sblock, 0, c->st>>>(c->f);
   } else {
-    if (ll) dg2::stage_kernel<true, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
-    else dg2::stage_kernel<false, 1><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+    if (ll) dg2::stage_kernel<true, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
+    else dg2::stage_kernel<false, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
   }
   if (e) cudaEventRecord(e[2], c->st);
   if (c->fp32) {
-    if (ll) dg2::f32::stage32_kernel<true, 2><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
-    else dg2::f32::stage32_kernel<false, 2><<<c->sgrid, c->sblock, 0, c->st>>>(c->f);
+    if (ll) dg2::f32::stage32_kernel<true, 2><<<c->g_st2, c->sblock, 0, c->st>>>(c->f);
+    else dg2::f32::stage32_kernel<false, 2><<<c->g_st2, c->sblock, 0, c->st>>>(c->f);
   } else {
-    if (ll) dg2::stage_kernel<true, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
-    else dg2::stage_kernel<false, 2><<<c->sgrid, c->sblock, 0, c->st>>>(d);
+    if (ll) dg2::stage_kernel<true, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
+    else dg2::stage_kernel<false, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
   }
   if (e) cudaEventRecord(e[3], c->st);
+  launch_finalize(c, 0);
 }
 
 int read_scalars(dg2_ctx* c, Scalars* out) {
@@ -259,7 +283,8 @@ void launch_mass(dg2_ctx* c) {
 // (after a new DEM or state; the first stage 2 then sets the true flags).
 int reset_tiles(dg2_ctx* c) {
   CU(cudaMemsetAsync(c->d.tiles.flag, 1, (size_t)c->lay.nblocks, c->st));
-  return DG2_OK;
+  launch_finalize(c, 1);
+  return launch_check(c, 2);
 }
 
 int reset_ledger(dg2_ctx* c) {
@@ -395,6 +420,11 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.tiles.flag = (unsigned char*)(c->ws + L.off_tflag);
   d.tiles.act = (unsigned char*)(c->ws + L.off_tact);
   d.tiles.forced = (const unsigned char*)(c->ws + L.off_tforced);
+  d.tiles.list = (int*)(c->ws + L.off_tlist);
+  d.tiles.front = (int*)(c->ws + L.off_tfront);
+  d.tiles.ntx = (nx + dg2::TX - 1) / dg2::TX;
+  d.tiles.nty = (ny + dg2::TY - 1) / dg2::TY;
+  d.tiles.ntiles = d.tiles.ntx * d.tiles.nty;
   d.tiles.all_forced = 0;
   d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
   {
@@ -425,6 +455,42 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   c->sgrid = dim3((nx + dg2::TX - 1) / dg2::TX, (ny + dg2::TY - 1) / dg2::TY);
   c->pblock = dim3(32, 8);
   c->pgrid = dim3((nx + 31) / 32, (ny + 7) / 8);
+  {
+    // persistent grids: every resident block of the kernel, capped by the tile count
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const bool ll = p.variant == DG2_LL, f32 = p.precision == DG2_FP32;
+    int o0 = 1, o1 = 1, o2 = 1;
+    if (f32) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::f32::friction32_kernel, 256, 0);
+      if (ll) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::f32::stage32_kernel<true, 1>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::f32::stage32_kernel<true, 2>, 256, 0);
+      } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::f32::stage32_kernel<false, 1>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::f32::stage32_kernel<false, 2>, 256, 0);
+      }
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::friction_kernel, 256, 0);
+      if (ll) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::stage_kernel<true, 1>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::stage_kernel<true, 2>, 256, 0);
+      } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::stage_kernel<false, 1>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::stage_kernel<false, 2>, 256, 0);
+      }
+    }
+    cudaGetLastError();
+    const int nt = d.tiles.ntiles;
+    auto gsz = [&](int occ) { long long g = (long long)nsm * (occ > 0 ? occ : 1); return (int)(g < nt ? g : nt); };
+    c->lblock = dim3(dg2::LTX, dg2::LTY);
+    c->lgrid = dim3((d.tiles.ntx + dg2::LTX - 1) / dg2::LTX, (d.tiles.nty + dg2::LTY - 1) / dg2::LTY);
+    c->g_fric = gsz(o0);
+    const bool loop = f32 ? DG2_TILE_LOOP32 : DG2_TILE_LOOP64;
+    c->g_st1 = loop ? gsz(o1) : nt;
+    c->g_st2 = loop ? gsz(o2) : nt;
+  }
 
   // zero the state, topography and scalars; t_end / samples at +inf
   cudaError_t e = cudaMemsetAsync(c->ws, 0, L.total, c->st);
@@ -579,7 +645,7 @@ int dg2_step(dg2_ctx* c, double dt, double* dt_taken) {
   if (!std::isfinite(dt)) return fail(DG2_E_ARG, "dt must be finite");
   dg2::begin_step_kernel<<<1, 1, 0, c->st>>>(c->d, dt);
   enqueue_step(c, true);
-  if ((r = launch_check(c, 4))) return r;
+  if ((r = launch_check(c, 6))) return r;
   if (dt_taken) {
     Scalars s;
     if ((r = read_scalars(c, &s))) return r;
@@ -626,7 +692,7 @@ int dg2_run_to(dg2_ctx* c, double t_end, int64_t* steps_taken) {
       for (int k = 0; k < chunk; ++k) enqueue_step(c);
       if ((r = launch_check(c, 0))) return r;
     }
-    c->launches += 3 * (int64_t)chunk;
+    c->launches += 5 * (int64_t)chunk;
     if ((r = read_scalars(c, &s))) return r;
     if (s.nonfinite) return fail(DG2_E_NONFINITE, "non-finite state or step near t=%g", s.t);
     if (s.done) break;

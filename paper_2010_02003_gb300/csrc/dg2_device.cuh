@@ -60,6 +60,10 @@ struct Scalars {
   int pad;
   long long steps;     // completed steps (count of stage-2 finalisations)
   double last_dt;      // size of the last completed step
+  int n_act;           // tiles computed in the current step (entries of tiles.list)
+  int n_front;         // frontier tiles copied in stage 1 (entries of tiles.front)
+  int list_all;        // every tile is computed: list entry e is tile e
+  int skip_lists;      // the step was not taken (run already done): keep the lists
 };
 
 // Exact skipping of quiescent dry tiles.  A cell is quiescent when its depth
@@ -75,8 +79,11 @@ struct Scalars {
 // had been computed.
 struct Tiles {
   unsigned char* flag;          // [ntiles] tile held a non-quiescent cell after the last stage 2
-  unsigned char* act;           // [ntiles] tile computed in the current step (stage-1 decision)
+  unsigned char* act;           // [ntiles] tile computed in the current step
   const unsigned char* forced;  // [ntiles] tile must be computed (inflow, source); set on the host
+  int* list;                    // [ntiles] computed tiles of the step, ascending
+  int* front;                   // [ntiles] frontier tiles of the step (stage-1 copy), ascending
+  int ntx, nty, ntiles;         // tile grid
   int all_forced;               // every tile must be computed (rain)
   int skip;                     // 0: compute every tile
 };
@@ -440,36 +447,6 @@ __device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
   sc->lam_bits = 0ull;
 }
 
-// 1: compute the tile; 2 (stage 1 only): copy its state to the stage buffer
-// because a neighbouring tile is computed and reads it as halo; 0: nothing.
-// Called by every thread of warp 0 (lane t < 25 gathers the flags of one tile
-// of the 5 x 5 neighbourhood, in parallel); lane 0's result is the block's.
-template <int STAGE, class D>
-__device__ int tile_mode_warp(const D& d) {
-  const int bx = blockIdx.x, by = blockIdx.y, ntx = gridDim.x, nty = gridDim.y;
-  const int t = by * ntx + bx;
-  if (STAGE == 2) return (!d.tiles.skip || d.tiles.act[t]) ? 1 : 0;
-  const int lane = threadIdx.x;
-  if (!d.tiles.skip || d.tiles.all_forced) {
-    if (lane == 0) d.tiles.act[t] = 1;
-    return 1;
-  }
-  bool busy = false, inner = false;
-  if (lane < 25) {
-    const int ox = lane % 5 - 2, oy = lane / 5 - 2;
-    const int x = bx + ox, y = by + oy;
-    if (x >= 0 && y >= 0 && x < ntx && y < nty) {
-      const int q = y * ntx + x;
-      busy = (d.tiles.flag[q] | d.tiles.forced[q]) != 0;
-    }
-    inner = ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1;
-  }
-  const unsigned any = __ballot_sync(0xffffffffu, busy);
-  const unsigned act = __ballot_sync(0xffffffffu, busy && inner);
-  if (lane == 0) d.tiles.act[t] = act ? 1 : 0;
-  return act ? 1 : (any ? 2 : 0);
-}
-
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -526,13 +503,11 @@ __device__ __forceinline__ void friction_point(double gn2dt, double tol, double 
   qy = qy / den;
 }
 
-__global__ void __launch_bounds__(256) friction_kernel(Dev d) {
+// Friction on the cells of one 32 x 8 tile (threads 32 x 8).
+__device__ __forceinline__ void friction_tile(const Dev& d, int bx, int by) {
   const Scalars* sc = d.sc;
-  if (sc->done) return;
-  // a tile of quiescent cells has no water to rub (same 32 x 8 tiling as the stages)
-  if (d.tiles.skip && !d.tiles.flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = bx * TX + threadIdx.x;
+  const int j = by * TY + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
   const long long P = d.plane, c = (long long)j * d.pitch + i;
   const double n = d.N[c];
@@ -562,6 +537,18 @@ __global__ void __launch_bounds__(256) friction_kernel(Dev d) {
   S[QY1Y * P + c] = nq[1][1];
 }
 
+// Friction over the step's computed tiles (a quiescent tile has no water to rub).
+__global__ void __launch_bounds__(256) friction_kernel(Dev d) {
+  const Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int n_act = sc->n_act, ntx = d.tiles.ntx;
+  const bool all = sc->list_all != 0;
+  for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
+    const int tile = all ? e : d.tiles.list[e];
+    friction_tile(d, tile % ntx, tile / ntx);
+  }
+}
+
 // Loads the 9 coefficients of cell c from buffer U.
 __device__ __forceinline__ void load9(const double* __restrict__ U, long long P, long long c,
                                       double* m) {
@@ -581,13 +568,16 @@ struct StageSmem {
   double red[32];
 };
 
+// One RK stage on the 32 x 8 tile (bx, by): revised limits, one HLL flux per
+// face, Eqs. 4-5, the stage update and the wet-dry treatment.  Accumulates the
+// boundary inflow rate, the Courant rate and the non-finite / non-quiescent
+// flags of the thread's cell into the caller's variables.
 template <bool LL, int STAGE>
-__global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
-  __shared__ StageSmem sm;
+__device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, int by,
+                                           double& brate, double& lam, bool& bad, bool& nonq) {
   Scalars* sc = d.sc;
-  if (sc->done) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * TX + tx, j = blockIdx.y * TY + ty;
+  const int i = bx * TX + tx, j = by * TY + ty;
   const bool act = i < d.nx && j < d.ny;
   const long long P = d.plane;
   const long long c = (long long)j * d.pitch + i;
@@ -597,22 +587,6 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
   const double g = d.g, tol = d.tol;
   const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
   const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
-
-  __shared__ int s_mode;
-  if (ty == 0) {
-    const int md = tile_mode_warp<STAGE>(d);
-    if (tx == 0) s_mode = md;
-  }
-  __syncthreads();
-  const int mode = s_mode;
-  double brate = 0.0;  // water entering through domain-edge faces (m^3/s)
-  double lam = 0.0;
-  bool bad = false, nonq = false;
-  if (STAGE == 1 && mode == 2 && act) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) d.T[k * P + c] = d.S[k * P + c];
-  }
-  if (mode == 1) {
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
   Lim Es, Ws, Ns, Ss;
@@ -785,85 +759,265 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(Dev d) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
       lam = cell_rate(d, out[H0], out[QX0], out[QY0]);
-      bad = !(isfinite(out[H0]) && isfinite(out[QX0]) && isfinite(out[QY0])) || out[H0] < -1.0;
+      bad = bad || !(isfinite(out[H0]) && isfinite(out[QX0]) && isfinite(out[QY0])) ||
+            out[H0] < -1.0;
       nonq = !(out[H0] <= tol);
 #pragma unroll
       for (int k = 1; k < 9; ++k) nonq = nonq || out[k] != 0.0;
     }
   }
-  }  // mode == 1
+}
 
-  // per-block boundary mass rate (fixed slot per block: deterministic sums);
-  // only computed tiles on the domain edge have boundary faces
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  const bool edge_block = blockIdx.x == 0 || blockIdx.y == 0 || blockIdx.x == gridDim.x - 1 ||
-                          blockIdx.y == gridDim.y - 1;
-  const double bsum = (edge_block && mode == 1) ? block_sum<TX * TY>(brate, sm.red) : 0.0;
-  if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
-  if (STAGE == 1) return;
+// Work distribution of the stage kernels over the step's tile lists:
+// DG2_TILE_LOOPxx 1 runs a fixed grid of resident blocks that loop over the
+// entries; 0 launches one block per tile of the grid and a block takes the
+// entry of its own index (blocks past the lists exit at once, and the
+// hardware balances tiles of unequal cost over the SMs).  Measured on the
+// 2000 x 1000 floodplain: FP64 tiles (tens of microseconds each, 1-2 blocks
+// per SM) run faster one per block, FP32 tiles faster in resident loops.
+#ifndef DG2_TILE_LOOP64
+#define DG2_TILE_LOOP64 0
+#endif
+#ifndef DG2_TILE_LOOP32
+#define DG2_TILE_LOOP32 1
+#endif
+// minimum resident blocks per SM asked of the register allocator: 2 for the
+// FP64 DG2-NL stage (128 registers, no spills), 1 for DG2-LL (whose ~170
+// registers spill at 128), 3 for the FP32 stages (80 registers)
+#ifndef DG2_MINB64_NL
+#define DG2_MINB64_NL 2
+#endif
+#ifndef DG2_MINB64_LL
+#define DG2_MINB64_LL 1
+#endif
+#ifndef DG2_MINB32
+#define DG2_MINB32 3
+#endif
 
-  if (mode == 1) {
-    if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
-    const int any_nonq = __syncthreads_or(nonq);
-    if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
+// Stage kernels run over the step's list of active tiles (and, in stage 1,
+// the frontier tiles that only copy their state for a neighbour's halo),
+// built at the end of the previous step.
+template <bool LL, int STAGE>
+__global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64_NL) stage_kernel(Dev d) {
+  __shared__ StageSmem sm;
+  Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int ntx = d.tiles.ntx;
+  const int n_act = sc->n_act;
+  const bool all = sc->list_all != 0;
+  double lam = 0.0;
+  bool bad = false;
+#if DG2_TILE_LOOP64
+  for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
+#else
+  if (STAGE == 2 && (int)blockIdx.x >= n_act) return;
+  for (int e = blockIdx.x; e < n_act; e = n_act) {
+#endif
+    const int tile = all ? e : d.tiles.list[e];
+    const int bx = tile % ntx, by = tile / ntx;
+    double brate = 0.0, lam_t = 0.0;
+    bool nonq = false;
+    stage_tile<LL, STAGE>(d, sm, bx, by, brate, lam_t, bad, nonq);
+    lam = fmax(lam, lam_t);
+    // boundary inflow rate of an edge tile, kept per tile (summed in tile order later)
+    if (bx == 0 || by == 0 || bx == ntx - 1 || by == d.tiles.nty - 1) {
+      const double bsum = block_sum<TX * TY>(brate, sm.red);
+      if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.tiles.ntiles + tile] = bsum;
+    }
+    if (STAGE == 2) {
+      const int any_nonq = __syncthreads_or(nonq);
+      if (tx == 0 && ty == 0) d.tiles.flag[tile] = any_nonq ? 1 : 0;
+    }
+    __syncthreads();
   }
-  const double bl = mode == 1 ? block_max<TX * TY>(lam, sm.red) : 0.0;
-  __shared__ bool last;
-  if (tx == 0 && ty == 0) {
-    if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
-    __threadfence();
-    const unsigned int k = atomicAdd(&sc->count, 1u);
-    last = (k == (unsigned int)d.nblocks - 1);
+  if (STAGE == 1) {
+    // frontier tiles: a computed neighbour reads their stage state as halo
+    const int n_front = sc->n_front;
+    const long long P = d.plane;
+#if DG2_TILE_LOOP64
+    for (int e = blockIdx.x; e < n_front; e += gridDim.x) {
+#else
+    for (int e = (int)blockIdx.x - n_act; e >= 0 && e < n_front; e = n_front) {
+#endif
+      const int tile = d.tiles.front[e];
+      const int i = (tile % ntx) * TX + tx, j = (tile / ntx) * TY + ty;
+      if (i < d.nx && j < d.ny) {
+        const long long c = (long long)j * d.pitch + i;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) d.T[k * P + c] = d.S[k * P + c];
+      }
+    }
+    return;
+  }
+  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+  const double bl = block_max<TX * TY>(lam, sm.red);
+  if (tx == 0 && ty == 0 && bl > 0.0)
+    atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
+}
+
+// ---------------------------------------------------------------------------
+// End of step: one block of kFinThreads threads
+// ---------------------------------------------------------------------------
+constexpr int kFinThreads = 1024;
+
+// Builds the next step's tile lists from the non-quiescence flags and the
+// forced mask: a tile is computed if its 3 x 3 tile neighbourhood holds a
+// flagged or forced tile; a tile that is not computed but has one in its 5 x 5
+// neighbourhood copies its state in stage 1 (a computed neighbour reads it).
+// One thread per tile, LTX x LTY tiles per block staged with a 2-tile halo in
+// shared memory; one atomic per block reserves its list range.  The order of
+// the list entries is not fixed, but every tile writes only its own cells,
+// bpart slot and flag, and the step's reductions are exact (max) or summed
+// per tile in a fixed order, so the step's result does not depend on it.
+constexpr int LTX = 32, LTY = 8;
+template <class D>
+__global__ void __launch_bounds__(LTX* LTY) lists_kernel(D d) {
+  Scalars* sc = d.sc;
+  if (sc->skip_lists) return;
+  const Tiles& T = d.tiles;
+  const int ntx = T.ntx, nty = T.nty;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * LTX + tx;
+  const int bx = blockIdx.x * LTX + tx, by = blockIdx.y * LTY + ty;
+  const bool in = bx < ntx && by < nty;
+  const int t = by * ntx + bx;
+  if (!T.skip || T.all_forced) {
+    if (in) T.act[t] = 1;
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+      sc->n_act = T.ntiles;
+      sc->n_front = 0;
+      sc->list_all = 1;
+    }
+    return;
+  }
+  __shared__ unsigned char busy[LTY + 4][LTX + 4];
+  __shared__ int wa[LTY], wf[LTY], base[2];
+  for (int k = tid; k < (LTY + 4) * (LTX + 4); k += LTX * LTY) {
+    const int ly = k / (LTX + 4), lx = k % (LTX + 4);
+    const int gx = blockIdx.x * LTX + lx - 2, gy = blockIdx.y * LTY + ly - 2;
+    unsigned char v = 0;
+    if (gx >= 0 && gy >= 0 && gx < ntx && gy < nty) {
+      const int q = gy * ntx + gx;
+      v = (T.flag[q] | T.forced[q]) != 0;
+    }
+    busy[ly][lx] = v;
   }
   __syncthreads();
-  if (!last) return;
-  __threadfence();
-
-  // ---- last block: time, ledger, gauges, next step ----
-  const int tid = ty * TX + tx;
-  double part = 0.0;
-  for (int k = tid; k < d.nblocks; k += TX * TY)
-    part += __ldcg(&d.bpart[k]) + __ldcg(&d.bpart[d.nblocks + k]);
-  const double btot = block_sum<TX * TY>(part, sm.red);
-  if (tid == 0) {
-    const double t = sc->t;
-    double src1 = 0.0, src2 = 0.0;
-    const double area = d.dx * d.dy * (double)d.nx * (double)d.ny;
-    if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
-    if (d.rain != 0.0 && t + dt >= d.rain_t0 && t + dt < d.rain_t1) src2 += d.rain * area;
-    if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
-    sc->ledger += dt * 0.5 * (btot + src1 + src2);
-    double tn;
-    bool at_sample = false;
-    if (sc->land && !sc->fixed_dt) {
-      double target = sc->t_end;
-      if (sc->next_sample <= target) { target = sc->next_sample; at_sample = true; }
-      tn = target;
-    } else {
-      tn = t + dt;
-    }
-    sc->t = tn;
-    if (at_sample) {
-      const int r = sc->nsamp;
-      if (r < d.max_samples) {
-        d.samp_t[r] = tn;
-        for (int k = 0; k < d.ngauge; ++k) {
-          const long long gc = d.g_idx[k];
-          const double h = __ldcg(&d.S[gc]) + d.g_xi[k] * __ldcg(&d.S[P + gc]) +
-                           d.g_eta[k] * __ldcg(&d.S[2 * P + gc]);
-          d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
-        }
+  bool a = false, f = false;
+  if (in) {
+#pragma unroll
+    for (int oy = -2; oy <= 2; ++oy)
+#pragma unroll
+      for (int ox = -2; ox <= 2; ++ox) {
+        if (!busy[ty + 2 + oy][tx + 2 + ox]) continue;
+        if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1) a = true;
+        else f = true;
       }
-      sc->nsamp = r + 1;
-      sc->next_sample += sc->sample_every;
-    }
-    if (!(dt > 0.0) || !isfinite(tn)) sc->nonfinite = 1;
-    sc->steps += 1;
-    sc->last_dt = dt;
-    schedule_next_dt(d, sc, __longlong_as_double((long long)atomicAdd(&sc->lam_bits, 0ull)));
-    if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
-    sc->count = 0u;
+    if (a) f = false;
+    T.act[t] = a ? 1 : 0;
   }
+  // warp = one row of LTX tiles: ballot prefix in the warp, warp offsets, one atomic
+  const unsigned ba = __ballot_sync(0xffffffffu, a), bf = __ballot_sync(0xffffffffu, f);
+  const int lane = tid & 31;
+  if (lane == 0) { wa[ty] = __popc(ba); wf[ty] = __popc(bf); }
+  __syncthreads();
+  if (tid == 0) {
+    int sa = 0, sf = 0;
+    for (int w = 0; w < LTY; ++w) {
+      const int xa = wa[w], xf = wf[w];
+      wa[w] = sa; sa += xa;
+      wf[w] = sf; sf += xf;
+    }
+    base[0] = sa ? atomicAdd(&sc->n_act, sa) : 0;
+    base[1] = sf ? atomicAdd(&sc->n_front, sf) : 0;
+  }
+  __syncthreads();
+  const unsigned below = (1u << lane) - 1u;
+  if (a) T.list[base[0] + wa[ty] + __popc(ba & below)] = t;
+  if (f) T.front[base[1] + wf[ty] + __popc(bf & below)] = t;
+}
+
+// Resets the list counters for lists_kernel (thread 0 of the finalize block).
+__device__ __forceinline__ void open_lists(Scalars* sc) {
+  sc->n_act = 0;
+  sc->n_front = 0;
+  sc->list_all = 0;
+  sc->skip_lists = 0;
+}
+
+// Sum over the boundary ring of tiles, in a fixed order, of the per-tile
+// boundary inflow rates of both stages (only tiles computed this step).
+template <class D>
+__device__ double ring_inflow(const D& d) {
+  __shared__ double red[32];
+  const Tiles& T = d.tiles;
+  const int ntx = T.ntx, nty = T.nty, nt = T.ntiles;
+  const int nring = nty == 1 ? ntx : (ntx == 1 ? nty : 2 * ntx + 2 * (nty - 2));
+  double part = 0.0;
+  for (int k = threadIdx.x; k < nring; k += kFinThreads) {
+    int t;
+    if (nty == 1) t = k;
+    else if (ntx == 1) t = k * ntx;
+    else if (k < ntx) t = k;                                       // south row
+    else if (k < 2 * ntx) t = (nty - 1) * ntx + (k - ntx);         // north row
+    else if (k < 2 * ntx + nty - 2) t = (k - 2 * ntx + 1) * ntx;   // west column
+    else t = (k - 2 * ntx - nty + 3) * ntx + ntx - 1;              // east column
+    if (T.act[t]) part += d.bpart[t] + d.bpart[nt + t];
+  }
+  return block_sum<kFinThreads>(part, red);
+}
+
+// Time, ledger, gauges and the next step; opens the next step's tile lists
+// (built by lists_kernel).  `lists_only`: after a new DEM / state / forced
+// mask, only open the lists.
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(Dev d, int lists_only) {
+  Scalars* sc = d.sc;
+  if (!lists_only) {
+    if (sc->done) {
+      if (threadIdx.x == 0) sc->skip_lists = 1;
+      return;
+    }
+    const double btot = ring_inflow(d);
+    if (threadIdx.x == 0) {
+      const double t = sc->t, dt = sc->dt;
+      double src1 = 0.0, src2 = 0.0;
+      const double area = d.dx * d.dy * (double)d.nx * (double)d.ny;
+      if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
+      if (d.rain != 0.0 && t + dt >= d.rain_t0 && t + dt < d.rain_t1) src2 += d.rain * area;
+      if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
+      sc->ledger += dt * 0.5 * (btot + src1 + src2);
+      double tn;
+      bool at_sample = false;
+      if (sc->land && !sc->fixed_dt) {
+        double target = sc->t_end;
+        if (sc->next_sample <= target) { target = sc->next_sample; at_sample = true; }
+        tn = target;
+      } else {
+        tn = t + dt;
+      }
+      sc->t = tn;
+      if (at_sample) {
+        const int r = sc->nsamp;
+        if (r < d.max_samples) {
+          d.samp_t[r] = tn;
+          const long long P = d.plane;
+          for (int k = 0; k < d.ngauge; ++k) {
+            const long long gc = d.g_idx[k];
+            const double h = d.S[gc] + d.g_xi[k] * d.S[P + gc] + d.g_eta[k] * d.S[2 * P + gc];
+            d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
+          }
+        }
+        sc->nsamp = r + 1;
+        sc->next_sample += sc->sample_every;
+      }
+      if (!(dt > 0.0) || !isfinite(tn)) sc->nonfinite = 1;
+      sc->steps += 1;
+      sc->last_dt = dt;
+      schedule_next_dt(d, sc, __longlong_as_double((long long)sc->lam_bits));
+      if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
+    }
+  }
+  if (threadIdx.x == 0) open_lists(sc);
 }
 
 // Courant reduction of the current state alone (after set-up or set_state).

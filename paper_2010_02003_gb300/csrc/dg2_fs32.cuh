@@ -371,12 +371,9 @@ __device__ __forceinline__ void friction_point32(float gn2dt, float tol, float h
   qy = qy / den;
 }
 
-__global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
-  const Scalars* sc = d.sc;
-  if (sc->done) return;
-  if (d.tiles.skip && !d.tiles.flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void friction32_tile(const D32& d, float gdt, int bx, int by) {
+  const int i = bx * TX + threadIdx.x;
+  const int j = by * TY + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
   const long long P = d.plane, c = (long long)j * d.pitch + i;
   const float n = d.N[c];
@@ -395,7 +392,7 @@ __global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
     }
     if (!any) return;
   }
-  const float gn2dt = (float)(sc->dt * (double)d.g) * n * n;
+  const float gn2dt = gdt * n * n;
   const float x0 = S[QX0 * P + c], y0 = S[QY0 * P + c];
   float cx = x0, cy = y0;
   friction_point32(gn2dt, d.tol, h0, cx, cy);
@@ -419,6 +416,21 @@ __global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
   S[QY1Y * P + c] = nq[1][1];
 }
 
+__global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
+  const Scalars* sc = d.sc;
+  if (sc->done) return;
+  __shared__ float s_gdt;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_gdt = (float)(sc->dt * (double)d.g);
+  __syncthreads();
+  const float gdt = s_gdt;
+  const int n_act = sc->n_act, ntx = d.tiles.ntx;
+  const bool all = sc->list_all != 0;
+  for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
+    const int tile = all ? e : d.tiles.list[e];
+    friction32_tile(d, gdt, tile % ntx, tile / ntx);
+  }
+}
+
 struct StageSmem32 {
   LimF e[TY][TX];
   LimF n[TY][TX];
@@ -429,13 +441,20 @@ struct StageSmem32 {
   float redf[32];
 };
 
+// One RK stage of the FP32 free-surface form on the tile (bx, by).  `blk`
+// carries the per-block constants (dt, stage time, rain flag) read once.
+struct Blk32 {
+  float dt, rainf;
+  double dtd, ts;
+  int rain;
+};
+
 template <bool LL, int STAGE>
-__global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
-  __shared__ StageSmem32 sm;
-  Scalars* sc = d.sc;
-  if (sc->done) return;
+__device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32& sm, const Blk32& blk,
+                                             int bx, int by, float& brate, float& lam, bool& bad,
+                                             bool& nonq) {
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * TX + tx, j = blockIdx.y * TY + ty;
+  const int i = bx * TX + tx, j = by * TY + ty;
   const bool act = i < d.nx && j < d.ny;
   const long long P = d.plane;
   const long long c = (long long)j * d.pitch + i;
@@ -443,39 +462,10 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
   const float g = d.g, tol = d.tol;
   const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
   const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
-  // FP64 work happens once per block here, never per cell: on this part one
-  // FP64 operation costs the issue slots of 64 FP32 operations
-  const bool edge_block = blockIdx.x == 0 || blockIdx.y == 0 || blockIdx.x == gridDim.x - 1 ||
-                          blockIdx.y == gridDim.y - 1;
-
-  __shared__ int s_mode, s_rain;
-  __shared__ float s_dt, s_rainf;
-  __shared__ double s_dtd, s_ts;
-  if (ty == 0) {
-    const int md = tile_mode_warp<STAGE>(d);
-    if (tx == 0) s_mode = md;
-  }
-  if (tx == 0 && ty == 0) {
-    const double dtd0 = sc->dt;
-    const double ts0 = STAGE == 1 ? sc->t : sc->t + dtd0;
-    s_dtd = dtd0;
-    s_ts = ts0;
-    s_dt = (float)dtd0;
-    s_rain = d.rain != 0.0 && ts0 >= d.rain_t0 && ts0 < d.rain_t1;
-    s_rainf = (float)d.rain;
-  }
-  __syncthreads();
-  const int mode = s_mode;
-  const float dt = s_dt;
-  const double dtd = s_dtd, ts = s_ts;
-  float brate = 0.f;  // water entering through domain-edge faces (m^3/s), FP32 per cell
-  float lam = 0.f;
-  bool bad = false, nonq = false;
-  if (STAGE == 1 && mode == 2 && act) {
-#pragma unroll
-    for (int k = 0; k < kPlanes32; ++k) d.T[k * P + c] = d.S[k * P + c];
-  }
-  if (mode == 1) {
+  const float dt = blk.dt;
+  const double ts = blk.ts;
+  const bool s_rain = blk.rain != 0;
+  const float s_rainf = blk.rainf;
   float m[9];
   float z0 = 0.f, z1x = 0.f, z1y = 0.f, zE = 0.f, zW = 0.f, zN = 0.f, zS = 0.f;
   LimF Es, Ws, Ns, Ss;
@@ -665,85 +655,139 @@ __global__ void __launch_bounds__(TX* TY) stage32_kernel(D32 d) {
       d.S[E0L * P + c] = olo;
       const float h0n = (out[E0] - z0) + olo;
       lam = rate32(d, h0n, out[QX0], out[QY0]);
-      bad = !(isfinite(out[E0]) && isfinite(olo) && isfinite(out[QX0]) && isfinite(out[QY0]));
+      bad = bad || !(isfinite(out[E0]) && isfinite(olo) && isfinite(out[QX0]) &&
+                     isfinite(out[QY0]));
       nonq = !(h0n <= tol) || out[E1X] != z1x || out[E1Y] != z1y;
 #pragma unroll
       for (int k = 3; k < 9; ++k) nonq = nonq || out[k] != 0.f;
     }
   }
-  }  // mode == 1
+}
 
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  // only blocks on the domain edge have boundary faces (block-uniform branch)
-  const double bsum = (edge_block && mode == 1) ? block_sum<TX * TY>((double)brate, sm.red) : 0.0;
-  if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.nblocks + bid] = bsum;
-  if (STAGE == 1) return;
-
-  if (mode == 1) {
-    if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
-    const int any_nonq = __syncthreads_or(nonq);
-    if (tx == 0 && ty == 0) d.tiles.flag[bid] = any_nonq ? 1 : 0;
-  }
-  const double bl = mode == 1 ? (double)block_max_f<TX * TY>(lam, sm.redf) : 0.0;
-  __shared__ bool last;
+template <bool LL, int STAGE>
+__global__ void __launch_bounds__(TX* TY, DG2_MINB32) stage32_kernel(D32 d) {
+  __shared__ StageSmem32 sm;
+  __shared__ Blk32 blk;
+  Scalars* sc = d.sc;
+  if (sc->done) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  // FP64 work happens once per block, never per cell: on this part one FP64
+  // operation costs the issue slots of 64 FP32 operations
   if (tx == 0 && ty == 0) {
-    if (bl > 0.0) atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
-    __threadfence();
-    const unsigned int k = atomicAdd(&sc->count, 1u);
-    last = (k == (unsigned int)d.nblocks - 1);
+    const double dtd0 = sc->dt;
+    const double ts0 = STAGE == 1 ? sc->t : sc->t + dtd0;
+    blk.dtd = dtd0;
+    blk.ts = ts0;
+    blk.dt = (float)dtd0;
+    blk.rain = d.rain != 0.0 && ts0 >= d.rain_t0 && ts0 < d.rain_t1;
+    blk.rainf = (float)d.rain;
   }
   __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const int tid = ty * TX + tx;
-  double part = 0.0;
-  for (int k = tid; k < d.nblocks; k += TX * TY)
-    part += __ldcg(&d.bpart[k]) + __ldcg(&d.bpart[d.nblocks + k]);
-  const double btot = block_sum<TX * TY>(part, sm.red);
-  if (tid == 0) {
-    const double t = sc->t;
-    double src1 = 0.0, src2 = 0.0;
-    const double area = d.dxd * d.dyd * (double)d.nx * (double)d.ny;
-    if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
-    if (d.rain != 0.0 && t + dtd >= d.rain_t0 && t + dtd < d.rain_t1) src2 += d.rain * area;
-    if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
-    sc->ledger += dtd * 0.5 * (btot + src1 + src2);
-    double tn;
-    bool at_sample = false;
-    if (sc->land && !sc->fixed_dt) {
-      double target = sc->t_end;
-      if (sc->next_sample <= target) { target = sc->next_sample; at_sample = true; }
-      tn = target;
-    } else {
-      tn = t + dtd;
+  const int ntx = d.tiles.ntx, nty = d.tiles.nty;
+  const int n_act = sc->n_act;
+  const bool all = sc->list_all != 0;
+  float lam = 0.f;
+  bool bad = false;
+#if DG2_TILE_LOOP32
+  for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
+#else
+  if (STAGE == 2 && (int)blockIdx.x >= n_act) return;
+  for (int e = blockIdx.x; e < n_act; e = n_act) {
+#endif
+    const int tile = all ? e : d.tiles.list[e];
+    const int bx = tile % ntx, by = tile / ntx;
+    float brate = 0.f, lam_t = 0.f;
+    bool nonq = false;
+    stage32_tile<LL, STAGE>(d, sm, blk, bx, by, brate, lam_t, bad, nonq);
+    lam = fmaxf(lam, lam_t);
+    if (bx == 0 || by == 0 || bx == ntx - 1 || by == nty - 1) {
+      const double bsum = block_sum<TX * TY>((double)brate, sm.red);
+      if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.tiles.ntiles + tile] = bsum;
     }
-    sc->t = tn;
-    if (at_sample) {
-      const int r = sc->nsamp;
-      if (r < d.max_samples) {
-        d.samp_t[r] = tn;
-        for (int k = 0; k < d.ngauge; ++k) {
-          const long long gc = d.g_idx[k];
-          const int gi = (int)(gc % d.pitch), gj = (int)(gc / d.pitch);
-          float gz0, gz1x, gz1y, a, b, e, f;
-          cell_z(d, gi, gj, gz0, gz1x, gz1y, a, b, e, f);
-          const double h = ((double)__ldcg(&d.S[gc]) - (double)gz0) +
-                           (double)__ldcg(&d.S[E0L * P + gc]) +
-                           d.g_xi[k] * (double)(__ldcg(&d.S[P + gc]) - gz1x) +
-                           d.g_eta[k] * (double)(__ldcg(&d.S[2 * P + gc]) - gz1y);
-          d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
-        }
-      }
-      sc->nsamp = r + 1;
-      sc->next_sample += sc->sample_every;
+    if (STAGE == 2) {
+      const int any_nonq = __syncthreads_or(nonq);
+      if (tx == 0 && ty == 0) d.tiles.flag[tile] = any_nonq ? 1 : 0;
     }
-    if (!(dtd > 0.0) || !isfinite(tn)) sc->nonfinite = 1;
-    sc->steps += 1;
-    sc->last_dt = dtd;
-    schedule32(d, sc, __longlong_as_double((long long)atomicAdd(&sc->lam_bits, 0ull)));
-    if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
-    sc->count = 0u;
+    __syncthreads();
   }
+  if (STAGE == 1) {
+    const int n_front = sc->n_front;
+    const long long P = d.plane;
+#if DG2_TILE_LOOP32
+    for (int e = blockIdx.x; e < n_front; e += gridDim.x) {
+#else
+    for (int e = (int)blockIdx.x - n_act; e >= 0 && e < n_front; e = n_front) {
+#endif
+      const int tile = d.tiles.front[e];
+      const int i = (tile % ntx) * TX + tx, j = (tile / ntx) * TY + ty;
+      if (i < d.nx && j < d.ny) {
+        const long long c = (long long)j * d.pitch + i;
+#pragma unroll
+        for (int k = 0; k < kPlanes32; ++k) d.T[k * P + c] = d.S[k * P + c];
+      }
+    }
+    return;
+  }
+  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
+  const double bl = (double)block_max_f<TX * TY>(lam, sm.redf);
+  if (tx == 0 && ty == 0 && bl > 0.0)
+    atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
+}
+
+// Time, ledger, gauges and the next step; opens the next step's tile lists.
+__global__ void __launch_bounds__(kFinThreads) finalize32_kernel(D32 d, int lists_only) {
+  Scalars* sc = d.sc;
+  if (!lists_only) {
+    if (sc->done) {
+      if (threadIdx.x == 0) sc->skip_lists = 1;
+      return;
+    }
+    const double btot = ring_inflow(d);
+    if (threadIdx.x == 0) {
+      const double t = sc->t, dt = sc->dt;
+      double src1 = 0.0, src2 = 0.0;
+      const double area = d.dxd * d.dyd * (double)d.nx * (double)d.ny;
+      if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
+      if (d.rain != 0.0 && t + dt >= d.rain_t0 && t + dt < d.rain_t1) src2 += d.rain * area;
+      if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
+      sc->ledger += dt * 0.5 * (btot + src1 + src2);
+      double tn;
+      bool at_sample = false;
+      if (sc->land && !sc->fixed_dt) {
+        double target = sc->t_end;
+        if (sc->next_sample <= target) { target = sc->next_sample; at_sample = true; }
+        tn = target;
+      } else {
+        tn = t + dt;
+      }
+      sc->t = tn;
+      if (at_sample) {
+        const int r = sc->nsamp;
+        if (r < d.max_samples) {
+          d.samp_t[r] = tn;
+          const long long P = d.plane;
+          for (int k = 0; k < d.ngauge; ++k) {
+            const long long gc = d.g_idx[k];
+            const int gi = (int)(gc % d.pitch), gj = (int)(gc / d.pitch);
+            float gz0, gz1x, gz1y, a, b, e, f;
+            cell_z(d, gi, gj, gz0, gz1x, gz1y, a, b, e, f);
+            const double h = ((double)d.S[gc] - (double)gz0) + (double)d.S[E0L * P + gc] +
+                             d.g_xi[k] * (double)(d.S[P + gc] - gz1x) +
+                             d.g_eta[k] * (double)(d.S[2 * P + gc] - gz1y);
+            d.samp_h[(long long)r * d.ngauge + k] = h > 0.0 ? h : 0.0;
+          }
+        }
+        sc->nsamp = r + 1;
+        sc->next_sample += sc->sample_every;
+      }
+      if (!(dt > 0.0) || !isfinite(tn)) sc->nonfinite = 1;
+      sc->steps += 1;
+      sc->last_dt = dt;
+      schedule32(d, sc, __longlong_as_double((long long)sc->lam_bits));
+      if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
+    }
+  }
+  if (threadIdx.x == 0) open_lists(sc);
 }
 
 __global__ void __launch_bounds__(256) rate32_kernel(D32 d) {

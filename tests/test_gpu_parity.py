@@ -63,11 +63,20 @@ CASES = {
 }
 
 
+# Free-running horizon: 100 steps, except the limited floodplain start, whose
+# thin film at the channel front amplifies round-off ~4000x between steps 88 and
+# 100 in the oracle itself (tests/test_oracle_conditioning.py), so no
+# implementation with another rounding order can hold 1e-12 there; it is held
+# over 80 steps, and every one of its 100 steps is checked from the oracle's
+# own state below.
+HORIZON = {("floodplain_dry_96x64", True): 80}
+
+
 @pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_parity_forced_dt_100_steps(name, limiter):
     case = CASES[name]()
-    s, o, _, _ = run_pair(case, limiter, 100)
+    s, o, _, _ = run_pair(case, limiter, HORIZON.get((name, limiter), 100))
     err = plane_err(s.state(), o.state())
     assert err.max() <= TOL, dict(enumerate(err))
     t_gpu, _ = s.time()
@@ -75,6 +84,27 @@ def test_parity_forced_dt_100_steps(name, limiter):
     m, led = s.mass()
     assert abs(m - o.mass()) <= 1e-12 * abs(o.mass())
     assert abs(led - o.ledger()) <= 1e-12 * abs(o.ledger())
+
+
+@pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_parity_along_oracle_trajectory(name, limiter):
+    """Each of 100 steps starts on the GPU from the oracle's own state and time and
+    must land within 1e-12 of the oracle's step: the per-step arithmetic of every
+    step of the run, without the round-off amplification of a long free run."""
+    case = CASES[name]()
+    B = _binding()
+    o = make_oracle(case, limiter=limiter)
+    s = B.solver_from_case(case, variant=B.DG2_LL if limiter else B.DG2_NL)
+    worst = 0.0
+    for _ in range(100):
+        s.set_state(o.state(), o.t)
+        dt = o.step()
+        s.step(dt)
+        worst = max(worst, plane_err(s.state(), o.state()).max())
+        m, _ = s.mass()
+        assert abs(m - o.mass()) <= 1e-12 * abs(o.mass())
+    assert worst <= TOL
 
 
 @pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
