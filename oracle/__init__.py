@@ -76,7 +76,6 @@ def _load():
         "orc_limit": (None, [P, dp, dp]),
         "orc_hll": (None, [P, I, dp, dp, dp]),
         "orc_minmod": (D, [D, D, D]),
-        "orc_take_tie": (D, [P]),
         "orc_gauge_h": (D, [P, D, D]),
         "orc_run_to": (ctypes.c_long, [P, D, D, I, dp, dp, dp, I, ip]),
     }
@@ -189,12 +188,6 @@ class Oracle:
 
     def ledger(self) -> float:
         return self.lib.orc_ledger(self.h)
-
-    def take_tie(self) -> float:
-        """Smallest relative margin of an Eq. 6 detector decision since the last
-        call: |J - thresh den| over the magnitudes J and den are formed from.
-        Below ~1e-11 the decision can flip under input round-off."""
-        return self.lib.orc_take_tie(self.h)
 
     def gauge_h(self, x, y) -> float:
         return self.lib.orc_gauge_h(self.h, float(x), float(y))

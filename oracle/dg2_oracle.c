@@ -78,7 +78,6 @@ typedef struct {
     double t;
     double ledger;         /* initial mass + boundary and source volumes */
     double last_bflux;     /* boundary + source volume rate of the last operator call */
-    double *tie;           /* diagnostic: smallest relative Eq. 6 detector margin seen */
 } orc_t;
 
 /* ------------------------------------------------------------------ */
@@ -431,17 +430,7 @@ static real limit_component(const orc_t *o, real half, real k0w, real k1w, real 
     if (m < o->tol_dry) m = o->tol_dry;       /* still water: round-off cannot trigger */
     real den = half * m;
     real jm = jE > jW ? jE : jW;
-    real tden = o->ds_thresh * den;
-    {
-        /* diagnostic only: how close the detector decision is to a tie,
-         * relative to the magnitudes its inputs are formed from (a decision
-         * this close can go either way under round-off of the inputs) */
-        double mag = fabs((double)k0w) + fabs((double)k1w) + 2.0 * (fabs((double)k0) + fabs((double)k1)) +
-                     fabs((double)k0e) + fabs((double)k1e) + (double)tden;
-        double gap = fabs((double)jm - (double)tden);
-        if (mag > 0.0 && gap < *o->tie * mag) *o->tie = gap / mag;
-    }
-    if (!(jm > tden)) return k1;                        /* Eq. 6 detector: no shock */
+    if (!(jm > o->ds_thresh * den)) return k1;          /* Eq. 6 detector: no shock */
     return minmod3(k1, k0e - k0, k0 - k0w);             /* Eq. 7 */
 }
 
@@ -609,15 +598,13 @@ orc_t *orc_create(int nx, int ny, double dx, double dy, double g, double cfl, do
     o->U1 = (double *)calloc(9 * N, sizeof(double));
     o->L = (double *)calloc(9 * N, sizeof(double));
     o->Ls = (double *)calloc(9 * N, sizeof(double));
-    o->tie = (double *)malloc(sizeof(double));
-    *o->tie = 1.0;
     return o;
 }
 
 void orc_destroy(orc_t *o)
 {
     if (!o) return;
-    free(o->z); free(o->nm); free(o->U); free(o->U1); free(o->L); free(o->Ls); free(o->tie);
+    free(o->z); free(o->nm); free(o->U); free(o->U1); free(o->L); free(o->Ls);
     free(o);
 }
 
@@ -697,14 +684,6 @@ void orc_hll(const orc_t *o, int dir, const double *l3, const double *r3, double
     f3[0] = f.h; f3[1] = f.qx; f3[2] = f.qy;
 }
 double orc_minmod(double a, double b, double c) { return minmod3(a, b, c); }
-/* Smallest relative Eq. 6 detector margin |J - thresh den| / (input magnitudes)
- * met since the last call (1 if none); resets it. */
-double orc_take_tie(orc_t *o)
-{
-    double v = *o->tie;
-    *o->tie = 1.0;
-    return v;
-}
 
 /* Depth at (x, y) from the planar solution of the containing cell, clipped at 0. */
 double orc_gauge_h(const orc_t *o, double x, double y)
