@@ -2,11 +2,13 @@
 """Throughput of the GB300 DG2 flood solver (cell-updates per second).
 
 Workload: the synthetic floodplain, 2000 x 1000 cells at dx = 2 m (fBm terrain,
-Hurst 0.8, 3 m relief, incised sinuous channel holding 1 m of water, triangular
-20 m^3/s inflow hydrograph on a 40 m west-edge segment, Manning 0.035 / 0.05,
-transmissive east/south/north edges), FP64.  A step is one full RK2 time step
-(friction, [local limiting], both stages with fluxes, operators, wet-dry
-treatment, Courant reduction, time/ledger update) through the C ABI.
+Hurst 0.8, 3 m relief, incised sinuous channel, triangular 20 m^3/s inflow
+hydrograph peaking at 1 h on a 40 m west-edge segment, Manning 0.035 / 0.05,
+transmissive east/south/north edges), started with 1 m of water in the channel
+and run to t = 1 h (the hydrograph peak) once by the FP32 DG2-NL path; every
+variant then times its steps from that saved state.  A step is one full RK2 time step (friction,
+[local limiting], both stages with fluxes, operators, wet-dry treatment,
+Courant reduction, time/ledger update) through the C ABI.
 
 One line of JSON on rank 0.  With --impl reference the CPU oracle is timed
 instead (a bounded 500 x 250 sample of the same workload recipe).
@@ -26,6 +28,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DG2 cell-updates/s (FP64, FP32) & % HBM roofline; adjoint/forward time ratio"
 NX, NY, DX = 2000, 1000, 2.0
+SPIN_T = 3600.0          # floodplain spin-up (s of simulated time): the hydrograph peak
+URBAN_SPIN_T = 30.0      # urban spin-up (s): 600 steps at dt_max 0.05 s
+TILE_CELLS = 32 * 8      # cells of one tile of the stage kernels
 # Unique bytes each kernel must move per cell (FP64): see the design doc (roofline section).
 BYTES_PER_CELL = {
     "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
@@ -49,11 +54,14 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default="", help="comma-separated variant keys (profiling)")
+    ap.add_argument("--state-cache", default="",
+                    help="npz file holding the spun-up floodplain state: loaded if present, "
+                         "else written (lets a profiler run skip the spin-up launches)")
     return ap.parse_args()
 
 
@@ -144,30 +152,21 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def active_cells(state, tol=1e-5, tx=32, ty=8, case=None):
-    """Cells of the tiles the kernels compute: tiles within one tile of a tile holding a
-    wet cell or a moving/sloped dry cell (the kernels' quiescence rule); every tile while
-    rain is configured."""
-    h0 = state[0]
-    if case is not None and case.rain[0] != 0.0:
-        return h0.size, float((h0 > tol).mean())
-    busy = (h0 > tol) | (np.abs(state[1:]).max(axis=0) != 0)
-    ny, nx = h0.shape
-    nty, ntx = -(-ny // ty), -(-nx // tx)
-    pad = np.zeros((nty * ty, ntx * tx), dtype=bool)
-    pad[:ny, :nx] = busy
-    t = pad.reshape(nty, ty, ntx, tx).any(axis=(1, 3))
-    d = t.copy()
-    d[1:] |= t[:-1]; d[:-1] |= t[1:]
-    d2 = d.copy()
-    d2[:, 1:] |= d[:, :-1]; d2[:, :-1] |= d[:, 1:]
-    return int(d2.sum()) * tx * ty, float(busy.mean())
+def spun_up(B, case, t_spin, variant=0):
+    """State of `case` at t_spin, from its initial state, by the FP32 path's run_to
+    (input preparation: not timed)."""
+    s = B.solver_from_case(case, variant=variant, precision=1)
+    n = s.run_to(t_spin)
+    st, t = s.state(), s.time()[0]
+    s.close()
+    return st, t, n
 
 
 def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
     """Roofline of the dominant kernel of one timed run (live CUDA-event timing).
     FP64: FP64-pipe bound, algorithmic FLOPs per wet cell; FP32: HBM bound, unique
-    bytes per cell of the tiles computed (dry tiles are exact fixed points, skipped)."""
+    bytes per cell of the tiles the kernels computed (counted on the device; dry
+    tiles are exact fixed points and are skipped)."""
     kms = run["kernel_ms"] / max(run["timed"], 1)
     dom = int(np.argmax(kms))
     names = {"friction": "friction", "stage1": "stage 1", "stage2": "stage 2"}
@@ -184,25 +183,31 @@ def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
                 "flops_per_wet_cell": per_cell, "wet_cells": wet, "kernel_ms": kernel_ms}
     tab = BYTES_PER_CELL[prec][KERNELS[dom]]
     per_cell = tab if dom == 0 else tab[var]
-    act = run.get("active_cells", cells)
+    act = run["active_cells"]
     achieved = per_cell * act / (kms[dom] * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_gbs,
             "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None, "peak_source": peak_src,
             "bytes_per_cell": per_cell, "active_cells": act, "kernel_ms": kernel_ms}
 
 
-def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=0):
-    """Device-timed steps of one variant; returns dict of timings."""
+def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=0, start=None):
+    """Device-timed steps of one variant, from `start` = (planes, t), or after running
+    the solver itself to t = `start` (a number; untimed spin-up), or from the case's
+    initial state (None)."""
     s = B.solver_from_case(case, variant=variant, precision=precision)
+    if isinstance(start, tuple):
+        s.set_state(start[0], start[1])
+    elif start is not None:
+        s.run_to(float(start))
     st = s.stream
     for _ in range(warmup):
         s.step(-1.0)
     torch.cuda.synchronize()
     st0 = s.state()
-    act, _ = active_cells(st0, case=case)
     wet = float((st0[0] > 1e-5).mean())
     if timing:
         B.dg2_enable_kernel_timing(s.ctx, True)
+    tiles0 = s.tile_stats()[3]
     l0 = s.launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -214,23 +219,24 @@ def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=
     ms = ev0.elapsed_time(ev1)
     launches = s.launches() - l0
     kt, n = B.dg2_kernel_times(s.ctx) if timing else (np.zeros(3), 0)
+    tiles = s.tile_stats()[3] - tiles0
     t_sim, _ = s.time()
     return {"solver": s, "ms": ms, "launches": launches, "kernel_ms": kt, "timed": n,
-            "wet_fraction": wet, "active_cells": act, "t_sim": t_sim}
+            "wet_fraction": wet, "active_cells": TILE_CELLS * tiles / max(steps, 1),
+            "t_sim": t_sim}
 
 
-def e2e_run(B, torch, case, variant, steps):
-    """Same steps through the public API with host buffers: the initial state goes up
+def e2e_run(B, torch, case, variant, steps, start):
+    """Same steps through the public API with host buffers: the start state goes up
     from pinned host memory, the final state and the mass come back, all timed."""
     s = B.solver_from_case(case, variant=variant)
     nx, ny = case.nx, case.ny
-    init = s.state()
     pin_in = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
     pin_out = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-    pin_in[...] = init
+    pin_in[...] = start[0]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    B.dg2_set_state(s.ctx, pin_in, 0.0)
+    B.dg2_set_state(s.ctx, pin_in, start[1])
     for _ in range(steps):
         s.step(-1.0)
     B.dg2_get_state(s.ctx, nx, ny, out=pin_out)
@@ -311,8 +317,18 @@ def main():
     torch.cuda.set_device(local)
     only = set(args.only.split(",")) if args.only else None
     cases = {"floodplain": workload(), "flooded": inputs.flooded_plain(NX, NY, DX)}
+    starts = {"flooded": None}
+    if args.state_cache and os.path.exists(args.state_cache):
+        z = np.load(args.state_cache)
+        st, t, nspin = z["planes"], float(z["t"]), int(z["steps"])
+    else:
+        st, t, nspin = spun_up(B, cases["floodplain"], SPIN_T)
+        if args.state_cache:
+            np.savez(args.state_cache, planes=st, t=t, steps=nspin)
+    starts["floodplain"] = (st, t)
     if not only or any(k.endswith("urban") for k in only):
         cases["urban"] = inputs.urban()
+        starts["urban"] = URBAN_SPIN_T
     cells = NX * NY
     warmup = max(3, args.warmup)
     pk, pk_src = peaks()
@@ -329,7 +345,7 @@ def main():
         case = cases[wl]
         ncell = case.nx * case.ny
         nsteps = URBAN_STEPS if (wl == "urban" and args.steps >= 50) else args.steps
-        run = time_variant(B, torch, case, var, nsteps, warmup, precision=prec)
+        run = time_variant(B, torch, case, var, nsteps, warmup, precision=prec, start=starts[wl])
         if clk:
             clocks = clk.stop()
         ms = max_over_ranks(run["ms"], world)
@@ -347,7 +363,8 @@ def main():
     hd = results[head]
     e2e = None
     if not only or "fp64_ll" in only:
-        e2e_s, h2d, d2h = e2e_run(B, torch, cases["floodplain"], B.DG2_LL, args.steps)
+        e2e_s, h2d, d2h = e2e_run(B, torch, cases["floodplain"], B.DG2_LL, args.steps,
+                                  starts["floodplain"])
         e2e = {"value": world * cells * args.steps / max_over_ranks(e2e_s, world),
                "unit": "cell-updates/s", "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps}
@@ -366,9 +383,11 @@ def main():
                 "steps": hd["steps"], "warmup": warmup, "ms_per_step": hd["ms_max"] / hd["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if head.startswith("fp64") else "f32", "data": "synthetic",
-                "config": {"workload": "floodplain 2000x1000 dx=2 m, DG2-LL, FP64"
+                "config": {"workload": "floodplain 2000x1000 dx=2 m from t=1 h (channel start run to "
+                                       "the hydrograph peak), DG2-LL, FP64"
                            if head == "fp64_ll" else head,
-                           "variant": head, "cells": cells,
+                           "variant": head, "cells": cells, "t_start_s": SPIN_T,
+                           "spin_up_steps": nspin,
                            "wet_fraction": hd["wet_fraction"],
                            "l2": "inputs larger than L2 (state 2 x 145 MB)",
                            "parallelism": f"replicas x{world}"},

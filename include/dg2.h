@@ -171,6 +171,14 @@ int dg2_kernel_times(dg2_ctx *ctx, double *ms3, int64_t *nsteps);
 /* Number of kernels this context has launched (for launch accounting). */
 int64_t dg2_launch_count(const dg2_ctx *ctx);
 
+/* Tile accounting of the exact dry-tile skipping (32 x 8-cell tiles): writes
+ * the number of tiles of the grid, the tiles the next step will compute and
+ * copy (frontier), and the running total of tiles computed by all completed
+ * steps (the units the stage kernels processed).  Any pointer may be NULL.
+ * Synchronises the context's stream.  Errors: DG2_E_ARG (null context). */
+int dg2_tile_stats(dg2_ctx *ctx, int *ntiles, int *n_active, int *n_frontier,
+                   int64_t *tiles_computed);
+
 /* Largest grid height (rows) that dg2_mass_noalloc accepts. */
 #define DG2_NOALLOC_MAX_ROWS 65536
 

@@ -30,7 +30,7 @@ EXPORTS = (
     "dg2_set_bc_inflow", "dg2_set_sources", "dg2_step", "dg2_run_to", "dg2_set_gauges",
     "dg2_read_gauges", "dg2_mass", "dg2_get_state", "dg2_set_state", "dg2_get_topo",
     "dg2_get_time", "dg2_enable_kernel_timing", "dg2_kernel_times", "dg2_launch_count",
-    "dg2_mass_noalloc", "dg2_destroy",
+    "dg2_tile_stats", "dg2_mass_noalloc", "dg2_destroy",
 )
 DG2_NOALLOC_MAX_ROWS = 65536
 
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
         "dg2_enable_kernel_timing": (I, [P, I]),
         "dg2_kernel_times": (I, [P, dp, i64p]),
         "dg2_launch_count": (ctypes.c_int64, [P]),
+        "dg2_tile_stats": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
         "dg2_mass_noalloc": (I, [P, I, I, I, D, D, P, P]),
         "dg2_destroy": (I, [P]),
     }
@@ -216,6 +218,15 @@ def dg2_launch_count(ctx) -> int:
     return int(load().dg2_launch_count(ctx))
 
 
+def dg2_tile_stats(ctx):
+    """(ntiles, n_active, n_frontier, tiles_computed) of the dry-tile skipping."""
+    nt, na, nf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    tc = ctypes.c_int64()
+    _check(load().dg2_tile_stats(ctx, ctypes.byref(nt), ctypes.byref(na), ctypes.byref(nf),
+                                 ctypes.byref(tc)))
+    return nt.value, na.value, nf.value, tc.value
+
+
 def dg2_mass_noalloc(h0_ptr: int, nx: int, ny: int, pitch: int, dx: float, dy: float,
                      mass_ptr: int, stream_ptr: int = 0):
     """Mass of a device depth plane into a device double, with no device allocation
@@ -324,6 +335,9 @@ class Solver:
 
     def launches(self) -> int:
         return dg2_launch_count(self.ctx)
+
+    def tile_stats(self):
+        return dg2_tile_stats(self.ctx)
 
 
 def solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, **kw) -> Solver:

@@ -929,6 +929,19 @@ int dg2_kernel_times(dg2_ctx* c, double* ms3, int64_t* nsteps) {
 
 int64_t dg2_launch_count(const dg2_ctx* c) { return c ? c->launches : -1; }
 
+int dg2_tile_stats(dg2_ctx* c, int* ntiles, int* n_active, int* n_frontier,
+                   int64_t* tiles_computed) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  if (ntiles) *ntiles = c->d.tiles.ntiles;
+  if (n_active) *n_active = s.n_act;
+  if (n_frontier) *n_frontier = s.n_front;
+  if (tiles_computed) *tiles_computed = s.tiles_done;
+  return DG2_OK;
+}
+
 int dg2_destroy(dg2_ctx* c) {
   if (!c) return fail(DG2_E_ARG, "null context");
   drop_graph(c);

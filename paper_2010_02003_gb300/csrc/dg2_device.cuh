@@ -64,6 +64,7 @@ struct Scalars {
   int n_front;         // frontier tiles copied in stage 1 (entries of tiles.front)
   int list_all;        // every tile is computed: list entry e is tile e
   int skip_lists;      // the step was not taken (run already done): keep the lists
+  long long tiles_done;  // tiles computed by the stage kernels of all completed steps
 };
 
 // Exact skipping of quiescent dry tiles.  A cell is quiescent when its depth
@@ -1015,6 +1016,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(Dev d, int lists_
       sc->last_dt = dt;
       schedule_next_dt(d, sc, __longlong_as_double((long long)sc->lam_bits));
       if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
+      sc->tiles_done += sc->n_act;
     }
   }
   if (threadIdx.x == 0) open_lists(sc);

@@ -785,6 +785,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize32_kernel(D32 d, int list
       sc->last_dt = dt;
       schedule32(d, sc, __longlong_as_double((long long)sc->lam_bits));
       if (!sc->fixed_dt && sc->t >= sc->t_end) sc->done = 1;
+      sc->tiles_done += sc->n_act;
     }
   }
   if (threadIdx.x == 0) open_lists(sc);

@@ -46,3 +46,58 @@ def test_skip_with_point_source_and_rain(precision):
     b = _run(case, 0, precision, False, 120, dt_max=0.02)
     assert np.array_equal(a[0], b[0]) and a[2] == b[2]
     assert a[0][0].max() > 0.0
+
+
+def _expected_active(state, tol=1e-5, tx=32, ty=8):
+    """Tiles within one tile (3 x 3 neighbourhood) of a tile holding a non-quiescent
+    cell (h0 > tol or any other mode non-zero), from the FP64 state."""
+    busy = (state[0] > tol) | (np.abs(state[1:]).max(axis=0) != 0)
+    ny, nx = busy.shape
+    nty, ntx = -(-ny // ty), -(-nx // tx)
+    pad = np.zeros((nty * ty, ntx * tx), dtype=bool)
+    pad[:ny, :nx] = busy
+    t = pad.reshape(nty, ty, ntx, tx).any(axis=(1, 3))
+    d = t.copy()
+    d[1:] |= t[:-1]
+    d[:-1] |= t[1:]
+    d2 = d.copy()
+    d2[:, 1:] |= d[:, :-1]
+    d2[:, :-1] |= d[:, 1:]
+    return int(d2.sum()), ntx * nty
+
+
+def test_tile_lists_match_host_classification():
+    """The device tile lists hold exactly the tiles of the 3 x 3 rule (dam in a dry basin,
+    no forced tiles), and the running total counts every computed tile."""
+    from paper_2010_02003_gb300 import binding as B
+    case = inputs.hump(nx=200, ny=120, eta=-1.0 + 0.0, dam_eta=1.0, dam_radius=12.0)
+    s = B.solver_from_case(case, variant=B.DG2_LL)
+    nt, na, nf, done = s.tile_stats()
+    assert na == nt and done == 0              # a new state computes every tile once
+    total = 0
+    for k in range(30):
+        _, na, nf, done0 = s.tile_stats()
+        s.step(-1.0)
+        _, na1, nf1, done1 = s.tile_stats()
+        assert done1 - done0 == na                # the step computed the listed tiles
+        exp, ntiles = _expected_active(s.state())
+        assert ntiles == nt and na1 == exp, (k, na1, exp)
+        assert 0 < na1 < nt and na1 + nf1 <= nt
+        total += na
+    assert done1 == total
+
+
+def test_tile_stats_without_skipping_and_all_dry():
+    from paper_2010_02003_gb300 import binding as B
+    case = inputs.hump(nx=100, ny=50, eta=0.5)
+    s = B.solver_from_case(case, skip_dry_tiles=False)
+    for _ in range(3):
+        s.step(-1.0)
+    nt, na, nf, done = s.tile_stats()
+    assert nt == 4 * 7 and na == nt and nf == 0 and done == 3 * nt
+    dry = inputs.hump(nx=100, ny=50, eta=-1.0)
+    s2 = B.solver_from_case(dry)
+    for _ in range(3):
+        s2.step(-1.0)
+    nt, na, nf, done = s2.tile_stats()
+    assert na == 0 and nf == 0 and done == nt   # only the first step after set-up computes
