@@ -31,7 +31,7 @@ NX, NY, DX = 2000, 1000, 2.0
 SPIN_T = 3600.0          # floodplain spin-up (s of simulated time): the hydrograph peak
 URBAN_SPIN_T = 30.0      # urban spin-up (s): 600 steps at dt_max 0.05 s
 TILE_CELLS = 32 * 8      # cells of one tile of the stage kernels
-# Unique bytes each kernel must move per cell (FP64): see the design doc (roofline section).
+# Unique bytes each kernel must move per cell: the planes it must read and write once.
 BYTES_PER_CELL = {
     "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
              "stage2": {"nl": 30 * 8, "ll": 30 * 8}},
@@ -46,6 +46,18 @@ KERNELS = ["friction", "stage1", "stage2"]
 # operator 381, limiter 70 per cell; RK combination 18 / 27; Courant rate 8).
 FLOPS_PER_WET_CELL = {"friction": 111, "stage1": {"nl": 399, "ll": 469},
                       "stage2": {"nl": 416, "ll": 486}}
+# DRAM bytes (read + write) per launch of a variant's dominant kernel from one ncu
+# capture (summarised in the named profile), valid only for the device sources it
+# was taken with: the key is a hash of paper_2010_02003_gb300/csrc, and the
+# roofline's traffic is null once those sources change.
+TRAFFIC = {
+    ("fp64_ll", "stage2"): (53_583_616, "297a919fc12579ad",
+                            "profiles/stage_kernel_fp64_ll_floodplain2000x1000_t3600.md"),
+    ("fp32_ll", "stage2"): (29_019_904, "297a919fc12579ad",
+                            "profiles/stage32_kernel_fp32_ll_floodplain2000x1000_t3600.md"),
+    ("fp32_nl_flooded", "stage2"): (222_384_640, "297a919fc12579ad",
+                                    "profiles/stage32_kernel_fp32_nl_flooded2000x1000.md"),
+}
 # FP64 issue rate of GB300: 2 DFMA per SM per cycle (ncu
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / cycle), 152 SMs
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
@@ -152,6 +164,26 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def device_src_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2010_02003_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(key, kernel):
+    """(bytes per launch, profile) if the capture matches the current device sources."""
+    t = TRAFFIC.get((key, kernel))
+    if t is None or t[1] != device_src_hash():
+        return None, None
+    return t[0], t[2]
+
+
 def spun_up(B, case, t_spin, variant=0):
     """State of `case` at t_spin, from its initial state, by the FP32 path's run_to
     (input preparation: not timed)."""
@@ -162,7 +194,7 @@ def spun_up(B, case, t_spin, variant=0):
     return st, t, n
 
 
-def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
+def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src, key=""):
     """Roofline of the dominant kernel of one timed run (live CUDA-event timing).
     FP64: FP64-pipe bound, algorithmic FLOPs per wet cell; FP32: HBM bound, unique
     bytes per cell of the tiles the kernels computed (counted on the device; dry
@@ -172,13 +204,15 @@ def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
     names = {"friction": "friction", "stage1": "stage 1", "stage2": "stage 2"}
     kname = f"{prec} {var.upper()} {names[KERNELS[dom]]}"
     kernel_ms = {n: float(k) for n, k in zip(KERNELS, kms)}
+    traffic, prof = traffic_of(key, KERNELS[dom])
     if prec == "fp64":
         tab = FLOPS_PER_WET_CELL[KERNELS[dom]]
         per_cell = tab if dom == 0 else tab[var]
         wet = run["wet_fraction"] * cells
         achieved = per_cell * wet / (kms[dom] * 1e-3) / 1e9
         return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "traffic_profile": prof,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
                 "flops_per_wet_cell": per_cell, "wet_cells": wet, "kernel_ms": kernel_ms}
     tab = BYTES_PER_CELL[prec][KERNELS[dom]]
@@ -186,7 +220,8 @@ def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src):
     act = run["active_cells"]
     achieved = per_cell * act / (kms[dom] * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_gbs,
-            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None, "peak_source": peak_src,
+            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
+            "traffic_profile": prof, "peak_source": peak_src,
             "bytes_per_cell": per_cell, "active_cells": act, "kernel_ms": kernel_ms}
 
 
@@ -354,7 +389,7 @@ def main():
         run["steps"] = nsteps
         run["cells"] = ncell
         run["roofline"] = kernel_roofline(run, "fp32" if prec else "fp64", "ll" if var else "nl",
-                                          ncell, pk["hbm_gbs"], pk_src)
+                                          ncell, pk["hbm_gbs"], pk_src, key)
         run.pop("solver").close()
         results[key] = run
         torch.cuda.empty_cache()

@@ -12,7 +12,7 @@
  * needs it, no blocking or fusion, so that each function can be read against
  * the paper.  Compiled with -ffp-contract=off (no fused multiply-add).
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - Riemann solver: HLL with Toro's wet/dry wave speeds (the paper uses Roe,
  *     Sec. 2.1.2; the HLL flux is this build's contract).
  *   - z* revision uses the cell's own limit at each of its faces (Sec. 2.1.2).

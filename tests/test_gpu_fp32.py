@@ -126,7 +126,8 @@ def test_fp32_urban_recipe_against_fp64_oracle():
     the building walls cross the wet-dry thresholds (tol_dry, the front rule) at slightly
     different steps -- the FP64 oracle does the same to a copy with its rain changed by
     1e-7 -- so after 100 steps only aggregates are compared: volume, wet area and the
-    relative L1 depth difference (measured: see the design doc)."""
+    relative L1 depth difference (measured after 100 steps: volume 2.9e-6, wet cells
+    30603 vs 30539, relative L1 depth 2.7e-3)."""
     B = _B()
     case = inputs.urban(nx=192, ny=160, dx=0.5, nblocks=30)
     o = make_oracle(case)
