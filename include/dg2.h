@@ -168,6 +168,10 @@ int dg2_get_time(dg2_ctx *ctx, double *t, double *dt_next);
 int dg2_enable_kernel_timing(dg2_ctx *ctx, int enable);
 int dg2_kernel_times(dg2_ctx *ctx, double *ms3, int64_t *nsteps);
 
+/* Completed steps since the last dg2_set_dem / dg2_set_state (also those an
+ * ensemble took for this member).  Synchronises the stream. */
+int dg2_get_steps(dg2_ctx *ctx, int64_t *steps);
+
 /* Number of kernels this context has launched (for launch accounting). */
 int64_t dg2_launch_count(const dg2_ctx *ctx);
 
@@ -205,6 +209,68 @@ int dg2_mass_noalloc(const double *h0_dev, int nx, int ny, int pitch, double dx,
 
 /* Releases the host-side context (the workspace stays the caller's). */
 int dg2_destroy(dg2_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Ensembles: many FP32 problems advanced together.
+ *
+ * An ensemble gathers existing DG2_FP32 contexts ("members", all of one
+ * variant, each already given its DEM or state, inflows, sources and gauges)
+ * and advances all of them with one set of launches per step: one list of
+ * (member, tile) work items per step, each member with its own Courant step,
+ * time, ledger, gauges and landing on t_end.  Each member's result is bit for
+ * bit the one dg2_run_to on that member alone gives (same cell arithmetic; the
+ * tile shape changes only the summation order of the mass ledger's boundary
+ * fluxes).  Members are read through their contexts while the ensemble runs:
+ * do not step, reconfigure or destroy a member during an ensemble call; the
+ * ensemble re-reads the members' parameters and recomputes every tile once at
+ * the start of each dg2_ens_run_to.  State, time, mass and gauges are read
+ * back through the member contexts (dg2_get_state, dg2_mass, ...).
+ * ---------------------------------------------------------------------- */
+typedef struct dg2_ens dg2_ens;
+
+/* Device workspace bytes for an ensemble of these members (0 if a member is
+ * NULL or not FP32, or nmembers is not 1..512).  Tile bookkeeping for every
+ * tile shape the ensemble can take, the work lists and member descriptors. */
+size_t dg2_ens_workspace_bytes(dg2_ctx *const *members, int nmembers);
+
+/* Creates an ensemble of nmembers contexts (copied pointer array; the
+ * contexts stay owned by the caller and must outlive the ensemble).  The
+ * device workspace (>= dg2_ens_workspace_bytes, 256-byte aligned) and the
+ * stream (void* cudaStream_t; a non-NULL stream enables CUDA-graph replay)
+ * are the caller's.  Tile shape 32 x 8.  DG2_E_ARG: a NULL, duplicate or
+ * non-FP32 member, mixed variants, bad workspace; DG2_E_STATE: a member
+ * without DEM or state; DG2_E_NOMEM: workspace too small. */
+int dg2_ens_create(dg2_ens **out, dg2_ctx *const *members, int nmembers, void *dev_workspace,
+                   size_t ws_bytes, void *cuda_stream);
+
+/* Advances every member to simulated time t_end (s) with its own Courant
+ * steps, landing exactly on t_end and on its gauge sample times.  Members
+ * already at or past t_end stay.  *steps_taken (may be NULL) = ensemble steps
+ * replayed (the longest member's count, rounded up to the last chunk).
+ * DG2_E_NONFINITE if a member's state or step became non-finite. */
+int dg2_ens_run_to(dg2_ens *ens, double t_end, int64_t *steps_taken);
+
+/* Picks the tile shape by timing: runs two passes over the supported shapes
+ * (32x8, 32x4, 16x8, 64x4, 16x16 cells), each trial one untimed and
+ * steps_per_trial (>= 4) timed steps of the run toward t_end (these are real
+ * steps: the members advance), keeps the fastest shape and writes it to
+ * *tile_w, *tile_h (may be NULL).  dg2_ens_tune_times gives the trial times. */
+int dg2_ens_autotune(dg2_ens *ens, double t_end, int steps_per_trial, int *tile_w, int *tile_h);
+
+/* Sets / reads the tile shape (one of the shapes listed above). */
+int dg2_ens_set_tile_shape(dg2_ens *ens, int tile_w, int tile_h);
+int dg2_ens_tile_shape(const dg2_ens *ens, int *tile_w, int *tile_h);
+
+/* Milliseconds per step of each shape's best autotune trial (in the order
+ * listed above; negative before dg2_ens_autotune).  Writes min(cap, count)
+ * entries and returns the count of shapes. */
+int dg2_ens_tune_times(const dg2_ens *ens, double *ms, int cap);
+
+/* Number of kernels the ensemble has launched. */
+int64_t dg2_ens_launch_count(const dg2_ens *ens);
+
+/* Releases the ensemble (members and workspace stay the caller's). */
+int dg2_ens_destroy(dg2_ens *ens);
 
 #ifdef __cplusplus
 }

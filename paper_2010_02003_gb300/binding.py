@@ -30,7 +30,10 @@ EXPORTS = (
     "dg2_set_bc_inflow", "dg2_set_sources", "dg2_step", "dg2_run_to", "dg2_set_gauges",
     "dg2_read_gauges", "dg2_mass", "dg2_get_state", "dg2_set_state", "dg2_get_topo",
     "dg2_get_time", "dg2_enable_kernel_timing", "dg2_kernel_times", "dg2_launch_count",
-    "dg2_tile_stats", "dg2_mass_noalloc", "dg2_destroy",
+    "dg2_tile_stats", "dg2_get_steps", "dg2_mass_noalloc", "dg2_destroy",
+    "dg2_ens_workspace_bytes", "dg2_ens_create", "dg2_ens_run_to", "dg2_ens_autotune",
+    "dg2_ens_set_tile_shape", "dg2_ens_tile_shape", "dg2_ens_tune_times",
+    "dg2_ens_launch_count", "dg2_ens_destroy",
 )
 DG2_NOALLOC_MAX_ROWS = 65536
 
@@ -85,10 +88,20 @@ def load(path: str = LIB_PATH):
         "dg2_enable_kernel_timing": (I, [P, I]),
         "dg2_kernel_times": (I, [P, dp, i64p]),
         "dg2_launch_count": (ctypes.c_int64, [P]),
+        "dg2_get_steps": (I, [P, i64p]),
         "dg2_tile_stats": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
         "dg2_mass_noalloc": (I, [P, I, I, I, D, D, P, P]),
         "dg2_destroy": (I, [P]),
+        "dg2_ens_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(P), I]),
+        "dg2_ens_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P, ctypes.c_size_t, P]),
+        "dg2_ens_run_to": (I, [P, D, i64p]),
+        "dg2_ens_autotune": (I, [P, D, I, ip, ip]),
+        "dg2_ens_set_tile_shape": (I, [P, I, I]),
+        "dg2_ens_tile_shape": (I, [P, ip, ip]),
+        "dg2_ens_tune_times": (I, [P, dp, I]),
+        "dg2_ens_launch_count": (ctypes.c_int64, [P]),
+        "dg2_ens_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -99,7 +112,7 @@ def load(path: str = LIB_PATH):
 
 
 def _check(code):
-    if code != DG2_OK:
+    if code < DG2_OK:
         raise Dg2Error(code, load().dg2_last_error().decode())
     return code
 
@@ -218,6 +231,12 @@ def dg2_launch_count(ctx) -> int:
     return int(load().dg2_launch_count(ctx))
 
 
+def dg2_get_steps(ctx) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().dg2_get_steps(ctx, ctypes.byref(n)))
+    return n.value
+
+
 def dg2_tile_stats(ctx):
     """(ntiles, n_active, n_frontier, tiles_computed) of the dry-tile skipping."""
     nt, na, nf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -237,6 +256,59 @@ def dg2_mass_noalloc(h0_ptr: int, nx: int, ny: int, pitch: int, dx: float, dy: f
 
 def dg2_destroy(ctx):
     _check(load().dg2_destroy(ctx))
+
+
+def _ctx_array(ctxs):
+    return (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c
+                                           for c in ctxs])
+
+
+def dg2_ens_workspace_bytes(ctxs) -> int:
+    return int(load().dg2_ens_workspace_bytes(_ctx_array(ctxs), len(ctxs)))
+
+
+def dg2_ens_create(ctxs, dev_ptr: int, ws_bytes: int, stream_ptr: int):
+    h = ctypes.c_void_p()
+    _check(load().dg2_ens_create(ctypes.byref(h), _ctx_array(ctxs), len(ctxs),
+                                 ctypes.c_void_p(dev_ptr), ws_bytes, ctypes.c_void_p(stream_ptr)))
+    return h
+
+
+def dg2_ens_run_to(ens, t_end: float) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().dg2_ens_run_to(ens, float(t_end), ctypes.byref(n)))
+    return n.value
+
+
+def dg2_ens_autotune(ens, t_end: float, steps_per_trial: int = 16):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    _check(load().dg2_ens_autotune(ens, float(t_end), int(steps_per_trial), ctypes.byref(w),
+                                   ctypes.byref(h)))
+    return w.value, h.value
+
+
+def dg2_ens_set_tile_shape(ens, w: int, h: int):
+    _check(load().dg2_ens_set_tile_shape(ens, int(w), int(h)))
+
+
+def dg2_ens_tile_shape(ens):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    _check(load().dg2_ens_tile_shape(ens, ctypes.byref(w), ctypes.byref(h)))
+    return w.value, h.value
+
+
+def dg2_ens_tune_times(ens):
+    ms = np.zeros(16)
+    n = _check(load().dg2_ens_tune_times(ens, _dp(ms), len(ms)))
+    return ms[:n].copy()
+
+
+def dg2_ens_launch_count(ens) -> int:
+    return int(load().dg2_ens_launch_count(ens))
+
+
+def dg2_ens_destroy(ens):
+    _check(load().dg2_ens_destroy(ens))
 
 
 # ---- convenience object owning a torch workspace ----------------------------
@@ -339,6 +411,9 @@ class Solver:
     def tile_stats(self):
         return dg2_tile_stats(self.ctx)
 
+    def steps(self) -> int:
+        return dg2_get_steps(self.ctx)
+
 
 def solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, **kw) -> Solver:
     """Builds a Solver from an inputs.Case (DEM, water, roughness, inflows, sources, gauges)."""
@@ -355,3 +430,52 @@ def solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, **kw) -> Solver:
     if case.gauges is not None and case.sample_every > 0:
         s.set_gauges(case.gauges, case.sample_every)
     return s
+
+
+class Ensemble:
+    """FP32 Solvers advanced together (one set of launches per step for all of them,
+    each member with its own time step).  Read results through the member Solvers."""
+
+    def __init__(self, members: Sequence[Solver], stream=None):
+        import torch
+        self.members = list(members)
+        ctxs = [m.ctx for m in self.members]
+        nbytes = dg2_ens_workspace_bytes(ctxs)
+        if nbytes == 0:
+            raise Dg2Error(DG2_E_ARG, "members must be FP32 solvers (1..512)")
+        dev = self.members[0].device
+        with torch.cuda.device(dev):
+            self.stream = torch.cuda.Stream(dev) if stream is None else stream
+            self.stream.wait_stream(torch.cuda.current_stream(dev))
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+            base = (self.workspace.data_ptr() + 255) // 256 * 256
+            self.ens = dg2_ens_create(ctxs, base, nbytes, self.stream.cuda_stream)
+
+    def run_to(self, t_end: float) -> int:
+        return dg2_ens_run_to(self.ens, t_end)
+
+    def autotune(self, t_end: float, steps_per_trial: int = 16):
+        return dg2_ens_autotune(self.ens, t_end, steps_per_trial)
+
+    def set_tile_shape(self, w: int, h: int):
+        dg2_ens_set_tile_shape(self.ens, w, h)
+
+    def tile_shape(self):
+        return dg2_ens_tile_shape(self.ens)
+
+    def tune_times(self):
+        return dg2_ens_tune_times(self.ens)
+
+    def launches(self) -> int:
+        return dg2_ens_launch_count(self.ens)
+
+    def close(self):
+        if getattr(self, "ens", None):
+            dg2_ens_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

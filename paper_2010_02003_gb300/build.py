@@ -11,8 +11,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "dg2_api.cu"), os.path.join(HERE, "csrc", "dg2_noalloc.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("dg2_device.cuh", "dg2_fs32.cuh")] + [
+SRC = [os.path.join(HERE, "csrc", f) for f in ("dg2_api.cu", "dg2_ens.cu", "dg2_noalloc.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f)
+              for f in ("dg2_device.cuh", "dg2_fs32.cuh", "dg2_internal.h")] + [
     os.path.join(ROOT, "include", "dg2.h")]
 LIB = os.path.join(HERE, "libdg2.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,12 +36,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     # single-precision division / square root use the hardware approximations and
     # FP32 denormals flush to zero (the FP32 path's error is stated against the FP64
     # oracle); these flags do not touch FP64 arithmetic, whose parity is 1e-12
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
-           "-ftz=true", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *SRC]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
+             "-ftz=true", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    # one object per translation unit, compiled in parallel, then linked
+    objs = [f"{tmp}.{i}.o" for i in range(len(SRC))]
+    procs = [subprocess.Popen([nvcc(), *flags, "-c", src, "-o", obj])
+             for src, obj in zip(SRC, objs)]
+    codes = [p.wait() for p in procs]
+    try:
+        if any(codes):
+            raise subprocess.CalledProcessError(max(codes, key=abs), "nvcc -c")
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

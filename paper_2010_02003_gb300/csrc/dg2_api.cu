@@ -17,6 +17,7 @@
 #include "../../include/dg2.h"
 #include "dg2_device.cuh"
 #include "dg2_fs32.cuh"
+#include "dg2_internal.h"
 
 using dg2::Dev;
 using dg2::f32::D32;
@@ -54,7 +55,7 @@ struct Layout {
   long long plane;
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
   size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, off_tforced,
-      off_tlist, off_tfront, total;
+      off_tlist, off_tfront, off_desc, off_es, total;
   int nblocks, mblocks;
 };
 
@@ -102,6 +103,9 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   L.off_tforced = take((size_t)L.nblocks);
   L.off_tlist = take((size_t)L.nblocks * sizeof(int));
   L.off_tfront = take((size_t)L.nblocks * sizeof(int));
+  // FP32: the problem's descriptor and step counters for the shared FP32 kernels
+  L.off_desc = take(f32 ? sizeof(D32) : 0);
+  L.off_es = take(f32 ? sizeof(dg2::ens::EnsScalars) : 0);
   L.total = o;
   return true;
 }
@@ -125,6 +129,7 @@ struct dg2_ctx {
   int64_t launches;
   dim3 sgrid, sblock, pgrid, pblock;
   int g_fric, g_st1, g_st2;   // persistent grid sizes (blocks) of friction / stage 1 / stage 2
+  dg2::ens::EnsDev e1;        // FP32: this problem as a set of one for the shared FP32 kernels
   dim3 lgrid, lblock;          // lists_kernel: one thread per tile
   std::vector<double> kt, kq;   // host copies of the knot tables
   // run_to graphs of 16 << k steps, k = 0..6 (dropped when the launch setup changes)
@@ -153,13 +158,21 @@ void drop_graph(dg2_ctx* c) {
 
 constexpr int kMaxTimedSteps = 8192;
 
+// FP32: uploads the problem's descriptor, which the shared FP32 kernels read
+// from device memory (stream-ordered before the next launch).
+int sync_desc(dg2_ctx* c) {
+  if (!c->fp32) return DG2_OK;
+  CU(cudaMemcpyAsync((void*)c->e1.desc, &c->f, sizeof(D32), cudaMemcpyHostToDevice, c->st));
+  CU(cudaStreamSynchronize(c->st));
+  return DG2_OK;
+}
+
 // End of step (time, ledger, gauges, next dt) and the next step's tile lists
 // (2 kernels); with lists_only, just the lists (after a new DEM / state /
 // forced mask).
 void launch_finalize(dg2_ctx* c, int lists_only) {
   if (c->fp32) {
-    dg2::f32::finalize32_kernel<<<1, dg2::kFinThreads, 0, c->st>>>(c->f, lists_only);
-    dg2::lists_kernel<<<c->lgrid, c->lblock, 0, c->st>>>(c->f);
+    dg2::ens::launch_end_of_step(c->e1, 1, c->lgrid, lists_only, c->st);
   } else {
     dg2::finalize_kernel<<<1, dg2::kFinThreads, 0, c->st>>>(c->d, lists_only);
     dg2::lists_kernel<<<c->lgrid, c->lblock, 0, c->st>>>(c->d);
@@ -169,13 +182,12 @@ void launch_finalize(dg2_ctx* c, int lists_only) {
 // Host-side mask of the tiles that must be computed whatever their state: the
 // tile holding the point source and the edge tiles whose faces an inflow
 // segment covers.  Rain marks every tile (all_forced).
-int update_forced_tiles(dg2_ctx* c) {
-  Dev& d = c->d;
-  const int ntx = (int)c->sgrid.x, nty = (int)c->sgrid.y;
-  std::vector<unsigned char> m((size_t)ntx * nty, 0);
+void forced_mask(const Dev& d, int tw, int th, std::vector<unsigned char>& m) {
+  const int ntx = (d.nx + tw - 1) / tw, nty = (d.ny + th - 1) / th;
+  m.assign((size_t)ntx * nty, 0);
   if (d.src_idx >= 0) {
     const int si = (int)(d.src_idx % d.pitch), sj = (int)(d.src_idx / d.pitch);
-    m[(size_t)(sj / dg2::TY) * ntx + si / dg2::TX] = 1;
+    m[(size_t)(sj / th) * ntx + si / tw] = 1;
   }
   for (int k = 0; k < d.n_in; ++k) {
     const dg2::InflowDesc& f = d.in[k];
@@ -186,13 +198,20 @@ int update_forced_tiles(dg2_ctx* c) {
       const double sc = (q + 0.5) * h;
       if (sc < f.s0 || sc > f.s1) continue;
       int bx, by;
-      if (ew) { by = q / dg2::TY; bx = f.edge == 0 ? 0 : ntx - 1; }
-      else { bx = q / dg2::TX; by = f.edge == 2 ? 0 : nty - 1; }
+      if (ew) { by = q / th; bx = f.edge == 0 ? 0 : ntx - 1; }
+      else { bx = q / tw; by = f.edge == 2 ? 0 : nty - 1; }
       m[(size_t)by * ntx + bx] = 1;
     }
   }
+}
+
+int update_forced_tiles(dg2_ctx* c) {
+  Dev& d = c->d;
+  std::vector<unsigned char> m;
+  forced_mask(d, dg2::TX, dg2::TY, m);
   d.tiles.all_forced = d.rain != 0.0 ? 1 : 0;
   c->f.tiles = d.tiles;
+  if (int r0 = sync_desc(c)) return r0;
   CU(cudaMemcpyAsync((void*)d.tiles.forced, m.data(), m.size(), cudaMemcpyHostToDevice, c->st));
   if (c->dem_set) {
     launch_finalize(c, 1);   // the computed set depends on the forced mask
@@ -233,21 +252,19 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   const bool ll = c->p.variant == DG2_LL;
   if (e) cudaEventRecord(e[0], c->st);
   if (c->fp32)
-    dg2::f32::friction32_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(c->f);
+    dg2::ens::launch_friction32x8(c->e1, c->g_fric, c->st);
   else
     dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
   if (c->fp32) {
-    if (ll) dg2::f32::stage32_kernel<true, 1><<<c->g_st1, c->sblock, 0, c->st>>>(c->f);
-    else dg2::f32::stage32_kernel<false, 1><<<c->g_st1, c->sblock, 0, c->st>>>(c->f);
+    dg2::ens::launch_stage32x8(c->e1, ll, 1, c->g_st1, c->st);
   } else {
     if (ll) dg2::stage_kernel<true, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
     else dg2::stage_kernel<false, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
   }
   if (e) cudaEventRecord(e[2], c->st);
   if (c->fp32) {
-    if (ll) dg2::f32::stage32_kernel<true, 2><<<c->g_st2, c->sblock, 0, c->st>>>(c->f);
-    else dg2::f32::stage32_kernel<false, 2><<<c->g_st2, c->sblock, 0, c->st>>>(c->f);
+    dg2::ens::launch_stage32x8(c->e1, ll, 2, c->g_st2, c->st);
   } else {
     if (ll) dg2::stage_kernel<true, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
     else dg2::stage_kernel<false, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
@@ -463,14 +480,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     const bool ll = p.variant == DG2_LL, f32 = p.precision == DG2_FP32;
     int o0 = 1, o1 = 1, o2 = 1;
     if (f32) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::f32::friction32_kernel, 256, 0);
-      if (ll) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::f32::stage32_kernel<true, 1>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::f32::stage32_kernel<true, 2>, 256, 0);
-      } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::f32::stage32_kernel<false, 1>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::f32::stage32_kernel<false, 2>, 256, 0);
-      }
+      dg2::ens::occupancy32x8(ll, &o0, &o1, &o2);
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::friction_kernel, 256, 0);
       if (ll) {
@@ -487,7 +497,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     c->lblock = dim3(dg2::LTX, dg2::LTY);
     c->lgrid = dim3((d.tiles.ntx + dg2::LTX - 1) / dg2::LTX, (d.tiles.nty + dg2::LTY - 1) / dg2::LTY);
     c->g_fric = gsz(o0);
-    const bool loop = f32 ? DG2_TILE_LOOP32 : DG2_TILE_LOOP64;
+    const bool loop = f32 ? true : DG2_TILE_LOOP64;
     c->g_st1 = loop ? gsz(o1) : nt;
     c->g_st2 = loop ? gsz(o2) : nt;
   }
@@ -506,6 +516,15 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   if (e != cudaSuccess) {
     delete c;
     return fail(DG2_E_CUDA, "workspace initialisation failed: %s", cudaGetErrorString(e));
+  }
+  c->e1.desc = c->fp32 ? (const D32*)(c->ws + L.off_desc) : nullptr;
+  c->e1.list = d.tiles.list;
+  c->e1.front = d.tiles.front;
+  c->e1.es = c->fp32 ? (dg2::ens::EnsScalars*)(c->ws + L.off_es) : nullptr;
+  c->e1.nmem = 1;
+  if (int r = sync_desc(c)) {
+    delete c;
+    return r;
   }
   *out = c;
   return DG2_OK;
@@ -611,7 +630,7 @@ int dg2_set_bc_inflow(dg2_ctx* c, int edge, double s0_m, double len_m, const dou
   c->d.n_in += 1;
   if ((r = update_forced_tiles(c))) return r;
   mirror(c);
-  return DG2_OK;
+  return sync_desc(c);
 }
 
 int dg2_set_sources(dg2_ctx* c, double rain, double t0, double t1, double px, double py,
@@ -636,7 +655,7 @@ int dg2_set_sources(dg2_ctx* c, double rain, double t0, double t1, double px, do
   int r2 = update_forced_tiles(c);
   if (r2) return r2;
   mirror(c);
-  return DG2_OK;
+  return sync_desc(c);
 }
 
 int dg2_step(dg2_ctx* c, double dt, double* dt_taken) {
@@ -743,7 +762,7 @@ int dg2_set_gauges(dg2_ctx* c, const double* xy, int ngauge, double every) {
   CU(cudaStreamSynchronize(c->st));
   c->d.ngauge = ngauge;
   mirror(c);
-  return DG2_OK;
+  return sync_desc(c);
 }
 
 int dg2_read_gauges(dg2_ctx* c, double* t_out, double* h_out, int cap, int* nsamp) {
@@ -929,6 +948,16 @@ int dg2_kernel_times(dg2_ctx* c, double* ms3, int64_t* nsteps) {
 
 int64_t dg2_launch_count(const dg2_ctx* c) { return c ? c->launches : -1; }
 
+int dg2_get_steps(dg2_ctx* c, int64_t* steps) {
+  int r = check_arg_ctx(c, false);
+  if (r) return r;
+  if (!steps) return fail(DG2_E_ARG, "steps is null");
+  Scalars s;
+  if ((r = read_scalars(c, &s))) return r;
+  *steps = s.steps;
+  return DG2_OK;
+}
+
 int dg2_tile_stats(dg2_ctx* c, int* ntiles, int* n_active, int* n_frontier,
                    int64_t* tiles_computed) {
   int r = check_arg_ctx(c, false);
@@ -951,3 +980,20 @@ int dg2_destroy(dg2_ctx* c) {
 }
 
 }  // extern "C"
+
+namespace dg2 {
+bool ctx_fp32(const dg2_ctx* c) { return c->fp32 != 0; }
+int ctx_variant(const dg2_ctx* c) { return c->p.variant; }
+bool ctx_ready(const dg2_ctx* c) { return c->dem_set != 0; }
+cudaStream_t ctx_stream(const dg2_ctx* c) { return c->st; }
+const f32::D32& ctx_d32(const dg2_ctx* c) { return c->f; }
+void ctx_forced_mask(const dg2_ctx* c, int tw, int th, std::vector<unsigned char>& m) {
+  forced_mask(c->d, tw, th, m);
+}
+bool ctx_rains(const dg2_ctx* c) { return c->d.rain != 0.0; }
+int ctx_reset_tiles(dg2_ctx* c) {
+  drop_graph(c);
+  return reset_tiles(c);
+}
+void ctx_count_launches(dg2_ctx* c, int64_t n) { c->launches += n; }
+}  // namespace dg2

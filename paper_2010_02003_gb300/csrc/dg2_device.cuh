@@ -233,7 +233,7 @@ __device__ __forceinline__ F3 phys_flux(double h, double qx, double qy, double g
 // Boundary ghosts
 // ---------------------------------------------------------------------------
 
-__device__ double hydrograph(const Dev& d, const InflowDesc& f, double t) {
+static __device__ double hydrograph(const Dev& d, const InflowDesc& f, double t) {
   const double* tk = d.knot_t + f.koff;
   const double* qk = d.knot_q + f.koff;
   if (t <= tk[0]) return qk[0];
@@ -248,7 +248,7 @@ __device__ double hydrograph(const Dev& d, const InflowDesc& f, double t) {
 
 // Outside state at a face of `edge` whose centre has edge coordinate s,
 // built from the cell's own unrevised limit (h, qx, qy).
-__device__ void ghost(const Dev& d, int edge, double s, double t, double& h, double& qx,
+static __device__ void ghost(const Dev& d, int edge, double s, double t, double& h, double& qx,
                       double& qy) {
   for (int k = 0; k < d.n_in; ++k) {
     const InflowDesc& f = d.in[k];
@@ -303,7 +303,7 @@ __device__ __forceinline__ double limit_component(double thresh, double tol, dou
 // Slopes (h, qx, qy) of cell (i, j) along `dir` (1 = x, 2 = y) from buffer U,
 // limited by Eqs. 6-7 when the cell and both neighbours are wet and the cell
 // is not on the edge normal to `dir`; eta = h + z is limited instead of h.
-__device__ void limited_slopes(const Dev& d, const double* __restrict__ U, int i, int j, int dir,
+static __device__ void limited_slopes(const Dev& d, const double* __restrict__ U, int i, int j, int dir,
                                double& sh, double& sqx, double& sqy) {
   const long long P = d.plane;
   const long long c = (long long)j * d.pitch + i;
@@ -428,7 +428,7 @@ __device__ __forceinline__ double cell_rate(const Dev& d, double h0, double qx0,
 
 // Turns the reduced rate into the next step: Courant step (capped by dt_max,
 // dt_max if nothing is wet) then capped to land on the next target time.
-__device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
+static __device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
   double dt = d.dt_max;
   if (lam > 0.0) {
     dt = d.cfl / lam;
@@ -455,7 +455,7 @@ __device__ void schedule_next_dt(const Dev& d, Scalars* sc, double lam) {
 // Initial modes from corner data (Eq. 3): corners staged in `zc` / `ec`
 // ((ny+1) x (nx+1) dense); ec == nullptr for a dry start; man == nullptr for
 // the uniform n.
-__global__ void init_kernel(Dev d, const double* __restrict__ zc, const double* __restrict__ ec,
+static __global__ void init_kernel(Dev d, const double* __restrict__ zc, const double* __restrict__ ec,
                             const double* __restrict__ man, double n_uniform, double* Zw,
                             double* Nw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -539,7 +539,7 @@ __device__ __forceinline__ void friction_tile(const Dev& d, int bx, int by) {
 }
 
 // Friction over the step's computed tiles (a quiescent tile has no water to rub).
-__global__ void __launch_bounds__(256) friction_kernel(Dev d) {
+static __global__ void __launch_bounds__(256) friction_kernel(Dev d) {
   const Scalars* sc = d.sc;
   if (sc->done) return;
   const int n_act = sc->n_act, ntx = d.tiles.ntx;
@@ -770,36 +770,31 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
 }
 
 // Work distribution of the stage kernels over the step's tile lists:
-// DG2_TILE_LOOPxx 1 runs a fixed grid of resident blocks that loop over the
+// DG2_TILE_LOOP64 1 runs a fixed grid of resident blocks that loop over the
 // entries; 0 launches one block per tile of the grid and a block takes the
 // entry of its own index (blocks past the lists exit at once, and the
 // hardware balances tiles of unequal cost over the SMs).  Measured on the
 // 2000 x 1000 floodplain: FP64 tiles (tens of microseconds each, 1-2 blocks
-// per SM) run faster one per block, FP32 tiles faster in resident loops.
+// per SM) run faster one per block; the FP32 kernels (shared with ensembles)
+// loop over the list in resident blocks.
 #ifndef DG2_TILE_LOOP64
 #define DG2_TILE_LOOP64 0
 #endif
-#ifndef DG2_TILE_LOOP32
-#define DG2_TILE_LOOP32 1
-#endif
 // minimum resident blocks per SM asked of the register allocator: 2 for the
 // FP64 DG2-NL stage (128 registers, no spills), 1 for DG2-LL (whose ~170
-// registers spill at 128), 3 for the FP32 stages (80 registers)
+// registers spill at 128)
 #ifndef DG2_MINB64_NL
 #define DG2_MINB64_NL 2
 #endif
 #ifndef DG2_MINB64_LL
 #define DG2_MINB64_LL 1
 #endif
-#ifndef DG2_MINB32
-#define DG2_MINB32 3
-#endif
 
 // Stage kernels run over the step's list of active tiles (and, in stage 1,
 // the frontier tiles that only copy their state for a neighbour's halo),
 // built at the end of the previous step.
 template <bool LL, int STAGE>
-__global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64_NL) stage_kernel(Dev d) {
+static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64_NL) stage_kernel(Dev d) {
   __shared__ StageSmem sm;
   Scalars* sc = d.sc;
   if (sc->done) return;
@@ -873,7 +868,7 @@ constexpr int kFinThreads = 1024;
 // per tile in a fixed order, so the step's result does not depend on it.
 constexpr int LTX = 32, LTY = 8;
 template <class D>
-__global__ void __launch_bounds__(LTX* LTY) lists_kernel(D d) {
+static __global__ void __launch_bounds__(LTX* LTY) lists_kernel(D d) {
   Scalars* sc = d.sc;
   if (sc->skip_lists) return;
   const Tiles& T = d.tiles;
@@ -949,7 +944,7 @@ __device__ __forceinline__ void open_lists(Scalars* sc) {
 // Sum over the boundary ring of tiles, in a fixed order, of the per-tile
 // boundary inflow rates of both stages (only tiles computed this step).
 template <class D>
-__device__ double ring_inflow(const D& d) {
+static __device__ double ring_inflow(const D& d) {
   __shared__ double red[32];
   const Tiles& T = d.tiles;
   const int ntx = T.ntx, nty = T.nty, nt = T.ntiles;
@@ -971,7 +966,7 @@ __device__ double ring_inflow(const D& d) {
 // Time, ledger, gauges and the next step; opens the next step's tile lists
 // (built by lists_kernel).  `lists_only`: after a new DEM / state / forced
 // mask, only open the lists.
-__global__ void __launch_bounds__(kFinThreads) finalize_kernel(Dev d, int lists_only) {
+static __global__ void __launch_bounds__(kFinThreads) finalize_kernel(Dev d, int lists_only) {
   Scalars* sc = d.sc;
   if (!lists_only) {
     if (sc->done) {
@@ -1023,7 +1018,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(Dev d, int lists_
 }
 
 // Courant reduction of the current state alone (after set-up or set_state).
-__global__ void __launch_bounds__(256) rate_kernel(Dev d) {
+static __global__ void __launch_bounds__(256) rate_kernel(Dev d) {
   __shared__ double red[32];
   __shared__ bool last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1052,8 +1047,7 @@ __global__ void __launch_bounds__(256) rate_kernel(Dev d) {
 
 // Starts a run_to: sets the target, recomputes the next sample time from the
 // current time and re-caps the pending Courant step to land on the targets.
-__global__ void begin_run_kernel(Dev d, double t_end) {
-  Scalars* sc = d.sc;
+static __device__ void begin_run_body(Scalars* sc, double t_end) {
   sc->t_end = t_end;
   sc->fixed_dt = 0;
   if (sc->sample_every > 0.0)
@@ -1070,8 +1064,10 @@ __global__ void begin_run_kernel(Dev d, double t_end) {
   sc->done = sc->t >= sc->t_end ? 1 : 0;
 }
 
+static __global__ void begin_run_kernel(Dev d, double t_end) { begin_run_body(d.sc, t_end); }
+
 // Starts a dg2_step: forced dt (> 0) or the pending Courant step, no landing.
-__global__ void begin_step_kernel(Dev d, double dt) {
+static __global__ void begin_step_kernel(Dev d, double dt) {
   Scalars* sc = d.sc;
   sc->fixed_dt = 1;
   sc->done = 0;
@@ -1081,7 +1077,7 @@ __global__ void begin_step_kernel(Dev d, double dt) {
 
 // Domain mass sum(h0) dx dy (Eq. 11): fixed-order block partials, then the
 // last block sums them in block order (deterministic).
-__global__ void __launch_bounds__(256) mass_kernel(Dev d) {
+static __global__ void __launch_bounds__(256) mass_kernel(Dev d) {
   __shared__ double red[32];
   __shared__ bool last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

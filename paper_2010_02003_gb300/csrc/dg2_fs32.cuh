@@ -97,32 +97,38 @@ __device__ __forceinline__ LimF revise32(float h, float qx, float qy, float tol)
 }
 
 // HLL (same wave speeds as the FP64 path) returned relative to the left pressure.
+// A face on a tile edge is evaluated by the edge thread of each tile beside it,
+// inside code inlined at different places; every product that could be fused
+// with a sum is therefore written as an explicit __fmaf_rn / __fmul_rn /
+// __fadd_rn, so the compiler's contraction choices cannot differ between the
+// copies and the flux does not depend on where the tile edges fall.
 __device__ __forceinline__ FaceF hll_dev(float hL, float qnL, float qtL, float unL, float utL,
                                          float hR, float qnR, float qtR, float unR, float utR,
                                          float g, float tol) {
   FaceF f;
-  const float hg = 0.5f * g;
-  f.dp = hg * (hL - hR) * (hL + hR);
+  const float hg = __fmul_rn(0.5f, g);
+  f.dp = __fmul_rn(__fmul_rn(hg, __fadd_rn(hL, -hR)), __fadd_rn(hL, hR));
   if (hL <= tol && hR <= tol) {
-    f.h = 0.f; f.n = -hg * hL * hL; f.t = 0.f;
+    f.h = 0.f; f.n = -__fmul_rn(__fmul_rn(hg, hL), hL); f.t = 0.f;
     return f;
   }
-  const float cL = sqrtf(g * hL), cR = sqrtf(g * hR);
+  const float cL = sqrtf(__fmul_rn(g, hL)), cR = sqrtf(__fmul_rn(g, hR));
   float sL, sR;
   if (hL <= tol) {
-    sL = unR - 2.f * cR;
-    sR = unR + cR;
+    sL = __fmaf_rn(-2.f, cR, unR);
+    sR = __fadd_rn(unR, cR);
   } else if (hR <= tol) {
-    sL = unL - cL;
-    sR = unL + 2.f * cL;
+    sL = __fadd_rn(unL, -cL);
+    sR = __fmaf_rn(2.f, cL, unL);
   } else {
-    const float us = 0.5f * (unL + unR) + cL - cR;
-    const float cs = 0.5f * (cL + cR) + 0.25f * (unL - unR);
-    sL = fminf(unL - cL, us - cs);
-    sR = fmaxf(unR + cR, us + cs);
+    const float us = __fadd_rn(__fmaf_rn(0.5f, __fadd_rn(unL, unR), cL), -cR);
+    const float cs = __fmaf_rn(0.25f, __fadd_rn(unL, -unR), __fmul_rn(0.5f, __fadd_rn(cL, cR)));
+    sL = fminf(__fadd_rn(unL, -cL), __fadd_rn(us, -cs));
+    sR = fmaxf(__fadd_rn(unR, cR), __fadd_rn(us, cs));
   }
-  const float fLh = hL * unL, fLn = hL * unL * unL, fLt = hL * unL * utL;
-  const float fRh = hR * unR, fRn = hR * unR * unR - f.dp, fRt = hR * unR * utR;
+  const float mL = __fmul_rn(hL, unL), mR = __fmul_rn(hR, unR);
+  const float fLh = mL, fLn = __fmul_rn(mL, unL), fLt = __fmul_rn(mL, utL);
+  const float fRh = mR, fRn = __fmaf_rn(mR, unR, -f.dp), fRt = __fmul_rn(mR, utR);
   if (sL >= 0.f) {
     f.h = fLh; f.n = fLn; f.t = fLt;
     return f;
@@ -131,10 +137,10 @@ __device__ __forceinline__ FaceF hll_dev(float hL, float qnL, float qtL, float u
     f.h = fRh; f.n = fRn; f.t = fRt;
     return f;
   }
-  const float inv = 1.f / (sR - sL), sLR = sL * sR;
-  f.h = (sR * fLh - sL * fRh + sLR * (hR - hL)) * inv;
-  f.n = (sR * fLn - sL * fRn + sLR * (qnR - qnL)) * inv;
-  f.t = (sR * fLt - sL * fRt + sLR * (qtR - qtL)) * inv;
+  const float inv = 1.f / __fadd_rn(sR, -sL), sLR = __fmul_rn(sL, sR);
+  f.h = __fmul_rn(__fmaf_rn(sR, fLh, __fmaf_rn(-sL, fRh, __fmul_rn(sLR, __fadd_rn(hR, -hL)))), inv);
+  f.n = __fmul_rn(__fmaf_rn(sR, fLn, __fmaf_rn(-sL, fRn, __fmul_rn(sLR, __fadd_rn(qnR, -qnL)))), inv);
+  f.t = __fmul_rn(__fmaf_rn(sR, fLt, __fmaf_rn(-sL, fRt, __fmul_rn(sLR, __fadd_rn(qtR, -qtL)))), inv);
   return f;
 }
 
@@ -160,7 +166,7 @@ __device__ __forceinline__ void gauss_dev(float h, float qx, float qy, float tol
   }
 }
 
-__device__ void ghost32(const D32& d, int edge, float s, double t, float& h, float& qx,
+static __device__ void ghost32(const D32& d, int edge, float s, double t, float& h, float& qx,
                         float& qy) {
   for (int k = 0; k < d.n_in; ++k) {
     const InflowDesc& f = d.in[k];
@@ -205,12 +211,14 @@ __device__ __forceinline__ float minmod3f(float a, float b, float c) {
 __device__ __forceinline__ float limit_comp32(float thresh, float tol, float half, float k0w,
                                               float k1w, float k0, float k1, float k0e,
                                               float k1e) {
+  // evaluated for a cell by its own thread and, at a tile edge, by the
+  // neighbouring tile's edge thread: explicit roundings (see hll_dev)
   const float r3 = 0.57735026918962576f;  // 1 / sqrt(3)
   const float jE = fabsf((k0e - k1e) - (k0 + k1));
   const float jW = fabsf((k0 - k1) - (k0w + k1w));
-  float mag = fmaxf(fabsf(k0 - k1 * r3), fabsf(k0 + k1 * r3));
+  float mag = fmaxf(fabsf(__fmaf_rn(-k1, r3, k0)), fabsf(__fmaf_rn(k1, r3, k0)));
   if (mag < tol) mag = tol;
-  if (!(fmaxf(jE, jW) > thresh * half * mag)) return k1;
+  if (!(fmaxf(jE, jW) > __fmul_rn(__fmul_rn(thresh, half), mag))) return k1;
   return minmod3f(k1, k0e - k0, k0 - k0w);
 }
 
@@ -228,7 +236,7 @@ __device__ __forceinline__ void cell_z(const D32& d, int i, int j, float& z0, fl
 // Limited slopes (eta, qx, qy) along dir of cell (i, j): Eqs. 6-7 on the
 // free surface and the discharges (the free-surface form makes Sec. 2.1.3's
 // eta limiting direct).
-__device__ void limited_slopes32(const D32& d, const float* __restrict__ U, int i, int j, int dir,
+static __device__ void limited_slopes32(const D32& d, const float* __restrict__ U, int i, int j, int dir,
                                  float& se, float& sqx, float& sqy) {
   const long long P = d.plane, c = (long long)j * d.pitch + i;
   se = U[dir * P + c];
@@ -292,7 +300,7 @@ __device__ __forceinline__ float rate32(const D32& d, float h0, float qx0, float
   return fmaxf((fabsf(u) + c) * d.inv_dx, (fabsf(v) + c) * d.inv_dy);
 }
 
-__device__ void schedule32(const D32& d, Scalars* sc, double lam) {
+static __device__ void schedule32(const D32& d, Scalars* sc, double lam) {
   double dt = d.dt_max;
   if (lam > 0.0) {
     dt = d.cfl / lam;
@@ -315,7 +323,7 @@ __device__ void schedule32(const D32& d, Scalars* sc, double lam) {
 // Initial modes from FP64 corner data: face-average topography (rounded to
 // FP32 once), free-surface modes by Eq. 3, dry cells with eta modes equal to
 // the FP32 topography modes (zero depth exactly).
-__global__ void init32_kernel(D32 d, const double* __restrict__ zc, const double* __restrict__ ec,
+static __global__ void init32_kernel(D32 d, const double* __restrict__ zc, const double* __restrict__ ec,
                               const double* __restrict__ man, double n_uniform, float* ZXw,
                               float* ZYw, float* Nw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,9 +379,11 @@ __device__ __forceinline__ void friction_point32(float gn2dt, float tol, float h
   qy = qy / den;
 }
 
+// Friction on the BX x BY tile (bx, by), one thread per cell.
+template <int BX = TX, int BY = TY>
 __device__ __forceinline__ void friction32_tile(const D32& d, float gdt, int bx, int by) {
-  const int i = bx * TX + threadIdx.x;
-  const int j = by * TY + threadIdx.y;
+  const int i = bx * BX + threadIdx.x;
+  const int j = by * BY + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
   const long long P = d.plane, c = (long long)j * d.pitch + i;
   const float n = d.N[c];
@@ -416,30 +426,17 @@ __device__ __forceinline__ void friction32_tile(const D32& d, float gdt, int bx,
   S[QY1Y * P + c] = nq[1][1];
 }
 
-__global__ void __launch_bounds__(256) friction32_kernel(D32 d) {
-  const Scalars* sc = d.sc;
-  if (sc->done) return;
-  __shared__ float s_gdt;
-  if (threadIdx.x == 0 && threadIdx.y == 0) s_gdt = (float)(sc->dt * (double)d.g);
-  __syncthreads();
-  const float gdt = s_gdt;
-  const int n_act = sc->n_act, ntx = d.tiles.ntx;
-  const bool all = sc->list_all != 0;
-  for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
-    const int tile = all ? e : d.tiles.list[e];
-    friction32_tile(d, gdt, tile % ntx, tile / ntx);
-  }
-}
-
-struct StageSmem32 {
-  LimF e[TY][TX];
-  LimF n[TY][TX];
-  LimF hw[TY], he[TY], hs[TX], hn[TX];
-  FaceF fx[TY][TX + 1];
-  FaceF fy[TY + 1][TX];
+template <int BX, int BY>
+struct StageSmem32T {
+  LimF e[BY][BX];
+  LimF n[BY][BX];
+  LimF hw[BY], he[BY], hs[BX], hn[BX];
+  FaceF fx[BY][BX + 1];
+  FaceF fy[BY + 1][BX];
   double red[32];
   float redf[32];
 };
+using StageSmem32 = StageSmem32T<TX, TY>;
 
 // One RK stage of the FP32 free-surface form on the tile (bx, by).  `blk`
 // carries the per-block constants (dt, stage time, rain flag) read once.
@@ -447,21 +444,22 @@ struct Blk32 {
   float dt, rainf;
   double dtd, ts;
   int rain;
+  int skip;  // the problem has reached t_end: leave its tiles
 };
 
-template <bool LL, int STAGE>
-__device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32& sm, const Blk32& blk,
-                                             int bx, int by, float& brate, float& lam, bool& bad,
-                                             bool& nonq) {
+template <bool LL, int STAGE, int BX = TX, int BY = TY>
+__device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>& sm,
+                                             const Blk32& blk, int bx, int by, float& brate,
+                                             float& lam, bool& bad, bool& nonq) {
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = bx * TX + tx, j = by * TY + ty;
+  const int i = bx * BX + tx, j = by * BY + ty;
   const bool act = i < d.nx && j < d.ny;
   const long long P = d.plane;
   const long long c = (long long)j * d.pitch + i;
   const float* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const float g = d.g, tol = d.tol;
-  const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
-  const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
+  const bool east_edge = act && (tx == BX - 1 || i == d.nx - 1);
+  const bool north_edge = act && (ty == BY - 1 || j == d.ny - 1);
   const float dt = blk.dt;
   const double ts = blk.ts;
   const bool s_rain = blk.rain != 0;
@@ -664,78 +662,9 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32& sm, cons
   }
 }
 
-template <bool LL, int STAGE>
-__global__ void __launch_bounds__(TX* TY, DG2_MINB32) stage32_kernel(D32 d) {
-  __shared__ StageSmem32 sm;
-  __shared__ Blk32 blk;
-  Scalars* sc = d.sc;
-  if (sc->done) return;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  // FP64 work happens once per block, never per cell: on this part one FP64
-  // operation costs the issue slots of 64 FP32 operations
-  if (tx == 0 && ty == 0) {
-    const double dtd0 = sc->dt;
-    const double ts0 = STAGE == 1 ? sc->t : sc->t + dtd0;
-    blk.dtd = dtd0;
-    blk.ts = ts0;
-    blk.dt = (float)dtd0;
-    blk.rain = d.rain != 0.0 && ts0 >= d.rain_t0 && ts0 < d.rain_t1;
-    blk.rainf = (float)d.rain;
-  }
-  __syncthreads();
-  const int ntx = d.tiles.ntx, nty = d.tiles.nty;
-  const int n_act = sc->n_act;
-  const bool all = sc->list_all != 0;
-  float lam = 0.f;
-  bool bad = false;
-#if DG2_TILE_LOOP32
-  for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
-#else
-  if (STAGE == 2 && (int)blockIdx.x >= n_act) return;
-  for (int e = blockIdx.x; e < n_act; e = n_act) {
-#endif
-    const int tile = all ? e : d.tiles.list[e];
-    const int bx = tile % ntx, by = tile / ntx;
-    float brate = 0.f, lam_t = 0.f;
-    bool nonq = false;
-    stage32_tile<LL, STAGE>(d, sm, blk, bx, by, brate, lam_t, bad, nonq);
-    lam = fmaxf(lam, lam_t);
-    if (bx == 0 || by == 0 || bx == ntx - 1 || by == nty - 1) {
-      const double bsum = block_sum<TX * TY>((double)brate, sm.red);
-      if (tx == 0 && ty == 0) d.bpart[(STAGE - 1) * d.tiles.ntiles + tile] = bsum;
-    }
-    if (STAGE == 2) {
-      const int any_nonq = __syncthreads_or(nonq);
-      if (tx == 0 && ty == 0) d.tiles.flag[tile] = any_nonq ? 1 : 0;
-    }
-    __syncthreads();
-  }
-  if (STAGE == 1) {
-    const int n_front = sc->n_front;
-    const long long P = d.plane;
-#if DG2_TILE_LOOP32
-    for (int e = blockIdx.x; e < n_front; e += gridDim.x) {
-#else
-    for (int e = (int)blockIdx.x - n_act; e >= 0 && e < n_front; e = n_front) {
-#endif
-      const int tile = d.tiles.front[e];
-      const int i = (tile % ntx) * TX + tx, j = (tile / ntx) * TY + ty;
-      if (i < d.nx && j < d.ny) {
-        const long long c = (long long)j * d.pitch + i;
-#pragma unroll
-        for (int k = 0; k < kPlanes32; ++k) d.T[k * P + c] = d.S[k * P + c];
-      }
-    }
-    return;
-  }
-  if (__syncthreads_or(bad) && tx == 0 && ty == 0) sc->nonfinite = 1;
-  const double bl = (double)block_max_f<TX * TY>(lam, sm.redf);
-  if (tx == 0 && ty == 0 && bl > 0.0)
-    atomicMax(&sc->lam_bits, (unsigned long long)__double_as_longlong(bl));
-}
-
 // Time, ledger, gauges and the next step; opens the next step's tile lists.
-__global__ void __launch_bounds__(kFinThreads) finalize32_kernel(D32 d, int lists_only) {
+// Run by one block of kFinThreads threads per problem.
+static __device__ void finalize32_body(const D32& d, int lists_only) {
   Scalars* sc = d.sc;
   if (!lists_only) {
     if (sc->done) {
@@ -791,7 +720,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize32_kernel(D32 d, int list
   if (threadIdx.x == 0) open_lists(sc);
 }
 
-__global__ void __launch_bounds__(256) rate32_kernel(D32 d) {
+static __global__ void __launch_bounds__(256) rate32_kernel(D32 d) {
   __shared__ double red[32];
   __shared__ bool last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -820,7 +749,7 @@ __global__ void __launch_bounds__(256) rate32_kernel(D32 d) {
 }
 
 // Mass sum(eta0 - z0) dx dy, accumulated in FP64 in a fixed order.
-__global__ void __launch_bounds__(256) mass32_kernel(D32 d) {
+static __global__ void __launch_bounds__(256) mass32_kernel(D32 d) {
   __shared__ double red[32];
   __shared__ bool last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -144,9 +144,12 @@ def floodplain(nx=2000, ny=1000, dx=2.0, seed=2010, hurst=0.8, relief=3.0, chann
     eta = None
     if initial == "channel":
         eta = np.where(in_ch, z + channel_fill, z)
+    tk, qk = [0.0, t_peak, 2.0 * t_peak], [0.0, q_peak, 0.0]
+    if t_end > 2.0 * t_peak:
+        tk.append(t_end)
+        qk.append(0.0)
     inflow = Inflow(edge=WEST, s0=yc(0.0) - 0.5 * inflow_len, length=inflow_len,
-                    t_knots=np.array([0.0, t_peak, 2.0 * t_peak, max(t_end, 2.0 * t_peak)]),
-                    q_knots=np.array([0.0, q_peak, 0.0, 0.0]))
+                    t_knots=np.array(tk), q_knots=np.array(qk))
     gx = (np.arange(ngauge) + 0.5) * Lx / ngauge
     gauges = np.stack([gx, yc(gx)], axis=1)
     return Case(name=f"floodplain{nx}x{ny}", nx=nx, ny=ny, dx=dx, dy=dx, z_corner=z,
@@ -235,3 +238,28 @@ def urban(nx=8192, ny=8192, dx=0.5, seed=2012, slope=1.0 / 500.0, noise=0.05, nb
                 manning=man, bc=(OPEN, OPEN, OPEN, OPEN), cfl=0.33, t_end=1800.0,
                 rain=(rain_mm_h / 1000.0 / 3600.0, 0.0, rain_minutes * 60.0),
                 point=(0.5 * Lx, 0.5 * Ly, q_point), dt_max=dt_max)
+
+
+# ----------------------------------------------------------------------------
+# Ensembles
+# ----------------------------------------------------------------------------
+
+def ensemble(n=256, seed=3000, nx_range=(64, 1024), ny_range=(64, 512), dx=2.0,
+             n_range=(0.02, 0.08), q_range=(5.0, 40.0), t_peak=1800.0, t_end=3600.0, ngauge=4,
+             sample_every=60.0):
+    """`n` floodplain scenarios of the recipe above, scenario s drawn with seed + s:
+    nx and ny log-uniform in their ranges, one uniform Manning n in `n_range`, an
+    inflow peak uniform in `q_range` (triangle peaking at `t_peak`), the terrain of
+    the floodplain generator at that size (seed + s), starting dry."""
+    cases = []
+    for s in range(n):
+        rng = np.random.Generator(np.random.PCG64(seed + s))
+        nx = int(round(np.exp(rng.uniform(np.log(nx_range[0]), np.log(nx_range[1])))))
+        ny = int(round(np.exp(rng.uniform(np.log(ny_range[0]), np.log(ny_range[1])))))
+        man = float(rng.uniform(*n_range))
+        q = float(rng.uniform(*q_range))
+        c = floodplain(nx=nx, ny=ny, dx=dx, seed=seed + s, q_peak=q, t_peak=t_peak, t_end=t_end,
+                       n_channel=man, n_plain=man, ngauge=ngauge, sample_every=sample_every)
+        c.name = f"member{s}_{nx}x{ny}"
+        cases.append(c)
+    return cases

@@ -1,6 +1,8 @@
 """The C-ABI library builds, loads and exports every symbol include/dg2.h declares
 (no compute calls: runs without a GPU)."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -55,3 +57,30 @@ def test_product_path_does_not_reference_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "dg2_oracle" not in text, f
+
+
+def test_ensemble_host_only_calls_without_gpu():
+    from paper_2010_02003_gb300 import binding as B
+    B.load()
+    assert B.dg2_ens_workspace_bytes([]) == 0
+    with pytest.raises(B.Dg2Error) as e:
+        B.dg2_ens_create([], 0, 0, 0)
+    assert e.value.code == B.DG2_E_ARG
+
+
+def test_ensemble_recipe_sizes_and_seeds():
+    """The 256-member recipe: sizes log-uniform in [64, 1024] x [64, 512], ~19M cells in
+    all, one Manning n and one inflow peak per member, reproducible from the seed."""
+    from paper_2010_02003_gb300 import inputs
+    a = inputs.ensemble(n=256)
+    nx = [c.nx for c in a]
+    ny = [c.ny for c in a]
+    assert 64 <= min(nx) and max(nx) <= 1024 and 64 <= min(ny) and max(ny) <= 512
+    assert 1.5e7 < sum(x * y for x, y in zip(nx, ny)) < 2.5e7
+    for c in a[:8]:
+        assert np.unique(c.manning).size == 1 and 0.02 <= c.manning[0, 0] <= 0.08
+        q = c.inflows[0].q_knots.max()
+        assert 5.0 <= q <= 40.0 and c.inflows[0].t_knots[1] == 1800.0
+    b = inputs.ensemble(n=3)
+    for x, y in zip(a[:3], b):
+        assert x.nx == y.nx and np.array_equal(x.z_corner, y.z_corner)
