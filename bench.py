@@ -10,6 +10,10 @@ variant then times its steps from that saved state.  A step is one full RK2 time
 [local limiting], both stages with fluxes, operators, wet-dry treatment,
 Courant reduction, time/ledger update) through the C ABI.
 
+The ensemble variant runs 256 members of log-uniform sizes (18.6 M cells) from
+dry to t = 1 h in FP32 with one set of launches per step, after the tile-shape
+autotuner.
+
 One line of JSON on rank 0.  With --impl reference the CPU oracle is timed
 instead (a bounded 500 x 250 sample of the same workload recipe).
 """
@@ -337,6 +341,67 @@ VARIANTS = [
     ("fp32_nl_urban", "urban", 0, 1),      # 8192 x 8192, rain + point inflow, 500 steps
 ]
 URBAN_STEPS = 500
+ENS_MEMBERS, ENS_T_END = 256, 3600.0
+ENS_SEQ_SAMPLE, ENS_SEQ_T = 16, 300.0
+
+
+def ensemble_variant(B, torch, inputs, n=ENS_MEMBERS, t_end=ENS_T_END):
+    """The ensemble recipe: n floodplain members of log-uniform sizes, each with its own
+    roughness, inflow and Courant step, FP32 DG2-NL, run from dry to t_end in one set of
+    launches per step (CUDA graphs), tile shape chosen by the autotuner first.  Timed
+    with CUDA events on the ensemble's stream; cell-updates count every cell of every
+    member for each of its own steps."""
+    cases = inputs.ensemble(n=n)
+    mem = [B.solver_from_case(c, variant=B.DG2_NL, precision=B.DG2_FP32) for c in cases]
+    ens = B.Ensemble(mem)
+    st = ens.stream
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    shape = ens.autotune(t_end, 16)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    steps0 = [m.steps() for m in mem]
+    tiles0 = [m.tile_stats()[3] for m in mem]
+    l0 = ens.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    nsteps = ens.run_to(t_end)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    upd = sum(c.nx * c.ny * (m.steps() - a) for c, m, a in zip(cases, mem, steps0))
+    tiles = sum(m.tile_stats()[3] - a for m, a in zip(mem, tiles0))
+    cells = sum(c.nx * c.ny for c in cases)
+    wet = sum(float((m.state()[0] > 1e-5).sum()) for m in mem) / cells
+    out = {"value": upd / (ms * 1e-3), "unit": "cell-updates/s", "members": n, "cells": cells,
+           "t_end_s": t_end, "ensemble_steps": nsteps, "member_cell_updates": upd,
+           "ms_total": ms, "ms_per_step": ms / max(nsteps, 1), "tile_shape": list(shape),
+           "autotune_ms_per_step": [float(x) for x in ens.tune_times()],
+           "autotune_s": tune_s, "launches": ens.launches() - l0,
+           "computed_cells": tiles * shape[0] * shape[1], "wet_fraction_end": wet}
+    # whole-step HBM figure: unique bytes of friction + both stages per computed cell
+    per_cell = sum(v if isinstance(v, int) else v["nl"] for v in BYTES_PER_CELL["fp32"].values())
+    out["step_bytes_per_s"] = per_cell * out["computed_cells"] / (ms * 1e-3)
+    ens.close()
+    for m in mem:
+        m.close()
+    # the same kind of members one after another through the single-problem path
+    seq = inputs.ensemble(n=ENS_SEQ_SAMPLE)
+    sol = [B.solver_from_case(c, variant=B.DG2_NL, precision=B.DG2_FP32) for c in seq]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s_ in sol:
+        s_.run_to(ENS_SEQ_T)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    seq_upd = sum(c.nx * c.ny * s_.steps() for c, s_ in zip(seq, sol))
+    out["sequential"] = {"members": ENS_SEQ_SAMPLE, "t_end_s": ENS_SEQ_T,
+                         "value": seq_upd / seq_s, "unit": "cell-updates/s",
+                         "how": "dg2_run_to on each member in turn (host wall clock)"}
+    for s_ in sol:
+        s_.close()
+    return out
 
 
 def main():
@@ -394,6 +459,18 @@ def main():
         results[key] = run
         torch.cuda.empty_cache()
 
+    ens = None
+    if not only or "fp32_nl_ensemble" in only:
+        barrier(world)
+        ens = ensemble_variant(B, torch, inputs)
+        if "fp64_nl" in results:
+            ens["vs_fp64_single_nl"] = ens["value"] / results["fp64_nl"]["value"]
+        torch.cuda.empty_cache()
+
+    if not results:
+        if rank == 0 and ens is not None:
+            print(json.dumps({"metric": METRIC, "variants": {"fp32_nl_ensemble": ens}}))
+        return
     head = "fp64_ll" if "fp64_ll" in results else next(iter(results))
     hd = results[head]
     e2e = None
@@ -414,6 +491,8 @@ def main():
                         "steps": r["steps"], "cells": r["cells"],
                         "wet_fraction": r["wet_fraction"], "roofline": r["roofline"]}
                     for k, r in results.items() if k != head}
+        if ens is not None:
+            variants["fp32_nl_ensemble"] = ens
         line = {"metric": METRIC, "value": hd["value"], "unit": "cell-updates/s", "n_gpus": world,
                 "steps": hd["steps"], "warmup": warmup, "ms_per_step": hd["ms_max"] / hd["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
