@@ -58,7 +58,7 @@ typedef struct {
     double s0, len;        /* segment [s0, s0+len] along the edge (m) */
     int nk;
     double tk[MAX_KNOTS];  /* piecewise-linear hydrograph Q(t), m^3/s */
-    double qk[MAX_KNOTS];
+    real qk[MAX_KNOTS];
 } inflow_t;
 
 typedef struct {
@@ -71,13 +71,13 @@ typedef struct {
     inflow_t in[MAX_INFLOW];
     double rain, rain_t0, rain_t1;   /* m/s over [t0, t1) */
     double px, py, qp;               /* point inflow (m^3/s) at (px, py) */
-    double *z;             /* 3 planes: z0, z1x, z1y (Eq. 3 applied to the DEM) */
-    double *nm;            /* Manning n per cell */
-    double *U;             /* 9 planes (Eq. 2) */
-    double *U1, *L, *Ls;   /* stage state, operator output, limiter scratch */
+    real *z;               /* 3 planes: z0, z1x, z1y (Eq. 3 applied to the DEM) */
+    real *nm;              /* Manning n per cell */
+    real *U;               /* 9 planes (Eq. 2) */
+    real *U1, *L, *Ls;     /* stage state, operator output, limiter scratch */
     double t;
-    double ledger;         /* initial mass + boundary and source volumes */
-    double last_bflux;     /* boundary + source volume rate of the last operator call */
+    real ledger;           /* initial mass + boundary and source volumes */
+    real last_bflux;       /* boundary + source volume rate of the last operator call */
 } orc_t;
 
 /* ------------------------------------------------------------------ */
@@ -169,7 +169,7 @@ static st3 hll_y(const orc_t *o, st3 Ss, st3 Ns)
 /* ------------------------------------------------------------------ */
 
 /* Piecewise-linear hydrograph, held constant outside its knots. */
-static double hydrograph(const inflow_t *f, double t)
+static real hydrograph(const inflow_t *f, double t)
 {
     if (f->nk <= 0) return 0.0;
     if (t <= f->tk[0]) return f->qk[0];
@@ -230,7 +230,7 @@ static st3 ghost(const orc_t *o, int edge, double s, st3 in, double t)
 /* Face limits of the planar solution (Eq. 2 evaluated at E, W, N, S)  */
 /* ------------------------------------------------------------------ */
 
-static st3 limit_at(const orc_t *o, const double *U, int i, int j, int face)
+static st3 limit_at(const orc_t *o, const real *U, int i, int j, int face)
 {
     size_t N = (size_t)o->nx * o->ny, c = (size_t)j * o->nx + i;
     int m = (face == EE || face == EW) ? 1 : 2;
@@ -250,7 +250,7 @@ static real zlimit_at(const orc_t *o, int i, int j, int face)
 
 /* Limit on the far side of face `face` of cell (i, j): the neighbour's
  * opposite limit, or the boundary ghost built from the cell's own limit. */
-static st3 outer_limit(const orc_t *o, const double *U, int i, int j, int face, double t)
+static st3 outer_limit(const orc_t *o, const real *U, int i, int j, int face, double t)
 {
     switch (face) {
     case EE: return i + 1 < o->nx ? limit_at(o, U, i + 1, j, EW)
@@ -281,14 +281,14 @@ static int source_cell(const orc_t *o)
 
 /* Writes the 9 operator planes of state U at time t into Lout and returns
  * the rate (m^3/s) at which boundary fluxes and sources add water. */
-static double spatial_operator(const orc_t *o, const double *U, double t, double *Lout)
+static real spatial_operator(const orc_t *o, const real *U, double t, real *Lout)
 {
     const int nx = o->nx, ny = o->ny;
     const size_t N = (size_t)nx * ny;
     const real g = o->g, dx = o->dx, dy = o->dy, s3 = sqrt(3.0);
     const int csrc = source_cell(o);
     const int raining = (o->rain != 0.0 && t >= o->rain_t0 && t < o->rain_t1);
-    double bsum = 0.0;
+    real bsum = 0.0;
 
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -368,7 +368,7 @@ static void friction_point(const orc_t *o, real n, real dt, real h, real *qx, re
     *qy = *qy / d;
 }
 
-static void apply_friction(orc_t *o, double *U, double dt)
+static void apply_friction(orc_t *o, real *U, double dt)
 {
     const size_t N = (size_t)o->nx * o->ny;
     const real s3 = sqrt(3.0);
@@ -435,11 +435,11 @@ static real limit_component(const orc_t *o, real half, real k0w, real k1w, real 
 }
 
 /* Jacobi sweep: Uout = limited copy of Uin. */
-static void apply_limiter(const orc_t *o, const double *Uin, double *Uout)
+static void apply_limiter(const orc_t *o, const real *Uin, real *Uout)
 {
     const int nx = o->nx, ny = o->ny;
     const size_t N = (size_t)nx * ny;
-    memcpy(Uout, Uin, 9 * N * sizeof(double));
+    memcpy(Uout, Uin, 9 * N * sizeof(real));
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
@@ -452,7 +452,7 @@ static void apply_limiter(const orc_t *o, const double *Uin, double *Uout)
                 if (Uin[cl] <= tol || Uin[c] <= tol || Uin[ch] <= tol) continue;   /* wet-dry front */
                 real half = 0.5 * (d == 1 ? o->dx : o->dy);
                 /* free-surface elevation eta = h + z instead of h */
-                const double *z0 = o->z, *z1 = o->z + d * N;
+                const real *z0 = o->z, *z1 = o->z + d * N;
                 real e1 = limit_component(o, half,
                                           Uin[cl] + z0[cl], Uin[PL(0, d) * N + cl] + z1[cl],
                                           Uin[c] + z0[c], Uin[PL(0, d) * N + c] + z1[c],
@@ -460,7 +460,7 @@ static void apply_limiter(const orc_t *o, const double *Uin, double *Uout)
                 if (e1 != Uin[PL(0, d) * N + c] + z1[c])
                     Uout[PL(0, d) * N + c] = e1 - z1[c];
                 for (int v = 1; v <= 2; ++v) {
-                    const double *k0 = Uin + PL(v, 0) * N, *k1 = Uin + PL(v, d) * N;
+                    const real *k0 = Uin + PL(v, 0) * N, *k1 = Uin + PL(v, d) * N;
                     Uout[PL(v, d) * N + c] = limit_component(o, half, k0[cl], k1[cl], k0[c], k1[c],
                                                              k0[ch], k1[ch]);
                 }
@@ -482,7 +482,7 @@ static void apply_limiter(const orc_t *o, const double *Uin, double *Uout)
  *    cell's mean free surface h0 + z0 -- there the planar solution is kept, so
  *    still water blocked by high ground stays balanced through z*.
  * Averages are never changed, so mass is untouched. */
-static void dry_reset(const orc_t *o, double *U)
+static void dry_reset(const orc_t *o, real *U)
 {
     const size_t N = (size_t)o->nx * o->ny;
     for (size_t c = 0; c < N; ++c) {
@@ -529,20 +529,20 @@ double orc_cfl_dt(const orc_t *o)
 void orc_step(orc_t *o, double dt)
 {
     const size_t N = (size_t)o->nx * o->ny;
-    double *Un = o->U, *U1 = o->U1, *L = o->L;
+    real *Un = o->U, *U1 = o->U1, *L = o->L;
     apply_friction(o, Un, dt);
     if (o->limiter) {
         apply_limiter(o, Un, o->Ls);
-        memcpy(Un, o->Ls, 9 * N * sizeof(double));
+        memcpy(Un, o->Ls, 9 * N * sizeof(real));
     }
-    double b1 = spatial_operator(o, Un, o->t, L);
+    real b1 = spatial_operator(o, Un, o->t, L);
     for (size_t k = 0; k < 9 * N; ++k) U1[k] = Un[k] + dt * L[k];
     dry_reset(o, U1);
     if (o->limiter) {
         apply_limiter(o, U1, o->Ls);
-        memcpy(U1, o->Ls, 9 * N * sizeof(double));
+        memcpy(U1, o->Ls, 9 * N * sizeof(real));
     }
-    double b2 = spatial_operator(o, U1, o->t + dt, L);
+    real b2 = spatial_operator(o, U1, o->t + dt, L);
     for (size_t k = 0; k < 9 * N; ++k) Un[k] = 0.5 * (Un[k] + U1[k] + dt * L[k]);
     dry_reset(o, Un);
     o->last_bflux = 0.5 * (b1 + b2);
@@ -556,7 +556,7 @@ void orc_step(orc_t *o, double dt)
 
 /* Modes of a field given at the (nx+1) x (ny+1) corner nodes: face-centre
  * values are averages of the two corners of each face, then Eq. 3. */
-static void corner_modes(int nx, int ny, const double *f, double *m0, double *m1x, double *m1y)
+static void corner_modes(int nx, int ny, const double *f, real *m0, real *m1x, real *m1y)
 {
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -592,12 +592,12 @@ orc_t *orc_create(int nx, int ny, double dx, double dy, double g, double cfl, do
     o->g = g; o->cfl = cfl; o->tol_dry = tol_dry; o->ds_thresh = ds_thresh; o->dt_max = dt_max;
     o->limiter = limiter;
     for (int k = 0; k < 4; ++k) o->bc[k] = bc[k];
-    o->z = (double *)calloc(3 * N, sizeof(double));
-    o->nm = (double *)calloc(N, sizeof(double));
-    o->U = (double *)calloc(9 * N, sizeof(double));
-    o->U1 = (double *)calloc(9 * N, sizeof(double));
-    o->L = (double *)calloc(9 * N, sizeof(double));
-    o->Ls = (double *)calloc(9 * N, sizeof(double));
+    o->z = (real *)calloc(3 * N, sizeof(real));
+    o->nm = (real *)calloc(N, sizeof(real));
+    o->U = (real *)calloc(9 * N, sizeof(real));
+    o->U1 = (real *)calloc(9 * N, sizeof(real));
+    o->L = (real *)calloc(9 * N, sizeof(real));
+    o->Ls = (real *)calloc(9 * N, sizeof(real));
     return o;
 }
 
@@ -617,7 +617,7 @@ void orc_set_dem(orc_t *o, const double *z_corner, const double *manning, double
     size_t N = (size_t)nx * ny, NC = (size_t)(nx + 1) * (ny + 1);
     corner_modes(nx, ny, z_corner, o->z, o->z + N, o->z + 2 * N);
     for (size_t c = 0; c < N; ++c) o->nm[c] = manning ? manning[c] : n_uniform;
-    memset(o->U, 0, 9 * N * sizeof(double));
+    memset(o->U, 0, 9 * N * sizeof(real));
     if (eta_corner) {
         /* corner depths eta - z, left unclipped so the planar depth keeps the
          * free surface flat; a cell whose average depth is not positive is dry */
@@ -648,22 +648,35 @@ void orc_set_sources(orc_t *o, double rain, double t0, double t1, double px, dou
     o->px = px; o->py = py; o->qp = qp;
 }
 
+/* Copies between the caller's double arrays and the oracle's `real` arrays. */
+static void to_double(double *dst, const real *src, size_t n)
+{
+    for (size_t k = 0; k < n; ++k) dst[k] = src[k];
+}
+
+static real *from_double(const double *src, size_t n)
+{
+    real *dst = (real *)calloc(n, sizeof(real));
+    for (size_t k = 0; k < n; ++k) dst[k] = src[k];
+    return dst;
+}
+
 void orc_get_state(const orc_t *o, double *planes, double *t)
 {
-    memcpy(planes, o->U, 9 * (size_t)o->nx * o->ny * sizeof(double));
+    to_double(planes, o->U, 9 * (size_t)o->nx * o->ny);
     if (t) *t = o->t;
 }
 
 void orc_set_state(orc_t *o, const double *planes, double t)
 {
-    memcpy(o->U, planes, 9 * (size_t)o->nx * o->ny * sizeof(double));
+    for (size_t k = 0; k < 9 * (size_t)o->nx * o->ny; ++k) o->U[k] = planes[k];
     o->t = t;
     o->ledger = orc_mass(o);
 }
 
 void orc_get_topo(const orc_t *o, double *planes3)
 {
-    memcpy(planes3, o->z, 3 * (size_t)o->nx * o->ny * sizeof(double));
+    to_double(planes3, o->z, 3 * (size_t)o->nx * o->ny);
 }
 
 double orc_time(const orc_t *o) { return o->t; }
@@ -672,11 +685,33 @@ double orc_ledger(const orc_t *o) { return o->ledger; }
 /* Exposed pieces for the pin tests. */
 double orc_operator(orc_t *o, const double *U, double t, double *Lout)
 {
-    return spatial_operator(o, U, t, Lout);
+    const size_t n = 9 * (size_t)o->nx * o->ny;
+    real *u = from_double(U, n), *l = (real *)calloc(n, sizeof(real));
+    double b = spatial_operator(o, u, t, l);
+    to_double(Lout, l, n);
+    free(u);
+    free(l);
+    return b;
 }
 
-void orc_friction(orc_t *o, double *U, double dt) { apply_friction(o, U, dt); }
-void orc_limit(const orc_t *o, const double *Uin, double *Uout) { apply_limiter(o, Uin, Uout); }
+void orc_friction(orc_t *o, double *U, double dt)
+{
+    const size_t n = 9 * (size_t)o->nx * o->ny;
+    real *u = from_double(U, n);
+    apply_friction(o, u, dt);
+    to_double(U, u, n);
+    free(u);
+}
+
+void orc_limit(const orc_t *o, const double *Uin, double *Uout)
+{
+    const size_t n = 9 * (size_t)o->nx * o->ny;
+    real *u = from_double(Uin, n), *v = (real *)calloc(n, sizeof(real));
+    apply_limiter(o, u, v);
+    to_double(Uout, v, n);
+    free(u);
+    free(v);
+}
 void orc_hll(const orc_t *o, int dir, const double *l3, const double *r3, double *f3)
 {
     st3 a = mk(l3[0], l3[1], l3[2]), b = mk(r3[0], r3[1], r3[2]);

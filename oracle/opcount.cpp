@@ -37,7 +37,8 @@ struct Cnt {
   inline Cnt operator op(Cnt a, Cnt b) { opc::counter(); return Cnt(a.v op b.v); }     \
   inline Cnt operator op(Cnt a, double b) { opc::counter(); return Cnt(a.v op b); }    \
   inline Cnt operator op(double a, Cnt b) { opc::counter(); return Cnt(a op b.v); }    \
-  inline Cnt operator op(Cnt a, int b) { opc::counter(); return Cnt(a.v op b); }
+  inline Cnt operator op(Cnt a, int b) { opc::counter(); return Cnt(a.v op b); }         \
+  inline Cnt operator op(int a, Cnt b) { opc::counter(); return Cnt(a op b.v); }
 BIN(+, count_add)
 BIN(-, count_add)
 BIN(*, count_mul)
@@ -51,6 +52,7 @@ inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
 CMP(<) CMP(>) CMP(<=) CMP(>=) CMP(==) CMP(!=)
 #undef CMP
 inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
 inline Cnt sqrt(Cnt a) { opc::count_sqrt(); return Cnt(std::sqrt(a.v)); }
 inline Cnt cbrt(Cnt a) { opc::count_cbrt(); return Cnt(std::cbrt(a.v)); }
 inline Cnt fabs(Cnt a) { return Cnt(std::fabs(a.v)); }
