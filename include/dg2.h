@@ -272,6 +272,71 @@ int64_t dg2_ens_launch_count(const dg2_ens *ens);
 /* Releases the ensemble (members and workspace stay the caller's). */
 int dg2_ens_destroy(dg2_ens *ens);
 
+/* ------------------------------------------------------------------------
+ * Discrete adjoint of the FP64 DG2-NL step (Sec. 2.1.2-2.1.3).
+ *
+ * Problem: nsteps DG2-NL steps (friction, the two RK stages of Eqs. 4-5, the
+ * wet-dry treatment) from a given state with a given sequence of step sizes
+ * (frozen: no derivative through the Courant step), one optional inflow
+ * segment with a piecewise-linear hydrograph, and the misfit
+ *     J = sum_s sum_g (h_g(U^{k_s}) - obs[s][g])^2
+ * of gauge depths h_g = max(0, h0 + xi h1x + eta h1y) sampled after step
+ * counts k_s (0..nsteps).  dg2_adj_gradient gives dJ/dn for the Manning n of
+ * every cell and dJ/dq for every hydrograph knot discharge, by a reverse
+ * sweep through each step's stages with the wet-dry, revision, HLL-regime
+ * and ghost branches of the forward state frozen, and binomial checkpointing
+ * of the step states in nsnap snapshot slots.  Rain and point sources are not
+ * part of the problem.  Planes are dense (ny rows of nx, x fastest).
+ * ---------------------------------------------------------------------- */
+typedef struct dg2_adj dg2_adj;
+
+/* Workspace bytes (0 if a size is invalid: nx, ny, nsnap, max_steps >= 1,
+ * max_gauges >= 0).  About (nsnap + 10) state-sized buffers of 9 planes. */
+size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps);
+
+/* params: g, tol_dry, bc[4] are used; variant must be DG2_NL and precision
+ * DG2_FP64 (DG2_E_ARG otherwise).  Workspace and stream as for
+ * dg2_init_grid. */
+int dg2_adj_create(dg2_adj **out, int nx, int ny, double dx, double dy, const dg2_params *params,
+                   int nsnap, int max_gauges, int max_steps, void *dev_workspace,
+                   size_t ws_bytes, void *cuda_stream);
+
+/* The problem: topography modes z3 (3 planes z0, z1x, z1y, as dg2_get_topo
+ * returns), the initial state (9 planes, as dg2_get_state returns) at time
+ * t0, the Manning n of every cell, the inflow segment (inflow_edge < 0: none;
+ * segment [s0, s0 + len] along the edge, nknots increasing times and
+ * discharges m^3/s) and ngauge gauge positions (x, y) in metres.  Host
+ * arrays, copied.  DG2_E_ARG on a NULL required array, bad knots, an empty
+ * segment or ngauge outside 0..max_gauges. */
+int dg2_adj_set_problem(dg2_adj *adj, const double *z3, const double *state9, double t0,
+                        const double *manning, int inflow_edge, double s0, double len,
+                        const double *t_knots, const double *q_knots, int nknots,
+                        const double *gauge_xy, int ngauge);
+
+/* Replaces the parameters (either may be NULL): Manning n of every cell and
+ * the knot discharges (same count as set). */
+int dg2_adj_set_params(dg2_adj *adj, const double *manning, const double *q_knots);
+
+/* Step sizes dts[nsteps] (> 0, nsteps <= max_steps), the step count after
+ * which each of nsamples samples is taken (0..nsteps) and the observed depths
+ * obs[nsamples][ngauge]. */
+int dg2_adj_set_schedule(dg2_adj *adj, const double *dts, int nsteps, const int *sample_steps,
+                         int nsamples, const double *obs);
+
+/* Runs the forward steps: *loss = J; gauge_h (may be NULL) receives the
+ * sampled depths [nsamples][ngauge]. */
+int dg2_adj_forward(dg2_adj *adj, double *loss, double *gauge_h);
+
+/* Forward and reverse sweeps: *loss = J, grad_manning[ny*nx] = dJ/dn,
+ * grad_q[nknots] = dJ/dq (either may be NULL).  DG2_E_NONFINITE if J is not
+ * finite. */
+int dg2_adj_gradient(dg2_adj *adj, double *loss, double *grad_manning, double *grad_q);
+
+/* Forward steps and reverse steps executed so far (checkpointing cost). */
+int dg2_adj_counts(const dg2_adj *adj, int64_t *forward_steps, int64_t *reverse_steps);
+
+int dg2_adj_destroy(dg2_adj *adj);
+
 #ifdef __cplusplus
 }
 #endif

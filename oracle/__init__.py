@@ -18,6 +18,9 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   - limiter: pinned by brute-force detector / minmod cases.
   - inflow ghost and point/rain sources: parity unpinned beyond the mass
     ledger (the paper does not define them).
+  - taped derivatives (``tape.cpp``, :func:`taped_gradient`): the same C
+    source compiled with a recording scalar type; pinned against central
+    finite differences of the oracle itself.
 """
 from __future__ import annotations
 
@@ -30,6 +33,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dg2_oracle.c")
 _LIB = os.path.join(_HERE, "libdg2_oracle.so")
+_TAPE_SRC = os.path.join(_HERE, "tape.cpp")
+_TAPE_LIB = os.path.join(_HERE, "liboracle_tape.so")
 
 WALL, OPEN = 0, 1
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
@@ -45,6 +50,64 @@ def build(force: bool = False) -> str:
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_tape(force: bool = False) -> str:
+    """Compile the taped oracle (tape.cpp including dg2_oracle.c) with g++."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_TAPE_SRC))
+    if force or not os.path.exists(_TAPE_LIB) or os.path.getmtime(_TAPE_LIB) < newest:
+        tmp = _TAPE_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _TAPE_SRC])
+        os.replace(tmp, _TAPE_LIB)
+    return _TAPE_LIB
+
+
+_tape = None
+
+
+def taped_gradient(case, manning, q_knots, dts, sample_steps, obs, limiter=False):
+    """Misfit J = sum over samples and gauges of (h_gauge - obs)^2 of the oracle run
+    of len(dts) steps from ``case`` (DEM, water, edges, its one inflow with the knot
+    discharges ``q_knots``, Manning field ``manning`` (ny, nx)), sampled after the
+    step counts ``sample_steps`` at ``case.gauges``; returns (J, dJ/dn (ny, nx),
+    dJ/dq (nk,)) from the oracle's own taped derivatives."""
+    global _tape
+    if _tape is None:
+        _tape = ctypes.CDLL(build_tape())
+        f = _tape.orc_tape_gradient
+        f.restype = ctypes.c_double
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    nx, ny = case.nx, case.ny
+    bc = (ctypes.c_int * 4)(*[int(b) for b in case.bc])
+    z = np.ascontiguousarray(case.z_corner, dtype=np.float64)
+    eta = None if case.eta_corner is None else np.ascontiguousarray(case.eta_corner, dtype=np.float64)
+    man = np.ascontiguousarray(manning, dtype=np.float64).reshape(ny, nx)
+    if case.inflows:
+        fl = case.inflows[0]
+        edge, s0, ln = int(fl.edge), float(fl.s0), float(fl.length)
+        tk = np.ascontiguousarray(fl.t_knots, dtype=np.float64)
+        qk = np.ascontiguousarray(q_knots, dtype=np.float64)
+    else:
+        edge, s0, ln = -1, 0.0, 0.0
+        tk = np.zeros(1)
+        qk = np.zeros(1)
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    ss = np.ascontiguousarray(sample_steps, dtype=np.int32)
+    g = np.ascontiguousarray(np.asarray(case.gauges, dtype=np.float64).reshape(-1, 2))
+    ob = np.ascontiguousarray(obs, dtype=np.float64).reshape(len(ss), g.shape[0])
+    gn = np.zeros((ny, nx))
+    gq = np.zeros(len(qk))
+    J = _tape.orc_tape_gradient(
+        ctypes.c_int(nx), ctypes.c_int(ny), ctypes.c_double(case.dx), ctypes.c_double(case.dy),
+        ctypes.c_double(9.80665), ctypes.c_double(case.cfl), ctypes.c_double(1e-5),
+        ctypes.c_double(10.0), ctypes.c_double(case.dt_max), ctypes.c_int(int(bool(limiter))), bc,
+        dp(z), None if eta is None else dp(eta), dp(man), ctypes.c_int(edge), ctypes.c_double(s0),
+        ctypes.c_double(ln), dp(tk), dp(qk), ctypes.c_int(len(qk) if edge >= 0 else 0),
+        ctypes.c_int(len(d)), dp(d), ctypes.c_int(len(ss)),
+        ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_int(g.shape[0]), dp(g), dp(ob),
+        dp(gn), dp(gq))
+    return J, gn, gq
 
 
 def _load():

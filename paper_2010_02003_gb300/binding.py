@@ -34,6 +34,9 @@ EXPORTS = (
     "dg2_ens_workspace_bytes", "dg2_ens_create", "dg2_ens_run_to", "dg2_ens_autotune",
     "dg2_ens_set_tile_shape", "dg2_ens_tile_shape", "dg2_ens_tune_times",
     "dg2_ens_launch_count", "dg2_ens_destroy",
+    "dg2_adj_workspace_bytes", "dg2_adj_create", "dg2_adj_set_problem", "dg2_adj_set_params",
+    "dg2_adj_set_schedule", "dg2_adj_forward", "dg2_adj_gradient", "dg2_adj_counts",
+    "dg2_adj_destroy",
 )
 DG2_NOALLOC_MAX_ROWS = 65536
 
@@ -102,6 +105,15 @@ def load(path: str = LIB_PATH):
         "dg2_ens_tune_times": (I, [P, dp, I]),
         "dg2_ens_launch_count": (ctypes.c_int64, [P]),
         "dg2_ens_destroy": (I, [P]),
+        "dg2_adj_workspace_bytes": (ctypes.c_size_t, [I, I, I, I, I]),
+        "dg2_adj_create": (I, [ctypes.POINTER(P), I, I, D, D, pp, I, I, I, P, ctypes.c_size_t, P]),
+        "dg2_adj_set_problem": (I, [P, dp, dp, D, dp, I, D, D, dp, dp, I, dp, I]),
+        "dg2_adj_set_params": (I, [P, dp, dp]),
+        "dg2_adj_set_schedule": (I, [P, dp, I, ip, I, dp]),
+        "dg2_adj_forward": (I, [P, dp, dp]),
+        "dg2_adj_gradient": (I, [P, dp, dp, dp]),
+        "dg2_adj_counts": (I, [P, i64p, i64p]),
+        "dg2_adj_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -311,6 +323,69 @@ def dg2_ens_destroy(ens):
     _check(load().dg2_ens_destroy(ens))
 
 
+def dg2_adj_workspace_bytes(nx, ny, nsnap, max_gauges, max_steps) -> int:
+    return int(load().dg2_adj_workspace_bytes(nx, ny, nsnap, max_gauges, max_steps))
+
+
+def dg2_adj_create(nx, ny, dx, dy, params, nsnap, max_gauges, max_steps, dev_ptr, ws_bytes,
+                   stream_ptr):
+    h = ctypes.c_void_p()
+    _check(load().dg2_adj_create(ctypes.byref(h), nx, ny, float(dx), float(dy), ctypes.byref(params),
+                                 nsnap, max_gauges, max_steps, ctypes.c_void_p(dev_ptr), ws_bytes,
+                                 ctypes.c_void_p(stream_ptr)))
+    return h
+
+
+def dg2_adj_set_problem(adj, z3, state9, t0, manning, inflow_edge=-1, s0=0.0, length=0.0,
+                        t_knots=None, q_knots=None, gauge_xy=None):
+    z, u, m = _f64(z3), _f64(state9), _f64(manning)
+    tk, qk = _f64(t_knots), _f64(q_knots)
+    g = None if gauge_xy is None else _f64(np.asarray(gauge_xy, dtype=np.float64).reshape(-1, 2))
+    _check(load().dg2_adj_set_problem(adj, _dp(z), _dp(u), float(t0), _dp(m), int(inflow_edge),
+                                      float(s0), float(length), _dp(tk), _dp(qk),
+                                      0 if tk is None else len(tk), _dp(g),
+                                      0 if g is None else g.shape[0]))
+
+
+def dg2_adj_set_params(adj, manning=None, q_knots=None):
+    m, q = _f64(manning), _f64(q_knots)
+    _check(load().dg2_adj_set_params(adj, _dp(m), _dp(q)))
+
+
+def dg2_adj_set_schedule(adj, dts, sample_steps, obs):
+    d = _f64(dts)
+    ss = np.ascontiguousarray(sample_steps, dtype=np.int32)
+    ob = _f64(obs)
+    _check(load().dg2_adj_set_schedule(adj, _dp(d), len(d),
+                                       ss.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(ss),
+                                       _dp(ob)))
+
+
+def dg2_adj_forward(adj, nsamples, ngauge):
+    J = ctypes.c_double()
+    h = np.zeros((nsamples, max(ngauge, 1)))
+    _check(load().dg2_adj_forward(adj, ctypes.byref(J), _dp(h)))
+    return J.value, h[:, :ngauge].copy()
+
+
+def dg2_adj_gradient(adj, nx, ny, nknots):
+    J = ctypes.c_double()
+    gn = np.zeros((ny, nx))
+    gq = np.zeros(max(nknots, 1))
+    _check(load().dg2_adj_gradient(adj, ctypes.byref(J), _dp(gn), _dp(gq)))
+    return J.value, gn, gq[:nknots].copy()
+
+
+def dg2_adj_counts(adj):
+    f, r = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().dg2_adj_counts(adj, ctypes.byref(f), ctypes.byref(r)))
+    return f.value, r.value
+
+
+def dg2_adj_destroy(adj):
+    _check(load().dg2_adj_destroy(adj))
+
+
 # ---- convenience object owning a torch workspace ----------------------------
 
 class Solver:
@@ -479,3 +554,100 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+class Adjoint:
+    """Discrete adjoint of the FP64 DG2-NL step for one problem built from an
+    inputs.Case (DEM, initial water, edges, its first inflow, gauges): the misfit of
+    sampled gauge depths against observations and its gradients with respect to the
+    Manning n of every cell and the inflow knot discharges."""
+
+    def __init__(self, case, *, nsnap=64, max_steps=100000, stream=None, device=None):
+        import torch
+        self.case = case
+        self.nx, self.ny = case.nx, case.ny
+        ref = solver_from_case(case, variant=DG2_NL, precision=DG2_FP64)
+        z3, st = ref.topo(), ref.state()
+        t0 = ref.time()[0]
+        ref.close()
+        p = dg2_default_params()
+        p.cfl, p.dt_max = case.cfl, case.dt_max
+        for k in range(4):
+            p.bc[k] = int(case.bc[k])
+        g = np.zeros((0, 2)) if case.gauges is None else np.asarray(case.gauges, dtype=np.float64)
+        self.ngauge = g.shape[0]
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = dg2_adj_workspace_bytes(self.nx, self.ny, nsnap, max(self.ngauge, 1), max_steps)
+        if nbytes == 0:
+            raise Dg2Error(DG2_E_ARG, "invalid adjoint sizes")
+        with torch.cuda.device(dev):
+            self.stream = torch.cuda.Stream(dev) if stream is None else stream
+            self.stream.wait_stream(torch.cuda.current_stream(dev))
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+            base = (self.workspace.data_ptr() + 255) // 256 * 256
+            self.adj = dg2_adj_create(self.nx, self.ny, case.dx, case.dy, p, nsnap,
+                                      max(self.ngauge, 1), max_steps, base, nbytes,
+                                      self.stream.cuda_stream)
+        man = case.manning if case.manning is not None else np.full((self.ny, self.nx), case.n_uniform)
+        if case.inflows:
+            f = case.inflows[0]
+            self.nknots = len(f.t_knots)
+            dg2_adj_set_problem(self.adj, z3, st, t0, man, f.edge, f.s0, f.length, f.t_knots,
+                                f.q_knots, g)
+        else:
+            self.nknots = 0
+            dg2_adj_set_problem(self.adj, z3, st, t0, man, -1, gauge_xy=g)
+        self.nsamples = 0
+
+    def set_schedule(self, dts, sample_steps, obs):
+        obs = np.asarray(obs, dtype=np.float64).reshape(len(sample_steps), self.ngauge)
+        dg2_adj_set_schedule(self.adj, dts, sample_steps, obs)
+        self.nsamples = len(sample_steps)
+
+    def set_params(self, manning=None, q_knots=None):
+        dg2_adj_set_params(self.adj, manning, q_knots)
+
+    def forward(self):
+        return dg2_adj_forward(self.adj, self.nsamples, self.ngauge)
+
+    def gradient(self):
+        return dg2_adj_gradient(self.adj, self.nx, self.ny, self.nknots)
+
+    def counts(self):
+        return dg2_adj_counts(self.adj)
+
+    def close(self):
+        if getattr(self, "adj", None):
+            dg2_adj_destroy(self.adj)
+            self.adj = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gauge_misfit(adjoint: Adjoint, manning, q_knots):
+    """torch.autograd entry point: J(manning, q_knots) as a 0-d float64 tensor whose
+    backward runs the discrete adjoint (dg2_adj_gradient)."""
+    import torch
+
+    class _GaugeMisfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, n_field, q):
+            adjoint.set_params(n_field.detach().cpu().numpy(), q.detach().cpu().numpy())
+            J, _ = adjoint.forward()
+            ctx.save_for_backward(n_field, q)
+            return torch.tensor(J, dtype=torch.float64, device=n_field.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            n_field, q = ctx.saved_tensors
+            adjoint.set_params(n_field.detach().cpu().numpy(), q.detach().cpu().numpy())
+            _, gn, gq = adjoint.gradient()
+            gn_t = torch.as_tensor(gn, dtype=torch.float64, device=n_field.device)
+            gq_t = torch.as_tensor(gq, dtype=torch.float64, device=q.device)
+            return gout * gn_t, gout * gq_t
+
+    return _GaugeMisfit.apply(manning, q_knots)

@@ -1,0 +1,1298 @@
+// dg2_adj.cu -- discrete adjoint of the FP64 DG2-NL RK2 step (C ABI in
+// include/dg2.h, dg2_adj_*).
+//
+// The problem: K steps of DG2-NL (friction, two RK stages with the wet-dry
+// treatment of each stage) from a given state with a given sequence of step
+// sizes (frozen: no derivative through the Courant step), and the misfit
+//   J = sum over samples s and gauges g of (h_g(U^{k_s}) - obs_{s,g})^2
+// of the sampled gauge depths h_g = max(0, h0 + xi h1x + eta h1y) (the gauge
+// rule of the forward solver).  Gradients of J with respect to the Manning n
+// of every cell and the discharges of the inflow hydrograph's knots.
+//
+// Reverse sweep written by hand: per step, the adjoint of stage 2, of stage 1
+// and of friction, each a transposed stencil evaluated as one pass over the
+// faces (the flux of each face, its two neighbouring cells' operator
+// adjoints, the face Jacobian) and one pass over the cells (the cell's own
+// terms of Eqs. 4-5 and the gather of its four faces).  The local Jacobians
+// (one face flux with its revisions and boundary ghost; one cell's own terms;
+// one cell's friction) come from forward-mode dual numbers run through the
+// same templated point functions the forward kernels of this file use, so
+// values and derivatives follow the same branches: the wet-dry, revision,
+// HLL-regime and ghost branches of the forward state are frozen.  The
+// wet-dry treatment is a frozen 0/1 mask per mode.
+//
+// Step states are kept by binomial checkpointing (Griewank's treeverse): with
+// c snapshot slots, K steps are reversed with at most r extra forward sweeps,
+// r the least integer with C(c + r, c) >= K.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg2.h"
+#include "dg2_internal.h"
+
+namespace dg2 {
+namespace adj {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers
+// ---------------------------------------------------------------------------
+
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+};
+
+template <int N>
+__device__ __forceinline__ Dual<N> cst(double x) {
+  Dual<N> r;
+  r.v = x;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = 0.0;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> var(double x, int k) {
+  Dual<N> r = cst<N>(x);
+  r.d[k] = 1.0;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v / b.v;
+  const double ib = 1.0 / b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, double b) { return a + cst<N>(b); }
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(double a, const Dual<N>& b) { return cst<N>(a) + b; }
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, double b) { return a - cst<N>(b); }
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(double a, const Dual<N>& b) { return cst<N>(a) - b; }
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, double b) {
+  Dual<N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(double a, const Dual<N>& b) { return b * a; }
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, double b) { return a / cst<N>(b); }
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(double a, const Dual<N>& b) { return cst<N>(a) / b; }
+// sqrt, cbrt and |.| with the derivative taken as 0 where the function has
+// none (a zero argument: a dry limit's celerity, a still point's |q|).
+template <int N>
+__device__ __forceinline__ Dual<N> sqrt(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = ::sqrt(a.v);
+  const double s = r.v > 0.0 ? 0.5 / r.v : 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * s;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> cbrt(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = ::cbrt(a.v);
+  const double s = r.v != 0.0 ? 1.0 / (3.0 * r.v * r.v) : 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * s;
+  return r;
+}
+__device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+__device__ __forceinline__ double cbrt(double x) { return ::cbrt(x); }
+__device__ __forceinline__ double val(double x) { return x; }
+template <int N>
+__device__ __forceinline__ double val(const Dual<N>& x) { return x.v; }
+// a if a <= b else b (and the max likewise), selecting the operand
+template <class T>
+__device__ __forceinline__ T tmin(const T& a, const T& b) { return val(b) < val(a) ? b : a; }
+template <class T>
+__device__ __forceinline__ T tmax(const T& a, const T& b) { return val(b) > val(a) ? b : a; }
+
+// ---------------------------------------------------------------------------
+// The scheme's point functions, templated on the scalar (double or Dual)
+// ---------------------------------------------------------------------------
+
+template <class T>
+struct LimT {
+  T h, qx, qy, u, v;
+};
+template <class T>
+struct F3T {
+  T h, x, y;
+};
+
+// Revised face limit (Sec. 2.1.2): h* = max(0, h), velocities q/h above tol.
+template <class T>
+__device__ __forceinline__ LimT<T> revise_t(const T& h, const T& qx, const T& qy, double tol) {
+  LimT<T> r;
+  const T zero = T(h - h);  // a zero of the right type
+  if (val(h) > tol) {
+    r.u = qx / h;
+    r.v = qy / h;
+  } else {
+    r.u = zero;
+    r.v = zero;
+  }
+  r.h = val(h) > 0.0 ? h : zero;
+  r.qx = r.h * r.u;
+  r.qy = r.h * r.v;
+  return r;
+}
+
+// HLL normal flux with Toro's wave speeds (n normal, t tangential).
+template <class T>
+__device__ __forceinline__ F3T<T> hll_t(const T& hL, const T& qnL, const T& qtL, const T& unL,
+                                        const T& utL, const T& hR, const T& qnR, const T& qtR,
+                                        const T& unR, const T& utR, double g, double tol) {
+  F3T<T> f;
+  const T zero = T(hL - hL);
+  if (val(hL) <= tol && val(hR) <= tol) {
+    f.h = zero; f.x = zero; f.y = zero;
+    return f;
+  }
+  const T cL = sqrt(g * hL), cR = sqrt(g * hR);
+  T sL, sR;
+  if (val(hL) <= tol) {
+    sL = unR - 2.0 * cR;
+    sR = unR + cR;
+  } else if (val(hR) <= tol) {
+    sL = unL - cL;
+    sR = unL + 2.0 * cL;
+  } else {
+    const T us = 0.5 * (unL + unR) + cL - cR;
+    const T cs = 0.5 * (cL + cR) + 0.25 * (unL - unR);
+    sL = tmin(unL - cL, us - cs);
+    sR = tmax(unR + cR, us + cs);
+  }
+  const T fLh = hL * unL, fLn = hL * unL * unL + 0.5 * g * hL * hL, fLt = hL * unL * utL;
+  const T fRh = hR * unR, fRn = hR * unR * unR + 0.5 * g * hR * hR, fRt = hR * unR * utR;
+  if (val(sL) >= 0.0) {
+    f.h = fLh; f.x = fLn; f.y = fLt;
+    return f;
+  }
+  if (val(sR) <= 0.0) {
+    f.h = fRh; f.x = fRn; f.y = fRt;
+    return f;
+  }
+  const T inv = 1.0 / (sR - sL), sLR = sL * sR;
+  f.h = (sR * fLh - sL * fRh + sLR * (hR - hL)) * inv;
+  f.x = (sR * fLn - sL * fRn + sLR * (qnR - qnL)) * inv;
+  f.y = (sR * fLt - sL * fRt + sLR * (qtR - qtL)) * inv;
+  return f;
+}
+
+template <class T>
+__device__ __forceinline__ F3T<T> flux_face(const LimT<T>& L, const LimT<T>& R, bool ydir,
+                                            double g, double tol) {
+  if (!ydir) return hll_t(L.h, L.qx, L.qy, L.u, L.v, R.h, R.qx, R.qy, R.u, R.v, g, tol);
+  const F3T<T> r = hll_t(L.h, L.qy, L.qx, L.v, L.u, R.h, R.qy, R.qx, R.v, R.u, g, tol);
+  F3T<T> o;
+  o.h = r.h; o.x = r.y; o.y = r.x;
+  return o;
+}
+
+template <class T>
+__device__ __forceinline__ F3T<T> phys_t(const T& h, const T& qx, const T& qy, double g, double tol,
+                                         bool ydir) {
+  const T zero = T(h - h);
+  T u = zero, v = zero;
+  if (val(h) > tol) {
+    u = qx / h;
+    v = qy / h;
+  }
+  F3T<T> f;
+  const T p = 0.5 * g * h * h;
+  if (!ydir) {
+    f.h = h * u; f.x = h * u * u + p; f.y = h * u * v;
+  } else {
+    f.h = h * v; f.x = h * u * v; f.y = h * v * v + p;
+  }
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Problem description
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxKnotsAdj = 4096;
+
+struct Prob {
+  int nx, ny;
+  long long N;                 // cells (dense planes, x fastest)
+  double dx, dy, inv_dx, inv_dy, g, tol;
+  int bc[4];
+  // one inflow segment (edge < 0: none)
+  int in_edge;
+  double in_s0, in_s1, in_width;
+  const double* Z;             // 3 planes z0, z1x, z1y
+  const double* Nm;            // Manning n
+  double rain, rain_t0, rain_t1;
+};
+
+__device__ __forceinline__ bool on_inflow(const Prob& p, int edge, double s) {
+  return p.in_edge == edge && s >= p.in_s0 && s <= p.in_s1;
+}
+
+// Outside state of an edge face from the own raw limit (h, qx, qy) and the
+// hydrograph discharge Q (m^3/s) of the inflow segment at the stage time.
+template <class T>
+__device__ __forceinline__ void ghost_t(const Prob& p, int edge, double s, const T& Q, T& h, T& qx,
+                                        T& qy) {
+  const T zero = T(h - h);
+  if (on_inflow(p, edge, s)) {
+    const T qin = Q / p.in_width;
+    const T hin = val(h) > 0.0 ? h : zero;
+    const T hc = cbrt(qin * qin / p.g);
+    const T hg = val(hin) > val(hc) ? hin : hc;
+    const T qn = (edge == 0 || edge == 2) ? qin : -qin;
+    h = hg;
+    if (edge <= 1) { qx = qn; qy = zero; } else { qx = zero; qy = qn; }
+    return;
+  }
+  if (p.bc[edge] == DG2_OPEN) {
+    if (edge == 0 && val(qx) > 0.0) qx = zero;
+    if (edge == 1 && val(qx) < 0.0) qx = zero;
+    if (edge == 2 && val(qy) > 0.0) qy = zero;
+    if (edge == 3 && val(qy) < 0.0) qy = zero;
+    return;
+  }
+  if (edge <= 1) qx = -qx; else qy = -qy;
+}
+
+enum { H0 = 0, H1X, H1Y, QX0, QX1X, QX1Y, QY0, QY1X, QY1Y };
+
+// Raw limit (h, qx, qy) of cell c at face f (0 E, 1 W, 2 N, 3 S).
+__device__ __forceinline__ void raw_limit(const double* __restrict__ U, long long N, long long c,
+                                          int f, double& h, double& qx, double& qy) {
+  const int m = f <= 1 ? 1 : 2;
+  const double sg = (f == 0 || f == 2) ? 1.0 : -1.0;
+  h = U[c] + sg * U[m * N + c];
+  qx = U[3 * N + c] + sg * U[(3 + m) * N + c];
+  qy = U[6 * N + c] + sg * U[(6 + m) * N + c];
+}
+
+// Cell's own terms of Eqs. 4-5 from its four raw limits (fluxes excluded):
+// revisions, z* of each face, dummy modes, Gauss-point fluxes and bed terms.
+template <class T>
+__device__ __forceinline__ void own_terms(const Prob& p, long long c, const T* E, const T* W,
+                                          const T* Nn, const T* S, T* L) {
+  const double z0 = p.Z[c], z1x = p.Z[p.N + c], z1y = p.Z[2 * p.N + c];
+  const T zero = T(E[0] - E[0]);
+  const LimT<T> Es = revise_t(E[0], E[1], E[2], p.tol), Ws = revise_t(W[0], W[1], W[2], p.tol);
+  const LimT<T> Ns = revise_t(Nn[0], Nn[1], Nn[2], p.tol), Ss = revise_t(S[0], S[1], S[2], p.tol);
+  const T zE = (z0 + z1x) - (val(E[0]) < 0.0 ? -E[0] : zero);
+  const T zW = (z0 - z1x) - (val(W[0]) < 0.0 ? -W[0] : zero);
+  const T zN = (z0 + z1y) - (val(Nn[0]) < 0.0 ? -Nn[0] : zero);
+  const T zS = (z0 - z1y) - (val(S[0]) < 0.0 ? -S[0] : zero);
+  const T zb1x = 0.5 * (zE - zW), zb1y = 0.5 * (zN - zS);
+  const T h0x = 0.5 * (Es.h + Ws.h), x0x = 0.5 * (Es.qx + Ws.qx), y0x = 0.5 * (Es.qy + Ws.qy);
+  const T h1x = 0.5 * (Es.h - Ws.h), x1x = 0.5 * (Es.qx - Ws.qx), y1x = 0.5 * (Es.qy - Ws.qy);
+  const T h0y = 0.5 * (Ns.h + Ss.h), x0y = 0.5 * (Ns.qx + Ss.qx), y0y = 0.5 * (Ns.qy + Ss.qy);
+  const T h1y = 0.5 * (Ns.h - Ss.h), x1y = 0.5 * (Ns.qx - Ss.qx), y1y = 0.5 * (Ns.qy - Ss.qy);
+  const double r3 = 1.0 / 1.7320508075688772;
+  const F3T<T> Fp = phys_t(h0x + h1x * r3, x0x + x1x * r3, y0x + y1x * r3, p.g, p.tol, false);
+  const F3T<T> Fm = phys_t(h0x - h1x * r3, x0x - x1x * r3, y0x - y1x * r3, p.g, p.tol, false);
+  const F3T<T> Gp = phys_t(h0y + h1y * r3, x0y + x1y * r3, y0y + y1y * r3, p.g, p.tol, true);
+  const F3T<T> Gm = phys_t(h0y - h1y * r3, x0y - x1y * r3, y0y - y1y * r3, p.g, p.tol, true);
+  const double g = p.g, idx = p.inv_dx, idy = p.inv_dy;
+  const double k3x = -3.0 * idx, k3y = -3.0 * idy, g23 = 2.0 * g / 3.0;
+  L[H0] = zero;
+  L[QX0] = -(2.0 * g * h0x * zb1x * idx);
+  L[QY0] = -(2.0 * g * h0y * zb1y * idy);
+  L[H1X] = k3x * (-(Fp.h + Fm.h));
+  L[QX1X] = k3x * (-(Fp.x + Fm.x) + g23 * h1x * zb1x);
+  L[QY1X] = k3x * (-(Fp.y + Fm.y));
+  L[H1Y] = k3y * (-(Gp.h + Gm.h));
+  L[QX1Y] = k3y * (-(Gp.x + Gm.x));
+  L[QY1Y] = k3y * (-(Gp.y + Gm.y) + g23 * h1y * zb1y);
+}
+
+// Flux of the face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at
+// stage time with hydrograph discharge Q, in double.
+__device__ F3T<double> face_flux(const Prob& p, const double* __restrict__ U, int i, int j, int f,
+                                 double Q) {
+  const long long N = p.N, c = (long long)j * p.nx + i;
+  double oh, ox, oy;  // own raw limit at the face
+  raw_limit(U, N, c, f, oh, ox, oy);
+  double nh, nxq, nyq;  // other side
+  const bool edge = (f == 0 && i == p.nx - 1) || (f == 1 && i == 0) || (f == 2 && j == p.ny - 1) ||
+                    (f == 3 && j == 0);
+  if (edge) {
+    nh = oh; nxq = ox; nyq = oy;
+    const int e = f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2;
+    const double s = f <= 1 ? (j + 0.5) * p.dy : (i + 0.5) * p.dx;
+    ghost_t<double>(p, e, s, Q, nh, nxq, nyq);
+  } else {
+    const long long cn = f == 0 ? c + 1 : f == 1 ? c - 1 : f == 2 ? c + p.nx : c - p.nx;
+    raw_limit(U, N, cn, f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2, nh, nxq, nyq);
+  }
+  const LimT<double> own = revise_t(oh, ox, oy, p.tol), oth = revise_t(nh, nxq, nyq, p.tol);
+  const bool y = f >= 2;
+  // left/lower side first
+  if (f == 0 || f == 2) return flux_face(own, oth, y, p.g, p.tol);
+  return flux_face(oth, own, y, p.g, p.tol);
+}
+
+// L(U) at cell (i, j) in double (Eq. 4 with the fluxes of its four faces).
+__device__ void cell_operator(const Prob& p, const double* __restrict__ U, int i, int j, double t,
+                              double Q, double* L) {
+  const long long N = p.N, c = (long long)j * p.nx + i;
+  double E[3], W[3], Nn[3], S[3];
+  raw_limit(U, N, c, 0, E[0], E[1], E[2]);
+  raw_limit(U, N, c, 1, W[0], W[1], W[2]);
+  raw_limit(U, N, c, 2, Nn[0], Nn[1], Nn[2]);
+  raw_limit(U, N, c, 3, S[0], S[1], S[2]);
+  own_terms<double>(p, c, E, W, Nn, S, L);
+  const F3T<double> FE = face_flux(p, U, i, j, 0, Q), FW = face_flux(p, U, i, j, 1, Q);
+  const F3T<double> GN = face_flux(p, U, i, j, 2, Q), GS = face_flux(p, U, i, j, 3, Q);
+  const double idx = p.inv_dx, idy = p.inv_dy, k3x = -3.0 * idx, k3y = -3.0 * idy;
+  L[H0] += -(FE.h - FW.h) * idx - (GN.h - GS.h) * idy;
+  L[QX0] += -(FE.x - FW.x) * idx - (GN.x - GS.x) * idy;
+  L[QY0] += -(FE.y - FW.y) * idx - (GN.y - GS.y) * idy;
+  L[H1X] += k3x * (FE.h + FW.h);
+  L[QX1X] += k3x * (FE.x + FW.x);
+  L[QY1X] += k3x * (FE.y + FW.y);
+  L[H1Y] += k3y * (GN.h + GS.h);
+  L[QX1Y] += k3y * (GN.x + GS.x);
+  L[QY1Y] += k3y * (GN.y + GS.y);
+  if (p.rain != 0.0 && t >= p.rain_t0 && t < p.rain_t1) L[H0] += p.rain;
+}
+
+// Wet-dry treatment after a stage (mass-neutral); returns the 9-bit mask of
+// the modes it keeps.
+__device__ __forceinline__ unsigned wetdry_mask(double* m, double z0, double z1x, double z1y,
+                                                double tol) {
+  const double h0 = m[H0];
+  if (h0 <= tol) {
+#pragma unroll
+    for (int k = 1; k < 9; ++k) m[k] = 0.0;
+    return 1u;
+  }
+  unsigned keep = 0x1FFu;
+  const double eta0 = h0 + z0;
+  {
+    const bool fe = (h0 + m[H1X] <= tol) && !(z0 + z1x > eta0);
+    const bool fw = (h0 - m[H1X] <= tol) && !(z0 - z1x > eta0);
+    if (fe || fw) {
+      m[H1X] = 0.0; m[QX1X] = 0.0; m[QY1X] = 0.0;
+      keep &= ~((1u << H1X) | (1u << QX1X) | (1u << QY1X));
+    }
+  }
+  {
+    const bool fn = (h0 + m[H1Y] <= tol) && !(z0 + z1y > eta0);
+    const bool fs = (h0 - m[H1Y] <= tol) && !(z0 - z1y > eta0);
+    if (fn || fs) {
+      m[H1Y] = 0.0; m[QX1Y] = 0.0; m[QY1Y] = 0.0;
+      keep &= ~((1u << H1Y) | (1u << QX1Y) | (1u << QY1Y));
+    }
+  }
+  return keep;
+}
+
+// Friction of one cell (Sec. 2.1.3, as the forward solver): modes m -> out.
+template <class T>
+__device__ __forceinline__ void friction_point_t(const T& gn2dt, double tol, const T& h, T& qx,
+                                                 T& qy) {
+  if (!(val(h) > tol)) return;
+  const T qm = sqrt(qx * qx + qy * qy);
+  const T den = 1.0 + gn2dt * qm / (h * h * cbrt(h));
+  qx = qx / den;
+  qy = qy / den;
+}
+
+template <class T>
+__device__ __forceinline__ void friction_cell(const T* m, const T& n, double dt, double g, double tol,
+                                              T* out) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out[k] = m[k];
+  const T gn2dt = dt * g * n * n;
+  T cx = m[QX0], cy = m[QY0];
+  friction_point_t(gn2dt, tol, m[H0], cx, cy);
+  const double r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
+#pragma unroll
+  for (int dd = 1; dd <= 2; ++dd) {
+    const T h1 = m[dd], x1 = m[3 + dd], y1 = m[6 + dd];
+    T xp = m[QX0] + x1 * r3, yp = m[QY0] + y1 * r3, xm = m[QX0] - x1 * r3, ym = m[QY0] - y1 * r3;
+    friction_point_t(gn2dt, tol, m[H0] + h1 * r3, xp, yp);
+    friction_point_t(gn2dt, tol, m[H0] - h1 * r3, xm, ym);
+    out[3 + dd] = hs3 * (xp - xm);
+    out[6 + dd] = hs3 * (yp - ym);
+  }
+  out[QX0] = cx;
+  out[QY0] = cy;
+}
+
+// ---------------------------------------------------------------------------
+// Forward kernels (one thread per cell, dense planes)
+// ---------------------------------------------------------------------------
+
+__global__ void fwd_friction_kernel(Prob p, const double* __restrict__ U, double* __restrict__ Us,
+                                    double dt) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  double m[9], o[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = U[k * p.N + c];
+  friction_cell<double>(m, p.Nm[c], dt, p.g, p.tol, o);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Us[k * p.N + c] = o[k];
+}
+
+// Stage 1: U1 = W(Us + dt L(Us, t)); stage 2: Uo = W((Us + U1 + dt L(U1, t)) / 2).
+template <int STAGE>
+__global__ void fwd_stage_kernel(Prob p, const double* __restrict__ Us, const double* __restrict__ U1,
+                                 double* __restrict__ Uo, unsigned short* __restrict__ mask, double dt,
+                                 double t, double Q) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const int i = (int)(c % p.nx), j = (int)(c / p.nx);
+  const double* In = STAGE == 1 ? Us : U1;
+  double L[9], o[9];
+  cell_operator(p, In, i, j, t, Q, L);
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    o[k] = STAGE == 1 ? Us[k * p.N + c] + dt * L[k]
+                      : 0.5 * (Us[k * p.N + c] + U1[k * p.N + c] + dt * L[k]);
+  const unsigned keep = wetdry_mask(o, p.Z[c], p.Z[p.N + c], p.Z[2 * p.N + c], p.tol);
+  mask[c] = (unsigned short)keep;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Uo[k * p.N + c] = o[k];
+}
+
+// Sampled gauge depths max(0, planar h) of state U.
+__global__ void gauge_kernel(const double* __restrict__ U, long long N, int ng,
+                             const long long* __restrict__ gc, const double* __restrict__ gx,
+                             const double* __restrict__ ge, double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ng) return;
+  const long long c = gc[k];
+  const double h = U[c] + gx[k] * U[N + c] + ge[k] * U[2 * N + c];
+  out[k] = h > 0.0 ? h : 0.0;
+}
+
+// lambda += dJ/dU for one sample: 2 (h - obs) (1, xi, eta) on the depth modes
+// where the clipped depth is positive (one thread: gauges may share a cell).
+__global__ void gauge_seed_kernel(double* __restrict__ lam, long long N, int ng,
+                                  const long long* __restrict__ gc, const double* __restrict__ gx,
+                                  const double* __restrict__ ge, const double* __restrict__ h,
+                                  const double* __restrict__ obs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k < ng; ++k) {
+    if (!(h[k] > 0.0)) continue;
+    const double r = 2.0 * (h[k] - obs[k]);
+    const long long c = gc[k];
+    lam[c] += r;
+    lam[N + c] += r * gx[k];
+    lam[2 * N + c] += r * ge[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse kernels
+// ---------------------------------------------------------------------------
+
+// Adjoint mu of the operator output of a stage at cell c:
+//   stage 2: mu = dt/2 * mask2 * lam2            (V2 = (Us + U1 + dt L) / 2)
+//   stage 1: mu = dt * mask1 * lamU1             (V1 = Us + dt L)
+__device__ __forceinline__ void stage_mu(const double* __restrict__ lam, const unsigned short* mask,
+                                         long long N, long long c, double w, double* mu) {
+  const unsigned m = mask[c];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) mu[k] = ((m >> k) & 1u) ? w * lam[k * N + c] : 0.0;
+}
+
+// One pass over the faces of a stage: face (left/lower cell a, right/upper cell
+// b) of direction dir (0 x, 1 y); index f runs over (nx+1) * ny x-faces or
+// nx * (ny+1) y-faces.  Writes the adjoint of each side's raw limit (the
+// boundary side folded into the own cell's limit) and, for inflow faces, the
+// adjoint of the hydrograph discharge.
+__global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
+                                const double* __restrict__ lam, const unsigned short* __restrict__ mask,
+                                double w, double Q, double* __restrict__ FL, double* __restrict__ FR,
+                                double* __restrict__ gq_face) {
+  const long long nfx = (long long)(p.nx + 1) * p.ny, nfy = (long long)p.nx * (p.ny + 1);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= (dir == 0 ? nfx : nfy)) return;
+  int i, j;  // cell on the right / upper side (may be outside)
+  if (dir == 0) { i = (int)(f % (p.nx + 1)); j = (int)(f / (p.nx + 1)); }
+  else { i = (int)(f % p.nx); j = (int)(f / p.nx); }
+  const long long N = p.N;
+  const bool has_a = dir == 0 ? i > 0 : j > 0;
+  const bool has_b = dir == 0 ? i < p.nx : j < p.ny;
+  const long long cb = (long long)j * p.nx + i;
+  const long long ca = dir == 0 ? cb - 1 : cb - p.nx;
+  const double inv = dir == 0 ? p.inv_dx : p.inv_dy;
+  const int l1 = dir == 0 ? 1 : 2;  // slope mode of the direction
+  // phi = dJ/dF for the face's three flux components
+  double phi[3] = {0.0, 0.0, 0.0};
+  double mua[9], mub[9];
+  if (has_a) {
+    stage_mu(lam, mask, N, ca, w, mua);
+    for (int v = 0; v < 3; ++v) phi[v] += -mua[3 * v] * inv - 3.0 * inv * mua[3 * v + l1];
+  }
+  if (has_b) {
+    stage_mu(lam, mask, N, cb, w, mub);
+    for (int v = 0; v < 3; ++v) phi[v] += mub[3 * v] * inv - 3.0 * inv * mub[3 * v + l1];
+  }
+  double la[3] = {0.0, 0.0, 0.0}, lb[3] = {0.0, 0.0, 0.0}, gq = 0.0;
+  const bool y = dir == 1;
+  if (has_a && has_b) {
+    double a3[3], b3[3];
+    raw_limit(In, N, ca, dir == 0 ? 0 : 2, a3[0], a3[1], a3[2]);
+    raw_limit(In, N, cb, dir == 0 ? 1 : 3, b3[0], b3[1], b3[2]);
+    Dual<6> A[3], Bv[3];
+    for (int k = 0; k < 3; ++k) { A[k] = var<6>(a3[k], k); Bv[k] = var<6>(b3[k], 3 + k); }
+    const LimT<Dual<6>> La = revise_t(A[0], A[1], A[2], p.tol), Lb = revise_t(Bv[0], Bv[1], Bv[2], p.tol);
+    const F3T<Dual<6>> F = flux_face(La, Lb, y, p.g, p.tol);
+    for (int k = 0; k < 3; ++k) {
+      la[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k];
+      lb[k] = phi[0] * F.h.d[3 + k] + phi[1] * F.x.d[3 + k] + phi[2] * F.y.d[3 + k];
+    }
+  } else {
+    // boundary face: the outside state is the ghost of the inside cell's limit
+    const bool inside_b = has_b;
+    const long long c = inside_b ? cb : ca;
+    const int ci = inside_b ? i : (dir == 0 ? i - 1 : i);
+    const int cj = inside_b ? j : (dir == 0 ? j : j - 1);
+    const int face = dir == 0 ? (inside_b ? 1 : 0) : (inside_b ? 3 : 2);  // own face
+    const int edge = dir == 0 ? (inside_b ? 0 : 1) : (inside_b ? 2 : 3);
+    const double s = dir == 0 ? (cj + 0.5) * p.dy : (ci + 0.5) * p.dx;
+    double o3[3];
+    raw_limit(In, N, c, face, o3[0], o3[1], o3[2]);
+    Dual<4> O[3], G[3];
+    for (int k = 0; k < 3; ++k) { O[k] = var<4>(o3[k], k); G[k] = O[k]; }
+    const Dual<4> Qd = var<4>(Q, 3);
+    ghost_t(p, edge, s, Qd, G[0], G[1], G[2]);
+    const LimT<Dual<4>> Lo = revise_t(O[0], O[1], O[2], p.tol), Lg = revise_t(G[0], G[1], G[2], p.tol);
+    const F3T<Dual<4>> F = inside_b ? flux_face(Lg, Lo, y, p.g, p.tol) : flux_face(Lo, Lg, y, p.g, p.tol);
+    double lo[3];
+    for (int k = 0; k < 3; ++k) lo[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k];
+    gq = phi[0] * F.h.d[3] + phi[1] * F.x.d[3] + phi[2] * F.y.d[3];
+    for (int k = 0; k < 3; ++k) { if (inside_b) lb[k] = lo[k]; else la[k] = lo[k]; }
+    // fold into the edge slot index: along-edge position
+    const int pos = dir == 0 ? cj : ci;
+    const int slot = edge * (p.nx > p.ny ? p.nx : p.ny) + pos;
+    gq_face[slot] = gq;
+  }
+  for (int k = 0; k < 3; ++k) {
+    FL[k * (dir == 0 ? nfx : nfy) + f] = la[k];
+    FR[k * (dir == 0 ? nfx : nfy) + f] = lb[k];
+  }
+}
+
+// One pass over the cells of a stage.  Stage 2 writes lamU1 = mask2 lam2 / 2 +
+// L'(U1)^T mu2.  Stage 1 writes lamUs = mask2 lam2 / 2 + mask1 lamU1 +
+// L'(Us)^T mu1, then the friction adjoint: lam <- Fric'(U)^T lamUs and the
+// Manning gradient.
+template <int STAGE>
+__global__ void adj_cell_kernel(Prob p, const double* __restrict__ In, const double* __restrict__ lamS,
+                                const unsigned short* __restrict__ maskS, double wS,
+                                const double* __restrict__ lam2, const unsigned short* __restrict__ mask2,
+                                const unsigned short* __restrict__ mask1, const double* __restrict__ lamU1,
+                                const double* __restrict__ FXL, const double* __restrict__ FXR,
+                                const double* __restrict__ FYL, const double* __restrict__ FYR,
+                                const double* __restrict__ U, double dt, double* __restrict__ out,
+                                double* __restrict__ gn) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const long long N = p.N;
+  const int i = (int)(c % p.nx), j = (int)(c / p.nx);
+  const long long nfx = (long long)(p.nx + 1) * p.ny, nfy = (long long)p.nx * (p.ny + 1);
+  double mu[9];
+  stage_mu(lamS, maskS, N, c, wS, mu);
+  // own terms: Jacobian of L_c with respect to the cell's 12 raw limits
+  double lr[4][3];
+  {
+    double E[3], W[3], Nn[3], S[3];
+    raw_limit(In, N, c, 0, E[0], E[1], E[2]);
+    raw_limit(In, N, c, 1, W[0], W[1], W[2]);
+    raw_limit(In, N, c, 2, Nn[0], Nn[1], Nn[2]);
+    raw_limit(In, N, c, 3, S[0], S[1], S[2]);
+    Dual<12> dE[3], dW[3], dN[3], dS[3], L[9];
+    for (int k = 0; k < 3; ++k) {
+      dE[k] = var<12>(E[k], k);
+      dW[k] = var<12>(W[k], 3 + k);
+      dN[k] = var<12>(Nn[k], 6 + k);
+      dS[k] = var<12>(S[k], 9 + k);
+    }
+    own_terms<Dual<12>>(p, c, dE, dW, dN, dS, L);
+    for (int f = 0; f < 4; ++f)
+      for (int k = 0; k < 3; ++k) {
+        double a = 0.0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a += mu[q] * L[q].d[3 * f + k];
+        lr[f][k] = a;
+      }
+  }
+  // the four faces' adjoints of this cell's limits
+  const long long fe = (long long)j * (p.nx + 1) + i + 1, fw = (long long)j * (p.nx + 1) + i;
+  const long long fn = (long long)(j + 1) * p.nx + i, fs = (long long)j * p.nx + i;
+  for (int k = 0; k < 3; ++k) {
+    lr[0][k] += FXL[k * nfx + fe];
+    lr[1][k] += FXR[k * nfx + fw];
+    lr[2][k] += FYL[k * nfy + fn];
+    lr[3][k] += FYR[k * nfy + fs];
+  }
+  // limits -> modes: E = U0 + U1x, W = U0 - U1x, N = U0 + U1y, S = U0 - U1y
+  double a[9];
+  for (int v = 0; v < 3; ++v) {
+    a[3 * v] = lr[0][v] + lr[1][v] + lr[2][v] + lr[3][v];
+    a[3 * v + 1] = lr[0][v] - lr[1][v];
+    a[3 * v + 2] = lr[2][v] - lr[3][v];
+  }
+  // direct RK terms
+  const unsigned m2 = mask2[c];
+  double half2[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) half2[k] = ((m2 >> k) & 1u) ? 0.5 * lam2[k * N + c] : 0.0;
+  if (STAGE == 2) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k * N + c] = half2[k] + a[k];
+    return;
+  }
+  const unsigned m1 = mask1[c];
+  double ls[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ls[k] = half2[k] + (((m1 >> k) & 1u) ? lamU1[k * N + c] : 0.0) + a[k];
+  // friction: Us = Fric(U; n)
+  Dual<10> m[9], o[9];
+  for (int k = 0; k < 9; ++k) m[k] = var<10>(U[k * N + c], k);
+  const Dual<10> n = var<10>(p.Nm[c], 9);
+  friction_cell<Dual<10>>(m, n, dt, p.g, p.tol, o);
+  for (int k = 0; k < 9; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) s += ls[q] * o[q].d[k];
+    out[k * N + c] = s;
+  }
+  double sn = 0.0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) sn += ls[q] * o[q].d[9];
+  gn[c] += sn;
+}
+
+// Sum of the inflow faces' discharge adjoints in a fixed order into one slot.
+__global__ void sum_gq_kernel(const double* __restrict__ gq_face, int n, double* __restrict__ slot) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += gq_face[k];
+  *slot = s;
+}
+
+}  // namespace adj
+}  // namespace dg2
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct dg2_adj;
+
+namespace dg2 {
+namespace adj {
+namespace {
+
+int afail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  dg2::set_error_text(buf);
+  return code;
+}
+
+#define ACU(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return afail(DG2_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct AdjLayout {
+  size_t off_Z, off_Nm, off_U0, off_snap, off_work, off_Us, off_U1, off_m1, off_m2, off_lam,
+      off_lamU1, off_tmp, off_FXL, off_FXR, off_FYL, off_FYR, off_gq_face, off_gn, off_gidx,
+      off_gxi, off_geta, off_gh, off_gq_step, total;
+  long long N, nfx, nfy, plane9;
+  int nsnap, ngq;
+};
+
+bool adj_layout(int nx, int ny, int nsnap, int max_gauges, int max_steps, AdjLayout& L) {
+  if (nx < 1 || ny < 1 || nsnap < 1 || max_gauges < 0 || max_steps < 1) return false;
+  L.N = (long long)nx * ny;
+  L.nfx = (long long)(nx + 1) * ny;
+  L.nfy = (long long)nx * (ny + 1);
+  L.plane9 = 9 * L.N;
+  L.nsnap = nsnap;
+  L.ngq = 4 * (nx > ny ? nx : ny);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t s9 = (size_t)L.plane9 * sizeof(double);
+  L.off_Z = take(3 * (size_t)L.N * sizeof(double));
+  L.off_Nm = take((size_t)L.N * sizeof(double));
+  L.off_U0 = take(s9);
+  L.off_snap = take((size_t)nsnap * s9);
+  L.off_work = take(2 * s9);
+  L.off_Us = take(s9);
+  L.off_U1 = take(s9);
+  L.off_m1 = take((size_t)L.N * sizeof(unsigned short));
+  L.off_m2 = take((size_t)L.N * sizeof(unsigned short));
+  L.off_lam = take(s9);
+  L.off_lamU1 = take(s9);
+  L.off_tmp = take(s9);
+  L.off_FXL = take(3 * (size_t)L.nfx * sizeof(double));
+  L.off_FXR = take(3 * (size_t)L.nfx * sizeof(double));
+  L.off_FYL = take(3 * (size_t)L.nfy * sizeof(double));
+  L.off_FYR = take(3 * (size_t)L.nfy * sizeof(double));
+  L.off_gq_face = take((size_t)L.ngq * sizeof(double));
+  L.off_gn = take((size_t)L.N * sizeof(double));
+  const size_t ng = max_gauges > 0 ? max_gauges : 1;
+  L.off_gidx = take(ng * sizeof(long long));
+  L.off_gxi = take(ng * sizeof(double));
+  L.off_geta = take(ng * sizeof(double));
+  L.off_gh = take(ng * sizeof(double));
+  L.off_gq_step = take(2 * (size_t)max_steps * sizeof(double));
+  L.total = o;
+  return true;
+}
+
+}  // namespace
+}  // namespace adj
+}  // namespace dg2
+
+struct dg2_adj {
+  dg2::adj::Prob p;
+  dg2::adj::AdjLayout lay;
+  char* ws;
+  cudaStream_t st;
+  int max_gauges, max_steps;
+  // problem
+  std::vector<double> tk, qk;       // hydrograph knots (times, discharges)
+  double t0;
+  std::vector<double> dts;          // frozen step sizes
+  std::vector<int> samp_step;       // step count after which each sample is taken
+  std::vector<double> obs;          // [nsamp][ngauge]
+  int ngauge;
+  bool have_state, have_schedule;
+  // per-run host results
+  std::vector<double> gauge_h;      // [nsamp][ngauge] from the last forward
+  int64_t fwd_steps, rev_steps;
+};
+
+namespace dg2 {
+namespace adj {
+namespace {
+
+double* dptr(dg2_adj* a, size_t off) { return (double*)(a->ws + off); }
+double* snap(dg2_adj* a, int s) { return dptr(a, a->lay.off_snap) + (size_t)s * a->lay.plane9; }
+
+double hydro(const dg2_adj* a, double t) {
+  const std::vector<double>& tk = a->tk;
+  const std::vector<double>& qk = a->qk;
+  if (tk.empty()) return 0.0;
+  if (t <= tk[0]) return qk[0];
+  for (size_t k = 0; k + 1 < tk.size(); ++k)
+    if (t <= tk[k + 1]) {
+      const double w = (t - tk[k]) / (tk[k + 1] - tk[k]);
+      return qk[k] + w * (qk[k + 1] - qk[k]);
+    }
+  return qk.back();
+}
+
+// dQ(t)/dq_k added into g with weight s
+void hydro_grad(const dg2_adj* a, double t, double s, double* g) {
+  const std::vector<double>& tk = a->tk;
+  if (tk.empty()) return;
+  if (t <= tk[0]) { g[0] += s; return; }
+  for (size_t k = 0; k + 1 < tk.size(); ++k)
+    if (t <= tk[k + 1]) {
+      const double w = (t - tk[k]) / (tk[k + 1] - tk[k]);
+      g[k] += s * (1.0 - w);
+      g[k + 1] += s * w;
+      return;
+    }
+  g[tk.size() - 1] += s;
+}
+
+double step_time(const dg2_adj* a, int k) {
+  // t_k = t0 + dt_0 + ... + dt_{k-1}, summed in step order as the forward does
+  double t = a->t0;
+  for (int q = 0; q < k; ++q) t += a->dts[q];
+  return t;
+}
+
+int launch_ok() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return afail(DG2_E_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  return DG2_OK;
+}
+
+unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
+
+// One forward step k from Uin to Uout (Us, U1, masks left in the workspace).
+int fwd_step(dg2_adj* a, int k, double t, const double* Uin, double* Uout) {
+  const double dt = a->dts[k];
+  double* Us = dptr(a, a->lay.off_Us);
+  double* U1 = dptr(a, a->lay.off_U1);
+  unsigned short* m1 = (unsigned short*)(a->ws + a->lay.off_m1);
+  unsigned short* m2 = (unsigned short*)(a->ws + a->lay.off_m2);
+  const unsigned nb = blocks(a->lay.N);
+  fwd_friction_kernel<<<nb, 256, 0, a->st>>>(a->p, Uin, Us, dt);
+  fwd_stage_kernel<1><<<nb, 256, 0, a->st>>>(a->p, Us, nullptr, U1, m1, dt, t, hydro(a, t));
+  fwd_stage_kernel<2><<<nb, 256, 0, a->st>>>(a->p, Us, U1, Uout, m2, dt, t + dt, hydro(a, t + dt));
+  a->fwd_steps++;
+  return launch_ok();
+}
+
+// Advances `buf` (the state after `from` steps) to the state after `to` steps.
+int advance(dg2_adj* a, double* buf, int from, int to) {
+  double* w = dptr(a, a->lay.off_work);
+  double t = step_time(a, from);
+  const size_t s9 = (size_t)a->lay.plane9 * sizeof(double);
+  for (int k = from; k < to; ++k) {
+    int r = fwd_step(a, k, t, buf, w);
+    if (r) return r;
+    ACU(cudaMemcpyAsync(buf, w, s9, cudaMemcpyDeviceToDevice, a->st));
+    t += a->dts[k];
+  }
+  return DG2_OK;
+}
+
+// Reverse of step k from state Uk: lam (adjoint of the state after step k)
+// becomes the adjoint of Uk; Manning gradient and discharge adjoints added.
+int rev_step(dg2_adj* a, int k, const double* Uk) {
+  const AdjLayout& L = a->lay;
+  const double dt = a->dts[k];
+  const double t = step_time(a, k);
+  double* Us = dptr(a, L.off_Us);
+  double* U1 = dptr(a, L.off_U1);
+  double* w = dptr(a, L.off_work);
+  unsigned short* m1 = (unsigned short*)(a->ws + L.off_m1);
+  unsigned short* m2 = (unsigned short*)(a->ws + L.off_m2);
+  int r = fwd_step(a, k, t, Uk, w);  // Us, U1, masks of this step
+  if (r) return r;
+  a->fwd_steps--;                     // counted as part of the reverse step
+  double* lam = dptr(a, L.off_lam);
+  double* lamU1 = dptr(a, L.off_lamU1);
+  double* tmp = dptr(a, L.off_tmp);
+  double* FXL = dptr(a, L.off_FXL);
+  double* FXR = dptr(a, L.off_FXR);
+  double* FYL = dptr(a, L.off_FYL);
+  double* FYR = dptr(a, L.off_FYR);
+  double* gqf = dptr(a, L.off_gq_face);
+  double* gn = dptr(a, L.off_gn);
+  double* gqs = dptr(a, L.off_gq_step);
+  const unsigned nb = blocks(L.N);
+  // stage 2 at U1, time t + dt: mu2 = dt/2 mask2 lam
+  ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(double), a->st));
+  adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
+                                                    FXL, FXR, gqf);
+  adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
+                                                    FYL, FYR, gqf);
+  sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k + 1);
+  adj_cell_kernel<2><<<nb, 256, 0, a->st>>>(a->p, U1, lam, m2, 0.5 * dt, lam, m2, m1, nullptr, FXL,
+                                            FXR, FYL, FYR, nullptr, dt, lamU1, gn);
+  // stage 1 at Us, time t: mu1 = dt mask1 lamU1
+  ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(double), a->st));
+  adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, Us, lamU1, m1, dt, hydro(a, t), FXL,
+                                                    FXR, gqf);
+  adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, Us, lamU1, m1, dt, hydro(a, t), FYL,
+                                                    FYR, gqf);
+  sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k);
+  adj_cell_kernel<1><<<nb, 256, 0, a->st>>>(a->p, Us, lamU1, m1, dt, lam, m2, m1, lamU1, FXL, FXR,
+                                            FYL, FYR, Uk, dt, tmp, gn);
+  ACU(cudaMemcpyAsync(lam, tmp, (size_t)L.plane9 * sizeof(double), cudaMemcpyDeviceToDevice, a->st));
+  a->rev_steps++;
+  return launch_ok();
+}
+
+// Adds dJ/dU of the samples taken after `k` steps into lam.
+int seed_samples(dg2_adj* a, int k) {
+  const AdjLayout& L = a->lay;
+  const int ns = (int)a->samp_step.size();
+  for (int s = 0; s < ns; ++s) {
+    if (a->samp_step[s] != k) continue;
+    double* gh = dptr(a, L.off_gh);
+    ACU(cudaMemcpyAsync(gh, a->gauge_h.data() + (size_t)s * a->ngauge, a->ngauge * sizeof(double),
+                        cudaMemcpyHostToDevice, a->st));
+    // observed depths staged behind the gauge depths in the same small buffer is
+    // not possible (max_gauges slots); stage them in the tmp plane instead
+    double* ob = dptr(a, L.off_tmp);
+    ACU(cudaMemcpyAsync(ob, a->obs.data() + (size_t)s * a->ngauge, a->ngauge * sizeof(double),
+                        cudaMemcpyHostToDevice, a->st));
+    gauge_seed_kernel<<<1, 32, 0, a->st>>>(dptr(a, L.off_lam), L.N, a->ngauge,
+                                           (const long long*)(a->ws + L.off_gidx), dptr(a, L.off_gxi),
+                                           dptr(a, L.off_geta), gh, ob);
+    int r = launch_ok();
+    if (r) return r;
+  }
+  return DG2_OK;
+}
+
+// Binomial checkpointing (treeverse): reverse steps s..e-1; the state after s
+// steps is in snapshot `slot`; `free` further slots (slot+1 ..) are usable.
+double binom(int c, int r) {
+  double b = 1.0;
+  for (int k = 1; k <= c; ++k) b = b * (r + k) / k;
+  return b;
+}
+
+int reverse_range(dg2_adj* a, int s, int e, int slot, int free) {
+  const size_t s9 = (size_t)a->lay.plane9 * sizeof(double);
+  if (e - s == 1) {
+    int r = rev_step(a, s, snap(a, slot));
+    if (r) return r;
+    return seed_samples(a, s);
+  }
+  if (free == 0) {
+    // no slot left: recompute from s for each step
+    double* w2 = dptr(a, a->lay.off_work) + a->lay.plane9;
+    for (int k = e - 1; k >= s; --k) {
+      ACU(cudaMemcpyAsync(w2, snap(a, slot), s9, cudaMemcpyDeviceToDevice, a->st));
+      int r = advance(a, w2, s, k);
+      if (!r) r = rev_step(a, k, w2);
+      if (!r) r = seed_samples(a, k);
+      if (r) return r;
+    }
+    return DG2_OK;
+  }
+  const int t = e - s;
+  int rr = 1;
+  while (binom(free, rr) < t) ++rr;
+  // the right part takes the steps that free - 1 slots reverse with rr sweeps
+  double right = binom(free - 1, rr);
+  int nr = right >= t - 1 ? t - 1 : (int)right;
+  if (nr < 1) nr = 1;
+  const int m = e - nr;
+  const int ns = slot + 1;
+  ACU(cudaMemcpyAsync(snap(a, ns), snap(a, slot), s9, cudaMemcpyDeviceToDevice, a->st));
+  int r = advance(a, snap(a, ns), s, m);
+  if (!r) r = reverse_range(a, m, e, ns, free - 1);
+  if (!r) r = reverse_range(a, s, m, slot, free);
+  return r;
+}
+
+int check_adj(dg2_adj* a) {
+  if (!a) return afail(DG2_E_ARG, "null adjoint context");
+  if (!a->have_state) return afail(DG2_E_STATE, "dg2_adj_set_problem first");
+  if (!a->have_schedule) return afail(DG2_E_STATE, "dg2_adj_set_schedule first");
+  return DG2_OK;
+}
+
+// Forward over all steps from U0; gauge depths of every sample to the host;
+// returns J.
+int forward_all(dg2_adj* a, double* loss) {
+  const AdjLayout& L = a->lay;
+  const int K = (int)a->dts.size();
+  const size_t s9 = (size_t)L.plane9 * sizeof(double);
+  double* cur = snap(a, 0);
+  ACU(cudaMemcpyAsync(cur, dptr(a, L.off_U0), s9, cudaMemcpyDeviceToDevice, a->st));
+  const int ns = (int)a->samp_step.size();
+  a->gauge_h.assign((size_t)ns * a->ngauge, 0.0);
+  double* w = dptr(a, L.off_work);
+  double t = a->t0;
+  auto sample = [&](int k) -> int {
+    for (int s = 0; s < ns; ++s) {
+      if (a->samp_step[s] != k) continue;
+      double* gh = dptr(a, L.off_gh);
+      gauge_kernel<<<1, 256, 0, a->st>>>(cur, L.N, a->ngauge, (const long long*)(a->ws + L.off_gidx),
+                                         dptr(a, L.off_gxi), dptr(a, L.off_geta), gh);
+      int r = launch_ok();
+      if (r) return r;
+      ACU(cudaMemcpyAsync(a->gauge_h.data() + (size_t)s * a->ngauge, gh, a->ngauge * sizeof(double),
+                          cudaMemcpyDeviceToHost, a->st));
+    }
+    return DG2_OK;
+  };
+  int r = sample(0);
+  for (int k = 0; k < K && !r; ++k) {
+    r = fwd_step(a, k, t, cur, w);
+    if (!r) {
+      cudaError_t e = cudaMemcpyAsync(cur, w, s9, cudaMemcpyDeviceToDevice, a->st);
+      if (e != cudaSuccess) r = afail(DG2_E_CUDA, "copy failed: %s", cudaGetErrorString(e));
+    }
+    t += a->dts[k];
+    if (!r) r = sample(k + 1);
+  }
+  if (r) return r;
+  ACU(cudaStreamSynchronize(a->st));
+  double J = 0.0;
+  for (size_t q = 0; q < a->gauge_h.size(); ++q) {
+    const double d = a->gauge_h[q] - a->obs[q];
+    J += d * d;
+  }
+  if (!std::isfinite(J)) return afail(DG2_E_NONFINITE, "non-finite misfit");
+  *loss = J;
+  return DG2_OK;
+}
+
+}  // namespace
+}  // namespace adj
+}  // namespace dg2
+
+using dg2::adj::AdjLayout;
+using dg2::adj::Prob;
+using dg2::adj::adj_layout;
+using dg2::adj::afail;
+using dg2::adj::check_adj;
+using dg2::adj::dptr;
+using dg2::adj::forward_all;
+using dg2::adj::hydro_grad;
+using dg2::adj::kAlign;
+using dg2::adj::kMaxKnotsAdj;
+using dg2::adj::reverse_range;
+using dg2::adj::seed_samples;
+using dg2::adj::snap;
+
+extern "C" {
+
+size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps) {
+  AdjLayout L;
+  if (!adj_layout(nx, ny, nsnap, max_gauges, max_steps, L)) return 0;
+  return L.total;
+}
+
+int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg2_params* prm,
+                   int nsnap, int max_gauges, int max_steps, void* dev_workspace, size_t ws_bytes,
+                   void* cuda_stream) {
+  if (!out) return afail(DG2_E_ARG, "out is null");
+  *out = nullptr;
+  if (!prm) return afail(DG2_E_ARG, "params is null");
+  if (prm->variant != DG2_NL || prm->precision != DG2_FP64)
+    return afail(DG2_E_ARG, "the adjoint is of the FP64 DG2-NL step");
+  if (!(dx > 0.0) || !(dy > 0.0)) return afail(DG2_E_ARG, "dx, dy must be > 0");
+  AdjLayout L;
+  if (!adj_layout(nx, ny, nsnap, max_gauges, max_steps, L))
+    return afail(DG2_E_ARG, "bad sizes (nx, ny, nsnap, max_steps >= 1; max_gauges >= 0)");
+  if (!dev_workspace || ((uintptr_t)dev_workspace % kAlign))
+    return afail(DG2_E_ARG, "workspace must be non-null and 256-byte aligned");
+  if (ws_bytes < L.total) return afail(DG2_E_NOMEM, "workspace too small: %zu < %zu", ws_bytes, L.total);
+  dg2_adj* a = new dg2_adj();
+  a->lay = L;
+  a->ws = (char*)dev_workspace;
+  a->st = (cudaStream_t)cuda_stream;
+  a->max_gauges = max_gauges;
+  a->max_steps = max_steps;
+  Prob& p = a->p;
+  memset(&p, 0, sizeof p);
+  p.nx = nx; p.ny = ny; p.N = L.N;
+  p.dx = dx; p.dy = dy; p.inv_dx = 1.0 / dx; p.inv_dy = 1.0 / dy;
+  p.g = prm->g; p.tol = prm->tol_dry;
+  for (int k = 0; k < 4; ++k) p.bc[k] = prm->bc[k];
+  p.in_edge = -1;
+  p.Z = dptr(a, L.off_Z);
+  p.Nm = dptr(a, L.off_Nm);
+  a->t0 = 0.0;
+  a->ngauge = 0;
+  a->have_state = a->have_schedule = false;
+  a->fwd_steps = a->rev_steps = 0;
+  *out = a;
+  return DG2_OK;
+}
+
+int dg2_adj_set_problem(dg2_adj* a, const double* z3, const double* state9, double t0,
+                        const double* manning, int inflow_edge, double s0, double len,
+                        const double* t_knots, const double* q_knots, int nknots,
+                        const double* gauge_xy, int ngauge) {
+  if (!a) return afail(DG2_E_ARG, "null adjoint context");
+  if (!z3 || !state9 || !manning) return afail(DG2_E_ARG, "z3, state9 and manning are required");
+  if (ngauge < 0 || ngauge > a->max_gauges) return afail(DG2_E_ARG, "ngauge must be 0..%d", a->max_gauges);
+  if (ngauge > 0 && !gauge_xy) return afail(DG2_E_ARG, "gauge_xy is null");
+  if (inflow_edge >= 0) {
+    if (inflow_edge > 3 || !t_knots || !q_knots || nknots < 1 || nknots > kMaxKnotsAdj)
+      return afail(DG2_E_ARG, "inflow needs edge 0..3 and 1..%d knots", kMaxKnotsAdj);
+    for (int k = 1; k < nknots; ++k)
+      if (!(t_knots[k] > t_knots[k - 1])) return afail(DG2_E_ARG, "t_knots must increase");
+  }
+  const AdjLayout& L = a->lay;
+  Prob& p = a->p;
+  const size_t N = (size_t)L.N;
+  ACU(cudaMemcpyAsync(dptr(a, L.off_Z), z3, 3 * N * sizeof(double), cudaMemcpyHostToDevice, a->st));
+  ACU(cudaMemcpyAsync(dptr(a, L.off_U0), state9, 9 * N * sizeof(double), cudaMemcpyHostToDevice, a->st));
+  ACU(cudaMemcpyAsync(dptr(a, L.off_Nm), manning, N * sizeof(double), cudaMemcpyHostToDevice, a->st));
+  a->t0 = t0;
+  p.in_edge = inflow_edge;
+  a->tk.clear();
+  a->qk.clear();
+  if (inflow_edge >= 0) {
+    a->tk.assign(t_knots, t_knots + nknots);
+    a->qk.assign(q_knots, q_knots + nknots);
+    const bool ew = inflow_edge <= 1;
+    const int n = ew ? p.ny : p.nx;
+    const double h = ew ? p.dy : p.dx;
+    int nf = 0;
+    for (int k = 0; k < n; ++k) {
+      const double s = (k + 0.5) * h;
+      if (s >= s0 && s <= s0 + len) ++nf;
+    }
+    if (nf == 0) return afail(DG2_E_ARG, "no face centre lies in the inflow segment");
+    p.in_s0 = s0;
+    p.in_s1 = s0 + len;
+    p.in_width = nf * h;
+  }
+  std::vector<long long> gi(ngauge > 0 ? ngauge : 1);
+  std::vector<double> gx(ngauge > 0 ? ngauge : 1), ge(ngauge > 0 ? ngauge : 1);
+  for (int k = 0; k < ngauge; ++k) {
+    int i = (int)std::floor(gauge_xy[2 * k] / p.dx), j = (int)std::floor(gauge_xy[2 * k + 1] / p.dy);
+    i = i < 0 ? 0 : (i >= p.nx ? p.nx - 1 : i);
+    j = j < 0 ? 0 : (j >= p.ny ? p.ny - 1 : j);
+    gi[k] = (long long)j * p.nx + i;
+    gx[k] = (gauge_xy[2 * k] - (i + 0.5) * p.dx) / (0.5 * p.dx);
+    ge[k] = (gauge_xy[2 * k + 1] - (j + 0.5) * p.dy) / (0.5 * p.dy);
+  }
+  if (ngauge > 0) {
+    ACU(cudaMemcpyAsync(a->ws + L.off_gidx, gi.data(), ngauge * sizeof(long long), cudaMemcpyHostToDevice, a->st));
+    ACU(cudaMemcpyAsync(a->ws + L.off_gxi, gx.data(), ngauge * sizeof(double), cudaMemcpyHostToDevice, a->st));
+    ACU(cudaMemcpyAsync(a->ws + L.off_geta, ge.data(), ngauge * sizeof(double), cudaMemcpyHostToDevice, a->st));
+  }
+  ACU(cudaStreamSynchronize(a->st));
+  a->ngauge = ngauge;
+  a->have_state = true;
+  return DG2_OK;
+}
+
+int dg2_adj_set_params(dg2_adj* a, const double* manning, const double* q_knots) {
+  if (!a || !a->have_state) return afail(DG2_E_STATE, "dg2_adj_set_problem first");
+  if (manning)
+    ACU(cudaMemcpyAsync(dptr(a, a->lay.off_Nm), manning, (size_t)a->lay.N * sizeof(double),
+                        cudaMemcpyHostToDevice, a->st));
+  if (q_knots) a->qk.assign(q_knots, q_knots + a->qk.size());
+  ACU(cudaStreamSynchronize(a->st));
+  return DG2_OK;
+}
+
+int dg2_adj_set_schedule(dg2_adj* a, const double* dts, int nsteps, const int* sample_steps,
+                         int nsamples, const double* obs) {
+  if (!a || !a->have_state) return afail(DG2_E_STATE, "dg2_adj_set_problem first");
+  if (!dts || nsteps < 1 || nsteps > a->max_steps)
+    return afail(DG2_E_ARG, "need 1..%d step sizes", a->max_steps);
+  for (int k = 0; k < nsteps; ++k)
+    if (!(dts[k] > 0.0) || !std::isfinite(dts[k])) return afail(DG2_E_ARG, "step %d: dt must be > 0", k);
+  if (nsamples < 0 || (nsamples > 0 && (!sample_steps || !obs)))
+    return afail(DG2_E_ARG, "bad samples");
+  for (int s = 0; s < nsamples; ++s)
+    if (sample_steps[s] < 0 || sample_steps[s] > nsteps)
+      return afail(DG2_E_ARG, "sample %d: step must be 0..%d", s, nsteps);
+  a->dts.assign(dts, dts + nsteps);
+  a->samp_step.assign(sample_steps, sample_steps + nsamples);
+  a->obs.assign(obs, obs + (size_t)nsamples * a->ngauge);
+  a->have_schedule = true;
+  return DG2_OK;
+}
+
+int dg2_adj_forward(dg2_adj* a, double* loss, double* gauge_h) {
+  int r = check_adj(a);
+  if (r) return r;
+  double J;
+  if ((r = forward_all(a, &J))) return r;
+  if (loss) *loss = J;
+  if (gauge_h) memcpy(gauge_h, a->gauge_h.data(), a->gauge_h.size() * sizeof(double));
+  return DG2_OK;
+}
+
+int dg2_adj_gradient(dg2_adj* a, double* loss, double* grad_manning, double* grad_q) {
+  int r = check_adj(a);
+  if (r) return r;
+  const AdjLayout& L = a->lay;
+  const int K = (int)a->dts.size();
+  double J;
+  if ((r = forward_all(a, &J))) return r;
+  ACU(cudaMemsetAsync(dptr(a, L.off_lam), 0, (size_t)L.plane9 * sizeof(double), a->st));
+  ACU(cudaMemsetAsync(dptr(a, L.off_gn), 0, (size_t)L.N * sizeof(double), a->st));
+  ACU(cudaMemsetAsync(dptr(a, L.off_gq_step), 0, 2 * (size_t)K * sizeof(double), a->st));
+  if ((r = seed_samples(a, K))) return r;
+  // snapshot 0 holds U0 again (forward_all advanced it in place)
+  ACU(cudaMemcpyAsync(snap(a, 0), dptr(a, L.off_U0), (size_t)L.plane9 * sizeof(double),
+                      cudaMemcpyDeviceToDevice, a->st));
+  if ((r = reverse_range(a, 0, K, 0, L.nsnap - 1))) return r;
+  if (grad_manning)
+    ACU(cudaMemcpyAsync(grad_manning, dptr(a, L.off_gn), (size_t)L.N * sizeof(double),
+                        cudaMemcpyDeviceToHost, a->st));
+  std::vector<double> gqs(2 * (size_t)K);
+  ACU(cudaMemcpyAsync(gqs.data(), dptr(a, L.off_gq_step), gqs.size() * sizeof(double),
+                      cudaMemcpyDeviceToHost, a->st));
+  ACU(cudaStreamSynchronize(a->st));
+  if (grad_q) {
+    std::vector<double> g(a->qk.size(), 0.0);
+    double t = a->t0;
+    for (int k = 0; k < K; ++k) {
+      hydro_grad(a, t, gqs[2 * (size_t)k], g.data());
+      hydro_grad(a, t + a->dts[k], gqs[2 * (size_t)k + 1], g.data());
+      t += a->dts[k];
+    }
+    memcpy(grad_q, g.data(), g.size() * sizeof(double));
+  }
+  if (loss) *loss = J;
+  return DG2_OK;
+}
+
+int dg2_adj_counts(const dg2_adj* a, int64_t* forward_steps, int64_t* reverse_steps) {
+  if (!a) return afail(DG2_E_ARG, "null adjoint context");
+  if (forward_steps) *forward_steps = a->fwd_steps;
+  if (reverse_steps) *reverse_steps = a->rev_steps;
+  return DG2_OK;
+}
+
+int dg2_adj_destroy(dg2_adj* a) {
+  if (!a) return afail(DG2_E_ARG, "null adjoint context");
+  delete a;
+  return DG2_OK;
+}
+
+}  // extern "C"
