@@ -12,7 +12,9 @@ Courant reduction, time/ledger update) through the C ABI.
 
 The ensemble variant runs 256 members of log-uniform sizes (18.6 M cells) from
 dry to t = 1 h in FP32 with one set of launches per step, after the tile-shape
-autotuner.
+autotuner.  The adjoint variant times the gauge-misfit gradient (Manning field
+and 64 inflow knots) of 4000 FP64 DG2-NL steps on 512 x 512 cells with 64
+checkpoints against the misfit alone (the adjoint/forward time ratio).
 
 One line of JSON on rank 0.  With --impl reference the CPU oracle is timed
 instead (a bounded 500 x 250 sample of the same workload recipe).
@@ -404,6 +406,74 @@ def ensemble_variant(B, torch, inputs, n=ENS_MEMBERS, t_end=ENS_T_END):
     return out
 
 
+ADJ_N, ADJ_STEPS, ADJ_SNAP, ADJ_KNOTS = 512, 4000, 64, 64
+
+
+def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS):
+    """Discrete adjoint on the calibration recipe: the 512 x 512 floodplain terrain
+    (dx 2 m, seed 2014) under a gently tilted free surface (every cell wet: the
+    channel start's thin films make the step map chaotic, and its exact derivative
+    over 4000 steps grows like its round-off amplification), whose truth is the
+    generator's two-zone Manning field and triangular inflow; step sizes frozen from
+    a Courant-step run of the truth; 8 gauges sampled every 10 s; misfit against the
+    truth's depths at Manning 0.04 everywhere and the inflow's 64 knots at 0.8 x
+    truth.  Times the
+    misfit alone (forward) and misfit + gradient (forward, checkpointed reverse)
+    with CUDA events on the adjoint's stream; the plain FP64 DG2-NL solver doing the
+    same steps is timed beside it."""
+    case = inputs.flooded_plain(ADJ_N, ADJ_N, 2.0, seed=2014)
+    s = B.solver_from_case(case, variant=B.DG2_NL, precision=B.DG2_FP64)
+    init = s.state()
+    dts = np.array([s.step(-1.0, want_dt=True) for _ in range(steps)])
+    # the plain solver over the same steps (forced dt), device-timed
+    s.set_state(init, 0.0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s.stream)
+    for dt in dts:
+        s.step(float(dt))
+    ev1.record(s.stream)
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)
+    s.close()
+    t = np.cumsum(dts)
+    samples = [int(np.argmax(t >= m)) + 1 for m in np.arange(10.0, t[-1], 10.0)]
+    # 64 knots over the run carrying the truth hydrograph
+    f = case.inflows[0]
+    tk = np.linspace(0.0, float(t[-1]), ADJ_KNOTS)
+    q_true = np.interp(tk, f.t_knots, f.q_knots)
+    f.t_knots, f.q_knots = tk, q_true
+    a = B.Adjoint(case, nsnap=ADJ_SNAP, max_steps=steps)
+    a.set_schedule(dts, samples, np.zeros((len(samples), a.ngauge)))
+    _, h_true = a.forward()
+    a.set_schedule(dts, samples, h_true)
+    man0 = np.full((case.ny, case.nx), 0.04)
+    a.set_params(man0, 0.8 * q_true)
+    st = a.stream
+    torch.cuda.synchronize()
+    ev0.record(st)
+    J, _ = a.forward()
+    ev1.record(st)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1)
+    f0, r0 = a.counts()
+    ev0.record(st)
+    J2, gn, gq = a.gradient()
+    ev1.record(st)
+    torch.cuda.synchronize()
+    grad_ms = ev0.elapsed_time(ev1)
+    f1, r1 = a.counts()
+    a.close()
+    return {"cells": case.nx * case.ny, "steps": steps, "t_end_s": float(t[-1]),
+            "samples": len(samples), "gauges": 8, "knots": ADJ_KNOTS, "checkpoints": ADJ_SNAP,
+            "misfit": J, "forward_ms": fwd_ms, "gradient_ms": grad_ms,
+            "value": grad_ms / fwd_ms, "unit": "adjoint/forward time ratio",
+            "vs_plain_fp64_nl": grad_ms / plain_ms, "plain_fp64_nl_ms": plain_ms,
+            "forward_steps_in_gradient": f1 - f0, "reverse_steps": r1 - r0,
+            "grad_manning_norm": float(np.linalg.norm(gn)),
+            "grad_knots_norm": float(np.linalg.norm(gq))}
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
@@ -459,6 +529,12 @@ def main():
         results[key] = run
         torch.cuda.empty_cache()
 
+    adj = None
+    if not only or "fp64_nl_adjoint" in only:
+        barrier(world)
+        adj = adjoint_variant(B, torch, inputs)
+        torch.cuda.empty_cache()
+
     ens = None
     if not only or "fp32_nl_ensemble" in only:
         barrier(world)
@@ -468,8 +544,9 @@ def main():
         torch.cuda.empty_cache()
 
     if not results:
-        if rank == 0 and ens is not None:
-            print(json.dumps({"metric": METRIC, "variants": {"fp32_nl_ensemble": ens}}))
+        if rank == 0:
+            extra = {k: v for k, v in (("fp32_nl_ensemble", ens), ("fp64_nl_adjoint", adj)) if v}
+            print(json.dumps({"metric": METRIC, "variants": extra}))
         return
     head = "fp64_ll" if "fp64_ll" in results else next(iter(results))
     hd = results[head]
@@ -493,6 +570,8 @@ def main():
                     for k, r in results.items() if k != head}
         if ens is not None:
             variants["fp32_nl_ensemble"] = ens
+        if adj is not None:
+            variants["fp64_nl_adjoint"] = adj
         line = {"metric": METRIC, "value": hd["value"], "unit": "cell-updates/s", "n_gpus": world,
                 "steps": hd["steps"], "warmup": warmup, "ms_per_step": hd["ms_max"] / hd["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
