@@ -57,6 +57,7 @@ enum { DG2_NL = 0, DG2_LL = 1 };            /* DG2-NL: no limiting; DG2-LL: Eqs.
  * the mass ledger stay FP64 in both.  State I/O is FP64 depth modes in both. */
 enum { DG2_FP64 = 0, DG2_FP32 = 1 };
 enum { DG2_WALL = 0, DG2_OPEN = 1 };        /* edge types                            */
+enum { DG2_HLL = 0, DG2_ROE = 1 };          /* Riemann solvers                       */
 enum { DG2_WEST = 0, DG2_EAST = 1, DG2_SOUTH = 2, DG2_NORTH = 3 };
 
 typedef struct dg2_params {
@@ -74,6 +75,8 @@ typedef struct dg2_params {
                            still, dry neighbours untouched -- they are exact fixed
                            points of a step, so results are bit-identical; 0: compute
                            every tile */
+    int flux;           /* Riemann solver: DG2_HLL (default) or DG2_ROE (Roe's solver
+                           named in Sec. 2.1.2, Harten's entropy fix; DG2_FP64 only) */
 } dg2_params;
 
 typedef struct dg2_ctx dg2_ctx;

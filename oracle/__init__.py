@@ -139,6 +139,7 @@ def _load():
         "orc_limit": (None, [P, dp, dp]),
         "orc_hll": (None, [P, I, dp, dp, dp]),
         "orc_minmod": (D, [D, D, D]),
+        "orc_set_flux": (None, [P, I]),
         "orc_gauge_h": (D, [P, D, D]),
         "orc_run_to": (ctypes.c_long, [P, D, D, I, dp, dp, dp, I, ip]),
     }
@@ -172,7 +173,7 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, dx, dy, *, g=9.80665, cfl=0.33, tol_dry=1e-5, ds_thresh=10.0,
-                 dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL)):
+                 dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL), flux="hll"):
         self.lib = _load()
         self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
         self.g, self.cfl, self.tol_dry = g, cfl, tol_dry
@@ -181,6 +182,9 @@ class Oracle:
                                      dt_max, int(bool(limiter)), bca)
         if not self.h:
             raise ValueError("bad grid size")
+        if flux not in ("hll", "roe"):
+            raise ValueError("flux must be 'hll' or 'roe'")
+        self.lib.orc_set_flux(self.h, 1 if flux == "roe" else 0)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -66,6 +66,7 @@ typedef struct {
     double dx, dy;
     double g, cfl, tol_dry, ds_thresh, dt_max;
     int limiter;           /* 0: DG2-NL, 1: DG2-LL */
+    int flux;              /* Riemann solver: 0 HLL, 1 Roe */
     int bc[4];
     int n_in;
     inflow_t in[MAX_INFLOW];
@@ -156,11 +157,62 @@ static st3 hll_x(const orc_t *o, st3 Ls, st3 Rs)
               (sR * FL.qy - sL * FR.qy + sL * sR * (Rs.qy - Ls.qy)) / den);
 }
 
-/* HLL flux across a face normal to y: the x-solver in the frame where y is
+/* Acoustic-wave speed magnitude with Harten's entropy fix: |lam| is
+ * replaced by (lam^2 + d^2) / (2 d) when |lam| < d, d = max(0, lam - lamL,
+ * lamR - lam) (the spread of the characteristic speeds across the face). */
+static real harten(real lam, real lamL, real lamR)
+{
+    real d = lam - lamL;
+    if (lamR - lam > d) d = lamR - lam;
+    if (d < 0.0) d = 0.0;
+    real a = fabs(lam);
+    if (a < d) a = (lam * lam + d * d) / (2.0 * d);
+    return a;
+}
+
+/* Roe flux across a face normal to x (Sec. 2.1.2 names Roe's solver): the
+ * average of the two physical fluxes minus the upwinding of the three waves of
+ * the Roe-linearised system, with Roe averages u^ = (sqrt(hL) uL +
+ * sqrt(hR) uR) / (sqrt(hL) + sqrt(hR)) (v^ alike), h^ = sqrt(hL hR),
+ * c^ = sqrt(g (hL + hR) / 2), eigenvalues u^ - c^, u^, u^ + c^, wave
+ * strengths a1,3 = (dh -+ h^ du / c^) / 2, a2 = h^ dv, eigenvectors
+ * (1, u^ -+ c^, v^) and (0, 0, 1); Harten's entropy fix on the acoustic
+ * waves; zero flux between two dry limits. */
+static st3 roe_x(const orc_t *o, st3 Ls, st3 Rs)
+{
+    const real tol = o->tol_dry, g = o->g;
+    if (Ls.h <= tol && Rs.h <= tol) return mk(0.0, 0.0, 0.0);
+    real uL, vL, uR, vR;
+    velocities(o, Ls, &uL, &vL);
+    velocities(o, Rs, &uR, &vR);
+    real sL = sqrt(Ls.h), sR = sqrt(Rs.h);
+    real uh = (sL * uL + sR * uR) / (sL + sR);
+    real vh = (sL * vL + sR * vR) / (sL + sR);
+    real hh = sL * sR;
+    real ch = sqrt(0.5 * g * (Ls.h + Rs.h));
+    real dh = Rs.h - Ls.h, du = uR - uL, dv = vR - vL;
+    real a1 = 0.5 * (dh - hh * du / ch), a2 = hh * dv, a3 = 0.5 * (dh + hh * du / ch);
+    real l1 = uh - ch, l3 = uh + ch;
+    real cL = sqrt(g * Ls.h), cR = sqrt(g * Rs.h);
+    real e1 = harten(l1, uL - cL, uR - cR), e2 = fabs(uh), e3 = harten(l3, uL + cL, uR + cR);
+    st3 FL = flux_x(o, Ls), FR = flux_x(o, Rs);
+    real w1 = e1 * a1, w2 = e2 * a2, w3 = e3 * a3;
+    return mk(0.5 * (FL.h + FR.h) - 0.5 * (w1 + w3),
+              0.5 * (FL.qx + FR.qx) - 0.5 * (w1 * l1 + w3 * l3),
+              0.5 * (FL.qy + FR.qy) - 0.5 * (w1 * vh + w2 + w3 * vh));
+}
+
+/* The Riemann solver of the run across a face normal to x. */
+static st3 riemann_x(const orc_t *o, st3 Ls, st3 Rs)
+{
+    return o->flux == 1 ? roe_x(o, Ls, Rs) : hll_x(o, Ls, Rs);
+}
+
+/* Flux across a face normal to y: the x-solver in the frame where y is
  * the normal direction (qy normal, qx tangential), rotated back. */
 static st3 hll_y(const orc_t *o, st3 Ss, st3 Ns)
 {
-    st3 r = hll_x(o, mk(Ss.h, Ss.qy, Ss.qx), mk(Ns.h, Ns.qy, Ns.qx));
+    st3 r = riemann_x(o, mk(Ss.h, Ss.qy, Ss.qx), mk(Ns.h, Ns.qy, Ns.qx));
     return mk(r.h, r.qy, r.qx);
 }
 
@@ -303,8 +355,8 @@ static real spatial_operator(const orc_t *o, const real *U, double t, real *Lout
             real zN = zlimit_at(o, i, j, EN) - (Nn.h < 0.0 ? -Nn.h : (real)0.0);
             real zS = zlimit_at(o, i, j, ES) - (S.h < 0.0 ? -S.h : (real)0.0);
             /* inter-elemental fluxes */
-            st3 FE = hll_x(o, Es, revise(o, outer_limit(o, U, i, j, EE, t)));
-            st3 FW = hll_x(o, revise(o, outer_limit(o, U, i, j, EW, t)), Ws);
+            st3 FE = riemann_x(o, Es, revise(o, outer_limit(o, U, i, j, EE, t)));
+            st3 FW = riemann_x(o, revise(o, outer_limit(o, U, i, j, EW, t)), Ws);
             st3 GN = hll_y(o, Ns, revise(o, outer_limit(o, U, i, j, EN, t)));
             st3 GS = hll_y(o, revise(o, outer_limit(o, U, i, j, ES, t)), Ss);
             if (i == 0) bsum += FW.h * dy;
@@ -715,10 +767,12 @@ void orc_limit(const orc_t *o, const double *Uin, double *Uout)
 void orc_hll(const orc_t *o, int dir, const double *l3, const double *r3, double *f3)
 {
     st3 a = mk(l3[0], l3[1], l3[2]), b = mk(r3[0], r3[1], r3[2]);
-    st3 f = dir == 0 ? hll_x(o, a, b) : hll_y(o, a, b);
+    st3 f = dir == 0 ? riemann_x(o, a, b) : hll_y(o, a, b);
     f3[0] = f.h; f3[1] = f.qx; f3[2] = f.qy;
 }
 double orc_minmod(double a, double b, double c) { return minmod3(a, b, c); }
+/* Riemann solver of the run: 0 HLL (default), 1 Roe. */
+void orc_set_flux(orc_t *o, int flux) { o->flux = flux; }
 
 /* Depth at (x, y) from the planar solution of the containing cell, clipped at 0. */
 double orc_gauge_h(const orc_t *o, double x, double y)

@@ -359,6 +359,7 @@ void dg2_default_params(dg2_params* p) {
   p->max_gauges = 64;
   p->max_samples = 4096;
   p->skip_dry_tiles = 1;
+  p->flux = DG2_HLL;
 }
 
 const char* dg2_last_error(void) { return g_err.c_str(); }
@@ -384,6 +385,9 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
       (p.variant != DG2_NL && p.variant != DG2_LL) ||
       (p.precision != DG2_FP64 && p.precision != DG2_FP32))
     return fail(DG2_E_ARG, "invalid parameters (g, cfl, tol_dry, dt_max, variant, precision)");
+  if (p.flux != DG2_HLL && p.flux != DG2_ROE) return fail(DG2_E_ARG, "flux must be HLL or ROE");
+  if (p.flux == DG2_ROE && p.precision != DG2_FP64)
+    return fail(DG2_E_ARG, "the Roe flux is built for DG2_FP64 only");
   for (int k = 0; k < 4; ++k)
     if (p.bc[k] != DG2_WALL && p.bc[k] != DG2_OPEN) return fail(DG2_E_ARG, "bad edge type");
   if ((long long)nx * ny > (1ll << 31)) return fail(DG2_E_ARG, "grid too large");
@@ -419,6 +423,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.S = (double*)(c->ws + L.off_S);
   d.T = (double*)(c->ws + L.off_T);
   d.Q = p.variant == DG2_LL ? (double*)(c->ws + L.off_Q) : nullptr;
+  d.flux = p.flux;
   d.Z = (const double*)(c->ws + L.off_Z);
   d.N = (const double*)(c->ws + L.off_N);
   d.bpart = (double*)(c->ws + L.off_bpart);

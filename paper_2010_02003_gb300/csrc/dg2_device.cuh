@@ -97,6 +97,7 @@ struct Dev {
   // parameters
   double g, cfl, tol, ds, dt_max;
   int bc[4];
+  int flux;                  // 0 HLL, 1 Roe
   // inflows
   int n_in;
   InflowDesc in[kMaxInflow];
@@ -198,14 +199,61 @@ __device__ __forceinline__ F3 hll(double hL, double qnL, double qtL, double unL,
   return f;
 }
 
+// |lam| with Harten's entropy fix: (lam^2 + d^2) / (2 d) below d = max(0,
+// lam - lamL, lamR - lam), the spread of the characteristic speeds at the face.
+__device__ __forceinline__ double harten(double lam, double lamL, double lamR) {
+  double d = lam - lamL;
+  if (lamR - lam > d) d = lamR - lam;
+  if (d < 0.0) d = 0.0;
+  double a = fabs(lam);
+  if (a < d) a = (lam * lam + d * d) / (2.0 * d);
+  return a;
+}
+
+// Roe flux normal to a face (Sec. 2.1.2 names Roe's solver): the average of
+// the physical fluxes minus the upwinding of the waves of the Roe-linearised
+// system (Roe averages, eigenvalues u^ -+ c^ and u^, wave strengths
+// (dh -+ h^ du / c^) / 2 and h^ dt), Harten's entropy fix on the acoustic waves.
+__device__ __forceinline__ F3 roe(double hL, double qnL, double qtL, double unL, double utL,
+                                  double hR, double qnR, double qtR, double unR, double utR,
+                                  double g, double tol) {
+  F3 f;
+  if (hL <= tol && hR <= tol) {
+    f.h = 0.0; f.x = 0.0; f.y = 0.0;
+    return f;
+  }
+  const double sL = sqrt(hL), sR = sqrt(hR);
+  const double uh = (sL * unL + sR * unR) / (sL + sR);
+  const double vh = (sL * utL + sR * utR) / (sL + sR);
+  const double hh = sL * sR;
+  const double ch = sqrt(0.5 * g * (hL + hR));
+  const double dh = hR - hL, du = unR - unL, dv = utR - utL;
+  const double a1 = 0.5 * (dh - hh * du / ch), a2 = hh * dv, a3 = 0.5 * (dh + hh * du / ch);
+  const double l1 = uh - ch, l3 = uh + ch;
+  const double cL = sqrt(g * hL), cR = sqrt(g * hR);
+  const double e1 = harten(l1, unL - cL, unR - cR), e2 = fabs(uh);
+  const double e3 = harten(l3, unL + cL, unR + cR);
+  const double w1 = e1 * a1, w2 = e2 * a2, w3 = e3 * a3;
+  const double fLh = hL * unL, fLn = hL * unL * unL + 0.5 * g * hL * hL, fLt = hL * unL * utL;
+  const double fRh = hR * unR, fRn = hR * unR * unR + 0.5 * g * hR * hR, fRt = hR * unR * utR;
+  f.h = 0.5 * (fLh + fRh) - 0.5 * (w1 + w3);
+  f.x = 0.5 * (fLn + fRn) - 0.5 * (w1 * l1 + w3 * l3);
+  f.y = 0.5 * (fLt + fRt) - 0.5 * (w1 * vh + w2 + w3 * vh);
+  return f;
+}
+
 // x-face flux: returns [F^h, F^qx, F^qy].
-__device__ __forceinline__ F3 flux_x(const Lim& L, const Lim& R, double g, double tol) {
+__device__ __forceinline__ F3 flux_x(const Lim& L, const Lim& R, double g, double tol,
+                                     int flux = 0) {
+  if (flux == 1) return roe(L.h, L.qx, L.qy, L.u, L.v, R.h, R.qx, R.qy, R.u, R.v, g, tol);
   return hll(L.h, L.qx, L.qy, L.u, L.v, R.h, R.qx, R.qy, R.u, R.v, g, tol);
 }
 
 // y-face flux in the rotated frame, mapped back: returns [G^h, G^qx, G^qy].
-__device__ __forceinline__ F3 flux_y(const Lim& S, const Lim& N, double g, double tol) {
-  F3 r = hll(S.h, S.qy, S.qx, S.v, S.u, N.h, N.qy, N.qx, N.v, N.u, g, tol);
+__device__ __forceinline__ F3 flux_y(const Lim& S, const Lim& N, double g, double tol,
+                                     int flux = 0) {
+  F3 r = flux == 1 ? roe(S.h, S.qy, S.qx, S.v, S.u, N.h, N.qy, N.qx, N.v, N.u, g, tol)
+                   : hll(S.h, S.qy, S.qx, S.v, S.u, N.h, N.qy, N.qx, N.v, N.u, g, tol);
   F3 o;
   o.h = r.h; o.x = r.y; o.y = r.x;
   return o;
@@ -679,20 +727,20 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   // one HLL flux per face of the tile
   if (act) {
     const Lim& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
-    const F3 fw = flux_x(Lw, Ws, g, tol);
+    const F3 fw = flux_x(Lw, Ws, g, tol, d.flux);
     sm.fx[ty][tx] = fw;
     if (i == 0) brate += fw.h * d.dy;
     if (east_edge) {
-      const F3 fe = flux_x(Es, sm.he[ty], g, tol);
+      const F3 fe = flux_x(Es, sm.he[ty], g, tol, d.flux);
       sm.fx[ty][tx + 1] = fe;
       if (i == d.nx - 1) brate -= fe.h * d.dy;
     }
     const Lim& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
-    const F3 fs = flux_y(Ls, Ss, g, tol);
+    const F3 fs = flux_y(Ls, Ss, g, tol, d.flux);
     sm.fy[ty][tx] = fs;
     if (j == 0) brate += fs.h * d.dx;
     if (north_edge) {
-      const F3 fn = flux_y(Ns, sm.hn[tx], g, tol);
+      const F3 fn = flux_y(Ns, sm.hn[tx], g, tol, d.flux);
       sm.fy[ty + 1][tx] = fn;
       if (j == d.ny - 1) brate -= fn.h * d.dx;
     }

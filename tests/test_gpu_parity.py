@@ -246,3 +246,75 @@ def test_urban_recipe_small(limiter):
     assert plane_err(s.state(), o.state()).max() <= TOL
     m, led = s.mass()
     assert abs(m - led) <= 1e-12 * m
+
+
+ROE_CASES = {
+    "hump_dam_128": lambda: inputs.hump(eta=0.5, dam_eta=1.0),
+    "terrain_77x53": lambda: inputs.random_terrain(77, 53, seed=5),
+    "blocks_48x40": lambda: inputs.wall_blocks(),
+    "floodplain_dry_96x64": lambda: inputs.floodplain(nx=96, ny=64, dx=2.0, q_peak=15.0,
+                                                      t_peak=20.0, channel_width=12.0),
+}
+
+
+def _oracle_step_sensitivity(case, limiter, state, t, dt, seeds=3):
+    """How far the oracle's own step moves when its input state is perturbed by
+    2e-16 of each variable's scale (max over a few seeds, in plane_err units): the
+    part of a GPU difference that rounding order alone explains."""
+    hs = np.abs(state[0]).max()
+    qs = max(np.abs(state[3]).max(), np.abs(state[6]).max())
+    scale = np.array([hs] * 3 + [qs] * 6)[:, None, None]
+    ref = make_oracle(case, limiter=limiter, flux="roe")
+    ref.set_state(state, t)
+    ref.step(dt)
+    base = ref.state()
+    worst = 0.0
+    for sd in range(seeds):
+        rng = np.random.default_rng(sd)
+        tw = make_oracle(case, limiter=limiter, flux="roe")
+        tw.set_state(state + rng.standard_normal(state.shape) * 2e-16 * scale * (state != 0), t)
+        tw.step(dt)
+        worst = max(worst, plane_err(tw.state(), base).max())
+    return worst
+
+
+@pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
+@pytest.mark.parametrize("name", list(ROE_CASES))
+def test_roe_step_parity_along_oracle_trajectory(name, limiter):
+    """The Roe flux option: each of 60 steps from the oracle's own state within
+    1e-12, or, on a step whose result the oracle itself moves by more than 1e-14
+    under a 2e-16 perturbation of its input (thin films at a wet-dry front, where
+    q/h amplifies rounding), within 100 times that sensitivity."""
+    case = ROE_CASES[name]()
+    B = _binding()
+    o = make_oracle(case, limiter=limiter, flux="roe")
+    s = B.solver_from_case(case, variant=B.DG2_LL if limiter else B.DG2_NL, flux=B.DG2_ROE)
+    for k in range(60):
+        st0, t0 = o.state(), o.t
+        s.set_state(st0, t0)
+        dt = o.step()
+        s.step(dt)
+        err = plane_err(s.state(), o.state()).max()
+        if err > TOL:
+            sens = _oracle_step_sensitivity(case, limiter, st0, t0, dt)
+            assert sens > 1e-14 and err <= 100.0 * sens, (k, err, sens)
+
+
+@pytest.mark.parametrize("name", ["hump_dam_128", "blocks_48x40"])
+def test_roe_free_run_100_steps(name):
+    case = ROE_CASES[name]()
+    B = _binding()
+    o = make_oracle(case, limiter=True, flux="roe")
+    s = B.solver_from_case(case, variant=B.DG2_LL, flux=B.DG2_ROE)
+    for _ in range(100):
+        s.step(o.step())
+    assert plane_err(s.state(), o.state()).max() <= TOL
+    m, led = s.mass()
+    assert abs(m - o.mass()) <= 1e-12 * o.mass()
+
+
+def test_roe_is_fp64_only():
+    B = _binding()
+    with pytest.raises(B.Dg2Error) as e:
+        B.Solver(16, 16, 1.0, precision=B.DG2_FP32, flux=B.DG2_ROE)
+    assert e.value.code == B.DG2_E_ARG
