@@ -140,6 +140,7 @@ def _load():
         "orc_hll": (None, [P, I, dp, dp, dp]),
         "orc_minmod": (D, [D, D, D]),
         "orc_set_flux": (None, [P, I]),
+        "orc_set_scheme": (None, [P, I]),
         "orc_gauge_h": (D, [P, D, D]),
         "orc_run_to": (ctypes.c_long, [P, D, D, I, dp, dp, dp, I, ip]),
     }
@@ -173,7 +174,8 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, dx, dy, *, g=9.80665, cfl=0.33, tol_dry=1e-5, ds_thresh=10.0,
-                 dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL), flux="hll"):
+                 dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL), flux="hll",
+                 scheme="dg2"):
         self.lib = _load()
         self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
         self.g, self.cfl, self.tol_dry = g, cfl, tol_dry
@@ -185,6 +187,9 @@ class Oracle:
         if flux not in ("hll", "roe"):
             raise ValueError("flux must be 'hll' or 'roe'")
         self.lib.orc_set_flux(self.h, 1 if flux == "roe" else 0)
+        if scheme not in ("dg2", "fv2", "fv1"):
+            raise ValueError("scheme must be 'dg2', 'fv2' or 'fv1'")
+        self.lib.orc_set_scheme(self.h, ("dg2", "fv2", "fv1").index(scheme))
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -67,6 +67,7 @@ typedef struct {
     double g, cfl, tol_dry, ds_thresh, dt_max;
     int limiter;           /* 0: DG2-NL, 1: DG2-LL */
     int flux;              /* Riemann solver: 0 HLL, 1 Roe */
+    int scheme;            /* 0 DG2, 1 MUSCL-FV2, 2 FV1 (Sec. 2.2 comparators) */
     int bc[4];
     int n_in;
     inflow_t in[MAX_INFLOW];
@@ -577,9 +578,200 @@ double orc_cfl_dt(const orc_t *o)
     return dt < o->dt_max ? dt : o->dt_max;
 }
 
+/* ------------------------------------------------------------------ */
+/* MUSCL-FV2 and FV1 comparators (Sec. 2.2, Eqs. 8-10)                 */
+/* ------------------------------------------------------------------ */
+
+/* Sweby's symmetric limiter with parameter beta (Sec. 2.2.3, beta = 1.25). */
+static real sweby(real r, real beta)
+{
+    real a = beta * r < 1.0 ? beta * r : (real)1.0;
+    real b = r < beta ? r : (real)beta;
+    real m = a > b ? a : b;
+    return m > 0.0 ? m : (real)0.0;
+}
+
+/* Component k of cell c for the reconstruction: 0 eta = h + z, 1 h, 2 qx, 3 qy. */
+static real fv_val(const orc_t *o, const real *U, size_t c, int k)
+{
+    const size_t N = (size_t)o->nx * o->ny;
+    switch (k) {
+    case 0: return U[c] + o->z[c];
+    case 1: return U[c];
+    case 2: return U[3 * N + c];
+    default: return U[6 * N + c];
+    }
+}
+
+/* Limited MUSCL slope of component k of cell (i, j) along dir (Eq. 10, read
+ * with r = forward / backward difference so that the slope stays in Sweby's
+ * TVD region); zero without both neighbours, at a wet-dry front (the cell or a
+ * neighbour along dir at or below tol_dry, as the DG2 limiter's guard) and for
+ * FV1. */
+static real fv_slope(const orc_t *o, const real *U, int i, int j, int dir, int k)
+{
+    if (o->scheme != 1) return 0.0;
+    const int nx = o->nx, ny = o->ny;
+    if (dir == 1 ? (i == 0 || i == nx - 1) : (j == 0 || j == ny - 1)) return 0.0;
+    size_t c = (size_t)j * nx + i;
+    size_t lo = dir == 1 ? c - 1 : c - nx, hi = dir == 1 ? c + 1 : c + nx;
+    if (U[lo] <= o->tol_dry || U[c] <= o->tol_dry || U[hi] <= o->tol_dry) return 0.0;
+    real vc = fv_val(o, U, c, k);
+    real db = vc - fv_val(o, U, lo, k), df = fv_val(o, U, hi, k) - vc;
+    if (db == 0.0) return 0.0;
+    return sweby(df / db, 1.25) * db;
+}
+
+typedef struct { real eta, h, qx, qy; } st4;
+
+/* Limit of cell (i, j) at its face (EE, EW, EN, ES): average + / - half the
+ * slope (Eq. 9). */
+static st4 fv_limit(const orc_t *o, const real *U, int i, int j, int face)
+{
+    const int dir = (face == EE || face == EW) ? 1 : 2;
+    const real sg = (face == EE || face == EN) ? 0.5 : -0.5;
+    size_t c = (size_t)j * o->nx + i;
+    st4 r;
+    r.eta = fv_val(o, U, c, 0) + sg * fv_slope(o, U, i, j, dir, 0);
+    r.h = fv_val(o, U, c, 1) + sg * fv_slope(o, U, i, j, dir, 1);
+    r.qx = fv_val(o, U, c, 2) + sg * fv_slope(o, U, i, j, dir, 2);
+    r.qy = fv_val(o, U, c, 3) + sg * fv_slope(o, U, i, j, dir, 3);
+    return r;
+}
+
+/* The limit beyond face `face` of cell (i, j): the neighbour's limit, or the
+ * boundary ghost of the own limit over the same bed. */
+static st4 fv_outer(const orc_t *o, const real *U, int i, int j, int face, double t)
+{
+    int ni = i + (face == EE) - (face == EW), nj = j + (face == EN) - (face == ES);
+    int opp = face == EE ? EW : face == EW ? EE : face == EN ? ES : EN;
+    if (ni >= 0 && ni < o->nx && nj >= 0 && nj < o->ny) return fv_limit(o, U, ni, nj, opp);
+    st4 own = fv_limit(o, U, i, j, face);
+    double s = (face == EE || face == EW) ? (j + 0.5) * o->dy : (i + 0.5) * o->dx;
+    st3 g = ghost(o, face, s, mk(own.h, own.qx, own.qy), t);
+    st4 r;
+    r.eta = g.h + (own.eta - own.h);
+    r.h = g.h;
+    r.qx = g.qx;
+    r.qy = g.qy;
+    return r;
+}
+
+/* Revised states of a face from its lower (a) and upper (b) limits
+ * (Sec. 2.2.2): z+- = eta+- - h+-, z* = max(z-, z+), h*+- = max(0, eta+- - z*),
+ * q*+- = h*+- u+- with u by the tol_dry rule; returns z*. */
+static real fv_face(const orc_t *o, st4 a, st4 b, st3 *ra, st3 *rb)
+{
+    real za = a.eta - a.h, zb = b.eta - b.h;
+    real zs = za > zb ? za : zb;
+    real ha = a.eta - zs, hb = b.eta - zs;
+    if (ha < 0.0) ha = 0.0;
+    if (hb < 0.0) hb = 0.0;
+    real ua, va, ub, vb;
+    velocities(o, mk(a.h, a.qx, a.qy), &ua, &va);
+    velocities(o, mk(b.h, b.qx, b.qy), &ub, &vb);
+    *ra = mk(ha, ha * ua, ha * va);
+    *rb = mk(hb, hb * ub, hb * vb);
+    return zs;
+}
+
+/* Eq. 8 at every cell (bed term read with the factor 2 / dx of Eq. 4a, which
+ * balances the face fluxes at rest); returns the boundary + source rate. */
+static real fv_operator(const orc_t *o, const real *U, double t, real *Lout)
+{
+    const int nx = o->nx, ny = o->ny;
+    const size_t N = (size_t)nx * ny;
+    const real g = o->g, dx = o->dx, dy = o->dy;
+    const int csrc = source_cell(o);
+    const int raining = (o->rain != 0.0 && t >= o->rain_t0 && t < o->rain_t1);
+    real bsum = 0.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t c = (size_t)j * nx + i;
+            st3 aE, bE, aW, bW, aN, bN, aS, bS;
+            st4 own_e = fv_limit(o, U, i, j, EE), own_w = fv_limit(o, U, i, j, EW);
+            st4 own_n = fv_limit(o, U, i, j, EN), own_s = fv_limit(o, U, i, j, ES);
+            real zE = fv_face(o, own_e, fv_outer(o, U, i, j, EE, t), &aE, &bE);
+            real zW = fv_face(o, fv_outer(o, U, i, j, EW, t), own_w, &aW, &bW);
+            real zN = fv_face(o, own_n, fv_outer(o, U, i, j, EN, t), &aN, &bN);
+            real zS = fv_face(o, fv_outer(o, U, i, j, ES, t), own_s, &aS, &bS);
+            st3 FE = riemann_x(o, aE, bE), FW = riemann_x(o, aW, bW);
+            st3 GN = hll_y(o, aN, bN), GS = hll_y(o, aS, bS);
+            if (i == 0) bsum += FW.h * dy;
+            if (i == nx - 1) bsum -= FE.h * dy;
+            if (j == 0) bsum += GS.h * dx;
+            if (j == ny - 1) bsum -= GN.h * dx;
+            /* own-side bed limits, lowered where the own free surface is below
+             * z* (water held by a higher wall) */
+            real dE = own_e.eta - zE, dW = own_w.eta - zW, dN = own_n.eta - zN, dS = own_s.eta - zS;
+            zE = zE - (dE < 0.0 ? -dE : (real)0.0);
+            zW = zW - (dW < 0.0 ? -dW : (real)0.0);
+            zN = zN - (dN < 0.0 ? -dN : (real)0.0);
+            zS = zS - (dS < 0.0 ? -dS : (real)0.0);
+            real h0x = 0.5 * (aE.h + bW.h), z1x = 0.5 * (zE - zW);
+            real h0y = 0.5 * (aN.h + bS.h), z1y = 0.5 * (zN - zS);
+            real Lh = -(FE.h - FW.h) / dx - (GN.h - GS.h) / dy;
+            real Lx = -(FE.qx - FW.qx) / dx - (GN.qx - GS.qx) / dy - 2.0 * g * h0x * z1x / dx;
+            real Ly = -(FE.qy - FW.qy) / dx - (GN.qy - GS.qy) / dy - 2.0 * g * h0y * z1y / dy;
+            if (raining) Lh += o->rain;
+            if ((int)c == csrc) Lh += o->qp / (dx * dy);
+            for (int k = 0; k < 9; ++k) Lout[k * N + c] = 0.0;
+            Lout[c] = Lh;
+            Lout[3 * N + c] = Lx;
+            Lout[6 * N + c] = Ly;
+        }
+    if (raining) bsum += o->rain * dx * dy * (double)N;
+    if (csrc >= 0) bsum += o->qp;
+    return bsum;
+}
+
+/* After a stage: a dry cell keeps no discharge. */
+static void fv_dry(const orc_t *o, real *U)
+{
+    const size_t N = (size_t)o->nx * o->ny;
+    for (size_t c = 0; c < N; ++c)
+        if (U[c] <= o->tol_dry) { U[3 * N + c] = 0.0; U[6 * N + c] = 0.0; }
+}
+
+/* One step of the FV comparators: friction on the averages (the DG2
+ * procedure at the centre point, Sec. 2.2.3), then RK2 (MUSCL-FV2) or forward
+ * Euler (FV1) on Eq. 8. */
+static void fv_step(orc_t *o, double dt)
+{
+    const size_t N = (size_t)o->nx * o->ny;
+    real *Un = o->U, *U1 = o->U1, *L = o->L;
+    for (size_t c = 0; c < N; ++c) {
+        real qx = Un[3 * N + c], qy = Un[6 * N + c];
+        friction_point(o, o->nm[c], dt, Un[c], &qx, &qy);
+        Un[3 * N + c] = qx;
+        Un[6 * N + c] = qy;
+    }
+    real b1 = fv_operator(o, Un, o->t, L);
+    if (o->scheme == 2) {
+        for (size_t k = 0; k < 9 * N; ++k) Un[k] = Un[k] + dt * L[k];
+        fv_dry(o, Un);
+        o->last_bflux = b1;
+        o->ledger += dt * b1;
+        o->t += dt;
+        return;
+    }
+    for (size_t k = 0; k < 9 * N; ++k) U1[k] = Un[k] + dt * L[k];
+    fv_dry(o, U1);
+    real b2 = fv_operator(o, U1, o->t + dt, L);
+    for (size_t k = 0; k < 9 * N; ++k) Un[k] = 0.5 * (Un[k] + U1[k] + dt * L[k]);
+    fv_dry(o, Un);
+    o->last_bflux = 0.5 * (b1 + b2);
+    o->ledger += dt * 0.5 * (b1 + b2);
+    o->t += dt;
+}
+
 /* One RK2 step of size dt: friction, [limit], stage 1, [limit], stage 2. */
 void orc_step(orc_t *o, double dt)
 {
+    if (o->scheme != 0) {
+        fv_step(o, dt);
+        return;
+    }
     const size_t N = (size_t)o->nx * o->ny;
     real *Un = o->U, *U1 = o->U1, *L = o->L;
     apply_friction(o, Un, dt);
@@ -680,6 +872,11 @@ void orc_set_dem(orc_t *o, const double *z_corner, const double *manning, double
         for (size_t c = 0; c < N; ++c)
             if (o->U[c] <= 0.0) { o->U[c] = 0.0; o->U[N + c] = 0.0; o->U[2 * N + c] = 0.0; }
     }
+    if (o->scheme != 0) {
+        /* the FV schemes hold cell averages only (Eq. 3a) */
+        for (int k = 0; k < 9; ++k)
+            if (k % 3) memset(o->U + k * N, 0, N * sizeof(real));
+    }
     o->t = 0.0;
     o->ledger = orc_mass(o);
 }
@@ -773,6 +970,8 @@ void orc_hll(const orc_t *o, int dir, const double *l3, const double *r3, double
 double orc_minmod(double a, double b, double c) { return minmod3(a, b, c); }
 /* Riemann solver of the run: 0 HLL (default), 1 Roe. */
 void orc_set_flux(orc_t *o, int flux) { o->flux = flux; }
+/* Scheme of the run: 0 DG2 (default), 1 MUSCL-FV2, 2 FV1 (set before orc_set_dem). */
+void orc_set_scheme(orc_t *o, int scheme) { o->scheme = scheme; }
 
 /* Depth at (x, y) from the planar solution of the containing cell, clipped at 0. */
 double orc_gauge_h(const orc_t *o, double x, double y)
