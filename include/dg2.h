@@ -58,6 +58,10 @@ enum { DG2_NL = 0, DG2_LL = 1 };            /* DG2-NL: no limiting; DG2-LL: Eqs.
 enum { DG2_FP64 = 0, DG2_FP32 = 1 };
 enum { DG2_WALL = 0, DG2_OPEN = 1 };        /* edge types                            */
 enum { DG2_HLL = 0, DG2_ROE = 1 };          /* Riemann solvers                       */
+/* Spatial schemes: the slope-decoupled DG2 (Sec. 2.1) or the finite-volume
+ * comparators of Sec. 2.2 (MUSCL-FV2: Eqs. 8-10, RK2; FV1: first order,
+ * forward Euler) */
+enum { DG2_SCHEME_DG2 = 0, DG2_SCHEME_FV2 = 1, DG2_SCHEME_FV1 = 2 };
 enum { DG2_WEST = 0, DG2_EAST = 1, DG2_SOUTH = 2, DG2_NORTH = 3 };
 
 typedef struct dg2_params {
@@ -77,6 +81,11 @@ typedef struct dg2_params {
                            every tile */
     int flux;           /* Riemann solver: DG2_HLL (default) or DG2_ROE (Roe's solver
                            named in Sec. 2.1.2, Harten's entropy fix; DG2_FP64 only) */
+    int scheme;         /* DG2_SCHEME_DG2 (default), or DG2_SCHEME_FV2 / DG2_SCHEME_FV1
+                           (Sec. 2.2): cell averages only (the slope planes of the
+                           state are zeroed by dg2_set_dem and otherwise left as
+                           they are), Sweby's limiter with beta = 1.25 for FV2,
+                           friction on the averages; DG2_FP64 and DG2_NL only */
 } dg2_params;
 
 typedef struct dg2_ctx dg2_ctx;

@@ -17,6 +17,7 @@
 #include "../../include/dg2.h"
 #include "dg2_device.cuh"
 #include "dg2_fs32.cuh"
+#include "dg2_fv.cuh"
 #include "dg2_internal.h"
 
 using dg2::Dev;
@@ -256,6 +257,21 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   else
     dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
+  if (c->p.scheme != DG2_SCHEME_DG2) {
+    // the FV comparators: one block per tile of the lists, as the DG2 stages
+    if (c->p.scheme == DG2_SCHEME_FV2)
+      dg2::fv::fv_stage_kernel<true, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
+    else
+      dg2::fv::fv_stage_kernel<false, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
+    if (e) cudaEventRecord(e[2], c->st);
+    if (c->p.scheme == DG2_SCHEME_FV2)
+      dg2::fv::fv_stage_kernel<true, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
+    else
+      dg2::fv::fv1_commit_kernel<<<c->g_st2, c->sblock, 0, c->st>>>(d);
+    if (e) cudaEventRecord(e[3], c->st);
+    launch_finalize(c, 0);
+    return;
+  }
   if (c->fp32) {
     dg2::ens::launch_stage32x8(c->e1, ll, 1, c->g_st1, c->st);
   } else {
@@ -360,6 +376,7 @@ void dg2_default_params(dg2_params* p) {
   p->max_samples = 4096;
   p->skip_dry_tiles = 1;
   p->flux = DG2_HLL;
+  p->scheme = DG2_SCHEME_DG2;
 }
 
 const char* dg2_last_error(void) { return g_err.c_str(); }
@@ -388,6 +405,10 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   if (p.flux != DG2_HLL && p.flux != DG2_ROE) return fail(DG2_E_ARG, "flux must be HLL or ROE");
   if (p.flux == DG2_ROE && p.precision != DG2_FP64)
     return fail(DG2_E_ARG, "the Roe flux is built for DG2_FP64 only");
+  if (p.scheme != DG2_SCHEME_DG2 && p.scheme != DG2_SCHEME_FV2 && p.scheme != DG2_SCHEME_FV1)
+    return fail(DG2_E_ARG, "scheme must be DG2, FV2 or FV1");
+  if (p.scheme != DG2_SCHEME_DG2 && (p.precision != DG2_FP64 || p.variant != DG2_NL))
+    return fail(DG2_E_ARG, "the FV schemes are built for DG2_FP64 and DG2_NL only");
   for (int k = 0; k < 4; ++k)
     if (p.bc[k] != DG2_WALL && p.bc[k] != DG2_OPEN) return fail(DG2_E_ARG, "bad edge type");
   if ((long long)nx * ny > (1ll << 31)) return fail(DG2_E_ARG, "grid too large");
@@ -424,6 +445,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.T = (double*)(c->ws + L.off_T);
   d.Q = p.variant == DG2_LL ? (double*)(c->ws + L.off_Q) : nullptr;
   d.flux = p.flux;
+  d.scheme = p.scheme;
   d.Z = (const double*)(c->ws + L.off_Z);
   d.N = (const double*)(c->ws + L.off_N);
   d.bpart = (double*)(c->ws + L.off_bpart);
@@ -502,7 +524,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     c->lblock = dim3(dg2::LTX, dg2::LTY);
     c->lgrid = dim3((d.tiles.ntx + dg2::LTX - 1) / dg2::LTX, (d.tiles.nty + dg2::LTY - 1) / dg2::LTY);
     c->g_fric = gsz(o0);
-    const bool loop = f32 ? true : DG2_TILE_LOOP64;
+    const bool loop = f32 ? true : (p.scheme == DG2_SCHEME_DG2 && DG2_TILE_LOOP64);
     c->g_st1 = loop ? gsz(o1) : nt;
     c->g_st2 = loop ? gsz(o2) : nt;
   }

@@ -98,6 +98,7 @@ struct Dev {
   double g, cfl, tol, ds, dt_max;
   int bc[4];
   int flux;                  // 0 HLL, 1 Roe
+  int scheme;                // 0 DG2, 1 MUSCL-FV2, 2 FV1 (Sec. 2.2)
   // inflows
   int n_in;
   InflowDesc in[kMaxInflow];
@@ -532,6 +533,7 @@ static __global__ void init_kernel(Dev d, const double* __restrict__ zc, const d
     h1x = 0.5 * (fE - fW);
     h1y = 0.5 * (fN - fS);
     if (h0 <= 0.0) { h0 = 0.0; h1x = 0.0; h1y = 0.0; }
+    if (d.scheme != 0) { h1x = 0.0; h1y = 0.0; }  // the FV schemes hold averages only
   }
   double* S = d.S;
   S[H0 * P + c] = h0;
@@ -1029,6 +1031,7 @@ static __global__ void __launch_bounds__(kFinThreads) finalize_kernel(Dev d, int
       if (d.rain != 0.0 && t >= d.rain_t0 && t < d.rain_t1) src1 += d.rain * area;
       if (d.rain != 0.0 && t + dt >= d.rain_t0 && t + dt < d.rain_t1) src2 += d.rain * area;
       if (d.src_idx >= 0) { src1 += d.qp; src2 += d.qp; }
+      if (d.scheme == 2) src2 = src1;  // FV1: one forward-Euler stage at time t
       sc->ledger += dt * 0.5 * (btot + src1 + src2);
       double tn;
       bool at_sample = false;

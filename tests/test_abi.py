@@ -39,6 +39,7 @@ def test_host_only_calls_without_gpu():
     B.load()
     p = B.dg2_default_params()
     assert p.cfl == pytest.approx(0.3) and p.tol_dry == 1e-5 and p.ds_thresh == 10.0
+    assert p.flux == B.DG2_HLL and p.scheme == B.DG2_SCHEME_DG2
     n1 = B.dg2_workspace_bytes(128, 128, p)
     p.variant = B.DG2_LL
     n2 = B.dg2_workspace_bytes(128, 128, p)
