@@ -474,6 +474,57 @@ def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS):
             "grad_knots_norm": float(np.linalg.norm(gq))}
 
 
+SCHEME_WINDOW_S = 120.0   # simulated seconds each scheme runs in the cost comparison
+FV_CFL = 0.5              # the Courant bound of the FV schemes' positivity (Sec. 2.2.2)
+
+
+def scheme_cost_variant(B, torch, case, start, coarse_case, coarse_start,
+                        window=SCHEME_WINDOW_S):
+    """Run-time cost of the schemes over the same simulated window from the same
+    state (the GB300 counterpart of the paper's Table 3): DG2-NL, DG2-LL, MUSCL-FV2
+    and FV1 in FP64 at 2 m, and DG2-NL on the twice-coarser 4 m grid of the same
+    recipe.  Each run is one dg2_run_to (CUDA graphs, own Courant steps), timed
+    with CUDA events after 3 warm-up steps."""
+    runs = {}
+    plan = [("dg2_nl", case, start, {"variant": B.DG2_NL}),
+            ("dg2_ll", case, start, {"variant": B.DG2_LL}),
+            ("fv2", case, start, {"scheme": B.DG2_SCHEME_FV2, "cfl": FV_CFL}),
+            ("fv1", case, start, {"scheme": B.DG2_SCHEME_FV1, "cfl": FV_CFL}),
+            ("dg2_nl_4m", coarse_case, coarse_start, {"variant": B.DG2_NL})]
+    for name, cs, (st, t0), kw in plan:
+        s = B.solver_from_case(cs, **kw)
+        planes = st.copy()
+        if "scheme" in kw:
+            planes[[1, 2, 4, 5, 7, 8]] = 0.0      # the FV schemes hold averages only
+        s.set_state(planes, t0)
+        for _ in range(3):
+            s.step(-1.0)
+        t_a = s.time()[0]
+        n0, l0 = s.steps(), s.launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(s.stream)
+        s.run_to(t_a + window)
+        ev1.record(s.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        n = s.steps() - n0
+        runs[name] = {"ms": ms, "steps": n, "ms_per_step": ms / max(n, 1),
+                      "ms_per_simulated_s": ms / window, "cells": cs.nx * cs.ny,
+                      "dx_m": cs.dx, "cfl": kw.get("cfl", cs.cfl),
+                      "launches": s.launches() - l0,
+                      "t_reached": s.time()[0] - t_a}
+        s.close()
+        torch.cuda.empty_cache()
+    r = lambda a, b: runs[a]["ms"] / runs[b]["ms"]
+    return {"workload": f"floodplain from t = {start[1]:.0f} s, {window:.0f} s of simulated time, "
+                        "FP64 (DG2 at Cr 0.33, FV at Cr 0.5)",
+            "runs": runs,
+            "time_ratios": {"dg2_ll/dg2_nl": r("dg2_ll", "dg2_nl"), "fv2/dg2_nl": r("fv2", "dg2_nl"),
+                            "fv1/dg2_nl": r("fv1", "dg2_nl"),
+                            "fv2_2m/dg2_nl_4m": r("fv2", "dg2_nl_4m")}}
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
@@ -535,6 +586,14 @@ def main():
         adj = adjoint_variant(B, torch, inputs)
         torch.cuda.empty_cache()
 
+    schemes = None
+    if not only or "fp64_schemes" in only:
+        barrier(world)
+        coarse = workload(NX // 2, NY // 2, 2 * DX)
+        cst, ct, _ = spun_up(B, coarse, SPIN_T)
+        schemes = scheme_cost_variant(B, torch, cases["floodplain"], starts["floodplain"],
+                                      coarse, (cst, ct))
+
     ens = None
     if not only or "fp32_nl_ensemble" in only:
         barrier(world)
@@ -545,7 +604,8 @@ def main():
 
     if not results:
         if rank == 0:
-            extra = {k: v for k, v in (("fp32_nl_ensemble", ens), ("fp64_nl_adjoint", adj)) if v}
+            extra = {k: v for k, v in (("fp32_nl_ensemble", ens), ("fp64_nl_adjoint", adj),
+                                       ("fp64_schemes", schemes)) if v}
             print(json.dumps({"metric": METRIC, "variants": extra}))
         return
     head = "fp64_ll" if "fp64_ll" in results else next(iter(results))
@@ -572,6 +632,8 @@ def main():
             variants["fp32_nl_ensemble"] = ens
         if adj is not None:
             variants["fp64_nl_adjoint"] = adj
+        if schemes is not None:
+            variants["fp64_schemes"] = schemes
         line = {"metric": METRIC, "value": hd["value"], "unit": "cell-updates/s", "n_gpus": world,
                 "steps": hd["steps"], "warmup": warmup, "ms_per_step": hd["ms_max"] / hd["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

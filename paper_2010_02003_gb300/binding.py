@@ -499,8 +499,9 @@ class Solver:
 def solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, **kw) -> Solver:
     """Builds a Solver from an inputs.Case (DEM, water, roughness, inflows, sources, gauges)."""
     kw.setdefault("dt_max", case.dt_max)
+    kw.setdefault("cfl", case.cfl)
     s = Solver(case.nx, case.ny, case.dx, case.dy, variant=variant, precision=precision,
-               cfl=case.cfl, bc=case.bc, **kw)
+               bc=case.bc, **kw)
     s.set_dem(case.z_corner, case.manning, case.n_uniform, case.eta_corner)
     for f in case.inflows:
         s.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)
