@@ -13,6 +13,11 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   - spatial operator, HLL flux, RK2 step, mass: pinned (lake at rest, wall
     balance, closed-wall mass, Ritter/Stoker closed forms, order of accuracy,
     transposition / mirror symmetry).
+  - face revision of partially wet cells (``wetdry="positive"``, the default;
+    ``"paper"`` is Sec. 2.1.2 as printed): pinned by the lake at rest in a basin
+    whose bed rises 2 m across a cell, by bit-identity with the printed revision
+    on fully wet flow, and by near-positivity and wave speeds on the floodplain's
+    dry start (tests/test_oracle_wetdry.py).
   - friction: pinned by the exact solution of the friction ODE at the centre
     and at every Gauss point.
   - limiter: pinned by brute-force detector / minmod cases.
@@ -141,6 +146,7 @@ def _load():
         "orc_minmod": (D, [D, D, D]),
         "orc_set_flux": (None, [P, I]),
         "orc_set_scheme": (None, [P, I]),
+        "orc_set_wetdry": (None, [P, I]),
         "orc_gauge_h": (D, [P, D, D]),
         "orc_run_to": (ctypes.c_long, [P, D, D, I, dp, dp, dp, I, ip]),
     }
@@ -175,7 +181,7 @@ class Oracle:
 
     def __init__(self, nx, ny, dx, dy, *, g=9.80665, cfl=0.33, tol_dry=1e-5, ds_thresh=10.0,
                  dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL), flux="hll",
-                 scheme="dg2"):
+                 scheme="dg2", wetdry="positive"):
         self.lib = _load()
         self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
         self.g, self.cfl, self.tol_dry = g, cfl, tol_dry
@@ -190,6 +196,9 @@ class Oracle:
         if scheme not in ("dg2", "fv2", "fv1"):
             raise ValueError("scheme must be 'dg2', 'fv2' or 'fv1'")
         self.lib.orc_set_scheme(self.h, ("dg2", "fv2", "fv1").index(scheme))
+        if wetdry not in ("paper", "positive"):
+            raise ValueError("wetdry must be 'paper' or 'positive'")
+        self.lib.orc_set_wetdry(self.h, 1 if wetdry == "positive" else 0)
 
     def __del__(self):
         h = getattr(self, "h", None)

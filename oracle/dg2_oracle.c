@@ -68,6 +68,8 @@ typedef struct {
     int limiter;           /* 0: DG2-NL, 1: DG2-LL */
     int flux;              /* Riemann solver: 0 HLL, 1 Roe */
     int scheme;            /* 0 DG2, 1 MUSCL-FV2, 2 FV1 (Sec. 2.2 comparators) */
+    int wd;                /* DG2 face revision: 1 (default) positivity-consistent depths
+                              in partially wet cells, 0 Sec. 2.1.2 as printed */
     int bc[4];
     int n_in;
     inflow_t in[MAX_INFLOW];
@@ -318,6 +320,101 @@ static st3 outer_limit(const orc_t *o, const real *U, int i, int j, int face, do
 }
 
 /* ------------------------------------------------------------------ */
+/* Revised face states (Sec. 2.1.2), and the positivity-consistent      */
+/* variant for partially wet cells                                      */
+/* ------------------------------------------------------------------ */
+
+/* One side of a face: its planar limit, the depth the face may draw on, the
+ * side's own bed level and free surface there. */
+typedef struct { st3 lim; real hs, zo, eta; int pw; } frec;
+
+/* The four face records of cell (i, j).  A wet cell (h0 > tol_dry) whose planar
+ * depth is negative at a face is partially wet: its clipped face depths
+ * max(0, h_f) average to more than h0, so they are scaled to average h0, and
+ * each face gets the bed level under the planar free surface at that depth
+ * (z_f raised by the depth removed).  Every other cell keeps max(0, h_f) over
+ * the continuous bed. */
+static void cell_recs(const orc_t *o, const real *U, int i, int j, frec r[4])
+{
+    const size_t c = (size_t)j * o->nx + i;
+    const real h0 = U[c];
+    real sum = 0.0;
+    int neg = 0;
+    for (int f = 0; f < 4; ++f) {
+        r[f].lim = limit_at(o, U, i, j, f);
+        real hf = r[f].lim.h;
+        if (hf < 0.0) neg = 1;
+        sum += hf > 0.0 ? hf : (real)0.0;
+    }
+    const int pw = h0 > o->tol_dry && neg;
+    const real sc = pw ? h0 / (0.25 * sum) : (real)1.0;
+    for (int f = 0; f < 4; ++f) {
+        real hf = r[f].lim.h, zf = zlimit_at(o, i, j, f);
+        real hp = hf > 0.0 ? hf : (real)0.0;
+        r[f].pw = pw;
+        if (pw) {
+            r[f].hs = sc * hp;
+            r[f].eta = hf + zf;
+            r[f].zo = r[f].eta - r[f].hs;
+        } else {
+            r[f].hs = hp;
+            r[f].zo = zf;
+            r[f].eta = zf + hp;
+        }
+    }
+}
+
+/* Record of the far side of face f of cell (i, j): the neighbour's, or the
+ * boundary ghost of the own planar limit over the own face bed. */
+static frec outer_rec(const orc_t *o, const real *U, int i, int j, int f, double t)
+{
+    int ni = i + (f == EE) - (f == EW), nj = j + (f == EN) - (f == ES);
+    int opp = f == EE ? EW : f == EW ? EE : f == EN ? ES : EN;
+    frec r;
+    if (ni >= 0 && ni < o->nx && nj >= 0 && nj < o->ny) {
+        frec nr[4];
+        cell_recs(o, U, ni, nj, nr);
+        return nr[opp];
+    }
+    r.lim = outer_limit(o, U, i, j, f, t);
+    real zf = zlimit_at(o, i, j, f);
+    r.hs = r.lim.h > 0.0 ? r.lim.h : (real)0.0;
+    r.zo = zf;
+    r.eta = zf + r.hs;
+    r.pw = 0;
+    return r;
+}
+
+/* Revised states of the face between lower side a and upper side b, and the
+ * bed level each side's own bed term uses.  Neither side partially wet: the
+ * revision of Sec. 2.1.2 over the continuous bed.  Otherwise the free-surface
+ * revision of Sec. 2.2.2 on the sides' own bed levels: z* = max(za, zb),
+ * h* = max(0, eta - z*), q* = h* u, and each side's bed term takes z* lowered
+ * by the amount its free surface lies below it. */
+static void face_revise(const orc_t *o, frec a, frec b, st3 *ra, st3 *rb, real *za, real *zb)
+{
+    if (!a.pw && !b.pw) {
+        *ra = revise(o, a.lim);
+        *rb = revise(o, b.lim);
+        *za = a.zo - (a.lim.h < 0.0 ? -a.lim.h : (real)0.0);
+        *zb = b.zo - (b.lim.h < 0.0 ? -b.lim.h : (real)0.0);
+        return;
+    }
+    real zs = a.zo > b.zo ? a.zo : b.zo;
+    real ha = a.eta - zs, hb = b.eta - zs;
+    if (ha < 0.0) ha = 0.0;
+    if (hb < 0.0) hb = 0.0;
+    real ua, va, ub, vb;
+    velocities(o, a.lim, &ua, &va);
+    velocities(o, b.lim, &ub, &vb);
+    *ra = mk(ha, ha * ua, ha * va);
+    *rb = mk(hb, hb * ub, hb * vb);
+    real da = a.eta - zs, db = b.eta - zs;
+    *za = zs - (da < 0.0 ? -da : (real)0.0);
+    *zb = zs - (db < 0.0 ? -db : (real)0.0);
+}
+
+/* ------------------------------------------------------------------ */
 /* Spatial operators L0, L1x, L1y (Eqs. 4a-c with Eq. 5)               */
 /* ------------------------------------------------------------------ */
 
@@ -346,20 +443,38 @@ static real spatial_operator(const orc_t *o, const real *U, double t, real *Lout
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
-            /* own limits and their revision */
-            st3 E = limit_at(o, U, i, j, EE), W = limit_at(o, U, i, j, EW);
-            st3 Nn = limit_at(o, U, i, j, EN), S = limit_at(o, U, i, j, ES);
-            st3 Es = revise(o, E), Ws = revise(o, W), Ns = revise(o, Nn), Ss = revise(o, S);
-            /* topography limits, revised with the own depth limit at each face */
-            real zE = zlimit_at(o, i, j, EE) - (E.h < 0.0 ? -E.h : (real)0.0);
-            real zW = zlimit_at(o, i, j, EW) - (W.h < 0.0 ? -W.h : (real)0.0);
-            real zN = zlimit_at(o, i, j, EN) - (Nn.h < 0.0 ? -Nn.h : (real)0.0);
-            real zS = zlimit_at(o, i, j, ES) - (S.h < 0.0 ? -S.h : (real)0.0);
-            /* inter-elemental fluxes */
-            st3 FE = riemann_x(o, Es, revise(o, outer_limit(o, U, i, j, EE, t)));
-            st3 FW = riemann_x(o, revise(o, outer_limit(o, U, i, j, EW, t)), Ws);
-            st3 GN = hll_y(o, Ns, revise(o, outer_limit(o, U, i, j, EN, t)));
-            st3 GS = hll_y(o, revise(o, outer_limit(o, U, i, j, ES, t)), Ss);
+            st3 Es, Ws, Ns, Ss;
+            real zE, zW, zN, zS;
+            st3 FE, FW, GN, GS;
+            if (!o->wd) {
+                /* own limits and their revision */
+                st3 E = limit_at(o, U, i, j, EE), W = limit_at(o, U, i, j, EW);
+                st3 Nn = limit_at(o, U, i, j, EN), S = limit_at(o, U, i, j, ES);
+                Es = revise(o, E); Ws = revise(o, W); Ns = revise(o, Nn); Ss = revise(o, S);
+                /* topography limits, revised with the own depth limit at each face */
+                zE = zlimit_at(o, i, j, EE) - (E.h < 0.0 ? -E.h : (real)0.0);
+                zW = zlimit_at(o, i, j, EW) - (W.h < 0.0 ? -W.h : (real)0.0);
+                zN = zlimit_at(o, i, j, EN) - (Nn.h < 0.0 ? -Nn.h : (real)0.0);
+                zS = zlimit_at(o, i, j, ES) - (S.h < 0.0 ? -S.h : (real)0.0);
+                /* inter-elemental fluxes */
+                FE = riemann_x(o, Es, revise(o, outer_limit(o, U, i, j, EE, t)));
+                FW = riemann_x(o, revise(o, outer_limit(o, U, i, j, EW, t)), Ws);
+                GN = hll_y(o, Ns, revise(o, outer_limit(o, U, i, j, EN, t)));
+                GS = hll_y(o, revise(o, outer_limit(o, U, i, j, ES, t)), Ss);
+            } else {
+                frec r[4];
+                cell_recs(o, U, i, j, r);
+                st3 oE, oW, oN, oS;
+                real zx;
+                face_revise(o, r[EE], outer_rec(o, U, i, j, EE, t), &Es, &oE, &zE, &zx);
+                face_revise(o, outer_rec(o, U, i, j, EW, t), r[EW], &oW, &Ws, &zx, &zW);
+                face_revise(o, r[EN], outer_rec(o, U, i, j, EN, t), &Ns, &oN, &zN, &zx);
+                face_revise(o, outer_rec(o, U, i, j, ES, t), r[ES], &oS, &Ss, &zx, &zS);
+                FE = riemann_x(o, Es, oE);
+                FW = riemann_x(o, oW, Ws);
+                GN = hll_y(o, Ns, oN);
+                GS = hll_y(o, oS, Ss);
+            }
             if (i == 0) bsum += FW.h * dy;
             if (i == nx - 1) bsum -= FE.h * dy;
             if (j == 0) bsum += GS.h * dx;
@@ -835,6 +950,7 @@ orc_t *orc_create(int nx, int ny, double dx, double dy, double g, double cfl, do
     o->nx = nx; o->ny = ny; o->dx = dx; o->dy = dy;
     o->g = g; o->cfl = cfl; o->tol_dry = tol_dry; o->ds_thresh = ds_thresh; o->dt_max = dt_max;
     o->limiter = limiter;
+    o->wd = 1;
     for (int k = 0; k < 4; ++k) o->bc[k] = bc[k];
     o->z = (real *)calloc(3 * N, sizeof(real));
     o->nm = (real *)calloc(N, sizeof(real));
@@ -972,6 +1088,7 @@ double orc_minmod(double a, double b, double c) { return minmod3(a, b, c); }
 void orc_set_flux(orc_t *o, int flux) { o->flux = flux; }
 /* Scheme of the run: 0 DG2 (default), 1 MUSCL-FV2, 2 FV1 (set before orc_set_dem). */
 void orc_set_scheme(orc_t *o, int scheme) { o->scheme = scheme; }
+void orc_set_wetdry(orc_t *o, int wd) { o->wd = wd; }
 
 /* Depth at (x, y) from the planar solution of the containing cell, clipped at 0. */
 double orc_gauge_h(const orc_t *o, double x, double y)

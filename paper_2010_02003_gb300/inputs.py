@@ -184,6 +184,19 @@ def smooth_wave_1d(nx=100, ny=2, length=1.0, h0=1.0, amp=0.1, bed_amp=0.05, t_en
                 manning=None, n_uniform=0.0, t_end=t_end)
 
 
+def diamond_basin(n=40, dx=2.0, level=6.5, n_uniform=0.03):
+    """Basin z = |x - x0| + |y - y0| (x0 = y0 = n m, bed rising 2 m across a 2 m cell),
+    planar inside every cell, under a flat free surface at `level`: with an even
+    height + 0.5 the surface crosses cells above their centres, so those cells are
+    partially wet (0.5 m average, 1.5 m at the low faces, -0.5 m at the high faces)
+    and every cell above them lies wholly above the surface.  Walls all round."""
+    x = np.arange(n + 1) * dx
+    X, Y = np.meshgrid(x, x)
+    z = np.abs(X - n * dx / 2.0) + np.abs(Y - n * dx / 2.0)
+    return Case("diamond_basin", n, n, dx, dx, z, np.full_like(z, level), None, n_uniform,
+                (WALL, WALL, WALL, WALL), cfl=0.33, t_end=60.0)
+
+
 def random_terrain(nx, ny, dx=1.0, seed=7, relief=1.0, eta=0.6, dam=True):
     """Small fBm terrain with a still lake (and optionally a raised circular dam) for
     parity runs on ragged sizes: wet/dry fronts everywhere."""
