@@ -62,6 +62,13 @@ enum { DG2_HLL = 0, DG2_ROE = 1 };          /* Riemann solvers                  
  * comparators of Sec. 2.2 (MUSCL-FV2: Eqs. 8-10, RK2; FV1: first order,
  * forward Euler) */
 enum { DG2_SCHEME_DG2 = 0, DG2_SCHEME_FV2 = 1, DG2_SCHEME_FV1 = 2 };
+/* DG2 face revision of partially wet cells (wet cells whose planar depth is
+ * negative at a face): DG2_WD_POSITIVE (default) scales such a cell's clipped
+ * face depths to average h0 and revises its faces on the free surface
+ * (Sec. 2.2.2) so that averages stay near non-negative and still water stays
+ * still; DG2_WD_PRINTED is Sec. 2.1.2 as printed (h* = max(0, h)).  Fully wet
+ * cells take the printed revision under both. */
+enum { DG2_WD_POSITIVE = 0, DG2_WD_PRINTED = 1 };
 enum { DG2_WEST = 0, DG2_EAST = 1, DG2_SOUTH = 2, DG2_NORTH = 3 };
 
 typedef struct dg2_params {
@@ -86,6 +93,7 @@ typedef struct dg2_params {
                            state are zeroed by dg2_set_dem and otherwise left as
                            they are), Sweby's limiter with beta = 1.25 for FV2,
                            friction on the averages; DG2_FP64 and DG2_NL only */
+    int wetdry;         /* DG2_WD_POSITIVE (default) or DG2_WD_PRINTED; see above */
 } dg2_params;
 
 typedef struct dg2_ctx dg2_ctx;

@@ -24,6 +24,7 @@ DG2_FP64, DG2_FP32 = 0, 1
 DG2_WALL, DG2_OPEN = 0, 1
 DG2_HLL, DG2_ROE = 0, 1
 DG2_SCHEME_DG2, DG2_SCHEME_FV2, DG2_SCHEME_FV1 = 0, 1, 2
+DG2_WD_POSITIVE, DG2_WD_PRINTED = 0, 1
 DG2_WEST, DG2_EAST, DG2_SOUTH, DG2_NORTH = 0, 1, 2, 3
 
 # Every symbol declared in include/dg2.h.
@@ -49,7 +50,7 @@ class Dg2Params(ctypes.Structure):
                 ("variant", ctypes.c_int), ("precision", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("max_gauges", ctypes.c_int), ("max_samples", ctypes.c_int),
                 ("skip_dry_tiles", ctypes.c_int), ("flux", ctypes.c_int),
-                ("scheme", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("wetdry", ctypes.c_int)]
 
 
 class Dg2Error(RuntimeError):
@@ -398,8 +399,8 @@ class Solver:
     def __init__(self, nx, ny, dx, dy=None, *, variant=DG2_NL, precision=DG2_FP64, cfl=0.3,
                  tol_dry=1e-5, ds_thresh=10.0, dt_max=1.0, g=9.80665,
                  bc: Sequence[int] = (DG2_WALL,) * 4, max_gauges=64, max_samples=4096,
-                 skip_dry_tiles=True, flux=DG2_HLL, scheme=DG2_SCHEME_DG2, stream=None,
-                 device=None):
+                 skip_dry_tiles=True, flux=DG2_HLL, scheme=DG2_SCHEME_DG2,
+                 wetdry=DG2_WD_POSITIVE, stream=None, device=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the DG2 solver needs a CUDA device")
@@ -415,6 +416,7 @@ class Solver:
         p.skip_dry_tiles = int(bool(skip_dry_tiles))
         p.flux = int(flux)
         p.scheme = int(scheme)
+        p.wetdry = int(wetdry)
         self.params = p
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         nbytes = dg2_workspace_bytes(self.nx, self.ny, p)

@@ -275,15 +275,15 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   if (c->fp32) {
     dg2::ens::launch_stage32x8(c->e1, ll, 1, c->g_st1, c->st);
   } else {
-    if (ll) dg2::stage_kernel<true, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
-    else dg2::stage_kernel<false, 1><<<c->g_st1, c->sblock, 0, c->st>>>(d);
+    if (ll) dg2::stage_kernel<true, 1><<<c->g_st1, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
+    else dg2::stage_kernel<false, 1><<<c->g_st1, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
   }
   if (e) cudaEventRecord(e[2], c->st);
   if (c->fp32) {
     dg2::ens::launch_stage32x8(c->e1, ll, 2, c->g_st2, c->st);
   } else {
-    if (ll) dg2::stage_kernel<true, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
-    else dg2::stage_kernel<false, 2><<<c->g_st2, c->sblock, 0, c->st>>>(d);
+    if (ll) dg2::stage_kernel<true, 2><<<c->g_st2, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
+    else dg2::stage_kernel<false, 2><<<c->g_st2, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
   }
   if (e) cudaEventRecord(e[3], c->st);
   launch_finalize(c, 0);
@@ -377,6 +377,7 @@ void dg2_default_params(dg2_params* p) {
   p->skip_dry_tiles = 1;
   p->flux = DG2_HLL;
   p->scheme = DG2_SCHEME_DG2;
+  p->wetdry = DG2_WD_POSITIVE;
 }
 
 const char* dg2_last_error(void) { return g_err.c_str(); }
@@ -405,6 +406,8 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   if (p.flux != DG2_HLL && p.flux != DG2_ROE) return fail(DG2_E_ARG, "flux must be HLL or ROE");
   if (p.flux == DG2_ROE && p.precision != DG2_FP64)
     return fail(DG2_E_ARG, "the Roe flux is built for DG2_FP64 only");
+  if (p.wetdry != DG2_WD_POSITIVE && p.wetdry != DG2_WD_PRINTED)
+    return fail(DG2_E_ARG, "wetdry must be DG2_WD_POSITIVE or DG2_WD_PRINTED");
   if (p.scheme != DG2_SCHEME_DG2 && p.scheme != DG2_SCHEME_FV2 && p.scheme != DG2_SCHEME_FV1)
     return fail(DG2_E_ARG, "scheme must be DG2, FV2 or FV1");
   if (p.scheme != DG2_SCHEME_DG2 && (p.precision != DG2_FP64 || p.variant != DG2_NL))
@@ -446,6 +449,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.Q = p.variant == DG2_LL ? (double*)(c->ws + L.off_Q) : nullptr;
   d.flux = p.flux;
   d.scheme = p.scheme;
+  d.wd = p.wetdry == DG2_WD_POSITIVE ? 1 : 0;
   d.Z = (const double*)(c->ws + L.off_Z);
   d.N = (const double*)(c->ws + L.off_N);
   d.bpart = (double*)(c->ws + L.off_bpart);
@@ -506,16 +510,29 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const bool ll = p.variant == DG2_LL, f32 = p.precision == DG2_FP32;
     int o0 = 1, o1 = 1, o2 = 1;
+    // the FP64 stage tile's shared memory is above the 48 KB static limit
+    cudaFuncSetAttribute(dg2::stage_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(dg2::StageSmem));
+    cudaFuncSetAttribute(dg2::stage_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(dg2::StageSmem));
+    cudaFuncSetAttribute(dg2::stage_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(dg2::StageSmem));
+    cudaFuncSetAttribute(dg2::stage_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(dg2::StageSmem));
     if (f32) {
       dg2::ens::occupancy32x8(ll, &o0, &o1, &o2);
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::friction_kernel, 256, 0);
       if (ll) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::stage_kernel<true, 1>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::stage_kernel<true, 2>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::stage_kernel<true, 1>, 256,
+                                                      sizeof(dg2::StageSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::stage_kernel<true, 2>, 256,
+                                                      sizeof(dg2::StageSmem));
       } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::stage_kernel<false, 1>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::stage_kernel<false, 2>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, dg2::stage_kernel<false, 1>, 256,
+                                                      sizeof(dg2::StageSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, dg2::stage_kernel<false, 2>, 256,
+                                                      sizeof(dg2::StageSmem));
       }
     }
     cudaGetLastError();

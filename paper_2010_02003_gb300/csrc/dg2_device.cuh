@@ -99,6 +99,7 @@ struct Dev {
   int bc[4];
   int flux;                  // 0 HLL, 1 Roe
   int scheme;                // 0 DG2, 1 MUSCL-FV2, 2 FV1 (Sec. 2.2)
+  int wd;                    // 1: positivity-consistent revision of partially wet cells
   // inflows
   int n_in;
   InflowDesc in[kMaxInflow];
@@ -607,22 +608,149 @@ __device__ __forceinline__ void load9(const double* __restrict__ U, long long P,
   for (int k = 0; k < 9; ++k) m[k] = U[k * P + c];
 }
 
+// One side of a face (Sec. 2.1.2 and its positivity-consistent reading): the
+// planar limit's depth h and velocities (u, v by the tol rule), the depth the
+// face may draw on (hs), the continuous face bed zf, and whether the side's
+// cell is partially wet (a wet cell whose planar depth is negative at a face).
+struct Rec {
+  double h, u, v, hs, zf;
+  int pw;
+};
+
+// A revised face: its flux and the lower (west / south) side's revised depth
+// and bed level for that side's own Eq. 5 and bed term.
+struct FaceR {
+  double fh, fx, fy, ha, za;
+};
+
 struct StageSmem {
-  Lim e[TY][TX];     // east limit of each cell (left state of the face to its east)
-  Lim n[TY][TX];     // north limit of each cell
-  Lim hw[TY];        // limit west of the tile's first column (neighbour or ghost)
-  Lim he[TY];        // limit east of the tile's last column
-  Lim hs[TX];        // limit south of the tile's first row
-  Lim hn[TX];        // limit north of the tile's last row
-  F3 fx[TY][TX + 1]; // x-face fluxes; fx[ty][tx] is the west face of column tx
-  F3 fy[TY + 1][TX]; // y-face fluxes; fy[ty][tx] is the south face of row ty
+  Rec e[TY][TX];     // east record of each cell (lower side of the face to its east)
+  Rec n[TY][TX];     // north record of each cell
+  Rec hw[TY];        // record west of the tile's first column (neighbour or ghost)
+  Rec he[TY];        // record east of the tile's last column
+  Rec hs[TX];        // record south of the tile's first row
+  Rec hn[TX];        // record north of the tile's last row
+  FaceR fx[TY][TX + 1];  // x faces; fx[ty][tx] is the west face of column tx
+  FaceR fy[TY + 1][TX];  // y faces; fy[ty][tx] is the south face of row ty
   double red[32];
 };
 
-// One RK stage on the 32 x 8 tile (bx, by): revised limits, one HLL flux per
-// face, Eqs. 4-5, the stage update and the wet-dry treatment.  Accumulates the
-// boundary inflow rate, the Courant rate and the non-finite / non-quiescent
-// flags of the thread's cell into the caller's variables.
+// Record of a side whose planar limit is (h, qx, qy) over face bed zf; `sc` is
+// the depth scale of a partially wet cell (pw), 1 otherwise.
+__device__ __forceinline__ Rec make_rec(double h, double qx, double qy, double zf, bool pw,
+                                        double sc, double tol) {
+  Rec r;
+  r.h = h;
+  r.u = 0.0;
+  r.v = 0.0;
+  if (h > tol) {
+    r.u = qx / h;
+    r.v = qy / h;
+  }
+  const double hp = h > 0.0 ? h : 0.0;
+  r.hs = pw ? sc * hp : hp;
+  r.zf = zf;
+  r.pw = pw ? 1 : 0;
+  return r;
+}
+
+// Partially wet test and depth scale of a cell from its four planar depth
+// limits (W, E, S, N); `positive` = 0 keeps the printed revision (never pw).
+__device__ __forceinline__ bool pw_scale(double h0, double hW, double hE, double hS, double hN,
+                                         double tol, int positive, double& sc) {
+  sc = 1.0;
+  if (!positive || !(h0 > tol)) return false;
+  if (!(hW < 0.0 || hE < 0.0 || hS < 0.0 || hN < 0.0)) return false;
+  double sum = 0.0;
+  sum += hW > 0.0 ? hW : 0.0;
+  sum += hE > 0.0 ? hE : 0.0;
+  sum += hS > 0.0 ? hS : 0.0;
+  sum += hN > 0.0 ? hN : 0.0;
+  sc = h0 / (0.25 * sum);
+  return true;
+}
+
+// Revision of the face between lower side a and upper side b and its flux
+// (normal y if ydir).  Neither side partially wet: h* = max(0, h) over the
+// continuous bed, each side's bed term on zf - max(0, -h).  Otherwise the
+// free-surface revision of Sec. 2.2.2 on the sides' own bed levels (zf raised
+// by the depth a partially wet side does not offer): z* = max(za, zb),
+// h* = max(0, eta - z*), q* = h* u, each side's bed term on z* lowered by the
+// amount its free surface lies below it.
+__device__ __forceinline__ F3 revise_face(const Rec& a, const Rec& b, bool ydir, double g, double tol,
+                                          int flux, double& ha, double& za, double& hb, double& zb) {
+  Lim ra, rb;
+  if (!a.pw && !b.pw) {
+    ha = a.hs;
+    hb = b.hs;
+    za = a.zf - (a.h < 0.0 ? -a.h : 0.0);
+    zb = b.zf - (b.h < 0.0 ? -b.h : 0.0);
+    ra.u = a.u; ra.v = a.v;
+    rb.u = b.u; rb.v = b.v;
+  } else {
+    double ea, oa, eb, ob;  // free surface and own bed level of each side
+    if (a.pw) { ea = a.h + a.zf; oa = ea - a.hs; } else { oa = a.zf; ea = a.zf + a.hs; }
+    if (b.pw) { eb = b.h + b.zf; ob = eb - b.hs; } else { ob = b.zf; eb = b.zf + b.hs; }
+    const double zs = oa > ob ? oa : ob;
+    const double da = ea - zs, db = eb - zs;
+    ha = da > 0.0 ? da : 0.0;
+    hb = db > 0.0 ? db : 0.0;
+    za = zs - (da < 0.0 ? -da : 0.0);
+    zb = zs - (db < 0.0 ? -db : 0.0);
+    ra.u = ha > tol ? a.u : 0.0; ra.v = ha > tol ? a.v : 0.0;
+    rb.u = hb > tol ? b.u : 0.0; rb.v = hb > tol ? b.v : 0.0;
+  }
+  ra.h = ha; ra.qx = ha * a.u; ra.qy = ha * a.v;
+  rb.h = hb; rb.qx = hb * b.u; rb.qy = hb * b.v;
+  return ydir ? flux_y(ra, rb, g, tol, flux) : flux_x(ra, rb, g, tol, flux);
+}
+
+// Planar depth slope of cell (i, j) along dir, limited (Eqs. 6-7 on eta) when
+// LL: the h part of limited_slopes.
+template <bool LL>
+__device__ __forceinline__ double h_slope(const Dev& d, const double* __restrict__ U, int i, int j,
+                                          int dir) {
+  double sh, sx, sy;
+  if (LL) {
+    limited_slopes(d, U, i, j, dir, sh, sx, sy);
+    return sh;
+  }
+  return U[dir * d.plane + (long long)j * d.pitch + i];
+}
+
+// Record, at the face it shares with a cell of the tile, of the neighbour
+// (ni, nj) on side `side` of that face (0: the neighbour is west / south, its
+// east / north limit; 1: east / north, its west / south limit), along dir.
+template <bool LL>
+__device__ __forceinline__ Rec neighbour_rec(const Dev& d, const double* __restrict__ In, int ni, int nj,
+                                             int dir, int side) {
+  const long long P = d.plane, c = (long long)nj * d.pitch + ni;
+  double s1h, s1x, s1y;
+  if (LL) limited_slopes(d, In, ni, nj, dir, s1h, s1x, s1y);
+  else { s1h = In[dir * P + c]; s1x = In[(3 + dir) * P + c]; s1y = In[(6 + dir) * P + c]; }
+  const double h0 = In[H0 * P + c];
+  const double o1 = h_slope<LL>(d, In, ni, nj, 3 - dir);   // the other direction's slope
+  const double hx1 = dir == 1 ? s1h : o1, hy1 = dir == 1 ? o1 : s1h;
+  double sc;
+  const bool pw = pw_scale(h0, h0 - hx1, h0 + hx1, h0 - hy1, h0 + hy1, d.tol, d.wd, sc);
+  const double sg = side == 0 ? 1.0 : -1.0;
+  const double zf = d.Z[c] + sg * d.Z[dir * P + c];
+  return make_rec(h0 + sg * s1h, In[QX0 * P + c] + sg * s1x, In[QY0 * P + c] + sg * s1y, zf, pw, sc,
+                  d.tol);
+}
+
+// Ghost record beyond a domain edge, from the own planar limit (h, qx, qy) at
+// that edge over the own face bed zf.
+__device__ __forceinline__ Rec ghost_rec(const Dev& d, int edge, double s, double t, double h,
+                                         double qx, double qy, double zf) {
+  ghost(d, edge, s, t, h, qx, qy);
+  return make_rec(h, qx, qy, zf, false, 1.0, d.tol);
+}
+
+// One RK stage on the 32 x 8 tile (bx, by): face records, one revision and
+// one flux per face, Eqs. 4-5, the stage update and the wet-dry treatment.
+// Accumulates the boundary inflow rate, the Courant rate and the non-finite /
+// non-quiescent flags of the thread's cell into the caller's variables.
 template <bool LL, int STAGE>
 __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, int by,
                                            double& brate, double& lam, bool& bad, bool& nonq) {
@@ -640,9 +768,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
-  Lim Es, Ws, Ns, Ss;
-  double eh = 0, eqx = 0, eqy = 0, nh = 0, nqx = 0, nqy = 0;  // own unrevised E / N limits
-  double zb1x = 0.0, zb1y = 0.0;
+  Rec rE, rW, rN, rS;  // own records
   if (act) {
     load9(In, P, c, m);
     if (LL) {
@@ -652,111 +778,81 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     z0 = d.Z[c];
     z1x = d.Z[P + c];
     z1y = d.Z[2 * P + c];
-    eh = m[H0] + m[H1X]; eqx = m[QX0] + m[QX1X]; eqy = m[QY0] + m[QY1X];
-    const double wh = m[H0] - m[H1X], wqx = m[QX0] - m[QX1X], wqy = m[QY0] - m[QY1X];
-    nh = m[H0] + m[H1Y]; nqx = m[QX0] + m[QX1Y]; nqy = m[QY0] + m[QY1Y];
-    const double shh = m[H0] - m[H1Y], sqx = m[QX0] - m[QX1Y], sqy = m[QY0] - m[QY1Y];
-    Es = revise(eh, eqx, eqy, tol);
-    Ws = revise(wh, wqx, wqy, tol);
-    Ns = revise(nh, nqx, nqy, tol);
-    Ss = revise(shh, sqx, sqy, tol);
-    // topography limits revised with the own depth limit at each face
-    const double zE = (z0 + z1x) - (eh < 0.0 ? -eh : 0.0);
-    const double zW = (z0 - z1x) - (wh < 0.0 ? -wh : 0.0);
-    const double zN = (z0 + z1y) - (nh < 0.0 ? -nh : 0.0);
-    const double zS = (z0 - z1y) - (shh < 0.0 ? -shh : 0.0);
-    zb1x = 0.5 * (zE - zW);
-    zb1y = 0.5 * (zN - zS);
-    sm.e[ty][tx] = Es;
-    sm.n[ty][tx] = Ns;
-
-    // west neighbour's east limit, or the west-edge ghost
-    if (tx == 0) {
-      double h, qx, qy;
-      if (i == 0) {
-        h = wh; qx = wqx; qy = wqy;
-        ghost(d, 0, (j + 0.5) * d.dy, ts, h, qx, qy);
-      } else {
-        const long long cw = c - 1;
-        double s1h = In[H1X * P + cw], s1x = In[QX1X * P + cw], s1y = In[QY1X * P + cw];
-        if (LL) limited_slopes(d, In, i - 1, j, 1, s1h, s1x, s1y);
-        h = In[H0 * P + cw] + s1h; qx = In[QX0 * P + cw] + s1x; qy = In[QY0 * P + cw] + s1y;
-      }
-      sm.hw[ty] = revise(h, qx, qy, tol);
-    }
-    if (east_edge) {
-      double h, qx, qy;
-      if (i == d.nx - 1) {
-        h = eh; qx = eqx; qy = eqy;
-        ghost(d, 1, (j + 0.5) * d.dy, ts, h, qx, qy);
-      } else {
-        const long long ce = c + 1;
-        double s1h = In[H1X * P + ce], s1x = In[QX1X * P + ce], s1y = In[QY1X * P + ce];
-        if (LL) limited_slopes(d, In, i + 1, j, 1, s1h, s1x, s1y);
-        h = In[H0 * P + ce] - s1h; qx = In[QX0 * P + ce] - s1x; qy = In[QY0 * P + ce] - s1y;
-      }
-      sm.he[ty] = revise(h, qx, qy, tol);
-    }
-    if (ty == 0) {
-      double h, qx, qy;
-      if (j == 0) {
-        h = shh; qx = sqx; qy = sqy;
-        ghost(d, 2, (i + 0.5) * d.dx, ts, h, qx, qy);
-      } else {
-        const long long cs = c - d.pitch;
-        double s1h = In[H1Y * P + cs], s1x = In[QX1Y * P + cs], s1y = In[QY1Y * P + cs];
-        if (LL) limited_slopes(d, In, i, j - 1, 2, s1h, s1x, s1y);
-        h = In[H0 * P + cs] + s1h; qx = In[QX0 * P + cs] + s1x; qy = In[QY0 * P + cs] + s1y;
-      }
-      sm.hs[tx] = revise(h, qx, qy, tol);
-    }
-    if (north_edge) {
-      double h, qx, qy;
-      if (j == d.ny - 1) {
-        h = nh; qx = nqx; qy = nqy;
-        ghost(d, 3, (i + 0.5) * d.dx, ts, h, qx, qy);
-      } else {
-        const long long cn = c + d.pitch;
-        double s1h = In[H1Y * P + cn], s1x = In[QX1Y * P + cn], s1y = In[QY1Y * P + cn];
-        if (LL) limited_slopes(d, In, i, j + 1, 2, s1h, s1x, s1y);
-        h = In[H0 * P + cn] - s1h; qx = In[QX0 * P + cn] - s1x; qy = In[QY0 * P + cn] - s1y;
-      }
-      sm.hn[tx] = revise(h, qx, qy, tol);
-    }
+    const double eh = m[H0] + m[H1X], wh = m[H0] - m[H1X];
+    const double nh = m[H0] + m[H1Y], shh = m[H0] - m[H1Y];
+    double scl;
+    const bool pw = pw_scale(m[H0], wh, eh, shh, nh, tol, d.wd, scl);
+    rE = make_rec(eh, m[QX0] + m[QX1X], m[QY0] + m[QY1X], z0 + z1x, pw, scl, tol);
+    rW = make_rec(wh, m[QX0] - m[QX1X], m[QY0] - m[QY1X], z0 - z1x, pw, scl, tol);
+    rN = make_rec(nh, m[QX0] + m[QX1Y], m[QY0] + m[QY1Y], z0 + z1y, pw, scl, tol);
+    rS = make_rec(shh, m[QX0] - m[QX1Y], m[QY0] - m[QY1Y], z0 - z1y, pw, scl, tol);
+    sm.e[ty][tx] = rE;
+    sm.n[ty][tx] = rN;
+    // the records beyond the tile: a neighbour's, or the edge ghost
+    if (tx == 0)
+      sm.hw[ty] = i == 0 ? ghost_rec(d, 0, (j + 0.5) * d.dy, ts, wh, m[QX0] - m[QX1X],
+                                     m[QY0] - m[QY1X], z0 - z1x)
+                         : neighbour_rec<LL>(d, In, i - 1, j, 1, 0);
+    if (east_edge)
+      sm.he[ty] = i == d.nx - 1 ? ghost_rec(d, 1, (j + 0.5) * d.dy, ts, eh, m[QX0] + m[QX1X],
+                                            m[QY0] + m[QY1X], z0 + z1x)
+                                : neighbour_rec<LL>(d, In, i + 1, j, 1, 1);
+    if (ty == 0)
+      sm.hs[tx] = j == 0 ? ghost_rec(d, 2, (i + 0.5) * d.dx, ts, shh, m[QX0] - m[QX1Y],
+                                     m[QY0] - m[QY1Y], z0 - z1y)
+                         : neighbour_rec<LL>(d, In, i, j - 1, 2, 0);
+    if (north_edge)
+      sm.hn[tx] = j == d.ny - 1 ? ghost_rec(d, 3, (i + 0.5) * d.dx, ts, nh, m[QX0] + m[QX1Y],
+                                            m[QY0] + m[QY1Y], z0 + z1y)
+                                : neighbour_rec<LL>(d, In, i, j + 1, 2, 1);
   }
   __syncthreads();
 
-  // one HLL flux per face of the tile
+  // one revision and one flux per face; the own (upper) side of the west and
+  // south faces stays in registers, the lower side goes to shared memory
+  double hWo = 0, zWo = 0, hSo = 0, zSo = 0, hEo = 0, zEo = 0, hNo = 0, zNo = 0;
   if (act) {
-    const Lim& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
-    const F3 fw = flux_x(Lw, Ws, g, tol, d.flux);
-    sm.fx[ty][tx] = fw;
+    double ha, za;
+    const Rec& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
+    const F3 fw = revise_face(Lw, rW, false, g, tol, d.flux, ha, za, hWo, zWo);
+    sm.fx[ty][tx] = FaceR{fw.h, fw.x, fw.y, ha, za};
     if (i == 0) brate += fw.h * d.dy;
     if (east_edge) {
-      const F3 fe = flux_x(Es, sm.he[ty], g, tol, d.flux);
-      sm.fx[ty][tx + 1] = fe;
+      double hb, zb;
+      const F3 fe = revise_face(rE, sm.he[ty], false, g, tol, d.flux, hEo, zEo, hb, zb);
+      sm.fx[ty][tx + 1] = FaceR{fe.h, fe.x, fe.y, hEo, zEo};
       if (i == d.nx - 1) brate -= fe.h * d.dy;
     }
-    const Lim& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
-    const F3 fs = flux_y(Ls, Ss, g, tol, d.flux);
-    sm.fy[ty][tx] = fs;
+    const Rec& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
+    const F3 fs = revise_face(Ls, rS, true, g, tol, d.flux, ha, za, hSo, zSo);
+    sm.fy[ty][tx] = FaceR{fs.h, fs.x, fs.y, ha, za};
     if (j == 0) brate += fs.h * d.dx;
     if (north_edge) {
-      const F3 fn = flux_y(Ns, sm.hn[tx], g, tol, d.flux);
-      sm.fy[ty + 1][tx] = fn;
+      double hb, zb;
+      const F3 fn = revise_face(rN, sm.hn[tx], true, g, tol, d.flux, hNo, zNo, hb, zb);
+      sm.fy[ty + 1][tx] = FaceR{fn.h, fn.x, fn.y, hNo, zNo};
       if (j == d.ny - 1) brate -= fn.h * d.dx;
     }
   }
   __syncthreads();
 
   if (act) {
-    const F3 FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
-    const F3 GS = sm.fy[ty][tx], GN = sm.fy[ty + 1][tx];
+    const FaceR FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
+    const FaceR GS = sm.fy[ty][tx], GN = sm.fy[ty + 1][tx];
+    // own side of the east / north faces: revised by the neighbour's thread
+    if (!east_edge) { hEo = FE.ha; zEo = FE.za; }
+    if (!north_edge) { hNo = GN.ha; zNo = GN.za; }
+    // own revised states (Eq. 5 operands): q* = h* u
+    const double Esh = hEo, Esx = hEo * rE.u, Esy = hEo * rE.v;
+    const double Wsh = hWo, Wsx = hWo * rW.u, Wsy = hWo * rW.v;
+    const double Nsh = hNo, Nsx = hNo * rN.u, Nsy = hNo * rN.v;
+    const double Ssh = hSo, Ssx = hSo * rS.u, Ssy = hSo * rS.v;
+    const double zb1x = 0.5 * (zEo - zWo), zb1y = 0.5 * (zNo - zSo);
     // dummy modes (Eq. 5; the second line read as the 0y mode)
-    const double h0x = 0.5 * (Es.h + Ws.h), x0x = 0.5 * (Es.qx + Ws.qx), y0x = 0.5 * (Es.qy + Ws.qy);
-    const double h1x_ = 0.5 * (Es.h - Ws.h), x1x = 0.5 * (Es.qx - Ws.qx), y1x = 0.5 * (Es.qy - Ws.qy);
-    const double h0y = 0.5 * (Ns.h + Ss.h), x0y = 0.5 * (Ns.qx + Ss.qx), y0y = 0.5 * (Ns.qy + Ss.qy);
-    const double h1y_ = 0.5 * (Ns.h - Ss.h), x1y = 0.5 * (Ns.qx - Ss.qx), y1y = 0.5 * (Ns.qy - Ss.qy);
+    const double h0x = 0.5 * (Esh + Wsh), x0x = 0.5 * (Esx + Wsx), y0x = 0.5 * (Esy + Wsy);
+    const double h1x_ = 0.5 * (Esh - Wsh), x1x = 0.5 * (Esx - Wsx), y1x = 0.5 * (Esy - Wsy);
+    const double h0y = 0.5 * (Nsh + Ssh), x0y = 0.5 * (Nsx + Ssx), y0y = 0.5 * (Nsy + Ssy);
+    const double h1y_ = 0.5 * (Nsh - Ssh), x1y = 0.5 * (Nsx - Ssx), y1y = 0.5 * (Nsy - Ssy);
     const double r3 = 1.0 / 1.7320508075688772;
     const F3 Fp = phys_flux(h0x + h1x_ * r3, x0x + x1x * r3, y0x + y1x * r3, g, tol, false);
     const F3 Fm = phys_flux(h0x - h1x_ * r3, x0x - x1x * r3, y0x - y1x * r3, g, tol, false);
@@ -765,20 +861,20 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     const double idx = d.inv_dx, idy = d.inv_dy;
     // Eq. 4a
     double L[9];
-    L[H0] = -(FE.h - FW.h) * idx - (GN.h - GS.h) * idy;
-    L[QX0] = -(FE.x - FW.x) * idx - (GN.x - GS.x) * idy - 2.0 * g * h0x * zb1x * idx;
-    L[QY0] = -(FE.y - FW.y) * idx - (GN.y - GS.y) * idy - 2.0 * g * h0y * zb1y * idy;
+    L[H0] = -(FE.fh - FW.fh) * idx - (GN.fh - GS.fh) * idy;
+    L[QX0] = -(FE.fx - FW.fx) * idx - (GN.fx - GS.fx) * idy - 2.0 * g * h0x * zb1x * idx;
+    L[QY0] = -(FE.fy - FW.fy) * idx - (GN.fy - GS.fy) * idy - 2.0 * g * h0y * zb1y * idy;
     if (d.rain != 0.0 && ts >= d.rain_t0 && ts < d.rain_t1) L[H0] += d.rain;
     if (c == d.src_idx) L[H0] += d.qp * idx * idy;
     // Eq. 4b
     const double k3x = -3.0 * idx, k3y = -3.0 * idy, g23 = 2.0 * g / 3.0;
-    L[H1X] = k3x * ((FE.h + FW.h) - (Fp.h + Fm.h));
-    L[QX1X] = k3x * ((FE.x + FW.x) - (Fp.x + Fm.x) + g23 * h1x_ * zb1x);
-    L[QY1X] = k3x * ((FE.y + FW.y) - (Fp.y + Fm.y));
+    L[H1X] = k3x * ((FE.fh + FW.fh) - (Fp.h + Fm.h));
+    L[QX1X] = k3x * ((FE.fx + FW.fx) - (Fp.x + Fm.x) + g23 * h1x_ * zb1x);
+    L[QY1X] = k3x * ((FE.fy + FW.fy) - (Fp.y + Fm.y));
     // Eq. 4c
-    L[H1Y] = k3y * ((GN.h + GS.h) - (Gp.h + Gm.h));
-    L[QX1Y] = k3y * ((GN.x + GS.x) - (Gp.x + Gm.x));
-    L[QY1Y] = k3y * ((GN.y + GS.y) - (Gp.y + Gm.y) + g23 * h1y_ * zb1y);
+    L[H1Y] = k3y * ((GN.fh + GS.fh) - (Gp.h + Gm.h));
+    L[QX1Y] = k3y * ((GN.fx + GS.fx) - (Gp.x + Gm.x));
+    L[QY1Y] = k3y * ((GN.fy + GS.fy) - (Gp.y + Gm.y) + g23 * h1y_ * zb1y);
 
     double out[9];
     if (STAGE == 1) {
@@ -845,7 +941,8 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
 // built at the end of the previous step.
 template <bool LL, int STAGE>
 static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64_NL) stage_kernel(Dev d) {
-  __shared__ StageSmem sm;
+  extern __shared__ double stage_smem[];  // one StageSmem (dynamic: above 48 KB)
+  StageSmem& sm = *reinterpret_cast<StageSmem*>(stage_smem);
   Scalars* sc = d.sc;
   if (sc->done) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
