@@ -314,9 +314,11 @@ typedef struct dg2_adj dg2_adj;
  * max_gauges >= 0).  About (nsnap + 10) state-sized buffers of 9 planes. */
 size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps);
 
-/* params: g, tol_dry, bc[4] are used; variant must be DG2_NL and precision
- * DG2_FP64 (DG2_E_ARG otherwise).  Workspace and stream as for
- * dg2_init_grid. */
+/* params: g, tol_dry, bc[4] are used; variant must be DG2_NL, precision
+ * DG2_FP64, flux DG2_HLL, scheme DG2_SCHEME_DG2 and wetdry DG2_WD_PRINTED (the
+ * step's face revision is Sec. 2.1.2 as printed, which equals the default
+ * revision wherever no cell is partially wet); DG2_E_ARG otherwise.
+ * Workspace and stream as for dg2_init_grid. */
 int dg2_adj_create(dg2_adj **out, int nx, int ny, double dx, double dy, const dg2_params *params,
                    int nsnap, int max_gauges, int max_steps, void *dev_workspace,
                    size_t ws_bytes, void *cuda_stream);

@@ -71,7 +71,8 @@ def build_tape(force: bool = False) -> str:
 _tape = None
 
 
-def taped_gradient(case, manning, q_knots, dts, sample_steps, obs, limiter=False):
+def taped_gradient(case, manning, q_knots, dts, sample_steps, obs, limiter=False,
+                   wetdry="positive"):
     """Misfit J = sum over samples and gauges of (h_gauge - obs)^2 of the oracle run
     of len(dts) steps from ``case`` (DEM, water, edges, its one inflow with the knot
     discharges ``q_knots``, Manning field ``manning`` (ny, nx)), sampled after the
@@ -106,7 +107,8 @@ def taped_gradient(case, manning, q_knots, dts, sample_steps, obs, limiter=False
     J = _tape.orc_tape_gradient(
         ctypes.c_int(nx), ctypes.c_int(ny), ctypes.c_double(case.dx), ctypes.c_double(case.dy),
         ctypes.c_double(9.80665), ctypes.c_double(case.cfl), ctypes.c_double(1e-5),
-        ctypes.c_double(10.0), ctypes.c_double(case.dt_max), ctypes.c_int(int(bool(limiter))), bc,
+        ctypes.c_double(10.0), ctypes.c_double(case.dt_max), ctypes.c_int(int(bool(limiter))),
+        ctypes.c_int(1 if wetdry == "positive" else 0), bc,
         dp(z), None if eta is None else dp(eta), dp(man), ctypes.c_int(edge), ctypes.c_double(s0),
         ctypes.c_double(ln), dp(tk), dp(qk), ctypes.c_int(len(qk) if edge >= 0 else 0),
         ctypes.c_int(len(d)), dp(d), ctypes.c_int(len(ss)),

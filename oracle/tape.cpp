@@ -85,7 +85,7 @@ extern "C" {
 // inflow given, and its derivatives with respect to the Manning n of every
 // cell (grad_n[ny*nx]) and the inflow knot discharges (grad_q[nk]).
 double orc_tape_gradient(int nx, int ny, double dx, double dy, double g, double cfl, double tol,
-                         double ds, double dt_max, int limiter, const int *bc,
+                         double ds, double dt_max, int limiter, int wd, const int *bc,
                          const double *z_corner, const double *eta_corner, const double *manning,
                          int edge, double s0, double len, const double *tk, const double *qk,
                          int nk, int nsteps, const double *dts, int nsamp, const int *samp_step,
@@ -96,6 +96,7 @@ double orc_tape_gradient(int nx, int ny, double dx, double dy, double g, double 
     tp::nodes.push_back(tp::Node{0, 0, 0.0, 0.0});
     orc_t *o = orc_create(nx, ny, dx, dy, g, cfl, tol, ds, dt_max, limiter, bc);
     const size_t N = (size_t)nx * ny;
+    orc_set_wetdry(o, wd);
     orc_set_dem(o, z_corner, manning, 0.0, eta_corner);
     // the parameters become tape variables
     std::vector<int> nid(N), qid(nk > 0 ? nk : 0);

@@ -1115,8 +1115,9 @@ int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg
   *out = nullptr;
   if (!prm) return afail(DG2_E_ARG, "params is null");
   if (prm->variant != DG2_NL || prm->precision != DG2_FP64 || prm->flux != DG2_HLL ||
-      prm->scheme != DG2_SCHEME_DG2)
-    return afail(DG2_E_ARG, "the adjoint is of the FP64 DG2-NL step with the HLL flux");
+      prm->scheme != DG2_SCHEME_DG2 || prm->wetdry != DG2_WD_PRINTED)
+    return afail(DG2_E_ARG, "the adjoint is of the FP64 DG2-NL step with the HLL flux and the "
+                            "printed face revision (wetdry = DG2_WD_PRINTED)");
   if (!(dx > 0.0) || !(dy > 0.0)) return afail(DG2_E_ARG, "dx, dy must be > 0");
   AdjLayout L;
   if (!adj_layout(nx, ny, nsnap, max_gauges, max_steps, L))

@@ -498,6 +498,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     f.nblocks = L.nblocks;
     f.src_idx = -1;
     f.tiles = d.tiles;
+    f.wd = d.wd;
   }
   c->sblock = dim3(dg2::TX, dg2::TY);
   c->sgrid = dim3((nx + dg2::TX - 1) / dg2::TX, (ny + dg2::TY - 1) / dg2::TY);

@@ -68,6 +68,7 @@ struct D32 {
   double* samp_h;
   int nblocks;
   Tiles tiles;
+  int wd;              // 1: positivity-consistent revision of partially wet cells
 };
 
 struct LimF {
@@ -426,17 +427,138 @@ __device__ __forceinline__ void friction32_tile(const D32& d, float gdt, int bx,
   S[QY1Y * P + c] = nq[1][1];
 }
 
+// One side of a face: the planar limit's depth h (free-surface form: eta_face
+// - z_face) and velocities (tol rule), the depth the face may draw on (hs:
+// max(0, h), scaled for a partially wet cell), and whether the side's cell is
+// partially wet.  Both sides share the face bed, so the revision below works
+// in heights above it.
+struct RecF {
+  float h, u, v, hs;
+  int pw;
+};
+
+// A face flux in deviation form plus the lower (west / south) side's revised depth.
+struct FaceR32 {
+  FaceF f;
+  float ha;
+};
+
 template <int BX, int BY>
 struct StageSmem32T {
-  LimF e[BY][BX];
-  LimF n[BY][BX];
-  LimF hw[BY], he[BY], hs[BX], hn[BX];
-  FaceF fx[BY][BX + 1];
-  FaceF fy[BY + 1][BX];
+  RecF e[BY][BX];
+  RecF n[BY][BX];
+  RecF hw[BY], he[BY], hs[BX], hn[BX];
+  FaceR32 fx[BY][BX + 1];
+  FaceR32 fy[BY + 1][BX];
   double red[32];
   float redf[32];
 };
 using StageSmem32 = StageSmem32T<TX, TY>;
+
+// Face depths (hi - z_face) +- eta1 + lo of a cell from its free-surface modes:
+// hi - z_face is exact for shallow water (Sterbenz), and both sides of a face
+// form it from the same terms at rest.
+__device__ __forceinline__ void face_depths32(float e0, float e1x, float e1y, float lo, float zE,
+                                              float zW, float zN, float zS, float& eh, float& wh,
+                                              float& nh, float& sh) {
+  eh = ((e0 - zE) + e1x) + lo;
+  wh = ((e0 - zW) - e1x) + lo;
+  nh = ((e0 - zN) + e1y) + lo;
+  sh = ((e0 - zS) - e1y) + lo;
+}
+
+// Partially wet test and depth scale of a cell (average depth h0, face depths
+// W, E, S, N); wd = 0 keeps the printed revision (never partially wet).
+__device__ __forceinline__ bool pw_scale32(float h0, float hW, float hE, float hS, float hN,
+                                           float tol, int wd, float& sc) {
+  sc = 1.f;
+  if (!wd || !(h0 > tol)) return false;
+  if (!(hW < 0.f || hE < 0.f || hS < 0.f || hN < 0.f)) return false;
+  const float sum = __fadd_rn(__fadd_rn(__fadd_rn(fmaxf(hW, 0.f), fmaxf(hE, 0.f)), fmaxf(hS, 0.f)),
+                              fmaxf(hN, 0.f));
+  sc = __fdiv_rn(h0, __fmul_rn(0.25f, sum));
+  return true;
+}
+
+__device__ __forceinline__ RecF make_rec32(float h, float qx, float qy, bool pw, float sc,
+                                           float tol) {
+  RecF r;
+  r.h = h;
+  r.u = 0.f;
+  r.v = 0.f;
+  if (h > tol) {
+    r.u = qx / h;
+    r.v = qy / h;
+  }
+  const float hp = h > 0.f ? h : 0.f;
+  r.hs = pw ? __fmul_rn(sc, hp) : hp;
+  r.pw = pw ? 1 : 0;
+  return r;
+}
+
+// Revision of the face between lower side a and upper side b (the rule of the
+// FP64 path): neither side partially wet, h* = max(0, h); otherwise the
+// free-surface revision on the sides' own bed levels, z* = max(za, zb),
+// h* = max(0, eta - z*), here in heights above the shared face bed (the free
+// surface at h, or hs on a side that is not partially wet; the own bed at
+// h - hs, or 0).
+// Either way h* + z* is the side's own face free surface, so the deviation
+// form of the pressure and bed terms holds.  Written with explicit roundings:
+// a face on a tile edge is revised by both tiles beside it.
+__device__ __forceinline__ void revise_face32(const RecF& a, const RecF& b, float tol, LimF& ra,
+                                              LimF& rb) {
+  if (!a.pw && !b.pw) {
+    ra.h = a.hs; ra.u = a.u; ra.v = a.v;
+    rb.h = b.hs; rb.u = b.u; rb.v = b.v;
+  } else {
+    const float ea = a.pw ? a.h : a.hs, eb = b.pw ? b.h : b.hs;
+    const float oa = a.pw ? __fadd_rn(a.h, -a.hs) : 0.f;
+    const float ob = b.pw ? __fadd_rn(b.h, -b.hs) : 0.f;
+    // the side whose bed is z* keeps its offered depth exactly; the other side
+    // lies (its free surface - that side's) above it: no thin depth is formed as
+    // a difference of two large heights, and equal free surfaces give equal depths
+    if (oa >= ob) {
+      ra.h = a.hs;
+      rb.h = fmaxf(__fadd_rn(a.hs, __fadd_rn(eb, -ea)), 0.f);
+    } else {
+      rb.h = b.hs;
+      ra.h = fmaxf(__fadd_rn(b.hs, __fadd_rn(ea, -eb)), 0.f);
+    }
+    ra.u = ra.h > tol ? a.u : 0.f; ra.v = ra.h > tol ? a.v : 0.f;
+    rb.u = rb.h > tol ? b.u : 0.f; rb.v = rb.h > tol ? b.v : 0.f;
+  }
+  ra.qx = __fmul_rn(ra.h, a.u); ra.qy = __fmul_rn(ra.h, a.v);
+  rb.qx = __fmul_rn(rb.h, b.u); rb.qy = __fmul_rn(rb.h, b.v);
+}
+
+// Record, at the face it shares with a cell of the tile, of the neighbour
+// (ni, nj) on side `side` (0: west / south of the face, its east / north
+// limit; 1: east / north, its west / south limit) along dir: the same
+// arithmetic as the neighbour's own thread.
+template <bool LL>
+__device__ __forceinline__ RecF neighbour_rec32(const D32& d, const float* __restrict__ In, int ni,
+                                                int nj, int dir, int side) {
+  const long long P = d.plane, c = (long long)nj * d.pitch + ni;
+  float ex = In[E1X * P + c], xx = In[QX1X * P + c], yx = In[QY1X * P + c];
+  float ey = In[E1Y * P + c], xy = In[QX1Y * P + c], yy = In[QY1Y * P + c];
+  if (LL) {
+    limited_slopes32(d, In, ni, nj, 1, ex, xx, yx);
+    limited_slopes32(d, In, ni, nj, 2, ey, xy, yy);
+  }
+  const float e0 = In[E0 * P + c], lo = In[E0L * P + c];
+  float z0, z1x, z1y, zE, zW, zN, zS;
+  cell_z(d, ni, nj, z0, z1x, z1y, zE, zW, zN, zS);
+  float eh, wh, nh, sh;
+  face_depths32(e0, ex, ey, lo, zE, zW, zN, zS, eh, wh, nh, sh);
+  float scl;
+  const bool pw = pw_scale32((e0 - z0) + lo, wh, eh, sh, nh, d.tol, d.wd, scl);
+  const float qx0 = In[QX0 * P + c], qy0 = In[QY0 * P + c];
+  if (dir == 1)
+    return side == 0 ? make_rec32(eh, qx0 + xx, qy0 + yx, pw, scl, d.tol)
+                     : make_rec32(wh, qx0 - xx, qy0 - yx, pw, scl, d.tol);
+  return side == 0 ? make_rec32(nh, qx0 + xy, qy0 + yy, pw, scl, d.tol)
+                   : make_rec32(sh, qx0 - xy, qy0 - yy, pw, scl, d.tol);
+}
 
 // One RK stage of the FP32 free-surface form on the tile (bx, by).  `blk`
 // carries the per-block constants (dt, stage time, rain flag) read once.
@@ -466,7 +588,7 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
   const float s_rainf = blk.rainf;
   float m[9];
   float z0 = 0.f, z1x = 0.f, z1y = 0.f, zE = 0.f, zW = 0.f, zN = 0.f, zS = 0.f;
-  LimF Es, Ws, Ns, Ss;
+  RecF rE, rW, rN, rS;
   float mlo = 0.f;
   if (act) {
 #pragma unroll
@@ -477,96 +599,88 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
       limited_slopes32(d, In, i, j, 2, m[E1Y], m[QX1Y], m[QY1Y]);
     }
     cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-    // face depths (hi - z_face) +- eta1 + lo: hi - z_face is exact for shallow water
-    // (Sterbenz), and both sides of a face form it from the same terms at rest
-    const float eh = ((m[E0] - zE) + m[E1X]) + mlo, wh = ((m[E0] - zW) - m[E1X]) + mlo;
-    const float nh = ((m[E0] - zN) + m[E1Y]) + mlo, shh = ((m[E0] - zS) - m[E1Y]) + mlo;
+    float eh, wh, nh, shh;
+    face_depths32(m[E0], m[E1X], m[E1Y], mlo, zE, zW, zN, zS, eh, wh, nh, shh);
     const float eqx = m[QX0] + m[QX1X], eqy = m[QY0] + m[QY1X];
     const float wqx = m[QX0] - m[QX1X], wqy = m[QY0] - m[QY1X];
     const float nqx = m[QX0] + m[QX1Y], nqy = m[QY0] + m[QY1Y];
     const float sqx = m[QX0] - m[QX1Y], sqy = m[QY0] - m[QY1Y];
-    Es = revise32(eh, eqx, eqy, tol);
-    Ws = revise32(wh, wqx, wqy, tol);
-    Ns = revise32(nh, nqx, nqy, tol);
-    Ss = revise32(shh, sqx, sqy, tol);
-    sm.e[ty][tx] = Es;
-    sm.n[ty][tx] = Ns;
+    float scl;
+    const bool pw = pw_scale32((m[E0] - z0) + mlo, wh, eh, shh, nh, tol, d.wd, scl);
+    rE = make_rec32(eh, eqx, eqy, pw, scl, tol);
+    rW = make_rec32(wh, wqx, wqy, pw, scl, tol);
+    rN = make_rec32(nh, nqx, nqy, pw, scl, tol);
+    rS = make_rec32(shh, sqx, sqy, pw, scl, tol);
+    sm.e[ty][tx] = rE;
+    sm.n[ty][tx] = rN;
     if (tx == 0) {
-      float h, qx, qy;
       if (i == 0) {
-        h = wh; qx = wqx; qy = wqy;
+        float h = wh, qx = wqx, qy = wqy;
         ghost32(d, 0, (j + 0.5f) * d.dy, ts, h, qx, qy);
+        sm.hw[ty] = make_rec32(h, qx, qy, false, 1.f, tol);
       } else {
-        const long long cw = c - 1;
-        float se = In[E1X * P + cw], s1x = In[QX1X * P + cw], s1y = In[QY1X * P + cw];
-        if (LL) limited_slopes32(d, In, i - 1, j, 1, se, s1x, s1y);
-        h = ((In[E0 * P + cw] - zW) + se) + In[E0L * P + cw];  // its east face is our west face
-        qx = In[QX0 * P + cw] + s1x; qy = In[QY0 * P + cw] + s1y;
+        sm.hw[ty] = neighbour_rec32<LL>(d, In, i - 1, j, 1, 0);
       }
-      sm.hw[ty] = revise32(h, qx, qy, tol);
     }
     if (east_edge) {
-      float h, qx, qy;
       if (i == d.nx - 1) {
-        h = eh; qx = eqx; qy = eqy;
+        float h = eh, qx = eqx, qy = eqy;
         ghost32(d, 1, (j + 0.5f) * d.dy, ts, h, qx, qy);
+        sm.he[ty] = make_rec32(h, qx, qy, false, 1.f, tol);
       } else {
-        const long long ce = c + 1;
-        float se = In[E1X * P + ce], s1x = In[QX1X * P + ce], s1y = In[QY1X * P + ce];
-        if (LL) limited_slopes32(d, In, i + 1, j, 1, se, s1x, s1y);
-        h = ((In[E0 * P + ce] - zE) - se) + In[E0L * P + ce];
-        qx = In[QX0 * P + ce] - s1x; qy = In[QY0 * P + ce] - s1y;
+        sm.he[ty] = neighbour_rec32<LL>(d, In, i + 1, j, 1, 1);
       }
-      sm.he[ty] = revise32(h, qx, qy, tol);
     }
     if (ty == 0) {
-      float h, qx, qy;
       if (j == 0) {
-        h = shh; qx = sqx; qy = sqy;
+        float h = shh, qx = sqx, qy = sqy;
         ghost32(d, 2, (i + 0.5f) * d.dx, ts, h, qx, qy);
+        sm.hs[tx] = make_rec32(h, qx, qy, false, 1.f, tol);
       } else {
-        const long long cs = c - d.pitch;
-        float se = In[E1Y * P + cs], s1x = In[QX1Y * P + cs], s1y = In[QY1Y * P + cs];
-        if (LL) limited_slopes32(d, In, i, j - 1, 2, se, s1x, s1y);
-        h = ((In[E0 * P + cs] - zS) + se) + In[E0L * P + cs];
-        qx = In[QX0 * P + cs] + s1x; qy = In[QY0 * P + cs] + s1y;
+        sm.hs[tx] = neighbour_rec32<LL>(d, In, i, j - 1, 2, 0);
       }
-      sm.hs[tx] = revise32(h, qx, qy, tol);
     }
     if (north_edge) {
-      float h, qx, qy;
       if (j == d.ny - 1) {
-        h = nh; qx = nqx; qy = nqy;
+        float h = nh, qx = nqx, qy = nqy;
         ghost32(d, 3, (i + 0.5f) * d.dx, ts, h, qx, qy);
+        sm.hn[tx] = make_rec32(h, qx, qy, false, 1.f, tol);
       } else {
-        const long long cn = c + d.pitch;
-        float se = In[E1Y * P + cn], s1x = In[QX1Y * P + cn], s1y = In[QY1Y * P + cn];
-        if (LL) limited_slopes32(d, In, i, j + 1, 2, se, s1x, s1y);
-        h = ((In[E0 * P + cn] - zN) - se) + In[E0L * P + cn];
-        qx = In[QX0 * P + cn] - s1x; qy = In[QY0 * P + cn] - s1y;
+        sm.hn[tx] = neighbour_rec32<LL>(d, In, i, j + 1, 2, 1);
       }
-      sm.hn[tx] = revise32(h, qx, qy, tol);
     }
   }
   __syncthreads();
 
+  // one revision and one flux per face; the own (upper) side of the west and
+  // south faces stays in registers, the lower side's depth goes with the flux
+  float hWo = 0.f, hSo = 0.f, hEo = 0.f, hNo = 0.f;
   if (act) {
-    const LimF& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
-    const FaceF fw = flux_x32(Lw, Ws, g, tol);
-    sm.fx[ty][tx] = fw;
+    LimF ra, rb;
+    const RecF& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
+    revise_face32(Lw, rW, tol, ra, rb);
+    hWo = rb.h;
+    const FaceF fw = flux_x32(ra, rb, g, tol);
+    sm.fx[ty][tx] = FaceR32{fw, ra.h};
     if (i == 0) brate += fw.h * d.dy;
     if (east_edge) {
-      const FaceF fe = flux_x32(Es, sm.he[ty], g, tol);
-      sm.fx[ty][tx + 1] = fe;
+      revise_face32(rE, sm.he[ty], tol, ra, rb);
+      hEo = ra.h;
+      const FaceF fe = flux_x32(ra, rb, g, tol);
+      sm.fx[ty][tx + 1] = FaceR32{fe, ra.h};
       if (i == d.nx - 1) brate -= fe.h * d.dy;
     }
-    const LimF& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
-    const FaceF fs = flux_y32(Ls, Ss, g, tol);
-    sm.fy[ty][tx] = fs;
+    const RecF& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
+    revise_face32(Ls, rS, tol, ra, rb);
+    hSo = rb.h;
+    const FaceF fs = flux_y32(ra, rb, g, tol);
+    sm.fy[ty][tx] = FaceR32{fs, ra.h};
     if (j == 0) brate += fs.h * d.dx;
     if (north_edge) {
-      const FaceF fn = flux_y32(Ns, sm.hn[tx], g, tol);
-      sm.fy[ty + 1][tx] = fn;
+      revise_face32(rN, sm.hn[tx], tol, ra, rb);
+      hNo = ra.h;
+      const FaceF fn = flux_y32(ra, rb, g, tol);
+      sm.fy[ty + 1][tx] = FaceR32{fn, ra.h};
       if (j == d.ny - 1) brate -= fn.h * d.dx;
     }
   }
@@ -575,12 +689,21 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
   if (act) {
     // own faces: east / north faces are referenced to our (left / south) pressure,
     // west / south faces to the neighbour's, so add dP to get ours
-    const FaceF fE = sm.fx[ty][tx + 1], fW = sm.fx[ty][tx];
-    const FaceF gN = sm.fy[ty + 1][tx], gS = sm.fy[ty][tx];
+    const FaceR32 rEf = sm.fx[ty][tx + 1], rWf = sm.fx[ty][tx];
+    const FaceR32 rNf = sm.fy[ty + 1][tx], rSf = sm.fy[ty][tx];
+    const FaceF fE = rEf.f, fW = rWf.f, gN = rNf.f, gS = rSf.f;
+    if (!east_edge) hEo = rEf.ha;
+    if (!north_edge) hNo = rNf.ha;
     const float FEh = fE.h, FEx = fE.n, FEy = fE.t;
     const float FWh = fW.h, FWx = fW.n + fW.dp, FWy = fW.t;
     const float GNh = gN.h, GNx = gN.t, GNy = gN.n;
     const float GSh = gS.h, GSx = gS.t, GSy = gS.n + gS.dp;
+    // own revised states (Eq. 5 operands): q* = h* u
+    LimF Es, Ws, Ns, Ss;
+    Es.h = hEo; Es.qx = hEo * rE.u; Es.qy = hEo * rE.v;
+    Ws.h = hWo; Ws.qx = hWo * rW.u; Ws.qy = hWo * rW.v;
+    Ns.h = hNo; Ns.qx = hNo * rN.u; Ns.qy = hNo * rN.v;
+    Ss.h = hSo; Ss.qx = hSo * rS.u; Ss.qy = hSo * rS.v;
     const float h0x = 0.5f * (Es.h + Ws.h), x0x = 0.5f * (Es.qx + Ws.qx), y0x = 0.5f * (Es.qy + Ws.qy);
     const float h1x_ = 0.5f * (Es.h - Ws.h), x1x = 0.5f * (Es.qx - Ws.qx), y1x = 0.5f * (Es.qy - Ws.qy);
     const float h0y = 0.5f * (Ns.h + Ss.h), x0y = 0.5f * (Ns.qx + Ss.qx), y0y = 0.5f * (Ns.qy + Ss.qy);
