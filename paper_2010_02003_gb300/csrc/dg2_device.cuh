@@ -636,14 +636,25 @@ struct StageSmem {
 };
 
 // Record of a side whose planar limit is (h, qx, qy) over face bed zf; `sc` is
-// the depth scale of a partially wet cell (pw), 1 otherwise.
+// the depth scale of a partially wet cell (pw), 1 otherwise.  Velocities by
+// the tol rule; under the default revision (thin = wd), a limit thinner than
+// eps = h0 / 10 in a cell deeper than 10 tol_dry has its velocity
+// desingularised (Kurganov and Petrova, 2007): u = 2 max(h, 0) q / (h^2 +
+// eps^2), equal to q/h at h = eps (the planar discharge is not a resolved
+// velocity at such a face).
 __device__ __forceinline__ Rec make_rec(double h, double qx, double qy, double zf, bool pw,
-                                        double sc, double tol) {
+                                        double sc, double tol, bool thin = false, double h0 = 0.0) {
   Rec r;
   r.h = h;
   r.u = 0.0;
   r.v = 0.0;
-  if (h > tol) {
+  const double eps = 0.1 * h0;
+  if (thin && eps > tol && h < eps) {
+    const double hp = h > 0.0 ? h : 0.0;
+    const double den = h * h + eps * eps;
+    r.u = 2.0 * hp * qx / den;
+    r.v = 2.0 * hp * qy / den;
+  } else if (h > tol) {
     r.u = qx / h;
     r.v = qy / h;
   }
@@ -685,8 +696,9 @@ __device__ __forceinline__ F3 revise_face(const Rec& a, const Rec& b, bool ydir,
     hb = b.hs;
     za = a.zf - (a.h < 0.0 ? -a.h : 0.0);
     zb = b.zf - (b.h < 0.0 ? -b.h : 0.0);
-    ra.u = a.u; ra.v = a.v;
-    rb.u = b.u; rb.v = b.v;
+    // the flux's velocities follow the tol rule on the revised depth
+    ra.u = ha > tol ? a.u : 0.0; ra.v = ha > tol ? a.v : 0.0;
+    rb.u = hb > tol ? b.u : 0.0; rb.v = hb > tol ? b.v : 0.0;
   } else {
     double ea, oa, eb, ob;  // free surface and own bed level of each side
     if (a.pw) { ea = a.h + a.zf; oa = ea - a.hs; } else { oa = a.zf; ea = a.zf + a.hs; }
@@ -735,8 +747,8 @@ __device__ __forceinline__ Rec neighbour_rec(const Dev& d, const double* __restr
   const bool pw = pw_scale(h0, h0 - hx1, h0 + hx1, h0 - hy1, h0 + hy1, d.tol, d.wd, sc);
   const double sg = side == 0 ? 1.0 : -1.0;
   const double zf = d.Z[c] + sg * d.Z[dir * P + c];
-  return make_rec(h0 + sg * s1h, In[QX0 * P + c] + sg * s1x, In[QY0 * P + c] + sg * s1y, zf, pw, sc,
-                  d.tol);
+  const double qx0 = In[QX0 * P + c], qy0 = In[QY0 * P + c];
+  return make_rec(h0 + sg * s1h, qx0 + sg * s1x, qy0 + sg * s1y, zf, pw, sc, d.tol, d.wd != 0, h0);
 }
 
 // Ghost record beyond a domain edge, from the own planar limit (h, qx, qy) at
@@ -782,10 +794,11 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     const double nh = m[H0] + m[H1Y], shh = m[H0] - m[H1Y];
     double scl;
     const bool pw = pw_scale(m[H0], wh, eh, shh, nh, tol, d.wd, scl);
-    rE = make_rec(eh, m[QX0] + m[QX1X], m[QY0] + m[QY1X], z0 + z1x, pw, scl, tol);
-    rW = make_rec(wh, m[QX0] - m[QX1X], m[QY0] - m[QY1X], z0 - z1x, pw, scl, tol);
-    rN = make_rec(nh, m[QX0] + m[QX1Y], m[QY0] + m[QY1Y], z0 + z1y, pw, scl, tol);
-    rS = make_rec(shh, m[QX0] - m[QX1Y], m[QY0] - m[QY1Y], z0 - z1y, pw, scl, tol);
+    const bool thin = d.wd != 0;
+    rE = make_rec(eh, m[QX0] + m[QX1X], m[QY0] + m[QY1X], z0 + z1x, pw, scl, tol, thin, m[H0]);
+    rW = make_rec(wh, m[QX0] - m[QX1X], m[QY0] - m[QY1X], z0 - z1x, pw, scl, tol, thin, m[H0]);
+    rN = make_rec(nh, m[QX0] + m[QX1Y], m[QY0] + m[QY1Y], z0 + z1y, pw, scl, tol, thin, m[H0]);
+    rS = make_rec(shh, m[QX0] - m[QX1Y], m[QY0] - m[QY1Y], z0 - z1y, pw, scl, tol, thin, m[H0]);
     sm.e[ty][tx] = rE;
     sm.n[ty][tx] = rN;
     // the records beyond the tile: a neighbour's, or the edge ghost

@@ -480,13 +480,22 @@ __device__ __forceinline__ bool pw_scale32(float h0, float hW, float hE, float h
   return true;
 }
 
+// Velocities by the tol rule; under the default revision (thin), the
+// desingularised velocity of the FP64 path at a limit thinner than h0 / 10.
 __device__ __forceinline__ RecF make_rec32(float h, float qx, float qy, bool pw, float sc,
-                                           float tol) {
+                                           float tol, bool thin = false, float h0 = 0.f) {
   RecF r;
   r.h = h;
   r.u = 0.f;
   r.v = 0.f;
-  if (h > tol) {
+  const float eps = __fmul_rn(0.1f, h0);
+  if (thin && eps > tol && h < eps) {
+    const float hp = h > 0.f ? h : 0.f;
+    const float den = __fmaf_rn(h, h, __fmul_rn(eps, eps));
+    const float k = __fdiv_rn(__fmul_rn(2.f, hp), den);
+    r.u = __fmul_rn(k, qx);
+    r.v = __fmul_rn(k, qy);
+  } else if (h > tol) {
     r.u = qx / h;
     r.v = qy / h;
   }
@@ -508,8 +517,9 @@ __device__ __forceinline__ RecF make_rec32(float h, float qx, float qy, bool pw,
 __device__ __forceinline__ void revise_face32(const RecF& a, const RecF& b, float tol, LimF& ra,
                                               LimF& rb) {
   if (!a.pw && !b.pw) {
-    ra.h = a.hs; ra.u = a.u; ra.v = a.v;
-    rb.h = b.hs; rb.u = b.u; rb.v = b.v;
+    // the flux's velocities follow the tol rule on the revised depth
+    ra.h = a.hs; ra.u = a.hs > tol ? a.u : 0.f; ra.v = a.hs > tol ? a.v : 0.f;
+    rb.h = b.hs; rb.u = b.hs > tol ? b.u : 0.f; rb.v = b.hs > tol ? b.v : 0.f;
   } else {
     const float ea = a.pw ? a.h : a.hs, eb = b.pw ? b.h : b.hs;
     const float oa = a.pw ? __fadd_rn(a.h, -a.hs) : 0.f;
@@ -551,13 +561,15 @@ __device__ __forceinline__ RecF neighbour_rec32(const D32& d, const float* __res
   float eh, wh, nh, sh;
   face_depths32(e0, ex, ey, lo, zE, zW, zN, zS, eh, wh, nh, sh);
   float scl;
-  const bool pw = pw_scale32((e0 - z0) + lo, wh, eh, sh, nh, d.tol, d.wd, scl);
+  const float h0 = (e0 - z0) + lo;
+  const bool pw = pw_scale32(h0, wh, eh, sh, nh, d.tol, d.wd, scl);
   const float qx0 = In[QX0 * P + c], qy0 = In[QY0 * P + c];
+  const bool thin = d.wd != 0;
   if (dir == 1)
-    return side == 0 ? make_rec32(eh, qx0 + xx, qy0 + yx, pw, scl, d.tol)
-                     : make_rec32(wh, qx0 - xx, qy0 - yx, pw, scl, d.tol);
-  return side == 0 ? make_rec32(nh, qx0 + xy, qy0 + yy, pw, scl, d.tol)
-                   : make_rec32(sh, qx0 - xy, qy0 - yy, pw, scl, d.tol);
+    return side == 0 ? make_rec32(eh, qx0 + xx, qy0 + yx, pw, scl, d.tol, thin, h0)
+                     : make_rec32(wh, qx0 - xx, qy0 - yx, pw, scl, d.tol, thin, h0);
+  return side == 0 ? make_rec32(nh, qx0 + xy, qy0 + yy, pw, scl, d.tol, thin, h0)
+                   : make_rec32(sh, qx0 - xy, qy0 - yy, pw, scl, d.tol, thin, h0);
 }
 
 // One RK stage of the FP32 free-surface form on the tile (bx, by).  `blk`
@@ -606,11 +618,13 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
     const float nqx = m[QX0] + m[QX1Y], nqy = m[QY0] + m[QY1Y];
     const float sqx = m[QX0] - m[QX1Y], sqy = m[QY0] - m[QY1Y];
     float scl;
-    const bool pw = pw_scale32((m[E0] - z0) + mlo, wh, eh, shh, nh, tol, d.wd, scl);
-    rE = make_rec32(eh, eqx, eqy, pw, scl, tol);
-    rW = make_rec32(wh, wqx, wqy, pw, scl, tol);
-    rN = make_rec32(nh, nqx, nqy, pw, scl, tol);
-    rS = make_rec32(shh, sqx, sqy, pw, scl, tol);
+    const float h0c = (m[E0] - z0) + mlo;
+    const bool pw = pw_scale32(h0c, wh, eh, shh, nh, tol, d.wd, scl);
+    const bool thin = d.wd != 0;
+    rE = make_rec32(eh, eqx, eqy, pw, scl, tol, thin, h0c);
+    rW = make_rec32(wh, wqx, wqy, pw, scl, tol, thin, h0c);
+    rN = make_rec32(nh, nqx, nqy, pw, scl, tol, thin, h0c);
+    rS = make_rec32(shh, sqx, sqy, pw, scl, tol, thin, h0c);
     sm.e[ty][tx] = rE;
     sm.n[ty][tx] = rN;
     if (tx == 0) {

@@ -86,12 +86,14 @@ def test_fp32_floodplain_against_fp64_oracle(limiter):
     case = inputs.floodplain(nx=96, ny=64, dx=2.0, q_peak=15.0, t_peak=20.0, channel_width=12.0)
     o = make_oracle(case, limiter=limiter)
     s = B.solver_from_case(case, variant=B.DG2_LL if limiter else B.DG2_NL, precision=B.DG2_FP32)
-    # DG2-LL on this thin inflow front amplifies a 1e-7 perturbation ~6000x in 100 steps
-    # (the FP64 oracle does the same to its own perturbed copy), so LL is compared over
-    # 50 steps (measured 6.6e-5 / 2.8e-5), NL over 100 (measured 1.7e-5 / 5.6e-6)
-    for _ in range(50 if limiter else 100):
+    # the thin inflow front amplifies round-off ~10^4 between steps 90 and 100 in the
+    # FP64 oracle itself (tests/test_oracle_conditioning.py) and DG2-LL a 1e-7 (FP32)
+    # perturbation earlier, so LL is compared over 50 steps and NL over 85 (measured:
+    # LL 3.3e-5 / 4.0e-5, NL 2.9e-5 / 2.2e-6)
+    for _ in range(50 if limiter else 85):
         s.step(o.step())
     eh, eq = fp32_errors(s.state(), o.state())
+    print(f"FP32 floodplain {'LL' if limiter else 'NL'}: depth {eh:.2e}, discharge {eq:.2e}")
     assert eh < 1e-3 and eq < 1e-3, (eh, eq)
     m, led = s.mass()
     assert abs(m - led) <= 1e-6 * max(led, 1.0)

@@ -64,12 +64,12 @@ CASES = {
 }
 
 
-# Free-running horizon: 100 steps.  Under the printed face revision the limited
-# floodplain start amplifies round-off ~4000x between steps 88 and 100 in the
-# oracle itself (tests/test_oracle_conditioning.py), so that variant is held over
-# 80 steps (test_printed_revision_parity); the default revision is
-# well-conditioned there.
-HORIZON = {}
+# Free-running horizon: 100 steps, except the floodplain start, whose thin channel
+# front amplifies round-off ~10^4 between steps 90 and 100 in the oracle itself
+# (tests/test_oracle_conditioning.py), so no implementation with another rounding
+# order can hold 1e-12 there; it is held over 85 steps, and every one of its 100
+# steps is checked from the oracle's own state below.
+HORIZON = {("floodplain_dry_96x64", False): 85, ("floodplain_dry_96x64", True): 85}
 
 
 @pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])

@@ -38,7 +38,9 @@ def test_taped_gradient_matches_oracle_finite_differences():
     qk = case.inflows[0].q_knots.copy()
     obs = np.full((3, 3), 0.3)
     J, gn, gq = oracle.taped_gradient(case, man, qk, DTS, SAMPLES, obs)
-    assert J == _misfit(man, qk, obs)          # the taped run is the oracle run, bit for bit
+    # the taped run is the oracle run (the C++ scalar type reproduces the misfit to the
+    # last unit or so; its derivatives are the subject of the checks below)
+    assert abs(J - _misfit(man, qk, obs)) <= 1e-15 * abs(J)
     checked = 0
     for j, i in [(5, 3), (4, 7), (6, 1), (3, 5)]:
         e = 1e-6
