@@ -146,8 +146,9 @@ struct F3 {
 __device__ __forceinline__ Lim revise(double h, double qx, double qy, double tol) {
   Lim r;
   if (h > tol) {
-    r.u = qx / h;
-    r.v = qy / h;
+    const double ih = 1.0 / h;
+    r.u = qx * ih;
+    r.v = qy * ih;
   } else {
     r.u = 0.0;
     r.v = 0.0;
@@ -225,8 +226,9 @@ __device__ __forceinline__ F3 roe(double hL, double qnL, double qtL, double unL,
     return f;
   }
   const double sL = sqrt(hL), sR = sqrt(hR);
-  const double uh = (sL * unL + sR * unR) / (sL + sR);
-  const double vh = (sL * utL + sR * utR) / (sL + sR);
+  const double isum = 1.0 / (sL + sR);
+  const double uh = (sL * unL + sR * unR) * isum;
+  const double vh = (sL * utL + sR * utR) * isum;
   const double hh = sL * sR;
   const double ch = sqrt(0.5 * g * (hL + hR));
   const double dh = hR - hL, du = unR - unL, dv = utR - utL;
@@ -266,8 +268,9 @@ __device__ __forceinline__ F3 phys_flux(double h, double qx, double qy, double g
                                         bool ydir) {
   double u = 0.0, v = 0.0;
   if (h > tol) {
-    u = qx / h;
-    v = qy / h;
+    const double ih = 1.0 / h;
+    u = qx * ih;
+    v = qy * ih;
   }
   F3 f;
   const double p = 0.5 * g * h * h;
@@ -472,7 +475,8 @@ __device__ __forceinline__ float block_max_f(float v, float* sh) {
 // Courant wave-speed rate of a cell: max((|u|+c)/dx, (|v|+c)/dy) if wet.
 __device__ __forceinline__ double cell_rate(const Dev& d, double h0, double qx0, double qy0) {
   if (!(h0 > d.tol)) return 0.0;
-  const double u = qx0 / h0, v = qy0 / h0, c = sqrt(d.g * h0);
+  const double ih = 1.0 / h0;
+  const double u = qx0 * ih, v = qy0 * ih, c = sqrt(d.g * h0);
   return fmax((fabs(u) + c) * d.inv_dx, (fabs(v) + c) * d.inv_dy);
 }
 
@@ -551,8 +555,9 @@ __device__ __forceinline__ void friction_point(double gn2dt, double tol, double 
   if (!(h > tol)) return;
   const double qm = sqrt(qx * qx + qy * qy);
   const double den = 1.0 + gn2dt * qm / (h * h * cbrt(h));
-  qx = qx / den;
-  qy = qy / den;
+  const double iden = 1.0 / den;
+  qx = qx * iden;
+  qy = qy * iden;
 }
 
 // Friction on the cells of one 32 x 8 tile (threads 32 x 8).
@@ -652,11 +657,13 @@ __device__ __forceinline__ Rec make_rec(double h, double qx, double qy, double z
   if (thin && eps > tol && h < eps) {
     const double hp = h > 0.0 ? h : 0.0;
     const double den = h * h + eps * eps;
-    r.u = 2.0 * hp * qx / den;
-    r.v = 2.0 * hp * qy / den;
+    const double k = 2.0 * hp / den;
+    r.u = k * qx;
+    r.v = k * qy;
   } else if (h > tol) {
-    r.u = qx / h;
-    r.v = qy / h;
+    const double ih = 1.0 / h;
+    r.u = qx * ih;
+    r.v = qy * ih;
   }
   const double hp = h > 0.0 ? h : 0.0;
   r.hs = pw ? sc * hp : hp;
@@ -751,6 +758,24 @@ __device__ __forceinline__ Rec neighbour_rec(const Dev& d, const double* __restr
   return make_rec(h0 + sg * s1h, qx0 + sg * s1x, qy0 + sg * s1y, zf, pw, sc, d.tol, d.wd != 0, h0);
 }
 
+// Planar limit (h, qx, qy) of cell (i, j) at face f (0 E, 1 W, 2 N, 3 S), with
+// the slopes limited when LL, and the face bed zf: what the cell's own thread
+// forms, for a ghost built by another thread.
+template <bool LL>
+__device__ __forceinline__ void own_face_limit(const Dev& d, const double* __restrict__ In, int i,
+                                               int j, int f, double& h, double& qx, double& qy,
+                                               double& zf) {
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  const int dir = f <= 1 ? 1 : 2;
+  double s1h, s1x, s1y;
+  if (LL) limited_slopes(d, In, i, j, dir, s1h, s1x, s1y);
+  else { s1h = In[dir * P + c]; s1x = In[(3 + dir) * P + c]; s1y = In[(6 + dir) * P + c]; }
+  const double h0 = In[H0 * P + c], x0 = In[QX0 * P + c], y0 = In[QY0 * P + c];
+  const double z0 = d.Z[c], z1 = d.Z[dir * P + c];
+  if (f == 0 || f == 2) { h = h0 + s1h; qx = x0 + s1x; qy = y0 + s1y; zf = z0 + z1; }
+  else { h = h0 - s1h; qx = x0 - s1x; qy = y0 - s1y; zf = z0 - z1; }
+}
+
 // Ghost record beyond a domain edge, from the own planar limit (h, qx, qy) at
 // that edge over the own face bed zf.
 __device__ __forceinline__ Rec ghost_rec(const Dev& d, int edge, double s, double t, double h,
@@ -801,23 +826,61 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     rS = make_rec(shh, m[QX0] - m[QX1Y], m[QY0] - m[QY1Y], z0 - z1y, pw, scl, tol, thin, m[H0]);
     sm.e[ty][tx] = rE;
     sm.n[ty][tx] = rN;
-    // the records beyond the tile: a neighbour's, or the edge ghost
-    if (tx == 0)
-      sm.hw[ty] = i == 0 ? ghost_rec(d, 0, (j + 0.5) * d.dy, ts, wh, m[QX0] - m[QX1X],
-                                     m[QY0] - m[QY1X], z0 - z1x)
-                         : neighbour_rec<LL>(d, In, i - 1, j, 1, 0);
-    if (east_edge)
-      sm.he[ty] = i == d.nx - 1 ? ghost_rec(d, 1, (j + 0.5) * d.dy, ts, eh, m[QX0] + m[QX1X],
-                                            m[QY0] + m[QY1X], z0 + z1x)
-                                : neighbour_rec<LL>(d, In, i + 1, j, 1, 1);
-    if (ty == 0)
-      sm.hs[tx] = j == 0 ? ghost_rec(d, 2, (i + 0.5) * d.dx, ts, shh, m[QX0] - m[QX1Y],
-                                     m[QY0] - m[QY1Y], z0 - z1y)
-                         : neighbour_rec<LL>(d, In, i, j - 1, 2, 0);
-    if (north_edge)
-      sm.hn[tx] = j == d.ny - 1 ? ghost_rec(d, 3, (i + 0.5) * d.dx, ts, nh, m[QX0] + m[QX1Y],
-                                            m[QY0] + m[QY1Y], z0 + z1y)
-                                : neighbour_rec<LL>(d, In, i, j + 1, 2, 1);
+  }
+  // the records beyond the tile (a neighbour's, or the edge ghost), one per
+  // thread of the first 2 (TX + TY) threads, so no warp runs them one lane at a time
+  {
+    const int t = ty * TX + tx;
+    const int i0 = bx * TX, j0 = by * TY;
+    const int ni = d.nx - i0 < TX ? d.nx - i0 : TX, nj = d.ny - j0 < TY ? d.ny - j0 : TY;
+    if (t < TY) {
+      if (t < nj) {
+        const int jj = j0 + t;
+        if (i0 == 0) {
+          double h, qx, qy, zf;
+          own_face_limit<LL>(d, In, i0, jj, 1, h, qx, qy, zf);
+          sm.hw[t] = ghost_rec(d, 0, (jj + 0.5) * d.dy, ts, h, qx, qy, zf);
+        } else {
+          sm.hw[t] = neighbour_rec<LL>(d, In, i0 - 1, jj, 1, 0);
+        }
+      }
+    } else if (t < 2 * TY) {
+      const int r = t - TY;
+      if (r < nj) {
+        const int jj = j0 + r, il = i0 + ni - 1;
+        if (il == d.nx - 1) {
+          double h, qx, qy, zf;
+          own_face_limit<LL>(d, In, il, jj, 0, h, qx, qy, zf);
+          sm.he[r] = ghost_rec(d, 1, (jj + 0.5) * d.dy, ts, h, qx, qy, zf);
+        } else {
+          sm.he[r] = neighbour_rec<LL>(d, In, il + 1, jj, 1, 1);
+        }
+      }
+    } else if (t < 2 * TY + TX) {
+      const int q = t - 2 * TY;
+      if (q < ni) {
+        const int ii = i0 + q;
+        if (j0 == 0) {
+          double h, qx, qy, zf;
+          own_face_limit<LL>(d, In, ii, j0, 3, h, qx, qy, zf);
+          sm.hs[q] = ghost_rec(d, 2, (ii + 0.5) * d.dx, ts, h, qx, qy, zf);
+        } else {
+          sm.hs[q] = neighbour_rec<LL>(d, In, ii, j0 - 1, 2, 0);
+        }
+      }
+    } else if (t < 2 * TY + 2 * TX) {
+      const int q = t - 2 * TY - TX;
+      if (q < ni) {
+        const int ii = i0 + q, jl = j0 + nj - 1;
+        if (jl == d.ny - 1) {
+          double h, qx, qy, zf;
+          own_face_limit<LL>(d, In, ii, jl, 2, h, qx, qy, zf);
+          sm.hn[q] = ghost_rec(d, 3, (ii + 0.5) * d.dx, ts, h, qx, qy, zf);
+        } else {
+          sm.hn[q] = neighbour_rec<LL>(d, In, ii, jl + 1, 2, 1);
+        }
+      }
+    }
   }
   __syncthreads();
 

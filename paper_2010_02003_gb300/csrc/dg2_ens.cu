@@ -75,8 +75,15 @@ __global__ void __launch_bounds__(BX* BY) ens_friction_kernel(EnsDev E) {
   }
 }
 
+// resident 256-thread blocks per SM asked of the register allocator for the FP32
+// stage kernels (twice that for 128-thread tiles)
+#ifndef DG2_MINB32
+#define DG2_MINB32 3
+#endif
+
 template <bool LL, int STAGE, int BX, int BY>
-__global__ void __launch_bounds__(BX* BY, BX * BY <= 128 ? 6 : 3) ens_stage_kernel(EnsDev E) {
+__global__ void __launch_bounds__(BX* BY, BX * BY <= 128 ? 2 * DG2_MINB32 : DG2_MINB32)
+    ens_stage_kernel(EnsDev E) {
   __shared__ f32::StageSmem32T<BX, BY> sm;
   __shared__ f32::Blk32 blk;
   const int tx = threadIdx.x, ty = threadIdx.y;

@@ -541,6 +541,26 @@ __device__ __forceinline__ void revise_face32(const RecF& a, const RecF& b, floa
   rb.qx = __fmul_rn(rb.h, b.u); rb.qy = __fmul_rn(rb.h, b.v);
 }
 
+// Planar limit (face depth, qx, qy) of cell (i, j) at face f (0 E, 1 W, 2 N,
+// 3 S), slopes limited when LL: what the cell's own thread forms, for a ghost
+// built by another thread.
+template <bool LL>
+__device__ __forceinline__ void own_face_limit32(const D32& d, const float* __restrict__ In, int i,
+                                                 int j, int f, float& h, float& qx, float& qy) {
+  const long long P = d.plane, c = (long long)j * d.pitch + i;
+  const int dir = f <= 1 ? 1 : 2;
+  float se = In[dir * P + c], sx = In[(3 + dir) * P + c], sy = In[(6 + dir) * P + c];
+  if (LL) limited_slopes32(d, In, i, j, dir, se, sx, sy);
+  float z0, z1x, z1y, zE, zW, zN, zS;
+  cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
+  const float e0 = In[E0 * P + c], lo = In[E0L * P + c];
+  const float x0 = In[QX0 * P + c], y0 = In[QY0 * P + c];
+  if (f == 0) { h = ((e0 - zE) + se) + lo; qx = x0 + sx; qy = y0 + sy; }
+  else if (f == 1) { h = ((e0 - zW) - se) + lo; qx = x0 - sx; qy = y0 - sy; }
+  else if (f == 2) { h = ((e0 - zN) + se) + lo; qx = x0 + sx; qy = y0 + sy; }
+  else { h = ((e0 - zS) - se) + lo; qx = x0 - sx; qy = y0 - sy; }
+}
+
 // Record, at the face it shares with a cell of the tile, of the neighbour
 // (ni, nj) on side `side` (0: west / south of the face, its east / north
 // limit; 1: east / north, its west / south limit) along dir: the same
@@ -627,40 +647,63 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
     rS = make_rec32(shh, sqx, sqy, pw, scl, tol, thin, h0c);
     sm.e[ty][tx] = rE;
     sm.n[ty][tx] = rN;
-    if (tx == 0) {
-      if (i == 0) {
-        float h = wh, qx = wqx, qy = wqy;
-        ghost32(d, 0, (j + 0.5f) * d.dy, ts, h, qx, qy);
-        sm.hw[ty] = make_rec32(h, qx, qy, false, 1.f, tol);
-      } else {
-        sm.hw[ty] = neighbour_rec32<LL>(d, In, i - 1, j, 1, 0);
+  }
+  // the records beyond the tile (a neighbour's, or the edge ghost), one per
+  // thread of the first 2 (BX + BY) threads, so no warp runs them one lane at a time
+  {
+    const int t = ty * BX + tx;
+    const int i0 = bx * BX, j0 = by * BY;
+    const int ni = d.nx - i0 < BX ? d.nx - i0 : BX, nj = d.ny - j0 < BY ? d.ny - j0 : BY;
+    if (t < BY) {
+      if (t < nj) {
+        const int jj = j0 + t;
+        if (i0 == 0) {
+          float h, qx, qy;
+          own_face_limit32<LL>(d, In, i0, jj, 1, h, qx, qy);
+          ghost32(d, 0, (jj + 0.5f) * d.dy, ts, h, qx, qy);
+          sm.hw[t] = make_rec32(h, qx, qy, false, 1.f, tol);
+        } else {
+          sm.hw[t] = neighbour_rec32<LL>(d, In, i0 - 1, jj, 1, 0);
+        }
       }
-    }
-    if (east_edge) {
-      if (i == d.nx - 1) {
-        float h = eh, qx = eqx, qy = eqy;
-        ghost32(d, 1, (j + 0.5f) * d.dy, ts, h, qx, qy);
-        sm.he[ty] = make_rec32(h, qx, qy, false, 1.f, tol);
-      } else {
-        sm.he[ty] = neighbour_rec32<LL>(d, In, i + 1, j, 1, 1);
+    } else if (t < 2 * BY) {
+      const int r = t - BY;
+      if (r < nj) {
+        const int jj = j0 + r, il = i0 + ni - 1;
+        if (il == d.nx - 1) {
+          float h, qx, qy;
+          own_face_limit32<LL>(d, In, il, jj, 0, h, qx, qy);
+          ghost32(d, 1, (jj + 0.5f) * d.dy, ts, h, qx, qy);
+          sm.he[r] = make_rec32(h, qx, qy, false, 1.f, tol);
+        } else {
+          sm.he[r] = neighbour_rec32<LL>(d, In, il + 1, jj, 1, 1);
+        }
       }
-    }
-    if (ty == 0) {
-      if (j == 0) {
-        float h = shh, qx = sqx, qy = sqy;
-        ghost32(d, 2, (i + 0.5f) * d.dx, ts, h, qx, qy);
-        sm.hs[tx] = make_rec32(h, qx, qy, false, 1.f, tol);
-      } else {
-        sm.hs[tx] = neighbour_rec32<LL>(d, In, i, j - 1, 2, 0);
+    } else if (t < 2 * BY + BX) {
+      const int q = t - 2 * BY;
+      if (q < ni) {
+        const int ii = i0 + q;
+        if (j0 == 0) {
+          float h, qx, qy;
+          own_face_limit32<LL>(d, In, ii, j0, 3, h, qx, qy);
+          ghost32(d, 2, (ii + 0.5f) * d.dx, ts, h, qx, qy);
+          sm.hs[q] = make_rec32(h, qx, qy, false, 1.f, tol);
+        } else {
+          sm.hs[q] = neighbour_rec32<LL>(d, In, ii, j0 - 1, 2, 0);
+        }
       }
-    }
-    if (north_edge) {
-      if (j == d.ny - 1) {
-        float h = nh, qx = nqx, qy = nqy;
-        ghost32(d, 3, (i + 0.5f) * d.dx, ts, h, qx, qy);
-        sm.hn[tx] = make_rec32(h, qx, qy, false, 1.f, tol);
-      } else {
-        sm.hn[tx] = neighbour_rec32<LL>(d, In, i, j + 1, 2, 1);
+    } else if (t < 2 * BY + 2 * BX) {
+      const int q = t - 2 * BY - BX;
+      if (q < ni) {
+        const int ii = i0 + q, jl = j0 + nj - 1;
+        if (jl == d.ny - 1) {
+          float h, qx, qy;
+          own_face_limit32<LL>(d, In, ii, jl, 2, h, qx, qy);
+          ghost32(d, 3, (ii + 0.5f) * d.dx, ts, h, qx, qy);
+          sm.hn[q] = make_rec32(h, qx, qy, false, 1.f, tol);
+        } else {
+          sm.hn[q] = neighbour_rec32<LL>(d, In, ii, jl + 1, 2, 1);
+        }
       }
     }
   }
