@@ -49,20 +49,21 @@ BYTES_PER_CELL = {
 KERNELS = ["friction", "stage1", "stage2"]
 # Algorithmic FP64 operations per wet cell (add, mul, div, sqrt, cbrt each one), each
 # face flux counted once: measured with oracle/opcount.cpp (friction 111, spatial
-# operator 381, limiter 70 per cell; RK combination 18 / 27; Courant rate 8).
-FLOPS_PER_WET_CELL = {"friction": 111, "stage1": {"nl": 399, "ll": 469},
-                      "stage2": {"nl": 416, "ll": 486}}
+# operator 381, limiter 83 per cell; RK combination 18 / 27; Courant rate 8), plus the
+# 4 multiplications of the default face revision's thin-limit thresholds.
+FLOPS_PER_WET_CELL = {"friction": 111, "stage1": {"nl": 403, "ll": 486},
+                      "stage2": {"nl": 420, "ll": 503}}
 # DRAM bytes (read + write) per launch of a variant's dominant kernel from one ncu
 # capture (summarised in the named profile), valid only for the device sources it
 # was taken with: the key is a hash of paper_2010_02003_gb300/csrc, and the
 # roofline's traffic is null once those sources change.
 TRAFFIC = {
-    ("fp64_ll", "stage2"): (53_583_616, "297a919fc12579ad",
+    ("fp64_ll", "stage2"): (47_315_712, "8043ed843c0e971f",
                             "profiles/stage_kernel_fp64_ll_floodplain2000x1000_t3600.md"),
-    ("fp32_ll", "stage2"): (29_019_904, "297a919fc12579ad",
-                            "profiles/stage32_kernel_fp32_ll_floodplain2000x1000_t3600.md"),
-    ("fp32_nl_flooded", "stage2"): (222_384_640, "297a919fc12579ad",
-                                    "profiles/stage32_kernel_fp32_nl_flooded2000x1000.md"),
+    ("fp32_ll", "stage2"): (25_678_080, "8043ed843c0e971f",
+                            "profiles/ens_stage_kernel_fp32_ll_floodplain2000x1000_t3600.md"),
+    ("fp32_nl_flooded", "stage2"): (222_608_128, "8043ed843c0e971f",
+                                    "profiles/ens_stage_kernel_fp32_nl_flooded2000x1000.md"),
 }
 # FP64 issue rate of GB300: 2 DFMA per SM per cycle (ncu
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / cycle), 152 SMs
