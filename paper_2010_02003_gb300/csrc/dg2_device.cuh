@@ -1002,14 +1002,14 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
 #ifndef DG2_TILE_LOOP64
 #define DG2_TILE_LOOP64 0
 #endif
-// minimum resident blocks per SM asked of the register allocator: 2 for the
-// FP64 DG2-NL stage (128 registers, no spills), 1 for DG2-LL (whose ~170
-// registers spill at 128)
+// minimum resident blocks per SM asked of the register allocator: 2 for both
+// FP64 stages (128 registers; measured on the floodplain, DG2-LL 0.857 ms/step
+// at 2 blocks against 0.955 at 1 block with 156 registers)
 #ifndef DG2_MINB64_NL
 #define DG2_MINB64_NL 2
 #endif
 #ifndef DG2_MINB64_LL
-#define DG2_MINB64_LL 1
+#define DG2_MINB64_LL 2
 #endif
 
 // Stage kernels run over the step's list of active tiles (and, in stage 1,
