@@ -801,8 +801,6 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   const double ts = STAGE == 1 ? sc->t : sc->t + dt;  // boundary-condition time
   const double* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const double g = d.g, tol = d.tol;
-  const bool east_edge = act && (tx == TX - 1 || i == d.nx - 1);
-  const bool north_edge = act && (ty == TY - 1 || j == d.ny - 1);
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
   Rec rE, rW, rN, rS;  // own records
@@ -884,30 +882,36 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   }
   __syncthreads();
 
-  // one revision and one flux per face; the own (upper) side of the west and
-  // south faces stays in registers, the lower side goes to shared memory
-  double hWo = 0, zWo = 0, hSo = 0, zSo = 0, hEo = 0, zEo = 0, hNo = 0, zNo = 0;
+  // one revision and one flux per face: each thread its west and south faces
+  // (the own, upper side stays in registers, the lower side's depth and bed go
+  // to shared memory with the flux), then the tile's east and north edge
+  // faces one per thread
+  double hWo = 0, zWo = 0, hSo = 0, zSo = 0;
   if (act) {
     double ha, za;
     const Rec& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
     const F3 fw = revise_face(Lw, rW, false, g, tol, d.flux, ha, za, hWo, zWo);
     sm.fx[ty][tx] = FaceR{fw.h, fw.x, fw.y, ha, za};
     if (i == 0) brate += fw.h * d.dy;
-    if (east_edge) {
-      double hb, zb;
-      const F3 fe = revise_face(rE, sm.he[ty], false, g, tol, d.flux, hEo, zEo, hb, zb);
-      sm.fx[ty][tx + 1] = FaceR{fe.h, fe.x, fe.y, hEo, zEo};
-      if (i == d.nx - 1) brate -= fe.h * d.dy;
-    }
     const Rec& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
     const F3 fs = revise_face(Ls, rS, true, g, tol, d.flux, ha, za, hSo, zSo);
     sm.fy[ty][tx] = FaceR{fs.h, fs.x, fs.y, ha, za};
     if (j == 0) brate += fs.h * d.dx;
-    if (north_edge) {
-      double hb, zb;
-      const F3 fn = revise_face(rN, sm.hn[tx], true, g, tol, d.flux, hNo, zNo, hb, zb);
-      sm.fy[ty + 1][tx] = FaceR{fn.h, fn.x, fn.y, hNo, zNo};
-      if (j == d.ny - 1) brate -= fn.h * d.dx;
+  }
+  {
+    const int t = ty * TX + tx;
+    const int ni = d.nx - bx * TX < TX ? d.nx - bx * TX : TX;
+    const int nj = d.ny - by * TY < TY ? d.ny - by * TY : TY;
+    double ha, za, hb, zb;
+    if (t < nj) {
+      const F3 fe = revise_face(sm.e[t][ni - 1], sm.he[t], false, g, tol, d.flux, ha, za, hb, zb);
+      sm.fx[t][ni] = FaceR{fe.h, fe.x, fe.y, ha, za};
+      if (bx * TX + ni == d.nx) brate -= fe.h * d.dy;
+    } else if (t >= TY && t < TY + ni) {
+      const int q = t - TY;
+      const F3 fn = revise_face(sm.n[nj - 1][q], sm.hn[q], true, g, tol, d.flux, ha, za, hb, zb);
+      sm.fy[nj][q] = FaceR{fn.h, fn.x, fn.y, ha, za};
+      if (by * TY + nj == d.ny) brate -= fn.h * d.dx;
     }
   }
   __syncthreads();
@@ -915,9 +919,8 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   if (act) {
     const FaceR FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
     const FaceR GS = sm.fy[ty][tx], GN = sm.fy[ty + 1][tx];
-    // own side of the east / north faces: revised by the neighbour's thread
-    if (!east_edge) { hEo = FE.ha; zEo = FE.za; }
-    if (!north_edge) { hNo = GN.ha; zNo = GN.za; }
+    // own side of the east / north faces: revised as their lower side
+    const double hEo = FE.ha, zEo = FE.za, hNo = GN.ha, zNo = GN.za;
     // own revised states (Eq. 5 operands): q* = h* u
     const double Esh = hEo, Esx = hEo * rE.u, Esy = hEo * rE.v;
     const double Wsh = hWo, Wsx = hWo * rW.u, Wsy = hWo * rW.v;

@@ -612,8 +612,6 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
   const long long c = (long long)j * d.pitch + i;
   const float* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const float g = d.g, tol = d.tol;
-  const bool east_edge = act && (tx == BX - 1 || i == d.nx - 1);
-  const bool north_edge = act && (ty == BY - 1 || j == d.ny - 1);
   const float dt = blk.dt;
   const double ts = blk.ts;
   const bool s_rain = blk.rain != 0;
@@ -709,9 +707,10 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
   }
   __syncthreads();
 
-  // one revision and one flux per face; the own (upper) side of the west and
-  // south faces stays in registers, the lower side's depth goes with the flux
-  float hWo = 0.f, hSo = 0.f, hEo = 0.f, hNo = 0.f;
+  // one revision and one flux per face: each thread its west and south faces
+  // (the own, upper side stays in registers, the lower side's depth goes with
+  // the flux), then the tile's east and north edge faces one per thread
+  float hWo = 0.f, hSo = 0.f;
   if (act) {
     LimF ra, rb;
     const RecF& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
@@ -720,25 +719,29 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
     const FaceF fw = flux_x32(ra, rb, g, tol);
     sm.fx[ty][tx] = FaceR32{fw, ra.h};
     if (i == 0) brate += fw.h * d.dy;
-    if (east_edge) {
-      revise_face32(rE, sm.he[ty], tol, ra, rb);
-      hEo = ra.h;
-      const FaceF fe = flux_x32(ra, rb, g, tol);
-      sm.fx[ty][tx + 1] = FaceR32{fe, ra.h};
-      if (i == d.nx - 1) brate -= fe.h * d.dy;
-    }
     const RecF& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
     revise_face32(Ls, rS, tol, ra, rb);
     hSo = rb.h;
     const FaceF fs = flux_y32(ra, rb, g, tol);
     sm.fy[ty][tx] = FaceR32{fs, ra.h};
     if (j == 0) brate += fs.h * d.dx;
-    if (north_edge) {
-      revise_face32(rN, sm.hn[tx], tol, ra, rb);
-      hNo = ra.h;
+  }
+  {
+    const int t = ty * BX + tx;
+    const int ni = d.nx - bx * BX < BX ? d.nx - bx * BX : BX;
+    const int nj = d.ny - by * BY < BY ? d.ny - by * BY : BY;
+    LimF ra, rb;
+    if (t < nj) {
+      revise_face32(sm.e[t][ni - 1], sm.he[t], tol, ra, rb);
+      const FaceF fe = flux_x32(ra, rb, g, tol);
+      sm.fx[t][ni] = FaceR32{fe, ra.h};
+      if (bx * BX + ni == d.nx) brate -= fe.h * d.dy;
+    } else if (t >= BY && t < BY + ni) {
+      const int q = t - BY;
+      revise_face32(sm.n[nj - 1][q], sm.hn[q], tol, ra, rb);
       const FaceF fn = flux_y32(ra, rb, g, tol);
-      sm.fy[ty + 1][tx] = FaceR32{fn, ra.h};
-      if (j == d.ny - 1) brate -= fn.h * d.dx;
+      sm.fy[nj][q] = FaceR32{fn, ra.h};
+      if (by * BY + nj == d.ny) brate -= fn.h * d.dx;
     }
   }
   __syncthreads();
@@ -749,8 +752,7 @@ __device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>&
     const FaceR32 rEf = sm.fx[ty][tx + 1], rWf = sm.fx[ty][tx];
     const FaceR32 rNf = sm.fy[ty + 1][tx], rSf = sm.fy[ty][tx];
     const FaceF fE = rEf.f, fW = rWf.f, gN = rNf.f, gS = rSf.f;
-    if (!east_edge) hEo = rEf.ha;
-    if (!north_edge) hNo = rNf.ha;
+    const float hEo = rEf.ha, hNo = rNf.ha;
     const float FEh = fE.h, FEx = fE.n, FEy = fE.t;
     const float FWh = fW.h, FWx = fW.n + fW.dp, FWy = fW.t;
     const float GNh = gN.h, GNx = gN.t, GNy = gN.n;
