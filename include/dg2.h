@@ -305,7 +305,10 @@ int dg2_ens_destroy(dg2_ens *ens);
  * every cell and dJ/dq for every hydrograph knot discharge, by a reverse
  * sweep through each step's stages with the wet-dry, revision, HLL-regime
  * and ghost branches of the forward state frozen, and binomial checkpointing
- * of the step states in nsnap snapshot slots.  Rain and point sources are not
+ * of the step states in nsnap snapshot slots.  Under the default face revision
+ * each face's revision depends on both cells' four depth limits (the partially
+ * wet scale) and the cell's own terms on its faces' revised depths and beds;
+ * both enter the reverse sweep.  Rain and point sources are not
  * part of the problem.  Planes are dense (ny rows of nx, x fastest).
  * ---------------------------------------------------------------------- */
 typedef struct dg2_adj dg2_adj;
@@ -314,11 +317,10 @@ typedef struct dg2_adj dg2_adj;
  * max_gauges >= 0).  About (nsnap + 10) state-sized buffers of 9 planes. */
 size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps);
 
-/* params: g, tol_dry, bc[4] are used; variant must be DG2_NL, precision
- * DG2_FP64, flux DG2_HLL, scheme DG2_SCHEME_DG2 and wetdry DG2_WD_PRINTED (the
- * step's face revision is Sec. 2.1.2 as printed, which equals the default
- * revision wherever no cell is partially wet); DG2_E_ARG otherwise.
- * Workspace and stream as for dg2_init_grid. */
+/* params: g, tol_dry, bc[4] and wetdry (the step's face revision, either) are
+ * used; variant must be DG2_NL, precision DG2_FP64, flux DG2_HLL and scheme
+ * DG2_SCHEME_DG2 (DG2_E_ARG otherwise).  Workspace and stream as for
+ * dg2_init_grid. */
 int dg2_adj_create(dg2_adj **out, int nx, int ny, double dx, double dy, const dg2_params *params,
                    int nsnap, int max_gauges, int max_steps, void *dev_workspace,
                    size_t ws_bytes, void *cuda_stream);

@@ -569,21 +569,21 @@ class Adjoint:
     """Discrete adjoint of the FP64 DG2-NL step for one problem built from an
     inputs.Case (DEM, initial water, edges, its first inflow, gauges): the misfit of
     sampled gauge depths against observations and its gradients with respect to the
-    Manning n of every cell and the inflow knot discharges.  The step is the one with
-    the face revision of Sec. 2.1.2 as printed (DG2_WD_PRINTED), which is the default
-    step wherever no cell is partially wet."""
+    Manning n of every cell and the inflow knot discharges, for the step with the
+    default face revision or (wetdry=DG2_WD_PRINTED) Sec. 2.1.2 as printed."""
 
-    def __init__(self, case, *, nsnap=64, max_steps=100000, stream=None, device=None):
+    def __init__(self, case, *, nsnap=64, max_steps=100000, wetdry=DG2_WD_POSITIVE, stream=None,
+                 device=None):
         import torch
         self.case = case
         self.nx, self.ny = case.nx, case.ny
-        ref = solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, wetdry=DG2_WD_PRINTED)
+        ref = solver_from_case(case, variant=DG2_NL, precision=DG2_FP64, wetdry=wetdry)
         z3, st = ref.topo(), ref.state()
         t0 = ref.time()[0]
         ref.close()
         p = dg2_default_params()
         p.cfl, p.dt_max = case.cfl, case.dt_max
-        p.wetdry = DG2_WD_PRINTED
+        p.wetdry = int(wetdry)
         for k in range(4):
             p.bc[k] = int(case.bc[k])
         g = np.zeros((0, 2)) if case.gauges is None else np.asarray(case.gauges, dtype=np.float64)

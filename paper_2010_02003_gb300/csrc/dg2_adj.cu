@@ -260,6 +260,112 @@ __device__ __forceinline__ F3T<T> phys_t(const T& h, const T& qx, const T& qy, d
 }
 
 // ---------------------------------------------------------------------------
+// Face records and their revision (Sec. 2.1.2 and its positivity-consistent
+// reading for partially wet cells, with the desingularised velocity of thin
+// face limits), templated like the functions above; operation order as the
+// CPU oracle's cell_recs / face_revise.
+// ---------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ T pos_t(const T& x) {
+  const T zero = T(x - x);
+  return val(x) > 0.0 ? x : zero;
+}
+
+// x with its value replaced by v (derivatives kept): the cell mean depth h0 is
+// the mode the forward holds, its derivative that of (hE + hW) / 2.
+__device__ __forceinline__ double with_value(double, double v) { return v; }
+template <int N>
+__device__ __forceinline__ Dual<N> with_value(Dual<N> x, double v) {
+  x.v = v;
+  return x;
+}
+
+template <class T>
+struct RecT {
+  T h, u, v, hs;  // planar depth limit, velocities, the depth the face may draw on
+  double zf;      // continuous face bed
+  bool pw;        // the side's cell is partially wet
+};
+
+// Partially wet test and depth scale from the cell's mean depth and its four
+// planar depth limits (summed W, E, S, N); wd = 0 keeps the printed revision.
+template <class T>
+__device__ __forceinline__ bool pw_scale_t(const T& h0, const T& hW, const T& hE, const T& hS,
+                                           const T& hN, double tol, int wd, T& sc) {
+  const T zero = T(h0 - h0);
+  sc = zero + 1.0;
+  if (!wd || !(val(h0) > tol)) return false;
+  if (!(val(hW) < 0.0 || val(hE) < 0.0 || val(hS) < 0.0 || val(hN) < 0.0)) return false;
+  T sum = zero;
+  sum = sum + pos_t(hW);
+  sum = sum + pos_t(hE);
+  sum = sum + pos_t(hS);
+  sum = sum + pos_t(hN);
+  sc = h0 / (0.25 * sum);
+  return true;
+}
+
+// Record of a side with planar limit (h, qx, qy) over face bed zf; velocities by
+// the tol rule, or desingularised below eps = h0 / 10 (thin: default revision).
+template <class T>
+__device__ __forceinline__ RecT<T> make_rec_t(const T& h, const T& qx, const T& qy, double zf,
+                                              bool pw, const T& sc, double tol, bool thin,
+                                              const T& h0) {
+  const T zero = T(h - h);
+  RecT<T> r;
+  r.h = h;
+  r.u = zero;
+  r.v = zero;
+  r.zf = zf;
+  r.pw = pw;
+  const T eps = 0.1 * h0;
+  if (thin && val(eps) > tol && val(h) < val(eps)) {
+    const T hp = pos_t(h);
+    const T den = h * h + eps * eps;
+    r.u = 2.0 * hp * qx / den;
+    r.v = 2.0 * hp * qy / den;
+  } else if (val(h) > tol) {
+    r.u = qx / h;
+    r.v = qy / h;
+  }
+  const T hp = pos_t(h);
+  r.hs = pw ? sc * hp : hp;
+  return r;
+}
+
+// Revision of the face between lower side a and upper side b: the flux's
+// states and each side's revised depth and bed level for its own terms.
+template <class T>
+__device__ __forceinline__ void revise_face_t(const RecT<T>& a, const RecT<T>& b, double tol,
+                                              LimT<T>& ra, LimT<T>& rb, T& ha, T& za, T& hb,
+                                              T& zb) {
+  const T zero = T(a.h - a.h);
+  if (!a.pw && !b.pw) {
+    ha = a.hs;
+    hb = b.hs;
+    za = a.zf - (val(a.h) < 0.0 ? -a.h : zero);
+    zb = b.zf - (val(b.h) < 0.0 ? -b.h : zero);
+  } else {
+    const T ea = a.pw ? a.h + a.zf : a.zf + a.hs;
+    const T eb = b.pw ? b.h + b.zf : b.zf + b.hs;
+    const T oa = a.pw ? ea - a.hs : zero + a.zf;
+    const T ob = b.pw ? eb - b.hs : zero + b.zf;
+    const T zs = val(oa) > val(ob) ? oa : ob;
+    const T da = ea - zs, db = eb - zs;
+    ha = pos_t(da);
+    hb = pos_t(db);
+    za = zs - (val(da) < 0.0 ? -da : zero);
+    zb = zs - (val(db) < 0.0 ? -db : zero);
+  }
+  // the flux's velocities follow the tol rule on the revised depth
+  ra.h = ha; ra.qx = ha * a.u; ra.qy = ha * a.v;
+  ra.u = val(ha) > tol ? a.u : zero; ra.v = val(ha) > tol ? a.v : zero;
+  rb.h = hb; rb.qx = hb * b.u; rb.qy = hb * b.v;
+  rb.u = val(hb) > tol ? b.u : zero; rb.v = val(hb) > tol ? b.v : zero;
+}
+
+// ---------------------------------------------------------------------------
 // Problem description
 // ---------------------------------------------------------------------------
 
@@ -276,6 +382,7 @@ struct Prob {
   const double* Z;             // 3 planes z0, z1x, z1y
   const double* Nm;            // Manning n
   double rain, rain_t0, rain_t1;
+  int wd;                      // 1: positivity-consistent revision (default), 0: printed
 };
 
 __device__ __forceinline__ bool on_inflow(const Prob& p, int edge, double s) {
@@ -320,20 +427,34 @@ __device__ __forceinline__ void raw_limit(const double* __restrict__ U, long lon
   qy = U[6 * N + c] + sg * U[(6 + m) * N + c];
 }
 
-// Cell's own terms of Eqs. 4-5 from its four raw limits (fluxes excluded):
-// revisions, z* of each face, dummy modes, Gauss-point fluxes and bed terms.
+// The four face records of cell c (faces 0 E, 1 W, 2 N, 3 S) from its raw
+// limits and mean depth h0.
 template <class T>
-__device__ __forceinline__ void own_terms(const Prob& p, long long c, const T* E, const T* W,
-                                          const T* Nn, const T* S, T* L) {
+__device__ __forceinline__ void cell_recs_t(const Prob& p, long long c, const T* E, const T* W,
+                                            const T* Nn, const T* S, const T& h0, RecT<T>* r) {
   const double z0 = p.Z[c], z1x = p.Z[p.N + c], z1y = p.Z[2 * p.N + c];
-  const T zero = T(E[0] - E[0]);
-  const LimT<T> Es = revise_t(E[0], E[1], E[2], p.tol), Ws = revise_t(W[0], W[1], W[2], p.tol);
-  const LimT<T> Ns = revise_t(Nn[0], Nn[1], Nn[2], p.tol), Ss = revise_t(S[0], S[1], S[2], p.tol);
-  const T zE = (z0 + z1x) - (val(E[0]) < 0.0 ? -E[0] : zero);
-  const T zW = (z0 - z1x) - (val(W[0]) < 0.0 ? -W[0] : zero);
-  const T zN = (z0 + z1y) - (val(Nn[0]) < 0.0 ? -Nn[0] : zero);
-  const T zS = (z0 - z1y) - (val(S[0]) < 0.0 ? -S[0] : zero);
-  const T zb1x = 0.5 * (zE - zW), zb1y = 0.5 * (zN - zS);
+  T sc;
+  const bool pw = pw_scale_t(h0, W[0], E[0], S[0], Nn[0], p.tol, p.wd, sc);
+  const bool thin = p.wd != 0;
+  r[0] = make_rec_t(E[0], E[1], E[2], z0 + z1x, pw, sc, p.tol, thin, h0);
+  r[1] = make_rec_t(W[0], W[1], W[2], z0 - z1x, pw, sc, p.tol, thin, h0);
+  r[2] = make_rec_t(Nn[0], Nn[1], Nn[2], z0 + z1y, pw, sc, p.tol, thin, h0);
+  r[3] = make_rec_t(S[0], S[1], S[2], z0 - z1y, pw, sc, p.tol, thin, h0);
+}
+
+// Cell's own terms of Eqs. 4-5 (fluxes excluded) from its revised face depths
+// h*, bed levels z* and face velocities (u, v): dummy modes, Gauss-point
+// fluxes and bed terms.
+template <class T>
+__device__ __forceinline__ void own_terms(const Prob& p, const T* hs, const T* zs, const T* u,
+                                          const T* v, T* L) {
+  const T zero = T(hs[0] - hs[0]);
+  LimT<T> Es, Ws, Ns, Ss;
+  Es.h = hs[0]; Es.qx = hs[0] * u[0]; Es.qy = hs[0] * v[0];
+  Ws.h = hs[1]; Ws.qx = hs[1] * u[1]; Ws.qy = hs[1] * v[1];
+  Ns.h = hs[2]; Ns.qx = hs[2] * u[2]; Ns.qy = hs[2] * v[2];
+  Ss.h = hs[3]; Ss.qx = hs[3] * u[3]; Ss.qy = hs[3] * v[3];
+  const T zb1x = 0.5 * (zs[0] - zs[1]), zb1y = 0.5 * (zs[2] - zs[3]);
   const T h0x = 0.5 * (Es.h + Ws.h), x0x = 0.5 * (Es.qx + Ws.qx), y0x = 0.5 * (Es.qy + Ws.qy);
   const T h1x = 0.5 * (Es.h - Ws.h), x1x = 0.5 * (Es.qx - Ws.qx), y1x = 0.5 * (Es.qy - Ws.qy);
   const T h0y = 0.5 * (Ns.h + Ss.h), x0y = 0.5 * (Ns.qx + Ss.qx), y0y = 0.5 * (Ns.qy + Ss.qy);
@@ -356,44 +477,64 @@ __device__ __forceinline__ void own_terms(const Prob& p, long long c, const T* E
   L[QY1Y] = k3y * (-(Gp.y + Gm.y) + g23 * h1y * zb1y);
 }
 
-// Flux of the face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at
-// stage time with hydrograph discharge Q, in double.
-__device__ F3T<double> face_flux(const Prob& p, const double* __restrict__ U, int i, int j, int f,
-                                 double Q) {
+// Records of cell (i, j) of state U in double.
+__device__ __forceinline__ void recs_double(const Prob& p, const double* __restrict__ U, long long c,
+                                            RecT<double>* r) {
+  double E[3], W[3], Nn[3], S[3];
+  raw_limit(U, p.N, c, 0, E[0], E[1], E[2]);
+  raw_limit(U, p.N, c, 1, W[0], W[1], W[2]);
+  raw_limit(U, p.N, c, 2, Nn[0], Nn[1], Nn[2]);
+  raw_limit(U, p.N, c, 3, S[0], S[1], S[2]);
+  cell_recs_t<double>(p, c, E, W, Nn, S, U[c], r);
+}
+
+// Face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at stage time
+// with hydrograph discharge Q, in double: its flux and the own side's revised
+// depth and bed level.
+__device__ void face_rev(const Prob& p, const double* __restrict__ U, int i, int j, int f, double Q,
+                         const RecT<double>* own, F3T<double>& F, double& ho, double& zo) {
   const long long N = p.N, c = (long long)j * p.nx + i;
-  double oh, ox, oy;  // own raw limit at the face
-  raw_limit(U, N, c, f, oh, ox, oy);
-  double nh, nxq, nyq;  // other side
+  RecT<double> oth;
   const bool edge = (f == 0 && i == p.nx - 1) || (f == 1 && i == 0) || (f == 2 && j == p.ny - 1) ||
                     (f == 3 && j == 0);
   if (edge) {
-    nh = oh; nxq = ox; nyq = oy;
+    double h, qx, qy;
+    raw_limit(U, N, c, f, h, qx, qy);
     const int e = f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2;
     const double s = f <= 1 ? (j + 0.5) * p.dy : (i + 0.5) * p.dx;
-    ghost_t<double>(p, e, s, Q, nh, nxq, nyq);
+    ghost_t<double>(p, e, s, Q, h, qx, qy);
+    oth = make_rec_t<double>(h, qx, qy, own[f].zf, false, 1.0, p.tol, false, 0.0);
   } else {
     const long long cn = f == 0 ? c + 1 : f == 1 ? c - 1 : f == 2 ? c + p.nx : c - p.nx;
-    raw_limit(U, N, cn, f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2, nh, nxq, nyq);
+    RecT<double> nr[4];
+    recs_double(p, U, cn, nr);
+    oth = nr[f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2];
   }
-  const LimT<double> own = revise_t(oh, ox, oy, p.tol), oth = revise_t(nh, nxq, nyq, p.tol);
-  const bool y = f >= 2;
-  // left/lower side first
-  if (f == 0 || f == 2) return flux_face(own, oth, y, p.g, p.tol);
-  return flux_face(oth, own, y, p.g, p.tol);
+  LimT<double> ra, rb;
+  double ha, za, hb, zb;
+  const bool own_lower = f == 0 || f == 2;
+  if (own_lower) revise_face_t(own[f], oth, p.tol, ra, rb, ha, za, hb, zb);
+  else revise_face_t(oth, own[f], p.tol, ra, rb, ha, za, hb, zb);
+  F = flux_face(ra, rb, f >= 2, p.g, p.tol);
+  ho = own_lower ? ha : hb;
+  zo = own_lower ? za : zb;
 }
 
 // L(U) at cell (i, j) in double (Eq. 4 with the fluxes of its four faces).
 __device__ void cell_operator(const Prob& p, const double* __restrict__ U, int i, int j, double t,
                               double Q, double* L) {
-  const long long N = p.N, c = (long long)j * p.nx + i;
-  double E[3], W[3], Nn[3], S[3];
-  raw_limit(U, N, c, 0, E[0], E[1], E[2]);
-  raw_limit(U, N, c, 1, W[0], W[1], W[2]);
-  raw_limit(U, N, c, 2, Nn[0], Nn[1], Nn[2]);
-  raw_limit(U, N, c, 3, S[0], S[1], S[2]);
-  own_terms<double>(p, c, E, W, Nn, S, L);
-  const F3T<double> FE = face_flux(p, U, i, j, 0, Q), FW = face_flux(p, U, i, j, 1, Q);
-  const F3T<double> GN = face_flux(p, U, i, j, 2, Q), GS = face_flux(p, U, i, j, 3, Q);
+  const long long c = (long long)j * p.nx + i;
+  RecT<double> r[4];
+  recs_double(p, U, c, r);
+  F3T<double> F[4];
+  double hs[4], zs[4], u[4], v[4];
+  for (int f = 0; f < 4; ++f) {
+    face_rev(p, U, i, j, f, Q, r, F[f], hs[f], zs[f]);
+    u[f] = r[f].u;
+    v[f] = r[f].v;
+  }
+  own_terms<double>(p, hs, zs, u, v, L);
+  const F3T<double> FE = F[0], FW = F[1], GN = F[2], GS = F[3];
   const double idx = p.inv_dx, idy = p.inv_dy, k3x = -3.0 * idx, k3y = -3.0 * idy;
   L[H0] += -(FE.h - FW.h) * idx - (GN.h - GS.h) * idy;
   L[QX0] += -(FE.x - FW.x) * idx - (GN.x - GS.x) * idy;
@@ -550,18 +691,101 @@ __device__ __forceinline__ void stage_mu(const double* __restrict__ lam, const u
   for (int k = 0; k < 9; ++k) mu[k] = ((m >> k) & 1u) ? w * lam[k * N + c] : 0.0;
 }
 
+// Per-cell pass of a stage, before the faces: the Jacobian of the cell's own
+// terms (Eqs. 4-5 without the fluxes) with respect to its 12 raw limits
+// (faces E, W, N, S; h, qx, qy each) and to the revised depth h* and bed z* of
+// each of its four faces.  Writes OWN planes 0..11 (the raw limits' adjoints)
+// and 12..19 (h*, z* of faces E, W, N, S).
+__global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const double* __restrict__ lam,
+                               const unsigned short* __restrict__ mask, double w, double Q,
+                               double* __restrict__ OWN) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const long long N = p.N;
+  const int i = (int)(c % p.nx), j = (int)(c / p.nx);
+  double mu[9];
+  stage_mu(lam, mask, N, c, w, mu);
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) any = any || mu[k] != 0.0;
+  if (!any) {
+    for (int q = 0; q < 20; ++q) OWN[q * N + c] = 0.0;
+    return;
+  }
+  double lim[4][3];
+  for (int f = 0; f < 4; ++f) raw_limit(In, N, c, f, lim[f][0], lim[f][1], lim[f][2]);
+  // the faces' revised depths and beds at this state
+  double hsv[4], zsv[4];
+  {
+    RecT<double> r[4];
+    recs_double(p, In, c, r);
+    for (int f = 0; f < 4; ++f) {
+      F3T<double> F;
+      face_rev(p, In, i, j, f, Q, r, F, hsv[f], zsv[f]);
+    }
+  }
+  // pass 1: the 12 raw limits (h*, z* held)
+  {
+    Dual<12> dl[4][3];
+    for (int f = 0; f < 4; ++f)
+      for (int k = 0; k < 3; ++k) dl[f][k] = var<12>(lim[f][k], 3 * f + k);
+    const Dual<12> h0 = with_value(0.5 * (dl[0][0] + dl[1][0]), In[c]);
+    RecT<Dual<12>> r[4];
+    cell_recs_t<Dual<12>>(p, c, dl[0], dl[1], dl[2], dl[3], h0, r);
+    Dual<12> hs[4], zs[4], u[4], v[4], L[9];
+    for (int f = 0; f < 4; ++f) {
+      hs[f] = cst<12>(hsv[f]);
+      zs[f] = cst<12>(zsv[f]);
+      u[f] = r[f].u;
+      v[f] = r[f].v;
+    }
+    own_terms<Dual<12>>(p, hs, zs, u, v, L);
+    for (int q = 0; q < 12; ++q) {
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
+      OWN[q * N + c] = a;
+    }
+  }
+  // pass 2: the faces' h* and z* (face velocities held)
+  {
+    RecT<double> r[4];
+    recs_double(p, In, c, r);
+    Dual<8> hs[4], zs[4], u[4], v[4], L[9];
+    for (int f = 0; f < 4; ++f) {
+      hs[f] = var<8>(hsv[f], 2 * f);
+      zs[f] = var<8>(zsv[f], 2 * f + 1);
+      u[f] = cst<8>(r[f].u);
+      v[f] = cst<8>(r[f].v);
+    }
+    own_terms<Dual<8>>(p, hs, zs, u, v, L);
+    for (int q = 0; q < 8; ++q) {
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
+      OWN[(12 + q) * N + c] = a;
+    }
+  }
+}
+
 // One pass over the faces of a stage: face (left/lower cell a, right/upper cell
 // b) of direction dir (0 x, 1 y); index f runs over (nx+1) * ny x-faces or
-// nx * (ny+1) y-faces.  Writes the adjoint of each side's raw limit (the
-// boundary side folded into the own cell's limit) and, for inflow faces, the
-// adjoint of the hydrograph discharge.
+// nx * (ny+1) y-faces.  The face's outputs are its flux (adjoint phi from both
+// cells' operator adjoints) and each side's revised depth and bed (adjoints
+// from OWN); its inputs per side are the cell's four depth limits (E, W, N, S:
+// they set the partially wet scale) and its discharge limits at this face.
+// Writes the six input adjoints of each side (FL: a, FR: b; the boundary side
+// folded into the own cell) and, for inflow faces, the adjoint of the
+// hydrograph discharge.
 __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
                                 const double* __restrict__ lam, const unsigned short* __restrict__ mask,
-                                double w, double Q, double* __restrict__ FL, double* __restrict__ FR,
+                                double w, double Q, const double* __restrict__ OWN,
+                                double* __restrict__ FL, double* __restrict__ FR,
                                 double* __restrict__ gq_face) {
   const long long nfx = (long long)(p.nx + 1) * p.ny, nfy = (long long)p.nx * (p.ny + 1);
+  const long long nf = dir == 0 ? nfx : nfy;
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= (dir == 0 ? nfx : nfy)) return;
+  if (f >= nf) return;
   int i, j;  // cell on the right / upper side (may be outside)
   if (dir == 0) { i = (int)(f % (p.nx + 1)); j = (int)(f / (p.nx + 1)); }
   else { i = (int)(f % p.nx); j = (int)(f / p.nx); }
@@ -571,71 +795,127 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
   const long long cb = (long long)j * p.nx + i;
   const long long ca = dir == 0 ? cb - 1 : cb - p.nx;
   const double inv = dir == 0 ? p.inv_dx : p.inv_dy;
-  const int l1 = dir == 0 ? 1 : 2;  // slope mode of the direction
-  // phi = dJ/dF for the face's three flux components
-  double phi[3] = {0.0, 0.0, 0.0};
+  const int l1 = dir == 0 ? 1 : 2;            // slope mode of the direction
+  const int fa = dir == 0 ? 0 : 2, fb = dir == 0 ? 1 : 3;  // the face as seen from a and b
+  // adjoints of the outputs: flux (3), a's h* and z*, b's h* and z*
+  double phi[3] = {0.0, 0.0, 0.0}, pha = 0.0, pza = 0.0, phb = 0.0, pzb = 0.0;
   double mua[9], mub[9];
   if (has_a) {
     stage_mu(lam, mask, N, ca, w, mua);
     for (int v = 0; v < 3; ++v) phi[v] += -mua[3 * v] * inv - 3.0 * inv * mua[3 * v + l1];
+    pha = OWN[(12 + 2 * fa) * N + ca];
+    pza = OWN[(13 + 2 * fa) * N + ca];
   }
   if (has_b) {
     stage_mu(lam, mask, N, cb, w, mub);
     for (int v = 0; v < 3; ++v) phi[v] += mub[3 * v] * inv - 3.0 * inv * mub[3 * v + l1];
+    phb = OWN[(12 + 2 * fb) * N + cb];
+    pzb = OWN[(13 + 2 * fb) * N + cb];
   }
-  double la[3] = {0.0, 0.0, 0.0}, lb[3] = {0.0, 0.0, 0.0}, gq = 0.0;
+  double la[6] = {0, 0, 0, 0, 0, 0}, lb[6] = {0, 0, 0, 0, 0, 0}, gq = 0.0;
+  const bool any = phi[0] != 0.0 || phi[1] != 0.0 || phi[2] != 0.0 || pha != 0.0 || pza != 0.0 ||
+                   phb != 0.0 || pzb != 0.0;
   const bool y = dir == 1;
-  if (has_a && has_b) {
-    double a3[3], b3[3];
-    raw_limit(In, N, ca, dir == 0 ? 0 : 2, a3[0], a3[1], a3[2]);
-    raw_limit(In, N, cb, dir == 0 ? 1 : 3, b3[0], b3[1], b3[2]);
-    Dual<6> A[3], Bv[3];
-    for (int k = 0; k < 3; ++k) { A[k] = var<6>(a3[k], k); Bv[k] = var<6>(b3[k], 3 + k); }
-    const LimT<Dual<6>> La = revise_t(A[0], A[1], A[2], p.tol), Lb = revise_t(Bv[0], Bv[1], Bv[2], p.tol);
-    const F3T<Dual<6>> F = flux_face(La, Lb, y, p.g, p.tol);
-    for (int k = 0; k < 3; ++k) {
-      la[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k];
-      lb[k] = phi[0] * F.h.d[3 + k] + phi[1] * F.x.d[3 + k] + phi[2] * F.y.d[3 + k];
+  if (any && has_a && has_b) {
+    double ha4[4], hb4[4], qa[3], qb[3];
+    for (int q = 0; q < 4; ++q) {
+      double t1, t2;
+      raw_limit(In, N, ca, q, ha4[q], t1, t2);
+      raw_limit(In, N, cb, q, hb4[q], t1, t2);
     }
-  } else {
+    raw_limit(In, N, ca, fa, qa[0], qa[1], qa[2]);
+    raw_limit(In, N, cb, fb, qb[0], qb[1], qb[2]);
+    const double za0 = p.Z[ca] + p.Z[l1 * N + ca], zb0 = p.Z[cb] - p.Z[l1 * N + cb];
+    // two passes of six derivatives: side a's inputs, then side b's
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      Dual<6> A[4], Bv[4], aqx, aqy, bqx, bqy;
+      for (int q = 0; q < 4; ++q) {
+        A[q] = side == 0 ? var<6>(ha4[q], q) : cst<6>(ha4[q]);
+        Bv[q] = side == 1 ? var<6>(hb4[q], q) : cst<6>(hb4[q]);
+      }
+      aqx = side == 0 ? var<6>(qa[1], 4) : cst<6>(qa[1]);
+      aqy = side == 0 ? var<6>(qa[2], 5) : cst<6>(qa[2]);
+      bqx = side == 1 ? var<6>(qb[1], 4) : cst<6>(qb[1]);
+      bqy = side == 1 ? var<6>(qb[2], 5) : cst<6>(qb[2]);
+      const Dual<6> h0a = with_value(0.5 * (A[0] + A[1]), In[ca]);
+      const Dual<6> h0b = with_value(0.5 * (Bv[0] + Bv[1]), In[cb]);
+      Dual<6> sca, scb;
+      const bool pwa = pw_scale_t(h0a, A[1], A[0], A[3], A[2], p.tol, p.wd, sca);
+      const bool pwb = pw_scale_t(h0b, Bv[1], Bv[0], Bv[3], Bv[2], p.tol, p.wd, scb);
+      const RecT<Dual<6>> Ra = make_rec_t(A[fa], aqx, aqy, za0, pwa, sca, p.tol, p.wd != 0, h0a);
+      const RecT<Dual<6>> Rb = make_rec_t(Bv[fb], bqx, bqy, zb0, pwb, scb, p.tol, p.wd != 0, h0b);
+      LimT<Dual<6>> ra, rb;
+      Dual<6> ha, za, hb, zb;
+      revise_face_t(Ra, Rb, p.tol, ra, rb, ha, za, hb, zb);
+      const F3T<Dual<6>> F = flux_face(ra, rb, y, p.g, p.tol);
+      double* out = side == 0 ? la : lb;
+      for (int k = 0; k < 6; ++k)
+        out[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pha * ha.d[k] +
+                 pza * za.d[k] + phb * hb.d[k] + pzb * zb.d[k];
+    }
+  } else if (!(has_a && has_b)) {
     // boundary face: the outside state is the ghost of the inside cell's limit
     const bool inside_b = has_b;
     const long long c = inside_b ? cb : ca;
     const int ci = inside_b ? i : (dir == 0 ? i - 1 : i);
     const int cj = inside_b ? j : (dir == 0 ? j : j - 1);
-    const int face = dir == 0 ? (inside_b ? 1 : 0) : (inside_b ? 3 : 2);  // own face
+    const int fo = inside_b ? fb : fa;  // own face
     const int edge = dir == 0 ? (inside_b ? 0 : 1) : (inside_b ? 2 : 3);
     const double s = dir == 0 ? (cj + 0.5) * p.dy : (ci + 0.5) * p.dx;
-    double o3[3];
-    raw_limit(In, N, c, face, o3[0], o3[1], o3[2]);
-    Dual<4> O[3], G[3];
-    for (int k = 0; k < 3; ++k) { O[k] = var<4>(o3[k], k); G[k] = O[k]; }
-    const Dual<4> Qd = var<4>(Q, 3);
-    ghost_t(p, edge, s, Qd, G[0], G[1], G[2]);
-    const LimT<Dual<4>> Lo = revise_t(O[0], O[1], O[2], p.tol), Lg = revise_t(G[0], G[1], G[2], p.tol);
-    const F3T<Dual<4>> F = inside_b ? flux_face(Lg, Lo, y, p.g, p.tol) : flux_face(Lo, Lg, y, p.g, p.tol);
-    double lo[3];
-    for (int k = 0; k < 3; ++k) lo[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k];
-    gq = phi[0] * F.h.d[3] + phi[1] * F.x.d[3] + phi[2] * F.y.d[3];
-    for (int k = 0; k < 3; ++k) { if (inside_b) lb[k] = lo[k]; else la[k] = lo[k]; }
+    const double pho = inside_b ? phb : pha, pzo = inside_b ? pzb : pza;
+    if (any) {
+      double h4[4], qo[3];
+      for (int q = 0; q < 4; ++q) {
+        double t1, t2;
+        raw_limit(In, N, c, q, h4[q], t1, t2);
+      }
+      raw_limit(In, N, c, fo, qo[0], qo[1], qo[2]);
+      Dual<7> O[4];
+      for (int q = 0; q < 4; ++q) O[q] = var<7>(h4[q], q);
+      const Dual<7> oqx = var<7>(qo[1], 4), oqy = var<7>(qo[2], 5), Qd = var<7>(Q, 6);
+      const Dual<7> h0 = with_value(0.5 * (O[0] + O[1]), In[c]);
+      Dual<7> sc;
+      const bool pw = pw_scale_t(h0, O[1], O[0], O[3], O[2], p.tol, p.wd, sc);
+      const double sg = (fo == 0 || fo == 2) ? 1.0 : -1.0;
+      const double zf = p.Z[c] + sg * p.Z[l1 * N + c];
+      const RecT<Dual<7>> Ro = make_rec_t(O[fo], oqx, oqy, zf, pw, sc, p.tol, p.wd != 0, h0);
+      Dual<7> G[3] = {O[fo], oqx, oqy};
+      ghost_t(p, edge, s, Qd, G[0], G[1], G[2]);
+      const RecT<Dual<7>> Rg = make_rec_t(G[0], G[1], G[2], zf, false, h0 - h0 + 1.0, p.tol, false,
+                                          h0);
+      LimT<Dual<7>> ra, rb;
+      Dual<7> ha, za, hb, zb;
+      if (inside_b) revise_face_t(Rg, Ro, p.tol, ra, rb, ha, za, hb, zb);
+      else revise_face_t(Ro, Rg, p.tol, ra, rb, ha, za, hb, zb);
+      const F3T<Dual<7>> F = flux_face(ra, rb, y, p.g, p.tol);
+      const Dual<7>& ho = inside_b ? hb : ha;
+      const Dual<7>& zo = inside_b ? zb : za;
+      double lo[6];
+      for (int k = 0; k < 6; ++k)
+        lo[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pho * ho.d[k] +
+                pzo * zo.d[k];
+      gq = phi[0] * F.h.d[6] + phi[1] * F.x.d[6] + phi[2] * F.y.d[6] + pho * ho.d[6] + pzo * zo.d[6];
+      for (int k = 0; k < 6; ++k) { if (inside_b) lb[k] = lo[k]; else la[k] = lo[k]; }
+    }
     // fold into the edge slot index: along-edge position
     const int pos = dir == 0 ? cj : ci;
     const int slot = edge * (p.nx > p.ny ? p.nx : p.ny) + pos;
     gq_face[slot] = gq;
   }
-  for (int k = 0; k < 3; ++k) {
-    FL[k * (dir == 0 ? nfx : nfy) + f] = la[k];
-    FR[k * (dir == 0 ? nfx : nfy) + f] = lb[k];
+  for (int k = 0; k < 6; ++k) {
+    FL[k * nf + f] = la[k];
+    FR[k * nf + f] = lb[k];
   }
 }
 
 // One pass over the cells of a stage.  Stage 2 writes lamU1 = mask2 lam2 / 2 +
 // L'(U1)^T mu2.  Stage 1 writes lamUs = mask2 lam2 / 2 + mask1 lamU1 +
 // L'(Us)^T mu1, then the friction adjoint: lam <- Fric'(U)^T lamUs and the
-// Manning gradient.
+// Manning gradient.  The raw limits' adjoints are the own terms' (OWN) plus
+// each of the four faces' for this side.
 template <int STAGE>
-__global__ void adj_cell_kernel(Prob p, const double* __restrict__ In, const double* __restrict__ lamS,
-                                const unsigned short* __restrict__ maskS, double wS,
+__global__ void adj_cell_kernel(Prob p, const double* __restrict__ OWN,
                                 const double* __restrict__ lam2, const unsigned short* __restrict__ mask2,
                                 const unsigned short* __restrict__ mask1, const double* __restrict__ lamU1,
                                 const double* __restrict__ FXL, const double* __restrict__ FXR,
@@ -647,40 +927,20 @@ __global__ void adj_cell_kernel(Prob p, const double* __restrict__ In, const dou
   const long long N = p.N;
   const int i = (int)(c % p.nx), j = (int)(c / p.nx);
   const long long nfx = (long long)(p.nx + 1) * p.ny, nfy = (long long)p.nx * (p.ny + 1);
-  double mu[9];
-  stage_mu(lamS, maskS, N, c, wS, mu);
-  // own terms: Jacobian of L_c with respect to the cell's 12 raw limits
   double lr[4][3];
-  {
-    double E[3], W[3], Nn[3], S[3];
-    raw_limit(In, N, c, 0, E[0], E[1], E[2]);
-    raw_limit(In, N, c, 1, W[0], W[1], W[2]);
-    raw_limit(In, N, c, 2, Nn[0], Nn[1], Nn[2]);
-    raw_limit(In, N, c, 3, S[0], S[1], S[2]);
-    Dual<12> dE[3], dW[3], dN[3], dS[3], L[9];
-    for (int k = 0; k < 3; ++k) {
-      dE[k] = var<12>(E[k], k);
-      dW[k] = var<12>(W[k], 3 + k);
-      dN[k] = var<12>(Nn[k], 6 + k);
-      dS[k] = var<12>(S[k], 9 + k);
-    }
-    own_terms<Dual<12>>(p, c, dE, dW, dN, dS, L);
-    for (int f = 0; f < 4; ++f)
-      for (int k = 0; k < 3; ++k) {
-        double a = 0.0;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) a += mu[q] * L[q].d[3 * f + k];
-        lr[f][k] = a;
-      }
-  }
-  // the four faces' adjoints of this cell's limits
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < 3; ++k) lr[f][k] = OWN[(3 * f + k) * N + c];
+  // faces: this cell is side a of its east and north faces, side b of its west and south
   const long long fe = (long long)j * (p.nx + 1) + i + 1, fw = (long long)j * (p.nx + 1) + i;
   const long long fn = (long long)(j + 1) * p.nx + i, fs = (long long)j * p.nx + i;
-  for (int k = 0; k < 3; ++k) {
-    lr[0][k] += FXL[k * nfx + fe];
-    lr[1][k] += FXR[k * nfx + fw];
-    lr[2][k] += FYL[k * nfy + fn];
-    lr[3][k] += FYR[k * nfy + fs];
+  const double* src[4] = {FXL, FXR, FYL, FYR};
+  const long long fi[4] = {fe, fw, fn, fs};
+  const long long fcount[4] = {nfx, nfx, nfy, nfy};
+  for (int f = 0; f < 4; ++f) {
+    const double* Fs = src[f];
+    for (int q = 0; q < 4; ++q) lr[q][0] += Fs[q * fcount[f] + fi[f]];
+    lr[f][1] += Fs[4 * fcount[f] + fi[f]];
+    lr[f][2] += Fs[5 * fcount[f] + fi[f]];
   }
   // limits -> modes: E = U0 + U1x, W = U0 - U1x, N = U0 + U1y, S = U0 - U1y
   double a[9];
@@ -763,7 +1023,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct AdjLayout {
   size_t off_Z, off_Nm, off_U0, off_snap, off_work, off_Us, off_U1, off_m1, off_m2, off_lam,
-      off_lamU1, off_tmp, off_FXL, off_FXR, off_FYL, off_FYR, off_gq_face, off_gn, off_gidx,
+      off_lamU1, off_tmp, off_own, off_FXL, off_FXR, off_FYL, off_FYR, off_gq_face, off_gn, off_gidx,
       off_gxi, off_geta, off_gh, off_gq_step, total;
   long long N, nfx, nfy, plane9;
   int nsnap, ngq;
@@ -796,10 +1056,11 @@ bool adj_layout(int nx, int ny, int nsnap, int max_gauges, int max_steps, AdjLay
   L.off_lam = take(s9);
   L.off_lamU1 = take(s9);
   L.off_tmp = take(s9);
-  L.off_FXL = take(3 * (size_t)L.nfx * sizeof(double));
-  L.off_FXR = take(3 * (size_t)L.nfx * sizeof(double));
-  L.off_FYL = take(3 * (size_t)L.nfy * sizeof(double));
-  L.off_FYR = take(3 * (size_t)L.nfy * sizeof(double));
+  L.off_own = take(20 * (size_t)L.N * sizeof(double));
+  L.off_FXL = take(6 * (size_t)L.nfx * sizeof(double));
+  L.off_FXR = take(6 * (size_t)L.nfx * sizeof(double));
+  L.off_FYL = take(6 * (size_t)L.nfy * sizeof(double));
+  L.off_FYR = take(6 * (size_t)L.nfy * sizeof(double));
   L.off_gq_face = take((size_t)L.ngq * sizeof(double));
   L.off_gn = take((size_t)L.N * sizeof(double));
   const size_t ng = max_gauges > 0 ? max_gauges : 1;
@@ -931,6 +1192,7 @@ int rev_step(dg2_adj* a, int k, const double* Uk) {
   double* lam = dptr(a, L.off_lam);
   double* lamU1 = dptr(a, L.off_lamU1);
   double* tmp = dptr(a, L.off_tmp);
+  double* OWN = dptr(a, L.off_own);
   double* FXL = dptr(a, L.off_FXL);
   double* FXR = dptr(a, L.off_FXR);
   double* FYL = dptr(a, L.off_FYL);
@@ -941,22 +1203,24 @@ int rev_step(dg2_adj* a, int k, const double* Uk) {
   const unsigned nb = blocks(L.N);
   // stage 2 at U1, time t + dt: mu2 = dt/2 mask2 lam
   ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(double), a->st));
+  adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, U1, lam, m2, 0.5 * dt, hydro(a, t + dt), OWN);
   adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
-                                                    FXL, FXR, gqf);
+                                                    OWN, FXL, FXR, gqf);
   adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
-                                                    FYL, FYR, gqf);
+                                                    OWN, FYL, FYR, gqf);
   sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k + 1);
-  adj_cell_kernel<2><<<nb, 256, 0, a->st>>>(a->p, U1, lam, m2, 0.5 * dt, lam, m2, m1, nullptr, FXL,
-                                            FXR, FYL, FYR, nullptr, dt, lamU1, gn);
+  adj_cell_kernel<2><<<nb, 256, 0, a->st>>>(a->p, OWN, lam, m2, m1, nullptr, FXL, FXR, FYL, FYR,
+                                            nullptr, dt, lamU1, gn);
   // stage 1 at Us, time t: mu1 = dt mask1 lamU1
   ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(double), a->st));
-  adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, Us, lamU1, m1, dt, hydro(a, t), FXL,
+  adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, Us, lamU1, m1, dt, hydro(a, t), OWN);
+  adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, Us, lamU1, m1, dt, hydro(a, t), OWN, FXL,
                                                     FXR, gqf);
-  adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, Us, lamU1, m1, dt, hydro(a, t), FYL,
+  adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, Us, lamU1, m1, dt, hydro(a, t), OWN, FYL,
                                                     FYR, gqf);
   sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k);
-  adj_cell_kernel<1><<<nb, 256, 0, a->st>>>(a->p, Us, lamU1, m1, dt, lam, m2, m1, lamU1, FXL, FXR,
-                                            FYL, FYR, Uk, dt, tmp, gn);
+  adj_cell_kernel<1><<<nb, 256, 0, a->st>>>(a->p, OWN, lam, m2, m1, lamU1, FXL, FXR, FYL, FYR, Uk,
+                                            dt, tmp, gn);
   ACU(cudaMemcpyAsync(lam, tmp, (size_t)L.plane9 * sizeof(double), cudaMemcpyDeviceToDevice, a->st));
   a->rev_steps++;
   return launch_ok();
@@ -1115,9 +1379,9 @@ int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg
   *out = nullptr;
   if (!prm) return afail(DG2_E_ARG, "params is null");
   if (prm->variant != DG2_NL || prm->precision != DG2_FP64 || prm->flux != DG2_HLL ||
-      prm->scheme != DG2_SCHEME_DG2 || prm->wetdry != DG2_WD_PRINTED)
-    return afail(DG2_E_ARG, "the adjoint is of the FP64 DG2-NL step with the HLL flux and the "
-                            "printed face revision (wetdry = DG2_WD_PRINTED)");
+      prm->scheme != DG2_SCHEME_DG2 ||
+      (prm->wetdry != DG2_WD_POSITIVE && prm->wetdry != DG2_WD_PRINTED))
+    return afail(DG2_E_ARG, "the adjoint is of the FP64 DG2-NL step with the HLL flux");
   if (!(dx > 0.0) || !(dy > 0.0)) return afail(DG2_E_ARG, "dx, dy must be > 0");
   AdjLayout L;
   if (!adj_layout(nx, ny, nsnap, max_gauges, max_steps, L))
@@ -1136,6 +1400,7 @@ int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg
   p.nx = nx; p.ny = ny; p.N = L.N;
   p.dx = dx; p.dy = dy; p.inv_dx = 1.0 / dx; p.inv_dy = 1.0 / dy;
   p.g = prm->g; p.tol = prm->tol_dry;
+  p.wd = prm->wetdry == DG2_WD_POSITIVE ? 1 : 0;
   for (int k = 0; k < 4; ++k) p.bc[k] = prm->bc[k];
   p.in_edge = -1;
   p.Z = dptr(a, L.off_Z);

@@ -5,9 +5,9 @@ oracle's own taped derivatives (tests/test_oracle_tape.py pins the tape against
 its finite differences), central finite differences of the GPU forward, and
 itself under every number of checkpoint slots (the gradient must not change a
 bit).  The wet-dry, revision, HLL-regime and ghost branches are frozen from the
-forward state, as the tape's are.  The step is the one with the printed face
-revision (the oracle's wetdry="paper"); this channel case has partially wet bank
-cells, where that revision differs from the default."""
+forward state, as the tape's are.  Both face revisions are checked (the default and
+the printed one, the oracle's wetdry="positive" / "paper"); this channel case has
+partially wet bank cells, where they differ."""
 import numpy as np
 import pytest
 
@@ -27,22 +27,27 @@ SAMPLES = [10, 20, 30]
 OBS = np.full((3, 3), 0.3)
 
 
-def _setup(nsnap=8):
+WD = ["positive", "paper"]
+
+
+def _setup(nsnap=8, wetdry="positive"):
     from paper_2010_02003_gb300 import binding as B
     case = _case()
     rng = np.random.default_rng(1)
     man = 0.03 + 0.02 * rng.random((case.ny, case.nx))
     case.manning = man
-    a = B.Adjoint(case, nsnap=nsnap, max_steps=64)
+    a = B.Adjoint(case, nsnap=nsnap, max_steps=64,
+                  wetdry=B.DG2_WD_POSITIVE if wetdry == "positive" else B.DG2_WD_PRINTED)
     a.set_schedule(DTS, SAMPLES, OBS)
     return case, man, a
 
 
-def test_adjoint_forward_matches_the_oracle():
+@pytest.mark.parametrize("wetdry", WD)
+def test_adjoint_forward_matches_the_oracle(wetdry):
     from conftest import make_oracle
-    case, man, a = _setup()
+    case, man, a = _setup(wetdry=wetdry)
     J, h = a.forward()
-    o = make_oracle(case, wetdry="paper")
+    o = make_oracle(case, wetdry=wetdry)
     hs = []
     for k in range(1, len(DTS) + 1):
         o.step(DTS[k - 1])
@@ -54,12 +59,13 @@ def test_adjoint_forward_matches_the_oracle():
     assert abs(J - Jo) <= 1e-12 * Jo
 
 
-def test_adjoint_gradient_matches_the_taped_oracle():
+@pytest.mark.parametrize("wetdry", WD)
+def test_adjoint_gradient_matches_the_taped_oracle(wetdry):
     import oracle
-    case, man, a = _setup()
+    case, man, a = _setup(wetdry=wetdry)
     J, gn, gq = a.gradient()
     Jt, gnt, gqt = oracle.taped_gradient(case, man, case.inflows[0].q_knots, DTS, SAMPLES, OBS,
-                                         wetdry="paper")
+                                         wetdry=wetdry)
     assert abs(J - Jt) <= 1e-12 * Jt
     assert np.abs(gnt).max() > 0
     assert np.abs(gn - gnt).max() <= 1e-9 * np.abs(gnt).max(), np.abs(gn - gnt).max()
@@ -131,6 +137,11 @@ def test_adjoint_rejects_other_forms():
     from paper_2010_02003_gb300 import binding as B
     p = B.dg2_default_params()
     p.variant = B.DG2_LL
+    with pytest.raises(B.Dg2Error) as e:
+        B.dg2_adj_create(8, 8, 1.0, 1.0, p, 4, 1, 10, 0, 0, 0)
+    assert e.value.code == B.DG2_E_ARG
+    p = B.dg2_default_params()
+    p.wetdry = 7
     with pytest.raises(B.Dg2Error) as e:
         B.dg2_adj_create(8, 8, 1.0, 1.0, p, 4, 1, 10, 0, 0, 0)
     assert e.value.code == B.DG2_E_ARG
