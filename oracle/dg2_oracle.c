@@ -13,8 +13,8 @@
  * the paper.  Compiled with -ffp-contract=off (no fused multiply-add).
  *
  * Readings where the paper is silent:
- *   - Riemann solver: HLL with Toro's wet/dry wave speeds (the paper uses Roe,
- *     Sec. 2.1.2; the HLL flux is this build's contract).
+ *   - Riemann solver: HLL with Toro's wet/dry wave speeds by default (the
+ *     paper uses Roe, Sec. 2.1.2, available as an option).
  *   - z* revision uses the cell's own limit at each of its faces (Sec. 2.1.2).
  *   - Friction: point-implicit backward Euler of S_f, once per time step
  *     before stage 1 (Sec. 2.1.3).
@@ -126,7 +126,7 @@ static st3 revise(const orc_t *o, st3 s)
 }
 
 /* HLL flux across a face normal to x, left state L, right state R.
- * Wave speeds (this build's reading; the paper names Roe): Toro's estimates,
+ * Wave speeds (not printed in the paper, which names Roe): Toro's estimates,
  * with the dry-bed forms when one side is at or below tol_dry. */
 static st3 hll_x(const orc_t *o, st3 Ls, st3 Rs)
 {
