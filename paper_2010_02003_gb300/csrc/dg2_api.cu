@@ -56,8 +56,8 @@ struct Layout {
   long long plane;
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
   size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, off_tforced,
-      off_tlist, off_tfront, off_desc, off_es, total;
-  int nblocks, mblocks;
+      off_tlist, off_tfront, off_desc, off_es, off_qm, off_busy1, total;
+  int nblocks, mblocks, nwx;
 };
 
 bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
@@ -104,6 +104,10 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   L.off_tforced = take((size_t)L.nblocks);
   L.off_tlist = take((size_t)L.nblocks * sizeof(int));
   L.off_tfront = take((size_t)L.nblocks * sizeof(int));
+  // FP64: the row-skipping masks of Un and U1 and stage 1's computed rows
+  L.nwx = (nx + 31) / 32;
+  L.off_qm = take(f32 ? 0 : 2 * (size_t)ny * L.nwx * sizeof(unsigned));
+  L.off_busy1 = take(f32 ? 0 : (size_t)L.nblocks);
   // FP32: the problem's descriptor and step counters for the shared FP32 kernels
   L.off_desc = take(f32 ? sizeof(D32) : 0);
   L.off_es = take(f32 ? sizeof(dg2::ens::EnsScalars) : 0);
@@ -316,6 +320,9 @@ void launch_mass(dg2_ctx* c) {
 // (after a new DEM or state; the first stage 2 then sets the true flags).
 int reset_tiles(dg2_ctx* c) {
   CU(cudaMemsetAsync(c->d.tiles.flag, 1, (size_t)c->lay.nblocks, c->st));
+  // every cell non-quiescent in the row masks: the first step computes every row
+  if (c->d.qm)
+    CU(cudaMemsetAsync(c->d.qm, 0xff, 2 * (size_t)c->d.qplane * sizeof(unsigned), c->st));
   launch_finalize(c, 1);
   return launch_check(c, 2);
 }
@@ -475,6 +482,10 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.tiles.ntiles = d.tiles.ntx * d.tiles.nty;
   d.tiles.all_forced = 0;
   d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
+  d.qm = c->fp32 ? nullptr : (unsigned*)(c->ws + L.off_qm);
+  d.busy1 = c->fp32 ? nullptr : (unsigned char*)(c->ws + L.off_busy1);
+  d.nwx = L.nwx;
+  d.qplane = (long long)ny * L.nwx;
   {
     D32& f = c->f;
     memset(&f, 0, sizeof f);

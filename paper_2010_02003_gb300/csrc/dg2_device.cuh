@@ -78,6 +78,17 @@ struct Scalars {
 // so a tile whose 3 x 3 tile neighbourhood holds no non-quiescent or forced
 // (inflow, point source, rain) tile is left untouched, bit for bit as if it
 // had been computed.
+//
+// The FP64 DG2 stage kernels refine this to rows of a computed tile.  Each
+// stage records, one bit per cell, which cells of its output are
+// non-quiescent (qm: plane 0 for Un, written by stage 2; plane 1 for U1,
+// written by stage 1).  A row of 32 cells with no non-quiescent input cell
+// within R cells (R = 2 for DG2-LL: a neighbour's limited slopes read its own
+// neighbours; R = 1 for DG2-NL) is a fixed point of the stage: stage 1 copies
+// it to U1, stage 2 leaves Un as it is when the row was also a fixed point of
+// stage 1 (busy1 holds stage 1's computed rows of each tile).  The tile's
+// faces are evaluated only where a computed row uses them.  Forced tiles,
+// rain and skip = 0 compute every row.
 struct Tiles {
   unsigned char* flag;          // [ntiles] tile held a non-quiescent cell after the last stage 2
   unsigned char* act;           // [ntiles] tile computed in the current step
@@ -127,6 +138,13 @@ struct Dev {
   double* samp_h;            // [max_samples][ngauge]
   int nblocks;               // blocks of the stage grid
   Tiles tiles;
+  // FP64 DG2 row skipping: non-quiescence bits, [2][ny][nwx] words of 32 cells
+  // (bit k of word (j, w): cell (32 w + k, j)), and stage 1's computed rows of
+  // each tile (bit r: row r of the tile)
+  unsigned int* qm;
+  unsigned char* busy1;
+  int nwx;
+  long long qplane;          // words per qm plane
 };
 
 // ---------------------------------------------------------------------------
@@ -784,10 +802,49 @@ __device__ __forceinline__ Rec ghost_rec(const Dev& d, int edge, double s, doubl
   return make_rec(h, qx, qy, zf, false, 1.0, d.tol);
 }
 
+// Rows of the tile (bit r: row by TY + r) with a non-quiescent cell of the
+// stage input within R cells, from the input's qm plane: the mask words of
+// rows by TY - R .. by TY + TY - 1 + R in the tile's column and its two
+// neighbours (their R nearest bits), one word per lane.  Warp-uniform; every
+// lane of the warp must call it.
+static_assert(TX == 32, "row masks hold one warp row of a tile per word");
+template <int R>
+__device__ __forceinline__ unsigned busy_rows(const Dev& d, const unsigned* __restrict__ qm, int bx,
+                                              int by) {
+  constexpr int NR = TY + 2 * R;  // mask rows read
+  constexpr int NW = 3 * NR;      // words read
+  static_assert(NW <= 64, "two words per lane at most");
+  const int lane = threadIdx.x;
+  unsigned long long nzw = 0;     // bit k: word k holds a relevant non-quiescent bit
+#pragma unroll
+  for (int k0 = 0; k0 < NW; k0 += 32) {
+    const int k = k0 + lane;
+    bool nz = false;
+    if (k < NW) {
+      const int jj = by * TY - R + k / 3, o = k % 3, w = bx + o - 1;
+      if (jj >= 0 && jj < d.ny && w >= 0 && w < d.nwx) {
+        const unsigned v = qm[(long long)jj * d.nwx + w];
+        nz = (o == 0 ? v >> (32 - R) : (o == 1 ? v : v & ((1u << R) - 1u))) != 0u;
+      }
+    }
+    nzw |= (unsigned long long)__ballot_sync(0xffffffffu, nz) << k0;
+  }
+  unsigned rows = 0;              // bit o: mask row by TY - R + o holds one
+#pragma unroll
+  for (int o = 0; o < NR; ++o)
+    if ((nzw >> (3 * o)) & 7ull) rows |= 1u << o;
+  unsigned busy = 0;
+#pragma unroll
+  for (int r = 0; r < TY; ++r)
+    if ((rows >> r) & ((1u << (2 * R + 1)) - 1u)) busy |= 1u << r;
+  return busy;
+}
+
 // One RK stage on the 32 x 8 tile (bx, by): face records, one revision and
 // one flux per face, Eqs. 4-5, the stage update and the wet-dry treatment.
 // Accumulates the boundary inflow rate, the Courant rate and the non-finite /
-// non-quiescent flags of the thread's cell into the caller's variables.
+// non-quiescent flags of the thread's cell into the caller's variables.  Rows
+// that are fixed points of the stage (see Tiles) skip the faces and Eqs. 4-5.
 template <bool LL, int STAGE>
 __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, int by,
                                            double& brate, double& lam, bool& bad, bool& nonq) {
@@ -801,10 +858,25 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   const double ts = STAGE == 1 ? sc->t : sc->t + dt;  // boundary-condition time
   const double* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const double g = d.g, tol = d.tol;
+  // rows this stage computes: all, or those near a non-quiescent input cell
+  // (stage 2: also those stage 1 computed, whose U1 may differ from Un)
+  const int tile = by * d.tiles.ntx + bx;
+  unsigned busy = (1u << TY) - 1u;
+  if (d.tiles.skip && !d.tiles.all_forced && !d.tiles.forced[tile]) {
+    busy = busy_rows<LL ? 2 : 1>(d, STAGE == 1 ? d.qm : d.qm + d.qplane, bx, by);
+    if (STAGE == 2) busy |= d.busy1[tile];
+  }
+  if (STAGE == 1 && tx == 0 && ty == 0) d.busy1[tile] = (unsigned char)busy;
+  const bool b_me = (busy >> ty) & 1u;
+  const bool b_dn = ty > 0 && ((busy >> (ty - 1)) & 1u);       // the row below
+  const bool b_up = ty + 1 < TY && ((busy >> (ty + 1)) & 1u);  // the row above
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
   Rec rE, rW, rN, rS;  // own records
-  if (act) {
+  // records: a computed row's, and those of the rows next to one (their
+  // north / south limits make the computed row's south / north face)
+  const bool recs = act && (b_me || b_dn || b_up);
+  if (recs) {
     load9(In, P, c, m);
     if (LL) {
       limited_slopes(d, In, i, j, 1, m[H1X], m[QX1X], m[QY1X]);
@@ -831,8 +903,9 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     const int t = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int ni = d.nx - i0 < TX ? d.nx - i0 : TX, nj = d.ny - j0 < TY ? d.ny - j0 : TY;
+    const bool b0 = busy & 1u, btop = (busy >> (nj - 1)) & 1u;
     if (t < TY) {
-      if (t < nj) {
+      if (t < nj && ((busy >> t) & 1u)) {
         const int jj = j0 + t;
         if (i0 == 0) {
           double h, qx, qy, zf;
@@ -844,7 +917,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY) {
       const int r = t - TY;
-      if (r < nj) {
+      if (r < nj && ((busy >> r) & 1u)) {
         const int jj = j0 + r, il = i0 + ni - 1;
         if (il == d.nx - 1) {
           double h, qx, qy, zf;
@@ -856,7 +929,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY + TX) {
       const int q = t - 2 * TY;
-      if (q < ni) {
+      if (q < ni && b0) {
         const int ii = i0 + q;
         if (j0 == 0) {
           double h, qx, qy, zf;
@@ -868,7 +941,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY + 2 * TX) {
       const int q = t - 2 * TY - TX;
-      if (q < ni) {
+      if (q < ni && btop) {
         const int ii = i0 + q, jl = j0 + nj - 1;
         if (jl == d.ny - 1) {
           double h, qx, qy, zf;
@@ -887,12 +960,15 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   // to shared memory with the flux), then the tile's east and north edge
   // faces one per thread
   double hWo = 0, zWo = 0, hSo = 0, zSo = 0;
-  if (act) {
+  if (act && b_me) {
     double ha, za;
     const Rec& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
     const F3 fw = revise_face(Lw, rW, false, g, tol, d.flux, ha, za, hWo, zWo);
     sm.fx[ty][tx] = FaceR{fw.h, fw.x, fw.y, ha, za};
     if (i == 0) brate += fw.h * d.dy;
+  }
+  if (act && (b_me || b_dn)) {
+    double ha, za;
     const Rec& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
     const F3 fs = revise_face(Ls, rS, true, g, tol, d.flux, ha, za, hSo, zSo);
     sm.fy[ty][tx] = FaceR{fs.h, fs.x, fs.y, ha, za};
@@ -904,10 +980,12 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     const int nj = d.ny - by * TY < TY ? d.ny - by * TY : TY;
     double ha, za, hb, zb;
     if (t < nj) {
+      if ((busy >> t) & 1u) {
       const F3 fe = revise_face(sm.e[t][ni - 1], sm.he[t], false, g, tol, d.flux, ha, za, hb, zb);
       sm.fx[t][ni] = FaceR{fe.h, fe.x, fe.y, ha, za};
       if (bx * TX + ni == d.nx) brate -= fe.h * d.dy;
-    } else if (t >= TY && t < TY + ni) {
+      }
+    } else if (t >= TY && t < TY + ni && ((busy >> (nj - 1)) & 1u)) {
       const int q = t - TY;
       const F3 fn = revise_face(sm.n[nj - 1][q], sm.hn[q], true, g, tol, d.flux, ha, za, hb, zb);
       sm.fy[nj][q] = FaceR{fn.h, fn.x, fn.y, ha, za};
@@ -916,7 +994,8 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   }
   __syncthreads();
 
-  if (act) {
+  bool nq_out = false;  // the cell's output is non-quiescent
+  if (act && b_me) {
     const FaceR FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
     const FaceR GS = sm.fy[ty][tx], GN = sm.fy[ty + 1][tx];
     // own side of the east / north faces: revised as their lower side
@@ -962,6 +1041,9 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       wetdry(out, z0, z1x, z1y, tol);
 #pragma unroll
       for (int k = 0; k < 9; ++k) d.T[k * P + c] = out[k];
+      nq_out = !(out[H0] <= tol);
+#pragma unroll
+      for (int k = 1; k < 9; ++k) nq_out = nq_out || out[k] != 0.0;
       if (LL) {
         d.Q[0 * P + c] = m[H1X]; d.Q[1 * P + c] = m[H1Y];
         d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
@@ -987,11 +1069,28 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       lam = cell_rate(d, out[H0], out[QX0], out[QY0]);
       bad = bad || !(isfinite(out[H0]) && isfinite(out[QX0]) && isfinite(out[QY0])) ||
             out[H0] < -1.0;
-      nonq = !(out[H0] <= tol);
+      nq_out = !(out[H0] <= tol);
 #pragma unroll
-      for (int k = 1; k < 9; ++k) nonq = nonq || out[k] != 0.0;
+      for (int k = 1; k < 9; ++k) nq_out = nq_out || out[k] != 0.0;
+    }
+  } else if (act && STAGE == 1) {
+    // a fixed point: U1 = Un as the computed stage writes it (a quiescent
+    // cell's rate is zero and the wet-dry treatment zeroes its other modes;
+    // its limited slopes are its own)
+    if (!recs) load9(In, P, c, m);
+    d.T[c] = m[H0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) d.T[k * P + c] = 0.0;
+    if (LL) {
+      d.Q[0 * P + c] = m[H1X]; d.Q[1 * P + c] = m[H1Y];
+      d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
+      d.Q[4 * P + c] = m[QY1X]; d.Q[5 * P + c] = m[QY1Y];
     }
   }
+  // (a stage-2 fixed point keeps Un in place)
+  nonq = nq_out;
+  const unsigned bits = __ballot_sync(0xffffffffu, nq_out);
+  if (tx == 0 && j < d.ny) d.qm[(STAGE == 1 ? d.qplane : 0) + (long long)j * d.nwx + bx] = bits;
 }
 
 // Work distribution of the stage kernels over the step's tile lists:
@@ -1064,11 +1163,19 @@ static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64
 #endif
       const int tile = d.tiles.front[e];
       const int i = (tile % ntx) * TX + tx, j = (tile / ntx) * TY + ty;
+      bool nq = false;
       if (i < d.nx && j < d.ny) {
         const long long c = (long long)j * d.pitch + i;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) d.T[k * P + c] = d.S[k * P + c];
+        for (int k = 0; k < 9; ++k) {
+          const double v = d.S[k * P + c];
+          d.T[k * P + c] = v;
+          nq = nq || (k == 0 ? !(v <= d.tol) : v != 0.0);
+        }
       }
+      // U1's non-quiescence bits of the copied rows, for a computed neighbour's stage 2
+      const unsigned bits = __ballot_sync(0xffffffffu, nq);
+      if (tx == 0 && j < d.ny) d.qm[d.qplane + (long long)j * d.nwx + tile % ntx] = bits;
     }
     return;
   }
