@@ -446,7 +446,8 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   memset(&d, 0, sizeof d);
   d.nx = nx; d.ny = ny; d.pitch = L.pitch; d.plane = L.plane;
   d.dx = dx; d.dy = dy; d.inv_dx = 1.0 / dx; d.inv_dy = 1.0 / dy;
-  d.g = p.g; d.cfl = p.cfl; d.tol = p.tol_dry; d.ds = p.ds_thresh; d.dt_max = p.dt_max;
+  d.g = p.g; d.cfl = p.cfl; d.ds = p.ds_thresh; d.dt_max = p.dt_max;
+  d.tol = p.tol_dry == 0.0 ? 0.0 : p.tol_dry;  // +0: the bit-pattern comparisons want c >= +0
   for (int k = 0; k < 4; ++k) d.bc[k] = p.bc[k];
   c->fp32 = p.precision == DG2_FP32;
   // plane buffers: FP64 depth modes, or FP32 free-surface modes (the FP64

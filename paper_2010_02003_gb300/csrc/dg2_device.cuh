@@ -83,8 +83,9 @@ struct Scalars {
 // stage records, one bit per cell, which cells of its output are
 // non-quiescent (qm: plane 0 for Un, written by stage 2; plane 1 for U1,
 // written by stage 1).  A row of 32 cells with no non-quiescent input cell
-// within R cells (R = 2 for DG2-LL: a neighbour's limited slopes read its own
-// neighbours; R = 1 for DG2-NL) is a fixed point of the stage: stage 1 copies
+// within one cell is a fixed point of the stage (a dry cell's limited slopes
+// are its own, so the records of a quiescent cell depend on it alone, in
+// DG2-LL too): stage 1 copies
 // it to U1, stage 2 leaves Un as it is when the row was also a fixed point of
 // stage 1 (busy1 holds stage 1's computed rows of each tile).  The tile's
 // faces are evaluated only where a computed row uses them.  Forced tiles,
@@ -148,6 +149,39 @@ struct Dev {
 };
 
 // ---------------------------------------------------------------------------
+// FP64 comparisons on the integer units
+// ---------------------------------------------------------------------------
+// GB300 runs every FP64 instruction, comparisons and min / max included, on a
+// pipe 64 times narrower than FP32, and the FP64 stage kernels are bound by
+// it.  Comparisons against zero and against a non-negative constant are taken
+// on the IEEE bit patterns instead, which order like the values: for x not a
+// NaN, x > 0 exactly when the pattern read as int64 is positive, x < 0 when
+// it is above the -0 pattern read as uint64, and, for c >= +0, x > c exactly
+// when bits(x) > bits(c) as int64.  A comparison of two values of any sign
+// uses the key (magnitude, negated for a set sign bit), which ranks -0 and +0
+// equal.  Every result equals the IEEE comparison for non-NaN operands.
+__device__ __forceinline__ long long fbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool is_pos(double x) { return fbits(x) > 0; }  // x > 0
+__device__ __forceinline__ bool is_neg(double x) {                        // x < 0
+  return (unsigned long long)fbits(x) > 0x8000000000000000ull;
+}
+// x > c for c >= +0
+__device__ __forceinline__ bool above(double x, double c) { return fbits(x) > fbits(c); }
+__device__ __forceinline__ double pos_part(double x) { return is_pos(x) ? x : 0.0; }  // max(x, 0)
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = fbits(x), m = b & 0x7fffffffffffffffll;
+  return b < 0 ? -m : m;
+}
+__device__ __forceinline__ bool gt(double a, double b) { return order_key(a) > order_key(b); }
+__device__ __forceinline__ double min2(double a, double b) { return gt(a, b) ? b : a; }
+__device__ __forceinline__ double max2(double a, double b) { return gt(b, a) ? b : a; }
+// comparisons of values known non-negative (sign bit clear or +0 after fabs)
+__device__ __forceinline__ double max_nn(double a, double b) { return fbits(b) > fbits(a) ? b : a; }
+__device__ __forceinline__ double min_nn(double a, double b) { return fbits(b) < fbits(a) ? b : a; }
+// x != 0 (either zero)
+__device__ __forceinline__ bool nonzero(double x) { return (fbits(x) << 1) != 0; }
+
+// ---------------------------------------------------------------------------
 // Point-state helpers
 // ---------------------------------------------------------------------------
 
@@ -163,7 +197,7 @@ struct F3 {
 
 __device__ __forceinline__ Lim revise(double h, double qx, double qy, double tol) {
   Lim r;
-  if (h > tol) {
+  if (above(h, tol)) {
     const double ih = 1.0 / h;
     r.u = qx * ih;
     r.v = qy * ih;
@@ -171,7 +205,7 @@ __device__ __forceinline__ Lim revise(double h, double qx, double qy, double tol
     r.u = 0.0;
     r.v = 0.0;
   }
-  r.h = h > 0.0 ? h : 0.0;
+  r.h = pos_part(h);
   r.qx = r.h * r.u;
   r.qy = r.h * r.v;
   return r;
@@ -184,32 +218,33 @@ __device__ __forceinline__ F3 hll(double hL, double qnL, double qtL, double unL,
                                   double hR, double qnR, double qtR, double unR, double utR,
                                   double g, double tol) {
   F3 f;
-  if (hL <= tol && hR <= tol) {
+  const bool dL = !above(hL, tol), dR = !above(hR, tol);
+  if (dL && dR) {
     f.h = 0.0; f.x = 0.0; f.y = 0.0;
     return f;
   }
   const double cL = sqrt(g * hL), cR = sqrt(g * hR);
   double sL, sR;
-  if (hL <= tol) {
+  if (dL) {
     sL = unR - 2.0 * cR;
     sR = unR + cR;
-  } else if (hR <= tol) {
+  } else if (dR) {
     sL = unL - cL;
     sR = unL + 2.0 * cL;
   } else {
     const double us = 0.5 * (unL + unR) + cL - cR;
     const double cs = 0.5 * (cL + cR) + 0.25 * (unL - unR);
-    sL = fmin(unL - cL, us - cs);
-    sR = fmax(unR + cR, us + cs);
+    sL = min2(unL - cL, us - cs);
+    sR = max2(unR + cR, us + cs);
   }
   // physical normal flux [h un, h un^2 + g h^2 / 2, h un ut] of each side
   const double fLh = hL * unL, fLn = hL * unL * unL + 0.5 * g * hL * hL, fLt = hL * unL * utL;
   const double fRh = hR * unR, fRn = hR * unR * unR + 0.5 * g * hR * hR, fRt = hR * unR * utR;
-  if (sL >= 0.0) {
+  if (!is_neg(sL)) {
     f.h = fLh; f.x = fLn; f.y = fLt;
     return f;
   }
-  if (sR <= 0.0) {
+  if (!is_pos(sR)) {
     f.h = fRh; f.x = fRn; f.y = fRt;
     return f;
   }
@@ -285,7 +320,7 @@ __device__ __forceinline__ F3 flux_y(const Lim& S, const Lim& N, double g, doubl
 __device__ __forceinline__ F3 phys_flux(double h, double qx, double qy, double g, double tol,
                                         bool ydir) {
   double u = 0.0, v = 0.0;
-  if (h > tol) {
+  if (above(h, tol)) {
     const double ih = 1.0 / h;
     u = qx * ih;
     v = qy * ih;
@@ -349,8 +384,12 @@ static __device__ void ghost(const Dev& d, int edge, double s, double t, double&
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double minmod3(double a, double b, double c) {
-  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(fmin(a, b), c);
-  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(fmax(a, b), c);
+  // same-signed operands: the bit patterns order the magnitudes
+  if (is_pos(a) && is_pos(b) && is_pos(c)) return min_nn(min_nn(a, b), c);
+  if (is_neg(a) && is_neg(b) && is_neg(c)) {
+    const double m = fbits(b) < fbits(a) ? b : a;  // the smaller magnitude
+    return fbits(c) < fbits(m) ? c : m;
+  }
   return 0.0;
 }
 
@@ -363,11 +402,11 @@ __device__ __forceinline__ double limit_component(double thresh, double tol, dou
   const double jE = fabs((k0e - k1e) - (k0 + k1));
   const double jW = fabs((k0 - k1) - (k0w + k1w));
   const double a = fabs(k0 - k1 / s3), b = fabs(k0 + k1 / s3);
-  double mag = a > b ? a : b;
-  if (mag < tol) mag = tol;  // still water: round-off never counts as a shock
+  double mag = max_nn(a, b);
+  if (fbits(mag) < fbits(tol)) mag = tol;  // still water: round-off never counts as a shock
   const double den = half * mag;
-  const double jm = jE > jW ? jE : jW;
-  if (!(jm > thresh * den)) return k1;
+  const double jm = max_nn(jE, jW);
+  if (!gt(jm, thresh * den)) return k1;
   return minmod3(k1, k0e - k0, k0 - k0w);
 }
 
@@ -387,7 +426,7 @@ static __device__ void limited_slopes(const Dev& d, const double* __restrict__ U
   const long long cl = dir == 1 ? c - 1 : c - d.pitch;
   const long long ch = dir == 1 ? c + 1 : c + d.pitch;
   const double hl = U[cl], hc = U[c], hh = U[ch];
-  if (hl <= d.tol || hc <= d.tol || hh <= d.tol) return;
+  if (!above(hl, d.tol) || !above(hc, d.tol) || !above(hh, d.tol)) return;
   const double half = 0.5 * (dir == 1 ? d.dx : d.dy);
   const double* z0 = d.Z;
   const double* z1 = d.Z + dir * P;
@@ -413,7 +452,7 @@ static __device__ void limited_slopes(const Dev& d, const double* __restrict__ U
 
 __device__ __forceinline__ void wetdry(double* m, double z0, double z1x, double z1y, double tol) {
   const double h0 = m[H0];
-  if (h0 <= tol) {
+  if (!above(h0, tol)) {
 #pragma unroll
     for (int k = 1; k < 9; ++k) m[k] = 0.0;
     return;
@@ -421,13 +460,13 @@ __device__ __forceinline__ void wetdry(double* m, double z0, double z1x, double 
   const double eta0 = h0 + z0;
   // x direction
   {
-    const bool fe = (h0 + m[H1X] <= tol) && !(z0 + z1x > eta0);
-    const bool fw = (h0 - m[H1X] <= tol) && !(z0 - z1x > eta0);
+    const bool fe = !above(h0 + m[H1X], tol) && !gt(z0 + z1x, eta0);
+    const bool fw = !above(h0 - m[H1X], tol) && !gt(z0 - z1x, eta0);
     if (fe || fw) { m[H1X] = 0.0; m[QX1X] = 0.0; m[QY1X] = 0.0; }
   }
   {
-    const bool fn = (h0 + m[H1Y] <= tol) && !(z0 + z1y > eta0);
-    const bool fs = (h0 - m[H1Y] <= tol) && !(z0 - z1y > eta0);
+    const bool fn = !above(h0 + m[H1Y], tol) && !gt(z0 + z1y, eta0);
+    const bool fs = !above(h0 - m[H1Y], tol) && !gt(z0 - z1y, eta0);
     if (fn || fs) { m[H1Y] = 0.0; m[QX1Y] = 0.0; m[QY1Y] = 0.0; }
   }
 }
@@ -492,10 +531,10 @@ __device__ __forceinline__ float block_max_f(float v, float* sh) {
 
 // Courant wave-speed rate of a cell: max((|u|+c)/dx, (|v|+c)/dy) if wet.
 __device__ __forceinline__ double cell_rate(const Dev& d, double h0, double qx0, double qy0) {
-  if (!(h0 > d.tol)) return 0.0;
+  if (!above(h0, d.tol)) return 0.0;
   const double ih = 1.0 / h0;
   const double u = qx0 * ih, v = qy0 * ih, c = sqrt(d.g * h0);
-  return fmax((fabs(u) + c) * d.inv_dx, (fabs(v) + c) * d.inv_dy);
+  return max_nn((fabs(u) + c) * d.inv_dx, (fabs(v) + c) * d.inv_dy);
 }
 
 // Turns the reduced rate into the next step: Courant step (capped by dt_max,
@@ -570,7 +609,7 @@ static __global__ void init_kernel(Dev d, const double* __restrict__ zc, const d
 // Point-implicit friction (Sec. 2.1.3) at one point: q /= 1 + dt g n^2 |q| / h^(7/3).
 __device__ __forceinline__ void friction_point(double gn2dt, double tol, double h, double& qx,
                                                double& qy) {
-  if (!(h > tol)) return;
+  if (!above(h, tol)) return;
   const double qm = sqrt(qx * qx + qy * qy);
   const double den = 1.0 + gn2dt * qm / (h * h * cbrt(h));
   const double iden = 1.0 / den;
@@ -672,18 +711,18 @@ __device__ __forceinline__ Rec make_rec(double h, double qx, double qy, double z
   r.u = 0.0;
   r.v = 0.0;
   const double eps = 0.1 * h0;
-  if (thin && eps > tol && h < eps) {
-    const double hp = h > 0.0 ? h : 0.0;
+  if (thin && above(eps, tol) && fbits(h) < fbits(eps)) {  // h < eps (eps > 0)
+    const double hp = pos_part(h);
     const double den = h * h + eps * eps;
     const double k = 2.0 * hp / den;
     r.u = k * qx;
     r.v = k * qy;
-  } else if (h > tol) {
+  } else if (above(h, tol)) {
     const double ih = 1.0 / h;
     r.u = qx * ih;
     r.v = qy * ih;
   }
-  const double hp = h > 0.0 ? h : 0.0;
+  const double hp = pos_part(h);
   r.hs = pw ? sc * hp : hp;
   r.zf = zf;
   r.pw = pw ? 1 : 0;
@@ -695,13 +734,13 @@ __device__ __forceinline__ Rec make_rec(double h, double qx, double qy, double z
 __device__ __forceinline__ bool pw_scale(double h0, double hW, double hE, double hS, double hN,
                                          double tol, int positive, double& sc) {
   sc = 1.0;
-  if (!positive || !(h0 > tol)) return false;
-  if (!(hW < 0.0 || hE < 0.0 || hS < 0.0 || hN < 0.0)) return false;
+  if (!positive || !above(h0, tol)) return false;
+  if (!(is_neg(hW) || is_neg(hE) || is_neg(hS) || is_neg(hN))) return false;
   double sum = 0.0;
-  sum += hW > 0.0 ? hW : 0.0;
-  sum += hE > 0.0 ? hE : 0.0;
-  sum += hS > 0.0 ? hS : 0.0;
-  sum += hN > 0.0 ? hN : 0.0;
+  sum += pos_part(hW);
+  sum += pos_part(hE);
+  sum += pos_part(hS);
+  sum += pos_part(hN);
   sc = h0 / (0.25 * sum);
   return true;
 }
@@ -719,23 +758,25 @@ __device__ __forceinline__ F3 revise_face(const Rec& a, const Rec& b, bool ydir,
   if (!a.pw && !b.pw) {
     ha = a.hs;
     hb = b.hs;
-    za = a.zf - (a.h < 0.0 ? -a.h : 0.0);
-    zb = b.zf - (b.h < 0.0 ? -b.h : 0.0);
+    za = a.zf - (is_neg(a.h) ? -a.h : 0.0);
+    zb = b.zf - (is_neg(b.h) ? -b.h : 0.0);
     // the flux's velocities follow the tol rule on the revised depth
-    ra.u = ha > tol ? a.u : 0.0; ra.v = ha > tol ? a.v : 0.0;
-    rb.u = hb > tol ? b.u : 0.0; rb.v = hb > tol ? b.v : 0.0;
+    const bool wa = above(ha, tol), wb = above(hb, tol);
+    ra.u = wa ? a.u : 0.0; ra.v = wa ? a.v : 0.0;
+    rb.u = wb ? b.u : 0.0; rb.v = wb ? b.v : 0.0;
   } else {
     double ea, oa, eb, ob;  // free surface and own bed level of each side
     if (a.pw) { ea = a.h + a.zf; oa = ea - a.hs; } else { oa = a.zf; ea = a.zf + a.hs; }
     if (b.pw) { eb = b.h + b.zf; ob = eb - b.hs; } else { ob = b.zf; eb = b.zf + b.hs; }
-    const double zs = oa > ob ? oa : ob;
+    const double zs = gt(oa, ob) ? oa : ob;
     const double da = ea - zs, db = eb - zs;
-    ha = da > 0.0 ? da : 0.0;
-    hb = db > 0.0 ? db : 0.0;
-    za = zs - (da < 0.0 ? -da : 0.0);
-    zb = zs - (db < 0.0 ? -db : 0.0);
-    ra.u = ha > tol ? a.u : 0.0; ra.v = ha > tol ? a.v : 0.0;
-    rb.u = hb > tol ? b.u : 0.0; rb.v = hb > tol ? b.v : 0.0;
+    ha = pos_part(da);
+    hb = pos_part(db);
+    za = zs - (is_neg(da) ? -da : 0.0);
+    zb = zs - (is_neg(db) ? -db : 0.0);
+    const bool wa = above(ha, tol), wb = above(hb, tol);
+    ra.u = wa ? a.u : 0.0; ra.v = wa ? a.v : 0.0;
+    rb.u = wb ? b.u : 0.0; rb.v = wb ? b.v : 0.0;
   }
   ra.h = ha; ra.qx = ha * a.u; ra.qy = ha * a.v;
   rb.h = hb; rb.qx = hb * b.u; rb.qy = hb * b.v;
@@ -863,7 +904,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   const int tile = by * d.tiles.ntx + bx;
   unsigned busy = (1u << TY) - 1u;
   if (d.tiles.skip && !d.tiles.all_forced && !d.tiles.forced[tile]) {
-    busy = busy_rows<LL ? 2 : 1>(d, STAGE == 1 ? d.qm : d.qm + d.qplane, bx, by);
+    busy = busy_rows<1>(d, STAGE == 1 ? d.qm : d.qm + d.qplane, bx, by);
     if (STAGE == 2) busy |= d.busy1[tile];
   }
   if (STAGE == 1 && tx == 0 && ty == 0) d.busy1[tile] = (unsigned char)busy;
@@ -1041,9 +1082,9 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       wetdry(out, z0, z1x, z1y, tol);
 #pragma unroll
       for (int k = 0; k < 9; ++k) d.T[k * P + c] = out[k];
-      nq_out = !(out[H0] <= tol);
+      nq_out = above(out[H0], tol);
 #pragma unroll
-      for (int k = 1; k < 9; ++k) nq_out = nq_out || out[k] != 0.0;
+      for (int k = 1; k < 9; ++k) nq_out = nq_out || nonzero(out[k]);
       if (LL) {
         d.Q[0 * P + c] = m[H1X]; d.Q[1 * P + c] = m[H1Y];
         d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
@@ -1069,9 +1110,9 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       lam = cell_rate(d, out[H0], out[QX0], out[QY0]);
       bad = bad || !(isfinite(out[H0]) && isfinite(out[QX0]) && isfinite(out[QY0])) ||
             out[H0] < -1.0;
-      nq_out = !(out[H0] <= tol);
+      nq_out = above(out[H0], tol);
 #pragma unroll
-      for (int k = 1; k < 9; ++k) nq_out = nq_out || out[k] != 0.0;
+      for (int k = 1; k < 9; ++k) nq_out = nq_out || nonzero(out[k]);
     }
   } else if (act && STAGE == 1) {
     // a fixed point: U1 = Un as the computed stage writes it (a quiescent
@@ -1170,7 +1211,7 @@ static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64
         for (int k = 0; k < 9; ++k) {
           const double v = d.S[k * P + c];
           d.T[k * P + c] = v;
-          nq = nq || (k == 0 ? !(v <= d.tol) : v != 0.0);
+          nq = nq || (k == 0 ? above(v, d.tol) : nonzero(v));
         }
       }
       // U1's non-quiescence bits of the copied rows, for a computed neighbour's stage 2
