@@ -57,7 +57,7 @@ struct Layout {
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
   size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, off_tforced,
       off_tlist, off_tfront, off_desc, off_es, off_qm, off_busy1, total;
-  int nblocks, mblocks, nwx;
+  int nblocks, mblocks, nbx, nby;
 };
 
 bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
@@ -104,9 +104,10 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   L.off_tforced = take((size_t)L.nblocks);
   L.off_tlist = take((size_t)L.nblocks * sizeof(int));
   L.off_tfront = take((size_t)L.nblocks * sizeof(int));
-  // FP64: the row-skipping masks of Un and U1 and stage 1's computed rows
-  L.nwx = (nx + 31) / 32;
-  L.off_qm = take(f32 ? 0 : 2 * (size_t)ny * L.nwx * sizeof(unsigned));
+  // FP64: the warp-block masks of Un and U1 and stage 1's computed blocks
+  L.nbx = (nx + dg2::TX - 1) / dg2::TX * dg2::TBX;
+  L.nby = (ny + dg2::TY - 1) / dg2::TY * dg2::TBY;
+  L.off_qm = take(f32 ? 0 : 2 * (size_t)L.nbx * L.nby * sizeof(unsigned));
   L.off_busy1 = take(f32 ? 0 : (size_t)L.nblocks);
   // FP32: the problem's descriptor and step counters for the shared FP32 kernels
   L.off_desc = take(f32 ? sizeof(D32) : 0);
@@ -485,8 +486,9 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
   d.qm = c->fp32 ? nullptr : (unsigned*)(c->ws + L.off_qm);
   d.busy1 = c->fp32 ? nullptr : (unsigned char*)(c->ws + L.off_busy1);
-  d.nwx = L.nwx;
-  d.qplane = (long long)ny * L.nwx;
+  d.nbx = L.nbx;
+  d.nby = L.nby;
+  d.qplane = (long long)L.nbx * L.nby;
   {
     D32& f = c->f;
     memset(&f, 0, sizeof f);

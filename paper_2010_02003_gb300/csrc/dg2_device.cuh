@@ -24,6 +24,20 @@ namespace dg2 {
 
 constexpr int TX = 32;
 constexpr int TY = 8;
+
+// A warp of the FP64 tile kernels covers a WX x WY block of cells (lane l:
+// column l % WX, row l / WX of the block); a 32 x 8 tile is 4 x 2 such blocks,
+// warp w the block (w % 4, w / 4).  Wet regions are compact, so square-ish
+// blocks hold fewer dry lanes than rows of 32.  The tile cell of the calling
+// thread:
+constexpr int WX = 8, WY = 4, TBX = TX / WX, TBY = TY / WY;
+static_assert(WX * WY == 32 && TBX * WX == TX && TBY * WY == TY, "warp blocks tile the tile");
+__device__ __forceinline__ void warp_cell(int& tx, int& ty) {
+  const int t = threadIdx.y * TX + threadIdx.x, w = t >> 5, l = t & 31;
+  tx = (w % TBX) * WX + (l % WX);
+  ty = (w / TBX) * WY + (l / WX);
+}
+
 constexpr int kMaxInflow = 8;
 constexpr int kMaxGauges = 256;
 
@@ -79,17 +93,17 @@ struct Scalars {
 // (inflow, point source, rain) tile is left untouched, bit for bit as if it
 // had been computed.
 //
-// The FP64 DG2 stage kernels refine this to rows of a computed tile.  Each
-// stage records, one bit per cell, which cells of its output are
-// non-quiescent (qm: plane 0 for Un, written by stage 2; plane 1 for U1,
-// written by stage 1).  A row of 32 cells with no non-quiescent input cell
+// The FP64 DG2 stage kernels refine this to the 8 x 4 cell block of each warp
+// of a computed tile.  Each stage records, one bit per cell, which cells of
+// its output are non-quiescent (qm: plane 0 for Un, written by stage 2; plane
+// 1 for U1, written by stage 1).  A block with no non-quiescent input cell
 // within one cell is a fixed point of the stage (a dry cell's limited slopes
 // are its own, so the records of a quiescent cell depend on it alone, in
-// DG2-LL too): stage 1 copies
-// it to U1, stage 2 leaves Un as it is when the row was also a fixed point of
-// stage 1 (busy1 holds stage 1's computed rows of each tile).  The tile's
-// faces are evaluated only where a computed row uses them.  Forced tiles,
-// rain and skip = 0 compute every row.
+// DG2-LL too): stage 1 copies it to U1, stage 2 leaves Un as it is when the
+// block was also a fixed point of stage 1 (busy1 holds stage 1's computed
+// blocks of each tile).  Records and faces are evaluated only where a
+// computed block uses them, and friction skips blocks of quiescent cells.
+// Forced tiles, rain and skip = 0 compute every block.
 struct Tiles {
   unsigned char* flag;          // [ntiles] tile held a non-quiescent cell after the last stage 2
   unsigned char* act;           // [ntiles] tile computed in the current step
@@ -139,12 +153,12 @@ struct Dev {
   double* samp_h;            // [max_samples][ngauge]
   int nblocks;               // blocks of the stage grid
   Tiles tiles;
-  // FP64 DG2 row skipping: non-quiescence bits, [2][ny][nwx] words of 32 cells
-  // (bit k of word (j, w): cell (32 w + k, j)), and stage 1's computed rows of
-  // each tile (bit r: row r of the tile)
+  // FP64 DG2 block skipping: non-quiescence bits, [2][nby][nbx] words, one per
+  // 8 x 4 warp block (bit l of word (Y, X): cell (8 X + l % 8, 4 Y + l / 8)),
+  // and stage 1's computed warp blocks of each tile
   unsigned int* qm;
   unsigned char* busy1;
-  int nwx;
+  int nbx, nby;              // warp blocks per row / column (whole tiles)
   long long qplane;          // words per qm plane
 };
 
@@ -620,9 +634,16 @@ __device__ __forceinline__ void friction_point(double gn2dt, double tol, double 
 // Friction on the cells of one 32 x 8 tile (threads 32 x 8).
 __device__ __forceinline__ void friction_tile(const Dev& d, int bx, int by) {
   const Scalars* sc = d.sc;
-  const int i = bx * TX + threadIdx.x;
-  const int j = by * TY + threadIdx.y;
+  int tx, ty;
+  warp_cell(tx, ty);
+  const int i = bx * TX + tx;
+  const int j = by * TY + ty;
   if (i >= d.nx || j >= d.ny) return;
+  // a quiescent cell (every Gauss-point depth at h0 <= tol_dry) has no water
+  // to rub: a warp block of them (Un's qm word zero) is left as it is
+  if (d.qm && d.tiles.skip && d.scheme == 0 &&
+      d.qm[(long long)(by * TBY + ty / WY) * d.nbx + bx * TBX + tx / WX] == 0u)
+    return;
   const long long P = d.plane, c = (long long)j * d.pitch + i;
   const double n = d.N[c];
   if (n == 0.0) return;
@@ -843,42 +864,42 @@ __device__ __forceinline__ Rec ghost_rec(const Dev& d, int edge, double s, doubl
   return make_rec(h, qx, qy, zf, false, 1.0, d.tol);
 }
 
-// Rows of the tile (bit r: row by TY + r) with a non-quiescent cell of the
-// stage input within R cells, from the input's qm plane: the mask words of
-// rows by TY - R .. by TY + TY - 1 + R in the tile's column and its two
-// neighbours (their R nearest bits), one word per lane.  Warp-uniform; every
-// lane of the warp must call it.
-static_assert(TX == 32, "row masks hold one warp row of a tile per word");
-template <int R>
-__device__ __forceinline__ unsigned busy_rows(const Dev& d, const unsigned* __restrict__ qm, int bx,
-                                              int by) {
-  constexpr int NR = TY + 2 * R;  // mask rows read
-  constexpr int NW = 3 * NR;      // words read
-  static_assert(NW <= 64, "two words per lane at most");
-  const int lane = threadIdx.x;
-  unsigned long long nzw = 0;     // bit k: word k holds a relevant non-quiescent bit
+// Warp blocks of tile (bx, by) (bit b: block (b % TBX, b / TBX)) with a
+// non-quiescent cell of the stage input within one cell, from the input's qm
+// plane (one word per block, bit l for lane l): the 6 x 4 words of the tile's
+// blocks and their ring, one per lane; each lane marks the blocks its word
+// touches (the whole word for the block itself, the adjacent column, row or
+// corner bit for a neighbour) and the marks are OR-reduced over the warp.
+// Warp-uniform; every lane of the warp must call it.
+__device__ __forceinline__ unsigned busy_blocks(const Dev& d, const unsigned* __restrict__ qm,
+                                                int bx, int by) {
+  const int k = (threadIdx.y * TX + threadIdx.x) & 31;
+  constexpr int RW = TBX + 2, RH = TBY + 2;  // ring region in blocks
+  static_assert(RW * RH <= 32, "one word per lane");
+  unsigned mark = 0;
+  if (k < RW * RH) {
+    const int rx = k % RW, ry = k / RW;
+    const int X = bx * TBX - 1 + rx, Y = by * TBY - 1 + ry;
+    if (X >= 0 && X < d.nbx && Y >= 0 && Y < d.nby) {
+      const unsigned v = qm[(long long)Y * d.nbx + X];
+      if (v) {
 #pragma unroll
-  for (int k0 = 0; k0 < NW; k0 += 32) {
-    const int k = k0 + lane;
-    bool nz = false;
-    if (k < NW) {
-      const int jj = by * TY - R + k / 3, o = k % 3, w = bx + o - 1;
-      if (jj >= 0 && jj < d.ny && w >= 0 && w < d.nwx) {
-        const unsigned v = qm[(long long)jj * d.nwx + w];
-        nz = (o == 0 ? v >> (32 - R) : (o == 1 ? v : v & ((1u << R) - 1u))) != 0u;
+        for (int b = 0; b < TBX * TBY; ++b) {
+          const int dx = rx - 1 - b % TBX, dy = ry - 1 - b / TBX;
+          if (dx < -1 || dx > 1 || dy < -1 || dy > 1) continue;
+          const unsigned cm = dx < 0 ? 0x80808080u : (dx > 0 ? 0x01010101u : 0xffffffffu);
+          const unsigned rm = dy < 0 ? 0xff000000u : (dy > 0 ? 0x000000ffu : 0xffffffffu);
+          if (v & cm & rm) mark |= 1u << b;
+        }
       }
     }
-    nzw |= (unsigned long long)__ballot_sync(0xffffffffu, nz) << k0;
   }
-  unsigned rows = 0;              // bit o: mask row by TY - R + o holds one
-#pragma unroll
-  for (int o = 0; o < NR; ++o)
-    if ((nzw >> (3 * o)) & 7ull) rows |= 1u << o;
-  unsigned busy = 0;
-#pragma unroll
-  for (int r = 0; r < TY; ++r)
-    if ((rows >> r) & ((1u << (2 * R + 1)) - 1u)) busy |= 1u << r;
-  return busy;
+  return __reduce_or_sync(0xffffffffu, mark);
+}
+
+// Whether tile cell (x, y) lies in a computed warp block.
+__device__ __forceinline__ bool in_busy(unsigned busy, int x, int y) {
+  return (busy >> ((y / WY) * TBX + x / WX)) & 1u;
 }
 
 // One RK stage on the 32 x 8 tile (bx, by): face records, one revision and
@@ -890,7 +911,8 @@ template <bool LL, int STAGE>
 __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, int by,
                                            double& brate, double& lam, bool& bad, bool& nonq) {
   Scalars* sc = d.sc;
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  int tx, ty;
+  warp_cell(tx, ty);
   const int i = bx * TX + tx, j = by * TY + ty;
   const bool act = i < d.nx && j < d.ny;
   const long long P = d.plane;
@@ -899,24 +921,24 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   const double ts = STAGE == 1 ? sc->t : sc->t + dt;  // boundary-condition time
   const double* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const double g = d.g, tol = d.tol;
-  // rows this stage computes: all, or those near a non-quiescent input cell
-  // (stage 2: also those stage 1 computed, whose U1 may differ from Un)
+  // warp blocks this stage computes: all, or those near a non-quiescent input
+  // cell (stage 2: also those stage 1 computed, whose U1 may differ from Un)
   const int tile = by * d.tiles.ntx + bx;
-  unsigned busy = (1u << TY) - 1u;
+  unsigned busy = (1u << (TBX * TBY)) - 1u;
   if (d.tiles.skip && !d.tiles.all_forced && !d.tiles.forced[tile]) {
-    busy = busy_rows<1>(d, STAGE == 1 ? d.qm : d.qm + d.qplane, bx, by);
+    busy = busy_blocks(d, STAGE == 1 ? d.qm : d.qm + d.qplane, bx, by);
     if (STAGE == 2) busy |= d.busy1[tile];
   }
-  if (STAGE == 1 && tx == 0 && ty == 0) d.busy1[tile] = (unsigned char)busy;
-  const bool b_me = (busy >> ty) & 1u;
-  const bool b_dn = ty > 0 && ((busy >> (ty - 1)) & 1u);       // the row below
-  const bool b_up = ty + 1 < TY && ((busy >> (ty + 1)) & 1u);  // the row above
+  if (STAGE == 1 && threadIdx.x == 0 && threadIdx.y == 0) d.busy1[tile] = (unsigned char)busy;
+  const bool b_me = in_busy(busy, tx, ty);
+  const bool b_w = tx > 0 && in_busy(busy, tx - 1, ty), b_e = tx + 1 < TX && in_busy(busy, tx + 1, ty);
+  const bool b_s = ty > 0 && in_busy(busy, tx, ty - 1), b_n = ty + 1 < TY && in_busy(busy, tx, ty + 1);
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
   Rec rE, rW, rN, rS;  // own records
-  // records: a computed row's, and those of the rows next to one (their
-  // north / south limits make the computed row's south / north face)
-  const bool recs = act && (b_me || b_dn || b_up);
+  // records: a computed cell's, and those of its neighbours (their limits make
+  // the computed cell's faces)
+  const bool recs = act && (b_me || b_w || b_e || b_s || b_n);
   if (recs) {
     load9(In, P, c, m);
     if (LL) {
@@ -941,12 +963,11 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   // the records beyond the tile (a neighbour's, or the edge ghost), one per
   // thread of the first 2 (TX + TY) threads, so no warp runs them one lane at a time
   {
-    const int t = ty * TX + tx;
+    const int t = threadIdx.y * TX + threadIdx.x;
     const int i0 = bx * TX, j0 = by * TY;
     const int ni = d.nx - i0 < TX ? d.nx - i0 : TX, nj = d.ny - j0 < TY ? d.ny - j0 : TY;
-    const bool b0 = busy & 1u, btop = (busy >> (nj - 1)) & 1u;
     if (t < TY) {
-      if (t < nj && ((busy >> t) & 1u)) {
+      if (t < nj && in_busy(busy, 0, t)) {
         const int jj = j0 + t;
         if (i0 == 0) {
           double h, qx, qy, zf;
@@ -958,7 +979,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY) {
       const int r = t - TY;
-      if (r < nj && ((busy >> r) & 1u)) {
+      if (r < nj && in_busy(busy, ni - 1, r)) {
         const int jj = j0 + r, il = i0 + ni - 1;
         if (il == d.nx - 1) {
           double h, qx, qy, zf;
@@ -970,7 +991,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY + TX) {
       const int q = t - 2 * TY;
-      if (q < ni && b0) {
+      if (q < ni && in_busy(busy, q, 0)) {
         const int ii = i0 + q;
         if (j0 == 0) {
           double h, qx, qy, zf;
@@ -982,7 +1003,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY + 2 * TX) {
       const int q = t - 2 * TY - TX;
-      if (q < ni && btop) {
+      if (q < ni && in_busy(busy, q, nj - 1)) {
         const int ii = i0 + q, jl = j0 + nj - 1;
         if (jl == d.ny - 1) {
           double h, qx, qy, zf;
@@ -1001,14 +1022,14 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   // to shared memory with the flux), then the tile's east and north edge
   // faces one per thread
   double hWo = 0, zWo = 0, hSo = 0, zSo = 0;
-  if (act && b_me) {
+  if (act && (b_me || b_w)) {
     double ha, za;
     const Rec& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
     const F3 fw = revise_face(Lw, rW, false, g, tol, d.flux, ha, za, hWo, zWo);
     sm.fx[ty][tx] = FaceR{fw.h, fw.x, fw.y, ha, za};
     if (i == 0) brate += fw.h * d.dy;
   }
-  if (act && (b_me || b_dn)) {
+  if (act && (b_me || b_s)) {
     double ha, za;
     const Rec& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
     const F3 fs = revise_face(Ls, rS, true, g, tol, d.flux, ha, za, hSo, zSo);
@@ -1016,17 +1037,17 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     if (j == 0) brate += fs.h * d.dx;
   }
   {
-    const int t = ty * TX + tx;
+    const int t = threadIdx.y * TX + threadIdx.x;
     const int ni = d.nx - bx * TX < TX ? d.nx - bx * TX : TX;
     const int nj = d.ny - by * TY < TY ? d.ny - by * TY : TY;
     double ha, za, hb, zb;
     if (t < nj) {
-      if ((busy >> t) & 1u) {
+      if (in_busy(busy, ni - 1, t)) {
       const F3 fe = revise_face(sm.e[t][ni - 1], sm.he[t], false, g, tol, d.flux, ha, za, hb, zb);
       sm.fx[t][ni] = FaceR{fe.h, fe.x, fe.y, ha, za};
       if (bx * TX + ni == d.nx) brate -= fe.h * d.dy;
       }
-    } else if (t >= TY && t < TY + ni && ((busy >> (nj - 1)) & 1u)) {
+    } else if (t >= TY && t < TY + ni && in_busy(busy, t - TY, nj - 1)) {
       const int q = t - TY;
       const F3 fn = revise_face(sm.n[nj - 1][q], sm.hn[q], true, g, tol, d.flux, ha, za, hb, zb);
       sm.fy[nj][q] = FaceR{fn.h, fn.x, fn.y, ha, za};
@@ -1131,7 +1152,10 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   // (a stage-2 fixed point keeps Un in place)
   nonq = nq_out;
   const unsigned bits = __ballot_sync(0xffffffffu, nq_out);
-  if (tx == 0 && j < d.ny) d.qm[(STAGE == 1 ? d.qplane : 0) + (long long)j * d.nwx + bx] = bits;
+  if ((threadIdx.x & 31) == 0) {
+    const int X = bx * TBX + tx / WX, Y = by * TBY + ty / WY;
+    d.qm[(STAGE == 1 ? d.qplane : 0) + (long long)Y * d.nbx + X] = bits;
+  }
 }
 
 // Work distribution of the stage kernels over the step's tile lists:
@@ -1203,7 +1227,9 @@ static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64
     for (int e = (int)blockIdx.x - n_act; e >= 0 && e < n_front; e = n_front) {
 #endif
       const int tile = d.tiles.front[e];
-      const int i = (tile % ntx) * TX + tx, j = (tile / ntx) * TY + ty;
+      int cx, cy;
+      warp_cell(cx, cy);
+      const int i = (tile % ntx) * TX + cx, j = (tile / ntx) * TY + cy;
       bool nq = false;
       if (i < d.nx && j < d.ny) {
         const long long c = (long long)j * d.pitch + i;
@@ -1214,9 +1240,12 @@ static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64
           nq = nq || (k == 0 ? above(v, d.tol) : nonzero(v));
         }
       }
-      // U1's non-quiescence bits of the copied rows, for a computed neighbour's stage 2
+      // U1's non-quiescence bits of the copied blocks, for a computed neighbour's stage 2
       const unsigned bits = __ballot_sync(0xffffffffu, nq);
-      if (tx == 0 && j < d.ny) d.qm[d.qplane + (long long)j * d.nwx + tile % ntx] = bits;
+      if ((threadIdx.x & 31) == 0) {
+        const int X = (tile % ntx) * TBX + cx / WX, Y = (tile / ntx) * TBY + cy / WY;
+        d.qm[d.qplane + (long long)Y * d.nbx + X] = bits;
+      }
     }
     return;
   }
