@@ -621,11 +621,29 @@ static __global__ void init_kernel(Dev d, const double* __restrict__ zc, const d
 }
 
 // Point-implicit friction (Sec. 2.1.3) at one point: q /= 1 + dt g n^2 |q| / h^(7/3).
+// h^(-7/3) for h in (1e-30, 1e30): the inverse cube root r = h^(-1/3) by two
+// Newton steps on f(r) = r^-3 - h, r <- r + r (1 - h r^3) / 3 (the error
+// squares at each step), from the FP32 inverse cube root as the seed (relative
+// error ~1e-7, so the second step reaches FP64 rounding), then r^7 = r (r^3)^2:
+// no FP64 cube root and no division.  Outside that range, h^2 cbrt(h) divides.
+__device__ __forceinline__ double h_m73(double h) {
+  if (!(fbits(h) > fbits(1e-30) && fbits(h) < fbits(1e30))) return 1.0 / (h * h * cbrt(h));
+  double r = (double)rcbrtf((float)h);
+  const double third = 1.0 / 3.0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double e = fma(-h, r * r * r, 1.0);
+    r = fma(r * third, e, r);
+  }
+  const double r3 = r * r * r;
+  return r * (r3 * r3);
+}
+
 __device__ __forceinline__ void friction_point(double gn2dt, double tol, double h, double& qx,
                                                double& qy) {
   if (!above(h, tol)) return;
   const double qm = sqrt(qx * qx + qy * qy);
-  const double den = 1.0 + gn2dt * qm / (h * h * cbrt(h));
+  const double den = 1.0 + gn2dt * qm * h_m73(h);
   const double iden = 1.0 / den;
   qx = qx * iden;
   qy = qy * iden;
