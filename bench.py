@@ -58,11 +58,11 @@ FLOPS_PER_WET_CELL = {"friction": 111, "stage1": {"nl": 403, "ll": 486},
 # was taken with: the key is a hash of paper_2010_02003_gb300/csrc, and the
 # roofline's traffic is null once those sources change.
 TRAFFIC = {
-    ("fp64_ll", "stage2"): (47_295_744, "d74f5547b8ce246a",
+    ("fp64_ll", "stage2"): (22_308_864, "b7aa2c7835d581d1",
                             "profiles/stage_kernel_fp64_ll_floodplain2000x1000_t3600.md"),
-    ("fp32_ll", "stage2"): (25_676_032, "d74f5547b8ce246a",
+    ("fp32_ll", "stage2"): (25_676_800, "b7aa2c7835d581d1",
                             "profiles/ens_stage_kernel_fp32_ll_floodplain2000x1000_t3600.md"),
-    ("fp32_nl_flooded", "stage2"): (222_254_080, "d74f5547b8ce246a",
+    ("fp32_nl_flooded", "stage2"): (222_937_344, "b7aa2c7835d581d1",
                                     "profiles/ens_stage_kernel_fp32_nl_flooded2000x1000.md"),
 }
 # FP64 issue rate of GB300: 2 DFMA per SM per cycle (ncu
