@@ -36,7 +36,6 @@ METRIC = "DG2 cell-updates/s (FP64, FP32) & % HBM roofline; adjoint/forward time
 NX, NY, DX = 2000, 1000, 2.0
 SPIN_T = 3600.0          # floodplain spin-up (s of simulated time): the hydrograph peak
 URBAN_SPIN_T = 30.0      # urban spin-up (s): 600 steps at dt_max 0.05 s
-TILE_CELLS = 32 * 8      # cells of one tile of the stage kernels
 # Unique bytes each kernel must move per cell: the planes it must read and write once.
 BYTES_PER_CELL = {
     "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
@@ -264,7 +263,8 @@ def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=
     tiles = s.tile_stats()[3] - tiles0
     t_sim, _ = s.time()
     return {"solver": s, "ms": ms, "launches": launches, "kernel_ms": kt, "timed": n,
-            "wet_fraction": wet, "active_cells": TILE_CELLS * tiles / max(steps, 1),
+            "wet_fraction": wet,
+            "active_cells": int(np.prod(s.tile_shape())) * tiles / max(steps, 1),
             "t_sim": t_sim}
 
 

@@ -195,8 +195,14 @@ int dg2_get_steps(dg2_ctx *ctx, int64_t *steps);
 /* Number of kernels this context has launched (for launch accounting). */
 int64_t dg2_launch_count(const dg2_ctx *ctx);
 
-/* Tile accounting of the exact dry-tile skipping (32 x 8-cell tiles): writes
- * the number of tiles of the grid, the tiles the next step will compute and
+/* Cells per tile of the context's exact dry-tile skipping, the tiles that
+ * dg2_tile_stats counts: writes the width (x) and height (y) of a tile, 32 x 8
+ * for FP64 contexts, 16 x 8 for FP32 ones.  Either pointer may be NULL.
+ * Errors: DG2_E_ARG (null context). */
+int dg2_tile_shape(dg2_ctx *ctx, int *w, int *h);
+
+/* Tile accounting of the exact dry-tile skipping (tiles of dg2_tile_shape):
+ * writes the number of tiles of the grid, the tiles the next step will compute and
  * copy (frontier), and the running total of tiles computed by all completed
  * steps (the units the stage kernels processed).  Any pointer may be NULL.
  * Synchronises the context's stream.  Errors: DG2_E_ARG (null context). */

@@ -33,7 +33,7 @@ EXPORTS = (
     "dg2_set_bc_inflow", "dg2_set_sources", "dg2_step", "dg2_run_to", "dg2_set_gauges",
     "dg2_read_gauges", "dg2_mass", "dg2_get_state", "dg2_set_state", "dg2_get_topo",
     "dg2_get_time", "dg2_enable_kernel_timing", "dg2_kernel_times", "dg2_launch_count",
-    "dg2_tile_stats", "dg2_get_steps", "dg2_mass_noalloc", "dg2_destroy",
+    "dg2_tile_stats", "dg2_tile_shape", "dg2_get_steps", "dg2_mass_noalloc", "dg2_destroy",
     "dg2_ens_workspace_bytes", "dg2_ens_create", "dg2_ens_run_to", "dg2_ens_autotune",
     "dg2_ens_set_tile_shape", "dg2_ens_tile_shape", "dg2_ens_tune_times",
     "dg2_ens_launch_count", "dg2_ens_destroy",
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "dg2_kernel_times": (I, [P, dp, i64p]),
         "dg2_launch_count": (ctypes.c_int64, [P]),
         "dg2_get_steps": (I, [P, i64p]),
+        "dg2_tile_shape": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "dg2_tile_stats": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
         "dg2_mass_noalloc": (I, [P, I, I, I, D, D, P, P]),
@@ -260,6 +261,13 @@ def dg2_tile_stats(ctx):
     _check(load().dg2_tile_stats(ctx, ctypes.byref(nt), ctypes.byref(na), ctypes.byref(nf),
                                  ctypes.byref(tc)))
     return nt.value, na.value, nf.value, tc.value
+
+
+def dg2_tile_shape(ctx):
+    """(width, height) in cells of the tiles that dg2_tile_stats counts."""
+    w, h = ctypes.c_int(), ctypes.c_int()
+    _check(load().dg2_tile_shape(ctx, ctypes.byref(w), ctypes.byref(h)))
+    return w.value, h.value
 
 
 def dg2_mass_noalloc(h0_ptr: int, nx: int, ny: int, pitch: int, dx: float, dy: float,
@@ -493,6 +501,9 @@ class Solver:
 
     def tile_stats(self):
         return dg2_tile_stats(self.ctx)
+
+    def tile_shape(self):
+        return dg2_tile_shape(self.ctx)
 
     def steps(self) -> int:
         return dg2_get_steps(self.ctx)

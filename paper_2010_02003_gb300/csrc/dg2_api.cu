@@ -72,7 +72,8 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   const size_t pb = (size_t)L.plane * esz;
   // set_dem stages the FP64 corner arrays and Manning field in the stage buffer
   const size_t staging = sizeof(double) * (2 * (size_t)(nx + 1) * (ny + 1) + (size_t)nx * ny);
-  L.nblocks = ((nx + dg2::TX - 1) / dg2::TX) * ((ny + dg2::TY - 1) / dg2::TY);
+  const int tw = f32 ? dg2::ens::kF32TW : dg2::TX, th = f32 ? dg2::ens::kF32TH : dg2::TY;
+  L.nblocks = ((nx + tw - 1) / tw) * ((ny + th - 1) / th);
   L.mblocks = ((nx + 31) / 32) * ((ny + 7) / 8);
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -148,6 +149,11 @@ struct dg2_ctx {
 
 namespace {
 
+// Cells per tile of the context's dry-tile skipping: 32 x 8 for the FP64
+// kernels, kF32TW x kF32TH for a single FP32 problem.
+int tile_w(const dg2_ctx* c) { return c->fp32 ? dg2::ens::kF32TW : dg2::TX; }
+int tile_h(const dg2_ctx* c) { return c->fp32 ? dg2::ens::kF32TH : dg2::TY; }
+
 int launch_check(dg2_ctx* c, int nkernels) {
   c->launches += nkernels;
   cudaError_t e = cudaGetLastError();
@@ -214,7 +220,7 @@ void forced_mask(const Dev& d, int tw, int th, std::vector<unsigned char>& m) {
 int update_forced_tiles(dg2_ctx* c) {
   Dev& d = c->d;
   std::vector<unsigned char> m;
-  forced_mask(d, dg2::TX, dg2::TY, m);
+  forced_mask(d, tile_w(c), tile_h(c), m);
   d.tiles.all_forced = d.rain != 0.0 ? 1 : 0;
   c->f.tiles = d.tiles;
   if (int r0 = sync_desc(c)) return r0;
@@ -258,7 +264,7 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   const bool ll = c->p.variant == DG2_LL;
   if (e) cudaEventRecord(e[0], c->st);
   if (c->fp32)
-    dg2::ens::launch_friction32x8(c->e1, c->g_fric, c->st);
+    dg2::ens::launch_friction32(c->e1, c->g_fric, c->st);
   else
     dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
@@ -278,14 +284,14 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
     return;
   }
   if (c->fp32) {
-    dg2::ens::launch_stage32x8(c->e1, ll, 1, c->g_st1, c->st);
+    dg2::ens::launch_stage32(c->e1, ll, 1, c->g_st1, c->st);
   } else {
     if (ll) dg2::stage_kernel<true, 1><<<c->g_st1, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
     else dg2::stage_kernel<false, 1><<<c->g_st1, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
   }
   if (e) cudaEventRecord(e[2], c->st);
   if (c->fp32) {
-    dg2::ens::launch_stage32x8(c->e1, ll, 2, c->g_st2, c->st);
+    dg2::ens::launch_stage32(c->e1, ll, 2, c->g_st2, c->st);
   } else {
     if (ll) dg2::stage_kernel<true, 2><<<c->g_st2, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
     else dg2::stage_kernel<false, 2><<<c->g_st2, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
@@ -479,8 +485,8 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.tiles.forced = (const unsigned char*)(c->ws + L.off_tforced);
   d.tiles.list = (int*)(c->ws + L.off_tlist);
   d.tiles.front = (int*)(c->ws + L.off_tfront);
-  d.tiles.ntx = (nx + dg2::TX - 1) / dg2::TX;
-  d.tiles.nty = (ny + dg2::TY - 1) / dg2::TY;
+  d.tiles.ntx = (nx + tile_w(c) - 1) / tile_w(c);
+  d.tiles.nty = (ny + tile_h(c) - 1) / tile_h(c);
   d.tiles.ntiles = d.tiles.ntx * d.tiles.nty;
   d.tiles.all_forced = 0;
   d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
@@ -535,7 +541,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     cudaFuncSetAttribute(dg2::stage_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(dg2::StageSmem));
     if (f32) {
-      dg2::ens::occupancy32x8(ll, &o0, &o1, &o2);
+      dg2::ens::occupancy32(ll, &o0, &o1, &o2);
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::friction_kernel, 256, 0);
       if (ll) {
@@ -1027,6 +1033,13 @@ int dg2_tile_stats(dg2_ctx* c, int* ntiles, int* n_active, int* n_frontier,
   if (n_active) *n_active = s.n_act;
   if (n_frontier) *n_frontier = s.n_front;
   if (tiles_computed) *tiles_computed = s.tiles_done;
+  return DG2_OK;
+}
+
+int dg2_tile_shape(dg2_ctx* c, int* w, int* h) {
+  if (!c) return fail(DG2_E_ARG, "null context");
+  if (w) *w = tile_w(c);
+  if (h) *h = tile_h(c);
   return DG2_OK;
 }
 

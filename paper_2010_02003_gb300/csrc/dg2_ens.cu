@@ -248,18 +248,18 @@ __global__ void ens_begin_run_kernel(EnsDev E, double t_end) {
   if (sc->done) atomicAdd(&E.es->n_done, 1);
 }
 
-void launch_friction32x8(const EnsDev& E, int grid, cudaStream_t st) {
-  ens_friction_kernel<TX, TY><<<grid, dim3(TX, TY), 0, st>>>(E);
+void launch_friction32(const EnsDev& E, int grid, cudaStream_t st) {
+  ens_friction_kernel<kF32TW, kF32TH><<<grid, dim3(kF32TW, kF32TH), 0, st>>>(E);
 }
 
-void launch_stage32x8(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st) {
-  const dim3 b(TX, TY);
+void launch_stage32(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st) {
+  const dim3 b(kF32TW, kF32TH);
   if (ll) {
-    if (stage == 1) ens_stage_kernel<true, 1, TX, TY><<<grid, b, 0, st>>>(E);
-    else ens_stage_kernel<true, 2, TX, TY><<<grid, b, 0, st>>>(E);
+    if (stage == 1) ens_stage_kernel<true, 1, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
+    else ens_stage_kernel<true, 2, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
   } else {
-    if (stage == 1) ens_stage_kernel<false, 1, TX, TY><<<grid, b, 0, st>>>(E);
-    else ens_stage_kernel<false, 2, TX, TY><<<grid, b, 0, st>>>(E);
+    if (stage == 1) ens_stage_kernel<false, 1, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
+    else ens_stage_kernel<false, 2, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
   }
 }
 
@@ -268,15 +268,15 @@ void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, c
   ens_lists_kernel<<<lgrid, dim3(LTX, LTY), 0, st>>>(E);
 }
 
-void occupancy32x8(bool ll, int* f, int* s1, int* s2) {
-  const int nt = TX * TY;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(f, ens_friction_kernel<TX, TY>, nt, 0);
+void occupancy32(bool ll, int* f, int* s1, int* s2) {
+  const int nt = kF32TW * kF32TH;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(f, ens_friction_kernel<kF32TW, kF32TH>, nt, 0);
   if (ll) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<true, 1, TX, TY>, nt, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<true, 2, TX, TY>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<true, 1, kF32TW, kF32TH>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<true, 2, kF32TW, kF32TH>, nt, 0);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<false, 1, TX, TY>, nt, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<false, 2, TX, TY>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<false, 1, kF32TW, kF32TH>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<false, 2, kF32TW, kF32TH>, nt, 0);
   }
 }
 

@@ -30,14 +30,19 @@ struct EnsDev {
 };
 constexpr int kTileBits = 22;
 
-// The FP32 kernels of one step on 32 x 8 tiles (a single problem is a set of
-// one): friction, one RK stage, and the end of step (finalize + lists; with
-// lists_only just the lists).  `grid` = persistent blocks; `lgrid` = tile
+// Tile of a single FP32 problem (cells, one thread each): 16 x 8, the shape
+// the ensemble autotuner picks on the floodplain (16 x 8 ran its steps 13 %
+// faster than 32 x 8 there; tiles of 128 cells leave fewer dry lanes around a
+// narrow wet region and give more resident blocks).
+constexpr int kF32TW = 16, kF32TH = 8;
+// The FP32 kernels of one step on kF32TW x kF32TH tiles (a single problem is a
+// set of one): friction, one RK stage, and the end of step (finalize + lists;
+// with lists_only just the lists).  `grid` = persistent blocks; `lgrid` = tile
 // blocks of the lists kernel (z = problems).
-void launch_friction32x8(const EnsDev& E, int grid, cudaStream_t st);
-void launch_stage32x8(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st);
+void launch_friction32(const EnsDev& E, int grid, cudaStream_t st);
+void launch_stage32(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st);
 void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, cudaStream_t st);
-void occupancy32x8(bool ll, int* fric, int* st1, int* st2);
+void occupancy32(bool ll, int* fric, int* st1, int* st2);
 }  // namespace ens
 
 // Reports through dg2_last_error().
