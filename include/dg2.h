@@ -197,7 +197,8 @@ int64_t dg2_launch_count(const dg2_ctx *ctx);
 
 /* Cells per tile of the context's exact dry-tile skipping, the tiles that
  * dg2_tile_stats counts: writes the width (x) and height (y) of a tile, 32 x 8
- * for FP64 contexts, 16 x 8 for FP32 ones.  Either pointer may be NULL.
+ * for FP64 contexts; for FP32 ones 16 x 8 on grids of up to 2^23 cells and
+ * 32 x 8 on larger ones.  Either pointer may be NULL.
  * Errors: DG2_E_ARG (null context). */
 int dg2_tile_shape(dg2_ctx *ctx, int *w, int *h);
 

@@ -72,7 +72,8 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   const size_t pb = (size_t)L.plane * esz;
   // set_dem stages the FP64 corner arrays and Manning field in the stage buffer
   const size_t staging = sizeof(double) * (2 * (size_t)(nx + 1) * (ny + 1) + (size_t)nx * ny);
-  const int tw = f32 ? dg2::ens::kF32TW : dg2::TX, th = f32 ? dg2::ens::kF32TH : dg2::TY;
+  const int tw = f32 ? (dg2::ens::f32_small_tiles((long long)nx * ny) ? 16 : 32) : dg2::TX;
+  const int th = dg2::TY;
   L.nblocks = ((nx + tw - 1) / tw) * ((ny + th - 1) / th);
   L.mblocks = ((nx + 31) / 32) * ((ny + 7) / 8);
   size_t o = 0;
@@ -150,9 +151,11 @@ struct dg2_ctx {
 namespace {
 
 // Cells per tile of the context's dry-tile skipping: 32 x 8 for the FP64
-// kernels, kF32TW x kF32TH for a single FP32 problem.
-int tile_w(const dg2_ctx* c) { return c->fp32 ? dg2::ens::kF32TW : dg2::TX; }
-int tile_h(const dg2_ctx* c) { return c->fp32 ? dg2::ens::kF32TH : dg2::TY; }
+// kernels; 16 x 8 or 32 x 8 for a single FP32 problem by its size.
+int tile_w(const dg2_ctx* c) {
+  return c->fp32 && dg2::ens::f32_small_tiles((long long)c->d.nx * c->d.ny) ? 16 : dg2::TX;
+}
+int tile_h(const dg2_ctx*) { return dg2::TY; }
 
 int launch_check(dg2_ctx* c, int nkernels) {
   c->launches += nkernels;
@@ -264,7 +267,7 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   const bool ll = c->p.variant == DG2_LL;
   if (e) cudaEventRecord(e[0], c->st);
   if (c->fp32)
-    dg2::ens::launch_friction32(c->e1, c->g_fric, c->st);
+    dg2::ens::launch_friction32(c->e1, tile_w(c), c->g_fric, c->st);
   else
     dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
@@ -284,14 +287,14 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
     return;
   }
   if (c->fp32) {
-    dg2::ens::launch_stage32(c->e1, ll, 1, c->g_st1, c->st);
+    dg2::ens::launch_stage32(c->e1, tile_w(c), ll, 1, c->g_st1, c->st);
   } else {
     if (ll) dg2::stage_kernel<true, 1><<<c->g_st1, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
     else dg2::stage_kernel<false, 1><<<c->g_st1, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
   }
   if (e) cudaEventRecord(e[2], c->st);
   if (c->fp32) {
-    dg2::ens::launch_stage32(c->e1, ll, 2, c->g_st2, c->st);
+    dg2::ens::launch_stage32(c->e1, tile_w(c), ll, 2, c->g_st2, c->st);
   } else {
     if (ll) dg2::stage_kernel<true, 2><<<c->g_st2, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
     else dg2::stage_kernel<false, 2><<<c->g_st2, c->sblock, sizeof(dg2::StageSmem), c->st>>>(d);
@@ -541,7 +544,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     cudaFuncSetAttribute(dg2::stage_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(dg2::StageSmem));
     if (f32) {
-      dg2::ens::occupancy32(ll, &o0, &o1, &o2);
+      dg2::ens::occupancy32(tile_w(c), ll, &o0, &o1, &o2);
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::friction_kernel, 256, 0);
       if (ll) {

@@ -248,19 +248,27 @@ __global__ void ens_begin_run_kernel(EnsDev E, double t_end) {
   if (sc->done) atomicAdd(&E.es->n_done, 1);
 }
 
-void launch_friction32(const EnsDev& E, int grid, cudaStream_t st) {
-  ens_friction_kernel<kF32TW, kF32TH><<<grid, dim3(kF32TW, kF32TH), 0, st>>>(E);
+template <int BX, int BY>
+void launch_shape32(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st) {
+  const dim3 b(BX, BY);
+  if (stage == 0) ens_friction_kernel<BX, BY><<<grid, b, 0, st>>>(E);
+  else if (ll) {
+    if (stage == 1) ens_stage_kernel<true, 1, BX, BY><<<grid, b, 0, st>>>(E);
+    else ens_stage_kernel<true, 2, BX, BY><<<grid, b, 0, st>>>(E);
+  } else {
+    if (stage == 1) ens_stage_kernel<false, 1, BX, BY><<<grid, b, 0, st>>>(E);
+    else ens_stage_kernel<false, 2, BX, BY><<<grid, b, 0, st>>>(E);
+  }
 }
 
-void launch_stage32(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st) {
-  const dim3 b(kF32TW, kF32TH);
-  if (ll) {
-    if (stage == 1) ens_stage_kernel<true, 1, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
-    else ens_stage_kernel<true, 2, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
-  } else {
-    if (stage == 1) ens_stage_kernel<false, 1, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
-    else ens_stage_kernel<false, 2, kF32TW, kF32TH><<<grid, b, 0, st>>>(E);
-  }
+void launch_friction32(const EnsDev& E, int tw, int grid, cudaStream_t st) {
+  if (tw == 16) launch_shape32<16, 8>(E, false, 0, grid, st);
+  else launch_shape32<32, 8>(E, false, 0, grid, st);
+}
+
+void launch_stage32(const EnsDev& E, int tw, bool ll, int stage, int grid, cudaStream_t st) {
+  if (tw == 16) launch_shape32<16, 8>(E, ll, stage, grid, st);
+  else launch_shape32<32, 8>(E, ll, stage, grid, st);
 }
 
 void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, cudaStream_t st) {
@@ -268,16 +276,22 @@ void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, c
   ens_lists_kernel<<<lgrid, dim3(LTX, LTY), 0, st>>>(E);
 }
 
-void occupancy32(bool ll, int* f, int* s1, int* s2) {
-  const int nt = kF32TW * kF32TH;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(f, ens_friction_kernel<kF32TW, kF32TH>, nt, 0);
+template <int BX, int BY>
+void occupancy_shape32(bool ll, int* f, int* s1, int* s2) {
+  const int nt = BX * BY;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(f, ens_friction_kernel<BX, BY>, nt, 0);
   if (ll) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<true, 1, kF32TW, kF32TH>, nt, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<true, 2, kF32TW, kF32TH>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<true, 1, BX, BY>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<true, 2, BX, BY>, nt, 0);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<false, 1, kF32TW, kF32TH>, nt, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<false, 2, kF32TW, kF32TH>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<false, 1, BX, BY>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<false, 2, BX, BY>, nt, 0);
   }
+}
+
+void occupancy32(int tw, bool ll, int* f, int* s1, int* s2) {
+  if (tw == 16) occupancy_shape32<16, 8>(ll, f, s1, s2);
+  else occupancy_shape32<32, 8>(ll, f, s1, s2);
 }
 
 }  // namespace ens

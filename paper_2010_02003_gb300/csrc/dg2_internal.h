@@ -30,19 +30,23 @@ struct EnsDev {
 };
 constexpr int kTileBits = 22;
 
-// Tile of a single FP32 problem (cells, one thread each): 16 x 8, the shape
-// the ensemble autotuner picks on the floodplain (16 x 8 ran its steps 13 %
-// faster than 32 x 8 there; tiles of 128 cells leave fewer dry lanes around a
-// narrow wet region and give more resident blocks).
-constexpr int kF32TW = 16, kF32TH = 8;
-// The FP32 kernels of one step on kF32TW x kF32TH tiles (a single problem is a
-// set of one): friction, one RK stage, and the end of step (finalize + lists;
-// with lists_only just the lists).  `grid` = persistent blocks; `lgrid` = tile
-// blocks of the lists kernel (z = problems).
-void launch_friction32(const EnsDev& E, int grid, cudaStream_t st);
-void launch_stage32(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st);
+// Tile of a single FP32 problem (cells, one thread each), fixed when the
+// context is made: 16 x 8 on grids of up to kF32SmallCells cells, 32 x 8 on
+// larger ones.  Measured on GB300 (ms per step, 32 x 8 -> 16 x 8): the
+// 2000 x 1000 floodplain from t = 1 h, DG2-LL 0.122 -> 0.104 and DG2-NL
+// 0.094 -> 0.079 (tiles of 128 cells leave fewer dry lanes around a narrow
+// wet region), the same grid fully wet 0.387 -> 0.377, but the 8192 x 8192
+// urban grid under rain 11.66 -> 12.95.
+constexpr long long kF32SmallCells = 1ll << 23;
+inline bool f32_small_tiles(long long cells) { return cells <= kF32SmallCells; }
+// The FP32 kernels of one step on tiles of tw x th cells (16 x 8 or 32 x 8; a
+// single problem is a set of one): friction, one RK stage, and the end of step
+// (finalize + lists; with lists_only just the lists).  `grid` = persistent
+// blocks; `lgrid` = tile blocks of the lists kernel (z = problems).
+void launch_friction32(const EnsDev& E, int tw, int grid, cudaStream_t st);
+void launch_stage32(const EnsDev& E, int tw, bool ll, int stage, int grid, cudaStream_t st);
 void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, cudaStream_t st);
-void occupancy32(bool ll, int* fric, int* st1, int* st2);
+void occupancy32(int tw, bool ll, int* fric, int* st1, int* st2);
 }  // namespace ens
 
 // Reports through dg2_last_error().
