@@ -48,6 +48,23 @@ def test_skip_with_point_source_and_rain(precision):
     assert a[0][0].max() > 0.0
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["FP64", "FP32"])
+@pytest.mark.parametrize("variant", [0, 1], ids=["NL", "LL"])
+def test_skip_on_ragged_grid_with_point_source(variant, precision):
+    """A ragged grid (neither side a multiple of the tile or of the 8 x 4 warp
+    block), a dam breaking into a dry basin from off-centre and a point source
+    without rain: fronts cross tile and warp-block edges in every direction, and
+    the source's tile is forced while its neighbours are not."""
+    case = inputs.hump(nx=203, ny=117, eta=-1.0, dam_eta=1.0, dam_radius=14.0)
+    case.eta_corner = np.roll(case.eta_corner, (9, -23), axis=(0, 1))
+    case.point = (40.5, 90.5, 0.5)
+    a = _run(case, variant, precision, True, 160, dt_max=0.05)
+    b = _run(case, variant, precision, False, 160, dt_max=0.05)
+    assert np.array_equal(a[0], b[0])
+    assert a[1] == b[1] and a[2] == b[2] and a[3] == b[3]
+    assert (a[0][0] > 1e-5).sum() > 500        # the flow has spread
+
+
 def _expected_active(state, tol=1e-5, tx=32, ty=8):
     """Tiles within one tile (3 x 3 neighbourhood) of a tile holding a non-quiescent
     cell (h0 > tol or any other mode non-zero), from the FP64 state."""
