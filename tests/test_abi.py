@@ -48,6 +48,9 @@ def test_host_only_calls_without_gpu():
     with pytest.raises(B.Dg2Error) as e:
         B.dg2_init_grid(8, 8, 1.0, 1.0, p, 0, 10 ** 6, 0)
     assert e.value.code == B.DG2_E_ARG
+    with pytest.raises(B.Dg2Error) as e:
+        B.dg2_tile_shape(None)
+    assert e.value.code == B.DG2_E_ARG
 
 
 def test_product_path_does_not_reference_the_oracle():
