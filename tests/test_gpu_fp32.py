@@ -166,3 +166,17 @@ def test_fp32_urban_recipe_against_fp64_oracle():
           f"wet cells {wet_a} vs {wet_b}, relative L1 depth {l1:.2e}")
     assert abs(wet_a - wet_b) <= 0.03 * wet_b, (wet_a, wet_b)
     assert l1 < 5e-2, l1
+
+
+def test_tile_shape_follows_precision_and_size():
+    """dg2_tile_shape: FP64 tiles are 32 x 8; FP32 tiles 16 x 8 up to 2^23 cells and
+    32 x 8 above (the workspace is laid out for the shape when the context is made)."""
+    from paper_2010_02003_gb300 import binding as B
+    assert B.Solver(40, 30, 1.0).tile_shape() == (32, 8)
+    assert B.Solver(40, 30, 1.0, precision=B.DG2_FP32).tile_shape() == (16, 8)
+    s = B.Solver(2048, 4096, 1.0, precision=B.DG2_FP32)          # 2^23 cells
+    assert s.tile_shape() == (16, 8)
+    s.close()
+    s = B.Solver(2049, 4096, 1.0, precision=B.DG2_FP32)
+    assert s.tile_shape() == (32, 8)
+    s.close()
