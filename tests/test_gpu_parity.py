@@ -344,3 +344,45 @@ def test_planar_basin_at_rest(limiter, wetdry):
     st = s.state()
     assert np.abs(st[3:]).max() <= 1e-12
     assert plane_err(st, o.state()).max() <= TOL
+
+
+def test_bench_workload_sampled_windows():
+    """The benchmark's workload in its launch configuration: the 2000 x 1000 (2 m)
+    floodplain, DG2-LL, FP64, tile and warp-block skipping on, stepped once from a
+    wet, flowing state (FP32 run from the channel start to t = 600 s).  A full-size
+    oracle step takes minutes, so the oracle steps 48 x 48 windows cut around sampled
+    wet cells with the GPU's dt; a step reads 4 cells around each cell (2 per stage,
+    friction is pointwise), so window cells 6 or more cells from the cut must agree
+    with the GPU's full-grid step."""
+    import oracle
+    B = _binding()
+    case = inputs.floodplain(initial="channel")
+    warm = B.solver_from_case(case, variant=B.DG2_LL, precision=B.DG2_FP32)
+    warm.run_to(600.0)
+    st, t = warm.state(), warm.time()[0]
+    warm.close()
+    s = B.solver_from_case(case, variant=B.DG2_LL)
+    s.set_state(st, t)
+    dt = s.step(-1.0, want_dt=True)
+    out = s.state()
+    W, M = 48, 6
+    hs = np.abs(out[0]).max()
+    qs = max(np.abs(out[3]).max(), np.abs(out[6]).max(), hs * np.sqrt(9.80665 * hs))
+    scale = np.array([hs] * 3 + [qs] * 6)[:, None, None]
+    wet = np.argwhere(st[0] > 1e-5)
+    wet = wet[(wet[:, 0] >= W) & (wet[:, 0] < case.ny - W) & (wet[:, 1] >= W) &
+              (wet[:, 1] < case.nx - W)]
+    assert len(wet) > 1000
+    rng = np.random.default_rng(11)
+    for j, i in wet[rng.choice(len(wet), 8, replace=False)]:
+        j0, i0 = j - W // 2, i - W // 2
+        o = oracle.Oracle(W, W, case.dx, case.dy, cfl=case.cfl, limiter=True,
+                          dt_max=case.dt_max)
+        man = None if case.manning is None else case.manning[j0:j0 + W, i0:i0 + W]
+        o.set_dem(case.z_corner[j0:j0 + W + 1, i0:i0 + W + 1], man, case.n_uniform)
+        o.set_state(st[:, j0:j0 + W, i0:i0 + W], t)
+        o.step(dt)
+        a = out[:, j0 + M:j0 + W - M, i0 + M:i0 + W - M]
+        b = o.state()[:, M:W - M, M:W - M]
+        err = (np.abs(a - b) / scale).max()
+        assert err <= TOL, (j, i, err)
