@@ -21,8 +21,12 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   - friction: pinned by the exact solution of the friction ODE at the centre
     and at every Gauss point.
   - limiter: pinned by brute-force detector / minmod cases.
-  - inflow ghost and point/rain sources: parity unpinned beyond the mass
-    ledger (the paper does not define them).
+  - inflow ghost, rain: pinned by Manning's normal flow down a plane slope fed
+    by the inflow boundary (normal depth; the step's mean face discharge equals
+    the inflow) and by rain on a flat closed basin (depth rising at exactly the
+    rain rate) (tests/test_oracle_sources.py).
+  - point source: parity unpinned beyond the mass ledger (the paper does not
+    define it).
   - taped derivatives (``tape.cpp``, :func:`taped_gradient`): the same C
     source compiled with a recording scalar type; pinned against central
     finite differences of the oracle itself.
