@@ -25,8 +25,8 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
     by the inflow boundary (normal depth; the step's mean face discharge equals
     the inflow) and by rain on a flat closed basin (depth rising at exactly the
     rain rate) (tests/test_oracle_sources.py).
-  - point source: parity unpinned beyond the mass ledger (the paper does not
-    define it).
+  - point source: pinned by a closed single cell filling at exactly Q / (dx dy)
+    and by a symmetric first step about the source cell of a closed basin.
   - taped derivatives (``tape.cpp``, :func:`taped_gradient`): the same C
     source compiled with a recording scalar type; pinned against central
     finite differences of the oracle itself.

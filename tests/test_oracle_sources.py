@@ -60,3 +60,25 @@ def test_normal_flow_on_a_slope_with_inflow(limiter):
     assert np.abs(mean_flux / q - 1.0).max() < 1e-4
     assert np.abs(st[6]).max() < 1e-9                  # no transverse flow
     assert abs(o.mass() - o.ledger()) <= 1e-12 * o.mass()
+
+
+def test_point_source_fills_its_cell():
+    """A point inflow Q into a closed single cell raises its depth at exactly
+    Q / (dx dy); on a 5 x 5 basin with the source at the centre cell, one step
+    leaves the depth symmetric about that cell and the volume up by Q dt."""
+    dx, dy, q, h0 = 2.0, 1.5, 0.03, 0.2
+    o = oracle.Oracle(1, 1, dx, dy)
+    o.set_dem(np.zeros((2, 2)), None, 0.0, np.full((2, 2), h0))
+    o.set_sources(px=0.7, py=0.4, qp=q)
+    for _ in range(10):
+        o.step(0.5)
+    assert abs(o.state()[0, 0, 0] - (h0 + q * 5.0 / (dx * dy))) <= 1e-15
+    o = oracle.Oracle(5, 5, dx, dy)
+    o.set_dem(np.zeros((6, 6)), None, 0.0, np.full((6, 6), h0))
+    o.set_sources(px=2.5 * dx, py=2.5 * dy, qp=q)
+    m0 = o.mass()
+    o.step(0.1)
+    h = o.state()[0]
+    assert np.abs(h - h[::-1, :]).max() <= 1e-15 and np.abs(h - h[:, ::-1]).max() <= 1e-15
+    assert h[2, 2] == h.max() and h[2, 2] > h0
+    assert abs(o.mass() - (m0 + q * 0.1)) <= 1e-15 * o.mass()
