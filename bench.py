@@ -64,9 +64,25 @@ TRAFFIC = {
     ("fp32_nl_flooded", "stage2"): (223_492_352, "ac7b8db0bf6b054e",
                                     "profiles/ens_stage_kernel_fp32_nl_flooded2000x1000.md"),
 }
-# FP64 issue rate of GB300: 2 DFMA per SM per cycle (ncu
-# sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / cycle), 152 SMs
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP64 issue rate of GB300 by ncu's peak_sustained (2 DFMA per SM per cycle), used only
+# if the live measurement below cannot run
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07
+FP64_PEAK_REPS, FP64_PEAK_ITERS = 30, 16384
+
+
+def fp64_peak(B, local):
+    """FP64 FMA throughput measured on this GPU (dg2_fp64_fma_peak: independent DFMA
+    chains on every SM, CUDA-event timed), median of back-to-back runs over about a
+    second, with the SM clock sampled meanwhile."""
+    clk = ClockSampler(local)
+    clk.start()
+    runs = [B.dg2_fp64_fma_peak(4, FP64_PEAK_ITERS)[0] for _ in range(FP64_PEAK_REPS)]
+    c = clk.stop()
+    return {"gflops": float(np.median(runs)), "max_gflops": float(np.max(runs)),
+            "runs": FP64_PEAK_REPS, "clocks": c,
+            "how": "dg2_fp64_fma_peak: 4 x 256 threads per SM, 8 independent DFMA chains of "
+                   f"{FP64_PEAK_ITERS} per thread, 2 FLOP per FMA, median of "
+                   f"{FP64_PEAK_REPS} back-to-back runs"}
 
 
 def parse():
@@ -200,7 +216,7 @@ def spun_up(B, case, t_spin, variant=0):
     return st, t, n
 
 
-def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src, key=""):
+def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src, key="", fp64=None):
     """Roofline of the dominant kernel of one timed run (live CUDA-event timing).
     FP64: FP64-pipe bound, algorithmic FLOPs per wet cell; FP32: HBM bound, unique
     bytes per cell of the tiles the kernels computed (counted on the device; dry
@@ -216,10 +232,13 @@ def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src, key=""):
         per_cell = tab if dom == 0 else tab[var]
         wet = run["wet_fraction"] * cells
         achieved = per_cell * wet / (kms[dom] * 1e-3) / 1e9
-        return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "traffic_profile": prof,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
+        if fp64:
+            peak, src = fp64["gflops"], "measured on this GPU (" + fp64["how"] + ")"
+        else:
+            peak, src = FP64_PEAK_DERIVED, "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"
+        return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "GFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_profile": prof, "peak_source": src,
                 "flops_per_wet_cell": per_cell, "wet_cells": wet, "kernel_ms": kernel_ms}
     tab = BYTES_PER_CELL[prec][KERNELS[dom]]
     per_cell = tab if dom == 0 else tab[var]
@@ -231,11 +250,12 @@ def kernel_roofline(run, prec, var, cells, peak_gbs, peak_src, key=""):
             "bytes_per_cell": per_cell, "active_cells": act, "kernel_ms": kernel_ms}
 
 
-def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=0, start=None):
+def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=0, start=None,
+                 wetdry=0):
     """Device-timed steps of one variant, from `start` = (planes, t), or after running
     the solver itself to t = `start` (a number; untimed spin-up), or from the case's
     initial state (None)."""
-    s = B.solver_from_case(case, variant=variant, precision=precision)
+    s = B.solver_from_case(case, variant=variant, precision=precision, wetdry=wetdry)
     if isinstance(start, tuple):
         s.set_state(start[0], start[1])
     elif start is not None:
@@ -262,10 +282,11 @@ def time_variant(B, torch, case, variant, steps, warmup, timing=True, precision=
     kt, n = B.dg2_kernel_times(s.ctx) if timing else (np.zeros(3), 0)
     tiles = s.tile_stats()[3] - tiles0
     t_sim, _ = s.time()
+    finite = bool(np.isfinite(s.state()).all())
     return {"solver": s, "ms": ms, "launches": launches, "kernel_ms": kt, "timed": n,
             "wet_fraction": wet,
             "active_cells": int(np.prod(s.tile_shape())) * tiles / max(steps, 1),
-            "t_sim": t_sim}
+            "t_sim": t_sim, "finite": finite}
 
 
 def e2e_run(B, torch, case, variant, steps, start):
@@ -287,20 +308,48 @@ def e2e_run(B, torch, case, variant, steps, start):
     return dt_s, pin_in.nbytes, pin_out.nbytes + 16
 
 
-def cpu_baseline(case_small, steps_budget_s=15.0, variant_ll=True):
+CPU_STEPS = 20            # oracle steps timed from the GPU's saved state
+CPU_SERIAL_BUDGET_S = 30.0
+
+
+def _oracle_from(case, start, threads, limiter=True):
     import oracle
-    o = oracle.Oracle(case_small.nx, case_small.ny, case_small.dx, case_small.dy, cfl=case_small.cfl,
-                      limiter=variant_ll, bc=case_small.bc)
-    o.set_dem(case_small.z_corner, case_small.manning, case_small.n_uniform, case_small.eta_corner)
-    for f in case_small.inflows:
+    o = oracle.Oracle(case.nx, case.ny, case.dx, case.dy, cfl=case.cfl, limiter=limiter,
+                      bc=case.bc, dt_max=case.dt_max, threads=threads)
+    o.set_dem(case.z_corner, case.manning, case.n_uniform, case.eta_corner)
+    for f in case.inflows:
         o.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)
-    o.step()
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < steps_budget_s:
+    o.set_state(start[0], start[1])
+    return o
+
+
+def cpu_baseline(case, start, steps=CPU_STEPS):
+    """The oracle (FP64 DG2-LL, default face revision) on the GPU's own workload: the
+    full floodplain grid from the same saved t = 1 h state the GPU variants step from,
+    `steps` Courant steps on every host core (the oracle's OpenMP build: rows in
+    parallel, bit-identical to the serial build) and on one core (the serial build,
+    stopped after CPU_SERIAL_BUDGET_S if slower).  Every cell counts, as on the GPU."""
+    import oracle
+    cores = os.cpu_count() or 1
+    o = _oracle_from(case, start, threads=True)
+    used = oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    for _ in range(steps):
         o.step()
-        n += 1
-    el = time.perf_counter() - t0
-    return case_small.nx * case_small.ny * n / el, n, el
+    el_all = time.perf_counter() - t0
+    o1 = _oracle_from(case, start, threads=False)
+    n1, t0 = 0, time.perf_counter()
+    while n1 < steps and time.perf_counter() - t0 < CPU_SERIAL_BUDGET_S:
+        o1.step()
+        n1 += 1
+    el_1 = time.perf_counter() - t0
+    cells = case.nx * case.ny
+    return {"value": cells * steps / el_all, "unit": "cell-updates/s", "cores": used,
+            "kind": "oracle",
+            "value_1core": cells * n1 / el_1,
+            "sample": f"{steps} DG2-LL steps of the full {case.nx}x{case.ny} floodplain from the "
+                      f"same saved t = {start[1]:.0f} s state the GPU times ({el_all:.1f} s on "
+                      f"{used} threads); one core: {n1} steps in {el_1:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -308,7 +357,9 @@ def run_reference(args, rank, world):
         return
     small = workload(500, 250)
     import oracle
-    o = oracle.Oracle(small.nx, small.ny, small.dx, small.dy, cfl=small.cfl, limiter=True, bc=small.bc)
+    o = oracle.Oracle(small.nx, small.ny, small.dx, small.dy, cfl=small.cfl, limiter=True, bc=small.bc,
+                      threads=True)
+    cores = oracle.set_threads(os.cpu_count() or 1)
     o.set_dem(small.z_corner, small.manning, small.n_uniform, small.eta_corner)
     for f in small.inflows:
         o.add_inflow(f.edge, f.s0, f.length, f.t_knots, f.q_knots)
@@ -325,16 +376,18 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "floodplain 500x250 dx=2 m (bounded sample of the 2000x1000 "
                                    "floodplain recipe), DG2-LL, FP64 CPU oracle"},
-            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} DG2-LL steps on a 500x250 floodplain"},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} DG2-LL steps on a 500x250 floodplain (same "
+                                       f"recipe, channel start), OpenMP build on {cores} threads"},
             "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 VARIANTS = [
-    # key, workload, variant, precision
+    # key, workload, variant, precision[, face revision: 1 = as printed in Sec. 2.1.2]
     ("fp64_ll", "floodplain", 1, 0),
+    ("fp64_ll_printed", "floodplain", 1, 0, 1),
     ("fp64_nl", "floodplain", 0, 0),
     ("fp32_ll", "floodplain", 1, 1),
     ("fp32_nl", "floodplain", 0, 1),
@@ -555,9 +608,16 @@ def main():
     warmup = max(3, args.warmup)
     pk, pk_src = peaks()
 
+    fp64 = None
+    try:
+        fp64 = fp64_peak(B, local)
+    except Exception as e:  # noqa: BLE001 -- reported, the derived peak is used instead
+        print(f"FP64 peak measurement failed: {e}", file=sys.stderr)
+
     results = {}
     clocks = None
-    for key, wl, var, prec in VARIANTS:
+    for key, wl, var, prec, *rest in VARIANTS:
+        wd = rest[0] if rest else 0
         if only and key not in only:
             continue
         barrier(world)
@@ -567,7 +627,8 @@ def main():
         case = cases[wl]
         ncell = case.nx * case.ny
         nsteps = URBAN_STEPS if (wl == "urban" and args.steps >= 50) else args.steps
-        run = time_variant(B, torch, case, var, nsteps, warmup, precision=prec, start=starts[wl])
+        run = time_variant(B, torch, case, var, nsteps, warmup, precision=prec, start=starts[wl],
+                           wetdry=wd)
         if clk:
             clocks = clk.stop()
         ms = max_over_ranks(run["ms"], world)
@@ -576,7 +637,7 @@ def main():
         run["steps"] = nsteps
         run["cells"] = ncell
         run["roofline"] = kernel_roofline(run, "fp32" if prec else "fp64", "ll" if var else "nl",
-                                          ncell, pk["hbm_gbs"], pk_src, key)
+                                          ncell, pk["hbm_gbs"], pk_src, key, fp64)
         run.pop("solver").close()
         results[key] = run
         torch.cuda.empty_cache()
@@ -621,13 +682,12 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n, el = cpu_baseline(workload(500, 250))
-        cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} DG2-LL steps of a 500x250 floodplain (same recipe), {el:.1f} s"}
+        cpu = cpu_baseline(cases["floodplain"], starts["floodplain"])
     if rank == 0:
         variants = {k: {"value": r["value"], "ms_per_step": r["ms_max"] / r["steps"],
                         "steps": r["steps"], "cells": r["cells"],
-                        "wet_fraction": r["wet_fraction"], "roofline": r["roofline"]}
+                        "wet_fraction": r["wet_fraction"], "finite": r["finite"],
+                        "roofline": r["roofline"]}
                     for k, r in results.items() if k != head}
         if ens is not None:
             variants["fp32_nl_ensemble"] = ens
@@ -640,7 +700,10 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if head.startswith("fp64") else "f32", "data": "synthetic",
                 "config": {"workload": "floodplain 2000x1000 dx=2 m from t=1 h (channel start run to "
-                                       "the hydrograph peak), DG2-LL, FP64"
+                                       "the hydrograph peak), DG2-LL, FP64, default face revision "
+                                       "(positivity-consistent revision of partially wet cells, a "
+                                       "repair of Sec. 2.1.2's; the printed revision is variant "
+                                       "fp64_ll_printed)"
                            if head == "fp64_ll" else head,
                            "variant": head, "cells": cells, "t_start_s": SPIN_T,
                            "spin_up_steps": nspin,
@@ -649,7 +712,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "variants": variants,
                 "gpu_launches": int(hd["launches"]), "roofline": hd["roofline"], "e2e": e2e,
-                "cpu_baseline": cpu, "clocks": clocks}
+                "cpu_baseline": cpu, "clocks": clocks, "fp64_peak": fp64}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

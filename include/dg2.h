@@ -109,14 +109,17 @@ const char *dg2_last_error(void);
  * Manning n, per-block partials, the gauge buffers and device scalars. */
 size_t dg2_workspace_bytes(int nx, int ny, const dg2_params *p);
 
-/* Creates a context on the current CUDA device.
+/* Creates a context on the current CUDA device for the uniform Cartesian grid
+ * of Sec. 2.1.1 (cells Q_c of size dx x dy, the stencil of Fig. 1).
  * nx, ny >= 1; dx, dy > 0; p may be NULL for defaults.  dev_workspace must be
  * 256-byte aligned device memory of ws_bytes >= dg2_workspace_bytes().  The
  * grid starts dry and flat until dg2_set_dem().  *out receives the context. */
 int dg2_init_grid(dg2_ctx **out, int nx, int ny, double dx, double dy, const dg2_params *p,
                   void *dev_workspace, size_t ws_bytes, void *cuda_stream);
 
-/* Topography, roughness and initial water (Sec. 2.1.1).
+/* Topography, roughness and initial water (Sec. 2.1.1: DEM values at the corner
+ * nodes, face-centred node values by averaging, modes by Eq. 3; Manning n of
+ * the friction term of Eq. 1).
  * z_corner: (ny+1)*(nx+1) DEM at corner nodes (m), required.
  * manning: ny*nx per-cell Manning n (s m^-1/3), or NULL to use n_uniform.
  * eta_corner: (ny+1)*(nx+1) initial free-surface elevation at corners, or NULL
@@ -129,7 +132,10 @@ int dg2_set_dem(dg2_ctx *ctx, const double *z_corner, const double *manning, dou
                 const double *eta_corner);
 
 /* Adds an inflow hydrograph Q(t) (m^3/s, piecewise linear in t_knots, held
- * constant outside them) on the faces of `edge` whose centres lie in
+ * constant outside them): the discharge hydrographs imposed at a breach or a
+ * west boundary in the paper's test cases (Sec. 3; Figs. 8, 11 and 14 show
+ * them; Fig. 5b is a water-level hydrograph, which this call does not model).
+ * It acts on the faces of `edge` whose centres lie in
  * [s0_m, s0_m + len_m] along the edge.  The discharge per unit width is Q
  * divided by the total length of those faces; it enters through a
  * critical-depth ghost state.  At most 8 inflows, 4096 knots each, t_knots
@@ -143,23 +149,32 @@ int dg2_set_bc_inflow(dg2_ctx *ctx, int edge, double s0_m, double len_m, const d
 int dg2_set_sources(dg2_ctx *ctx, double rain_mps, double rain_t0, double rain_t1, double px,
                     double py, double q_point_m3s);
 
-/* One RK2 time step (Sec. 2.1.2).  dt > 0 forces that step size; dt <= 0
- * takes the Courant-number step computed from the current state.  The step
+/* One RK2 time step (Sec. 2.1.2: two Runge-Kutta stages of the operators of
+ * Eqs. 4-5 with the revised face limits; Sec. 2.1.3: friction by implicit
+ * splitting before the step and, for DG2_LL, local limiting by Eqs. 6-7 before
+ * each stage; wet-dry flags by h0 against tol_dry).  dt > 0 forces that step
+ * size; dt <= 0 takes the Courant-number step (Cr of Sec. 2.1.2) computed from
+ * the current state.  The step
  * taken is written to *dt_taken (may be NULL; writing it synchronises). */
 int dg2_step(dg2_ctx *ctx, double dt, double *dt_taken);
 
-/* Advances until t_end with Courant-number steps, landing exactly on t_end
- * and on every gauge sample time.  Runs on the device with no host round
+/* Advances until t_end with Courant-number RK2 steps (as dg2_step, Sec. 2.1.2),
+ * landing exactly on t_end (the output time T of Table 2) and on every gauge
+ * sample time, so the time series of Sec. 3 (water level and velocity
+ * hydrographs at sampling points, compared by Eqs. 13-14) are recorded at
+ * exact times.  Runs on the device with no host round
  * trip per step (chunks of steps; a device flag stops work past t_end).
  * *steps_taken (may be NULL) receives the number of steps. */
 int dg2_run_to(dg2_ctx *ctx, double t_end, int64_t *steps_taken);
 
-/* Gauges: xy = ngauge (x, y) pairs in metres; depth max(0, planar h) in the
- * containing cell is recorded at every multiple of sample_every_s reached by
+/* Gauges: the sampling points of Sec. 3 (red dots of Figs. 5a, 8, 11, 14),
+ * whose depth time series the paper compares.  xy = ngauge (x, y) pairs in
+ * metres; depth max(0, planar h) of the containing cell's piecewise-planar
+ * solution (Eq. 2) is recorded at every multiple of sample_every_s reached by
  * dg2_run_to.  Replaces earlier gauges and clears the sample buffer. */
 int dg2_set_gauges(dg2_ctx *ctx, const double *xy, int ngauge, double sample_every_s);
 
-/* Copies the recorded samples out and clears the buffer: t_out[cap],
+/* The recorded gauge time series (Sec. 3), copied out; clears the buffer: t_out[cap],
  * h_out[cap][ngauge]; *nsamp = rows written.  DG2_E_OVERFLOW if samples were
  * dropped since the last read (the rows kept are still returned). */
 int dg2_read_gauges(dg2_ctx *ctx, double *t_out, double *h_out, int cap, int *nsamp);
@@ -224,9 +239,10 @@ int dg2_tile_stats(dg2_ctx *ctx, int *ntiles, int *n_active, int *n_frontier,
  *            legacy default stream); the call returns before it finishes.
  * Scratch: one partial per grid row and a block counter in a fixed
  * file-scope __device__ array (DG2_NOALLOC_MAX_ROWS doubles, 512 KiB), held by
- * every GPU that loads the library until the process exits.  The first call on
- * a device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  Every call
+ * every GPU that loads the library until the process exits.  Each call looks
+ * up that array's device address in the current context (cudaGetSymbolAddress,
+ * not cached, so a recreated context is followed); the first call on a device
+ * may load the module, so make it before any stream capture.  Every call
  * shares the array, so calls that overlap on the GPU race; the counter is
  * cleared at the start of each call.  DG2_E_ARG if ny > DG2_NOALLOC_MAX_ROWS,
  * nx or ny < 1, pitch < nx, dx or dy <= 0, or a pointer is NULL.  Calls no
@@ -236,6 +252,17 @@ int dg2_mass_noalloc(const double *h0_dev, int nx, int ny, int pitch, double dx,
 
 /* Releases the host-side context (the workspace stays the caller's). */
 int dg2_destroy(dg2_ctx *ctx);
+
+/* Measured FP64 arithmetic peak of the current GPU, the denominator of the FP64
+ * stage kernels' roofline (they are bound by the FP64 pipe, not by HBM; the paper
+ * has no counterpart).  Launches blocks_per_sm (1..8) blocks of 256 threads per SM,
+ * each thread running 8 independent chains of iters FP64 fused multiply-adds, once
+ * untimed and once timed with CUDA events on cuda_stream (void* cudaStream_t, NULL =
+ * legacy default stream); writes 2 x FMAs / time in GFLOP/s to *gflops and the
+ * timed kernel's milliseconds to *ms (may be NULL).  Synchronises the stream.
+ * Allocates nothing.  Errors: DG2_E_ARG (bad counts, gflops NULL), DG2_E_CUDA. */
+int dg2_fp64_fma_peak(int blocks_per_sm, int iters, void *cuda_stream, double *gflops,
+                      double *ms);
 
 /* ------------------------------------------------------------------------
  * Ensembles: many FP32 problems advanced together.

@@ -42,6 +42,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dg2_oracle.c")
 _LIB = os.path.join(_HERE, "libdg2_oracle.so")
+_OMP_LIB = os.path.join(_HERE, "libdg2_oracle_omp.so")
 _TAPE_SRC = os.path.join(_HERE, "tape.cpp")
 _TAPE_LIB = os.path.join(_HERE, "liboracle_tape.so")
 
@@ -49,6 +50,7 @@ WALL, OPEN = 0, 1
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 
 _lib = None
+_omp_lib = None
 
 
 def build(force: bool = False) -> str:
@@ -59,6 +61,19 @@ def build(force: bool = False) -> str:
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source with its rows-parallel loops enabled (gcc -fopenmp), for timing the
+    oracle on every host core: each cell writes only its own outputs and the edge-flux
+    sum is taken afterwards in cell order, so results equal the serial build's bit for
+    bit (tests/test_oracle_threads.py)."""
+    if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_SRC):
+        tmp = _OMP_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OMP_LIB)
+    return _OMP_LIB
 
 
 def build_tape(force: bool = False) -> str:
@@ -121,11 +136,13 @@ def taped_gradient(case, manning, q_knots, dts, sample_steps, obs, limiter=False
     return J, gn, gq
 
 
-def _load():
-    global _lib
-    if _lib is not None:
+def _load(omp: bool = False):
+    global _lib, _omp_lib
+    if omp and _omp_lib is not None:
+        return _omp_lib
+    if not omp and _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    lib = ctypes.CDLL(build_omp() if omp else build())
     P = ctypes.c_void_p
     D = ctypes.c_double
     I = ctypes.c_int
@@ -155,13 +172,23 @@ def _load():
         "orc_set_wetdry": (None, [P, I]),
         "orc_gauge_h": (D, [P, D, D]),
         "orc_run_to": (ctypes.c_long, [P, D, D, I, dp, dp, dp, I, ip]),
+        "orc_set_threads": (I, [I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
+    if omp:
+        _omp_lib = lib
+    else:
+        _lib = lib
     return lib
+
+
+def set_threads(n: int) -> int:
+    """Thread count of the OpenMP build (the serial build always uses one); returns the
+    count in use."""
+    return _load(omp=True).orc_set_threads(int(n))
 
 
 def _dp(a):
@@ -187,8 +214,9 @@ class Oracle:
 
     def __init__(self, nx, ny, dx, dy, *, g=9.80665, cfl=0.33, tol_dry=1e-5, ds_thresh=10.0,
                  dt_max=1.0, limiter=False, bc=(WALL, WALL, WALL, WALL), flux="hll",
-                 scheme="dg2", wetdry="positive"):
-        self.lib = _load()
+                 scheme="dg2", wetdry="positive", threads=False):
+        # threads=True: the OpenMP build (same results, rows in parallel; set_threads)
+        self.lib = _load(omp=bool(threads))
         self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
         self.g, self.cfl, self.tol_dry = g, cfl, tol_dry
         bca = (ctypes.c_int * 4)(*[int(b) for b in bc])

@@ -36,6 +36,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef ORC_REAL
 typedef double real;
@@ -79,6 +82,8 @@ typedef struct {
     real *nm;              /* Manning n per cell */
     real *U;               /* 9 planes (Eq. 2) */
     real *U1, *L, *Ls;     /* stage state, operator output, limiter scratch */
+    real *bnd;             /* mass fluxes of the edge faces of the last operator call:
+                              west [ny], east [ny], south [nx], north [nx] */
     double t;
     real ledger;           /* initial mass + boundary and source volumes */
     real last_bflux;       /* boundary + source volume rate of the last operator call */
@@ -458,7 +463,11 @@ static real spatial_operator(const orc_t *o, const real *U, double t, real *Lout
     const int csrc = source_cell(o);
     const int raining = (o->rain != 0.0 && t >= o->rain_t0 && t < o->rain_t1);
     real bsum = 0.0;
+    real *bw = o->bnd, *be = o->bnd + ny, *bs = o->bnd + 2 * ny, *bn = o->bnd + 2 * ny + nx;
 
+    /* every cell writes only its own outputs (rows may run in parallel when built
+     * with OpenMP: the results do not depend on it) */
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
@@ -494,10 +503,10 @@ static real spatial_operator(const orc_t *o, const real *U, double t, real *Lout
                 GN = hll_y(o, Ns, oN);
                 GS = hll_y(o, oS, Ss);
             }
-            if (i == 0) bsum += FW.h * dy;
-            if (i == nx - 1) bsum -= FE.h * dy;
-            if (j == 0) bsum += GS.h * dx;
-            if (j == ny - 1) bsum -= GN.h * dx;
+            if (i == 0) bw[j] = FW.h;
+            if (i == nx - 1) be[j] = FE.h;
+            if (j == 0) bs[i] = GS.h;
+            if (j == ny - 1) bn[i] = GN.h;
             /* dummy modes, Eq. 5 (Eq. 5b read as the 0y mode) */
             st3 U0x = mk(0.5 * (Es.h + Ws.h), 0.5 * (Es.qx + Ws.qx), 0.5 * (Es.qy + Ws.qy));
             st3 U1x = mk(0.5 * (Es.h - Ws.h), 0.5 * (Es.qx - Ws.qx), 0.5 * (Es.qy - Ws.qy));
@@ -534,6 +543,14 @@ static real spatial_operator(const orc_t *o, const real *U, double t, real *Lout
             Lout[PL(1, 2) * N + c] = L1yx;
             Lout[PL(2, 2) * N + c] = L1yy;
         }
+    /* volume rate through the domain edges, summed in cell order */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            if (i == 0) bsum += bw[j] * dy;
+            if (i == nx - 1) bsum -= be[j] * dy;
+            if (j == 0) bsum += bs[i] * dx;
+            if (j == ny - 1) bsum -= bn[i] * dx;
+        }
     if (raining) bsum += o->rain * dx * dy * (double)N;
     if (csrc >= 0) bsum += o->qp;
     return bsum;
@@ -559,6 +576,7 @@ static void apply_friction(orc_t *o, real *U, double dt)
 {
     const size_t N = (size_t)o->nx * o->ny;
     const real s3 = sqrt(3.0);
+#pragma omp parallel for schedule(static)
     for (size_t c = 0; c < N; ++c) {
         real n = o->nm[c];
         real h0 = U[PL(0, 0) * N + c], x0 = U[PL(1, 0) * N + c], y0 = U[PL(2, 0) * N + c];
@@ -627,6 +645,7 @@ static void apply_limiter(const orc_t *o, const real *Uin, real *Uout)
     const int nx = o->nx, ny = o->ny;
     const size_t N = (size_t)nx * ny;
     memcpy(Uout, Uin, 9 * N * sizeof(real));
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
@@ -672,6 +691,7 @@ static void apply_limiter(const orc_t *o, const real *Uin, real *Uout)
 static void dry_reset(const orc_t *o, real *U)
 {
     const size_t N = (size_t)o->nx * o->ny;
+#pragma omp parallel for schedule(static)
     for (size_t c = 0; c < N; ++c) {
         real h0 = U[c];
         if (h0 <= o->tol_dry) {
@@ -914,6 +934,7 @@ void orc_step(orc_t *o, double dt)
         memcpy(Un, o->Ls, 9 * N * sizeof(real));
     }
     real b1 = spatial_operator(o, Un, o->t, L);
+#pragma omp parallel for schedule(static)
     for (size_t k = 0; k < 9 * N; ++k) U1[k] = Un[k] + dt * L[k];
     dry_reset(o, U1);
     if (o->limiter) {
@@ -921,6 +942,7 @@ void orc_step(orc_t *o, double dt)
         memcpy(U1, o->Ls, 9 * N * sizeof(real));
     }
     real b2 = spatial_operator(o, U1, o->t + dt, L);
+#pragma omp parallel for schedule(static)
     for (size_t k = 0; k < 9 * N; ++k) Un[k] = 0.5 * (Un[k] + U1[k] + dt * L[k]);
     dry_reset(o, Un);
     o->last_bflux = 0.5 * (b1 + b2);
@@ -977,13 +999,14 @@ orc_t *orc_create(int nx, int ny, double dx, double dy, double g, double cfl, do
     o->U1 = (real *)calloc(9 * N, sizeof(real));
     o->L = (real *)calloc(9 * N, sizeof(real));
     o->Ls = (real *)calloc(9 * N, sizeof(real));
+    o->bnd = (real *)calloc(2 * ((size_t)nx + ny), sizeof(real));
     return o;
 }
 
 void orc_destroy(orc_t *o)
 {
     if (!o) return;
-    free(o->z); free(o->nm); free(o->U); free(o->U1); free(o->L); free(o->Ls);
+    free(o->z); free(o->nm); free(o->U); free(o->U1); free(o->L); free(o->Ls); free(o->bnd);
     free(o);
 }
 
@@ -1108,6 +1131,19 @@ void orc_set_flux(orc_t *o, int flux) { o->flux = flux; }
 /* Scheme of the run: 0 DG2 (default), 1 MUSCL-FV2, 2 FV1 (set before orc_set_dem). */
 void orc_set_scheme(orc_t *o, int scheme) { o->scheme = scheme; }
 void orc_set_wetdry(orc_t *o, int wd) { o->wd = wd; }
+
+/* Threads of the rows-parallel loops: effective only in a build with OpenMP
+ * (the results are the same for any count); returns the count in use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* Depth at (x, y) from the planar solution of the containing cell, clipped at 0. */
 double orc_gauge_h(const orc_t *o, double x, double y)

@@ -33,7 +33,8 @@ EXPORTS = (
     "dg2_set_bc_inflow", "dg2_set_sources", "dg2_step", "dg2_run_to", "dg2_set_gauges",
     "dg2_read_gauges", "dg2_mass", "dg2_get_state", "dg2_set_state", "dg2_get_topo",
     "dg2_get_time", "dg2_enable_kernel_timing", "dg2_kernel_times", "dg2_launch_count",
-    "dg2_tile_stats", "dg2_tile_shape", "dg2_get_steps", "dg2_mass_noalloc", "dg2_destroy",
+    "dg2_tile_stats", "dg2_tile_shape", "dg2_get_steps", "dg2_mass_noalloc", "dg2_fp64_fma_peak",
+    "dg2_destroy",
     "dg2_ens_workspace_bytes", "dg2_ens_create", "dg2_ens_run_to", "dg2_ens_autotune",
     "dg2_ens_set_tile_shape", "dg2_ens_tile_shape", "dg2_ens_tune_times",
     "dg2_ens_launch_count", "dg2_ens_destroy",
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH):
         "dg2_tile_stats": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
         "dg2_mass_noalloc": (I, [P, I, I, I, D, D, P, P]),
+        "dg2_fp64_fma_peak": (I, [I, I, P, dp, dp]),
         "dg2_destroy": (I, [P]),
         "dg2_ens_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(P), I]),
         "dg2_ens_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P, ctypes.c_size_t, P]),
@@ -276,6 +278,14 @@ def dg2_mass_noalloc(h0_ptr: int, nx: int, ny: int, pitch: int, dx: float, dy: f
     (the library's fixed scratch); see include/dg2.h."""
     _check(load().dg2_mass_noalloc(ctypes.c_void_p(h0_ptr), nx, ny, pitch, float(dx), float(dy),
                                    ctypes.c_void_p(mass_ptr), ctypes.c_void_p(stream_ptr)))
+
+
+def dg2_fp64_fma_peak(blocks_per_sm: int = 4, iters: int = 4096, stream_ptr: int = 0):
+    """Measured FP64 FMA throughput of the current GPU: (GFLOP/s, kernel ms)."""
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().dg2_fp64_fma_peak(int(blocks_per_sm), int(iters), stream_ptr, ctypes.byref(g),
+                                    ctypes.byref(ms)))
+    return g.value, ms.value
 
 
 def dg2_destroy(ctx):

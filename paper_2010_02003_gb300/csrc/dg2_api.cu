@@ -134,6 +134,9 @@ struct dg2_ctx {
   cudaStream_t st;
   char* ws;
   int dem_set;
+  // a read of the device scalars found the non-finite flag raised: further steps are
+  // refused until dg2_set_dem / dg2_set_state give a valid state again
+  int poisoned;
   int64_t launches;
   dim3 sgrid, sblock, pgrid, pblock;
   int g_fric, g_st1, g_st2;   // persistent grid sizes (blocks) of friction / stage 1 / stage 2
@@ -306,6 +309,16 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
 int read_scalars(dg2_ctx* c, Scalars* out) {
   CU(cudaMemcpyAsync(out, c->d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
   CU(cudaStreamSynchronize(c->st));
+  if (out->nonfinite) c->poisoned = 1;
+  return DG2_OK;
+}
+
+// Steps refuse to run on a state already known to be non-finite.
+int check_not_poisoned(dg2_ctx* c) {
+  if (c->poisoned)
+    return fail(DG2_E_NONFINITE,
+                "the state became non-finite in an earlier step; dg2_set_state or dg2_set_dem "
+                "must provide a valid state before stepping again");
   return DG2_OK;
 }
 
@@ -644,6 +657,7 @@ int dg2_set_dem(dg2_ctx* c, const double* z_corner, const double* manning, doubl
   s0.nsamp = 0;
   s0.done = 0;
   s0.nonfinite = 0;
+  c->poisoned = 0;
   s0.steps = 0;
   s0.count = 0;
   s0.lam_bits = 0;
@@ -730,6 +744,7 @@ int dg2_step(dg2_ctx* c, double dt, double* dt_taken) {
   int r = check_arg_ctx(c, true);
   if (r) return r;
   if (!std::isfinite(dt)) return fail(DG2_E_ARG, "dt must be finite");
+  if ((r = check_not_poisoned(c))) return r;
   dg2::begin_step_kernel<<<1, 1, 0, c->st>>>(c->d, dt);
   enqueue_step(c, true);
   if ((r = launch_check(c, 6))) return r;
@@ -746,8 +761,10 @@ int dg2_run_to(dg2_ctx* c, double t_end, int64_t* steps_taken) {
   int r = check_arg_ctx(c, true);
   if (r) return r;
   if (!std::isfinite(t_end)) return fail(DG2_E_ARG, "t_end must be finite");
+  if ((r = check_not_poisoned(c))) return r;
   Scalars s;
   if ((r = read_scalars(c, &s))) return r;
+  if ((r = check_not_poisoned(c))) return r;
   const long long steps0 = s.steps;
   if (s.t >= t_end) {
     if (steps_taken) *steps_taken = 0;
@@ -943,6 +960,7 @@ int dg2_set_state(dg2_ctx* c, const double* planes, double t) {
   s.t = t;
   s.done = 0;
   s.nonfinite = 0;
+  c->poisoned = 0;
   s.t_end = INFINITY;
   s.next_sample = s.sample_every > 0.0 ? (std::floor(t / s.sample_every + 1e-9) + 1.0) * s.sample_every
                                        : INFINITY;

@@ -661,6 +661,11 @@ int dg2_ens_run_to(dg2_ens* e, double t_end, int64_t* steps_taken) {
   if ((r = begin_run(e, t_end))) return r;
   EnsScalars s;
   if ((r = read_es(e, &s))) return r;
+  // the start of a run gathers the members' non-finite flags: a member whose state
+  // became non-finite is refused until dg2_set_state / dg2_set_dem restore it
+  if (s.bad)
+    return efail(DG2_E_NONFINITE, "a member's state is non-finite; restore it with "
+                                  "dg2_set_state or dg2_set_dem before running");
   const int n = (int)e->mem.size();
   int64_t taken = 0;
   int lv = 0;
@@ -685,6 +690,13 @@ int dg2_ens_autotune(dg2_ens* e, double t_end, int steps_per_trial, int* tile_w,
   if (steps_per_trial < 4) return efail(DG2_E_ARG, "steps_per_trial must be >= 4");
   if ((r = sync_members(e))) return r;
   if ((r = begin_run(e, t_end))) return r;
+  {
+    EnsScalars s0;
+    if ((r = read_es(e, &s0))) return r;
+    if (s0.bad)
+      return efail(DG2_E_NONFINITE, "a member's state is non-finite; restore it with "
+                                    "dg2_set_state or dg2_set_dem before tuning");
+  }
   cudaEvent_t a, b;
   ECU(cudaEventCreate(&a));
   ECU(cudaEventCreate(&b));

@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "../../include/dg2.h"
@@ -25,7 +24,6 @@ void set_error_text(const std::string& s);  // dg2_api.cu
 namespace {
 
 constexpr int kRowsPerBlock = 8;   // one warp per grid row
-constexpr int kMaxDevices = 64;
 
 // Per-row sums of the last call (row j of the grid in slot j) and the count of
 // blocks that have finished; the count is cleared before every call and by the
@@ -37,32 +35,27 @@ struct DevScratch {
   double* rows = nullptr;
   unsigned int* done = nullptr;
 };
-DevScratch g_dev[kMaxDevices];
-std::mutex g_mu;
 
 int noalloc_fail(int code, const std::string& msg) {
   dg2::set_error_text(msg);  // reported by dg2_last_error()
   return code;
 }
 
-// Looks up the device addresses of the scratch for the current device, once.
-int scratch_for_current_device(DevScratch* out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return noalloc_fail(DG2_E_CUDA, "no current CUDA device");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev[dev].rows) {
-    void* rows = nullptr;
-    void* done = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&rows, g_row_sum);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(&done, g_blocks_done);
-    if (e != cudaSuccess)
-      return noalloc_fail(DG2_E_CUDA, std::string("cudaGetSymbolAddress failed: ") +
-                                          cudaGetErrorString(e));
-    g_dev[dev].rows = (double*)rows;
-    g_dev[dev].done = (unsigned int*)done;
-  }
-  *out = g_dev[dev];
+// Looks up the device addresses of the scratch in the current context.  The
+// lookup is repeated on every call rather than cached: a context that is torn
+// down and recreated (cudaDeviceReset, a host that rebuilds its context) loads
+// the module again, possibly at another address, and a cached pointer would
+// then point at memory that is no longer this array.
+int scratch_for_current_context(DevScratch* out) {
+  void* rows = nullptr;
+  void* done = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&rows, g_row_sum);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&done, g_blocks_done);
+  if (e != cudaSuccess)
+    return noalloc_fail(DG2_E_CUDA, std::string("cudaGetSymbolAddress failed: ") +
+                                        cudaGetErrorString(e));
+  out->rows = (double*)rows;
+  out->done = (unsigned int*)done;
   return DG2_OK;
 }
 
@@ -117,7 +110,7 @@ extern "C" int dg2_mass_noalloc(const double* h0_dev, int nx, int ny, int pitch,
                         "partial sum per grid row");
   if (!(dx > 0.0) || !(dy > 0.0)) return noalloc_fail(DG2_E_ARG, "dx, dy must be positive");
   DevScratch sc;
-  int r = scratch_for_current_device(&sc);
+  int r = scratch_for_current_context(&sc);
   if (r) return r;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // the block counter must start at zero (an earlier failed launch may have left it set)

@@ -27,6 +27,12 @@ MUTANTS = [
      "for (int k = 1; k < 3; ++k) U[k * N + c] = 0.0;"),
     ("y flux: u for v in the mass flux", "return mk(s.h * v, s.h * u * v,",
      "return mk(s.h * u, s.h * u * v,"),
+    ("gauge xi over dx, not dx / 2", "double xi = (x - (i + 0.5) * o->dx) / (0.5 * o->dx)",
+     "double xi = (x - (i + 0.5) * o->dx) / o->dx"),
+    ("gauge eta scaled by dx", "et = (y - (j + 0.5) * o->dy) / (0.5 * o->dy)",
+     "et = (y - (j + 0.5) * o->dy) / (0.5 * o->dx)"),
+    ("gauge depth not clipped", "    return h > 0.0 ? h : 0.0;\n}\n\n/* Advances to t_end",
+     "    return h;\n}\n\n/* Advances to t_end"),
 ]
 
 

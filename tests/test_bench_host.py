@@ -17,20 +17,29 @@ def bench():
     return m
 
 
-def test_fp64_peak_is_the_derived_dfma_rate(bench):
-    assert bench.FP64_PEAK_GFLOPS == pytest.approx(152 * 2 * 2 * 2.07)
+def test_fp64_peak_falls_back_to_the_derived_dfma_rate(bench):
+    assert bench.FP64_PEAK_DERIVED == pytest.approx(152 * 2 * 2 * 2.07)
+    run = {"kernel_ms": np.array([1.0, 2.0, 3.0]), "timed": 10, "wet_fraction": 0.25,
+           "active_cells": 123.0}
+    r = bench.kernel_roofline(run, "fp64", "ll", 1_000_000, 7000.0, "measured")
+    assert r["peak"] == pytest.approx(bench.FP64_PEAK_DERIVED) and "derived" in r["peak_source"]
+    m = bench.kernel_roofline(run, "fp64", "ll", 1_000_000, 7000.0, "measured",
+                              fp64={"gflops": 1000.0, "how": "test"})
+    assert m["peak"] == 1000.0 and m["frac"] == pytest.approx(r["achieved"] / 1000.0)
+    assert m["peak_source"].startswith("measured")
 
 
 def test_alu_roofline_counts_wet_cells(bench):
     # three kernels' summed milliseconds over 10 timed steps; stage 2 dominates
     run = {"kernel_ms": np.array([1.0, 2.0, 3.0]), "timed": 10, "wet_fraction": 0.25,
            "active_cells": 123.0}
-    r = bench.kernel_roofline(run, "fp64", "ll", 1_000_000, 7000.0, "measured")
+    r = bench.kernel_roofline(run, "fp64", "ll", 1_000_000, 7000.0, "measured",
+                              fp64={"gflops": 1200.0, "how": "test"})
     per = bench.FLOPS_PER_WET_CELL["stage2"]["ll"]
     expect = per * 250_000 / (0.3e-3) / 1e9
     assert r["bound"] == "alu" and r["unit"] == "GFLOP/s"
     assert r["achieved"] == pytest.approx(expect)
-    assert r["frac"] == pytest.approx(expect / bench.FP64_PEAK_GFLOPS)
+    assert r["frac"] == pytest.approx(expect / 1200.0)
     assert r["kernel_ms"]["stage2"] == pytest.approx(0.3)
 
 

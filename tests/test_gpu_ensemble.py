@@ -151,3 +151,71 @@ def test_ensemble_arguments_are_checked():
         ens.set_tile_shape(8, 8)
     with pytest.raises(B.Dg2Error):
         ens.autotune(10.0, steps_per_trial=2)
+
+
+def _fp32_errors(gpu, orc, g=9.80665):
+    hs = max(np.abs(orc[0]).max(), 1e-30)
+    qs = max(np.abs(orc[3]).max(), np.abs(orc[6]).max(), hs * np.sqrt(g * hs))
+    return np.abs(gpu[:3] - orc[:3]).max() / hs, np.abs(gpu[3:] - orc[3:]).max() / qs
+
+
+def _solo_dt_sequence(B, case, variant, t_end):
+    """The Courant steps a member takes alone up to t_end, found by stepping an FP32 twin
+    with dg2_step: each step the pending Courant step, the last one landing on t_end (the
+    rule of dg2_run_to, which the ensemble follows for every member)."""
+    s = B.solver_from_case(case, variant=variant, precision=B.DG2_FP32)
+    dts = []
+    while True:
+        t, dt_next = s.time()
+        if t + dt_next >= t_end:
+            dts.append(t_end - t)
+            s.step(t_end - t)
+            break
+        dts.append(s.step(-1.0, want_dt=True))
+    st = s.state()
+    s.close()
+    return np.array(dts), st
+
+
+# FP32 member error against the FP64 oracle over each member's own step sequence
+# (depth / discharge, relative to the member's depth and discharge scales).
+ENS_BAR = {0: (1e-3, 1e-3), 1: (1e-3, 1e-3)}
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["NL", "LL"])
+def test_uneven_members_against_the_fp64_oracle(variant):
+    """Six members of uneven sizes (33 x 17 to 96 x 64 cells), each with its own Manning
+    n, inflow peak and Courant steps, advanced together to t = 30 s; every member is
+    compared with the FP64 oracle run alone through that member's own step sequence
+    (the FP32 steps it takes alone, which the ensemble reproduces bit for bit)."""
+    from conftest import make_oracle
+    B = _B()
+    t_end = 30.0
+    cases = inputs.ensemble(n=6, seed=4242, nx_range=(33, 96), ny_range=(17, 64), t_peak=15.0,
+                            t_end=t_end, ngauge=2, sample_every=0.0)
+    sizes = {(c.nx, c.ny) for c in cases}
+    assert len(sizes) == 6
+    mem = _members(cases, variant)
+    ens = B.Ensemble(mem)
+    ens.run_to(t_end)
+    worst = (0.0, 0.0)
+    nsteps = []
+    for k, (case, s) in enumerate(zip(cases, mem)):
+        dts, solo = _solo_dt_sequence(B, case, variant, t_end)
+        got = s.state()
+        assert np.array_equal(got, solo), k                # ensemble == the member alone
+        assert s.time()[0] == t_end
+        o = make_oracle(case, limiter=bool(variant))
+        for dt in dts:
+            o.step(dt)
+        nsteps.append(len(dts))
+        eh, eq = _fp32_errors(got, o.state())
+        worst = (max(worst[0], eh), max(worst[1], eq))
+        assert np.abs(o.state()[0]).max() > 1e-3, k        # water has entered the member
+        m, led = s.mass()
+        assert abs(m - led) <= 1e-6 * max(led, 1.0), k
+    assert len(set(nsteps)) > 1                            # the members' steps differ
+    print(f"ensemble members vs FP64 oracle ({'LL' if variant else 'NL'}): depth {worst[0]:.2e}, "
+          f"discharge {worst[1]:.2e}, steps {nsteps}")
+    bh, bq = ENS_BAR[variant]
+    assert worst[0] < bh and worst[1] < bq, worst

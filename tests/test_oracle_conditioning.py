@@ -30,8 +30,13 @@ def _scaled_err(a, b, g=9.80665):
     return (np.abs(a - b).max(axis=1) / scale).max()
 
 
-def _twin_growth(start, steps, seeds, wetdry, limiter=True):
-    case = inputs.floodplain(nx=96, ny=64, dx=2.0, q_peak=15.0, t_peak=20.0, channel_width=12.0)
+def _twin_growth(start, steps, seeds, wetdry, limiter=True, initial="dry"):
+    if initial == "dry":
+        case = inputs.floodplain(nx=96, ny=64, dx=2.0, q_peak=15.0, t_peak=20.0,
+                                 channel_width=12.0)
+    else:
+        case = inputs.floodplain(nx=96, ny=64, dx=2.0, q_peak=15.0, t_peak=60.0,
+                                 initial="channel", channel_width=12.0)
     o = make_oracle(case, limiter=limiter, wetdry=wetdry)
     for _ in range(start):
         o.step()
@@ -63,3 +68,26 @@ def test_floodplain_windows_before_the_front_are_well_conditioned(limiter, wetdr
 @pytest.mark.parametrize("wetdry", ["positive", "paper"])
 def test_floodplain_ll_front_amplifies_roundoff(wetdry):
     assert _twin_growth(88, 12, range(6), wetdry, True).max() > 5e-13
+
+
+# The free-running parity horizons of the GPU tests: from the first wet state, the
+# twin runs stay well below the 1e-12 bar over the steps each case is held.
+HELD = {("positive", False): 84, ("positive", True): 84, ("paper", False): 99,
+        ("paper", True): 89}
+
+
+@pytest.mark.parametrize("wetdry", ["positive", "paper"])
+@pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
+def test_floodplain_start_is_well_conditioned_over_the_held_horizon(limiter, wetdry):
+    assert _twin_growth(1, HELD[(wetdry, limiter)], range(2), wetdry, limiter).max() < 1e-13
+
+
+@pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
+def test_channel_start_under_the_default_revision_is_well_conditioned(limiter):
+    assert _twin_growth(0, 100, range(2), "positive", limiter, "channel").max() < 1e-13
+
+
+def test_channel_start_under_the_printed_revision_amplifies_roundoff():
+    # partially wet bank cells offer their full planar face depth: held 50 steps on the GPU
+    assert _twin_growth(0, 50, range(2), "paper", False, "channel").max() < 1e-12
+    assert _twin_growth(0, 80, range(2), "paper", False, "channel").max() > 1e-13
