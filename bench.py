@@ -41,9 +41,12 @@ BYTES_PER_CELL = {
     "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
              "stage2": {"nl": 30 * 8, "ll": 30 * 8}},
     # FP32 free-surface form: 10 state planes (eta0 as hi + lo), 2 face-topography planes,
-    # Manning n
-    "fp32": {"friction": (13 + 6) * 4, "stage1": {"nl": (10 + 2 + 10) * 4, "ll": (10 + 2 + 16) * 4},
-             "stage2": {"nl": (10 + 10 + 2 + 10) * 4, "ll": (10 + 10 + 2 + 10) * 4}},
+    # Manning n; friction is fused into the stages (stage 1 applies it to the U^n it reads,
+    # stage 2 recomputes it for the RK average from U^n and n), so it moves no bytes of its own.
+    # Stage 1 reads U^n, the beds and n and writes U1 (+ the limited slopes Q in DG2-LL);
+    # stage 2 reads U1, U^n (DG2-LL: its averages and Q), the beds and n and writes U^n+1.
+    "fp32": {"friction": 0, "stage1": {"nl": (10 + 2 + 1 + 10) * 4, "ll": (10 + 2 + 1 + 16) * 4},
+             "stage2": {"nl": (10 + 10 + 1 + 2 + 10) * 4, "ll": (10 + 4 + 6 + 1 + 2 + 10) * 4}},
 }
 KERNELS = ["friction", "stage1", "stage2"]
 # Algorithmic FP64 operations per wet cell (add, mul, div, sqrt, cbrt each one), each
@@ -436,7 +439,7 @@ def ensemble_variant(B, torch, inputs, n=ENS_MEMBERS, t_end=ENS_T_END):
            "autotune_ms_per_step": [float(x) for x in ens.tune_times()],
            "autotune_s": tune_s, "launches": ens.launches() - l0,
            "computed_cells": tiles * shape[0] * shape[1], "wet_fraction_end": wet}
-    # whole-step HBM figure: unique bytes of friction + both stages per computed cell
+    # whole-step HBM figure: unique bytes of both stages per computed cell
     per_cell = sum(v if isinstance(v, int) else v["nl"] for v in BYTES_PER_CELL["fp32"].values())
     out["step_bytes_per_s"] = per_cell * out["computed_cells"] / (ms * 1e-3)
     ens.close()

@@ -253,8 +253,9 @@ void mirror(dg2_ctx* c) {
   f.tiles = d.tiles;
 }
 
-// Enqueues one RK2 step: friction, stage 1, stage 2, finalize, lists (5 kernels).  With
-// `timed`, records an event before and after each kernel.
+// Enqueues one RK2 step: friction, stage 1, stage 2, finalize, lists (5 kernels; 4 in
+// FP32, whose stages apply friction themselves).  With `timed`, records an event before
+// and after each kernel.
 void enqueue_step(dg2_ctx* c, bool timed = false) {
   const Dev& d = c->d;
   cudaEvent_t* e = nullptr;
@@ -269,10 +270,8 @@ void enqueue_step(dg2_ctx* c, bool timed = false) {
   }
   const bool ll = c->p.variant == DG2_LL;
   if (e) cudaEventRecord(e[0], c->st);
-  if (c->fp32)
-    dg2::ens::launch_friction32(c->e1, tile_w(c), c->g_fric, c->st);
-  else
-    dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
+  // FP32: friction is fused into the stage kernels (no launch of its own)
+  if (!c->fp32) dg2::friction_kernel<<<c->g_fric, c->pblock, 0, c->st>>>(d);
   if (e) cudaEventRecord(e[1], c->st);
   if (c->p.scheme != DG2_SCHEME_DG2) {
     // the FV comparators: one block per tile of the lists, as the DG2 stages
@@ -557,7 +556,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     cudaFuncSetAttribute(dg2::stage_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(dg2::StageSmem));
     if (f32) {
-      dg2::ens::occupancy32(tile_w(c), ll, &o0, &o1, &o2);
+      dg2::ens::occupancy32(tile_w(c), ll, &o1, &o2);
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, dg2::friction_kernel, 256, 0);
       if (ll) {
@@ -747,7 +746,7 @@ int dg2_step(dg2_ctx* c, double dt, double* dt_taken) {
   if ((r = check_not_poisoned(c))) return r;
   dg2::begin_step_kernel<<<1, 1, 0, c->st>>>(c->d, dt);
   enqueue_step(c, true);
-  if ((r = launch_check(c, 6))) return r;
+  if ((r = launch_check(c, c->fp32 ? 5 : 6))) return r;
   if (dt_taken) {
     Scalars s;
     if ((r = read_scalars(c, &s))) return r;
@@ -796,7 +795,7 @@ int dg2_run_to(dg2_ctx* c, double t_end, int64_t* steps_taken) {
       for (int k = 0; k < chunk; ++k) enqueue_step(c);
       if ((r = launch_check(c, 0))) return r;
     }
-    c->launches += 5 * (int64_t)chunk;
+    c->launches += (c->fp32 ? 4 : 5) * (int64_t)chunk;
     if ((r = read_scalars(c, &s))) return r;
     if (s.nonfinite) return fail(DG2_E_NONFINITE, "non-finite state or step near t=%g", s.t);
     if (s.done) break;

@@ -2,12 +2,12 @@
 // include/dg2.h, dg2_ens_*).
 //
 // Every member is an ordinary FP32 context (its own grid, DEM, Manning field,
-// inflows, gauges, time and Courant step).  One step of the ensemble is five
-// launches for all members at once: friction, stage 1, stage 2 over one list
-// of (member, tile) entries, a one-block-per-member end of step (time, ledger,
-// gauges, the member's next dt), and a lists kernel that classifies every
-// tile of every unfinished member and appends the computed ones to the next
-// step's list.  A member whose run has reached t_end drops out of the lists;
+// inflows, gauges, time and Courant step).  One step of the ensemble is four
+// launches for all members at once: stage 1 (with friction fused) and stage 2
+// over one list of (member, tile) entries, a one-block-per-member end of step
+// (time, ledger, gauges, the member's next dt), and a lists kernel that
+// classifies every tile of every unfinished member and appends the computed
+// ones to the next step's list.  A member whose run has reached t_end drops out of the lists;
 // the others keep stepping with their own dt.  Chunks of steps are replayed
 // from CUDA graphs.  The tile shape (cells per tile, one thread per cell) is a
 // template parameter picked among kShapes by dg2_ens_autotune, which times
@@ -26,6 +26,7 @@
 #include "../../include/dg2.h"
 #include "dg2_device.cuh"
 #include "dg2_fs32.cuh"
+#include "dg2_fs32_staged.cuh"
 #include "dg2_internal.h"
 
 using dg2::Scalars;
@@ -52,28 +53,7 @@ __device__ __forceinline__ void unpack(int ent, int& m, int& tile) {
 
 // A member that reached t_end in the previous step keeps its list entries for
 // that one step (its lists were built before it was known); its tiles are
-// skipped here and in the stage kernels.
-template <int BX, int BY>
-__global__ void __launch_bounds__(BX* BY) ens_friction_kernel(EnsDev E) {
-  __shared__ float s_gdt;
-  __shared__ int s_skip;
-  const int n = E.es->n_act;
-  for (int e = blockIdx.x; e < n; e += gridDim.x) {
-    int m, tile;
-    unpack(E.list[e], m, tile);
-    const D32& d = E.desc[m];
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      s_gdt = (float)(d.sc->dt * (double)d.g);
-      s_skip = d.sc->done;
-    }
-    __syncthreads();
-    if (!s_skip) {
-      const int ntx = d.tiles.ntx;
-      f32::friction32_tile<BX, BY>(d, s_gdt, tile % ntx, tile / ntx);
-    }
-    __syncthreads();
-  }
-}
+// skipped in the stage kernels.
 
 // resident 256-thread blocks per SM asked of the register allocator for the FP32
 // stage kernels (twice that for 128-thread tiles)
@@ -81,10 +61,18 @@ __global__ void __launch_bounds__(BX* BY) ens_friction_kernel(EnsDev E) {
 #define DG2_MINB32 3
 #endif
 
+// Shared memory of a stage block (dynamic: above the 48 KB static limit for some
+// shapes; the limit is raised once per process by prepare_stage32).
+template <bool LL, int STAGE, int BX, int BY>
+constexpr int stage32_smem() {
+  return (int)sizeof(f32::StagedSmem32<LL, STAGE, BX, BY>);
+}
+
 template <bool LL, int STAGE, int BX, int BY>
 __global__ void __launch_bounds__(BX* BY, BX * BY <= 128 ? 2 * DG2_MINB32 : DG2_MINB32)
     ens_stage_kernel(EnsDev E) {
-  __shared__ f32::StageSmem32T<BX, BY> sm;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<f32::StagedSmem32<LL, STAGE, BX, BY>*>(smem_raw);
   __shared__ f32::Blk32 blk;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool t0 = tx == 0 && ty == 0;
@@ -101,6 +89,7 @@ __global__ void __launch_bounds__(BX* BY, BX * BY <= 128 ? 2 * DG2_MINB32 : DG2_
       blk.dtd = dtd;
       blk.ts = ts;
       blk.dt = (float)dtd;
+      blk.gdt = (float)(dtd * (double)d.g);
       blk.rain = d.rain != 0.0 && ts >= d.rain_t0 && ts < d.rain_t1;
       blk.rainf = (float)d.rain;
       blk.skip = sc->done;
@@ -114,7 +103,7 @@ __global__ void __launch_bounds__(BX* BY, BX * BY <= 128 ? 2 * DG2_MINB32 : DG2_
     const int bx = tile % ntx, by = tile / ntx;
     float brate = 0.f, lam = 0.f;
     bool bad = false, nonq = false;
-    f32::stage32_tile<LL, STAGE, BX, BY>(d, sm, blk, bx, by, brate, lam, bad, nonq);
+    f32::stage32_staged<LL, STAGE, BX, BY>(d, sm, blk, bx, by, brate, lam, bad, nonq);
     if (bx == 0 || by == 0 || bx == ntx - 1 || by == nty - 1) {
       const double bsum = block_sum<BX * BY>((double)brate, sm.red);
       if (t0) d.bpart[(STAGE - 1) * d.tiles.ntiles + tile] = bsum;
@@ -251,19 +240,29 @@ __global__ void ens_begin_run_kernel(EnsDev E, double t_end) {
 template <int BX, int BY>
 void launch_shape32(const EnsDev& E, bool ll, int stage, int grid, cudaStream_t st) {
   const dim3 b(BX, BY);
-  if (stage == 0) ens_friction_kernel<BX, BY><<<grid, b, 0, st>>>(E);
-  else if (ll) {
-    if (stage == 1) ens_stage_kernel<true, 1, BX, BY><<<grid, b, 0, st>>>(E);
-    else ens_stage_kernel<true, 2, BX, BY><<<grid, b, 0, st>>>(E);
+  if (ll) {
+    if (stage == 1)
+      ens_stage_kernel<true, 1, BX, BY><<<grid, b, stage32_smem<true, 1, BX, BY>(), st>>>(E);
+    else
+      ens_stage_kernel<true, 2, BX, BY><<<grid, b, stage32_smem<true, 2, BX, BY>(), st>>>(E);
   } else {
-    if (stage == 1) ens_stage_kernel<false, 1, BX, BY><<<grid, b, 0, st>>>(E);
-    else ens_stage_kernel<false, 2, BX, BY><<<grid, b, 0, st>>>(E);
+    if (stage == 1)
+      ens_stage_kernel<false, 1, BX, BY><<<grid, b, stage32_smem<false, 1, BX, BY>(), st>>>(E);
+    else
+      ens_stage_kernel<false, 2, BX, BY><<<grid, b, stage32_smem<false, 2, BX, BY>(), st>>>(E);
   }
 }
 
-void launch_friction32(const EnsDev& E, int tw, int grid, cudaStream_t st) {
-  if (tw == 16) launch_shape32<16, 8>(E, false, 0, grid, st);
-  else launch_shape32<32, 8>(E, false, 0, grid, st);
+template <int BX, int BY>
+void prepare_shape32() {
+  cudaFuncSetAttribute(ens_stage_kernel<true, 1, BX, BY>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, stage32_smem<true, 1, BX, BY>());
+  cudaFuncSetAttribute(ens_stage_kernel<true, 2, BX, BY>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, stage32_smem<true, 2, BX, BY>());
+  cudaFuncSetAttribute(ens_stage_kernel<false, 1, BX, BY>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, stage32_smem<false, 1, BX, BY>());
+  cudaFuncSetAttribute(ens_stage_kernel<false, 2, BX, BY>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, stage32_smem<false, 2, BX, BY>());
 }
 
 void launch_stage32(const EnsDev& E, int tw, bool ll, int stage, int grid, cudaStream_t st) {
@@ -277,21 +276,25 @@ void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, c
 }
 
 template <int BX, int BY>
-void occupancy_shape32(bool ll, int* f, int* s1, int* s2) {
+void occupancy_shape32(bool ll, int* s1, int* s2) {
   const int nt = BX * BY;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(f, ens_friction_kernel<BX, BY>, nt, 0);
+  prepare_shape32<BX, BY>();
   if (ll) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<true, 1, BX, BY>, nt, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<true, 2, BX, BY>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<true, 1, BX, BY>, nt,
+                                                  stage32_smem<true, 1, BX, BY>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<true, 2, BX, BY>, nt,
+                                                  stage32_smem<true, 2, BX, BY>());
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<false, 1, BX, BY>, nt, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<false, 2, BX, BY>, nt, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s1, ens_stage_kernel<false, 1, BX, BY>, nt,
+                                                  stage32_smem<false, 1, BX, BY>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(s2, ens_stage_kernel<false, 2, BX, BY>, nt,
+                                                  stage32_smem<false, 2, BX, BY>());
   }
 }
 
-void occupancy32(int tw, bool ll, int* f, int* s1, int* s2) {
-  if (tw == 16) occupancy_shape32<16, 8>(ll, f, s1, s2);
-  else occupancy_shape32<32, 8>(ll, f, s1, s2);
+void occupancy32(int tw, bool ll, int* s1, int* s2) {
+  if (tw == 16) occupancy_shape32<16, 8>(ll, s1, s2);
+  else occupancy_shape32<32, 8>(ll, s1, s2);
 }
 
 }  // namespace ens
@@ -378,7 +381,7 @@ struct dg2_ens {
   EnsDev E;
   int variant;
   int shape;              // index into kShapes
-  int grid_fric, grid_st1, grid_st2;
+  int grid_st1, grid_st2;
   dim3 lgrid;
   int max_ntx, max_nty;
   cudaGraphExec_t graph[kLevels];
@@ -397,16 +400,8 @@ void drop_graphs(dg2_ens* e) {
 }
 
 template <int BX, int BY>
-void occupancy(dg2_ens* e, int& f, int& s1, int& s2) {
-  const bool ll = e->variant == DG2_LL;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, ens_friction_kernel<BX, BY>, BX * BY, 0);
-  if (ll) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s1, ens_stage_kernel<true, 1, BX, BY>, BX * BY, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, ens_stage_kernel<true, 2, BX, BY>, BX * BY, 0);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s1, ens_stage_kernel<false, 1, BX, BY>, BX * BY, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, ens_stage_kernel<false, 2, BX, BY>, BX * BY, 0);
-  }
+void occupancy(dg2_ens* e, int& s1, int& s2) {
+  occupancy_shape32<BX, BY>(e->variant == DG2_LL, &s1, &s2);
 }
 
 // Lays the members' tiling out for shape `si` from their current parameters:
@@ -453,20 +448,19 @@ int set_shape(dg2_ens* e, int si) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int of = 1, o1 = 1, o2 = 1;
+  int o1 = 1, o2 = 1;
   switch (si) {
-    case 0: occupancy<32, 8>(e, of, o1, o2); break;
-    case 1: occupancy<32, 4>(e, of, o1, o2); break;
-    case 2: occupancy<16, 8>(e, of, o1, o2); break;
-    case 3: occupancy<64, 4>(e, of, o1, o2); break;
-    default: occupancy<16, 16>(e, of, o1, o2); break;
+    case 0: occupancy<32, 8>(e, o1, o2); break;
+    case 1: occupancy<32, 4>(e, o1, o2); break;
+    case 2: occupancy<16, 8>(e, o1, o2); break;
+    case 3: occupancy<64, 4>(e, o1, o2); break;
+    default: occupancy<16, 16>(e, o1, o2); break;
   }
   cudaGetLastError();
   auto gsz = [&](int occ) {
     long long g = (long long)nsm * (occ > 0 ? occ : 1);
     return (int)(g < total_tiles ? g : total_tiles);
   };
-  e->grid_fric = gsz(of);
   e->grid_st1 = gsz(o1);
   e->grid_st2 = gsz(o2);
   e->lgrid = dim3((e->max_ntx + dg2::LTX - 1) / dg2::LTX, (e->max_nty + dg2::LTY - 1) / dg2::LTY, n);
@@ -475,16 +469,9 @@ int set_shape(dg2_ens* e, int si) {
 
 template <int BX, int BY>
 void enqueue_step_shape(dg2_ens* e) {
-  const dim3 blk(BX, BY);
-  const EnsDev& E = e->E;
-  ens_friction_kernel<BX, BY><<<e->grid_fric, blk, 0, e->st>>>(E);
-  if (e->variant == DG2_LL) {
-    ens_stage_kernel<true, 1, BX, BY><<<e->grid_st1, blk, 0, e->st>>>(E);
-    ens_stage_kernel<true, 2, BX, BY><<<e->grid_st2, blk, 0, e->st>>>(E);
-  } else {
-    ens_stage_kernel<false, 1, BX, BY><<<e->grid_st1, blk, 0, e->st>>>(E);
-    ens_stage_kernel<false, 2, BX, BY><<<e->grid_st2, blk, 0, e->st>>>(E);
-  }
+  const bool ll = e->variant == DG2_LL;
+  launch_shape32<BX, BY>(e->E, ll, 1, e->grid_st1, e->st);
+  launch_shape32<BX, BY>(e->E, ll, 2, e->grid_st2, e->st);
 }
 
 void enqueue_lists(dg2_ens* e, int lists_only) {
@@ -493,7 +480,7 @@ void enqueue_lists(dg2_ens* e, int lists_only) {
   ens_lists_kernel<<<e->lgrid, dim3(dg2::LTX, dg2::LTY), 0, e->st>>>(e->E);
 }
 
-// One step of every unfinished member: 5 launches.
+// One step of every unfinished member: 4 launches.
 void enqueue_step(dg2_ens* e) {
   switch (e->shape) {
     case 0: enqueue_step_shape<32, 8>(e); break;
@@ -542,10 +529,10 @@ int run_chunk(dg2_ens* e, int lv) {
       if (err != cudaSuccess) return efail(DG2_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(err));
     }
     ECU(cudaGraphLaunch(e->graph[lv], e->st));
-    return check_launch(e, 5 * (int64_t)chunk);
+    return check_launch(e, 4 * (int64_t)chunk);
   }
   for (int k = 0; k < chunk; ++k) enqueue_step(e);
-  return check_launch(e, 5 * (int64_t)chunk);
+  return check_launch(e, 4 * (int64_t)chunk);
 }
 
 // After the ensemble moved the members' states, their own tilings must
@@ -710,11 +697,11 @@ int dg2_ens_autotune(dg2_ens* e, double t_end, int steps_per_trial, int* tile_w,
       if ((r = set_shape(e, k))) break;
       enqueue_lists(e, 1);  // lists for the new tiling (every tile once)
       enqueue_step(e);
-      if ((r = check_launch(e, 7))) break;
+      if ((r = check_launch(e, 6))) break;
       cudaEventRecord(a, e->st);
       for (int q = 0; q < steps_per_trial; ++q) enqueue_step(e);
       cudaEventRecord(b, e->st);
-      if ((r = check_launch(e, 5 * (int64_t)steps_per_trial))) break;
+      if ((r = check_launch(e, 4 * (int64_t)steps_per_trial))) break;
       cudaError_t err = cudaEventSynchronize(b);
       if (err != cudaSuccess) { r = efail(DG2_E_CUDA, "autotune: %s", cudaGetErrorString(err)); break; }
       float ms = 0.f;

@@ -234,43 +234,6 @@ __device__ __forceinline__ void cell_z(const D32& d, int i, int j, float& z0, fl
   z1y = 0.5f * (zN - zS);
 }
 
-// Limited slopes (eta, qx, qy) along dir of cell (i, j): Eqs. 6-7 on the
-// free surface and the discharges (the free-surface form makes Sec. 2.1.3's
-// eta limiting direct).
-static __device__ void limited_slopes32(const D32& d, const float* __restrict__ U, int i, int j, int dir,
-                                 float& se, float& sqx, float& sqy) {
-  const long long P = d.plane, c = (long long)j * d.pitch + i;
-  se = U[dir * P + c];
-  sqx = U[(3 + dir) * P + c];
-  sqy = U[(6 + dir) * P + c];
-  const bool lo = dir == 1 ? i > 0 : j > 0;
-  const bool hi = dir == 1 ? i + 1 < d.nx : j + 1 < d.ny;
-  if (!lo || !hi) return;
-  const int il = dir == 1 ? i - 1 : i, jl = dir == 1 ? j : j - 1;
-  const int ih = dir == 1 ? i + 1 : i, jh = dir == 1 ? j : j + 1;
-  const long long cl = (long long)jl * d.pitch + il, ch = (long long)jh * d.pitch + ih;
-  float z0, z1x, z1y, zE, zW, zN, zS;
-  cell_z(d, il, jl, z0, z1x, z1y, zE, zW, zN, zS);
-  const float hl = (U[cl] - z0) + U[E0L * P + cl];
-  cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-  const float hc = (U[c] - z0) + U[E0L * P + c];
-  cell_z(d, ih, jh, z0, z1x, z1y, zE, zW, zN, zS);
-  const float hh = (U[ch] - z0) + U[E0L * P + ch];
-  if (hl <= d.tol || hc <= d.tol || hh <= d.tol) return;
-  const float half = 0.5f * (dir == 1 ? d.dx : d.dy);
-  se = limit_comp32(d.ds, d.tol, half, U[cl], U[dir * P + cl], U[c], se, U[ch], U[dir * P + ch]);
-  {
-    const float* k0 = U + 3 * P;
-    const float* k1 = U + (3 + dir) * P;
-    sqx = limit_comp32(d.ds, d.tol, half, k0[cl], k1[cl], k0[c], k1[c], k0[ch], k1[ch]);
-  }
-  {
-    const float* k0 = U + 6 * P;
-    const float* k1 = U + (6 + dir) * P;
-    sqy = limit_comp32(d.ds, d.tol, half, k0[cl], k1[cl], k0[c], k1[c], k0[ch], k1[ch]);
-  }
-}
-
 // Wet-dry treatment in free-surface variables (same rule as the FP64 path):
 // a zeroed depth slope is eta1 = z1.
 __device__ __forceinline__ void wetdry32(float* m, float lo, float z0, float z1x, float z1y,
@@ -371,62 +334,6 @@ static __global__ void init32_kernel(D32 d, const double* __restrict__ zc, const
   Nw[c] = (float)(man ? man[(long long)j * d.nx + i] : n_uniform);
 }
 
-__device__ __forceinline__ void friction_point32(float gn2dt, float tol, float h, float& qx,
-                                                 float& qy) {
-  if (!(h > tol)) return;
-  const float qm = sqrtf(qx * qx + qy * qy);
-  const float den = 1.f + gn2dt * qm / (h * h * cbrtf(h));
-  qx = qx / den;
-  qy = qy / den;
-}
-
-// Friction on the BX x BY tile (bx, by), one thread per cell.
-template <int BX = TX, int BY = TY>
-__device__ __forceinline__ void friction32_tile(const D32& d, float gdt, int bx, int by) {
-  const int i = bx * BX + threadIdx.x;
-  const int j = by * BY + threadIdx.y;
-  if (i >= d.nx || j >= d.ny) return;
-  const long long P = d.plane, c = (long long)j * d.pitch + i;
-  const float n = d.N[c];
-  if (n == 0.f) return;
-  float* S = d.S;
-  float z0, z1x, z1y, zE, zW, zN, zS;
-  cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-  const float h0 = (S[E0 * P + c] - z0) + S[E0L * P + c];
-  if (!(h0 > d.tol)) {
-    // a dry average can still have wet Gauss points only through slopes, which
-    // the wet-dry treatment has zeroed; nothing to do
-    bool any = false;
-    for (int dd = 1; dd <= 2 && !any; ++dd) {
-      const float h1 = S[dd * P + c] - (dd == 1 ? z1x : z1y);
-      any = fabsf(h1) * 0.57735026918962576f + h0 > d.tol;
-    }
-    if (!any) return;
-  }
-  const float gn2dt = gdt * n * n;
-  const float x0 = S[QX0 * P + c], y0 = S[QY0 * P + c];
-  float cx = x0, cy = y0;
-  friction_point32(gn2dt, d.tol, h0, cx, cy);
-  const float r3 = 0.57735026918962576f, hs3 = 0.86602540378443865f;
-  float nq[2][2];
-#pragma unroll
-  for (int dd = 1; dd <= 2; ++dd) {
-    const float h1 = S[dd * P + c] - (dd == 1 ? z1x : z1y);
-    const float x1 = S[(3 + dd) * P + c], y1 = S[(6 + dd) * P + c];
-    float xp = x0 + x1 * r3, yp = y0 + y1 * r3, xm = x0 - x1 * r3, ym = y0 - y1 * r3;
-    friction_point32(gn2dt, d.tol, h0 + h1 * r3, xp, yp);
-    friction_point32(gn2dt, d.tol, h0 - h1 * r3, xm, ym);
-    nq[dd - 1][0] = hs3 * (xp - xm);
-    nq[dd - 1][1] = hs3 * (yp - ym);
-  }
-  S[QX0 * P + c] = cx;
-  S[QY0 * P + c] = cy;
-  S[QX1X * P + c] = nq[0][0];
-  S[QY1X * P + c] = nq[0][1];
-  S[QX1Y * P + c] = nq[1][0];
-  S[QY1Y * P + c] = nq[1][1];
-}
-
 // One side of a face: the planar limit's depth h (free-surface form: eta_face
 // - z_face) and velocities (tol rule), the depth the face may draw on (hs:
 // max(0, h), scaled for a partially wet cell), and whether the side's cell is
@@ -442,18 +349,6 @@ struct FaceR32 {
   FaceF f;
   float ha;
 };
-
-template <int BX, int BY>
-struct StageSmem32T {
-  RecF e[BY][BX];
-  RecF n[BY][BX];
-  RecF hw[BY], he[BY], hs[BX], hn[BX];
-  FaceR32 fx[BY][BX + 1];
-  FaceR32 fy[BY + 1][BX];
-  double red[32];
-  float redf[32];
-};
-using StageSmem32 = StageSmem32T<TX, TY>;
 
 // Face depths (hi - z_face) +- eta1 + lo of a cell from its free-surface modes:
 // hi - z_face is exact for shallow water (Sterbenz), and both sides of a face
@@ -541,308 +436,15 @@ __device__ __forceinline__ void revise_face32(const RecF& a, const RecF& b, floa
   rb.qx = __fmul_rn(rb.h, b.u); rb.qy = __fmul_rn(rb.h, b.v);
 }
 
-// Planar limit (face depth, qx, qy) of cell (i, j) at face f (0 E, 1 W, 2 N,
-// 3 S), slopes limited when LL: what the cell's own thread forms, for a ghost
-// built by another thread.
-template <bool LL>
-__device__ __forceinline__ void own_face_limit32(const D32& d, const float* __restrict__ In, int i,
-                                                 int j, int f, float& h, float& qx, float& qy) {
-  const long long P = d.plane, c = (long long)j * d.pitch + i;
-  const int dir = f <= 1 ? 1 : 2;
-  float se = In[dir * P + c], sx = In[(3 + dir) * P + c], sy = In[(6 + dir) * P + c];
-  if (LL) limited_slopes32(d, In, i, j, dir, se, sx, sy);
-  float z0, z1x, z1y, zE, zW, zN, zS;
-  cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-  const float e0 = In[E0 * P + c], lo = In[E0L * P + c];
-  const float x0 = In[QX0 * P + c], y0 = In[QY0 * P + c];
-  if (f == 0) { h = ((e0 - zE) + se) + lo; qx = x0 + sx; qy = y0 + sy; }
-  else if (f == 1) { h = ((e0 - zW) - se) + lo; qx = x0 - sx; qy = y0 - sy; }
-  else if (f == 2) { h = ((e0 - zN) + se) + lo; qx = x0 + sx; qy = y0 + sy; }
-  else { h = ((e0 - zS) - se) + lo; qx = x0 - sx; qy = y0 - sy; }
-}
-
-// Record, at the face it shares with a cell of the tile, of the neighbour
-// (ni, nj) on side `side` (0: west / south of the face, its east / north
-// limit; 1: east / north, its west / south limit) along dir: the same
-// arithmetic as the neighbour's own thread.
-template <bool LL>
-__device__ __forceinline__ RecF neighbour_rec32(const D32& d, const float* __restrict__ In, int ni,
-                                                int nj, int dir, int side) {
-  const long long P = d.plane, c = (long long)nj * d.pitch + ni;
-  float ex = In[E1X * P + c], xx = In[QX1X * P + c], yx = In[QY1X * P + c];
-  float ey = In[E1Y * P + c], xy = In[QX1Y * P + c], yy = In[QY1Y * P + c];
-  if (LL) {
-    limited_slopes32(d, In, ni, nj, 1, ex, xx, yx);
-    limited_slopes32(d, In, ni, nj, 2, ey, xy, yy);
-  }
-  const float e0 = In[E0 * P + c], lo = In[E0L * P + c];
-  float z0, z1x, z1y, zE, zW, zN, zS;
-  cell_z(d, ni, nj, z0, z1x, z1y, zE, zW, zN, zS);
-  float eh, wh, nh, sh;
-  face_depths32(e0, ex, ey, lo, zE, zW, zN, zS, eh, wh, nh, sh);
-  float scl;
-  const float h0 = (e0 - z0) + lo;
-  const bool pw = pw_scale32(h0, wh, eh, sh, nh, d.tol, d.wd, scl);
-  const float qx0 = In[QX0 * P + c], qy0 = In[QY0 * P + c];
-  const bool thin = d.wd != 0;
-  if (dir == 1)
-    return side == 0 ? make_rec32(eh, qx0 + xx, qy0 + yx, pw, scl, d.tol, thin, h0)
-                     : make_rec32(wh, qx0 - xx, qy0 - yx, pw, scl, d.tol, thin, h0);
-  return side == 0 ? make_rec32(nh, qx0 + xy, qy0 + yy, pw, scl, d.tol, thin, h0)
-                   : make_rec32(sh, qx0 - xy, qy0 - yy, pw, scl, d.tol, thin, h0);
-}
-
-// One RK stage of the FP32 free-surface form on the tile (bx, by).  `blk`
-// carries the per-block constants (dt, stage time, rain flag) read once.
+// Per-block constants of an RK stage (dt, stage time, rain flag), read once per
+// tile; the stage itself is in dg2_fs32_staged.cuh.
 struct Blk32 {
   float dt, rainf;
+  float gdt;  // friction's g dt (FP32 of the FP64 product)
   double dtd, ts;
   int rain;
   int skip;  // the problem has reached t_end: leave its tiles
 };
-
-template <bool LL, int STAGE, int BX = TX, int BY = TY>
-__device__ __forceinline__ void stage32_tile(const D32& d, StageSmem32T<BX, BY>& sm,
-                                             const Blk32& blk, int bx, int by, float& brate,
-                                             float& lam, bool& bad, bool& nonq) {
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = bx * BX + tx, j = by * BY + ty;
-  const bool act = i < d.nx && j < d.ny;
-  const long long P = d.plane;
-  const long long c = (long long)j * d.pitch + i;
-  const float* __restrict__ In = STAGE == 1 ? d.S : d.T;
-  const float g = d.g, tol = d.tol;
-  const float dt = blk.dt;
-  const double ts = blk.ts;
-  const bool s_rain = blk.rain != 0;
-  const float s_rainf = blk.rainf;
-  float m[9];
-  float z0 = 0.f, z1x = 0.f, z1y = 0.f, zE = 0.f, zW = 0.f, zN = 0.f, zS = 0.f;
-  RecF rE, rW, rN, rS;
-  float mlo = 0.f;
-  if (act) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) m[k] = In[k * P + c];
-    mlo = In[E0L * P + c];
-    if (LL) {
-      limited_slopes32(d, In, i, j, 1, m[E1X], m[QX1X], m[QY1X]);
-      limited_slopes32(d, In, i, j, 2, m[E1Y], m[QX1Y], m[QY1Y]);
-    }
-    cell_z(d, i, j, z0, z1x, z1y, zE, zW, zN, zS);
-    float eh, wh, nh, shh;
-    face_depths32(m[E0], m[E1X], m[E1Y], mlo, zE, zW, zN, zS, eh, wh, nh, shh);
-    const float eqx = m[QX0] + m[QX1X], eqy = m[QY0] + m[QY1X];
-    const float wqx = m[QX0] - m[QX1X], wqy = m[QY0] - m[QY1X];
-    const float nqx = m[QX0] + m[QX1Y], nqy = m[QY0] + m[QY1Y];
-    const float sqx = m[QX0] - m[QX1Y], sqy = m[QY0] - m[QY1Y];
-    float scl;
-    const float h0c = (m[E0] - z0) + mlo;
-    const bool pw = pw_scale32(h0c, wh, eh, shh, nh, tol, d.wd, scl);
-    const bool thin = d.wd != 0;
-    rE = make_rec32(eh, eqx, eqy, pw, scl, tol, thin, h0c);
-    rW = make_rec32(wh, wqx, wqy, pw, scl, tol, thin, h0c);
-    rN = make_rec32(nh, nqx, nqy, pw, scl, tol, thin, h0c);
-    rS = make_rec32(shh, sqx, sqy, pw, scl, tol, thin, h0c);
-    sm.e[ty][tx] = rE;
-    sm.n[ty][tx] = rN;
-  }
-  // the records beyond the tile (a neighbour's, or the edge ghost), one per
-  // thread of the first 2 (BX + BY) threads, so no warp runs them one lane at a time
-  {
-    const int t = ty * BX + tx;
-    const int i0 = bx * BX, j0 = by * BY;
-    const int ni = d.nx - i0 < BX ? d.nx - i0 : BX, nj = d.ny - j0 < BY ? d.ny - j0 : BY;
-    if (t < BY) {
-      if (t < nj) {
-        const int jj = j0 + t;
-        if (i0 == 0) {
-          float h, qx, qy;
-          own_face_limit32<LL>(d, In, i0, jj, 1, h, qx, qy);
-          ghost32(d, 0, (jj + 0.5f) * d.dy, ts, h, qx, qy);
-          sm.hw[t] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.hw[t] = neighbour_rec32<LL>(d, In, i0 - 1, jj, 1, 0);
-        }
-      }
-    } else if (t < 2 * BY) {
-      const int r = t - BY;
-      if (r < nj) {
-        const int jj = j0 + r, il = i0 + ni - 1;
-        if (il == d.nx - 1) {
-          float h, qx, qy;
-          own_face_limit32<LL>(d, In, il, jj, 0, h, qx, qy);
-          ghost32(d, 1, (jj + 0.5f) * d.dy, ts, h, qx, qy);
-          sm.he[r] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.he[r] = neighbour_rec32<LL>(d, In, il + 1, jj, 1, 1);
-        }
-      }
-    } else if (t < 2 * BY + BX) {
-      const int q = t - 2 * BY;
-      if (q < ni) {
-        const int ii = i0 + q;
-        if (j0 == 0) {
-          float h, qx, qy;
-          own_face_limit32<LL>(d, In, ii, j0, 3, h, qx, qy);
-          ghost32(d, 2, (ii + 0.5f) * d.dx, ts, h, qx, qy);
-          sm.hs[q] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.hs[q] = neighbour_rec32<LL>(d, In, ii, j0 - 1, 2, 0);
-        }
-      }
-    } else if (t < 2 * BY + 2 * BX) {
-      const int q = t - 2 * BY - BX;
-      if (q < ni) {
-        const int ii = i0 + q, jl = j0 + nj - 1;
-        if (jl == d.ny - 1) {
-          float h, qx, qy;
-          own_face_limit32<LL>(d, In, ii, jl, 2, h, qx, qy);
-          ghost32(d, 3, (ii + 0.5f) * d.dx, ts, h, qx, qy);
-          sm.hn[q] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.hn[q] = neighbour_rec32<LL>(d, In, ii, jl + 1, 2, 1);
-        }
-      }
-    }
-  }
-  __syncthreads();
-
-  // one revision and one flux per face: each thread its west and south faces
-  // (the own, upper side stays in registers, the lower side's depth goes with
-  // the flux), then the tile's east and north edge faces one per thread
-  float hWo = 0.f, hSo = 0.f;
-  if (act) {
-    LimF ra, rb;
-    const RecF& Lw = tx > 0 ? sm.e[ty][tx - 1] : sm.hw[ty];
-    revise_face32(Lw, rW, tol, ra, rb);
-    hWo = rb.h;
-    const FaceF fw = flux_x32(ra, rb, g, tol);
-    sm.fx[ty][tx] = FaceR32{fw, ra.h};
-    if (i == 0) brate += fw.h * d.dy;
-    const RecF& Ls = ty > 0 ? sm.n[ty - 1][tx] : sm.hs[tx];
-    revise_face32(Ls, rS, tol, ra, rb);
-    hSo = rb.h;
-    const FaceF fs = flux_y32(ra, rb, g, tol);
-    sm.fy[ty][tx] = FaceR32{fs, ra.h};
-    if (j == 0) brate += fs.h * d.dx;
-  }
-  {
-    const int t = ty * BX + tx;
-    const int ni = d.nx - bx * BX < BX ? d.nx - bx * BX : BX;
-    const int nj = d.ny - by * BY < BY ? d.ny - by * BY : BY;
-    LimF ra, rb;
-    if (t < nj) {
-      revise_face32(sm.e[t][ni - 1], sm.he[t], tol, ra, rb);
-      const FaceF fe = flux_x32(ra, rb, g, tol);
-      sm.fx[t][ni] = FaceR32{fe, ra.h};
-      if (bx * BX + ni == d.nx) brate -= fe.h * d.dy;
-    } else if (t >= BY && t < BY + ni) {
-      const int q = t - BY;
-      revise_face32(sm.n[nj - 1][q], sm.hn[q], tol, ra, rb);
-      const FaceF fn = flux_y32(ra, rb, g, tol);
-      sm.fy[nj][q] = FaceR32{fn, ra.h};
-      if (by * BY + nj == d.ny) brate -= fn.h * d.dx;
-    }
-  }
-  __syncthreads();
-
-  if (act) {
-    // own faces: east / north faces are referenced to our (left / south) pressure,
-    // west / south faces to the neighbour's, so add dP to get ours
-    const FaceR32 rEf = sm.fx[ty][tx + 1], rWf = sm.fx[ty][tx];
-    const FaceR32 rNf = sm.fy[ty + 1][tx], rSf = sm.fy[ty][tx];
-    const FaceF fE = rEf.f, fW = rWf.f, gN = rNf.f, gS = rSf.f;
-    const float hEo = rEf.ha, hNo = rNf.ha;
-    const float FEh = fE.h, FEx = fE.n, FEy = fE.t;
-    const float FWh = fW.h, FWx = fW.n + fW.dp, FWy = fW.t;
-    const float GNh = gN.h, GNx = gN.t, GNy = gN.n;
-    const float GSh = gS.h, GSx = gS.t, GSy = gS.n + gS.dp;
-    // own revised states (Eq. 5 operands): q* = h* u
-    LimF Es, Ws, Ns, Ss;
-    Es.h = hEo; Es.qx = hEo * rE.u; Es.qy = hEo * rE.v;
-    Ws.h = hWo; Ws.qx = hWo * rW.u; Ws.qy = hWo * rW.v;
-    Ns.h = hNo; Ns.qx = hNo * rN.u; Ns.qy = hNo * rN.v;
-    Ss.h = hSo; Ss.qx = hSo * rS.u; Ss.qy = hSo * rS.v;
-    const float h0x = 0.5f * (Es.h + Ws.h), x0x = 0.5f * (Es.qx + Ws.qx), y0x = 0.5f * (Es.qy + Ws.qy);
-    const float h1x_ = 0.5f * (Es.h - Ws.h), x1x = 0.5f * (Es.qx - Ws.qx), y1x = 0.5f * (Es.qy - Ws.qy);
-    const float h0y = 0.5f * (Ns.h + Ss.h), x0y = 0.5f * (Ns.qx + Ss.qx), y0y = 0.5f * (Ns.qy + Ss.qy);
-    const float h1y_ = 0.5f * (Ns.h - Ss.h), x1y = 0.5f * (Ns.qx - Ss.qx), y1y = 0.5f * (Ns.qy - Ss.qy);
-    const float r3 = 0.57735026918962576f;
-    float Fph, Fpx, Fpy, Fmh, Fmx, Fmy, Gph, Gpx, Gpy, Gmh, Gmx, Gmy;
-    gauss_dev(h0x + h1x_ * r3, x0x + x1x * r3, y0x + y1x * r3, tol, false, Fph, Fpx, Fpy);
-    gauss_dev(h0x - h1x_ * r3, x0x - x1x * r3, y0x - y1x * r3, tol, false, Fmh, Fmx, Fmy);
-    gauss_dev(h0y + h1y_ * r3, x0y + x1y * r3, y0y + y1y * r3, tol, true, Gph, Gpx, Gpy);
-    gauss_dev(h0y - h1y_ * r3, x0y - x1y * r3, y0y - y1y * r3, tol, true, Gmh, Gmx, Gmy);
-    const float idx = d.inv_dx, idy = d.inv_dy;
-    const float dEx = 2.f * m[E1X], dEy = 2.f * m[E1Y];  // eta_E - eta_W, eta_N - eta_S
-    float L[9];
-    L[E0] = -(FEh - FWh) * idx - (GNh - GSh) * idy;
-    L[QX0] = -(FEx - FWx) * idx - (GNx - GSx) * idy - g * h0x * dEx * idx;
-    L[QY0] = -(FEy - FWy) * idx - (GNy - GSy) * idy - g * h0y * dEy * idy;
-    if (s_rain) L[E0] += s_rainf;
-    if (c == d.src_idx) L[E0] += (float)(d.qp / (d.dxd * d.dyd));
-    const float k3x = -3.f * idx, k3y = -3.f * idy, g23 = 2.f * g / 3.f;
-    L[E1X] = k3x * ((FEh + FWh) - (Fph + Fmh));
-    L[QX1X] = k3x * ((FEx + FWx) - (Fpx + Fmx) + g23 * h1x_ * (0.5f * dEx));
-    L[QY1X] = k3x * ((FEy + FWy) - (Fpy + Fmy));
-    L[E1Y] = k3y * ((GNh + GSh) - (Gph + Gmh));
-    L[QX1Y] = k3y * ((GNx + GSx) - (Gpx + Gmx));
-    L[QY1Y] = k3y * ((GNy + GSy) - (Gpy + Gmy) + g23 * h1y_ * (0.5f * dEy));
-
-    float out[9];
-    if (STAGE == 1) {
-#pragma unroll
-      for (int k = 1; k < 9; ++k) out[k] = m[k] + dt * L[k];
-      float olo;
-      two_sum(m[E0], mlo + dt * L[E0], out[E0], olo);
-      wetdry32(out, olo, z0, z1x, z1y, zE, zW, zN, zS, tol);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) d.T[k * P + c] = out[k];
-      d.T[E0L * P + c] = olo;
-      if (LL) {
-        d.Q[0 * P + c] = m[E1X]; d.Q[1 * P + c] = m[E1Y];
-        d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
-        d.Q[4 * P + c] = m[QY1X]; d.Q[5 * P + c] = m[QY1Y];
-      }
-    } else {
-      float un[9];
-      un[E0] = d.S[E0 * P + c]; un[QX0] = d.S[QX0 * P + c]; un[QY0] = d.S[QY0 * P + c];
-      if (LL) {
-        un[E1X] = d.Q[0 * P + c]; un[E1Y] = d.Q[1 * P + c];
-        un[QX1X] = d.Q[2 * P + c]; un[QX1Y] = d.Q[3 * P + c];
-        un[QY1X] = d.Q[4 * P + c]; un[QY1Y] = d.Q[5 * P + c];
-      } else {
-        un[E1X] = d.S[E1X * P + c]; un[E1Y] = d.S[E1Y * P + c];
-        un[QX1X] = d.S[QX1X * P + c]; un[QX1Y] = d.S[QX1Y * P + c];
-        un[QY1X] = d.S[QY1X * P + c]; un[QY1Y] = d.S[QY1Y * P + c];
-      }
-#pragma unroll
-      for (int k = 1; k < 9; ++k) out[k] = 0.5f * (un[k] + m[k] + dt * L[k]);
-      // (Un + U1 + dt L) / 2 for the pair: TwoSum of the high parts, the rest added to
-      // the error term, renormalised, halved exactly
-      float olo;
-      {
-        float s1, e1, r1, e2;
-        two_sum(un[E0], m[E0], s1, e1);
-        e1 += (d.S[E0L * P + c] + mlo) + dt * L[E0];
-        two_sum(s1, e1, r1, e2);
-        out[E0] = 0.5f * r1;
-        olo = 0.5f * e2;
-      }
-      wetdry32(out, olo, z0, z1x, z1y, zE, zW, zN, zS, tol);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) d.S[k * P + c] = out[k];
-      d.S[E0L * P + c] = olo;
-      const float h0n = (out[E0] - z0) + olo;
-      lam = rate32(d, h0n, out[QX0], out[QY0]);
-      bad = bad || !(isfinite(out[E0]) && isfinite(olo) && isfinite(out[QX0]) &&
-                     isfinite(out[QY0]));
-      nonq = !(h0n <= tol) || out[E1X] != z1x || out[E1Y] != z1y;
-#pragma unroll
-      for (int k = 3; k < 9; ++k) nonq = nonq || out[k] != 0.f;
-    }
-  }
-}
 
 // Time, ledger, gauges and the next step; opens the next step's tile lists.
 // Run by one block of kFinThreads threads per problem.

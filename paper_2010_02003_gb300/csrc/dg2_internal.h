@@ -40,13 +40,14 @@ constexpr int kTileBits = 22;
 constexpr long long kF32SmallCells = 1ll << 23;
 inline bool f32_small_tiles(long long cells) { return cells <= kF32SmallCells; }
 // The FP32 kernels of one step on tiles of tw x th cells (16 x 8 or 32 x 8; a
-// single problem is a set of one): friction, one RK stage, and the end of step
-// (finalize + lists; with lists_only just the lists).  `grid` = persistent
-// blocks; `lgrid` = tile blocks of the lists kernel (z = problems).
-void launch_friction32(const EnsDev& E, int tw, int grid, cudaStream_t st);
+// single problem is a set of one): one RK stage (stage 1 with friction fused),
+// and the end of step (finalize + lists; with lists_only just the lists).
+// `grid` = persistent blocks; `lgrid` = tile blocks of the lists kernel (z =
+// problems).  occupancy32 also raises the stage kernels' dynamic shared memory
+// limit for the shape, which must precede their first launch.
 void launch_stage32(const EnsDev& E, int tw, bool ll, int stage, int grid, cudaStream_t st);
 void launch_end_of_step(const EnsDev& E, int nmem, dim3 lgrid, int lists_only, cudaStream_t st);
-void occupancy32(int tw, bool ll, int* fric, int* st1, int* st2);
+void occupancy32(int tw, bool ll, int* st1, int* st2);
 }  // namespace ens
 
 // Reports through dg2_last_error().

@@ -178,20 +178,25 @@ def _solo_dt_sequence(B, case, variant, t_end):
 
 
 # FP32 member error against the FP64 oracle over each member's own step sequence
-# (depth / discharge, relative to the member's depth and discharge scales).
-ENS_BAR = {0: (1e-3, 1e-3), 1: (1e-3, 1e-3)}
+# (depth / discharge, relative to the member's depth and discharge scales): measured
+# NL 4.9e-6 / 2.2e-6, LL 4.2e-6 / 1.8e-6 at most over the six members; bars at 3x.
+ENS_BAR = {0: (1.5e-5, 7e-6), 1: (1.3e-5, 6e-6)}
 
 
 @pytest.mark.parametrize("variant", [0, 1], ids=["NL", "LL"])
 def test_uneven_members_against_the_fp64_oracle(variant):
     """Six members of uneven sizes (33 x 17 to 96 x 64 cells), each with its own Manning
-    n, inflow peak and Courant steps, advanced together to t = 30 s; every member is
-    compared with the FP64 oracle run alone through that member's own step sequence
-    (the FP32 steps it takes alone, which the ensemble reproduces bit for bit)."""
+    n, inflow peak and Courant steps, advanced together to t = 8 s (37 to 51 steps); every
+    member is compared with the FP64 oracle run alone through that member's own step
+    sequence (the FP32 steps it takes alone, which the ensemble reproduces bit for bit).
+    The window is where the members' dry-start inflow fronts are well conditioned: the
+    oracle moves by 8e-8 there under a 1e-7 perturbation of its state, but by 0.2-0.6
+    over 30 s, where FP32 and FP64 runs part at wet-dry decisions
+    (tests/test_oracle_conditioning.py)."""
     from conftest import make_oracle
     B = _B()
-    t_end = 30.0
-    cases = inputs.ensemble(n=6, seed=4242, nx_range=(33, 96), ny_range=(17, 64), t_peak=15.0,
+    t_end = 8.0
+    cases = inputs.ensemble(n=6, seed=4242, nx_range=(33, 96), ny_range=(17, 64), t_peak=3.0,
                             t_end=t_end, ngauge=2, sample_every=0.0)
     sizes = {(c.nx, c.ny) for c in cases}
     assert len(sizes) == 6

@@ -69,6 +69,7 @@ def test_fp32_dam_break_against_fp64_oracle(limiter):
     for _ in range(100):
         s.step(o.step())
     eh, eq = fp32_errors(s.state(), o.state())
+    print(f"FP32 dam break {'LL' if limiter else 'NL'}: depth {eh:.2e}, discharge {eq:.2e}")
     # measured: NL 5.7e-7 / 4.2e-7 (plain FP32 accumulation); LL 1.6e-5 / 1.4e-4 (the
     # Eq. 6 detector switches on FP32-sized differences near its threshold)
     if limiter:
@@ -89,12 +90,13 @@ def test_fp32_floodplain_against_fp64_oracle(limiter):
     # the thin inflow front amplifies round-off ~10^4 between steps 90 and 100 in the
     # FP64 oracle itself (tests/test_oracle_conditioning.py) and DG2-LL a 1e-7 (FP32)
     # perturbation earlier, so LL is compared over 50 steps and NL over 85 (measured:
-    # LL 3.3e-5 / 4.0e-5, NL 2.9e-5 / 2.2e-6)
+    # LL 1.9e-5 / 2.4e-5, NL 2.9e-5 / 2.3e-6; bars at 3x)
     for _ in range(50 if limiter else 85):
         s.step(o.step())
     eh, eq = fp32_errors(s.state(), o.state())
     print(f"FP32 floodplain {'LL' if limiter else 'NL'}: depth {eh:.2e}, discharge {eq:.2e}")
-    assert eh < 1e-3 and eq < 1e-3, (eh, eq)
+    bh, bq = (6e-5, 7e-5) if limiter else (9e-5, 7e-6)
+    assert eh < bh and eq < bq, (eh, eq)
     m, led = s.mass()
     assert abs(m - led) <= 1e-6 * max(led, 1.0)
 
@@ -124,6 +126,7 @@ def test_fp32_degenerate_grids_run_and_conserve():
         for _ in range(40):
             s.step(o.step())
         eh, eq = fp32_errors(s.state(), o.state())
+        print(f"FP32 degenerate {nx}x{ny}: depth {eh:.2e}, discharge {eq:.2e}")
         assert eh < 1e-4 and eq < 1e-3, (nx, ny, eh, eq)
 
 

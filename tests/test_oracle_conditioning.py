@@ -91,3 +91,32 @@ def test_channel_start_under_the_printed_revision_amplifies_roundoff():
     # partially wet bank cells offer their full planar face depth: held 50 steps on the GPU
     assert _twin_growth(0, 50, range(2), "paper", False, "channel").max() < 1e-12
     assert _twin_growth(0, 80, range(2), "paper", False, "channel").max() > 1e-13
+
+
+def _member_twin(t_end, t_pert, limiter):
+    """Largest FP32-size (1e-7 relative) twin difference over the six members of the
+    GPU ensemble-against-oracle test, from t_pert to t_end on the same steps."""
+    cases = inputs.ensemble(n=6, seed=4242, nx_range=(33, 96), ny_range=(17, 64), t_peak=3.0,
+                            t_end=t_end, ngauge=2, sample_every=0.0)
+    worst = 0.0
+    for c in cases:
+        o = make_oracle(c, limiter=limiter)
+        while o.t < t_pert:
+            o.step()
+        s0, t0 = o.state(), o.t
+        dts = []
+        while o.t + o.cfl_dt() < t_end:
+            dts.append(o.step())
+        dts.append(t_end - o.t)
+        o.step(dts[-1])
+        tw = make_oracle(c, limiter=limiter)
+        tw.set_state(s0 * (1 + 1e-7 * np.random.default_rng(1).standard_normal(s0.shape)), t0)
+        for dt in dts:
+            tw.step(dt)
+        worst = max(worst, _scaled_err(tw.state(), o.state()))
+    return worst
+
+
+@pytest.mark.parametrize("limiter", [False, True], ids=["NL", "LL"])
+def test_ensemble_members_are_well_conditioned_to_8_s(limiter):
+    assert _member_twin(8.0, 1.5, limiter) < 1e-6
