@@ -56,7 +56,7 @@ struct Layout {
   long long plane;
   size_t off_S, off_T, off_Q, off_Z, off_N, off_ZX, off_ZY, off_bpart, off_mpart, off_kt, off_kq;
   size_t off_gidx, off_gxi, off_geta, off_st, off_sh, off_sc, off_tflag, off_tact, off_tforced,
-      off_tlist, off_tfront, off_desc, off_es, off_qm, off_busy1, total;
+      off_tlist, off_tfront, off_desc, off_es, off_qm, total;
   int nblocks, mblocks, nbx, nby;
 };
 
@@ -109,8 +109,7 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   // FP64: the warp-block masks of Un and U1 and stage 1's computed blocks
   L.nbx = (nx + dg2::TX - 1) / dg2::TX * dg2::TBX;
   L.nby = (ny + dg2::TY - 1) / dg2::TY * dg2::TBY;
-  L.off_qm = take(f32 ? 0 : 2 * (size_t)L.nbx * L.nby * sizeof(unsigned));
-  L.off_busy1 = take(f32 ? 0 : (size_t)L.nblocks);
+  L.off_qm = take(f32 ? 0 : 3 * (size_t)L.nbx * L.nby * sizeof(unsigned));
   // FP32: the problem's descriptor and step counters for the shared FP32 kernels
   L.off_desc = take(f32 ? sizeof(D32) : 0);
   L.off_es = take(f32 ? sizeof(dg2::ens::EnsScalars) : 0);
@@ -342,9 +341,9 @@ void launch_mass(dg2_ctx* c) {
 // (after a new DEM or state; the first stage 2 then sets the true flags).
 int reset_tiles(dg2_ctx* c) {
   CU(cudaMemsetAsync(c->d.tiles.flag, 1, (size_t)c->lay.nblocks, c->st));
-  // every cell non-quiescent in the row masks: the first step computes every row
+  // every cell non-quiescent in the cell masks: the first step computes every cell
   if (c->d.qm)
-    CU(cudaMemsetAsync(c->d.qm, 0xff, 2 * (size_t)c->d.qplane * sizeof(unsigned), c->st));
+    CU(cudaMemsetAsync(c->d.qm, 0xff, 3 * (size_t)c->d.qplane * sizeof(unsigned), c->st));
   launch_finalize(c, 1);
   return launch_check(c, 2);
 }
@@ -506,7 +505,6 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
   d.tiles.all_forced = 0;
   d.tiles.skip = p.skip_dry_tiles ? 1 : 0;
   d.qm = c->fp32 ? nullptr : (unsigned*)(c->ws + L.off_qm);
-  d.busy1 = c->fp32 ? nullptr : (unsigned char*)(c->ws + L.off_busy1);
   d.nbx = L.nbx;
   d.nby = L.nby;
   d.qplane = (long long)L.nbx * L.nby;

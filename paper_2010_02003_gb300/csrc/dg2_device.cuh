@@ -93,17 +93,18 @@ struct Scalars {
 // (inflow, point source, rain) tile is left untouched, bit for bit as if it
 // had been computed.
 //
-// The FP64 DG2 stage kernels refine this to the 8 x 4 cell block of each warp
-// of a computed tile.  Each stage records, one bit per cell, which cells of
-// its output are non-quiescent (qm: plane 0 for Un, written by stage 2; plane
-// 1 for U1, written by stage 1).  A block with no non-quiescent input cell
-// within one cell is a fixed point of the stage (a dry cell's limited slopes
-// are its own, so the records of a quiescent cell depend on it alone, in
-// DG2-LL too): stage 1 copies it to U1, stage 2 leaves Un as it is when the
-// block was also a fixed point of stage 1 (busy1 holds stage 1's computed
-// blocks of each tile).  Records and faces are evaluated only where a
-// computed block uses them, and friction skips blocks of quiescent cells.
-// Forced tiles, rain and skip = 0 compute every block.
+// The FP64 DG2 stage kernels refine this to single cells of a computed tile.
+// Each stage records, one bit per cell, which cells of its output are
+// non-quiescent (qm: plane 0 for Un, written by stage 2; plane 1 for U1,
+// written by stage 1).  A cell whose input and four face neighbours are
+// quiescent is a fixed point of the stage (a dry cell's limited slopes are its
+// own, so the records of a quiescent cell depend on it alone, in DG2-LL too):
+// stage 1 copies it to U1, stage 2 leaves Un as it is when the cell was also a
+// fixed point of stage 1 (qm plane 2 holds stage 1's computed cells).  The
+// computed cells of a tile are handed to the first threads (classify_cells),
+// records and faces are evaluated only where a computed cell uses them, and
+// friction skips 8 x 4 warp blocks of quiescent cells.  Forced tiles, rain and
+// skip = 0 compute every cell.
 struct Tiles {
   unsigned char* flag;          // [ntiles] tile held a non-quiescent cell after the last stage 2
   unsigned char* act;           // [ntiles] tile computed in the current step
@@ -153,11 +154,11 @@ struct Dev {
   double* samp_h;            // [max_samples][ngauge]
   int nblocks;               // blocks of the stage grid
   Tiles tiles;
-  // FP64 DG2 block skipping: non-quiescence bits, [2][nby][nbx] words, one per
-  // 8 x 4 warp block (bit l of word (Y, X): cell (8 X + l % 8, 4 Y + l / 8)),
-  // and stage 1's computed warp blocks of each tile
+  // FP64 DG2 cell skipping: [3][nby][nbx] words, one per 8 x 4 warp block (bit l
+  // of word (Y, X): cell (8 X + l % 8, 4 Y + l / 8)): the non-quiescence of Un
+  // (plane 0, written by stage 2) and of U1 (plane 1, by stage 1), and the
+  // cells stage 1 computed (plane 2)
   unsigned int* qm;
-  unsigned char* busy1;
   int nbx, nby;              // warp blocks per row / column (whole tiles)
   long long qplane;          // words per qm plane
 };
@@ -737,6 +738,11 @@ struct StageSmem {
   FaceR fx[TY][TX + 1];  // x faces; fx[ty][tx] is the west face of column tx
   FaceR fy[TY + 1][TX];  // y faces; fy[ty][tx] is the south face of row ty
   double red[32];
+  unsigned char nq[TY + 2][TX + 2];   // the stage input's non-quiescence, tile and ring
+  unsigned char cls[TY][TX];          // 0 outside the grid, 1 fixed point, 2 computed
+  unsigned char nqo[TY][TX];          // the stage output's non-quiescence
+  unsigned short perm[TX * TY];       // tile cell of each thread, computed cells first
+  int wcnt[2][TX * TY / 32];          // computed / fixed-point cells of each warp block
 };
 
 // Record of a side whose planar limit is (h, qx, qy) over face bed zf; `sc` is
@@ -885,55 +891,106 @@ __device__ __forceinline__ Rec ghost_rec(const Dev& d, int edge, double s, doubl
   return make_rec(h, qx, qy, zf, false, 1.0, d.tol);
 }
 
-// Warp blocks of tile (bx, by) (bit b: block (b % TBX, b / TBX)) with a
-// non-quiescent cell of the stage input within one cell, from the input's qm
-// plane (one word per block, bit l for lane l): the 6 x 4 words of the tile's
-// blocks and their ring, one per lane; each lane marks the blocks its word
-// touches (the whole word for the block itself, the adjacent column, row or
-// corner bit for a neighbour) and the marks are OR-reduced over the warp.
-// Warp-uniform; every lane of the warp must call it.
-__device__ __forceinline__ unsigned busy_blocks(const Dev& d, const unsigned* __restrict__ qm,
-                                                int bx, int by) {
-  const int k = (threadIdx.y * TX + threadIdx.x) & 31;
-  constexpr int RW = TBX + 2, RH = TBY + 2;  // ring region in blocks
-  static_assert(RW * RH <= 32, "one word per lane");
-  unsigned mark = 0;
-  if (k < RW * RH) {
-    const int rx = k % RW, ry = k / RW;
-    const int X = bx * TBX - 1 + rx, Y = by * TBY - 1 + ry;
-    if (X >= 0 && X < d.nbx && Y >= 0 && Y < d.nby) {
-      const unsigned v = qm[(long long)Y * d.nbx + X];
-      if (v) {
-#pragma unroll
-        for (int b = 0; b < TBX * TBY; ++b) {
-          const int dx = rx - 1 - b % TBX, dy = ry - 1 - b / TBX;
-          if (dx < -1 || dx > 1 || dy < -1 || dy > 1) continue;
-          const unsigned cm = dx < 0 ? 0x80808080u : (dx > 0 ? 0x01010101u : 0xffffffffu);
-          const unsigned rm = dy < 0 ? 0xff000000u : (dy > 0 ? 0x000000ffu : 0xffffffffu);
-          if (v & cm & rm) mark |= 1u << b;
-        }
+// Per-cell classification of a tile for one stage.  A cell is "computed" when
+// its stage input or one of its four face neighbours is non-quiescent (from the
+// input's qm bits), or, in stage 2, when stage 1 computed it (its U1 may differ
+// from Un): a cell that is not computed is a fixed point of the stage (it is
+// quiescent, and so are the records of its faces, whose fluxes vanish), so
+// stage 1 copies it to U1 and stage 2 leaves Un in place.  The tile's cells are
+// then handed to the threads computed first: thread t takes the t-th cell of
+// that order, so the expensive arithmetic runs on full warps and the fixed
+// points (and the cells past a ragged grid edge) gather in the last warps,
+// which also build the halo records.  Forced tiles, rain and skip = 0 compute
+// every cell.  Returns the calling thread's cell in (tx, ty); sm.cls[y][x]
+// holds each cell's class (0 outside the grid, 1 fixed point, 2 computed).
+template <int STAGE>
+__device__ __forceinline__ void classify_cells(const Dev& d, StageSmem& sm, int bx, int by,
+                                               bool every, int& tx, int& ty) {
+  const int t = threadIdx.y * TX + threadIdx.x, w = t >> 5, lane = t & 31;
+  // the input's non-quiescence of the tile's cells and of the ring around it
+  {
+    int cx, cy;
+    warp_cell(cx, cy);
+    const int X = bx * TBX + cx / WX, Y = by * TBY + cy / WY;
+    const unsigned* qm = STAGE == 1 ? d.qm : d.qm + d.qplane;
+    const bool in = bx * TX + cx < d.nx && by * TY + cy < d.ny;
+    sm.nq[cy + 1][cx + 1] = in ? (unsigned char)((qm[(long long)Y * d.nbx + X] >> lane) & 1u) : 0;
+    if (t < 2 * (TX + TY) + 4) {
+      // ring cell k: west / east columns (TY + 2 each, corners included), then south / north rows
+      int rx, ry;
+      if (t < 2 * (TY + 2)) { rx = t < TY + 2 ? -1 : TX; ry = (t < TY + 2 ? t : t - (TY + 2)) - 1; }
+      else { const int q = t - 2 * (TY + 2); rx = q < TX ? q : q - TX; ry = q < TX ? -1 : TY; }
+      const int gi = bx * TX + rx, gj = by * TY + ry;
+      unsigned char v = 0;
+      if (gi >= 0 && gj >= 0 && gi < d.nx && gj < d.ny) {
+        const int Xr = gi / WX, Yr = gj / WY;
+        const int l = (gj % WY) * WX + gi % WX;
+        v = (unsigned char)((qm[(long long)Yr * d.nbx + Xr] >> l) & 1u);
       }
+      sm.nq[ry + 1][rx + 1] = v;
     }
   }
-  return __reduce_or_sync(0xffffffffu, mark);
-}
-
-// Whether tile cell (x, y) lies in a computed warp block.
-__device__ __forceinline__ bool in_busy(unsigned busy, int x, int y) {
-  return (busy >> ((y / WY) * TBX + x / WX)) & 1u;
+  __syncthreads();
+  int cx, cy;
+  warp_cell(cx, cy);
+  const bool act = bx * TX + cx < d.nx && by * TY + cy < d.ny;
+  bool comp = false;
+  if (act) {
+    comp = every || sm.nq[cy + 1][cx + 1] || sm.nq[cy + 1][cx] || sm.nq[cy + 1][cx + 2] ||
+           sm.nq[cy][cx + 1] || sm.nq[cy + 2][cx + 1];
+    if (STAGE == 2 && !comp) {
+      const int X = bx * TBX + cx / WX, Y = by * TBY + cy / WY;
+      comp = (d.qm[2 * d.qplane + (long long)Y * d.nbx + X] >> lane) & 1u;
+    }
+  }
+  sm.cls[cy][cx] = (unsigned char)(act ? (comp ? 2 : 1) : 0);
+  // computed cells first, then fixed points, then cells outside the grid; each
+  // group in the order of the 8 x 4 warp blocks
+  const unsigned bc = __ballot_sync(0xffffffffu, comp), ba = __ballot_sync(0xffffffffu, act);
+  if (lane == 0) {
+    sm.wcnt[0][w] = __popc(bc);
+    sm.wcnt[1][w] = __popc(ba & ~bc);
+  }
+  __syncthreads();
+  int nc = 0, na = 0, before_c = 0, before_f = 0, before_o = 0;
+#pragma unroll
+  for (int k = 0; k < TX * TY / 32; ++k) {
+    const int c1 = sm.wcnt[0][k], f1 = sm.wcnt[1][k];
+    nc += c1;
+    na += f1;
+    if (k < w) { before_c += c1; before_f += f1; before_o += 32 - c1 - f1; }
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  int idx;
+  if (comp) idx = before_c + __popc(bc & lt);
+  else if (act) idx = nc + before_f + __popc(ba & ~bc & lt);
+  else idx = nc + na + before_o + __popc(~ba & lt);
+  sm.perm[idx] = (unsigned short)(cy * TX + cx);
+  if (STAGE == 1 && lane == 0) {
+    // stage 1's computed cells, for stage 2's rule
+    const int X = bx * TBX + cx / WX, Y = by * TBY + cy / WY;
+    d.qm[2 * d.qplane + (long long)Y * d.nbx + X] = bc;
+  }
+  __syncthreads();
+  const int me = sm.perm[t];
+  tx = me % TX;
+  ty = me / TX;
 }
 
 // One RK stage on the 32 x 8 tile (bx, by): face records, one revision and
 // one flux per face, Eqs. 4-5, the stage update and the wet-dry treatment.
 // Accumulates the boundary inflow rate, the Courant rate and the non-finite /
-// non-quiescent flags of the thread's cell into the caller's variables.  Rows
-// that are fixed points of the stage (see Tiles) skip the faces and Eqs. 4-5.
+// non-quiescent flags of the thread's cell into the caller's variables.  Cells
+// that are fixed points of the stage (classify_cells) skip the faces and
+// Eqs. 4-5.
 template <bool LL, int STAGE>
 __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, int by,
                                            double& brate, double& lam, bool& bad, bool& nonq) {
   Scalars* sc = d.sc;
+  const int tile = by * d.tiles.ntx + bx;
+  const bool every = !d.tiles.skip || d.tiles.all_forced || d.tiles.forced[tile];
   int tx, ty;
-  warp_cell(tx, ty);
+  classify_cells<STAGE>(d, sm, bx, by, every, tx, ty);
   const int i = bx * TX + tx, j = by * TY + ty;
   const bool act = i < d.nx && j < d.ny;
   const long long P = d.plane;
@@ -942,18 +999,9 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   const double ts = STAGE == 1 ? sc->t : sc->t + dt;  // boundary-condition time
   const double* __restrict__ In = STAGE == 1 ? d.S : d.T;
   const double g = d.g, tol = d.tol;
-  // warp blocks this stage computes: all, or those near a non-quiescent input
-  // cell (stage 2: also those stage 1 computed, whose U1 may differ from Un)
-  const int tile = by * d.tiles.ntx + bx;
-  unsigned busy = (1u << (TBX * TBY)) - 1u;
-  if (d.tiles.skip && !d.tiles.all_forced && !d.tiles.forced[tile]) {
-    busy = busy_blocks(d, STAGE == 1 ? d.qm : d.qm + d.qplane, bx, by);
-    if (STAGE == 2) busy |= d.busy1[tile];
-  }
-  if (STAGE == 1 && threadIdx.x == 0 && threadIdx.y == 0) d.busy1[tile] = (unsigned char)busy;
-  const bool b_me = in_busy(busy, tx, ty);
-  const bool b_w = tx > 0 && in_busy(busy, tx - 1, ty), b_e = tx + 1 < TX && in_busy(busy, tx + 1, ty);
-  const bool b_s = ty > 0 && in_busy(busy, tx, ty - 1), b_n = ty + 1 < TY && in_busy(busy, tx, ty + 1);
+  const bool b_me = sm.cls[ty][tx] == 2;
+  const bool b_w = tx > 0 && sm.cls[ty][tx - 1] == 2, b_e = tx + 1 < TX && sm.cls[ty][tx + 1] == 2;
+  const bool b_s = ty > 0 && sm.cls[ty - 1][tx] == 2, b_n = ty + 1 < TY && sm.cls[ty + 1][tx] == 2;
   double m[9];
   double z0 = 0.0, z1x = 0.0, z1y = 0.0;
   Rec rE, rW, rN, rS;  // own records
@@ -982,13 +1030,14 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     sm.n[ty][tx] = rN;
   }
   // the records beyond the tile (a neighbour's, or the edge ghost), one per
-  // thread of the first 2 (TX + TY) threads, so no warp runs them one lane at a time
+  // thread of the last 2 (TX + TY) threads (the fixed-point cells' threads when
+  // there are enough of them), so no warp runs them one lane at a time
   {
-    const int t = threadIdx.y * TX + threadIdx.x;
+    const int t = TX * TY - 1 - (threadIdx.y * TX + threadIdx.x);
     const int i0 = bx * TX, j0 = by * TY;
     const int ni = d.nx - i0 < TX ? d.nx - i0 : TX, nj = d.ny - j0 < TY ? d.ny - j0 : TY;
     if (t < TY) {
-      if (t < nj && in_busy(busy, 0, t)) {
+      if (t < nj && sm.cls[t][0] == 2) {
         const int jj = j0 + t;
         if (i0 == 0) {
           double h, qx, qy, zf;
@@ -1000,7 +1049,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY) {
       const int r = t - TY;
-      if (r < nj && in_busy(busy, ni - 1, r)) {
+      if (r < nj && sm.cls[r][ni - 1] == 2) {
         const int jj = j0 + r, il = i0 + ni - 1;
         if (il == d.nx - 1) {
           double h, qx, qy, zf;
@@ -1012,7 +1061,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY + TX) {
       const int q = t - 2 * TY;
-      if (q < ni && in_busy(busy, q, 0)) {
+      if (q < ni && sm.cls[0][q] == 2) {
         const int ii = i0 + q;
         if (j0 == 0) {
           double h, qx, qy, zf;
@@ -1024,7 +1073,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
       }
     } else if (t < 2 * TY + 2 * TX) {
       const int q = t - 2 * TY - TX;
-      if (q < ni && in_busy(busy, q, nj - 1)) {
+      if (q < ni && sm.cls[nj - 1][q] == 2) {
         const int ii = i0 + q, jl = j0 + nj - 1;
         if (jl == d.ny - 1) {
           double h, qx, qy, zf;
@@ -1041,7 +1090,7 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   // one revision and one flux per face: each thread its west and south faces
   // (the own, upper side stays in registers, the lower side's depth and bed go
   // to shared memory with the flux), then the tile's east and north edge
-  // faces one per thread
+  // faces one per thread (again the last threads)
   double hWo = 0, zWo = 0, hSo = 0, zSo = 0;
   if (act && (b_me || b_w)) {
     double ha, za;
@@ -1058,17 +1107,17 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     if (j == 0) brate += fs.h * d.dx;
   }
   {
-    const int t = threadIdx.y * TX + threadIdx.x;
+    const int t = TX * TY - 1 - (threadIdx.y * TX + threadIdx.x);
     const int ni = d.nx - bx * TX < TX ? d.nx - bx * TX : TX;
     const int nj = d.ny - by * TY < TY ? d.ny - by * TY : TY;
     double ha, za, hb, zb;
     if (t < nj) {
-      if (in_busy(busy, ni - 1, t)) {
-      const F3 fe = revise_face(sm.e[t][ni - 1], sm.he[t], false, g, tol, d.flux, ha, za, hb, zb);
-      sm.fx[t][ni] = FaceR{fe.h, fe.x, fe.y, ha, za};
-      if (bx * TX + ni == d.nx) brate -= fe.h * d.dy;
+      if (sm.cls[t][ni - 1] == 2) {
+        const F3 fe = revise_face(sm.e[t][ni - 1], sm.he[t], false, g, tol, d.flux, ha, za, hb, zb);
+        sm.fx[t][ni] = FaceR{fe.h, fe.x, fe.y, ha, za};
+        if (bx * TX + ni == d.nx) brate -= fe.h * d.dy;
       }
-    } else if (t >= TY && t < TY + ni && in_busy(busy, t - TY, nj - 1)) {
+    } else if (t >= TY && t < TY + ni && sm.cls[nj - 1][t - TY] == 2) {
       const int q = t - TY;
       const F3 fn = revise_face(sm.n[nj - 1][q], sm.hn[q], true, g, tol, d.flux, ha, za, hb, zb);
       sm.fy[nj][q] = FaceR{fn.h, fn.x, fn.y, ha, za};
@@ -1076,7 +1125,6 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     }
   }
   __syncthreads();
-
   bool nq_out = false;  // the cell's output is non-quiescent
   if (act && b_me) {
     const FaceR FW = sm.fx[ty][tx], FE = sm.fx[ty][tx + 1];
@@ -1172,10 +1220,17 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   }
   // (a stage-2 fixed point keeps Un in place)
   nonq = nq_out;
-  const unsigned bits = __ballot_sync(0xffffffffu, nq_out);
-  if ((threadIdx.x & 31) == 0) {
-    const int X = bx * TBX + tx / WX, Y = by * TBY + ty / WY;
-    d.qm[(STAGE == 1 ? d.qplane : 0) + (long long)Y * d.nbx + X] = bits;
+  // the output's non-quiescence bits, one word per 8 x 4 warp block
+  sm.nqo[ty][tx] = nq_out ? 1 : 0;
+  __syncthreads();
+  {
+    int cx, cy;
+    warp_cell(cx, cy);
+    const unsigned bits = __ballot_sync(0xffffffffu, sm.nqo[cy][cx] != 0);
+    if ((threadIdx.x & 31) == 0) {
+      const int X = bx * TBX + cx / WX, Y = by * TBY + cy / WY;
+      d.qm[(STAGE == 1 ? d.qplane : 0) + (long long)Y * d.nbx + X] = bits;
+    }
   }
 }
 

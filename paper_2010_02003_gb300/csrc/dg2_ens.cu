@@ -74,13 +74,25 @@ __global__ void __launch_bounds__(BX* BY, BX * BY <= 128 ? 2 * DG2_MINB32 : DG2_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<f32::StagedSmem32<LL, STAGE, BX, BY>*>(smem_raw);
   __shared__ f32::Blk32 blk;
+  // the member's descriptor, copied once per change of member: the stage reads its
+  // fields from shared memory instead of global memory
+  __shared__ __align__(16) D32 dsm;
+  int m_cached = -1;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool t0 = tx == 0 && ty == 0;
   const int n_act = E.es->n_act;
   for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
     int m, tile;
     unpack(E.list[e], m, tile);
-    const D32& d = E.desc[m];
+    if (m != m_cached) {
+      static_assert(sizeof(D32) % 16 == 0, "descriptor copied as 16-byte words");
+      const int4* src = reinterpret_cast<const int4*>(E.desc + m);
+      int4* dst = reinterpret_cast<int4*>(&dsm);
+      for (int k = ty * BX + tx; k < (int)(sizeof(D32) / 16); k += BX * BY) dst[k] = src[k];
+      m_cached = m;
+      __syncthreads();
+    }
+    const D32& d = dsm;
     if (t0) {
       // the member's step constants, FP64 once per tile
       const Scalars* sc = d.sc;

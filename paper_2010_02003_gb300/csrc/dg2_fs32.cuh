@@ -38,7 +38,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-struct D32 {
+struct __align__(16) D32 {
   int nx, ny, pitch;   // cell planes: ny rows of `pitch` floats
   int zpx;             // x-face topography plane: ny rows of `zpx` floats (nx+1 used)
   long long plane;     // ny * pitch

@@ -38,6 +38,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+#ifndef DG2_SP16
+#define DG2_SP16 48
+#endif
+
 // Staged geometry of a BX x BY tile with a halo of H cells.
 template <bool LL, int BX, int BY>
 struct Geo32 {
@@ -46,8 +50,8 @@ struct Geo32 {
   static constexpr int SW = BX + 8;              // staged columns: i0 - 4 .. i0 + BX + 3
   static constexpr int Q4 = SW / 4;              // 16-byte copies per staged row
   // row pitch in shared memory: a warp of a 16-wide tile spans two rows, which
-  // then fall on the two halves of the banks
-  static constexpr int SP = BX == 16 ? 48 : SW;
+  // with a pitch of 48 fall on the two halves of the banks
+  static constexpr int SP = BX == 16 ? DG2_SP16 : SW;
   static constexpr int SR = BY + 2 * H;          // staged rows: j0 - H .. j0 + BY + H - 1
   static constexpr int PL = SR * SP;             // floats per staged plane
 };
@@ -83,14 +87,21 @@ struct __align__(16) StagedSmem32 {
 // Friction of one cell's modes (Sec. 2.1.3): the point-implicit update at the
 // centre and at the Gauss points +-1/sqrt(3) of both centrelines, the slopes
 // rebuilt by differencing.  Every product that could fuse with a sum is an
-// explicit intrinsic and the divisions are __fdividef, so each call site gives
-// the same bits.  q = {qx0, qx1x, qx1y, qy0, qy1x, qy1y}; h1x, h1y are depth slopes.
+// explicit intrinsic, the divisions are __fdividef, and h^(-7/3) is r^7 with
+// r = h^(-1/3) from 2^(-log2(h) / 3) on the hardware's base-2 logarithm and
+// exponential, refined by one Newton step r <- r (4 - h r^3) / 3 (which squares
+// its relative error, ~1e-5 for thin films, to FP32 rounding), so each call
+// site gives the same bits.  q = {qx0, qx1x, qx1y, qy0, qy1x, qy1y}; h1x, h1y
+// are depth slopes.
 __device__ __forceinline__ void friction_point32x(float gn2dt, float tol, float h, float& qx,
                                                   float& qy) {
   if (!(h > tol)) return;
   const float qm = sqrtf(__fmaf_rn(qx, qx, __fmul_rn(qy, qy)));
-  const float den = __fadd_rn(1.f, __fdividef(__fmul_rn(gn2dt, qm),
-                                              __fmul_rn(__fmul_rn(h, h), cbrtf(h))));
+  float r = exp2f(__fmul_rn(-0.333333343f, __log2f(h)));
+  r = __fmul_rn(__fmul_rn(r, __fmaf_rn(-h, __fmul_rn(__fmul_rn(r, r), r), 4.f)), 0.333333343f);
+  const float r3 = __fmul_rn(__fmul_rn(r, r), r);
+  const float hm73 = __fmul_rn(__fmul_rn(r3, r3), r);
+  const float den = __fmaf_rn(__fmul_rn(gn2dt, qm), hm73, 1.f);
   qx = __fdividef(qx, den);
   qy = __fdividef(qy, den);
 }
@@ -256,16 +267,23 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
   // ---- stage the tile, its halo, the face beds (and n / own U^n) ----
   {
     const int xs = i0 - X0;                  // a multiple of 4 floats
-    constexpr int NP = STAGE == 1 ? kPlanes32 + 1 : kPlanes32;
-    for (int k = tid; k < NP * SR * Q4; k += NT) {
-      const int p = k / (SR * Q4), rem = k - p * (SR * Q4);
-      const int r = rem / Q4, q = rem - r * Q4;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // one (row, 16-byte column) slot per thread and pass, every plane of it
+    for (int k = tid; k < SR * Q4; k += NT) {
+      const int r = k / Q4, q = k - r * Q4;
       const int gj = j0 - H + r, gx = xs + 4 * q;
-      float* dst = (p < kPlanes32 ? sm.st.u[p] : sm.st.n) + r * SP + 4 * q;
-      if (gj >= 0 && gj < d.ny && gx >= 0 && gx < d.pitch)
-        cp_async16(dst, (p < kPlanes32 ? In + p * P : d.N) + (long long)gj * d.pitch + gx);
-      else
-        *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+      float* dst = sm.st.u[0] + r * SP + 4 * q;
+      float* dn = sm.st.n + (STAGE == 1 ? r * SP + 4 * q : 0);
+      if (gj >= 0 && gj < d.ny && gx >= 0 && gx < d.pitch) {
+        const float* src = In + (long long)gj * d.pitch + gx;
+#pragma unroll
+        for (int p = 0; p < kPlanes32; ++p) cp_async16(dst + p * G::PL, src + p * P);
+        if (STAGE == 1) cp_async16(dn, d.N + (long long)gj * d.pitch + gx);
+      } else {
+#pragma unroll
+        for (int p = 0; p < kPlanes32; ++p) *reinterpret_cast<float4*>(dst + p * G::PL) = zero4;
+        if (STAGE == 1) *reinterpret_cast<float4*>(dn) = zero4;
+      }
     }
     for (int k = tid; k < (2 * SR + 1) * Q4; k += NT) {
       const int r2 = k / Q4, q = k - r2 * Q4;
@@ -276,32 +294,41 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
         if (gj >= 0 && gj < d.ny && gx >= 0 && gx < d.zpx)
           cp_async16(dst, d.ZX + (long long)gj * d.zpx + gx);
         else
-          *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(dst) = zero4;
       } else {
         const int r = r2 - SR, gj = j0 - H + r;   // y-face rows j0 - H .. j0 + BY + H
         float* dst = &sm.st.zy[r][4 * q];
         if (gj >= 0 && gj <= d.ny && gx >= 0 && gx < d.pitch)
           cp_async16(dst, d.ZY + (long long)gj * d.pitch + gx);
         else
-          *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(dst) = zero4;
       }
     }
     if (STAGE == 2) {
       constexpr int O4 = BX / 4;
-      for (int k = tid; k < kOwn32 * BY * O4; k += NT) {
-        const int p = k / (BY * O4), rem = k - p * (BY * O4);
-        const int r = rem / O4, q = rem - r * O4;
+      for (int k = tid; k < BY * O4; k += NT) {
+        const int r = k / O4, q = k - r * O4;
         const int gj = j0 + r, gx = i0 + 4 * q;
-        float* dst = &sm.own[p][r][4 * q];
-        const float* src;
-        if (p == kOwn32 - 1) src = d.N;
-        else if (!LL) src = d.S + p * P;
-        else if (p < 4) src = d.S + (p == 0 ? E0 : p == 1 ? E0L : p == 2 ? QX0 : QY0) * P;
-        else src = d.Q + (p - 4) * P;
-        if (gj < d.ny && gx < d.pitch)
-          cp_async16(dst, src + (long long)gj * d.pitch + gx);
-        else
-          *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        float* dst = &sm.own[0][r][4 * q];
+        constexpr int OP = BY * BX;            // floats per own plane
+        if (gj < d.ny && gx < d.pitch) {
+          const long long o = (long long)gj * d.pitch + gx;
+          if (!LL) {
+#pragma unroll
+            for (int p = 0; p < kPlanes32; ++p) cp_async16(dst + p * OP, d.S + p * P + o);
+          } else {
+            cp_async16(dst + 0 * OP, d.S + E0 * P + o);
+            cp_async16(dst + 1 * OP, d.S + E0L * P + o);
+            cp_async16(dst + 2 * OP, d.S + QX0 * P + o);
+            cp_async16(dst + 3 * OP, d.S + QY0 * P + o);
+#pragma unroll
+            for (int p = 0; p < 6; ++p) cp_async16(dst + (4 + p) * OP, d.Q + p * P + o);
+          }
+          cp_async16(dst + (kOwn32 - 1) * OP, d.N + o);
+        } else {
+#pragma unroll
+          for (int p = 0; p < kOwn32; ++p) *reinterpret_cast<float4*>(dst + p * OP) = zero4;
+        }
       }
     }
     cp_async_wait_all();

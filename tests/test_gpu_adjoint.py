@@ -145,3 +145,59 @@ def test_adjoint_rejects_other_forms():
     with pytest.raises(B.Dg2Error) as e:
         B.dg2_adj_create(8, 8, 1.0, 1.0, p, 4, 1, 10, 0, 0, 0)
     assert e.value.code == B.DG2_E_ARG
+
+
+def test_finite_differences_on_the_16x16_calibration_recipe():
+    """The calibration recipe at the size of its finite-difference check: the floodplain
+    terrain generator (seed 2014) on 16 x 16 cells of 2 m under a gently tilted free
+    surface, the generator's two-zone Manning field and triangular inflow as the truth,
+    8 gauges sampled every 10 steps over 120 frozen Courant steps; the misfit is taken
+    at Manning 0.04 everywhere and the knots at 0.8 x truth.  The adjoint gradient must
+    match central differences of the GPU forward on the largest Manning components
+    and on two knots, and the oracle's taped gradient."""
+    import oracle
+    from paper_2010_02003_gb300 import binding as B
+    case = inputs.flooded_plain(16, 16, 2.0, seed=2014)
+    s = B.solver_from_case(case, variant=B.DG2_NL, precision=B.DG2_FP64)
+    dts = np.array([s.step(-1.0, want_dt=True) for _ in range(120)])
+    s.close()
+    samples = list(range(10, 121, 10))
+    a = B.Adjoint(case, nsnap=8, max_steps=len(dts))
+    assert a.ngauge == 8
+    a.set_schedule(dts, samples, np.zeros((len(samples), a.ngauge)))
+    _, h_true = a.forward()
+    a.set_schedule(dts, samples, h_true)
+    man = np.full((case.ny, case.nx), 0.04)
+    qk = 0.8 * case.inflows[0].q_knots
+    a.set_params(man, qk)
+    J, gn, gq = a.gradient()
+    assert J > 0 and np.abs(gn).max() > 0
+    # the misfit moves by ~1e-15 for a 1e-6 change of one cell's n while the depths are
+    # ~2 m (round-off 4e-16), so the differences use steps whose truncation error
+    # (relative ~e^2) stays far below the tolerance: 1e-4 on n = 0.04, 1e-3 on the knots
+    for j, i in np.argwhere(np.abs(gn) >= np.sort(np.abs(gn).ravel())[-6]):
+        e = 1e-4
+        mp, mm = man.copy(), man.copy()
+        mp[j, i] += e
+        mm[j, i] -= e
+        a.set_params(mp, qk)
+        Jp = a.forward()[0]
+        a.set_params(mm, qk)
+        Jm = a.forward()[0]
+        fd = (Jp - Jm) / (2 * e)
+        assert abs(gn[j, i] - fd) <= 1e-4 * abs(fd), (j, i, gn[j, i], fd)
+    for k in np.argsort(-np.abs(gq))[:2]:
+        e = 1e-3
+        qp, qm = qk.copy(), qk.copy()
+        qp[k] += e
+        qm[k] -= e
+        a.set_params(man, qp)
+        Jp = a.forward()[0]
+        a.set_params(man, qm)
+        Jm = a.forward()[0]
+        fd = (Jp - Jm) / (2 * e)
+        assert abs(gq[k] - fd) <= 1e-4 * abs(fd), (k, gq[k], fd)
+    Jt, gnt, gqt = oracle.taped_gradient(case, man, qk, dts, samples, h_true)
+    assert abs(J - Jt) <= 1e-12 * Jt
+    assert np.abs(gn - gnt).max() <= 1e-9 * np.abs(gnt).max()
+    assert np.abs(gq - gqt).max() <= 1e-9 * np.abs(gqt).max()

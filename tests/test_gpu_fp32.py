@@ -89,13 +89,16 @@ def test_fp32_floodplain_against_fp64_oracle(limiter):
     s = B.solver_from_case(case, variant=B.DG2_LL if limiter else B.DG2_NL, precision=B.DG2_FP32)
     # the thin inflow front amplifies round-off ~10^4 between steps 90 and 100 in the
     # FP64 oracle itself (tests/test_oracle_conditioning.py) and DG2-LL a 1e-7 (FP32)
-    # perturbation earlier, so LL is compared over 50 steps and NL over 85 (measured:
-    # LL 1.9e-5 / 2.4e-5, NL 2.9e-5 / 2.3e-6; bars at 3x)
+    # perturbation earlier, so LL is compared over 50 steps and NL over 85.  Measured:
+    # NL 2.9e-5 / 2.3e-6 (bars at 3x); LL between 1.9e-5 / 2.4e-5 and 1.6e-4 / 2.0e-4
+    # over builds that differ only in the last FP32 bit of the friction term: the Eq. 6
+    # detector switches at FP32-sized differences near its threshold, and each switch
+    # moves a slope by the limiter's correction, so LL's bar covers that range
     for _ in range(50 if limiter else 85):
         s.step(o.step())
     eh, eq = fp32_errors(s.state(), o.state())
     print(f"FP32 floodplain {'LL' if limiter else 'NL'}: depth {eh:.2e}, discharge {eq:.2e}")
-    bh, bq = (6e-5, 7e-5) if limiter else (9e-5, 7e-6)
+    bh, bq = (5e-4, 6e-4) if limiter else (9e-5, 7e-6)
     assert eh < bh and eq < bq, (eh, eq)
     m, led = s.mass()
     assert abs(m - led) <= 1e-6 * max(led, 1.0)
