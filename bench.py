@@ -466,7 +466,7 @@ def ensemble_variant(B, torch, inputs, n=ENS_MEMBERS, t_end=ENS_T_END):
 ADJ_N, ADJ_STEPS, ADJ_SNAP, ADJ_KNOTS = 512, 4000, 64, 64
 
 
-def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS):
+def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS, precision=0, ref=None):
     """Discrete adjoint on the calibration recipe: the 512 x 512 floodplain terrain
     (dx 2 m, seed 2014) under a gently tilted free surface (every cell wet: the
     channel start's thin films make the step map chaotic, and its exact derivative
@@ -477,7 +477,9 @@ def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS):
     truth.  Times the
     misfit alone (forward) and misfit + gradient (forward, checkpointed reverse)
     with CUDA events on the adjoint's stream; the plain FP64 DG2-NL solver doing the
-    same steps is timed beside it."""
+    same steps is timed beside it.  precision 1: the FP32-storage adjoint (FP32 state,
+    checkpoints and adjoint fields, FP64 arithmetic), whose gradient is compared with
+    the FP64 run's (`ref`)."""
     case = inputs.flooded_plain(ADJ_N, ADJ_N, 2.0, seed=2014)
     s = B.solver_from_case(case, variant=B.DG2_NL, precision=B.DG2_FP64)
     init = s.state()
@@ -500,9 +502,11 @@ def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS):
     tk = np.linspace(0.0, float(t[-1]), ADJ_KNOTS)
     q_true = np.interp(tk, f.t_knots, f.q_knots)
     f.t_knots, f.q_knots = tk, q_true
-    a = B.Adjoint(case, nsnap=ADJ_SNAP, max_steps=steps)
-    a.set_schedule(dts, samples, np.zeros((len(samples), a.ngauge)))
-    _, h_true = a.forward()
+    truth = B.Adjoint(case, nsnap=ADJ_SNAP, max_steps=steps)
+    truth.set_schedule(dts, samples, np.zeros((len(samples), truth.ngauge)))
+    _, h_true = truth.forward()
+    truth.close()
+    a = B.Adjoint(case, nsnap=ADJ_SNAP, max_steps=steps, precision=precision)
     a.set_schedule(dts, samples, h_true)
     man0 = np.full((case.ny, case.nx), 0.04)
     a.set_params(man0, 0.8 * q_true)
@@ -521,7 +525,16 @@ def adjoint_variant(B, torch, inputs, steps=ADJ_STEPS):
     grad_ms = ev0.elapsed_time(ev1)
     f1, r1 = a.counts()
     a.close()
-    return {"cells": case.nx * case.ny, "steps": steps, "t_end_s": float(t[-1]),
+    out_ref = {}
+    if ref is not None:
+        out_ref = {"misfit_vs_fp64": abs(J - ref["misfit"]) / ref["misfit"],
+                   "grad_manning_vs_fp64": float(np.abs(gn - ref["gn"]).max() /
+                                                 np.abs(ref["gn"]).max()),
+                   "grad_knots_vs_fp64": float(np.abs(gq - ref["gq"]).max() /
+                                               np.abs(ref["gq"]).max())}
+    return {**out_ref, "precision": "fp32 storage, fp64 arithmetic" if precision else "fp64",
+            "gn": gn, "gq": gq,
+            "cells": case.nx * case.ny, "steps": steps, "t_end_s": float(t[-1]),
             "samples": len(samples), "gauges": 8, "knots": ADJ_KNOTS, "checkpoints": ADJ_SNAP,
             "misfit": J, "forward_ms": fwd_ms, "gradient_ms": grad_ms,
             "value": grad_ms / fwd_ms, "unit": "adjoint/forward time ratio",
@@ -645,11 +658,18 @@ def main():
         results[key] = run
         torch.cuda.empty_cache()
 
-    adj = None
-    if not only or "fp64_nl_adjoint" in only:
+    adj = adj32 = None
+    if not only or "fp64_nl_adjoint" in only or "fp32_nl_adjoint" in only:
         barrier(world)
         adj = adjoint_variant(B, torch, inputs)
         torch.cuda.empty_cache()
+        if not only or "fp32_nl_adjoint" in only:
+            adj32 = adjoint_variant(B, torch, inputs, precision=1, ref=adj)
+            torch.cuda.empty_cache()
+        for r in (adj, adj32):
+            if r is not None:
+                r.pop("gn")
+                r.pop("gq")
 
     schemes = None
     if not only or "fp64_schemes" in only:
@@ -670,7 +690,8 @@ def main():
     if not results:
         if rank == 0:
             extra = {k: v for k, v in (("fp32_nl_ensemble", ens), ("fp64_nl_adjoint", adj),
-                                       ("fp64_schemes", schemes)) if v}
+                                       ("fp32_nl_adjoint", adj32), ("fp64_schemes", schemes))
+                     if v}
             print(json.dumps({"metric": METRIC, "variants": extra}))
         return
     head = "fp64_ll" if "fp64_ll" in results else next(iter(results))
@@ -696,6 +717,8 @@ def main():
             variants["fp32_nl_ensemble"] = ens
         if adj is not None:
             variants["fp64_nl_adjoint"] = adj
+        if adj32 is not None:
+            variants["fp32_nl_adjoint"] = adj32
         if schemes is not None:
             variants["fp64_schemes"] = schemes
         line = {"metric": METRIC, "value": hd["value"], "unit": "cell-updates/s", "n_gpus": world,

@@ -327,7 +327,7 @@ int64_t dg2_ens_launch_count(const dg2_ens *ens);
 int dg2_ens_destroy(dg2_ens *ens);
 
 /* ------------------------------------------------------------------------
- * Discrete adjoint of the FP64 DG2-NL step (Sec. 2.1.2-2.1.3).
+ * Discrete adjoint of the DG2-NL step (Sec. 2.1.2-2.1.3), FP64 or FP32.
  *
  * Problem: nsteps DG2-NL steps (friction, the two RK stages of Eqs. 4-5, the
  * wet-dry treatment) from a given state with a given sequence of step sizes
@@ -344,6 +344,12 @@ int dg2_ens_destroy(dg2_ens *ens);
  * wet scale) and the cell's own terms on its faces' revised depths and beds;
  * both enter the reverse sweep.  Rain and point sources are not
  * part of the problem.  Planes are dense (ny rows of nx, x fastest).
+ * Precision (dg2_params.precision): DG2_FP64, or DG2_FP32 -- the same step and
+ * reverse sweep with every device buffer (state, checkpoints, adjoints, face
+ * Jacobians, topography, Manning n, gradients) stored in FP32 and the
+ * arithmetic kept in FP64 registers (the depth form's pressure / bed-term
+ * balance does not survive FP32 arithmetic); half the checkpoint memory.  Host
+ * arrays are FP64 in both.
  * ---------------------------------------------------------------------- */
 typedef struct dg2_adj dg2_adj;
 
@@ -351,10 +357,10 @@ typedef struct dg2_adj dg2_adj;
  * max_gauges >= 0).  About (nsnap + 10) state-sized buffers of 9 planes. */
 size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps);
 
-/* params: g, tol_dry, bc[4] and wetdry (the step's face revision, either) are
- * used; variant must be DG2_NL, precision DG2_FP64, flux DG2_HLL and scheme
- * DG2_SCHEME_DG2 (DG2_E_ARG otherwise).  Workspace and stream as for
- * dg2_init_grid. */
+/* params: g, tol_dry, bc[4], wetdry (the step's face revision, either) and
+ * precision (DG2_FP64 or DG2_FP32) are used; variant must be DG2_NL, flux
+ * DG2_HLL and scheme DG2_SCHEME_DG2 (DG2_E_ARG otherwise).  Workspace and
+ * stream as for dg2_init_grid (dg2_adj_workspace_bytes serves both precisions). */
 int dg2_adj_create(dg2_adj **out, int nx, int ny, double dx, double dy, const dg2_params *params,
                    int nsnap, int max_gauges, int max_steps, void *dev_workspace,
                    size_t ws_bytes, void *cuda_stream);

@@ -587,14 +587,15 @@ class Ensemble:
 
 
 class Adjoint:
-    """Discrete adjoint of the FP64 DG2-NL step for one problem built from an
-    inputs.Case (DEM, initial water, edges, its first inflow, gauges): the misfit of
-    sampled gauge depths against observations and its gradients with respect to the
-    Manning n of every cell and the inflow knot discharges, for the step with the
-    default face revision or (wetdry=DG2_WD_PRINTED) Sec. 2.1.2 as printed."""
+    """Discrete adjoint of the DG2-NL step for one problem built from an inputs.Case
+    (DEM, initial water, edges, its first inflow, gauges): the misfit of sampled gauge
+    depths against observations and its gradients with respect to the Manning n of
+    every cell and the inflow knot discharges, for the step with the default face
+    revision or (wetdry=DG2_WD_PRINTED) Sec. 2.1.2 as printed, in FP64 or
+    (precision=DG2_FP32) FP32 state and arithmetic."""
 
-    def __init__(self, case, *, nsnap=64, max_steps=100000, wetdry=DG2_WD_POSITIVE, stream=None,
-                 device=None):
+    def __init__(self, case, *, nsnap=64, max_steps=100000, wetdry=DG2_WD_POSITIVE,
+                 precision=DG2_FP64, stream=None, device=None):
         import torch
         self.case = case
         self.nx, self.ny = case.nx, case.ny
@@ -605,6 +606,7 @@ class Adjoint:
         p = dg2_default_params()
         p.cfl, p.dt_max = case.cfl, case.dt_max
         p.wetdry = int(wetdry)
+        p.precision = int(precision)
         for k in range(4):
             p.bc[k] = int(case.bc[k])
         g = np.zeros((0, 2)) if case.gauges is None else np.asarray(case.gauges, dtype=np.float64)

@@ -12,7 +12,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f)
-       for f in ("dg2_api.cu", "dg2_ens.cu", "dg2_adj.cu", "dg2_noalloc.cu", "dg2_peak.cu")]
+       for f in ("dg2_api.cu", "dg2_ens.cu", "dg2_adj.cu", "dg2_adj32.cu", "dg2_adj_api.cu",
+                 "dg2_noalloc.cu", "dg2_peak.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f)
               for f in ("dg2_device.cuh", "dg2_fs32.cuh", "dg2_fs32_staged.cuh", "dg2_fv.cuh", "dg2_internal.h")] + [
     os.path.join(ROOT, "include", "dg2.h")]

@@ -36,8 +36,24 @@
 #include "../../include/dg2.h"
 #include "dg2_internal.h"
 
+// Storage of this translation unit: FP64 by default (namespace dg2::adj);
+// dg2_adj32.cu compiles the same file with FP32 storage (namespace dg2::adj32).
+#ifndef DG2_ADJ_STORE
+#define DG2_ADJ_STORE double
+#define DG2_ADJ_NS adj
+#endif
+
 namespace dg2 {
-namespace adj {
+namespace DG2_ADJ_NS {
+
+// Arithmetic type (FP64 in both builds) and storage type of every device buffer:
+// state, checkpoints, operator adjoints, face Jacobians, topography, Manning n,
+// gauge tables and gradients -- double, or float for the FP32 adjoint (this file
+// is compiled once for each).  Kernels load stored values into FP64 registers and
+// round their results to the storage type; the hydrograph, the step times, the
+// per-step discharge adjoint sums and the misfit stay FP64.
+using real = double;
+using store = DG2_ADJ_STORE;
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual numbers
@@ -45,12 +61,12 @@ namespace adj {
 
 template <int N>
 struct Dual {
-  double v;
-  double d[N];
+  real v;
+  real d[N];
 };
 
 template <int N>
-__device__ __forceinline__ Dual<N> cst(double x) {
+__device__ __forceinline__ Dual<N> cst(real x) {
   Dual<N> r;
   r.v = x;
 #pragma unroll
@@ -58,7 +74,7 @@ __device__ __forceinline__ Dual<N> cst(double x) {
   return r;
 }
 template <int N>
-__device__ __forceinline__ Dual<N> var(double x, int k) {
+__device__ __forceinline__ Dual<N> var(real x, int k) {
   Dual<N> r = cst<N>(x);
   r.d[k] = 1.0;
   return r;
@@ -99,21 +115,21 @@ template <int N>
 __device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
   Dual<N> r;
   r.v = a.v / b.v;
-  const double ib = 1.0 / b.v;
+  const real ib = 1.0 / b.v;
 #pragma unroll
   for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
   return r;
 }
 template <int N>
-__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, double b) { return a + cst<N>(b); }
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, real b) { return a + cst<N>(b); }
 template <int N>
-__device__ __forceinline__ Dual<N> operator+(double a, const Dual<N>& b) { return cst<N>(a) + b; }
+__device__ __forceinline__ Dual<N> operator+(real a, const Dual<N>& b) { return cst<N>(a) + b; }
 template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, double b) { return a - cst<N>(b); }
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, real b) { return a - cst<N>(b); }
 template <int N>
-__device__ __forceinline__ Dual<N> operator-(double a, const Dual<N>& b) { return cst<N>(a) - b; }
+__device__ __forceinline__ Dual<N> operator-(real a, const Dual<N>& b) { return cst<N>(a) - b; }
 template <int N>
-__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, double b) {
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, real b) {
   Dual<N> r;
   r.v = a.v * b;
 #pragma unroll
@@ -121,18 +137,18 @@ __device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, double b) {
   return r;
 }
 template <int N>
-__device__ __forceinline__ Dual<N> operator*(double a, const Dual<N>& b) { return b * a; }
+__device__ __forceinline__ Dual<N> operator*(real a, const Dual<N>& b) { return b * a; }
 template <int N>
-__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, double b) { return a / cst<N>(b); }
+__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, real b) { return a / cst<N>(b); }
 template <int N>
-__device__ __forceinline__ Dual<N> operator/(double a, const Dual<N>& b) { return cst<N>(a) / b; }
+__device__ __forceinline__ Dual<N> operator/(real a, const Dual<N>& b) { return cst<N>(a) / b; }
 // sqrt, cbrt and |.| with the derivative taken as 0 where the function has
 // none (a zero argument: a dry limit's celerity, a still point's |q|).
 template <int N>
 __device__ __forceinline__ Dual<N> sqrt(const Dual<N>& a) {
   Dual<N> r;
   r.v = ::sqrt(a.v);
-  const double s = r.v > 0.0 ? 0.5 / r.v : 0.0;
+  const real s = r.v > 0.0 ? 0.5 / r.v : 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * s;
   return r;
@@ -141,16 +157,16 @@ template <int N>
 __device__ __forceinline__ Dual<N> cbrt(const Dual<N>& a) {
   Dual<N> r;
   r.v = ::cbrt(a.v);
-  const double s = r.v != 0.0 ? 1.0 / (3.0 * r.v * r.v) : 0.0;
+  const real s = r.v != 0.0 ? 1.0 / (3.0 * r.v * r.v) : 0.0;
 #pragma unroll
   for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * s;
   return r;
 }
-__device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
-__device__ __forceinline__ double cbrt(double x) { return ::cbrt(x); }
-__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ real sqrt(real x) { return ::sqrt(x); }
+__device__ __forceinline__ real cbrt(real x) { return ::cbrt(x); }
+__device__ __forceinline__ real val(real x) { return x; }
 template <int N>
-__device__ __forceinline__ double val(const Dual<N>& x) { return x.v; }
+__device__ __forceinline__ real val(const Dual<N>& x) { return x.v; }
 // a if a <= b else b (and the max likewise), selecting the operand
 template <class T>
 __device__ __forceinline__ T tmin(const T& a, const T& b) { return val(b) < val(a) ? b : a; }
@@ -158,7 +174,7 @@ template <class T>
 __device__ __forceinline__ T tmax(const T& a, const T& b) { return val(b) > val(a) ? b : a; }
 
 // ---------------------------------------------------------------------------
-// The scheme's point functions, templated on the scalar (double or Dual)
+// The scheme's point functions, templated on the scalar (real or Dual)
 // ---------------------------------------------------------------------------
 
 template <class T>
@@ -172,7 +188,7 @@ struct F3T {
 
 // Revised face limit (Sec. 2.1.2): h* = max(0, h), velocities q/h above tol.
 template <class T>
-__device__ __forceinline__ LimT<T> revise_t(const T& h, const T& qx, const T& qy, double tol) {
+__device__ __forceinline__ LimT<T> revise_t(const T& h, const T& qx, const T& qy, real tol) {
   LimT<T> r;
   const T zero = T(h - h);  // a zero of the right type
   if (val(h) > tol) {
@@ -192,7 +208,7 @@ __device__ __forceinline__ LimT<T> revise_t(const T& h, const T& qx, const T& qy
 template <class T>
 __device__ __forceinline__ F3T<T> hll_t(const T& hL, const T& qnL, const T& qtL, const T& unL,
                                         const T& utL, const T& hR, const T& qnR, const T& qtR,
-                                        const T& unR, const T& utR, double g, double tol) {
+                                        const T& unR, const T& utR, real g, real tol) {
   F3T<T> f;
   const T zero = T(hL - hL);
   if (val(hL) <= tol && val(hR) <= tol) {
@@ -232,7 +248,7 @@ __device__ __forceinline__ F3T<T> hll_t(const T& hL, const T& qnL, const T& qtL,
 
 template <class T>
 __device__ __forceinline__ F3T<T> flux_face(const LimT<T>& L, const LimT<T>& R, bool ydir,
-                                            double g, double tol) {
+                                            real g, real tol) {
   if (!ydir) return hll_t(L.h, L.qx, L.qy, L.u, L.v, R.h, R.qx, R.qy, R.u, R.v, g, tol);
   const F3T<T> r = hll_t(L.h, L.qy, L.qx, L.v, L.u, R.h, R.qy, R.qx, R.v, R.u, g, tol);
   F3T<T> o;
@@ -241,7 +257,7 @@ __device__ __forceinline__ F3T<T> flux_face(const LimT<T>& L, const LimT<T>& R, 
 }
 
 template <class T>
-__device__ __forceinline__ F3T<T> phys_t(const T& h, const T& qx, const T& qy, double g, double tol,
+__device__ __forceinline__ F3T<T> phys_t(const T& h, const T& qx, const T& qy, real g, real tol,
                                          bool ydir) {
   const T zero = T(h - h);
   T u = zero, v = zero;
@@ -274,9 +290,9 @@ __device__ __forceinline__ T pos_t(const T& x) {
 
 // x with its value replaced by v (derivatives kept): the cell mean depth h0 is
 // the mode the forward holds, its derivative that of (hE + hW) / 2.
-__device__ __forceinline__ double with_value(double, double v) { return v; }
+__device__ __forceinline__ real with_value(real, real v) { return v; }
 template <int N>
-__device__ __forceinline__ Dual<N> with_value(Dual<N> x, double v) {
+__device__ __forceinline__ Dual<N> with_value(Dual<N> x, real v) {
   x.v = v;
   return x;
 }
@@ -284,7 +300,7 @@ __device__ __forceinline__ Dual<N> with_value(Dual<N> x, double v) {
 template <class T>
 struct RecT {
   T h, u, v, hs;  // planar depth limit, velocities, the depth the face may draw on
-  double zf;      // continuous face bed
+  real zf;      // continuous face bed
   bool pw;        // the side's cell is partially wet
 };
 
@@ -292,7 +308,7 @@ struct RecT {
 // planar depth limits (summed W, E, S, N); wd = 0 keeps the printed revision.
 template <class T>
 __device__ __forceinline__ bool pw_scale_t(const T& h0, const T& hW, const T& hE, const T& hS,
-                                           const T& hN, double tol, int wd, T& sc) {
+                                           const T& hN, real tol, int wd, T& sc) {
   const T zero = T(h0 - h0);
   sc = zero + 1.0;
   if (!wd || !(val(h0) > tol)) return false;
@@ -309,8 +325,8 @@ __device__ __forceinline__ bool pw_scale_t(const T& h0, const T& hW, const T& hE
 // Record of a side with planar limit (h, qx, qy) over face bed zf; velocities by
 // the tol rule, or desingularised below eps = h0 / 10 (thin: default revision).
 template <class T>
-__device__ __forceinline__ RecT<T> make_rec_t(const T& h, const T& qx, const T& qy, double zf,
-                                              bool pw, const T& sc, double tol, bool thin,
+__device__ __forceinline__ RecT<T> make_rec_t(const T& h, const T& qx, const T& qy, real zf,
+                                              bool pw, const T& sc, real tol, bool thin,
                                               const T& h0) {
   const T zero = T(h - h);
   RecT<T> r;
@@ -337,7 +353,7 @@ __device__ __forceinline__ RecT<T> make_rec_t(const T& h, const T& qx, const T& 
 // Revision of the face between lower side a and upper side b: the flux's
 // states and each side's revised depth and bed level for its own terms.
 template <class T>
-__device__ __forceinline__ void revise_face_t(const RecT<T>& a, const RecT<T>& b, double tol,
+__device__ __forceinline__ void revise_face_t(const RecT<T>& a, const RecT<T>& b, real tol,
                                               LimT<T>& ra, LimT<T>& rb, T& ha, T& za, T& hb,
                                               T& zb) {
   const T zero = T(a.h - a.h);
@@ -374,25 +390,25 @@ constexpr int kMaxKnotsAdj = 4096;
 struct Prob {
   int nx, ny;
   long long N;                 // cells (dense planes, x fastest)
-  double dx, dy, inv_dx, inv_dy, g, tol;
+  real dx, dy, inv_dx, inv_dy, g, tol;
   int bc[4];
   // one inflow segment (edge < 0: none)
   int in_edge;
-  double in_s0, in_s1, in_width;
-  const double* Z;             // 3 planes z0, z1x, z1y
-  const double* Nm;            // Manning n
-  double rain, rain_t0, rain_t1;
+  real in_s0, in_s1, in_width;
+  const store* Z;            // 3 planes z0, z1x, z1y
+  const store* Nm;           // Manning n
+  real rain, rain_t0, rain_t1;
   int wd;                      // 1: positivity-consistent revision (default), 0: printed
 };
 
-__device__ __forceinline__ bool on_inflow(const Prob& p, int edge, double s) {
+__device__ __forceinline__ bool on_inflow(const Prob& p, int edge, real s) {
   return p.in_edge == edge && s >= p.in_s0 && s <= p.in_s1;
 }
 
 // Outside state of an edge face from the own raw limit (h, qx, qy) and the
 // hydrograph discharge Q (m^3/s) of the inflow segment at the stage time.
 template <class T>
-__device__ __forceinline__ void ghost_t(const Prob& p, int edge, double s, const T& Q, T& h, T& qx,
+__device__ __forceinline__ void ghost_t(const Prob& p, int edge, real s, const T& Q, T& h, T& qx,
                                         T& qy) {
   const T zero = T(h - h);
   if (on_inflow(p, edge, s)) {
@@ -418,10 +434,10 @@ __device__ __forceinline__ void ghost_t(const Prob& p, int edge, double s, const
 enum { H0 = 0, H1X, H1Y, QX0, QX1X, QX1Y, QY0, QY1X, QY1Y };
 
 // Raw limit (h, qx, qy) of cell c at face f (0 E, 1 W, 2 N, 3 S).
-__device__ __forceinline__ void raw_limit(const double* __restrict__ U, long long N, long long c,
-                                          int f, double& h, double& qx, double& qy) {
+__device__ __forceinline__ void raw_limit(const store* __restrict__ U, long long N, long long c,
+                                          int f, real& h, real& qx, real& qy) {
   const int m = f <= 1 ? 1 : 2;
-  const double sg = (f == 0 || f == 2) ? 1.0 : -1.0;
+  const real sg = (f == 0 || f == 2) ? 1.0 : -1.0;
   h = U[c] + sg * U[m * N + c];
   qx = U[3 * N + c] + sg * U[(3 + m) * N + c];
   qy = U[6 * N + c] + sg * U[(6 + m) * N + c];
@@ -432,7 +448,7 @@ __device__ __forceinline__ void raw_limit(const double* __restrict__ U, long lon
 template <class T>
 __device__ __forceinline__ void cell_recs_t(const Prob& p, long long c, const T* E, const T* W,
                                             const T* Nn, const T* S, const T& h0, RecT<T>* r) {
-  const double z0 = p.Z[c], z1x = p.Z[p.N + c], z1y = p.Z[2 * p.N + c];
+  const real z0 = p.Z[c], z1x = p.Z[p.N + c], z1y = p.Z[2 * p.N + c];
   T sc;
   const bool pw = pw_scale_t(h0, W[0], E[0], S[0], Nn[0], p.tol, p.wd, sc);
   const bool thin = p.wd != 0;
@@ -459,13 +475,13 @@ __device__ __forceinline__ void own_terms(const Prob& p, const T* hs, const T* z
   const T h1x = 0.5 * (Es.h - Ws.h), x1x = 0.5 * (Es.qx - Ws.qx), y1x = 0.5 * (Es.qy - Ws.qy);
   const T h0y = 0.5 * (Ns.h + Ss.h), x0y = 0.5 * (Ns.qx + Ss.qx), y0y = 0.5 * (Ns.qy + Ss.qy);
   const T h1y = 0.5 * (Ns.h - Ss.h), x1y = 0.5 * (Ns.qx - Ss.qx), y1y = 0.5 * (Ns.qy - Ss.qy);
-  const double r3 = 1.0 / 1.7320508075688772;
+  const real r3 = 1.0 / 1.7320508075688772;
   const F3T<T> Fp = phys_t(h0x + h1x * r3, x0x + x1x * r3, y0x + y1x * r3, p.g, p.tol, false);
   const F3T<T> Fm = phys_t(h0x - h1x * r3, x0x - x1x * r3, y0x - y1x * r3, p.g, p.tol, false);
   const F3T<T> Gp = phys_t(h0y + h1y * r3, x0y + x1y * r3, y0y + y1y * r3, p.g, p.tol, true);
   const F3T<T> Gm = phys_t(h0y - h1y * r3, x0y - x1y * r3, y0y - y1y * r3, p.g, p.tol, true);
-  const double g = p.g, idx = p.inv_dx, idy = p.inv_dy;
-  const double k3x = -3.0 * idx, k3y = -3.0 * idy, g23 = 2.0 * g / 3.0;
+  const real g = p.g, idx = p.inv_dx, idy = p.inv_dy;
+  const real k3x = -3.0 * idx, k3y = -3.0 * idy, g23 = 2.0 * g / 3.0;
   L[H0] = zero;
   L[QX0] = -(2.0 * g * h0x * zb1x * idx);
   L[QY0] = -(2.0 * g * h0y * zb1y * idy);
@@ -477,41 +493,41 @@ __device__ __forceinline__ void own_terms(const Prob& p, const T* hs, const T* z
   L[QY1Y] = k3y * (-(Gp.y + Gm.y) + g23 * h1y * zb1y);
 }
 
-// Records of cell (i, j) of state U in double.
-__device__ __forceinline__ void recs_double(const Prob& p, const double* __restrict__ U, long long c,
-                                            RecT<double>* r) {
-  double E[3], W[3], Nn[3], S[3];
+// Records of cell (i, j) of state U in real.
+__device__ __forceinline__ void recs_double(const Prob& p, const store* __restrict__ U, long long c,
+                                            RecT<real>* r) {
+  real E[3], W[3], Nn[3], S[3];
   raw_limit(U, p.N, c, 0, E[0], E[1], E[2]);
   raw_limit(U, p.N, c, 1, W[0], W[1], W[2]);
   raw_limit(U, p.N, c, 2, Nn[0], Nn[1], Nn[2]);
   raw_limit(U, p.N, c, 3, S[0], S[1], S[2]);
-  cell_recs_t<double>(p, c, E, W, Nn, S, U[c], r);
+  cell_recs_t<real>(p, c, E, W, Nn, S, U[c], r);
 }
 
 // Face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at stage time
-// with hydrograph discharge Q, in double: its flux and the own side's revised
+// with hydrograph discharge Q, in real: its flux and the own side's revised
 // depth and bed level.
-__device__ void face_rev(const Prob& p, const double* __restrict__ U, int i, int j, int f, double Q,
-                         const RecT<double>* own, F3T<double>& F, double& ho, double& zo) {
+__device__ void face_rev(const Prob& p, const store* __restrict__ U, int i, int j, int f, real Q,
+                         const RecT<real>* own, F3T<real>& F, real& ho, real& zo) {
   const long long N = p.N, c = (long long)j * p.nx + i;
-  RecT<double> oth;
+  RecT<real> oth;
   const bool edge = (f == 0 && i == p.nx - 1) || (f == 1 && i == 0) || (f == 2 && j == p.ny - 1) ||
                     (f == 3 && j == 0);
   if (edge) {
-    double h, qx, qy;
+    real h, qx, qy;
     raw_limit(U, N, c, f, h, qx, qy);
     const int e = f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2;
-    const double s = f <= 1 ? (j + 0.5) * p.dy : (i + 0.5) * p.dx;
-    ghost_t<double>(p, e, s, Q, h, qx, qy);
-    oth = make_rec_t<double>(h, qx, qy, own[f].zf, false, 1.0, p.tol, false, 0.0);
+    const real s = f <= 1 ? (j + 0.5) * p.dy : (i + 0.5) * p.dx;
+    ghost_t<real>(p, e, s, Q, h, qx, qy);
+    oth = make_rec_t<real>(h, qx, qy, own[f].zf, false, 1.0, p.tol, false, 0.0);
   } else {
     const long long cn = f == 0 ? c + 1 : f == 1 ? c - 1 : f == 2 ? c + p.nx : c - p.nx;
-    RecT<double> nr[4];
+    RecT<real> nr[4];
     recs_double(p, U, cn, nr);
     oth = nr[f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2];
   }
-  LimT<double> ra, rb;
-  double ha, za, hb, zb;
+  LimT<real> ra, rb;
+  real ha, za, hb, zb;
   const bool own_lower = f == 0 || f == 2;
   if (own_lower) revise_face_t(own[f], oth, p.tol, ra, rb, ha, za, hb, zb);
   else revise_face_t(oth, own[f], p.tol, ra, rb, ha, za, hb, zb);
@@ -520,22 +536,22 @@ __device__ void face_rev(const Prob& p, const double* __restrict__ U, int i, int
   zo = own_lower ? za : zb;
 }
 
-// L(U) at cell (i, j) in double (Eq. 4 with the fluxes of its four faces).
-__device__ void cell_operator(const Prob& p, const double* __restrict__ U, int i, int j, double t,
-                              double Q, double* L) {
+// L(U) at cell (i, j) in real (Eq. 4 with the fluxes of its four faces).
+__device__ void cell_operator(const Prob& p, const store* __restrict__ U, int i, int j, real t,
+                              real Q, real* L) {
   const long long c = (long long)j * p.nx + i;
-  RecT<double> r[4];
+  RecT<real> r[4];
   recs_double(p, U, c, r);
-  F3T<double> F[4];
-  double hs[4], zs[4], u[4], v[4];
+  F3T<real> F[4];
+  real hs[4], zs[4], u[4], v[4];
   for (int f = 0; f < 4; ++f) {
     face_rev(p, U, i, j, f, Q, r, F[f], hs[f], zs[f]);
     u[f] = r[f].u;
     v[f] = r[f].v;
   }
-  own_terms<double>(p, hs, zs, u, v, L);
-  const F3T<double> FE = F[0], FW = F[1], GN = F[2], GS = F[3];
-  const double idx = p.inv_dx, idy = p.inv_dy, k3x = -3.0 * idx, k3y = -3.0 * idy;
+  own_terms<real>(p, hs, zs, u, v, L);
+  const F3T<real> FE = F[0], FW = F[1], GN = F[2], GS = F[3];
+  const real idx = p.inv_dx, idy = p.inv_dy, k3x = -3.0 * idx, k3y = -3.0 * idy;
   L[H0] += -(FE.h - FW.h) * idx - (GN.h - GS.h) * idy;
   L[QX0] += -(FE.x - FW.x) * idx - (GN.x - GS.x) * idy;
   L[QY0] += -(FE.y - FW.y) * idx - (GN.y - GS.y) * idy;
@@ -550,16 +566,16 @@ __device__ void cell_operator(const Prob& p, const double* __restrict__ U, int i
 
 // Wet-dry treatment after a stage (mass-neutral); returns the 9-bit mask of
 // the modes it keeps.
-__device__ __forceinline__ unsigned wetdry_mask(double* m, double z0, double z1x, double z1y,
-                                                double tol) {
-  const double h0 = m[H0];
+__device__ __forceinline__ unsigned wetdry_mask(real* m, real z0, real z1x, real z1y,
+                                                real tol) {
+  const real h0 = m[H0];
   if (h0 <= tol) {
 #pragma unroll
     for (int k = 1; k < 9; ++k) m[k] = 0.0;
     return 1u;
   }
   unsigned keep = 0x1FFu;
-  const double eta0 = h0 + z0;
+  const real eta0 = h0 + z0;
   {
     const bool fe = (h0 + m[H1X] <= tol) && !(z0 + z1x > eta0);
     const bool fw = (h0 - m[H1X] <= tol) && !(z0 - z1x > eta0);
@@ -581,7 +597,7 @@ __device__ __forceinline__ unsigned wetdry_mask(double* m, double z0, double z1x
 
 // Friction of one cell (Sec. 2.1.3, as the forward solver): modes m -> out.
 template <class T>
-__device__ __forceinline__ void friction_point_t(const T& gn2dt, double tol, const T& h, T& qx,
+__device__ __forceinline__ void friction_point_t(const T& gn2dt, real tol, const T& h, T& qx,
                                                  T& qy) {
   if (!(val(h) > tol)) return;
   const T qm = sqrt(qx * qx + qy * qy);
@@ -591,14 +607,14 @@ __device__ __forceinline__ void friction_point_t(const T& gn2dt, double tol, con
 }
 
 template <class T>
-__device__ __forceinline__ void friction_cell(const T* m, const T& n, double dt, double g, double tol,
+__device__ __forceinline__ void friction_cell(const T* m, const T& n, real dt, real g, real tol,
                                               T* out) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) out[k] = m[k];
   const T gn2dt = dt * g * n * n;
   T cx = m[QX0], cy = m[QY0];
   friction_point_t(gn2dt, tol, m[H0], cx, cy);
-  const double r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
+  const real r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
 #pragma unroll
   for (int dd = 1; dd <= 2; ++dd) {
     const T h1 = m[dd], x1 = m[3 + dd], y1 = m[6 + dd];
@@ -616,28 +632,28 @@ __device__ __forceinline__ void friction_cell(const T* m, const T& n, double dt,
 // Forward kernels (one thread per cell, dense planes)
 // ---------------------------------------------------------------------------
 
-__global__ void fwd_friction_kernel(Prob p, const double* __restrict__ U, double* __restrict__ Us,
-                                    double dt) {
+__global__ void fwd_friction_kernel(Prob p, const store* __restrict__ U, store* __restrict__ Us,
+                                    real dt) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
-  double m[9], o[9];
+  real m[9], o[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) m[k] = U[k * p.N + c];
-  friction_cell<double>(m, p.Nm[c], dt, p.g, p.tol, o);
+  friction_cell<real>(m, p.Nm[c], dt, p.g, p.tol, o);
 #pragma unroll
   for (int k = 0; k < 9; ++k) Us[k * p.N + c] = o[k];
 }
 
 // Stage 1: U1 = W(Us + dt L(Us, t)); stage 2: Uo = W((Us + U1 + dt L(U1, t)) / 2).
 template <int STAGE>
-__global__ void fwd_stage_kernel(Prob p, const double* __restrict__ Us, const double* __restrict__ U1,
-                                 double* __restrict__ Uo, unsigned short* __restrict__ mask, double dt,
-                                 double t, double Q) {
+__global__ void fwd_stage_kernel(Prob p, const store* __restrict__ Us, const store* __restrict__ U1,
+                                 store* __restrict__ Uo, unsigned short* __restrict__ mask, real dt,
+                                 real t, real Q) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const int i = (int)(c % p.nx), j = (int)(c / p.nx);
-  const double* In = STAGE == 1 ? Us : U1;
-  double L[9], o[9];
+  const store* In = STAGE == 1 ? Us : U1;
+  real L[9], o[9];
   cell_operator(p, In, i, j, t, Q, L);
 #pragma unroll
   for (int k = 0; k < 9; ++k)
@@ -650,26 +666,26 @@ __global__ void fwd_stage_kernel(Prob p, const double* __restrict__ Us, const do
 }
 
 // Sampled gauge depths max(0, planar h) of state U.
-__global__ void gauge_kernel(const double* __restrict__ U, long long N, int ng,
-                             const long long* __restrict__ gc, const double* __restrict__ gx,
-                             const double* __restrict__ ge, double* __restrict__ out) {
+__global__ void gauge_kernel(const store* __restrict__ U, long long N, int ng,
+                             const long long* __restrict__ gc, const store* __restrict__ gx,
+                             const store* __restrict__ ge, store* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ng) return;
   const long long c = gc[k];
-  const double h = U[c] + gx[k] * U[N + c] + ge[k] * U[2 * N + c];
+  const real h = U[c] + gx[k] * U[N + c] + ge[k] * U[2 * N + c];
   out[k] = h > 0.0 ? h : 0.0;
 }
 
 // lambda += dJ/dU for one sample: 2 (h - obs) (1, xi, eta) on the depth modes
 // where the clipped depth is positive (one thread: gauges may share a cell).
-__global__ void gauge_seed_kernel(double* __restrict__ lam, long long N, int ng,
-                                  const long long* __restrict__ gc, const double* __restrict__ gx,
-                                  const double* __restrict__ ge, const double* __restrict__ h,
-                                  const double* __restrict__ obs) {
+__global__ void gauge_seed_kernel(store* __restrict__ lam, long long N, int ng,
+                                  const long long* __restrict__ gc, const store* __restrict__ gx,
+                                  const store* __restrict__ ge, const store* __restrict__ h,
+                                  const store* __restrict__ obs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int k = 0; k < ng; ++k) {
     if (!(h[k] > 0.0)) continue;
-    const double r = 2.0 * (h[k] - obs[k]);
+    const real r = 2.0 * (h[k] - obs[k]);
     const long long c = gc[k];
     lam[c] += r;
     lam[N + c] += r * gx[k];
@@ -684,8 +700,8 @@ __global__ void gauge_seed_kernel(double* __restrict__ lam, long long N, int ng,
 // Adjoint mu of the operator output of a stage at cell c:
 //   stage 2: mu = dt/2 * mask2 * lam2            (V2 = (Us + U1 + dt L) / 2)
 //   stage 1: mu = dt * mask1 * lamU1             (V1 = Us + dt L)
-__device__ __forceinline__ void stage_mu(const double* __restrict__ lam, const unsigned short* mask,
-                                         long long N, long long c, double w, double* mu) {
+__device__ __forceinline__ void stage_mu(const store* __restrict__ lam, const unsigned short* mask,
+                                         long long N, long long c, real w, real* mu) {
   const unsigned m = mask[c];
 #pragma unroll
   for (int k = 0; k < 9; ++k) mu[k] = ((m >> k) & 1u) ? w * lam[k * N + c] : 0.0;
@@ -696,14 +712,14 @@ __device__ __forceinline__ void stage_mu(const double* __restrict__ lam, const u
 // (faces E, W, N, S; h, qx, qy each) and to the revised depth h* and bed z* of
 // each of its four faces.  Writes OWN planes 0..11 (the raw limits' adjoints)
 // and 12..19 (h*, z* of faces E, W, N, S).
-__global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const double* __restrict__ lam,
-                               const unsigned short* __restrict__ mask, double w, double Q,
-                               double* __restrict__ OWN) {
+__global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store* __restrict__ lam,
+                               const unsigned short* __restrict__ mask, real w, real Q,
+                               store* __restrict__ OWN) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const long long N = p.N;
   const int i = (int)(c % p.nx), j = (int)(c / p.nx);
-  double mu[9];
+  real mu[9];
   stage_mu(lam, mask, N, c, w, mu);
   bool any = false;
 #pragma unroll
@@ -712,15 +728,15 @@ __global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const doub
     for (int q = 0; q < 20; ++q) OWN[q * N + c] = 0.0;
     return;
   }
-  double lim[4][3];
+  real lim[4][3];
   for (int f = 0; f < 4; ++f) raw_limit(In, N, c, f, lim[f][0], lim[f][1], lim[f][2]);
   // the faces' revised depths and beds at this state
-  double hsv[4], zsv[4];
+  real hsv[4], zsv[4];
   {
-    RecT<double> r[4];
+    RecT<real> r[4];
     recs_double(p, In, c, r);
     for (int f = 0; f < 4; ++f) {
-      F3T<double> F;
+      F3T<real> F;
       face_rev(p, In, i, j, f, Q, r, F, hsv[f], zsv[f]);
     }
   }
@@ -741,7 +757,7 @@ __global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const doub
     }
     own_terms<Dual<12>>(p, hs, zs, u, v, L);
     for (int q = 0; q < 12; ++q) {
-      double a = 0.0;
+      real a = 0.0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
       OWN[q * N + c] = a;
@@ -749,7 +765,7 @@ __global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const doub
   }
   // pass 2: the faces' h* and z* (face velocities held)
   {
-    RecT<double> r[4];
+    RecT<real> r[4];
     recs_double(p, In, c, r);
     Dual<8> hs[4], zs[4], u[4], v[4], L[9];
     for (int f = 0; f < 4; ++f) {
@@ -760,7 +776,7 @@ __global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const doub
     }
     own_terms<Dual<8>>(p, hs, zs, u, v, L);
     for (int q = 0; q < 8; ++q) {
-      double a = 0.0;
+      real a = 0.0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
       OWN[(12 + q) * N + c] = a;
@@ -777,11 +793,11 @@ __global__ void adj_own_kernel(Prob p, const double* __restrict__ In, const doub
 // Writes the six input adjoints of each side (FL: a, FR: b; the boundary side
 // folded into the own cell) and, for inflow faces, the adjoint of the
 // hydrograph discharge.
-__global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
-                                const double* __restrict__ lam, const unsigned short* __restrict__ mask,
-                                double w, double Q, const double* __restrict__ OWN,
-                                double* __restrict__ FL, double* __restrict__ FR,
-                                double* __restrict__ gq_face) {
+__global__ void adj_face_kernel(Prob p, int dir, const store* __restrict__ In,
+                                const store* __restrict__ lam, const unsigned short* __restrict__ mask,
+                                real w, real Q, const store* __restrict__ OWN,
+                                store* __restrict__ FL, store* __restrict__ FR,
+                                store* __restrict__ gq_face) {
   const long long nfx = (long long)(p.nx + 1) * p.ny, nfy = (long long)p.nx * (p.ny + 1);
   const long long nf = dir == 0 ? nfx : nfy;
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -794,12 +810,12 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
   const bool has_b = dir == 0 ? i < p.nx : j < p.ny;
   const long long cb = (long long)j * p.nx + i;
   const long long ca = dir == 0 ? cb - 1 : cb - p.nx;
-  const double inv = dir == 0 ? p.inv_dx : p.inv_dy;
+  const real inv = dir == 0 ? p.inv_dx : p.inv_dy;
   const int l1 = dir == 0 ? 1 : 2;            // slope mode of the direction
   const int fa = dir == 0 ? 0 : 2, fb = dir == 0 ? 1 : 3;  // the face as seen from a and b
   // adjoints of the outputs: flux (3), a's h* and z*, b's h* and z*
-  double phi[3] = {0.0, 0.0, 0.0}, pha = 0.0, pza = 0.0, phb = 0.0, pzb = 0.0;
-  double mua[9], mub[9];
+  real phi[3] = {0.0, 0.0, 0.0}, pha = 0.0, pza = 0.0, phb = 0.0, pzb = 0.0;
+  real mua[9], mub[9];
   if (has_a) {
     stage_mu(lam, mask, N, ca, w, mua);
     for (int v = 0; v < 3; ++v) phi[v] += -mua[3 * v] * inv - 3.0 * inv * mua[3 * v + l1];
@@ -812,20 +828,20 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
     phb = OWN[(12 + 2 * fb) * N + cb];
     pzb = OWN[(13 + 2 * fb) * N + cb];
   }
-  double la[6] = {0, 0, 0, 0, 0, 0}, lb[6] = {0, 0, 0, 0, 0, 0}, gq = 0.0;
+  real la[6] = {0, 0, 0, 0, 0, 0}, lb[6] = {0, 0, 0, 0, 0, 0}, gq = 0.0;
   const bool any = phi[0] != 0.0 || phi[1] != 0.0 || phi[2] != 0.0 || pha != 0.0 || pza != 0.0 ||
                    phb != 0.0 || pzb != 0.0;
   const bool y = dir == 1;
   if (any && has_a && has_b) {
-    double ha4[4], hb4[4], qa[3], qb[3];
+    real ha4[4], hb4[4], qa[3], qb[3];
     for (int q = 0; q < 4; ++q) {
-      double t1, t2;
+      real t1, t2;
       raw_limit(In, N, ca, q, ha4[q], t1, t2);
       raw_limit(In, N, cb, q, hb4[q], t1, t2);
     }
     raw_limit(In, N, ca, fa, qa[0], qa[1], qa[2]);
     raw_limit(In, N, cb, fb, qb[0], qb[1], qb[2]);
-    const double za0 = p.Z[ca] + p.Z[l1 * N + ca], zb0 = p.Z[cb] - p.Z[l1 * N + cb];
+    const real za0 = p.Z[ca] + p.Z[l1 * N + ca], zb0 = p.Z[cb] - p.Z[l1 * N + cb];
     // two passes of six derivatives: side a's inputs, then side b's
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
@@ -849,7 +865,7 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
       Dual<6> ha, za, hb, zb;
       revise_face_t(Ra, Rb, p.tol, ra, rb, ha, za, hb, zb);
       const F3T<Dual<6>> F = flux_face(ra, rb, y, p.g, p.tol);
-      double* out = side == 0 ? la : lb;
+      real* out = side == 0 ? la : lb;
       for (int k = 0; k < 6; ++k)
         out[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pha * ha.d[k] +
                  pza * za.d[k] + phb * hb.d[k] + pzb * zb.d[k];
@@ -862,12 +878,12 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
     const int cj = inside_b ? j : (dir == 0 ? j : j - 1);
     const int fo = inside_b ? fb : fa;  // own face
     const int edge = dir == 0 ? (inside_b ? 0 : 1) : (inside_b ? 2 : 3);
-    const double s = dir == 0 ? (cj + 0.5) * p.dy : (ci + 0.5) * p.dx;
-    const double pho = inside_b ? phb : pha, pzo = inside_b ? pzb : pza;
+    const real s = dir == 0 ? (cj + 0.5) * p.dy : (ci + 0.5) * p.dx;
+    const real pho = inside_b ? phb : pha, pzo = inside_b ? pzb : pza;
     if (any) {
-      double h4[4], qo[3];
+      real h4[4], qo[3];
       for (int q = 0; q < 4; ++q) {
-        double t1, t2;
+        real t1, t2;
         raw_limit(In, N, c, q, h4[q], t1, t2);
       }
       raw_limit(In, N, c, fo, qo[0], qo[1], qo[2]);
@@ -877,8 +893,8 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
       const Dual<7> h0 = with_value(0.5 * (O[0] + O[1]), In[c]);
       Dual<7> sc;
       const bool pw = pw_scale_t(h0, O[1], O[0], O[3], O[2], p.tol, p.wd, sc);
-      const double sg = (fo == 0 || fo == 2) ? 1.0 : -1.0;
-      const double zf = p.Z[c] + sg * p.Z[l1 * N + c];
+      const real sg = (fo == 0 || fo == 2) ? 1.0 : -1.0;
+      const real zf = p.Z[c] + sg * p.Z[l1 * N + c];
       const RecT<Dual<7>> Ro = make_rec_t(O[fo], oqx, oqy, zf, pw, sc, p.tol, p.wd != 0, h0);
       Dual<7> G[3] = {O[fo], oqx, oqy};
       ghost_t(p, edge, s, Qd, G[0], G[1], G[2]);
@@ -891,7 +907,7 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
       const F3T<Dual<7>> F = flux_face(ra, rb, y, p.g, p.tol);
       const Dual<7>& ho = inside_b ? hb : ha;
       const Dual<7>& zo = inside_b ? zb : za;
-      double lo[6];
+      real lo[6];
       for (int k = 0; k < 6; ++k)
         lo[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pho * ho.d[k] +
                 pzo * zo.d[k];
@@ -915,35 +931,35 @@ __global__ void adj_face_kernel(Prob p, int dir, const double* __restrict__ In,
 // Manning gradient.  The raw limits' adjoints are the own terms' (OWN) plus
 // each of the four faces' for this side.
 template <int STAGE>
-__global__ void adj_cell_kernel(Prob p, const double* __restrict__ OWN,
-                                const double* __restrict__ lam2, const unsigned short* __restrict__ mask2,
-                                const unsigned short* __restrict__ mask1, const double* __restrict__ lamU1,
-                                const double* __restrict__ FXL, const double* __restrict__ FXR,
-                                const double* __restrict__ FYL, const double* __restrict__ FYR,
-                                const double* __restrict__ U, double dt, double* __restrict__ out,
-                                double* __restrict__ gn) {
+__global__ void adj_cell_kernel(Prob p, const store* __restrict__ OWN,
+                                const store* __restrict__ lam2, const unsigned short* __restrict__ mask2,
+                                const unsigned short* __restrict__ mask1, const store* __restrict__ lamU1,
+                                const store* __restrict__ FXL, const store* __restrict__ FXR,
+                                const store* __restrict__ FYL, const store* __restrict__ FYR,
+                                const store* __restrict__ U, real dt, store* __restrict__ out,
+                                store* __restrict__ gn) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const long long N = p.N;
   const int i = (int)(c % p.nx), j = (int)(c / p.nx);
   const long long nfx = (long long)(p.nx + 1) * p.ny, nfy = (long long)p.nx * (p.ny + 1);
-  double lr[4][3];
+  real lr[4][3];
   for (int f = 0; f < 4; ++f)
     for (int k = 0; k < 3; ++k) lr[f][k] = OWN[(3 * f + k) * N + c];
   // faces: this cell is side a of its east and north faces, side b of its west and south
   const long long fe = (long long)j * (p.nx + 1) + i + 1, fw = (long long)j * (p.nx + 1) + i;
   const long long fn = (long long)(j + 1) * p.nx + i, fs = (long long)j * p.nx + i;
-  const double* src[4] = {FXL, FXR, FYL, FYR};
+  const store* src[4] = {FXL, FXR, FYL, FYR};
   const long long fi[4] = {fe, fw, fn, fs};
   const long long fcount[4] = {nfx, nfx, nfy, nfy};
   for (int f = 0; f < 4; ++f) {
-    const double* Fs = src[f];
+    const store* Fs = src[f];
     for (int q = 0; q < 4; ++q) lr[q][0] += Fs[q * fcount[f] + fi[f]];
     lr[f][1] += Fs[4 * fcount[f] + fi[f]];
     lr[f][2] += Fs[5 * fcount[f] + fi[f]];
   }
   // limits -> modes: E = U0 + U1x, W = U0 - U1x, N = U0 + U1y, S = U0 - U1y
-  double a[9];
+  real a[9];
   for (int v = 0; v < 3; ++v) {
     a[3 * v] = lr[0][v] + lr[1][v] + lr[2][v] + lr[3][v];
     a[3 * v + 1] = lr[0][v] - lr[1][v];
@@ -951,7 +967,7 @@ __global__ void adj_cell_kernel(Prob p, const double* __restrict__ OWN,
   }
   // direct RK terms
   const unsigned m2 = mask2[c];
-  double half2[9];
+  real half2[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) half2[k] = ((m2 >> k) & 1u) ? 0.5 * lam2[k * N + c] : 0.0;
   if (STAGE == 2) {
@@ -960,7 +976,7 @@ __global__ void adj_cell_kernel(Prob p, const double* __restrict__ OWN,
     return;
   }
   const unsigned m1 = mask1[c];
-  double ls[9];
+  real ls[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) ls[k] = half2[k] + (((m1 >> k) & 1u) ? lamU1[k * N + c] : 0.0) + a[k];
   // friction: Us = Fric(U; n)
@@ -969,36 +985,34 @@ __global__ void adj_cell_kernel(Prob p, const double* __restrict__ OWN,
   const Dual<10> n = var<10>(p.Nm[c], 9);
   friction_cell<Dual<10>>(m, n, dt, p.g, p.tol, o);
   for (int k = 0; k < 9; ++k) {
-    double s = 0.0;
+    real s = 0.0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) s += ls[q] * o[q].d[k];
     out[k * N + c] = s;
   }
-  double sn = 0.0;
+  real sn = 0.0;
 #pragma unroll
   for (int q = 0; q < 9; ++q) sn += ls[q] * o[q].d[9];
   gn[c] += sn;
 }
 
 // Sum of the inflow faces' discharge adjoints in a fixed order into one slot.
-__global__ void sum_gq_kernel(const double* __restrict__ gq_face, int n, double* __restrict__ slot) {
+__global__ void sum_gq_kernel(const store* __restrict__ gq_face, int n, double* __restrict__ slot) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
   for (int k = 0; k < n; ++k) s += gq_face[k];
   *slot = s;
 }
 
-}  // namespace adj
+}  // namespace DG2_ADJ_NS
 }  // namespace dg2
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
-struct dg2_adj;
-
 namespace dg2 {
-namespace adj {
+namespace DG2_ADJ_NS {
 namespace {
 
 int afail(int code, const char* fmt, ...) {
@@ -1043,9 +1057,9 @@ bool adj_layout(int nx, int ny, int nsnap, int max_gauges, int max_steps, AdjLay
     o = align_up(o + bytes);
     return at;
   };
-  const size_t s9 = (size_t)L.plane9 * sizeof(double);
-  L.off_Z = take(3 * (size_t)L.N * sizeof(double));
-  L.off_Nm = take((size_t)L.N * sizeof(double));
+  const size_t s9 = (size_t)L.plane9 * sizeof(store);
+  L.off_Z = take(3 * (size_t)L.N * sizeof(store));
+  L.off_Nm = take((size_t)L.N * sizeof(store));
   L.off_U0 = take(s9);
   L.off_snap = take((size_t)nsnap * s9);
   L.off_work = take(2 * s9);
@@ -1056,30 +1070,29 @@ bool adj_layout(int nx, int ny, int nsnap, int max_gauges, int max_steps, AdjLay
   L.off_lam = take(s9);
   L.off_lamU1 = take(s9);
   L.off_tmp = take(s9);
-  L.off_own = take(20 * (size_t)L.N * sizeof(double));
-  L.off_FXL = take(6 * (size_t)L.nfx * sizeof(double));
-  L.off_FXR = take(6 * (size_t)L.nfx * sizeof(double));
-  L.off_FYL = take(6 * (size_t)L.nfy * sizeof(double));
-  L.off_FYR = take(6 * (size_t)L.nfy * sizeof(double));
-  L.off_gq_face = take((size_t)L.ngq * sizeof(double));
-  L.off_gn = take((size_t)L.N * sizeof(double));
+  L.off_own = take(20 * (size_t)L.N * sizeof(store));
+  L.off_FXL = take(6 * (size_t)L.nfx * sizeof(store));
+  L.off_FXR = take(6 * (size_t)L.nfx * sizeof(store));
+  L.off_FYL = take(6 * (size_t)L.nfy * sizeof(store));
+  L.off_FYR = take(6 * (size_t)L.nfy * sizeof(store));
+  L.off_gq_face = take((size_t)L.ngq * sizeof(store));
+  L.off_gn = take((size_t)L.N * sizeof(store));
   const size_t ng = max_gauges > 0 ? max_gauges : 1;
   L.off_gidx = take(ng * sizeof(long long));
-  L.off_gxi = take(ng * sizeof(double));
-  L.off_geta = take(ng * sizeof(double));
-  L.off_gh = take(ng * sizeof(double));
+  L.off_gxi = take(ng * sizeof(store));
+  L.off_geta = take(ng * sizeof(store));
+  L.off_gh = take(ng * sizeof(store));
   L.off_gq_step = take(2 * (size_t)max_steps * sizeof(double));
   L.total = o;
   return true;
 }
 
 }  // namespace
-}  // namespace adj
-}  // namespace dg2
 
-struct dg2_adj {
-  dg2::adj::Prob p;
-  dg2::adj::AdjLayout lay;
+// An adjoint problem of this precision (the C ABI's dg2_adj wraps one).
+struct Ctx {
+  Prob p;
+  AdjLayout lay;
   char* ws;
   cudaStream_t st;
   int max_gauges, max_steps;
@@ -1096,14 +1109,33 @@ struct dg2_adj {
   int64_t fwd_steps, rev_steps;
 };
 
-namespace dg2 {
-namespace adj {
 namespace {
 
-double* dptr(dg2_adj* a, size_t off) { return (double*)(a->ws + off); }
-double* snap(dg2_adj* a, int s) { return dptr(a, a->lay.off_snap) + (size_t)s * a->lay.plane9; }
+// Host FP64 values to device storage (converted on the host when it is FP32).
+int upload(const double* src, size_t n, store* dst, cudaStream_t st) {
+  if (sizeof(store) == sizeof(double)) {
+    ACU(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    return cudaStreamSynchronize(st) == cudaSuccess ? DG2_OK : afail(DG2_E_CUDA, "copy failed");
+  }
+  std::vector<store> tmp(src, src + n);
+  ACU(cudaMemcpyAsync(dst, tmp.data(), n * sizeof(store), cudaMemcpyHostToDevice, st));
+  ACU(cudaStreamSynchronize(st));
+  return DG2_OK;
+}
 
-double hydro(const dg2_adj* a, double t) {
+// Device storage to host FP64 values (synchronises the stream).
+int download(const store* src, size_t n, double* dst, cudaStream_t st) {
+  std::vector<store> tmp(n);
+  ACU(cudaMemcpyAsync(tmp.data(), src, n * sizeof(store), cudaMemcpyDeviceToHost, st));
+  ACU(cudaStreamSynchronize(st));
+  for (size_t k = 0; k < n; ++k) dst[k] = (double)tmp[k];
+  return DG2_OK;
+}
+
+store* dptr(Ctx* a, size_t off) { return (store*)(a->ws + off); }
+store* snap(Ctx* a, int s) { return dptr(a, a->lay.off_snap) + (size_t)s * a->lay.plane9; }
+
+double hydro(const Ctx* a, double t) {
   const std::vector<double>& tk = a->tk;
   const std::vector<double>& qk = a->qk;
   if (tk.empty()) return 0.0;
@@ -1117,7 +1149,7 @@ double hydro(const dg2_adj* a, double t) {
 }
 
 // dQ(t)/dq_k added into g with weight s
-void hydro_grad(const dg2_adj* a, double t, double s, double* g) {
+void hydro_grad(const Ctx* a, double t, double s, double* g) {
   const std::vector<double>& tk = a->tk;
   if (tk.empty()) return;
   if (t <= tk[0]) { g[0] += s; return; }
@@ -1131,7 +1163,7 @@ void hydro_grad(const dg2_adj* a, double t, double s, double* g) {
   g[tk.size() - 1] += s;
 }
 
-double step_time(const dg2_adj* a, int k) {
+double step_time(const Ctx* a, int k) {
   // t_k = t0 + dt_0 + ... + dt_{k-1}, summed in step order as the forward does
   double t = a->t0;
   for (int q = 0; q < k; ++q) t += a->dts[q];
@@ -1147,10 +1179,10 @@ int launch_ok() {
 unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
 // One forward step k from Uin to Uout (Us, U1, masks left in the workspace).
-int fwd_step(dg2_adj* a, int k, double t, const double* Uin, double* Uout) {
+int fwd_step(Ctx* a, int k, double t, const store* Uin, store* Uout) {
   const double dt = a->dts[k];
-  double* Us = dptr(a, a->lay.off_Us);
-  double* U1 = dptr(a, a->lay.off_U1);
+  store* Us = dptr(a, a->lay.off_Us);
+  store* U1 = dptr(a, a->lay.off_U1);
   unsigned short* m1 = (unsigned short*)(a->ws + a->lay.off_m1);
   unsigned short* m2 = (unsigned short*)(a->ws + a->lay.off_m2);
   const unsigned nb = blocks(a->lay.N);
@@ -1162,10 +1194,10 @@ int fwd_step(dg2_adj* a, int k, double t, const double* Uin, double* Uout) {
 }
 
 // Advances `buf` (the state after `from` steps) to the state after `to` steps.
-int advance(dg2_adj* a, double* buf, int from, int to) {
-  double* w = dptr(a, a->lay.off_work);
+int advance(Ctx* a, store* buf, int from, int to) {
+  store* w = dptr(a, a->lay.off_work);
   double t = step_time(a, from);
-  const size_t s9 = (size_t)a->lay.plane9 * sizeof(double);
+  const size_t s9 = (size_t)a->lay.plane9 * sizeof(store);
   for (int k = from; k < to; ++k) {
     int r = fwd_step(a, k, t, buf, w);
     if (r) return r;
@@ -1177,32 +1209,32 @@ int advance(dg2_adj* a, double* buf, int from, int to) {
 
 // Reverse of step k from state Uk: lam (adjoint of the state after step k)
 // becomes the adjoint of Uk; Manning gradient and discharge adjoints added.
-int rev_step(dg2_adj* a, int k, const double* Uk) {
+int rev_step(Ctx* a, int k, const store* Uk) {
   const AdjLayout& L = a->lay;
   const double dt = a->dts[k];
   const double t = step_time(a, k);
-  double* Us = dptr(a, L.off_Us);
-  double* U1 = dptr(a, L.off_U1);
-  double* w = dptr(a, L.off_work);
+  store* Us = dptr(a, L.off_Us);
+  store* U1 = dptr(a, L.off_U1);
+  store* w = dptr(a, L.off_work);
   unsigned short* m1 = (unsigned short*)(a->ws + L.off_m1);
   unsigned short* m2 = (unsigned short*)(a->ws + L.off_m2);
   int r = fwd_step(a, k, t, Uk, w);  // Us, U1, masks of this step
   if (r) return r;
   a->fwd_steps--;                     // counted as part of the reverse step
-  double* lam = dptr(a, L.off_lam);
-  double* lamU1 = dptr(a, L.off_lamU1);
-  double* tmp = dptr(a, L.off_tmp);
-  double* OWN = dptr(a, L.off_own);
-  double* FXL = dptr(a, L.off_FXL);
-  double* FXR = dptr(a, L.off_FXR);
-  double* FYL = dptr(a, L.off_FYL);
-  double* FYR = dptr(a, L.off_FYR);
-  double* gqf = dptr(a, L.off_gq_face);
-  double* gn = dptr(a, L.off_gn);
-  double* gqs = dptr(a, L.off_gq_step);
+  store* lam = dptr(a, L.off_lam);
+  store* lamU1 = dptr(a, L.off_lamU1);
+  store* tmp = dptr(a, L.off_tmp);
+  store* OWN = dptr(a, L.off_own);
+  store* FXL = dptr(a, L.off_FXL);
+  store* FXR = dptr(a, L.off_FXR);
+  store* FYL = dptr(a, L.off_FYL);
+  store* FYR = dptr(a, L.off_FYR);
+  store* gqf = dptr(a, L.off_gq_face);
+  store* gn = dptr(a, L.off_gn);
+  double* gqs = (double*)(a->ws + L.off_gq_step);
   const unsigned nb = blocks(L.N);
   // stage 2 at U1, time t + dt: mu2 = dt/2 mask2 lam
-  ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(double), a->st));
+  ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(store), a->st));
   adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, U1, lam, m2, 0.5 * dt, hydro(a, t + dt), OWN);
   adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
                                                     OWN, FXL, FXR, gqf);
@@ -1212,7 +1244,7 @@ int rev_step(dg2_adj* a, int k, const double* Uk) {
   adj_cell_kernel<2><<<nb, 256, 0, a->st>>>(a->p, OWN, lam, m2, m1, nullptr, FXL, FXR, FYL, FYR,
                                             nullptr, dt, lamU1, gn);
   // stage 1 at Us, time t: mu1 = dt mask1 lamU1
-  ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(double), a->st));
+  ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(store), a->st));
   adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, Us, lamU1, m1, dt, hydro(a, t), OWN);
   adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, Us, lamU1, m1, dt, hydro(a, t), OWN, FXL,
                                                     FXR, gqf);
@@ -1221,29 +1253,29 @@ int rev_step(dg2_adj* a, int k, const double* Uk) {
   sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k);
   adj_cell_kernel<1><<<nb, 256, 0, a->st>>>(a->p, OWN, lam, m2, m1, lamU1, FXL, FXR, FYL, FYR, Uk,
                                             dt, tmp, gn);
-  ACU(cudaMemcpyAsync(lam, tmp, (size_t)L.plane9 * sizeof(double), cudaMemcpyDeviceToDevice, a->st));
+  ACU(cudaMemcpyAsync(lam, tmp, (size_t)L.plane9 * sizeof(store), cudaMemcpyDeviceToDevice, a->st));
   a->rev_steps++;
   return launch_ok();
 }
 
 // Adds dJ/dU of the samples taken after `k` steps into lam.
-int seed_samples(dg2_adj* a, int k) {
+int seed_samples(Ctx* a, int k) {
   const AdjLayout& L = a->lay;
   const int ns = (int)a->samp_step.size();
   for (int s = 0; s < ns; ++s) {
     if (a->samp_step[s] != k) continue;
-    double* gh = dptr(a, L.off_gh);
-    ACU(cudaMemcpyAsync(gh, a->gauge_h.data() + (size_t)s * a->ngauge, a->ngauge * sizeof(double),
-                        cudaMemcpyHostToDevice, a->st));
+    store* gh = dptr(a, L.off_gh);
+    int r = upload(a->gauge_h.data() + (size_t)s * a->ngauge, a->ngauge, gh, a->st);
+    if (r) return r;
     // observed depths staged behind the gauge depths in the same small buffer is
     // not possible (max_gauges slots); stage them in the tmp plane instead
-    double* ob = dptr(a, L.off_tmp);
-    ACU(cudaMemcpyAsync(ob, a->obs.data() + (size_t)s * a->ngauge, a->ngauge * sizeof(double),
-                        cudaMemcpyHostToDevice, a->st));
+    store* ob = dptr(a, L.off_tmp);
+    r = upload(a->obs.data() + (size_t)s * a->ngauge, a->ngauge, ob, a->st);
+    if (r) return r;
     gauge_seed_kernel<<<1, 32, 0, a->st>>>(dptr(a, L.off_lam), L.N, a->ngauge,
                                            (const long long*)(a->ws + L.off_gidx), dptr(a, L.off_gxi),
                                            dptr(a, L.off_geta), gh, ob);
-    int r = launch_ok();
+    r = launch_ok();
     if (r) return r;
   }
   return DG2_OK;
@@ -1257,8 +1289,8 @@ double binom(int c, int r) {
   return b;
 }
 
-int reverse_range(dg2_adj* a, int s, int e, int slot, int free) {
-  const size_t s9 = (size_t)a->lay.plane9 * sizeof(double);
+int reverse_range(Ctx* a, int s, int e, int slot, int free) {
+  const size_t s9 = (size_t)a->lay.plane9 * sizeof(store);
   if (e - s == 1) {
     int r = rev_step(a, s, snap(a, slot));
     if (r) return r;
@@ -1266,7 +1298,7 @@ int reverse_range(dg2_adj* a, int s, int e, int slot, int free) {
   }
   if (free == 0) {
     // no slot left: recompute from s for each step
-    double* w2 = dptr(a, a->lay.off_work) + a->lay.plane9;
+    store* w2 = dptr(a, a->lay.off_work) + a->lay.plane9;
     for (int k = e - 1; k >= s; --k) {
       ACU(cudaMemcpyAsync(w2, snap(a, slot), s9, cudaMemcpyDeviceToDevice, a->st));
       int r = advance(a, w2, s, k);
@@ -1292,7 +1324,7 @@ int reverse_range(dg2_adj* a, int s, int e, int slot, int free) {
   return r;
 }
 
-int check_adj(dg2_adj* a) {
+int check_adj(Ctx* a) {
   if (!a) return afail(DG2_E_ARG, "null adjoint context");
   if (!a->have_state) return afail(DG2_E_STATE, "dg2_adj_set_problem first");
   if (!a->have_schedule) return afail(DG2_E_STATE, "dg2_adj_set_schedule first");
@@ -1301,26 +1333,26 @@ int check_adj(dg2_adj* a) {
 
 // Forward over all steps from U0; gauge depths of every sample to the host;
 // returns J.
-int forward_all(dg2_adj* a, double* loss) {
+int forward_all(Ctx* a, double* loss) {
   const AdjLayout& L = a->lay;
   const int K = (int)a->dts.size();
-  const size_t s9 = (size_t)L.plane9 * sizeof(double);
-  double* cur = snap(a, 0);
+  const size_t s9 = (size_t)L.plane9 * sizeof(store);
+  store* cur = snap(a, 0);
   ACU(cudaMemcpyAsync(cur, dptr(a, L.off_U0), s9, cudaMemcpyDeviceToDevice, a->st));
   const int ns = (int)a->samp_step.size();
   a->gauge_h.assign((size_t)ns * a->ngauge, 0.0);
-  double* w = dptr(a, L.off_work);
+  store* w = dptr(a, L.off_work);
   double t = a->t0;
   auto sample = [&](int k) -> int {
     for (int s = 0; s < ns; ++s) {
       if (a->samp_step[s] != k) continue;
-      double* gh = dptr(a, L.off_gh);
+      store* gh = dptr(a, L.off_gh);
       gauge_kernel<<<1, 256, 0, a->st>>>(cur, L.N, a->ngauge, (const long long*)(a->ws + L.off_gidx),
                                          dptr(a, L.off_gxi), dptr(a, L.off_geta), gh);
       int r = launch_ok();
       if (r) return r;
-      ACU(cudaMemcpyAsync(a->gauge_h.data() + (size_t)s * a->ngauge, gh, a->ngauge * sizeof(double),
-                          cudaMemcpyDeviceToHost, a->st));
+      r = download(gh, a->ngauge, a->gauge_h.data() + (size_t)s * a->ngauge, a->st);
+      if (r) return r;
     }
     return DG2_OK;
   };
@@ -1347,41 +1379,25 @@ int forward_all(dg2_adj* a, double* loss) {
 }
 
 }  // namespace
-}  // namespace adj
-}  // namespace dg2
 
-using dg2::adj::AdjLayout;
-using dg2::adj::Prob;
-using dg2::adj::adj_layout;
-using dg2::adj::afail;
-using dg2::adj::check_adj;
-using dg2::adj::dptr;
-using dg2::adj::forward_all;
-using dg2::adj::hydro_grad;
-using dg2::adj::kAlign;
-using dg2::adj::kMaxKnotsAdj;
-using dg2::adj::reverse_range;
-using dg2::adj::seed_samples;
-using dg2::adj::snap;
+// The entry points of this precision (the C ABI dispatches to them).
 
-extern "C" {
 
-size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps) {
+size_t workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps) {
   AdjLayout L;
   if (!adj_layout(nx, ny, nsnap, max_gauges, max_steps, L)) return 0;
   return L.total;
 }
 
-int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg2_params* prm,
-                   int nsnap, int max_gauges, int max_steps, void* dev_workspace, size_t ws_bytes,
-                   void* cuda_stream) {
+int create(Ctx** out, int nx, int ny, double dx, double dy, const dg2_params* prm, int nsnap,
+           int max_gauges, int max_steps, void* dev_workspace, size_t ws_bytes, void* cuda_stream) {
   if (!out) return afail(DG2_E_ARG, "out is null");
   *out = nullptr;
   if (!prm) return afail(DG2_E_ARG, "params is null");
-  if (prm->variant != DG2_NL || prm->precision != DG2_FP64 || prm->flux != DG2_HLL ||
+  if (prm->variant != DG2_NL || prm->flux != DG2_HLL ||
       prm->scheme != DG2_SCHEME_DG2 ||
       (prm->wetdry != DG2_WD_POSITIVE && prm->wetdry != DG2_WD_PRINTED))
-    return afail(DG2_E_ARG, "the adjoint is of the FP64 DG2-NL step with the HLL flux");
+    return afail(DG2_E_ARG, "the adjoint is of the DG2-NL step with the HLL flux");
   if (!(dx > 0.0) || !(dy > 0.0)) return afail(DG2_E_ARG, "dx, dy must be > 0");
   AdjLayout L;
   if (!adj_layout(nx, ny, nsnap, max_gauges, max_steps, L))
@@ -1389,7 +1405,7 @@ int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg
   if (!dev_workspace || ((uintptr_t)dev_workspace % kAlign))
     return afail(DG2_E_ARG, "workspace must be non-null and 256-byte aligned");
   if (ws_bytes < L.total) return afail(DG2_E_NOMEM, "workspace too small: %zu < %zu", ws_bytes, L.total);
-  dg2_adj* a = new dg2_adj();
+  Ctx* a = new Ctx();
   a->lay = L;
   a->ws = (char*)dev_workspace;
   a->st = (cudaStream_t)cuda_stream;
@@ -1413,10 +1429,9 @@ int dg2_adj_create(dg2_adj** out, int nx, int ny, double dx, double dy, const dg
   return DG2_OK;
 }
 
-int dg2_adj_set_problem(dg2_adj* a, const double* z3, const double* state9, double t0,
-                        const double* manning, int inflow_edge, double s0, double len,
-                        const double* t_knots, const double* q_knots, int nknots,
-                        const double* gauge_xy, int ngauge) {
+int set_problem(Ctx* a, const double* z3, const double* state9, double t0, const double* manning,
+                int inflow_edge, double s0, double len, const double* t_knots,
+                const double* q_knots, int nknots, const double* gauge_xy, int ngauge) {
   if (!a) return afail(DG2_E_ARG, "null adjoint context");
   if (!z3 || !state9 || !manning) return afail(DG2_E_ARG, "z3, state9 and manning are required");
   if (ngauge < 0 || ngauge > a->max_gauges) return afail(DG2_E_ARG, "ngauge must be 0..%d", a->max_gauges);
@@ -1430,9 +1445,10 @@ int dg2_adj_set_problem(dg2_adj* a, const double* z3, const double* state9, doub
   const AdjLayout& L = a->lay;
   Prob& p = a->p;
   const size_t N = (size_t)L.N;
-  ACU(cudaMemcpyAsync(dptr(a, L.off_Z), z3, 3 * N * sizeof(double), cudaMemcpyHostToDevice, a->st));
-  ACU(cudaMemcpyAsync(dptr(a, L.off_U0), state9, 9 * N * sizeof(double), cudaMemcpyHostToDevice, a->st));
-  ACU(cudaMemcpyAsync(dptr(a, L.off_Nm), manning, N * sizeof(double), cudaMemcpyHostToDevice, a->st));
+  int r = upload(z3, 3 * N, dptr(a, L.off_Z), a->st);
+  if (!r) r = upload(state9, 9 * N, dptr(a, L.off_U0), a->st);
+  if (!r) r = upload(manning, N, dptr(a, L.off_Nm), a->st);
+  if (r) return r;
   a->t0 = t0;
   p.in_edge = inflow_edge;
   a->tk.clear();
@@ -1465,8 +1481,8 @@ int dg2_adj_set_problem(dg2_adj* a, const double* z3, const double* state9, doub
   }
   if (ngauge > 0) {
     ACU(cudaMemcpyAsync(a->ws + L.off_gidx, gi.data(), ngauge * sizeof(long long), cudaMemcpyHostToDevice, a->st));
-    ACU(cudaMemcpyAsync(a->ws + L.off_gxi, gx.data(), ngauge * sizeof(double), cudaMemcpyHostToDevice, a->st));
-    ACU(cudaMemcpyAsync(a->ws + L.off_geta, ge.data(), ngauge * sizeof(double), cudaMemcpyHostToDevice, a->st));
+    if ((r = upload(gx.data(), ngauge, dptr(a, L.off_gxi), a->st))) return r;
+    if ((r = upload(ge.data(), ngauge, dptr(a, L.off_geta), a->st))) return r;
   }
   ACU(cudaStreamSynchronize(a->st));
   a->ngauge = ngauge;
@@ -1474,18 +1490,19 @@ int dg2_adj_set_problem(dg2_adj* a, const double* z3, const double* state9, doub
   return DG2_OK;
 }
 
-int dg2_adj_set_params(dg2_adj* a, const double* manning, const double* q_knots) {
+int set_params(Ctx* a, const double* manning, const double* q_knots) {
   if (!a || !a->have_state) return afail(DG2_E_STATE, "dg2_adj_set_problem first");
-  if (manning)
-    ACU(cudaMemcpyAsync(dptr(a, a->lay.off_Nm), manning, (size_t)a->lay.N * sizeof(double),
-                        cudaMemcpyHostToDevice, a->st));
+  if (manning) {
+    const int r = upload(manning, (size_t)a->lay.N, dptr(a, a->lay.off_Nm), a->st);
+    if (r) return r;
+  }
   if (q_knots) a->qk.assign(q_knots, q_knots + a->qk.size());
   ACU(cudaStreamSynchronize(a->st));
   return DG2_OK;
 }
 
-int dg2_adj_set_schedule(dg2_adj* a, const double* dts, int nsteps, const int* sample_steps,
-                         int nsamples, const double* obs) {
+int set_schedule(Ctx* a, const double* dts, int nsteps, const int* sample_steps, int nsamples,
+                 const double* obs) {
   if (!a || !a->have_state) return afail(DG2_E_STATE, "dg2_adj_set_problem first");
   if (!dts || nsteps < 1 || nsteps > a->max_steps)
     return afail(DG2_E_ARG, "need 1..%d step sizes", a->max_steps);
@@ -1503,7 +1520,7 @@ int dg2_adj_set_schedule(dg2_adj* a, const double* dts, int nsteps, const int* s
   return DG2_OK;
 }
 
-int dg2_adj_forward(dg2_adj* a, double* loss, double* gauge_h) {
+int forward(Ctx* a, double* loss, double* gauge_h) {
   int r = check_adj(a);
   if (r) return r;
   double J;
@@ -1513,26 +1530,25 @@ int dg2_adj_forward(dg2_adj* a, double* loss, double* gauge_h) {
   return DG2_OK;
 }
 
-int dg2_adj_gradient(dg2_adj* a, double* loss, double* grad_manning, double* grad_q) {
+int gradient(Ctx* a, double* loss, double* grad_manning, double* grad_q) {
   int r = check_adj(a);
   if (r) return r;
   const AdjLayout& L = a->lay;
   const int K = (int)a->dts.size();
   double J;
   if ((r = forward_all(a, &J))) return r;
-  ACU(cudaMemsetAsync(dptr(a, L.off_lam), 0, (size_t)L.plane9 * sizeof(double), a->st));
-  ACU(cudaMemsetAsync(dptr(a, L.off_gn), 0, (size_t)L.N * sizeof(double), a->st));
-  ACU(cudaMemsetAsync(dptr(a, L.off_gq_step), 0, 2 * (size_t)K * sizeof(double), a->st));
+  ACU(cudaMemsetAsync(dptr(a, L.off_lam), 0, (size_t)L.plane9 * sizeof(store), a->st));
+  ACU(cudaMemsetAsync(dptr(a, L.off_gn), 0, (size_t)L.N * sizeof(store), a->st));
+  ACU(cudaMemsetAsync(a->ws + L.off_gq_step, 0, 2 * (size_t)K * sizeof(double), a->st));
   if ((r = seed_samples(a, K))) return r;
   // snapshot 0 holds U0 again (forward_all advanced it in place)
-  ACU(cudaMemcpyAsync(snap(a, 0), dptr(a, L.off_U0), (size_t)L.plane9 * sizeof(double),
+  ACU(cudaMemcpyAsync(snap(a, 0), dptr(a, L.off_U0), (size_t)L.plane9 * sizeof(store),
                       cudaMemcpyDeviceToDevice, a->st));
   if ((r = reverse_range(a, 0, K, 0, L.nsnap - 1))) return r;
-  if (grad_manning)
-    ACU(cudaMemcpyAsync(grad_manning, dptr(a, L.off_gn), (size_t)L.N * sizeof(double),
-                        cudaMemcpyDeviceToHost, a->st));
+  if (grad_manning && (r = download(dptr(a, L.off_gn), (size_t)L.N, grad_manning, a->st)))
+    return r;
   std::vector<double> gqs(2 * (size_t)K);
-  ACU(cudaMemcpyAsync(gqs.data(), dptr(a, L.off_gq_step), gqs.size() * sizeof(double),
+  ACU(cudaMemcpyAsync(gqs.data(), a->ws + L.off_gq_step, gqs.size() * sizeof(double),
                       cudaMemcpyDeviceToHost, a->st));
   ACU(cudaStreamSynchronize(a->st));
   if (grad_q) {
@@ -1549,17 +1565,18 @@ int dg2_adj_gradient(dg2_adj* a, double* loss, double* grad_manning, double* gra
   return DG2_OK;
 }
 
-int dg2_adj_counts(const dg2_adj* a, int64_t* forward_steps, int64_t* reverse_steps) {
+int counts(const Ctx* a, int64_t* forward_steps, int64_t* reverse_steps) {
   if (!a) return afail(DG2_E_ARG, "null adjoint context");
   if (forward_steps) *forward_steps = a->fwd_steps;
   if (reverse_steps) *reverse_steps = a->rev_steps;
   return DG2_OK;
 }
 
-int dg2_adj_destroy(dg2_adj* a) {
+int destroy(Ctx* a) {
   if (!a) return afail(DG2_E_ARG, "null adjoint context");
   delete a;
   return DG2_OK;
 }
 
-}  // extern "C"
+}  // namespace DG2_ADJ_NS
+}  // namespace dg2
