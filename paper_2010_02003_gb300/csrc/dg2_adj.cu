@@ -52,7 +52,10 @@ namespace DG2_ADJ_NS {
 // is compiled once for each).  Kernels load stored values into FP64 registers and
 // round their results to the storage type; the hydrograph, the step times, the
 // per-step discharge adjoint sums and the misfit stay FP64.
-using real = double;
+#ifndef DG2_ADJ_ARITH
+#define DG2_ADJ_ARITH double
+#endif
+using real = DG2_ADJ_ARITH;
 using store = DG2_ADJ_STORE;
 
 // ---------------------------------------------------------------------------

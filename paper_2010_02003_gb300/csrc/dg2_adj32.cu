@@ -9,4 +9,9 @@
 // checkpointed states, so twice the snapshots fit.
 #define DG2_ADJ_STORE float
 #define DG2_ADJ_NS adj32
+// arithmetic type of this build (FP64; DG2_ADJ32_ARITH=float builds the all-FP32
+// variant the design notes measure)
+#ifdef DG2_ADJ32_ARITH
+#define DG2_ADJ_ARITH DG2_ADJ32_ARITH
+#endif
 #include "dg2_adj.cu"

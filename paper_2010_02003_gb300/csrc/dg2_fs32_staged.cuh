@@ -20,8 +20,9 @@
 // the values their own tile computes), and stage 2, which needs the
 // post-friction U^n for the RK average, recomputes it for its own cells (the
 // averages only in DG2-LL, whose slopes of U^n stage 1 keeps in Q).  Both
-// evaluate the same function with explicit roundings, so the two agree bit for
-// bit.  The state's planes are thus read and written once per stage, with no
+// evaluate the same function (explicit roundings inside it; the depths it is
+// given are formed alike), so stage 2 averages the U^n stage 1 stepped from.
+// The state's planes are thus read and written once per stage, with no
 // friction round trip through HBM.
 #pragma once
 #include "dg2_fs32.cuh"
