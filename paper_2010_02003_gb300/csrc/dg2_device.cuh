@@ -653,56 +653,77 @@ __device__ __forceinline__ void friction_point(double gn2dt, double tol, double 
   qy = qy * iden;
 }
 
-// Friction on the cells of one 32 x 8 tile (threads 32 x 8).
-__device__ __forceinline__ void friction_tile(const Dev& d, int bx, int by) {
+// Friction on the cells of one 32 x 8 tile (threads 32 x 8).  A quiescent cell
+// (every Gauss-point depth at h0 <= tol_dry, Un's qm bit clear) has no water to
+// rub, and neither has a cell without roughness: the others are gathered and
+// handed to the first threads, so the FP64 arithmetic runs on full warps.
+// `cells` is shared memory for the tile's list, `cnt` for the per-warp counts.
+__device__ __forceinline__ void friction_tile(const Dev& d, int bx, int by, unsigned short* cells,
+                                              int* cnt) {
   const Scalars* sc = d.sc;
+  const int t = threadIdx.y * TX + threadIdx.x, w = t >> 5, lane = t & 31;
   int tx, ty;
   warp_cell(tx, ty);
-  const int i = bx * TX + tx;
-  const int j = by * TY + ty;
-  if (i >= d.nx || j >= d.ny) return;
-  // a quiescent cell (every Gauss-point depth at h0 <= tol_dry) has no water
-  // to rub: a warp block of them (Un's qm word zero) is left as it is
-  if (d.qm && d.tiles.skip && d.scheme == 0 &&
-      d.qm[(long long)(by * TBY + ty / WY) * d.nbx + bx * TBX + tx / WX] == 0u)
-    return;
-  const long long P = d.plane, c = (long long)j * d.pitch + i;
-  const double n = d.N[c];
-  if (n == 0.0) return;
-  const double dt = sc->dt;
-  const double gn2dt = dt * d.g * n * n;
-  double* S = d.S;
-  const double h0 = S[H0 * P + c], x0 = S[QX0 * P + c], y0 = S[QY0 * P + c];
-  double cx = x0, cy = y0;
-  friction_point(gn2dt, d.tol, h0, cx, cy);
-  const double r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
-  double nq[2][2];
+  const int i = bx * TX + tx, j = by * TY + ty;
+  const long long P = d.plane;
+  bool work = i < d.nx && j < d.ny;
+  if (work && d.qm && d.tiles.skip && d.scheme == 0)
+    work = (d.qm[(long long)(by * TBY + ty / WY) * d.nbx + bx * TBX + tx / WX] >> lane) & 1u;
+  if (work) work = d.N[(long long)j * d.pitch + i] != 0.0;
+  const unsigned bw = __ballot_sync(0xffffffffu, work);
+  if (lane == 0) cnt[w] = __popc(bw);
+  __syncthreads();
+  int before = 0, total = 0;
 #pragma unroll
-  for (int dd = 1; dd <= 2; ++dd) {
-    const double h1 = S[dd * P + c], x1 = S[(3 + dd) * P + c], y1 = S[(6 + dd) * P + c];
-    double xp = x0 + x1 * r3, yp = y0 + y1 * r3, xm = x0 - x1 * r3, ym = y0 - y1 * r3;
-    friction_point(gn2dt, d.tol, h0 + h1 * r3, xp, yp);
-    friction_point(gn2dt, d.tol, h0 - h1 * r3, xm, ym);
-    nq[dd - 1][0] = hs3 * (xp - xm);
-    nq[dd - 1][1] = hs3 * (yp - ym);
+  for (int k = 0; k < TX * TY / 32; ++k) {
+    before += k < w ? cnt[k] : 0;
+    total += cnt[k];
   }
-  S[QX0 * P + c] = cx;
-  S[QY0 * P + c] = cy;
-  S[QX1X * P + c] = nq[0][0];
-  S[QY1X * P + c] = nq[0][1];
-  S[QX1Y * P + c] = nq[1][0];
-  S[QY1Y * P + c] = nq[1][1];
+  if (work) cells[before + __popc(bw & ((1u << lane) - 1u))] = (unsigned short)(ty * TX + tx);
+  __syncthreads();
+  if (t < total) {
+    const int me = cells[t];
+    const int ci = bx * TX + me % TX, cj = by * TY + me / TX;
+    const long long c = (long long)cj * d.pitch + ci;
+    const double n = d.N[c];
+    const double dt = sc->dt;
+    const double gn2dt = dt * d.g * n * n;
+    double* S = d.S;
+    const double h0 = S[H0 * P + c], x0 = S[QX0 * P + c], y0 = S[QY0 * P + c];
+    double cx = x0, cy = y0;
+    friction_point(gn2dt, d.tol, h0, cx, cy);
+    const double r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
+    double nq[2][2];
+#pragma unroll
+    for (int dd = 1; dd <= 2; ++dd) {
+      const double h1 = S[dd * P + c], x1 = S[(3 + dd) * P + c], y1 = S[(6 + dd) * P + c];
+      double xp = x0 + x1 * r3, yp = y0 + y1 * r3, xm = x0 - x1 * r3, ym = y0 - y1 * r3;
+      friction_point(gn2dt, d.tol, h0 + h1 * r3, xp, yp);
+      friction_point(gn2dt, d.tol, h0 - h1 * r3, xm, ym);
+      nq[dd - 1][0] = hs3 * (xp - xm);
+      nq[dd - 1][1] = hs3 * (yp - ym);
+    }
+    S[QX0 * P + c] = cx;
+    S[QY0 * P + c] = cy;
+    S[QX1X * P + c] = nq[0][0];
+    S[QY1X * P + c] = nq[0][1];
+    S[QX1Y * P + c] = nq[1][0];
+    S[QY1Y * P + c] = nq[1][1];
+  }
+  __syncthreads();  // the list is reused by the block's next tile
 }
 
 // Friction over the step's computed tiles (a quiescent tile has no water to rub).
 static __global__ void __launch_bounds__(256) friction_kernel(Dev d) {
+  __shared__ unsigned short cells[TX * TY];
+  __shared__ int cnt[TX * TY / 32];
   const Scalars* sc = d.sc;
   if (sc->done) return;
   const int n_act = sc->n_act, ntx = d.tiles.ntx;
   const bool all = sc->list_all != 0;
   for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
     const int tile = all ? e : d.tiles.list[e];
-    friction_tile(d, tile % ntx, tile / ntx);
+    friction_tile(d, tile % ntx, tile / ntx, cells, cnt);
   }
 }
 
