@@ -999,12 +999,24 @@ __global__ void adj_cell_kernel(Prob p, const store* __restrict__ OWN,
   gn[c] += sn;
 }
 
-// Sum of the inflow faces' discharge adjoints in a fixed order into one slot.
-__global__ void sum_gq_kernel(const store* __restrict__ gq_face, int n, double* __restrict__ slot) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Sum of the inflow faces' discharge adjoints in a fixed order into one slot:
+// one block of kSumThreads threads, thread r summing entries r, r + kSumThreads,
+// ... in turn, then a fixed pairwise tree over the threads (the same order on
+// every call, so the gradient does not depend on scheduling).
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) sum_gq_kernel(const store* __restrict__ gq_face,
+                                                             int n, double* __restrict__ slot) {
+  __shared__ double part[kSumThreads];
+  const int r = threadIdx.x;
   double s = 0.0;
-  for (int k = 0; k < n; ++k) s += gq_face[k];
-  *slot = s;
+  for (int k = r; k < n; k += kSumThreads) s += gq_face[k];
+  part[r] = s;
+  __syncthreads();
+  for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+    if (r < w) part[r] += part[r + w];
+    __syncthreads();
+  }
+  if (r == 0) *slot = part[0];
 }
 
 }  // namespace DG2_ADJ_NS
@@ -1243,7 +1255,7 @@ int rev_step(Ctx* a, int k, const store* Uk) {
                                                     OWN, FXL, FXR, gqf);
   adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
                                                     OWN, FYL, FYR, gqf);
-  sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k + 1);
+  sum_gq_kernel<<<1, kSumThreads, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k + 1);
   adj_cell_kernel<2><<<nb, 256, 0, a->st>>>(a->p, OWN, lam, m2, m1, nullptr, FXL, FXR, FYL, FYR,
                                             nullptr, dt, lamU1, gn);
   // stage 1 at Us, time t: mu1 = dt mask1 lamU1
@@ -1253,7 +1265,7 @@ int rev_step(Ctx* a, int k, const store* Uk) {
                                                     FXR, gqf);
   adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, Us, lamU1, m1, dt, hydro(a, t), OWN, FYL,
                                                     FYR, gqf);
-  sum_gq_kernel<<<1, 32, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k);
+  sum_gq_kernel<<<1, kSumThreads, 0, a->st>>>(gqf, L.ngq, gqs + 2 * (size_t)k);
   adj_cell_kernel<1><<<nb, 256, 0, a->st>>>(a->p, OWN, lam, m2, m1, lamU1, FXL, FXR, FYL, FYR, Uk,
                                             dt, tmp, gn);
   ACU(cudaMemcpyAsync(lam, tmp, (size_t)L.plane9 * sizeof(store), cudaMemcpyDeviceToDevice, a->st));
