@@ -22,7 +22,13 @@
 
 namespace dg2 {
 
-constexpr int TX = 32;
+// FP64 tile of TX x TY cells.  Measured on GB300 with the weight-class lists
+// (floodplain 2000 x 1000 from t = 1 h, ms per step, 32 -> 16 wide): DG2-LL
+// 0.421 -> 0.422, DG2-NL 0.345 -> 0.335; 32 x 8 is kept.
+#ifndef DG2_TX64
+#define DG2_TX64 32
+#endif
+constexpr int TX = DG2_TX64;
 constexpr int TY = 8;
 
 // A warp of the FP64 tile kernels covers a WX x WY block of cells (lane l:
@@ -53,6 +59,16 @@ struct InflowDesc {
   double width;    // nfaces * face length
 };
 
+// The step's list of computed tiles is kept in kListClasses weight classes, by
+// the count of non-quiescent cells of each tile when the list is built
+// (heaviest class first), so the blocks of long tiles start first and short
+// ones fill the end of a stage.  The order of the entries does not change the
+// result (lists_kernel).
+#ifndef DG2_LIST_CLASSES
+#define DG2_LIST_CLASSES 8
+#endif
+constexpr int kListClasses = DG2_LIST_CLASSES;
+
 // Device-resident scalars of a context (one per context, in the workspace).
 struct Scalars {
   double t;            // simulated time
@@ -75,6 +91,7 @@ struct Scalars {
   long long steps;     // completed steps (count of stage-2 finalisations)
   double last_dt;      // size of the last completed step
   int n_act;           // tiles computed in the current step (entries of tiles.list)
+  int n_b[kListClasses];  // of these, the entries of each weight class
   int n_front;         // frontier tiles copied in stage 1 (entries of tiles.front)
   int list_all;        // every tile is computed: list entry e is tile e
   int skip_lists;      // the step was not taken (run already done): keep the lists
@@ -109,12 +126,24 @@ struct Tiles {
   unsigned char* flag;          // [ntiles] tile held a non-quiescent cell after the last stage 2
   unsigned char* act;           // [ntiles] tile computed in the current step
   const unsigned char* forced;  // [ntiles] tile must be computed (inflow, source); set on the host
-  int* list;                    // [ntiles] computed tiles of the step, ascending
+  int* list;                    // [kListClasses * ntiles] computed tiles of the step, by weight class
   int* front;                   // [ntiles] frontier tiles of the step (stage-1 copy), ascending
   int ntx, nty, ntiles;         // tile grid
   int all_forced;               // every tile must be computed (rain)
   int skip;                     // 0: compute every tile
 };
+
+// Tile of entry e of the step's list: the weight classes' entries in turn.
+template <class S>
+__device__ __forceinline__ int list_tile(const Tiles& T, const S* sc, int e) {
+  int k = 0;
+  for (; k < kListClasses - 1; ++k) {
+    const int n = sc->n_b[k];
+    if (e < n) break;
+    e -= n;
+  }
+  return T.list[k * T.ntiles + e];
+}
 
 struct Dev {
   // grid
@@ -714,7 +743,7 @@ __device__ __forceinline__ void friction_tile(const Dev& d, int bx, int by, unsi
 }
 
 // Friction over the step's computed tiles (a quiescent tile has no water to rub).
-static __global__ void __launch_bounds__(256) friction_kernel(Dev d) {
+static __global__ void __launch_bounds__(TX * TY) friction_kernel(Dev d) {
   __shared__ unsigned short cells[TX * TY];
   __shared__ int cnt[TX * TY / 32];
   const Scalars* sc = d.sc;
@@ -722,7 +751,7 @@ static __global__ void __launch_bounds__(256) friction_kernel(Dev d) {
   const int n_act = sc->n_act, ntx = d.tiles.ntx;
   const bool all = sc->list_all != 0;
   for (int e = blockIdx.x; e < n_act; e += gridDim.x) {
-    const int tile = all ? e : d.tiles.list[e];
+    const int tile = all ? e : list_tile(d.tiles, sc, e);
     friction_tile(d, tile % ntx, tile / ntx, cells, cnt);
   }
 }
@@ -1297,7 +1326,7 @@ static __global__ void __launch_bounds__(TX* TY, LL ? DG2_MINB64_LL : DG2_MINB64
   if (STAGE == 2 && (int)blockIdx.x >= n_act) return;
   for (int e = blockIdx.x; e < n_act; e = n_act) {
 #endif
-    const int tile = all ? e : d.tiles.list[e];
+    const int tile = all ? e : list_tile(d.tiles, sc, e);
     const int bx = tile % ntx, by = tile / ntx;
     double brate = 0.0, lam_t = 0.0;
     bool nonq = false;
@@ -1387,7 +1416,7 @@ static __global__ void __launch_bounds__(LTX* LTY) lists_kernel(D d) {
     return;
   }
   __shared__ unsigned char busy[LTY + 4][LTX + 4];
-  __shared__ int wa[LTY], wf[LTY], base[2];
+  __shared__ int wa[LTY][kListClasses], wf[LTY], base[kListClasses + 1];
   for (int k = tid; k < (LTY + 4) * (LTX + 4); k += LTX * LTY) {
     const int ly = k / (LTX + 4), lx = k % (LTX + 4);
     const int gx = blockIdx.x * LTX + lx - 2, gy = blockIdx.y * LTY + ly - 2;
@@ -1412,25 +1441,54 @@ static __global__ void __launch_bounds__(LTX* LTY) lists_kernel(D d) {
     if (a) f = false;
     T.act[t] = a ? 1 : 0;
   }
-  // warp = one row of LTX tiles: ballot prefix in the warp, warp offsets, one atomic
-  const unsigned ba = __ballot_sync(0xffffffffu, a), bf = __ballot_sync(0xffffffffu, f);
+  // weight class of a computed tile: its count of non-quiescent cells (the DG2
+  // cell masks of the new state) in kListClasses equal parts of the tile, the
+  // fullest part first
+  int cls = kListClasses - 1;
+  if (a && d.qm && d.scheme == 0) {
+    int nq = 0;
+    for (int yy = 0; yy < TBY; ++yy)
+      for (int xx = 0; xx < TBX; ++xx)
+        nq += __popc(d.qm[(long long)(by * TBY + yy) * d.nbx + bx * TBX + xx]);
+    cls = kListClasses - 1 - nq * kListClasses / (TX * TY + 1);
+  }
+  // warp = one row of LTX tiles: ballot prefix in the warp, warp offsets, one
+  // atomic per class
   const int lane = tid & 31;
-  if (lane == 0) { wa[ty] = __popc(ba); wf[ty] = __popc(bf); }
-  __syncthreads();
-  if (tid == 0) {
-    int sa = 0, sf = 0;
-    for (int w = 0; w < LTY; ++w) {
-      const int xa = wa[w], xf = wf[w];
-      wa[w] = sa; sa += xa;
-      wf[w] = sf; sf += xf;
-    }
-    base[0] = sa ? atomicAdd(&sc->n_act, sa) : 0;
-    base[1] = sf ? atomicAdd(&sc->n_front, sf) : 0;
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned bf = __ballot_sync(0xffffffffu, f);
+  unsigned bk[kListClasses];
+#pragma unroll
+  for (int k = 0; k < kListClasses; ++k) bk[k] = __ballot_sync(0xffffffffu, a && cls == k);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kListClasses; ++k) wa[ty][k] = __popc(bk[k]);
+    wf[ty] = __popc(bf);
   }
   __syncthreads();
-  const unsigned below = (1u << lane) - 1u;
-  if (a) T.list[base[0] + wa[ty] + __popc(ba & below)] = t;
-  if (f) T.front[base[1] + wf[ty] + __popc(bf & below)] = t;
+  if (tid == 0) {
+    int sall = 0, sf = 0;
+    for (int k = 0; k < kListClasses; ++k) {
+      int sa = 0;
+      for (int w = 0; w < LTY; ++w) {
+        const int xa = wa[w][k];
+        wa[w][k] = sa;
+        sa += xa;
+      }
+      base[k] = sa ? atomicAdd(&sc->n_b[k], sa) : 0;
+      sall += sa;
+    }
+    for (int w = 0; w < LTY; ++w) {
+      const int xf = wf[w];
+      wf[w] = sf;
+      sf += xf;
+    }
+    if (sall) atomicAdd(&sc->n_act, sall);
+    base[kListClasses] = sf ? atomicAdd(&sc->n_front, sf) : 0;
+  }
+  __syncthreads();
+  if (a) T.list[cls * T.ntiles + base[cls] + wa[ty][cls] + __popc(bk[cls] & below)] = t;
+  if (f) T.front[base[kListClasses] + wf[ty] + __popc(bf & below)] = t;
 }
 
 // Resets the list counters for lists_kernel (thread 0 of the finalize block).
@@ -1439,6 +1497,7 @@ __device__ __forceinline__ void open_lists(Scalars* sc) {
   sc->n_front = 0;
   sc->list_all = 0;
   sc->skip_lists = 0;
+  for (int k = 0; k < kListClasses; ++k) sc->n_b[k] = 0;
 }
 
 // Sum over the boundary ring of tiles, in a fixed order, of the per-tile

@@ -291,7 +291,7 @@ static __global__ void __launch_bounds__(TX* TY, 2) fv_stage_kernel(Dev d) {
   bool bad = false;
   if (STAGE == 2 && (int)blockIdx.x >= n_act) return;
   if ((int)blockIdx.x < n_act) {
-    const int tile = all ? (int)blockIdx.x : d.tiles.list[blockIdx.x];
+    const int tile = all ? (int)blockIdx.x : list_tile(d.tiles, sc, (int)blockIdx.x);
     const int bx = tile % ntx, by = tile / ntx;
     double brate = 0.0;
     bool nonq = false;
@@ -337,7 +337,7 @@ static __global__ void __launch_bounds__(TX* TY) fv1_commit_kernel(Dev d) {
   const int n_act = sc->n_act;
   if ((int)blockIdx.x >= n_act) return;
   const int ntx = d.tiles.ntx;
-  const int tile = sc->list_all ? (int)blockIdx.x : d.tiles.list[blockIdx.x];
+  const int tile = sc->list_all ? (int)blockIdx.x : list_tile(d.tiles, sc, (int)blockIdx.x);
   const int i = (tile % ntx) * TX + threadIdx.x, j = (tile / ntx) * TY + threadIdx.y;
   if (i >= d.nx || j >= d.ny) return;
   const long long P = d.plane, c = (long long)j * d.pitch + i;

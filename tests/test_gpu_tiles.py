@@ -97,7 +97,7 @@ def test_tile_lists_match_host_classification():
         s.step(-1.0)
         _, na1, nf1, done1 = s.tile_stats()
         assert done1 - done0 == na                # the step computed the listed tiles
-        exp, ntiles = _expected_active(s.state())
+        exp, ntiles = _expected_active(s.state(), tx=s.tile_shape()[0], ty=s.tile_shape()[1])
         assert ntiles == nt and na1 == exp, (k, na1, exp)
         assert 0 < na1 < nt and na1 + nf1 <= nt
         total += na
@@ -111,7 +111,8 @@ def test_tile_stats_without_skipping_and_all_dry():
     for _ in range(3):
         s.step(-1.0)
     nt, na, nf, done = s.tile_stats()
-    assert nt == 4 * 7 and na == nt and nf == 0 and done == 3 * nt
+    tw, th = s.tile_shape()
+    assert nt == -(-100 // tw) * -(-50 // th) and na == nt and nf == 0 and done == 3 * nt
     dry = inputs.hump(nx=100, ny=50, eta=-1.0)
     s2 = B.solver_from_case(dry)
     for _ in range(3):
