@@ -787,6 +787,20 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
   }
 }
 
+// Record of one side of a face from the side's four depth limits (E, W, N, S),
+// its discharge limits (qx, qy) at the face and its cell-mean depth h0v, over
+// face bed zf; fo is the face as the side sees it.  The mean depth carries the
+// derivative of (hE + hW) / 2 (with_value).
+template <class T>
+__device__ __forceinline__ RecT<T> side_rec(const Prob& p, const T* h4, const T& qx, const T& qy,
+                                            real h0v, int fo, real zf) {
+  const T h0 = with_value(0.5 * (h4[0] + h4[1]), h0v);
+  T sc;
+  const bool pw = pw_scale_t(h0, h4[1], h4[0], h4[3], h4[2], p.tol, p.wd, sc);
+  const T& hf = fo == 0 ? h4[0] : fo == 1 ? h4[1] : fo == 2 ? h4[2] : h4[3];
+  return make_rec_t(hf, qx, qy, zf, pw, sc, p.tol, p.wd != 0, h0);
+}
+
 // One pass over the faces of a stage: face (left/lower cell a, right/upper cell
 // b) of direction dir (0 x, 1 y); index f runs over (nx+1) * ny x-faces or
 // nx * (ny+1) y-faces.  The face's outputs are its flux (adjoint phi from both
@@ -845,33 +859,41 @@ __global__ void adj_face_kernel(Prob p, int dir, const store* __restrict__ In,
     raw_limit(In, N, ca, fa, qa[0], qa[1], qa[2]);
     raw_limit(In, N, cb, fb, qb[0], qb[1], qb[2]);
     const real za0 = p.Z[ca] + p.Z[l1 * N + ca], zb0 = p.Z[cb] - p.Z[l1 * N + cb];
-    // two passes of six derivatives: side a's inputs, then side b's
+    // The face's outputs depend on the inputs only through each side's record
+    // (h, u, v, hs; its bed and partially wet flag are constants of the state).
+    // Their adjoint is taken back to the eight record fields in one pass of
+    // eight derivatives over the revision and flux, then to each side's six
+    // inputs in a pass of six derivatives over that side's record alone.
+    const RecT<real> Ra = side_rec(p, ha4, qa[1], qa[2], In[ca], fa, za0);
+    const RecT<real> Rb = side_rec(p, hb4, qb[1], qb[2], In[cb], fb, zb0);
+    real grec[8];
+    {
+      RecT<Dual<8>> Da, Db;
+      Da.h = var<8>(Ra.h, 0); Da.u = var<8>(Ra.u, 1); Da.v = var<8>(Ra.v, 2);
+      Da.hs = var<8>(Ra.hs, 3); Da.zf = Ra.zf; Da.pw = Ra.pw;
+      Db.h = var<8>(Rb.h, 4); Db.u = var<8>(Rb.u, 5); Db.v = var<8>(Rb.v, 6);
+      Db.hs = var<8>(Rb.hs, 7); Db.zf = Rb.zf; Db.pw = Rb.pw;
+      LimT<Dual<8>> ra, rb;
+      Dual<8> ha, za, hb, zb;
+      revise_face_t(Da, Db, p.tol, ra, rb, ha, za, hb, zb);
+      const F3T<Dual<8>> F = flux_face(ra, rb, y, p.g, p.tol);
+      for (int k = 0; k < 8; ++k)
+        grec[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pha * ha.d[k] +
+                  pza * za.d[k] + phb * hb.d[k] + pzb * zb.d[k];
+    }
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
-      Dual<6> A[4], Bv[4], aqx, aqy, bqx, bqy;
-      for (int q = 0; q < 4; ++q) {
-        A[q] = side == 0 ? var<6>(ha4[q], q) : cst<6>(ha4[q]);
-        Bv[q] = side == 1 ? var<6>(hb4[q], q) : cst<6>(hb4[q]);
-      }
-      aqx = side == 0 ? var<6>(qa[1], 4) : cst<6>(qa[1]);
-      aqy = side == 0 ? var<6>(qa[2], 5) : cst<6>(qa[2]);
-      bqx = side == 1 ? var<6>(qb[1], 4) : cst<6>(qb[1]);
-      bqy = side == 1 ? var<6>(qb[2], 5) : cst<6>(qb[2]);
-      const Dual<6> h0a = with_value(0.5 * (A[0] + A[1]), In[ca]);
-      const Dual<6> h0b = with_value(0.5 * (Bv[0] + Bv[1]), In[cb]);
-      Dual<6> sca, scb;
-      const bool pwa = pw_scale_t(h0a, A[1], A[0], A[3], A[2], p.tol, p.wd, sca);
-      const bool pwb = pw_scale_t(h0b, Bv[1], Bv[0], Bv[3], Bv[2], p.tol, p.wd, scb);
-      const RecT<Dual<6>> Ra = make_rec_t(A[fa], aqx, aqy, za0, pwa, sca, p.tol, p.wd != 0, h0a);
-      const RecT<Dual<6>> Rb = make_rec_t(Bv[fb], bqx, bqy, zb0, pwb, scb, p.tol, p.wd != 0, h0b);
-      LimT<Dual<6>> ra, rb;
-      Dual<6> ha, za, hb, zb;
-      revise_face_t(Ra, Rb, p.tol, ra, rb, ha, za, hb, zb);
-      const F3T<Dual<6>> F = flux_face(ra, rb, y, p.g, p.tol);
+      const real* h4 = side == 0 ? ha4 : hb4;
+      const real* q3 = side == 0 ? qa : qb;
+      Dual<6> D4[4];
+      for (int q = 0; q < 4; ++q) D4[q] = var<6>(h4[q], q);
+      const RecT<Dual<6>> R = side_rec(p, D4, var<6>(q3[1], 4), var<6>(q3[2], 5),
+                                       In[side == 0 ? ca : cb], side == 0 ? fa : fb,
+                                       side == 0 ? za0 : zb0);
+      const real* gr = grec + 4 * side;
       real* out = side == 0 ? la : lb;
       for (int k = 0; k < 6; ++k)
-        out[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pha * ha.d[k] +
-                 pza * za.d[k] + phb * hb.d[k] + pzb * zb.d[k];
+        out[k] = gr[0] * R.h.d[k] + gr[1] * R.u.d[k] + gr[2] * R.v.d[k] + gr[3] * R.hs.d[k];
     }
   } else if (!(has_a && has_b)) {
     // boundary face: the outside state is the ghost of the inside cell's limit
@@ -890,32 +912,40 @@ __global__ void adj_face_kernel(Prob p, int dir, const store* __restrict__ In,
         raw_limit(In, N, c, q, h4[q], t1, t2);
       }
       raw_limit(In, N, c, fo, qo[0], qo[1], qo[2]);
-      Dual<7> O[4];
-      for (int q = 0; q < 4; ++q) O[q] = var<7>(h4[q], q);
-      const Dual<7> oqx = var<7>(qo[1], 4), oqy = var<7>(qo[2], 5), Qd = var<7>(Q, 6);
-      const Dual<7> h0 = with_value(0.5 * (O[0] + O[1]), In[c]);
-      Dual<7> sc;
-      const bool pw = pw_scale_t(h0, O[1], O[0], O[3], O[2], p.tol, p.wd, sc);
+      // seven inputs (the four depth limits, qx, qy, the discharge Q) in three
+      // passes of three derivatives: boundary faces are few, and narrow duals
+      // keep the kernel's registers for the interior faces
       const real sg = (fo == 0 || fo == 2) ? 1.0 : -1.0;
       const real zf = p.Z[c] + sg * p.Z[l1 * N + c];
-      const RecT<Dual<7>> Ro = make_rec_t(O[fo], oqx, oqy, zf, pw, sc, p.tol, p.wd != 0, h0);
-      Dual<7> G[3] = {O[fo], oqx, oqy};
-      ghost_t(p, edge, s, Qd, G[0], G[1], G[2]);
-      const RecT<Dual<7>> Rg = make_rec_t(G[0], G[1], G[2], zf, false, h0 - h0 + 1.0, p.tol, false,
-                                          h0);
-      LimT<Dual<7>> ra, rb;
-      Dual<7> ha, za, hb, zb;
-      if (inside_b) revise_face_t(Rg, Ro, p.tol, ra, rb, ha, za, hb, zb);
-      else revise_face_t(Ro, Rg, p.tol, ra, rb, ha, za, hb, zb);
-      const F3T<Dual<7>> F = flux_face(ra, rb, y, p.g, p.tol);
-      const Dual<7>& ho = inside_b ? hb : ha;
-      const Dual<7>& zo = inside_b ? zb : za;
-      real lo[6];
-      for (int k = 0; k < 6; ++k)
-        lo[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pho * ho.d[k] +
-                pzo * zo.d[k];
-      gq = phi[0] * F.h.d[6] + phi[1] * F.x.d[6] + phi[2] * F.y.d[6] + pho * ho.d[6] + pzo * zo.d[6];
-      for (int k = 0; k < 6; ++k) { if (inside_b) lb[k] = lo[k]; else la[k] = lo[k]; }
+      real lo7[9];
+#pragma unroll 1
+      for (int l0 = 0; l0 < 9; l0 += 3) {
+        auto seed = [l0](real x, int input) {
+          return input >= l0 && input < l0 + 3 ? var<3>(x, input - l0) : cst<3>(x);
+        };
+        Dual<3> O[4];
+        for (int q = 0; q < 4; ++q) O[q] = seed(h4[q], q);
+        const Dual<3> Qd = seed(Q, 6);
+        const RecT<Dual<3>> Ro = side_rec(p, O, seed(qo[1], 4), seed(qo[2], 5), In[c], fo, zf);
+        Dual<3> G[3] = {fo == 0 ? O[0] : fo == 1 ? O[1] : fo == 2 ? O[2] : O[3], seed(qo[1], 4),
+                        seed(qo[2], 5)};
+        ghost_t(p, edge, s, Qd, G[0], G[1], G[2]);
+        const Dual<3> h0 = with_value(0.5 * (O[0] + O[1]), In[c]);
+        const RecT<Dual<3>> Rg = make_rec_t(G[0], G[1], G[2], zf, false, h0 - h0 + 1.0, p.tol,
+                                            false, h0);
+        LimT<Dual<3>> ra, rb;
+        Dual<3> ha, za, hb, zb;
+        if (inside_b) revise_face_t(Rg, Ro, p.tol, ra, rb, ha, za, hb, zb);
+        else revise_face_t(Ro, Rg, p.tol, ra, rb, ha, za, hb, zb);
+        const F3T<Dual<3>> F = flux_face(ra, rb, y, p.g, p.tol);
+        const Dual<3>& ho = inside_b ? hb : ha;
+        const Dual<3>& zo = inside_b ? zb : za;
+        for (int k = 0; k < 3; ++k)
+          lo7[l0 + k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] +
+                        pho * ho.d[k] + pzo * zo.d[k];
+      }
+      gq = lo7[6];
+      for (int k = 0; k < 6; ++k) { if (inside_b) lb[k] = lo7[k]; else la[k] = lo7[k]; }
     }
     // fold into the edge slot index: along-edge position
     const int pos = dir == 0 ? cj : ci;
