@@ -734,48 +734,60 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
   real lim[4][3];
   for (int f = 0; f < 4; ++f) raw_limit(In, N, c, f, lim[f][0], lim[f][1], lim[f][2]);
   // the faces' revised depths and beds at this state
-  real hsv[4], zsv[4];
+  real hsv[4], zsv[4], ru[4], rv[4];
   {
     RecT<real> r[4];
     recs_double(p, In, c, r);
     for (int f = 0; f < 4; ++f) {
       F3T<real> F;
       face_rev(p, In, i, j, f, Q, r, F, hsv[f], zsv[f]);
+      ru[f] = r[f].u;
+      rv[f] = r[f].v;
     }
   }
-  // pass 1: the 12 raw limits (h*, z* held)
+  // pass 1: the 12 raw limits (h*, z* held).  The own terms depend on them only
+  // through the four face velocities (u, v): their adjoint is taken back to the
+  // eight velocities in a pass of eight derivatives over the own terms, then to
+  // the raw limits in a pass of twelve over the records alone.
   {
+    real guv[8];
+    {
+      Dual<8> hs[4], zs[4], u[4], v[4], L[9];
+      for (int f = 0; f < 4; ++f) {
+        hs[f] = cst<8>(hsv[f]);
+        zs[f] = cst<8>(zsv[f]);
+        u[f] = var<8>(ru[f], f);
+        v[f] = var<8>(rv[f], 4 + f);
+      }
+      own_terms<Dual<8>>(p, hs, zs, u, v, L);
+      for (int q = 0; q < 8; ++q) {
+        real a = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
+        guv[q] = a;
+      }
+    }
     Dual<12> dl[4][3];
     for (int f = 0; f < 4; ++f)
       for (int k = 0; k < 3; ++k) dl[f][k] = var<12>(lim[f][k], 3 * f + k);
     const Dual<12> h0 = with_value(0.5 * (dl[0][0] + dl[1][0]), In[c]);
-    RecT<Dual<12>> r[4];
-    cell_recs_t<Dual<12>>(p, c, dl[0], dl[1], dl[2], dl[3], h0, r);
-    Dual<12> hs[4], zs[4], u[4], v[4], L[9];
-    for (int f = 0; f < 4; ++f) {
-      hs[f] = cst<12>(hsv[f]);
-      zs[f] = cst<12>(zsv[f]);
-      u[f] = r[f].u;
-      v[f] = r[f].v;
-    }
-    own_terms<Dual<12>>(p, hs, zs, u, v, L);
+    RecT<Dual<12>> rd[4];
+    cell_recs_t<Dual<12>>(p, c, dl[0], dl[1], dl[2], dl[3], h0, rd);
     for (int q = 0; q < 12; ++q) {
       real a = 0.0;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
+      for (int f = 0; f < 4; ++f) a += guv[f] * rd[f].u.d[q] + guv[4 + f] * rd[f].v.d[q];
       OWN[q * N + c] = a;
     }
   }
   // pass 2: the faces' h* and z* (face velocities held)
   {
-    RecT<real> r[4];
-    recs_double(p, In, c, r);
     Dual<8> hs[4], zs[4], u[4], v[4], L[9];
     for (int f = 0; f < 4; ++f) {
       hs[f] = var<8>(hsv[f], 2 * f);
       zs[f] = var<8>(zsv[f], 2 * f + 1);
-      u[f] = cst<8>(r[f].u);
-      v[f] = cst<8>(r[f].v);
+      u[f] = cst<8>(ru[f]);
+      v[f] = cst<8>(rv[f]);
     }
     own_terms<Dual<8>>(p, hs, zs, u, v, L);
     for (int q = 0; q < 8; ++q) {
