@@ -507,6 +507,20 @@ __device__ __forceinline__ void recs_double(const Prob& p, const store* __restri
   cell_recs_t<real>(p, c, E, W, Nn, S, U[c], r);
 }
 
+// Record of one side of a face from the side's four depth limits (E, W, N, S),
+// its discharge limits (qx, qy) at the face and its cell-mean depth h0v, over
+// face bed zf; fo is the face as the side sees it.  The mean depth carries the
+// derivative of (hE + hW) / 2 (with_value).
+template <class T>
+__device__ __forceinline__ RecT<T> side_rec(const Prob& p, const T* h4, const T& qx, const T& qy,
+                                            real h0v, int fo, real zf) {
+  const T h0 = with_value(0.5 * (h4[0] + h4[1]), h0v);
+  T sc;
+  const bool pw = pw_scale_t(h0, h4[1], h4[0], h4[3], h4[2], p.tol, p.wd, sc);
+  const T& hf = fo == 0 ? h4[0] : fo == 1 ? h4[1] : fo == 2 ? h4[2] : h4[3];
+  return make_rec_t(hf, qx, qy, zf, pw, sc, p.tol, p.wd != 0, h0);
+}
+
 // Face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at stage time
 // with hydrograph discharge Q, in real: its flux and the own side's revised
 // depth and bed level.
@@ -524,10 +538,21 @@ __device__ void face_rev(const Prob& p, const store* __restrict__ U, int i, int 
     ghost_t<real>(p, e, s, Q, h, qx, qy);
     oth = make_rec_t<real>(h, qx, qy, own[f].zf, false, 1.0, p.tol, false, 0.0);
   } else {
+    // the neighbour's record of this face alone (its four depth limits set
+    // its partially wet scale)
     const long long cn = f == 0 ? c + 1 : f == 1 ? c - 1 : f == 2 ? c + p.nx : c - p.nx;
-    RecT<real> nr[4];
-    recs_double(p, U, cn, nr);
-    oth = nr[f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2];
+    const int fn = f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 3 : 2;
+    const int m = fn <= 1 ? 1 : 2;
+    const real sg = (fn == 0 || fn == 2) ? 1.0 : -1.0;
+    const real u0 = U[cn], u1x = U[N + cn], u1y = U[2 * N + cn];  // in real, as raw_limit
+    real h4[4];
+    h4[0] = u0 + u1x;
+    h4[1] = u0 - u1x;
+    h4[2] = u0 + u1y;
+    h4[3] = u0 - u1y;
+    const real qx = U[3 * N + cn] + sg * U[(3 + m) * N + cn];
+    const real qy = U[6 * N + cn] + sg * U[(6 + m) * N + cn];
+    oth = side_rec<real>(p, h4, qx, qy, U[cn], fn, p.Z[cn] + sg * p.Z[m * N + cn]);
   }
   LimT<real> ra, rb;
   real ha, za, hb, zb;
@@ -797,20 +822,6 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
       OWN[(12 + q) * N + c] = a;
     }
   }
-}
-
-// Record of one side of a face from the side's four depth limits (E, W, N, S),
-// its discharge limits (qx, qy) at the face and its cell-mean depth h0v, over
-// face bed zf; fo is the face as the side sees it.  The mean depth carries the
-// derivative of (hE + hW) / 2 (with_value).
-template <class T>
-__device__ __forceinline__ RecT<T> side_rec(const Prob& p, const T* h4, const T& qx, const T& qy,
-                                            real h0v, int fo, real zf) {
-  const T h0 = with_value(0.5 * (h4[0] + h4[1]), h0v);
-  T sc;
-  const bool pw = pw_scale_t(h0, h4[1], h4[0], h4[3], h4[2], p.tol, p.wd, sc);
-  const T& hf = fo == 0 ? h4[0] : fo == 1 ? h4[1] : fo == 2 ? h4[2] : h4[3];
-  return make_rec_t(hf, qx, qy, zf, pw, sc, p.tol, p.wd != 0, h0);
 }
 
 // One pass over the faces of a stage: face (left/lower cell a, right/upper cell
