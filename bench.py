@@ -60,11 +60,11 @@ FLOPS_PER_WET_CELL = {"friction": 111, "stage1": {"nl": 403, "ll": 486},
 # was taken with: the key is a hash of paper_2010_02003_gb300/csrc, and the
 # roofline's traffic is null once those sources change.
 TRAFFIC = {
-    ("fp64_ll", "stage2"): (22_282_240, "ac7b8db0bf6b054e",
+    ("fp64_ll", "stage2"): (19_467_264, "33e655ba3b13e412",
                             "profiles/stage_kernel_fp64_ll_floodplain2000x1000_t3600.md"),
-    ("fp32_ll", "stage2"): (21_041_152, "ac7b8db0bf6b054e",
+    ("fp32_ll", "stage2"): (22_740_992, "33e655ba3b13e412",
                             "profiles/ens_stage_kernel_fp32_ll_floodplain2000x1000_t3600.md"),
-    ("fp32_nl_flooded", "stage2"): (223_492_352, "ac7b8db0bf6b054e",
+    ("fp32_nl_flooded", "stage2"): (232_666_624, "33e655ba3b13e412",
                                     "profiles/ens_stage_kernel_fp32_nl_flooded2000x1000.md"),
 }
 # FP64 issue rate of GB300 by ncu's peak_sustained (2 DFMA per SM per cycle), used only
