@@ -41,12 +41,13 @@ BYTES_PER_CELL = {
     "fp64": {"friction": 16 * 8, "stage1": {"nl": 21 * 8, "ll": 27 * 8},
              "stage2": {"nl": 30 * 8, "ll": 30 * 8}},
     # FP32 free-surface form: 10 state planes (eta0 as hi + lo), 2 face-topography planes,
-    # Manning n; friction is fused into the stages (stage 1 applies it to the U^n it reads,
-    # stage 2 recomputes it for the RK average from U^n and n), so it moves no bytes of its own.
-    # Stage 1 reads U^n, the beds and n and writes U1 (+ the limited slopes Q in DG2-LL);
-    # stage 2 reads U1, U^n (DG2-LL: its averages and Q), the beds and n and writes U^n+1.
-    "fp32": {"friction": 0, "stage1": {"nl": (10 + 2 + 1 + 10) * 4, "ll": (10 + 2 + 1 + 16) * 4},
-             "stage2": {"nl": (10 + 10 + 1 + 2 + 10) * 4, "ll": (10 + 4 + 6 + 1 + 2 + 10) * 4}},
+    # Manning n; friction is fused into the stages (stage 1 applies it to the U^n it reads),
+    # so it moves no bytes of its own.  Stage 1 reads U^n, the beds and n and writes U1 and
+    # Q (DG2-LL: the limited slopes; DG2-NL: U^n's discharge modes after friction); stage 2
+    # reads U1, the beds, U^n's depth planes and Q (DG2-LL also U^n's average discharges and
+    # n, whose friction it recomputes) and writes U^n+1.
+    "fp32": {"friction": 0, "stage1": {"nl": (10 + 2 + 1 + 16) * 4, "ll": (10 + 2 + 1 + 16) * 4},
+             "stage2": {"nl": (10 + 4 + 6 + 2 + 10) * 4, "ll": (10 + 4 + 6 + 1 + 2 + 10) * 4}},
 }
 KERNELS = ["friction", "stage1", "stage2"]
 # Algorithmic FP64 operations per wet cell (add, mul, div, sqrt, cbrt each one), each

@@ -85,7 +85,7 @@ bool make_layout(int nx, int ny, const dg2_params& p, Layout& L) {
   const size_t nplanes = f32 ? dg2::f32::kPlanes32 : 9;
   L.off_S = take(nplanes * pb);
   L.off_T = take(nplanes * pb > staging ? nplanes * pb : staging);
-  L.off_Q = take(p.variant == DG2_LL ? 6 * pb : 0);
+  L.off_Q = take(p.variant == DG2_LL || f32 ? 6 * pb : 0);
   L.off_Z = take(f32 ? 0 : 3 * pb);
   L.off_ZX = take(f32 ? (size_t)ny * L.zpx * sizeof(float) : 0);
   L.off_ZY = take(f32 ? (size_t)(ny + 1) * L.pitch * sizeof(float) : 0);
@@ -520,7 +520,7 @@ int dg2_init_grid(dg2_ctx** out, int nx, int ny, double dx, double dy, const dg2
     f.knot_t = d.knot_t; f.knot_q = d.knot_q;
     f.S = (float*)(c->ws + L.off_S);
     f.T = (float*)(c->ws + L.off_T);
-    f.Q = p.variant == DG2_LL ? (float*)(c->ws + L.off_Q) : nullptr;
+    f.Q = (float*)(c->ws + L.off_Q);
     f.ZX = (const float*)(c->ws + L.off_ZX);
     f.ZY = (const float*)(c->ws + L.off_ZY);
     f.N = (const float*)(c->ws + L.off_N);

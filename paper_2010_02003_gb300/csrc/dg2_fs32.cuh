@@ -53,7 +53,8 @@ struct __align__(16) D32 {
   long long src_idx;
   float* S;            // 10 planes: eta0 eta1x eta1y qx0 qx1x qx1y qy0 qy1x qy1y, eta0 lo
   float* T;            // 10 planes: stage state
-  float* Q;            // 6 planes: limited slopes of Un (DG2-LL)
+  float* Q;            // 6 planes written by stage 1 for stage 2: DG2-LL the limited slopes
+                       // of Un, DG2-NL Un's discharge modes after friction
   const float* ZX;     // z at x-faces: face i of row j at ZX[j * zpx + i], i = 0..nx
   const float* ZY;     // z at y-faces: face j of column i at ZY[j * pitch + i], j = 0..ny
   const float* N;      // Manning n

@@ -17,13 +17,13 @@
 // applied here instead of in a pass of its own: stage 1 applies it to every
 // staged cell in shared memory before anything else reads them (a cell's
 // friction depends on that cell alone, so the halo cells of a tile get exactly
-// the values their own tile computes), and stage 2, which needs the
-// post-friction U^n for the RK average, recomputes it for its own cells (the
-// averages only in DG2-LL, whose slopes of U^n stage 1 keeps in Q).  Both
-// evaluate the same function (explicit roundings inside it; the depths it is
-// given are formed alike), so stage 2 averages the U^n stage 1 stepped from.
-// The state's planes are thus read and written once per stage, with no
-// friction round trip through HBM.
+// the values their own tile computes).  Stage 2 needs the post-friction U^n
+// for the RK average: in DG2-NL stage 1 stores its own cells' six discharge
+// modes after friction in Q (stage 2 reads them in place of U^n's, so it
+// evaluates no friction); in DG2-LL, whose Q holds the limited slopes of U^n,
+// stage 2 recomputes the averages' friction (the same function with explicit
+// roundings inside it, on depths formed alike), so stage 2 averages the U^n
+// stage 1 stepped from.
 #pragma once
 #include "dg2_fs32.cuh"
 
@@ -63,9 +63,10 @@ struct Geo32 {
   static constexpr int PL = SR * SP;             // floats per staged plane
 };
 
-// Planes of U^n a stage-2 tile stages for its own cells: DG2-NL all ten (the
-// full friction is recomputed), DG2-LL eta0 hi / lo, qx0, qy0 and the six
-// limited slopes stage 1 left in Q; plus the Manning n.
+// Planes of U^n a stage-2 tile stages for its own cells: DG2-NL the four
+// depth planes (eta0 hi / lo and its slopes) and the six discharge modes after
+// friction stage 1 left in Q; DG2-LL eta0 hi / lo, qx0, qy0, the six limited
+// slopes stage 1 left in Q and the Manning n.
 constexpr int kOwn32 = 11;
 
 template <bool LL, int STAGE, int BX, int BY>
@@ -321,8 +322,13 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
         if (gj < d.ny && gx < d.pitch) {
           const long long o = (long long)gj * d.pitch + gx;
           if (!LL) {
+            // the depth modes of U^n, its discharge modes after friction (stage 1)
+            cp_async16(dst + E0 * OP, d.S + E0 * P + o);
+            cp_async16(dst + E1X * OP, d.S + E1X * P + o);
+            cp_async16(dst + E1Y * OP, d.S + E1Y * P + o);
+            cp_async16(dst + E0L * OP, d.S + E0L * P + o);
 #pragma unroll
-            for (int p = 0; p < kPlanes32; ++p) cp_async16(dst + p * OP, d.S + p * P + o);
+            for (int p = 0; p < 6; ++p) cp_async16(dst + (QX0 + p) * OP, d.Q + p * P + o);
           } else {
             cp_async16(dst + 0 * OP, d.S + E0 * P + o);
             cp_async16(dst + 1 * OP, d.S + E0L * P + o);
@@ -331,7 +337,7 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
 #pragma unroll
             for (int p = 0; p < 6; ++p) cp_async16(dst + (4 + p) * OP, d.Q + p * P + o);
           }
-          cp_async16(dst + (kOwn32 - 1) * OP, d.N + o);
+          if (LL) cp_async16(dst + (kOwn32 - 1) * OP, d.N + o);
         } else {
 #pragma unroll
           for (int p = 0; p < kOwn32; ++p) *reinterpret_cast<float4*>(dst + p * OP) = zero4;
@@ -545,13 +551,17 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
         d.Q[0 * P + c] = m[E1X]; d.Q[1 * P + c] = m[E1Y];
         d.Q[2 * P + c] = m[QX1X]; d.Q[3 * P + c] = m[QX1Y];
         d.Q[4 * P + c] = m[QY1X]; d.Q[5 * P + c] = m[QY1Y];
+      } else {
+        // U^n's discharge modes after friction, for stage 2's RK average
+#pragma unroll
+        for (int p = 0; p < 6; ++p) d.Q[p * P + c] = m[QX0 + p];
       }
     } else {
       // U^n after friction (and, in DG2-LL, the limiter of stage 1): the average
       // of the RK2 combination
       float un[9], unlo;
-      const float nn = sm.own[kOwn32 - 1][ty][tx];
       if (LL) {
+        const float nn = sm.own[kOwn32 - 1][ty][tx];
         un[E0] = sm.own[0][ty][tx];
         unlo = sm.own[1][ty][tx];
         un[QX0] = sm.own[2][ty][tx];
@@ -561,13 +571,10 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
         un[QY1X] = sm.own[8][ty][tx]; un[QY1Y] = sm.own[9][ty][tx];
         friction_centre32(gdt, nn, tol, (un[E0] - z0) + unlo, un[QX0], un[QY0]);
       } else {
+        // the discharges arrive with friction applied (stage 1 stored them)
 #pragma unroll
         for (int k = 0; k < 9; ++k) un[k] = sm.own[k][ty][tx];
         unlo = sm.own[E0L][ty][tx];
-        float q[6] = {un[QX0], un[QX1X], un[QX1Y], un[QY0], un[QY1X], un[QY1Y]};
-        friction_modes32(gdt, nn, tol, (un[E0] - z0) + unlo, un[E1X] - z1x, un[E1Y] - z1y, q);
-        un[QX0] = q[0]; un[QX1X] = q[1]; un[QX1Y] = q[2];
-        un[QY0] = q[3]; un[QY1X] = q[4]; un[QY1Y] = q[5];
       }
 #pragma unroll
       for (int k = 1; k < 9; ++k) out[k] = 0.5f * (un[k] + m[k] + dt * L[k]);
