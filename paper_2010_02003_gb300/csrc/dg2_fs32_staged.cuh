@@ -247,11 +247,11 @@ __device__ __forceinline__ RecF staged_neighbour_rec(const D32& d, const SM& sm,
   const bool pw = pw_scale32(h0, wh, eh, sh, nh, d.tol, d.wd, scl);
   const float qx0 = sm.st.u[QX0][c], qy0 = sm.st.u[QY0][c];
   const bool thin = d.wd != 0;
-  if (dir == 1)
-    return side == 0 ? make_rec32(eh, qx0 + xx, qy0 + yx, pw, scl, d.tol, thin, h0)
-                     : make_rec32(wh, qx0 - xx, qy0 - yx, pw, scl, d.tol, thin, h0);
-  return side == 0 ? make_rec32(nh, qx0 + xy, qy0 + yy, pw, scl, d.tol, thin, h0)
-                   : make_rec32(sh, qx0 - xy, qy0 - yy, pw, scl, d.tol, thin, h0);
+  // the limit at the shared face, selected (one record built whatever dir and side)
+  const float hf = dir == 1 ? (side == 0 ? eh : wh) : (side == 0 ? nh : sh);
+  const float dqx = dir == 1 ? xx : xy, dqy = dir == 1 ? yx : yy;
+  const float qxf = side == 0 ? qx0 + dqx : qx0 - dqx, qyf = side == 0 ? qy0 + dqy : qy0 - dqy;
+  return make_rec32(hf, qxf, qyf, pw, scl, d.tol, thin, h0);
 }
 
 // One RK stage of the FP32 free-surface form on the tile (bx, by) of problem d.
@@ -401,59 +401,38 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
     sm.n[ty][tx] = rN;
   }
   {
+    // the records beyond the tile, one per thread of the first 2 (BX + BY)
+    // threads: west column, east column, south row, north row.  Every thread
+    // runs the same code on its side's indices, so a warp holding several
+    // sides builds their records together.
     const int t = tid;
     const int ni = d.nx - i0 < BX ? d.nx - i0 : BX, nj = d.ny - j0 < BY ? d.ny - j0 : BY;
-    if (t < BY) {
-      if (t < nj) {
-        const int jj = j0 + t, r = t + H;
-        if (i0 == 0) {
-          float h, qx, qy;
-          staged_face_limit<LL, SP>(d, sm, r, X0, i0, jj, 1, h, qx, qy);
-          ghost32(d, 0, (jj + 0.5f) * d.dy, ts, h, qx, qy);
-          sm.hw[t] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.hw[t] = staged_neighbour_rec<LL, SP>(d, sm, r, X0 - 1, i0 - 1, jj, 1, 0);
-        }
+    const int kind = t < BY ? 0 : t < 2 * BY ? 1 : t < 2 * BY + BX ? 2 : 3;
+    const int q = kind == 0 ? t : kind == 1 ? t - BY : kind == 2 ? t - 2 * BY : t - 2 * BY - BX;
+    if (t < 2 * (BX + BY) && q < (kind <= 1 ? nj : ni)) {
+      const int dir = kind <= 1 ? 1 : 2, side = kind & 1;
+      // the tile cell beside the face (staged row r, column x; grid gi, gj)
+      const int r = kind == 0 || kind == 1 ? q + H : kind == 2 ? H : H + nj - 1;
+      const int x = kind == 0 ? X0 : kind == 1 ? X0 + ni - 1 : X0 + q;
+      const int gi = i0 + x - X0, gj = j0 + r - H;
+      // step from it to the neighbour across the face
+      const int sx = dir == 1 ? (side == 0 ? -1 : 1) : 0, sy = dir == 2 ? (side == 0 ? -1 : 1) : 0;
+      const bool at_edge = dir == 1 ? (side == 0 ? gi == 0 : gi == d.nx - 1)
+                                    : (side == 0 ? gj == 0 : gj == d.ny - 1);
+      RecF rec;
+      if (at_edge) {
+        // the ghost of the tile cell's own limit at that face
+        const int fo = kind == 0 ? 1 : kind == 1 ? 0 : kind == 2 ? 3 : 2;
+        float h, qx, qy;
+        staged_face_limit<LL, SP>(d, sm, r, x, gi, gj, fo, h, qx, qy);
+        const float s = dir == 1 ? (gj + 0.5f) * d.dy : (gi + 0.5f) * d.dx;
+        ghost32(d, kind, s, ts, h, qx, qy);
+        rec = make_rec32(h, qx, qy, false, 1.f, tol);
+      } else {
+        rec = staged_neighbour_rec<LL, SP>(d, sm, r + sy, x + sx, gi + sx, gj + sy, dir, side);
       }
-    } else if (t < 2 * BY) {
-      const int q = t - BY;
-      if (q < nj) {
-        const int jj = j0 + q, r = q + H, il = i0 + ni - 1;
-        if (il == d.nx - 1) {
-          float h, qx, qy;
-          staged_face_limit<LL, SP>(d, sm, r, X0 + ni - 1, il, jj, 0, h, qx, qy);
-          ghost32(d, 1, (jj + 0.5f) * d.dy, ts, h, qx, qy);
-          sm.he[q] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.he[q] = staged_neighbour_rec<LL, SP>(d, sm, r, X0 + ni, il + 1, jj, 1, 1);
-        }
-      }
-    } else if (t < 2 * BY + BX) {
-      const int q = t - 2 * BY;
-      if (q < ni) {
-        const int ii = i0 + q;
-        if (j0 == 0) {
-          float h, qx, qy;
-          staged_face_limit<LL, SP>(d, sm, H, X0 + q, ii, j0, 3, h, qx, qy);
-          ghost32(d, 2, (ii + 0.5f) * d.dx, ts, h, qx, qy);
-          sm.hs[q] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.hs[q] = staged_neighbour_rec<LL, SP>(d, sm, H - 1, X0 + q, ii, j0 - 1, 2, 0);
-        }
-      }
-    } else if (t < 2 * BY + 2 * BX) {
-      const int q = t - 2 * BY - BX;
-      if (q < ni) {
-        const int ii = i0 + q, jl = j0 + nj - 1;
-        if (jl == d.ny - 1) {
-          float h, qx, qy;
-          staged_face_limit<LL, SP>(d, sm, H + nj - 1, X0 + q, ii, jl, 2, h, qx, qy);
-          ghost32(d, 3, (ii + 0.5f) * d.dx, ts, h, qx, qy);
-          sm.hn[q] = make_rec32(h, qx, qy, false, 1.f, tol);
-        } else {
-          sm.hn[q] = staged_neighbour_rec<LL, SP>(d, sm, H + nj, X0 + q, ii, jl + 1, 2, 1);
-        }
-      }
+      RecF* dst = kind == 0 ? sm.hw : kind == 1 ? sm.he : kind == 2 ? sm.hs : sm.hn;
+      dst[q] = rec;
     }
   }
   __syncthreads();   // the staged planes are dead from here: the face fluxes reuse them
@@ -479,18 +458,19 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
     const int t = tid;
     const int ni = d.nx - i0 < BX ? d.nx - i0 : BX;
     const int nj = d.ny - j0 < BY ? d.ny - j0 : BY;
-    LimF ra, rb;
-    if (t < nj) {
-      revise_face32(sm.e[t][ni - 1], sm.he[t], tol, ra, rb);
-      const FaceF fe = flux_x32(ra, rb, g, tol);
-      sm.fc.fx[t][ni] = FaceR32{fe, ra.h};
-      if (i0 + ni == d.nx) brate -= fe.h * d.dy;
-    } else if (t >= BY && t < BY + ni) {
-      const int q = t - BY;
-      revise_face32(sm.n[nj - 1][q], sm.hn[q], tol, ra, rb);
-      const FaceF fn = flux_y32(ra, rb, g, tol);
-      sm.fc.fy[nj][q] = FaceR32{fn, ra.h};
-      if (j0 + nj == d.ny) brate -= fn.h * d.dx;
+    // the tile's east edge faces (threads 0 .. nj - 1) and north edge faces
+    // (threads BY .. BY + ni - 1) on one code path: the north faces' normal is y
+    const bool yf = t >= BY;
+    const int q = yf ? t - BY : t;
+    if (yf ? q < ni : q < nj) {
+      LimF ra, rb;
+      revise_face32(yf ? sm.n[nj - 1][q] : sm.e[q][ni - 1], yf ? sm.hn[q] : sm.he[q], tol, ra, rb);
+      const FaceF f = hll_dev(ra.h, yf ? ra.qy : ra.qx, yf ? ra.qx : ra.qy, yf ? ra.v : ra.u,
+                              yf ? ra.u : ra.v, rb.h, yf ? rb.qy : rb.qx, yf ? rb.qx : rb.qy,
+                              yf ? rb.v : rb.u, yf ? rb.u : rb.v, g, tol);
+      FaceR32* dst = yf ? &sm.fc.fy[nj][q] : &sm.fc.fx[q][ni];
+      *dst = FaceR32{f, ra.h};
+      if (yf ? j0 + nj == d.ny : i0 + ni == d.nx) brate -= f.h * (yf ? d.dx : d.dy);
     }
   }
   __syncthreads();
