@@ -360,6 +360,24 @@ __device__ __forceinline__ F3 flux_y(const Lim& S, const Lim& N, double g, doubl
   return o;
 }
 
+// Face flux along x or y by a run-time flag: the normal and tangential
+// components selected, so a warp holding both kinds of faces evaluates one flux
+// (the same arithmetic as flux_x / flux_y).
+__device__ __forceinline__ F3 flux_dir(const Lim& A, const Lim& B, bool ydir, double g, double tol,
+                                       int flux) {
+  const double an = ydir ? A.qy : A.qx, at = ydir ? A.qx : A.qy;
+  const double aun = ydir ? A.v : A.u, aut = ydir ? A.u : A.v;
+  const double bn = ydir ? B.qy : B.qx, bt = ydir ? B.qx : B.qy;
+  const double bun = ydir ? B.v : B.u, but = ydir ? B.u : B.v;
+  const F3 r = flux == 1 ? roe(A.h, an, at, aun, aut, B.h, bn, bt, bun, but, g, tol)
+                         : hll(A.h, an, at, aun, aut, B.h, bn, bt, bun, but, g, tol);
+  F3 o;
+  o.h = r.h;
+  o.x = ydir ? r.y : r.x;
+  o.y = ydir ? r.x : r.y;
+  return o;
+}
+
 // Physical flux F (x) or G (y) of a point state, velocities by the tol rule.
 __device__ __forceinline__ F3 phys_flux(double h, double qx, double qy, double g, double tol,
                                         bool ydir) {
@@ -878,7 +896,7 @@ __device__ __forceinline__ F3 revise_face(const Rec& a, const Rec& b, bool ydir,
   }
   ra.h = ha; ra.qx = ha * a.u; ra.qy = ha * a.v;
   rb.h = hb; rb.qx = hb * b.u; rb.qy = hb * b.v;
-  return ydir ? flux_y(ra, rb, g, tol, flux) : flux_x(ra, rb, g, tol, flux);
+  return flux_dir(ra, rb, ydir, g, tol, flux);
 }
 
 // Planar depth slope of cell (i, j) along dir, limited (Eqs. 6-7 on eta) when
@@ -1081,58 +1099,38 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
   }
   // the records beyond the tile (a neighbour's, or the edge ghost), one per
   // thread of the last 2 (TX + TY) threads (the fixed-point cells' threads when
-  // there are enough of them), so no warp runs them one lane at a time
+  // there are enough of them), so no warp runs them one lane at a time: west
+  // column, east column, south row, north row, every thread on the same code
+  // with its side's indices, so a warp holding several sides builds their
+  // records together
   {
     const int t = TX * TY - 1 - (threadIdx.y * TX + threadIdx.x);
     const int i0 = bx * TX, j0 = by * TY;
     const int ni = d.nx - i0 < TX ? d.nx - i0 : TX, nj = d.ny - j0 < TY ? d.ny - j0 : TY;
-    if (t < TY) {
-      if (t < nj && sm.cls[t][0] == 2) {
-        const int jj = j0 + t;
-        if (i0 == 0) {
-          double h, qx, qy, zf;
-          own_face_limit<LL>(d, In, i0, jj, 1, h, qx, qy, zf);
-          sm.hw[t] = ghost_rec(d, 0, (jj + 0.5) * d.dy, ts, h, qx, qy, zf);
-        } else {
-          sm.hw[t] = neighbour_rec<LL>(d, In, i0 - 1, jj, 1, 0);
-        }
+    const int kind = t < TY ? 0 : t < 2 * TY ? 1 : t < 2 * TY + TX ? 2 : 3;
+    const int q = kind == 0 ? t : kind == 1 ? t - TY : kind == 2 ? t - 2 * TY : t - 2 * TY - TX;
+    // the tile cell beside the face
+    const int ci = kind == 0 ? 0 : kind == 1 ? ni - 1 : q;
+    const int cj = kind <= 1 ? q : kind == 2 ? 0 : nj - 1;
+    if (t < 2 * (TX + TY) && q < (kind <= 1 ? nj : ni) && sm.cls[cj][ci] == 2) {
+      const int dir = kind <= 1 ? 1 : 2, side = kind & 1;
+      const int gi = i0 + ci, gj = j0 + cj;
+      const bool at_edge = dir == 1 ? (side == 0 ? gi == 0 : gi == d.nx - 1)
+                                    : (side == 0 ? gj == 0 : gj == d.ny - 1);
+      Rec rec;
+      if (at_edge) {
+        // the ghost of the tile cell's own limit at that face
+        const int fo = kind == 0 ? 1 : kind == 1 ? 0 : kind == 2 ? 3 : 2;
+        double h, qx, qy, zf;
+        own_face_limit<LL>(d, In, gi, gj, fo, h, qx, qy, zf);
+        const double s = dir == 1 ? (gj + 0.5) * d.dy : (gi + 0.5) * d.dx;
+        rec = ghost_rec(d, kind, s, ts, h, qx, qy, zf);
+      } else {
+        const int sx = dir == 1 ? (side == 0 ? -1 : 1) : 0, sy = dir == 2 ? (side == 0 ? -1 : 1) : 0;
+        rec = neighbour_rec<LL>(d, In, gi + sx, gj + sy, dir, side);
       }
-    } else if (t < 2 * TY) {
-      const int r = t - TY;
-      if (r < nj && sm.cls[r][ni - 1] == 2) {
-        const int jj = j0 + r, il = i0 + ni - 1;
-        if (il == d.nx - 1) {
-          double h, qx, qy, zf;
-          own_face_limit<LL>(d, In, il, jj, 0, h, qx, qy, zf);
-          sm.he[r] = ghost_rec(d, 1, (jj + 0.5) * d.dy, ts, h, qx, qy, zf);
-        } else {
-          sm.he[r] = neighbour_rec<LL>(d, In, il + 1, jj, 1, 1);
-        }
-      }
-    } else if (t < 2 * TY + TX) {
-      const int q = t - 2 * TY;
-      if (q < ni && sm.cls[0][q] == 2) {
-        const int ii = i0 + q;
-        if (j0 == 0) {
-          double h, qx, qy, zf;
-          own_face_limit<LL>(d, In, ii, j0, 3, h, qx, qy, zf);
-          sm.hs[q] = ghost_rec(d, 2, (ii + 0.5) * d.dx, ts, h, qx, qy, zf);
-        } else {
-          sm.hs[q] = neighbour_rec<LL>(d, In, ii, j0 - 1, 2, 0);
-        }
-      }
-    } else if (t < 2 * TY + 2 * TX) {
-      const int q = t - 2 * TY - TX;
-      if (q < ni && sm.cls[nj - 1][q] == 2) {
-        const int ii = i0 + q, jl = j0 + nj - 1;
-        if (jl == d.ny - 1) {
-          double h, qx, qy, zf;
-          own_face_limit<LL>(d, In, ii, jl, 2, h, qx, qy, zf);
-          sm.hn[q] = ghost_rec(d, 3, (ii + 0.5) * d.dx, ts, h, qx, qy, zf);
-        } else {
-          sm.hn[q] = neighbour_rec<LL>(d, In, ii, jl + 1, 2, 1);
-        }
-      }
+      Rec* dst = kind == 0 ? sm.hw : kind == 1 ? sm.he : kind == 2 ? sm.hs : sm.hn;
+      dst[q] = rec;
     }
   }
   __syncthreads();
@@ -1161,17 +1159,16 @@ __device__ __forceinline__ void stage_tile(const Dev& d, StageSmem& sm, int bx, 
     const int ni = d.nx - bx * TX < TX ? d.nx - bx * TX : TX;
     const int nj = d.ny - by * TY < TY ? d.ny - by * TY : TY;
     double ha, za, hb, zb;
-    if (t < nj) {
-      if (sm.cls[t][ni - 1] == 2) {
-        const F3 fe = revise_face(sm.e[t][ni - 1], sm.he[t], false, g, tol, d.flux, ha, za, hb, zb);
-        sm.fx[t][ni] = FaceR{fe.h, fe.x, fe.y, ha, za};
-        if (bx * TX + ni == d.nx) brate -= fe.h * d.dy;
-      }
-    } else if (t >= TY && t < TY + ni && sm.cls[nj - 1][t - TY] == 2) {
-      const int q = t - TY;
-      const F3 fn = revise_face(sm.n[nj - 1][q], sm.hn[q], true, g, tol, d.flux, ha, za, hb, zb);
-      sm.fy[nj][q] = FaceR{fn.h, fn.x, fn.y, ha, za};
-      if (by * TY + nj == d.ny) brate -= fn.h * d.dx;
+    // east edge faces (t < nj) and north edge faces (TY <= t < TY + ni) on one
+    // code path: the north faces' normal is y
+    const bool yf = t >= TY;
+    const int q = yf ? t - TY : t;
+    if ((yf ? q < ni : q < nj) && (yf ? sm.cls[nj - 1][q] : sm.cls[q][ni - 1]) == 2) {
+      const F3 f = revise_face(yf ? sm.n[nj - 1][q] : sm.e[q][ni - 1], yf ? sm.hn[q] : sm.he[q], yf,
+                               g, tol, d.flux, ha, za, hb, zb);
+      FaceR* dst = yf ? &sm.fy[nj][q] : &sm.fx[q][ni];
+      *dst = FaceR{f.h, f.x, f.y, ha, za};
+      if (yf ? by * TY + nj == d.ny : bx * TX + ni == d.nx) brate -= f.h * (yf ? d.dx : d.dy);
     }
   }
   __syncthreads();
