@@ -38,6 +38,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// waits until at most one committed group of the thread's copies is in flight
+__device__ __forceinline__ void cp_async_wait_but_one() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
 
 // Row pitch of a 16-wide tile's staging (floats).  48 puts the two rows a warp
 // reads at once on disjoint bank halves; 24 (no padding) halves the staging's
@@ -313,6 +318,9 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
       }
     }
     if (STAGE == 2) {
+      // the own cells' U^n is read only by the update: its copies form a group of
+      // their own, waited for after the faces
+      cp_async_commit();
       constexpr int O4 = BX / 4;
       for (int k = tid; k < BY * O4; k += NT) {
         const int r = k / O4, q = k - r * O4;
@@ -344,7 +352,12 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
         }
       }
     }
-    cp_async_wait_all();
+    if (STAGE == 2) {
+      cp_async_commit();
+      cp_async_wait_but_one();
+    } else {
+      cp_async_wait_all();
+    }
     __syncthreads();
   }
 
@@ -473,6 +486,7 @@ __device__ __forceinline__ void stage32_staged(const D32& d, StagedSmem32<LL, ST
       if (yf ? j0 + nj == d.ny : i0 + ni == d.nx) brate -= f.h * (yf ? d.dx : d.dy);
     }
   }
+  if (STAGE == 2) cp_async_wait_all();   // the own cells' U^n
   __syncthreads();
 
   // ---- operator (Eqs. 4-5) and the RK update ----
