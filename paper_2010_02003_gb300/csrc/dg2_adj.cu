@@ -384,6 +384,165 @@ __device__ __forceinline__ void revise_face_t(const RecT<T>& a, const RecT<T>& b
   rb.u = val(hb) > tol ? b.u : zero; rb.v = val(hb) > tol ? b.v : zero;
 }
 
+// Reverse-mode adjoint of one face's revision and flux (revise_face_t, then
+// flux_face): the gradient of S = wF . F + wha ha + wza za + whb hb + wzb zb
+// (F the flux in x / y components, ha, za, hb, zb the revised depths and beds
+// of the lower side a and the upper side b) with respect to each side's record
+// fields (h, u, v, hs), added into ga and gb.  The forward values are formed
+// by the same operations and value tests as the templated functions, so the
+// same branches are taken: the wet-dry, revision, HLL-regime and partially
+// wet branches are frozen, sqrt has derivative 0 at 0, and a tie in the wave
+// speeds' min / max or the revision's bed level goes to the same operand.
+// One forward and one backward sweep replace forward-mode derivatives in
+// eight directions.
+__device__ __noinline__ void revise_flux_adj(const RecT<real>& a, const RecT<real>& b, bool ydir,
+                                             real gr, real tol, const real* wF, real wha,
+                                             real wza, real whb, real wzb, real* ga, real* gb) {
+  // ---- forward: the revision (revise_face_t) ----
+  const bool np = !a.pw && !b.pw;
+  // (the revised beds za, zb enter S linearly; their values are not needed)
+  real ha, hb, ea = 0.0, eb = 0.0, zs = 0.0, da = 0.0, db = 0.0;
+  bool zs_a = false;
+  if (np) {
+    ha = a.hs;
+    hb = b.hs;
+  } else {
+    ea = a.pw ? a.h + a.zf : a.zf + a.hs;
+    eb = b.pw ? b.h + b.zf : b.zf + b.hs;
+    const real oa = a.pw ? ea - a.hs : a.zf;
+    const real ob = b.pw ? eb - b.hs : b.zf;
+    zs_a = oa > ob;
+    zs = zs_a ? oa : ob;
+    da = ea - zs;
+    db = eb - zs;
+    ha = da > 0.0 ? da : 0.0;
+    hb = db > 0.0 ? db : 0.0;
+  }
+  // the flux's states in the face frame (normal n, tangential t)
+  const bool wa = ha > tol, wb = hb > tol;
+  const real an = ydir ? a.v : a.u, at = ydir ? a.u : a.v;
+  const real bn = ydir ? b.v : b.u, bt = ydir ? b.u : b.v;
+  const real hL = ha, qnL = ha * an, qtL = ha * at, unL = wa ? an : 0.0, utL = wa ? at : 0.0;
+  const real hR = hb, qnR = hb * bn, qtR = hb * bt, unR = wb ? bn : 0.0, utR = wb ? bt : 0.0;
+  // weights of the frame's components
+  const real w[3] = {wF[0], ydir ? wF[2] : wF[1], ydir ? wF[1] : wF[2]};
+  // adjoints of the HLL inputs
+  real g_hL = 0.0, g_qnL = 0.0, g_qtL = 0.0, g_unL = 0.0, g_utL = 0.0;
+  real g_hR = 0.0, g_qnR = 0.0, g_qtR = 0.0, g_unR = 0.0, g_utR = 0.0;
+  if (!(hL <= tol && hR <= tol)) {
+    // ---- forward: HLL (hll_t) ----
+    const real cL = sqrt(gr * hL), cR = sqrt(gr * hR);
+    real sL, sR, us = 0.0, cs = 0.0;
+    int mode;
+    bool sL_first = true, sR_first = true;
+    if (hL <= tol) {
+      mode = 1;
+      sL = unR - 2.0 * cR;
+      sR = unR + cR;
+    } else if (hR <= tol) {
+      mode = 2;
+      sL = unL - cL;
+      sR = unL + 2.0 * cL;
+    } else {
+      mode = 0;
+      us = 0.5 * (unL + unR) + cL - cR;
+      cs = 0.5 * (cL + cR) + 0.25 * (unL - unR);
+      const real s1 = unL - cL, s2 = us - cs, r1 = unR + cR, r2 = us + cs;
+      sL_first = !(s2 < s1);
+      sR_first = !(r2 > r1);
+      sL = sL_first ? s1 : s2;
+      sR = sR_first ? r1 : r2;
+    }
+    const real fL[3] = {hL * unL, hL * unL * unL + 0.5 * gr * hL * hL, hL * unL * utL};
+    const real fR[3] = {hR * unR, hR * unR * unR + 0.5 * gr * hR * hR, hR * unR * utR};
+    real g_fL[3] = {0.0, 0.0, 0.0}, g_fR[3] = {0.0, 0.0, 0.0};
+    // ---- backward: HLL ----
+    if (sL >= 0.0) {
+      for (int k = 0; k < 3; ++k) g_fL[k] = w[k];
+    } else if (sR <= 0.0) {
+      for (int k = 0; k < 3; ++k) g_fR[k] = w[k];
+    } else {
+      // F_k = (sR fL_k - sL fR_k + sL sR (qR_k - qL_k)) / (sR - sL)
+      const real inv = 1.0 / (sR - sL), sLR = sL * sR;
+      const real dq[3] = {hR - hL, qnR - qnL, qtR - qtL};
+      real g_sL = 0.0, g_sR = 0.0, g_inv = 0.0, g_dq[3];
+      for (int k = 0; k < 3; ++k) {
+        const real nk = sR * fL[k] - sL * fR[k] + sLR * dq[k];
+        const real gn = w[k] * inv;
+        g_inv += w[k] * nk;
+        g_fL[k] = gn * sR;
+        g_fR[k] = -gn * sL;
+        g_sR += gn * (fL[k] + sL * dq[k]);
+        g_sL += gn * (sR * dq[k] - fR[k]);
+        g_dq[k] = gn * sLR;
+      }
+      g_sR -= g_inv * inv * inv;
+      g_sL += g_inv * inv * inv;
+      g_hR += g_dq[0]; g_hL -= g_dq[0];
+      g_qnR += g_dq[1]; g_qnL -= g_dq[1];
+      g_qtR += g_dq[2]; g_qtL -= g_dq[2];
+      // wave speeds
+      real g_cL = 0.0, g_cR = 0.0;
+      if (mode == 1) {
+        g_unR += g_sL + g_sR;
+        g_cR += -2.0 * g_sL + g_sR;
+      } else if (mode == 2) {
+        g_unL += g_sL + g_sR;
+        g_cL += -g_sL + 2.0 * g_sR;
+      } else {
+        real g_us = 0.0, g_cs = 0.0;
+        if (sL_first) { g_unL += g_sL; g_cL -= g_sL; } else { g_us += g_sL; g_cs -= g_sL; }
+        if (sR_first) { g_unR += g_sR; g_cR += g_sR; } else { g_us += g_sR; g_cs += g_sR; }
+        g_unL += 0.5 * g_us + 0.25 * g_cs;
+        g_unR += 0.5 * g_us - 0.25 * g_cs;
+        g_cL += g_us + 0.5 * g_cs;
+        g_cR += -g_us + 0.5 * g_cs;
+      }
+      // c = sqrt(g h): dc/dh = g / (2 c), 0 at c = 0
+      if (cL > 0.0) g_hL += g_cL * (0.5 * gr / cL);
+      if (cR > 0.0) g_hR += g_cR * (0.5 * gr / cR);
+    }
+    // physical fluxes f = (h un, h un^2 + g h^2 / 2, h un ut)
+    g_hL += g_fL[0] * unL + g_fL[1] * (unL * unL + gr * hL) + g_fL[2] * unL * utL;
+    g_unL += g_fL[0] * hL + g_fL[1] * 2.0 * hL * unL + g_fL[2] * hL * utL;
+    g_utL += g_fL[2] * hL * unL;
+    g_hR += g_fR[0] * unR + g_fR[1] * (unR * unR + gr * hR) + g_fR[2] * unR * utR;
+    g_unR += g_fR[0] * hR + g_fR[1] * 2.0 * hR * unR + g_fR[2] * hR * utR;
+    g_utR += g_fR[2] * hR * unR;
+  }
+  // ---- backward: the flux states to the records and the revised depths ----
+  const real g_ha = wha + g_hL + g_qnL * an + g_qtL * at;
+  const real g_hb = whb + g_hR + g_qnR * bn + g_qtR * bt;
+  const real g_an = g_qnL * ha + (wa ? g_unL : 0.0), g_at = g_qtL * ha + (wa ? g_utL : 0.0);
+  const real g_bn = g_qnR * hb + (wb ? g_unR : 0.0), g_bt = g_qtR * hb + (wb ? g_utR : 0.0);
+  ga[1] += ydir ? g_at : g_an;
+  ga[2] += ydir ? g_an : g_at;
+  gb[1] += ydir ? g_bt : g_bn;
+  gb[2] += ydir ? g_bn : g_bt;
+  // ---- backward: the revision ----
+  if (np) {
+    ga[3] += g_ha;
+    gb[3] += g_hb;
+    if (a.h < 0.0) ga[0] += wza;
+    if (b.h < 0.0) gb[0] += wzb;
+  } else {
+    // ha = max(da, 0), za = zs + min(da, 0), da = ea - zs (and b's)
+    const real g_da = (da > 0.0 ? g_ha : 0.0) + (da < 0.0 ? wza : 0.0);
+    const real g_db = (db > 0.0 ? g_hb : 0.0) + (db < 0.0 ? wzb : 0.0);
+    const real g_zs = wza + wzb - g_da - g_db;
+    real g_ea = g_da, g_eb = g_db;
+    // zs = max(oa, ob), oa = ea - hs (partially wet) or the face bed
+    if (zs_a) {
+      if (a.pw) { g_ea += g_zs; ga[3] -= g_zs; }
+    } else {
+      if (b.pw) { g_eb += g_zs; gb[3] -= g_zs; }
+    }
+    // ea = h + zf (partially wet) or zf + hs
+    if (a.pw) ga[0] += g_ea; else ga[3] += g_ea;
+    if (b.pw) gb[0] += g_eb; else gb[3] += g_eb;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Problem description
 // ---------------------------------------------------------------------------
@@ -522,8 +681,9 @@ __device__ __forceinline__ RecT<T> side_rec(const Prob& p, const T* h4, const T&
 }
 
 // Face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at stage time
-// with hydrograph discharge Q, in real: its flux and the own side's revised
-// depth and bed level.
+// with hydrograph discharge Q, in real: its flux (FLUX) and the own side's
+// revised depth and bed level.
+template <bool FLUX = true>
 __device__ void face_rev(const Prob& p, const store* __restrict__ U, int i, int j, int f, real Q,
                          const RecT<real>* own, F3T<real>& F, real& ho, real& zo) {
   const long long N = p.N, c = (long long)j * p.nx + i;
@@ -559,7 +719,7 @@ __device__ void face_rev(const Prob& p, const store* __restrict__ U, int i, int 
   const bool own_lower = f == 0 || f == 2;
   if (own_lower) revise_face_t(own[f], oth, p.tol, ra, rb, ha, za, hb, zb);
   else revise_face_t(oth, own[f], p.tol, ra, rb, ha, za, hb, zb);
-  F = flux_face(ra, rb, f >= 2, p.g, p.tol);
+  if (FLUX) F = flux_face(ra, rb, f >= 2, p.g, p.tol);
   ho = own_lower ? ha : hb;
   zo = own_lower ? za : zb;
 }
@@ -765,7 +925,7 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
     recs_double(p, In, c, r);
     for (int f = 0; f < 4; ++f) {
       F3T<real> F;
-      face_rev(p, In, i, j, f, Q, r, F, hsv[f], zsv[f]);
+      face_rev<false>(p, In, i, j, f, Q, r, F, hsv[f], zsv[f]);  // revised values only
       ru[f] = r[f].u;
       rv[f] = r[f].v;
     }
@@ -884,26 +1044,13 @@ __global__ void adj_face_kernel(Prob p, int dir, const store* __restrict__ In,
     const real za0 = p.Z[ca] + p.Z[l1 * N + ca], zb0 = p.Z[cb] - p.Z[l1 * N + cb];
     // The face's outputs depend on the inputs only through each side's record
     // (h, u, v, hs; its bed and partially wet flag are constants of the state).
-    // Their adjoint is taken back to the eight record fields in one pass of
-    // eight derivatives over the revision and flux, then to each side's six
-    // inputs in a pass of six derivatives over that side's record alone.
+    // Their adjoint is taken back to the eight record fields by one reverse
+    // sweep of the revision and flux, then to each side's six inputs in a pass
+    // of six derivatives over that side's record alone.
     const RecT<real> Ra = side_rec(p, ha4, qa[1], qa[2], In[ca], fa, za0);
     const RecT<real> Rb = side_rec(p, hb4, qb[1], qb[2], In[cb], fb, zb0);
-    real grec[8];
-    {
-      RecT<Dual<8>> Da, Db;
-      Da.h = var<8>(Ra.h, 0); Da.u = var<8>(Ra.u, 1); Da.v = var<8>(Ra.v, 2);
-      Da.hs = var<8>(Ra.hs, 3); Da.zf = Ra.zf; Da.pw = Ra.pw;
-      Db.h = var<8>(Rb.h, 4); Db.u = var<8>(Rb.u, 5); Db.v = var<8>(Rb.v, 6);
-      Db.hs = var<8>(Rb.hs, 7); Db.zf = Rb.zf; Db.pw = Rb.pw;
-      LimT<Dual<8>> ra, rb;
-      Dual<8> ha, za, hb, zb;
-      revise_face_t(Da, Db, p.tol, ra, rb, ha, za, hb, zb);
-      const F3T<Dual<8>> F = flux_face(ra, rb, y, p.g, p.tol);
-      for (int k = 0; k < 8; ++k)
-        grec[k] = phi[0] * F.h.d[k] + phi[1] * F.x.d[k] + phi[2] * F.y.d[k] + pha * ha.d[k] +
-                  pza * za.d[k] + phb * hb.d[k] + pzb * zb.d[k];
-    }
+    real grec[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    revise_flux_adj(Ra, Rb, y, p.g, p.tol, phi, pha, pza, phb, pzb, grec, grec + 4);
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
       const real* h4 = side == 0 ? ha4 : hb4;
