@@ -655,6 +655,109 @@ __device__ __forceinline__ void own_terms(const Prob& p, const T* hs, const T* z
   L[QY1Y] = k3y * (-(Gp.y + Gm.y) + g23 * h1y * zb1y);
 }
 
+// Adjoint of a Gauss-point physical flux (phys_t) of state (h, qx, qy) along x
+// or y: adds the gradient of gf . f into g_h, g_qx, g_qy (velocities by the
+// tol rule, frozen below it).
+__device__ __forceinline__ void phys_adj(real h, real qx, real qy, real gr, real tol, bool ydir,
+                                         const real* gf, real& g_h, real& g_qx, real& g_qy) {
+  const bool wet = h > tol;
+  const real u = wet ? qx / h : 0.0, v = wet ? qy / h : 0.0;
+  real gh, gu, gv;
+  if (!ydir) {  // (h u, h u^2 + g h^2 / 2, h u v)
+    gh = gf[0] * u + gf[1] * (u * u + gr * h) + gf[2] * u * v;
+    gu = gf[0] * h + gf[1] * 2.0 * h * u + gf[2] * h * v;
+    gv = gf[2] * h * u;
+  } else {      // (h v, h u v, h v^2 + g h^2 / 2)
+    gh = gf[0] * v + gf[1] * u * v + gf[2] * (v * v + gr * h);
+    gu = gf[1] * h * v;
+    gv = gf[0] * h + gf[1] * h * u + gf[2] * 2.0 * h * v;
+  }
+  if (wet) {  // u = qx / h, v = qy / h
+    g_qx += gu / h;
+    g_qy += gv / h;
+    gh -= (gu * u + gv * v) / h;
+  }
+  g_h += gh;
+}
+
+// Reverse-mode adjoint of own_terms contracted with mu: the gradient of
+// sum_k mu[k] L[k] with respect to the faces' revised depths hs, beds zs and
+// velocities u, v (written to g_hs, g_zs, g_u, g_v; faces E, W, N, S).
+__device__ __noinline__ void own_terms_adj(const Prob& p, const real* hs, const real* zs,
+                                           const real* u, const real* v, const real* mu,
+                                           real* g_hs, real* g_zs, real* g_u, real* g_v) {
+  const real gr = p.g, idx = p.inv_dx, idy = p.inv_dy;
+  const real k3x = -3.0 * idx, k3y = -3.0 * idy, g23 = 2.0 * gr / 3.0;
+  const real r3 = 1.0 / 1.7320508075688772;
+  // forward: the revised states (q* = h* u) and the dummy modes of both directions
+  real sh[4], sx[4], sy[4];
+  for (int f = 0; f < 4; ++f) {
+    sh[f] = hs[f];
+    sx[f] = hs[f] * u[f];
+    sy[f] = hs[f] * v[f];
+  }
+  const real zb1x = 0.5 * (zs[0] - zs[1]), zb1y = 0.5 * (zs[2] - zs[3]);
+  // mean and slope of (h, qx, qy) along x (faces E, W) and y (faces N, S)
+  real m0[2][3], m1[2][3];
+  for (int dd = 0; dd < 2; ++dd) {
+    const int fp = 2 * dd, fm = 2 * dd + 1;
+    m0[dd][0] = 0.5 * (sh[fp] + sh[fm]);
+    m1[dd][0] = 0.5 * (sh[fp] - sh[fm]);
+    m0[dd][1] = 0.5 * (sx[fp] + sx[fm]);
+    m1[dd][1] = 0.5 * (sx[fp] - sx[fm]);
+    m0[dd][2] = 0.5 * (sy[fp] + sy[fm]);
+    m1[dd][2] = 0.5 * (sy[fp] - sy[fm]);
+  }
+  // backward: adjoints of the modes and of the bed slopes
+  real g_m0[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  real g_m1[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  real g_zb1x = 0.0, g_zb1y = 0.0;
+  // bed terms of the average and slope equations
+  g_m0[0][0] += -2.0 * gr * idx * zb1x * mu[QX0];
+  g_zb1x += -2.0 * gr * idx * m0[0][0] * mu[QX0];
+  g_m0[1][0] += -2.0 * gr * idy * zb1y * mu[QY0];
+  g_zb1y += -2.0 * gr * idy * m0[1][0] * mu[QY0];
+  g_m1[0][0] += k3x * g23 * zb1x * mu[QX1X];
+  g_zb1x += k3x * g23 * m1[0][0] * mu[QX1X];
+  g_m1[1][0] += k3y * g23 * zb1y * mu[QY1Y];
+  g_zb1y += k3y * g23 * m1[1][0] * mu[QY1Y];
+  // Gauss-point fluxes: L = k3 (-(Fp + Fm)) in the slope equations
+  for (int dd = 0; dd < 2; ++dd) {
+    const real k3 = dd == 0 ? k3x : k3y;
+    const real gf[3] = {-k3 * mu[dd == 0 ? H1X : H1Y], -k3 * mu[dd == 0 ? QX1X : QX1Y],
+                        -k3 * mu[dd == 0 ? QY1X : QY1Y]};
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const real r = sgn == 0 ? r3 : -r3;
+      real gh = 0.0, gx = 0.0, gy = 0.0;
+      phys_adj(m0[dd][0] + m1[dd][0] * r, m0[dd][1] + m1[dd][1] * r, m0[dd][2] + m1[dd][2] * r,
+               gr, p.tol, dd == 1, gf, gh, gx, gy);
+      g_m0[dd][0] += gh;
+      g_m1[dd][0] += gh * r;
+      g_m0[dd][1] += gx;
+      g_m1[dd][1] += gx * r;
+      g_m0[dd][2] += gy;
+      g_m1[dd][2] += gy * r;
+    }
+  }
+  // modes to the faces' revised states, then to hs, u, v
+  for (int dd = 0; dd < 2; ++dd) {
+    const int fp = 2 * dd, fm = 2 * dd + 1;
+    const real ghp = 0.5 * (g_m0[dd][0] + g_m1[dd][0]), ghm = 0.5 * (g_m0[dd][0] - g_m1[dd][0]);
+    const real gxp = 0.5 * (g_m0[dd][1] + g_m1[dd][1]), gxm = 0.5 * (g_m0[dd][1] - g_m1[dd][1]);
+    const real gyp = 0.5 * (g_m0[dd][2] + g_m1[dd][2]), gym = 0.5 * (g_m0[dd][2] - g_m1[dd][2]);
+    g_hs[fp] = ghp + gxp * u[fp] + gyp * v[fp];
+    g_hs[fm] = ghm + gxm * u[fm] + gym * v[fm];
+    g_u[fp] = gxp * hs[fp];
+    g_v[fp] = gyp * hs[fp];
+    g_u[fm] = gxm * hs[fm];
+    g_v[fm] = gym * hs[fm];
+  }
+  g_zs[0] = 0.5 * g_zb1x;
+  g_zs[1] = -0.5 * g_zb1x;
+  g_zs[2] = 0.5 * g_zb1y;
+  g_zs[3] = -0.5 * g_zb1y;
+}
+
 // Records of cell (i, j) of state U in real.
 __device__ __forceinline__ void recs_double(const Prob& p, const store* __restrict__ U, long long c,
                                             RecT<real>* r) {
@@ -930,57 +1033,28 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
       rv[f] = r[f].v;
     }
   }
-  // pass 1: the 12 raw limits (h*, z* held).  The own terms depend on them only
-  // through the four face velocities (u, v): their adjoint is taken back to the
-  // eight velocities in a pass of eight derivatives over the own terms, then to
-  // the raw limits in a pass of twelve over the records alone.
-  {
-    real guv[8];
-    {
-      Dual<8> hs[4], zs[4], u[4], v[4], L[9];
-      for (int f = 0; f < 4; ++f) {
-        hs[f] = cst<8>(hsv[f]);
-        zs[f] = cst<8>(zsv[f]);
-        u[f] = var<8>(ru[f], f);
-        v[f] = var<8>(rv[f], 4 + f);
-      }
-      own_terms<Dual<8>>(p, hs, zs, u, v, L);
-      for (int q = 0; q < 8; ++q) {
-        real a = 0.0;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
-        guv[q] = a;
-      }
-    }
-    Dual<12> dl[4][3];
-    for (int f = 0; f < 4; ++f)
-      for (int k = 0; k < 3; ++k) dl[f][k] = var<12>(lim[f][k], 3 * f + k);
-    const Dual<12> h0 = with_value(0.5 * (dl[0][0] + dl[1][0]), In[c]);
-    RecT<Dual<12>> rd[4];
-    cell_recs_t<Dual<12>>(p, c, dl[0], dl[1], dl[2], dl[3], h0, rd);
-    for (int q = 0; q < 12; ++q) {
-      real a = 0.0;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) a += guv[f] * rd[f].u.d[q] + guv[4 + f] * rd[f].v.d[q];
-      OWN[q * N + c] = a;
-    }
+  // The own terms depend on the raw limits only through the four face
+  // velocities (u, v), and on the faces' h* and z* as inputs of their own: one
+  // reverse sweep of the own terms gives the adjoints of all sixteen, and the
+  // velocities' are taken to the 12 raw limits in a pass of twelve
+  // derivatives over the records alone.
+  real g_hs[4], g_zs[4], g_u[4], g_v[4];
+  own_terms_adj(p, hsv, zsv, ru, rv, mu, g_hs, g_zs, g_u, g_v);
+  for (int f = 0; f < 4; ++f) {
+    OWN[(12 + 2 * f) * N + c] = g_hs[f];
+    OWN[(13 + 2 * f) * N + c] = g_zs[f];
   }
-  // pass 2: the faces' h* and z* (face velocities held)
-  {
-    Dual<8> hs[4], zs[4], u[4], v[4], L[9];
-    for (int f = 0; f < 4; ++f) {
-      hs[f] = var<8>(hsv[f], 2 * f);
-      zs[f] = var<8>(zsv[f], 2 * f + 1);
-      u[f] = cst<8>(ru[f]);
-      v[f] = cst<8>(rv[f]);
-    }
-    own_terms<Dual<8>>(p, hs, zs, u, v, L);
-    for (int q = 0; q < 8; ++q) {
-      real a = 0.0;
+  Dual<12> dl[4][3];
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < 3; ++k) dl[f][k] = var<12>(lim[f][k], 3 * f + k);
+  const Dual<12> h0 = with_value(0.5 * (dl[0][0] + dl[1][0]), In[c]);
+  RecT<Dual<12>> rd[4];
+  cell_recs_t<Dual<12>>(p, c, dl[0], dl[1], dl[2], dl[3], h0, rd);
+  for (int q = 0; q < 12; ++q) {
+    real acc = 0.0;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) a += mu[k] * L[k].d[q];
-      OWN[(12 + q) * N + c] = a;
-    }
+    for (int f = 0; f < 4; ++f) acc += g_u[f] * rd[f].u.d[q] + g_v[f] * rd[f].v.d[q];
+    OWN[q * N + c] = acc;
   }
 }
 
