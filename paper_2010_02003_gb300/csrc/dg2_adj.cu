@@ -783,6 +783,73 @@ __device__ __forceinline__ RecT<T> side_rec(const Prob& p, const T* h4, const T&
   return make_rec_t(hf, qx, qy, zf, pw, sc, p.tol, p.wd != 0, h0);
 }
 
+// Reverse-mode adjoint of a record's velocities (make_rec_t): adds the
+// gradient of gu u + gv v with respect to the planar limit (h, qx, qy) and the
+// cell's mean depth h0 (through the thin-limit threshold eps = h0 / 10), the
+// forward's branches frozen.
+__device__ __forceinline__ void rec_uv_adj(real h, real qx, real qy, bool thin, real tol, real h0,
+                                           real gu, real gv, real& g_h, real& g_qx, real& g_qy,
+                                           real& g_h0) {
+  const real eps = 0.1 * h0;
+  if (thin && eps > tol && h < eps) {
+    // u = k qx, v = k qy with k = 2 max(h, 0) / (h^2 + eps^2)
+    const real hp = h > 0.0 ? h : 0.0;
+    const real den = h * h + eps * eps;
+    const real k = 2.0 * hp / den;
+    g_qx += gu * k;
+    g_qy += gv * k;
+    const real g_k = gu * qx + gv * qy;
+    if (h > 0.0) g_h += g_k * 2.0 / den;
+    const real g_den = -g_k * k / den;
+    g_h += g_den * 2.0 * h;
+    g_h0 += g_den * 2.0 * eps * 0.1;
+  } else if (h > tol) {
+    const real u = qx / h, v = qy / h;
+    g_qx += gu / h;
+    g_qy += gv / h;
+    g_h -= (gu * u + gv * v) / h;
+  }
+}
+
+// Reverse-mode adjoint of side_rec: the gradient of gr . (h, u, v, hs) of the
+// record with respect to the side's four depth limits (E, W, N, S) and its
+// discharge limits (qx, qy), written to g[0..5].
+__device__ __noinline__ void side_rec_adj(const Prob& p, const real* h4, real qx, real qy,
+                                          real h0, int fo, const real* gr, real* g) {
+  const real tol = p.tol;
+  // the partially wet test and scale of pw_scale_t (limits W, E, S, N)
+  bool pw = false;
+  real sc = 1.0, sum = 0.0;
+  if (p.wd && h0 > tol && (h4[1] < 0.0 || h4[0] < 0.0 || h4[3] < 0.0 || h4[2] < 0.0)) {
+    pw = true;
+    const int order[4] = {1, 0, 3, 2};
+    for (int k = 0; k < 4; ++k) sum += h4[order[k]] > 0.0 ? h4[order[k]] : 0.0;
+    sc = h0 / (0.25 * sum);
+  }
+  const real hf = fo == 0 ? h4[0] : fo == 1 ? h4[1] : fo == 2 ? h4[2] : h4[3];
+  const real hp = hf > 0.0 ? hf : 0.0;
+  real g_hf = gr[0], g_h0 = 0.0, g_qx = 0.0, g_qy = 0.0;
+  // hs = sc max(h, 0) (partially wet) or max(h, 0)
+  const real g_hp = pw ? gr[3] * sc : gr[3];
+  const real g_sc = pw ? gr[3] * hp : 0.0;
+  if (hf > 0.0) g_hf += g_hp;
+  rec_uv_adj(hf, qx, qy, p.wd != 0, tol, h0, gr[1], gr[2], g_hf, g_qx, g_qy, g_h0);
+  real g4[4] = {0.0, 0.0, 0.0, 0.0};
+  if (pw) {  // sc = h0 / (sum / 4)
+    g_h0 += g_sc / (0.25 * sum);
+    const real g_sum = -g_sc * sc / sum;
+    for (int k = 0; k < 4; ++k)
+      if (h4[k] > 0.0) g4[k] += g_sum;
+  }
+  g4[fo] += g_hf;
+  // h0 carries the derivative of (hE + hW) / 2
+  g4[0] += 0.5 * g_h0;
+  g4[1] += 0.5 * g_h0;
+  for (int k = 0; k < 4; ++k) g[k] = g4[k];
+  g[4] = g_qx;
+  g[5] = g_qy;
+}
+
 // Face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at stage time
 // with hydrograph discharge Q, in real: its flux (FLUX) and the own side's
 // revised depth and bed level.
@@ -1036,26 +1103,26 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
   // The own terms depend on the raw limits only through the four face
   // velocities (u, v), and on the faces' h* and z* as inputs of their own: one
   // reverse sweep of the own terms gives the adjoints of all sixteen, and the
-  // velocities' are taken to the 12 raw limits in a pass of twelve
-  // derivatives over the records alone.
+  // velocities' are taken to the 12 raw limits by a reverse sweep of the
+  // records.
   real g_hs[4], g_zs[4], g_u[4], g_v[4];
   own_terms_adj(p, hsv, zsv, ru, rv, mu, g_hs, g_zs, g_u, g_v);
   for (int f = 0; f < 4; ++f) {
     OWN[(12 + 2 * f) * N + c] = g_hs[f];
     OWN[(13 + 2 * f) * N + c] = g_zs[f];
   }
-  Dual<12> dl[4][3];
+  // the records' velocities depend on each face's limit and, through the
+  // thin-limit threshold, on the mean depth (hE + hW) / 2
+  real glim[4][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  real g_h0 = 0.0;
+  const real h0v = In[c];
   for (int f = 0; f < 4; ++f)
-    for (int k = 0; k < 3; ++k) dl[f][k] = var<12>(lim[f][k], 3 * f + k);
-  const Dual<12> h0 = with_value(0.5 * (dl[0][0] + dl[1][0]), In[c]);
-  RecT<Dual<12>> rd[4];
-  cell_recs_t<Dual<12>>(p, c, dl[0], dl[1], dl[2], dl[3], h0, rd);
-  for (int q = 0; q < 12; ++q) {
-    real acc = 0.0;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) acc += g_u[f] * rd[f].u.d[q] + g_v[f] * rd[f].v.d[q];
-    OWN[q * N + c] = acc;
-  }
+    rec_uv_adj(lim[f][0], lim[f][1], lim[f][2], p.wd != 0, p.tol, h0v, g_u[f], g_v[f], glim[f][0],
+               glim[f][1], glim[f][2], g_h0);
+  glim[0][0] += 0.5 * g_h0;
+  glim[1][0] += 0.5 * g_h0;
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < 3; ++k) OWN[(3 * f + k) * N + c] = glim[f][k];
 }
 
 // One pass over the faces of a stage: face (left/lower cell a, right/upper cell
@@ -1119,26 +1186,14 @@ __global__ void adj_face_kernel(Prob p, int dir, const store* __restrict__ In,
     // The face's outputs depend on the inputs only through each side's record
     // (h, u, v, hs; its bed and partially wet flag are constants of the state).
     // Their adjoint is taken back to the eight record fields by one reverse
-    // sweep of the revision and flux, then to each side's six inputs in a pass
-    // of six derivatives over that side's record alone.
+    // sweep of the revision and flux, then to each side's six inputs by a
+    // reverse sweep of that side's record.
     const RecT<real> Ra = side_rec(p, ha4, qa[1], qa[2], In[ca], fa, za0);
     const RecT<real> Rb = side_rec(p, hb4, qb[1], qb[2], In[cb], fb, zb0);
     real grec[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     revise_flux_adj(Ra, Rb, y, p.g, p.tol, phi, pha, pza, phb, pzb, grec, grec + 4);
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-      const real* h4 = side == 0 ? ha4 : hb4;
-      const real* q3 = side == 0 ? qa : qb;
-      Dual<6> D4[4];
-      for (int q = 0; q < 4; ++q) D4[q] = var<6>(h4[q], q);
-      const RecT<Dual<6>> R = side_rec(p, D4, var<6>(q3[1], 4), var<6>(q3[2], 5),
-                                       In[side == 0 ? ca : cb], side == 0 ? fa : fb,
-                                       side == 0 ? za0 : zb0);
-      const real* gr = grec + 4 * side;
-      real* out = side == 0 ? la : lb;
-      for (int k = 0; k < 6; ++k)
-        out[k] = gr[0] * R.h.d[k] + gr[1] * R.u.d[k] + gr[2] * R.v.d[k] + gr[3] * R.hs.d[k];
-    }
+    side_rec_adj(p, ha4, qa[1], qa[2], In[ca], fa, grec, la);
+    side_rec_adj(p, hb4, qb[1], qb[2], In[cb], fb, grec + 4, lb);
   } else if (!(has_a && has_b)) {
     // boundary face: the outside state is the ghost of the inside cell's limit
     const bool inside_b = has_b;
