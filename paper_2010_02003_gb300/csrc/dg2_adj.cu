@@ -986,6 +986,70 @@ __device__ __forceinline__ void friction_cell(const T* m, const T& n, real dt, r
   out[QY0] = cy;
 }
 
+// Reverse-mode adjoint of one friction point (friction_point_t): given the
+// adjoints (wx, wy) of the updated discharges, adds the gradient into g_gn2dt,
+// g_h, g_qx, g_qy (a dry point is the identity).
+__device__ __forceinline__ void friction_point_adj(real gn2dt, real tol, real h, real qx, real qy,
+                                                   real wx, real wy, real& g_gn2dt, real& g_h,
+                                                   real& g_qx, real& g_qy) {
+  if (!(h > tol)) {
+    g_qx += wx;
+    g_qy += wy;
+    return;
+  }
+  const real qm = sqrt(qx * qx + qy * qy);
+  const real D = h * h * cbrt(h);  // h^(7/3)
+  const real den = 1.0 + gn2dt * qm / D;
+  const real ox = qx / den, oy = qy / den;
+  g_qx += wx / den;
+  g_qy += wy / den;
+  const real g_den = -(wx * ox + wy * oy) / den;
+  g_gn2dt += g_den * qm / D;
+  const real g_qm = g_den * gn2dt / D;
+  const real g_D = -g_den * gn2dt * qm / (D * D);
+  g_h += g_D * (7.0 / 3.0) * D / h;
+  if (qm > 0.0) {
+    g_qx += g_qm * qx / qm;
+    g_qy += g_qm * qy / qm;
+  }
+}
+
+// Reverse-mode adjoint of friction_cell: the gradient of ls . Fric(m; n) with
+// respect to the modes m (g_m) and the Manning n (g_n).
+__device__ __noinline__ void friction_cell_adj(const real* m, real n, real dt, real g, real tol,
+                                               const real* ls, real* g_m, real& g_n) {
+  const real gn2dt = dt * g * n * n;
+  real g_gn2dt = 0.0;
+  for (int k = 0; k < 9; ++k) g_m[k] = 0.0;
+  // depth modes pass through
+  g_m[H0] += ls[H0];
+  g_m[H1X] += ls[H1X];
+  g_m[H1Y] += ls[H1Y];
+  // centre
+  friction_point_adj(gn2dt, tol, m[H0], m[QX0], m[QY0], ls[QX0], ls[QY0], g_gn2dt, g_m[H0],
+                     g_m[QX0], g_m[QY0]);
+  const real r3 = 1.0 / 1.7320508075688772, hs3 = 0.5 * 1.7320508075688772;
+  for (int dd = 1; dd <= 2; ++dd) {
+    // out[3 + dd] = hs3 (xp - xm), out[6 + dd] = hs3 (yp - ym)
+    const real wx = hs3 * ls[3 + dd], wy = hs3 * ls[6 + dd];
+    const real h1 = m[dd], x1 = m[3 + dd], y1 = m[6 + dd];
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const real r = sgn == 0 ? r3 : -r3, w = sgn == 0 ? 1.0 : -1.0;
+      real gh = 0.0, gx = 0.0, gy = 0.0;
+      friction_point_adj(gn2dt, tol, m[H0] + h1 * r, m[QX0] + x1 * r, m[QY0] + y1 * r, w * wx,
+                         w * wy, g_gn2dt, gh, gx, gy);
+      g_m[H0] += gh;
+      g_m[dd] += gh * r;
+      g_m[QX0] += gx;
+      g_m[3 + dd] += gx * r;
+      g_m[QY0] += gy;
+      g_m[6 + dd] += gy * r;
+    }
+  }
+  // gn2dt = dt g n^2
+  g_n = g_gn2dt * 2.0 * dt * g * n;
+}
+
 // ---------------------------------------------------------------------------
 // Forward kernels (one thread per cell, dense planes)
 // ---------------------------------------------------------------------------
@@ -1311,20 +1375,11 @@ __global__ void adj_cell_kernel(Prob p, const store* __restrict__ OWN,
   real ls[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) ls[k] = half2[k] + (((m1 >> k) & 1u) ? lamU1[k * N + c] : 0.0) + a[k];
-  // friction: Us = Fric(U; n)
-  Dual<10> m[9], o[9];
-  for (int k = 0; k < 9; ++k) m[k] = var<10>(U[k * N + c], k);
-  const Dual<10> n = var<10>(p.Nm[c], 9);
-  friction_cell<Dual<10>>(m, n, dt, p.g, p.tol, o);
-  for (int k = 0; k < 9; ++k) {
-    real s = 0.0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) s += ls[q] * o[q].d[k];
-    out[k * N + c] = s;
-  }
-  real sn = 0.0;
-#pragma unroll
-  for (int q = 0; q < 9; ++q) sn += ls[q] * o[q].d[9];
+  // friction: Us = Fric(U; n), its adjoint by one reverse sweep
+  real m[9], gm[9], sn;
+  for (int k = 0; k < 9; ++k) m[k] = U[k * N + c];
+  friction_cell_adj(m, p.Nm[c], dt, p.g, p.tol, ls, gm, sn);
+  for (int k = 0; k < 9; ++k) out[k * N + c] = gm[k];
   gn[c] += sn;
 }
 
