@@ -851,9 +851,8 @@ __device__ __noinline__ void side_rec_adj(const Prob& p, const real* h4, real qx
 }
 
 // Face on side f (0 E, 1 W, 2 N, 3 S) of cell (i, j) of state U at stage time
-// with hydrograph discharge Q, in real: its flux (FLUX) and the own side's
-// revised depth and bed level.
-template <bool FLUX = true>
+// with hydrograph discharge Q, in real: its flux and the own side's revised
+// depth and bed level.
 __device__ void face_rev(const Prob& p, const store* __restrict__ U, int i, int j, int f, real Q,
                          const RecT<real>* own, F3T<real>& F, real& ho, real& zo) {
   const long long N = p.N, c = (long long)j * p.nx + i;
@@ -889,14 +888,16 @@ __device__ void face_rev(const Prob& p, const store* __restrict__ U, int i, int 
   const bool own_lower = f == 0 || f == 2;
   if (own_lower) revise_face_t(own[f], oth, p.tol, ra, rb, ha, za, hb, zb);
   else revise_face_t(oth, own[f], p.tol, ra, rb, ha, za, hb, zb);
-  if (FLUX) F = flux_face(ra, rb, f >= 2, p.g, p.tol);
+  F = flux_face(ra, rb, f >= 2, p.g, p.tol);
   ho = own_lower ? ha : hb;
   zo = own_lower ? za : zb;
 }
 
-// L(U) at cell (i, j) in real (Eq. 4 with the fluxes of its four faces).
+// L(U) at cell (i, j) in real (Eq. 4 with the fluxes of its four faces).  With
+// rev, also writes the revised depth and bed of each face (planes 2f, 2f + 1 of
+// faces E, W, N, S), which the reverse sweep's own-terms pass reads.
 __device__ void cell_operator(const Prob& p, const store* __restrict__ U, int i, int j, real t,
-                              real Q, real* L) {
+                              real Q, real* L, store* __restrict__ rev = nullptr) {
   const long long c = (long long)j * p.nx + i;
   RecT<real> r[4];
   recs_double(p, U, c, r);
@@ -906,6 +907,12 @@ __device__ void cell_operator(const Prob& p, const store* __restrict__ U, int i,
     face_rev(p, U, i, j, f, Q, r, F[f], hs[f], zs[f]);
     u[f] = r[f].u;
     v[f] = r[f].v;
+  }
+  if (rev) {
+    for (int f = 0; f < 4; ++f) {
+      rev[(2 * f) * p.N + c] = hs[f];
+      rev[(2 * f + 1) * p.N + c] = zs[f];
+    }
   }
   own_terms<real>(p, hs, zs, u, v, L);
   const F3T<real> FE = F[0], FW = F[1], GN = F[2], GS = F[3];
@@ -1070,13 +1077,13 @@ __global__ void fwd_friction_kernel(Prob p, const store* __restrict__ U, store* 
 template <int STAGE>
 __global__ void fwd_stage_kernel(Prob p, const store* __restrict__ Us, const store* __restrict__ U1,
                                  store* __restrict__ Uo, unsigned short* __restrict__ mask, real dt,
-                                 real t, real Q) {
+                                 real t, real Q, store* __restrict__ rev) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const int i = (int)(c % p.nx), j = (int)(c / p.nx);
   const store* In = STAGE == 1 ? Us : U1;
   real L[9], o[9];
-  cell_operator(p, In, i, j, t, Q, L);
+  cell_operator(p, In, i, j, t, Q, L, rev);
 #pragma unroll
   for (int k = 0; k < 9; ++k)
     o[k] = STAGE == 1 ? Us[k * p.N + c] + dt * L[k]
@@ -1133,14 +1140,14 @@ __device__ __forceinline__ void stage_mu(const store* __restrict__ lam, const un
 // terms (Eqs. 4-5 without the fluxes) with respect to its 12 raw limits
 // (faces E, W, N, S; h, qx, qy each) and to the revised depth h* and bed z* of
 // each of its four faces.  Writes OWN planes 0..11 (the raw limits' adjoints)
-// and 12..19 (h*, z* of faces E, W, N, S).
+// and 12..19 (h*, z* of faces E, W, N, S).  rev holds the faces' revised
+// depths and beds at this state, written by the stage's forward recomputation.
 __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store* __restrict__ lam,
-                               const unsigned short* __restrict__ mask, real w, real Q,
-                               store* __restrict__ OWN) {
+                               const unsigned short* __restrict__ mask, real w,
+                               const store* __restrict__ rev, store* __restrict__ OWN) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const long long N = p.N;
-  const int i = (int)(c % p.nx), j = (int)(c / p.nx);
   real mu[9];
   stage_mu(lam, mask, N, c, w, mu);
   bool any = false;
@@ -1152,14 +1159,15 @@ __global__ void adj_own_kernel(Prob p, const store* __restrict__ In, const store
   }
   real lim[4][3];
   for (int f = 0; f < 4; ++f) raw_limit(In, N, c, f, lim[f][0], lim[f][1], lim[f][2]);
-  // the faces' revised depths and beds at this state
+  // the faces' revised depths and beds (from the forward) and the records'
+  // velocities at this state
   real hsv[4], zsv[4], ru[4], rv[4];
   {
     RecT<real> r[4];
     recs_double(p, In, c, r);
     for (int f = 0; f < 4; ++f) {
-      F3T<real> F;
-      face_rev<false>(p, In, i, j, f, Q, r, F, hsv[f], zsv[f]);  // revised values only
+      hsv[f] = rev[(2 * f) * N + c];
+      zsv[f] = rev[(2 * f + 1) * N + c];
       ru[f] = r[f].u;
       rv[f] = r[f].v;
     }
@@ -1436,7 +1444,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct AdjLayout {
   size_t off_Z, off_Nm, off_U0, off_snap, off_work, off_Us, off_U1, off_m1, off_m2, off_lam,
-      off_lamU1, off_tmp, off_own, off_FXL, off_FXR, off_FYL, off_FYR, off_gq_face, off_gn, off_gidx,
+      off_lamU1, off_tmp, off_own, off_rev, off_FXL, off_FXR, off_FYL, off_FYR, off_gq_face, off_gn, off_gidx,
       off_gxi, off_geta, off_gh, off_gq_step, total;
   long long N, nfx, nfy, plane9;
   int nsnap, ngq;
@@ -1470,6 +1478,7 @@ bool adj_layout(int nx, int ny, int nsnap, int max_gauges, int max_steps, AdjLay
   L.off_lamU1 = take(s9);
   L.off_tmp = take(s9);
   L.off_own = take(20 * (size_t)L.N * sizeof(store));
+  L.off_rev = take(16 * (size_t)L.N * sizeof(store));
   L.off_FXL = take(6 * (size_t)L.nfx * sizeof(store));
   L.off_FXR = take(6 * (size_t)L.nfx * sizeof(store));
   L.off_FYL = take(6 * (size_t)L.nfy * sizeof(store));
@@ -1577,8 +1586,9 @@ int launch_ok() {
 
 unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
-// One forward step k from Uin to Uout (Us, U1, masks left in the workspace).
-int fwd_step(Ctx* a, int k, double t, const store* Uin, store* Uout) {
+// One forward step k from Uin to Uout (Us, U1, masks left in the workspace;
+// with keep_rev also each stage's revised face depths and beds).
+int fwd_step(Ctx* a, int k, double t, const store* Uin, store* Uout, bool keep_rev = false) {
   const double dt = a->dts[k];
   store* Us = dptr(a, a->lay.off_Us);
   store* U1 = dptr(a, a->lay.off_U1);
@@ -1586,8 +1596,12 @@ int fwd_step(Ctx* a, int k, double t, const store* Uin, store* Uout) {
   unsigned short* m2 = (unsigned short*)(a->ws + a->lay.off_m2);
   const unsigned nb = blocks(a->lay.N);
   fwd_friction_kernel<<<nb, 256, 0, a->st>>>(a->p, Uin, Us, dt);
-  fwd_stage_kernel<1><<<nb, 256, 0, a->st>>>(a->p, Us, nullptr, U1, m1, dt, t, hydro(a, t));
-  fwd_stage_kernel<2><<<nb, 256, 0, a->st>>>(a->p, Us, U1, Uout, m2, dt, t + dt, hydro(a, t + dt));
+  store* rev = dptr(a, a->lay.off_rev);
+  const long long r8 = 8 * (long long)a->lay.N;
+  fwd_stage_kernel<1><<<nb, 256, 0, a->st>>>(a->p, Us, nullptr, U1, m1, dt, t, hydro(a, t),
+                                             keep_rev ? rev : nullptr);
+  fwd_stage_kernel<2><<<nb, 256, 0, a->st>>>(a->p, Us, U1, Uout, m2, dt, t + dt, hydro(a, t + dt),
+                                             keep_rev ? rev + r8 : nullptr);
   a->fwd_steps++;
   return launch_ok();
 }
@@ -1617,7 +1631,7 @@ int rev_step(Ctx* a, int k, const store* Uk) {
   store* w = dptr(a, L.off_work);
   unsigned short* m1 = (unsigned short*)(a->ws + L.off_m1);
   unsigned short* m2 = (unsigned short*)(a->ws + L.off_m2);
-  int r = fwd_step(a, k, t, Uk, w);  // Us, U1, masks of this step
+  int r = fwd_step(a, k, t, Uk, w, true);  // Us, U1, masks, revised faces of this step
   if (r) return r;
   a->fwd_steps--;                     // counted as part of the reverse step
   store* lam = dptr(a, L.off_lam);
@@ -1634,7 +1648,8 @@ int rev_step(Ctx* a, int k, const store* Uk) {
   const unsigned nb = blocks(L.N);
   // stage 2 at U1, time t + dt: mu2 = dt/2 mask2 lam
   ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(store), a->st));
-  adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, U1, lam, m2, 0.5 * dt, hydro(a, t + dt), OWN);
+  const store* rev = dptr(a, L.off_rev);
+  adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, U1, lam, m2, 0.5 * dt, rev + 8 * (long long)L.N, OWN);
   adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
                                                     OWN, FXL, FXR, gqf);
   adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, U1, lam, m2, 0.5 * dt, hydro(a, t + dt),
@@ -1644,7 +1659,7 @@ int rev_step(Ctx* a, int k, const store* Uk) {
                                             nullptr, dt, lamU1, gn);
   // stage 1 at Us, time t: mu1 = dt mask1 lamU1
   ACU(cudaMemsetAsync(gqf, 0, (size_t)L.ngq * sizeof(store), a->st));
-  adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, Us, lamU1, m1, dt, hydro(a, t), OWN);
+  adj_own_kernel<<<nb, 256, 0, a->st>>>(a->p, Us, lamU1, m1, dt, rev, OWN);
   adj_face_kernel<<<blocks(L.nfx), 256, 0, a->st>>>(a->p, 0, Us, lamU1, m1, dt, hydro(a, t), OWN, FXL,
                                                     FXR, gqf);
   adj_face_kernel<<<blocks(L.nfy), 256, 0, a->st>>>(a->p, 1, Us, lamU1, m1, dt, hydro(a, t), OWN, FYL,
