@@ -354,7 +354,9 @@ int dg2_ens_destroy(dg2_ens *ens);
 typedef struct dg2_adj dg2_adj;
 
 /* Workspace bytes (0 if a size is invalid: nx, ny, nsnap, max_steps >= 1,
- * max_gauges >= 0).  About (nsnap + 10) state-sized buffers of 9 planes. */
+ * max_gauges >= 0).  About (nsnap + 15) state-sized buffers of 9 planes: the
+ * snapshots, the step's states and adjoints, the own terms' and faces'
+ * adjoints and the revised faces of the step being reversed. */
 size_t dg2_adj_workspace_bytes(int nx, int ny, int nsnap, int max_gauges, int max_steps);
 
 /* params: g, tol_dry, bc[4], wetdry (the step's face revision, either) and
