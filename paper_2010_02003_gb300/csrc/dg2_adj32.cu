@@ -9,8 +9,9 @@
 // checkpointed states, so twice the snapshots fit.
 #define DG2_ADJ_STORE float
 #define DG2_ADJ_NS adj32
-// arithmetic type of this build (FP64; DG2_ADJ32_ARITH=float builds the all-FP32
-// variant the design notes measure)
+// arithmetic type of this translation unit (FP64; DG2_ADJ32_ARITH=float compiles an
+// all-FP32 variant, which measured unusable for calibration: the hydrostatic
+// pressure and bed term of Eqs. 4-5 cancel only to working precision)
 #ifdef DG2_ADJ32_ARITH
 #define DG2_ADJ_ARITH DG2_ADJ32_ARITH
 #endif
